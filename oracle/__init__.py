@@ -1,0 +1,207 @@
+"""FP64 CPU oracle for the QFCA hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
+baseline leg may import this package.  The product path (the CUDA library and
+its binding) never imports, links or calls it, and it imports nothing from the
+product package.
+
+The arithmetic lives in ``qfca_oracle.c`` (plain C, FP64, following the
+paper's definitions step by step); this module compiles it with gcc when
+needed and wraps it with ctypes.  Every function cites the passage of
+arXiv 2510.15602 it follows.
+
+Parity status: ``fit`` (Sec. 3.3), ``project`` (Sec. 3.3), ``quantize``
+(Sec. 3.1), ``ref_hist`` and ``score`` (Sec. 3.1, supplement's Wasserstein
+closed form) are each pinned by tests against closed forms, library routines
+or brute force (tests/test_oracle_pins.py).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qfca_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+NCHW = 0
+NHWC = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C source into ``oracle/_build/liboracle.so``."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c99",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            I = ctypes.c_int
+            L = ctypes.c_long
+            lib.orc_covariance.argtypes = [P, I, I, I, I, P, P]
+            lib.orc_covariance.restype = None
+            lib.orc_eigh_topd.argtypes = [P, I, I, P, P, P]
+            lib.orc_eigh_topd.restype = I
+            lib.orc_fit.argtypes = [P, I, I, I, I, I, P, P, P, P, P]
+            lib.orc_fit.restype = I
+            lib.orc_project.argtypes = [P, I, I, I, I, P, P, I, P]
+            lib.orc_project.restype = None
+            lib.orc_quantize.argtypes = [P, I, L, I, I, P, P, I, P, P, P]
+            lib.orc_quantize.restype = None
+            lib.orc_ref_hist.argtypes = [P, I, L, I, P]
+            lib.orc_ref_hist.restype = None
+            lib.orc_window_hist.argtypes = [P, I, I, I, I, I, I, P]
+            lib.orc_window_hist.restype = L
+            lib.orc_score.argtypes = [P, I, I, I, I, I, P, ctypes.c_uint64, P, P, P]
+            lib.orc_score.restype = I
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _fmap(X: np.ndarray, layout: int):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    if layout == NCHW:
+        C, H, W = X.shape
+    else:
+        H, W, C = X.shape
+    return X, C, H, W
+
+
+def covariance(X: np.ndarray, layout: int = NCHW):
+    """Mean and 1/N covariance of the channels (Sec. 3.3, single-image PCA)."""
+    X, C, H, W = _fmap(X, layout)
+    mean = np.zeros(C, np.float64)
+    cov = np.zeros((C, C), np.float64)
+    _load().orc_covariance(_p(X), layout, H, W, C, _p(mean), _p(cov))
+    return mean, cov
+
+
+def eigh_topd(S: np.ndarray, d: int):
+    """Cyclic-Jacobi eigendecomposition, top-d descending, sign-normalised."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    C = S.shape[0]
+    V = np.zeros((C, d), np.float64)
+    ev = np.zeros(d, np.float64)
+    allev = np.zeros(C, np.float64)
+    rc = _load().orc_eigh_topd(_p(S), C, d, _p(V), _p(ev), _p(allev))
+    if rc < 0:
+        raise MemoryError("oracle eigh_topd")
+    return V, ev, allev
+
+
+def fit(X: np.ndarray, d: int, layout: int = NCHW):
+    """PCA fit on one image (Sec. 3.3): returns mean[C], V[C,d], eigvals[d], all eigvals[C]."""
+    X, C, H, W = _fmap(X, layout)
+    mean = np.zeros(C, np.float64)
+    V = np.zeros((C, d), np.float64)
+    ev = np.zeros(d, np.float64)
+    allev = np.zeros(C, np.float64)
+    rc = _load().orc_fit(_p(X), layout, H, W, C, d, _p(mean), _p(V), _p(ev), _p(allev), None)
+    if rc < 0:
+        raise MemoryError("oracle fit")
+    return mean, V, ev, allev
+
+
+def project(X: np.ndarray, mean: np.ndarray, V: np.ndarray, layout: int = NCHW) -> np.ndarray:
+    """Principal components Y[k, y, x] = sum_c (x_c - mean_c) V[c, k] in FP64 (Sec. 3.3)."""
+    X, C, H, W = _fmap(X, layout)
+    mean = np.ascontiguousarray(mean, np.float64)
+    V = np.ascontiguousarray(V, np.float64)
+    d = V.shape[1]
+    Y = np.zeros((d, H, W), np.float64)
+    _load().orc_project(_p(X), layout, H, W, C, _p(mean), _p(V), d, _p(Y))
+    return Y
+
+
+def quantize(Y: np.ndarray, B: int, lo=None, hi=None, fp32_decision: bool = False):
+    """Uniform quantisation into B bins (Sec. 3.1).
+
+    With ``lo``/``hi`` None the range is each component's image-wide min/max,
+    otherwise the given fixed range (values clamped).  Returns (q uint8
+    [d,H,W], lo[d], hi[d]).
+    """
+    Y = np.ascontiguousarray(Y, np.float64)
+    d = Y.shape[0]
+    N = int(np.prod(Y.shape[1:]))
+    q = np.zeros(Y.shape, np.uint8)
+    lo_out = np.zeros(d, np.float64)
+    hi_out = np.zeros(d, np.float64)
+    mode = 0 if lo is None else 1
+    lo_in = np.ascontiguousarray(lo if lo is not None else np.zeros(d), np.float64)
+    hi_in = np.ascontiguousarray(hi if hi is not None else np.zeros(d), np.float64)
+    _load().orc_quantize(_p(Y), d, N, B, mode, _p(lo_in), _p(hi_in), int(bool(fp32_decision)),
+                         _p(lo_out), _p(hi_out), _p(q))
+    return q, lo_out, hi_out
+
+
+def ref_hist(q: np.ndarray, B: int) -> np.ndarray:
+    """Reference histogram R[k, b] = #pixels of component k in bin b."""
+    q = np.ascontiguousarray(q, np.uint8)
+    d = q.shape[0]
+    N = int(np.prod(q.shape[1:]))
+    R = np.zeros((d, B), np.uint32)
+    _load().orc_ref_hist(_p(q), d, N, B, _p(R))
+    return R
+
+
+def window_hist(qk: np.ndarray, B: int, r: int, y: int, x: int):
+    """Histogram of one component plane over the clipped window of (y, x) (Sec. 3.1).
+
+    Returns (L int64 [B], N_loc).
+    """
+    qk = np.ascontiguousarray(qk, np.uint8)
+    H, W = qk.shape
+    L = np.zeros(B, np.int64)
+    n = _load().orc_window_hist(_p(qk), H, W, B, r, y, x, _p(L))
+    return L, int(n)
+
+
+def score(q: np.ndarray, B: int, r: int, R: np.ndarray, Nref: int | None = None):
+    """Window histograms + 1-D EMD to R + mean over components (Sec. 3.1, Sec. 3).
+
+    Returns (score float64 [H,W], numer int64 [d,H,W], nloc int32 [H,W]).
+    """
+    q = np.ascontiguousarray(q, np.uint8)
+    d, H, W = q.shape
+    R = np.ascontiguousarray(R, np.uint32)
+    if Nref is None:
+        Nref = int(R[0].sum())
+    s = np.zeros((H, W), np.float64)
+    numer = np.zeros((d, H, W), np.int64)
+    nloc = np.zeros((H, W), np.int32)
+    rc = _load().orc_score(_p(q), d, H, W, B, r, _p(R), int(Nref), _p(s), _p(numer), _p(nloc))
+    if rc < 0:
+        raise MemoryError("oracle score")
+    return s, numer, nloc
+
+
+def pipeline(X: np.ndarray, d: int, B: int, r: int, layout: int = NCHW):
+    """The whole path on one image: fit, project, quantize, ref hist, score."""
+    mean, V, ev, allev = fit(X, d, layout)
+    Y = project(X, mean, V, layout)
+    q, lo, hi = quantize(Y, B)
+    R = ref_hist(q, B)
+    H, W = q.shape[1:]
+    s, numer, nloc = score(q, B, r, R, H * W)
+    return dict(mean=mean, V=V, eigvals=ev, all_eigvals=allev, Y=Y, q=q, lo=lo, hi=hi, R=R,
+                score=s, numer=numer, nloc=nloc)
