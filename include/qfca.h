@@ -1,0 +1,156 @@
+/*
+ * qfca.h -- C ABI of libqfca.so, the GB300 (sm_103a) implementation of the
+ * hot path of quantized feature correspondence analysis (QFCA, arXiv
+ * 2510.15602): PCA projection of a dense feature map, per-component uniform
+ * quantisation, per-pixel sliding-window histograms and the 1-D earth mover's
+ * distance to a reference histogram, averaged over components into a score
+ * map.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns a qfca_status.  Arguments are validated on the
+ *    host before anything is enqueued; an invalid argument returns
+ *    QFCA_ERR_INVALID_ARG and enqueues nothing.
+ *  - Tensor arguments are DEVICE pointers owned by the caller unless stated
+ *    otherwise.  The library owns only the context, its workspace (device
+ *    scratch memory it allocates itself) and the resident class table.
+ *  - Work is enqueued asynchronously on the caller's CUDA stream (`stream`,
+ *    a cudaStream_t passed as void*, NULL = legacy default stream).  Results
+ *    are valid once that stream has reached the enqueued work.
+ *  - Calls that share one context share its workspace: issue them on one
+ *    stream (or synchronise between streams).  Use one context per stream for
+ *    concurrent single-image calls, or the batch / serving entry points.
+ *  - A CUDA error (launch failure, device fault) returns QFCA_ERR_CUDA; it is
+ *    sticky: destroy the context.  Messages: qfca_status_string(),
+ *    qfca_last_error().  No C++ exception crosses this ABI.
+ *
+ * Notation (the paper's, Sec. 3): feature map F(I) in R^{C x H x W};
+ * d principal components; B quantisation bins ("N" in Sec. 3.1); window
+ * radius r (patch size 2r+1); reference histogram R_k[b] with mass N_ref;
+ * local window histogram P_k[b] with mass N_loc (the window clipped to the
+ * image).
+ */
+#ifndef QFCA_H
+#define QFCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int qfca_status;
+#define QFCA_OK 0
+#define QFCA_PENDING 1
+#define QFCA_ERR_INVALID_ARG (-1)
+#define QFCA_ERR_UNSUPPORTED (-2)
+#define QFCA_ERR_OOM (-3)
+#define QFCA_ERR_CUDA (-4)
+#define QFCA_ERR_TIMEOUT (-5)
+#define QFCA_ERR_BUSY (-6)
+
+/* Feature-map layouts.  NCHW = [C][H][W] (channel planes), NHWC = [H][W][C]. */
+#define QFCA_NCHW 0
+#define QFCA_NHWC 1
+
+/* Projection precisions.  All accumulate in FP32. */
+#define QFCA_F32 0       /* FP32 SIMT FFMA */
+#define QFCA_BF16 1      /* BF16 operands on tcgen05 tensor cores */
+#define QFCA_FP8_E4M3 2  /* e4m3 operands, per-channel scales (reserved) */
+
+/* Quantisation ranges. */
+#define QFCA_RANGE_IMAGE 0  /* lo/hi = each component's min/max over the image */
+#define QFCA_RANGE_FIXED 1  /* lo/hi given by the caller; values clamped */
+
+typedef struct qfca_ctx qfca_ctx;
+
+/* One FP32 feature map F(I) (Sec. 3.1: F(I) in R^{C x H x W}). */
+typedef struct {
+    int H, W, C;
+    int layout; /* QFCA_NCHW or QFCA_NHWC */
+} qfca_fmap;
+
+/* A PCA basis (Sec. 3.3): device pointers, FP64.
+ *   mean    [C]      channel means
+ *   V       [C][d]   row-major; column k is principal axis k (unit norm,
+ *                    sign: largest-magnitude entry positive)
+ *   eigvals [d]      descending eigenvalues of the 1/N covariance        */
+typedef struct {
+    double *mean;
+    double *V;
+    double *eigvals;
+} qfca_basis;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  `workspace_bytes` is the initial
+ * workspace size (0 = a default); the workspace grows on demand (a blocking
+ * cudaMalloc) the first time a larger problem arrives, so warm up once per
+ * shape before timing or graph capture.  *out receives the context. */
+qfca_status qfca_create(int device, size_t workspace_bytes, qfca_ctx **out);
+
+/* Destroy a context and free its workspace (synchronises the device). */
+qfca_status qfca_destroy(qfca_ctx *ctx);
+
+/* Static description of a status code. */
+const char *qfca_status_string(qfca_status s);
+
+/* Last error message recorded on `ctx` ("" if none).  Valid until the next
+ * call on the same context. */
+const char *qfca_last_error(const qfca_ctx *ctx);
+
+/* Library version string. */
+const char *qfca_version(void);
+
+/* ---------------------------------------------------------------- the path */
+
+/* qfca_fit_pca -- single-image PCA fit (Sec. 3.3; the paper fits PCA on the
+ * features of the one input image).
+ *   X     device FP32 feature map described by `desc`.
+ *   d     number of components, 1 <= d <= min(C, 64).
+ *   out   device pointers receiving mean[C], V[C][d], eigvals[d] (FP64).
+ * Computes mu = (1/N) sum_p x_p and Sigma = (1/N) sum_p (x_p - mu)(x_p - mu)^T
+ * with FP64 accumulation, then the top-d eigenpairs of Sigma in FP64
+ * (Householder tridiagonalisation, bisection, inverse iteration).
+ * Requires 2 <= C <= 512 and H*W >= 2. */
+qfca_status qfca_fit_pca(qfca_ctx *ctx, const float *X, qfca_fmap desc, int d,
+                         const qfca_basis *out, void *stream);
+
+/* qfca_quantize -- projection Y = (X - mean) V (Sec. 3.3) followed by uniform
+ * quantisation of each component into B equally spaced bins (Sec. 3.1) and
+ * the reference histogram.
+ *   precision   QFCA_F32 or QFCA_BF16 (FP32 accumulation in both).
+ *   range_mode  QFCA_RANGE_IMAGE: lo_k/hi_k = min/max of component k;
+ *               QFCA_RANGE_FIXED: lo_in/hi_in (device f32[d]) are used and
+ *               values are clamped into [0, B-1].
+ *   bins        device u8 [d][H][pitch]; pitch >= W and a multiple of 16.
+ *               q = (int)(((y - lo)/(hi - lo)) * B) in FP32, clamped to
+ *               [0, B-1]; hi == lo gives 0.
+ *   lo_out, hi_out   device f32[d] (may be NULL).
+ *   ref_hist_out     device u32 [d][B] (may be NULL): R_k[b] = #{p : q_kp = b}.
+ *   Y_out            device f32 [d][H*W] (may be NULL): the projection.
+ * Requires 2 <= B <= 255, d <= 64. */
+qfca_status qfca_quantize(qfca_ctx *ctx, const float *X, qfca_fmap desc, const qfca_basis *basis,
+                          int d, int B, int precision, int range_mode, const float *lo_in,
+                          const float *hi_in, uint8_t *bins, int pitch, float *lo_out,
+                          float *hi_out, uint32_t *ref_hist_out, float *Y_out, void *stream);
+
+/* qfca_score -- per-pixel window histogram and 1-D EMD against the
+ * reference, averaged over the d components (Sec. 3.1; W1 closed form in
+ * the supplement).  For pixel p with clipped window of N_loc pixels:
+ *   D_k(p) = sum_{b=0}^{B-1} |cumP_b * N_ref - cumR_b * N_loc|   (exact),
+ *   score(p) = (sum_k D_k(p)) / (d * N_loc * N_ref)              (FP32 out).
+ *   bins       device u8 [d][H][pitch]; values >= B are treated as B-1.
+ *   ref_hist   device u32 [d][B]; every row sums to ref_total = N_ref.
+ *   score      device f32 [H][W].
+ *   numer_out  device u64 [d][H][W] or NULL: the exact D_k(p).
+ * Requires 1 <= r, 2 <= B <= 255, (2r+1) <= 127, d <= 64. */
+qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pitch, int d, int B,
+                       int r, const uint32_t *ref_hist, uint32_t ref_total, float *score,
+                       uint64_t *numer_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QFCA_H */

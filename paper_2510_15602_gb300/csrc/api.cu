@@ -1,0 +1,244 @@
+// api.cu -- host side of the C ABI (include/qfca.h): context, workspace,
+// argument validation, and the enqueueing of the kernels on the caller's
+// stream.  No C++ exception crosses the ABI; every entry point returns a
+// qfca_status and records a message on the context.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <mutex>
+#include <string>
+
+#include "internal.cuh"
+
+struct qfca_ctx {
+    int device = 0;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool sticky = false;
+    std::string err;
+    std::mutex mu;
+};
+
+namespace {
+
+using namespace qfca;
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+qfca_status fail(qfca_ctx *ctx, qfca_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) {
+        ctx->err = buf;
+        if (s == QFCA_ERR_CUDA) ctx->sticky = true;
+    }
+    return s;
+}
+
+qfca_status cuda_fail(qfca_ctx *ctx, cudaError_t e, const char *where) {
+    return fail(ctx, QFCA_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// Grow the context workspace to at least `need` bytes (blocking; frees the old one).
+qfca_status ensure_ws(qfca_ctx *ctx, size_t need) {
+    if (need <= ctx->ws_bytes) return QFCA_OK;
+    if (ctx->ws) {
+        cudaError_t e = cudaFree(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFree(workspace)");
+    }
+    size_t sz = align_up(need + need / 4, 1 << 20);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sz);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, QFCA_ERR_OOM, "workspace of %zu bytes: %s", sz, cudaGetErrorString(e));
+    }
+    ctx->ws = p;
+    ctx->ws_bytes = sz;
+    return QFCA_OK;
+}
+
+qfca_status check_ctx(qfca_ctx *ctx) {
+    if (!ctx) return QFCA_ERR_INVALID_ARG;
+    if (ctx->sticky) return fail(ctx, QFCA_ERR_CUDA, "context has a sticky CUDA error: %s", ctx->err.c_str());
+    return QFCA_OK;
+}
+
+qfca_status check_fmap(qfca_ctx *ctx, const float *X, const qfca_fmap &m) {
+    if (!X) return fail(ctx, QFCA_ERR_INVALID_ARG, "X is NULL");
+    if (m.layout != QFCA_NCHW && m.layout != QFCA_NHWC) return fail(ctx, QFCA_ERR_INVALID_ARG, "bad layout %d", m.layout);
+    if (m.H < 1 || m.W < 1 || (long)m.H * m.W < 2) return fail(ctx, QFCA_ERR_INVALID_ARG, "bad H x W = %d x %d", m.H, m.W);
+    if ((long)m.H * m.W > (1L << 31) - 1) return fail(ctx, QFCA_ERR_UNSUPPORTED, "H*W too large");
+    if (m.C < 2 || m.C > kMaxC) return fail(ctx, QFCA_ERR_UNSUPPORTED, "C = %d outside [2, %d]", m.C, kMaxC);
+    return QFCA_OK;
+}
+
+size_t bytes_mmkeys(int d) { return align_up(sizeof(uint32_t) * 2 * d, 256); }
+
+}  // namespace
+
+extern "C" {
+
+const char *qfca_version(void) { return "qfca-gb300 0.1 (sm_103a)"; }
+
+const char *qfca_status_string(qfca_status s) {
+    switch (s) {
+        case QFCA_OK: return "QFCA_OK";
+        case QFCA_PENDING: return "QFCA_PENDING";
+        case QFCA_ERR_INVALID_ARG: return "QFCA_ERR_INVALID_ARG";
+        case QFCA_ERR_UNSUPPORTED: return "QFCA_ERR_UNSUPPORTED";
+        case QFCA_ERR_OOM: return "QFCA_ERR_OOM";
+        case QFCA_ERR_CUDA: return "QFCA_ERR_CUDA";
+        case QFCA_ERR_TIMEOUT: return "QFCA_ERR_TIMEOUT";
+        case QFCA_ERR_BUSY: return "QFCA_ERR_BUSY";
+        default: return "QFCA_ERR_UNKNOWN";
+    }
+}
+
+const char *qfca_last_error(const qfca_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+qfca_status qfca_create(int device, size_t workspace_bytes, qfca_ctx **out) {
+    if (!out) return QFCA_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return QFCA_ERR_CUDA;
+    }
+    if (device < 0 || device >= n) return QFCA_ERR_INVALID_ARG;
+    qfca_ctx *ctx = new (std::nothrow) qfca_ctx();
+    if (!ctx) return QFCA_ERR_OOM;
+    ctx->device = device;
+    DeviceGuard g(device);
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return QFCA_ERR_CUDA;
+    }
+    if (prop.major * 10 + prop.minor < 100) {
+        delete ctx;
+        return QFCA_ERR_UNSUPPORTED;
+    }
+    const qfca_status s = ensure_ws(ctx, workspace_bytes ? workspace_bytes : (64u << 20));
+    if (s != QFCA_OK) {
+        delete ctx;
+        return s;
+    }
+    *out = ctx;
+    return QFCA_OK;
+}
+
+qfca_status qfca_destroy(qfca_ctx *ctx) {
+    if (!ctx) return QFCA_ERR_INVALID_ARG;
+    {
+        DeviceGuard g(ctx->device);
+        if (ctx->ws) {
+            cudaDeviceSynchronize();
+            cudaFree(ctx->ws);
+        }
+    }
+    delete ctx;
+    return QFCA_OK;
+}
+
+qfca_status qfca_fit_pca(qfca_ctx *ctx, const float *X, qfca_fmap desc, int d, const qfca_basis *out,
+                         void *stream) {
+    qfca_status s = check_ctx(ctx);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if ((s = check_fmap(ctx, X, desc))) return s;
+    if (!out || !out->mean || !out->V || !out->eigvals) return fail(ctx, QFCA_ERR_INVALID_ARG, "basis pointers NULL");
+    if (d < 1 || d > desc.C || d > kMaxD) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, min(C, %d)]", d, kMaxD);
+    DeviceGuard g(ctx->device);
+    const long N = (long)desc.H * desc.W;
+    if ((s = ensure_ws(ctx, fit_workspace_bytes(desc.C, N, d)))) return s;
+    cudaError_t e = launch_fit(X, desc.layout, desc.H, desc.W, desc.C, d, out->mean, out->V, out->eigvals, ctx->ws,
+                               (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_fit_pca");
+    return QFCA_OK;
+}
+
+qfca_status qfca_quantize(qfca_ctx *ctx, const float *X, qfca_fmap desc, const qfca_basis *basis, int d, int B,
+                          int precision, int range_mode, const float *lo_in, const float *hi_in, uint8_t *bins,
+                          int pitch, float *lo_out, float *hi_out, uint32_t *ref_hist_out, float *Y_out,
+                          void *stream) {
+    qfca_status s = check_ctx(ctx);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if ((s = check_fmap(ctx, X, desc))) return s;
+    if (!basis || !basis->mean || !basis->V) return fail(ctx, QFCA_ERR_INVALID_ARG, "basis NULL");
+    if (d < 1 || d > desc.C || d > kMaxD) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, min(C, %d)]", d, kMaxD);
+    if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
+    if (precision != QFCA_F32 && precision != QFCA_BF16)
+        return fail(ctx, precision == QFCA_FP8_E4M3 ? QFCA_ERR_UNSUPPORTED : QFCA_ERR_INVALID_ARG,
+                    "precision %d not available", precision);
+    if (range_mode != QFCA_RANGE_IMAGE && range_mode != QFCA_RANGE_FIXED)
+        return fail(ctx, QFCA_ERR_INVALID_ARG, "bad range_mode %d", range_mode);
+    if (range_mode == QFCA_RANGE_FIXED && (!lo_in || !hi_in))
+        return fail(ctx, QFCA_ERR_INVALID_ARG, "fixed range needs lo_in and hi_in");
+    if (!bins) return fail(ctx, QFCA_ERR_INVALID_ARG, "bins NULL");
+    if (pitch < desc.W || pitch % 16 != 0) return fail(ctx, QFCA_ERR_INVALID_ARG, "pitch %d must be >= W and a multiple of 16", pitch);
+    DeviceGuard g(ctx->device);
+    const long N = (long)desc.H * desc.W;
+    const size_t o_mm = 0;
+    const size_t o_y = o_mm + bytes_mmkeys(d);
+    const size_t o_p = o_y + (Y_out ? 0 : align_up(sizeof(float) * d * N, 256));
+    if ((s = ensure_ws(ctx, o_p + project_workspace_bytes(desc.C, N, d)))) return s;
+    char *base = (char *)ctx->ws;
+    uint32_t *mm = (uint32_t *)(base + o_mm);
+    float *Y = Y_out ? Y_out : (float *)(base + o_y);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_project(X, desc.layout, desc.H, desc.W, desc.C, basis->mean, basis->V, d, precision, Y, mm,
+                                   base + o_p, st);
+    if (e == cudaErrorNotSupported) {
+        cudaGetLastError();
+        return fail(ctx, QFCA_ERR_UNSUPPORTED, "projection precision %d not supported for this shape", precision);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_quantize/project");
+    e = launch_quantize(Y, N, desc.H, desc.W, d, B, range_mode, mm, lo_in, hi_in, bins, pitch, lo_out, hi_out,
+                        ref_hist_out, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_quantize/quantize");
+    return QFCA_OK;
+}
+
+qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pitch, int d, int B, int r,
+                       const uint32_t *ref_hist, uint32_t ref_total, float *score, uint64_t *numer_out,
+                       void *stream) {
+    qfca_status s = check_ctx(ctx);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!bins || !ref_hist || !score) return fail(ctx, QFCA_ERR_INVALID_ARG, "NULL pointer");
+    if (H < 1 || W < 1) return fail(ctx, QFCA_ERR_INVALID_ARG, "bad H x W");
+    if (pitch < W || pitch % 16 != 0) return fail(ctx, QFCA_ERR_INVALID_ARG, "pitch %d must be >= W and a multiple of 16", pitch);
+    if (d < 1 || d > kMaxD) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, %d]", d, kMaxD);
+    if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
+    if (r < 1 || 2 * r + 1 > 127) return fail(ctx, QFCA_ERR_INVALID_ARG, "r = %d outside [1, 63]", r);
+    if (ref_total < 1) return fail(ctx, QFCA_ERR_INVALID_ARG, "ref_total must be >= 1");
+    DeviceGuard g(ctx->device);
+    if ((s = ensure_ws(ctx, score_workspace_bytes(H, W)))) return s;
+    cudaError_t e = launch_score_ws(bins, H, W, pitch, d, B, r, ref_hist, ref_total, score, numer_out, ctx->ws,
+                                    (cudaStream_t)stream);
+    if (e == cudaErrorNotSupported)
+        return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d needs more shared memory than a CTA has", B, r);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_score");
+    return QFCA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// internal.cuh -- declarations shared by the translation units of libqfca.so.
+// Not part of the public ABI (include/qfca.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/qfca.h"
+
+namespace qfca {
+
+constexpr int kMaxC = 512;   // channels supported by the fit and projection
+constexpr int kMaxD = 64;    // components
+constexpr int kMaxB = 255;   // bins
+
+// ------------------------------------------------------------------ fit (fit.cu)
+
+// Workspace bytes needed by one fit of a C-channel map of N pixels.
+size_t fit_workspace_bytes(int C, long N, int d);
+
+// Enqueue the PCA fit of one image.  ws: device scratch of fit_workspace_bytes.
+cudaError_t launch_fit(const float *X, int layout, int H, int W, int C, int d, double *mean,
+                       double *V, double *eigvals, void *ws, cudaStream_t st);
+
+// ------------------------------------------------------------------ projection (project.cu)
+
+size_t project_workspace_bytes(int C, long N, int d);
+
+// Y[k][p] = sum_c (x_cp - mean_c) V[c][k] in FP32 (precision QFCA_F32) or with
+// BF16 operands on tcgen05 (QFCA_BF16); also the per-component min/max
+// (as order-preserving u32 keys in mm_keys[2*d]).
+cudaError_t launch_project(const float *X, int layout, int H, int W, int C, const double *mean,
+                           const double *V, int d, int precision, float *Y, uint32_t *mm_keys,
+                           void *ws, cudaStream_t st);
+
+// ------------------------------------------------------------------ quantize (quantize.cu)
+
+cudaError_t launch_quantize(const float *Y, long N, int H, int W, int d, int B, int range_mode,
+                            const uint32_t *mm_keys, const float *lo_in, const float *hi_in,
+                            uint8_t *bins, int pitch, float *lo_out, float *hi_out,
+                            uint32_t *hist, cudaStream_t st);
+
+// ------------------------------------------------------------------ score (score.cu)
+
+size_t score_workspace_bytes(int H, int W);
+
+cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d, int B, int r,
+                            const uint32_t *ref_hist, uint32_t ref_total, float *score,
+                            uint64_t *numer, void *ws, cudaStream_t st);
+
+// ------------------------------------------------------------------ helpers
+
+// Order-preserving map float -> u32 (larger float -> larger key).
+__host__ __device__ inline uint32_t f2key(float f) {
+    uint32_t u;
+#ifdef __CUDA_ARCH__
+    u = __float_as_uint(f);
+#else
+    memcpy(&u, &f, 4);
+#endif
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ inline float key2f(uint32_t k) {
+    uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+#endif
+}
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace qfca

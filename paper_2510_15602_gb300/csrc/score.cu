@@ -1,0 +1,169 @@
+// score.cu -- per-pixel sliding-window histograms and the 1-D earth mover's
+// distance to the reference histogram, averaged over components (arXiv
+// 2510.15602, Sec. 3.1; W1 closed form of the supplement).
+//
+// For pixel p and component k with clipped window of N_loc pixels:
+//     D_k(p) = sum_b |cumP_b * N_ref - cumR_b * N_loc|      (exact integers)
+//     score(p) = sum_k D_k(p) / (d * N_loc * N_ref)
+//
+// k_window_emd: one CTA = a band of TH rows x a strip of SW columns x a group of
+// components.  The bin tile with an r-pixel halo is staged in shared memory;
+// each thread owns one output column and keeps its window histogram in shared
+// memory (bin-major, thread-minor: conflict-free), sliding it down the band:
+// one row of 2r+1 bins leaves and one enters per step (running window counts).
+// The CDF walk is sequential per thread.  The per-pixel integer sum over the
+// CTA's components goes to a u64 accumulator (atomic integer adds:
+// order-independent and exact); k_finalize divides once per pixel.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+
+namespace qfca {
+namespace {
+
+constexpr int kTH = 32;
+
+struct ScoreGeom {
+    int SW, TH, TR, TC, TCp, kg, n_kg;
+    size_t smem;
+};
+
+ScoreGeom score_geom(int H, int W, int d, int B, int r) {
+    ScoreGeom g;
+    g.SW = W >= 128 ? 128 : 64;
+    g.TH = kTH;
+    g.TR = g.TH + 2 * r;
+    g.TC = g.SW + 2 * r;
+    g.TCp = (int)align_up(g.TC, 16);
+    const long tiles = (long)((W + g.SW - 1) / g.SW) * ((H + g.TH - 1) / g.TH);
+    int n_kg = (int)((2 * 152 + tiles - 1) / tiles);
+    if (n_kg < 1) n_kg = 1;
+    if (n_kg > d) n_kg = d;
+    g.kg = (d + n_kg - 1) / n_kg;
+    g.n_kg = (d + g.kg - 1) / g.kg;
+    g.smem = sizeof(uint32_t) * (size_t)B * g.SW               // histograms
+             + sizeof(unsigned long long) * (size_t)g.TH * g.SW  // per-pixel sums
+             + sizeof(uint32_t) * 256                            // cumR
+             + (size_t)g.TR * g.TCp;                             // bin tile
+    return g;
+}
+
+__global__ void k_window_emd(const uint8_t *__restrict__ bins, int H, int W, int pitch, int d, int B, int r,
+                             ScoreGeom g, const uint32_t *__restrict__ ref_hist, uint32_t Nref,
+                             unsigned long long *__restrict__ acc, uint64_t *__restrict__ numer) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int SW = g.SW;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
+    unsigned long long *accS = reinterpret_cast<unsigned long long *>(hist + (size_t)B * SW);
+    uint32_t *cumR = reinterpret_cast<uint32_t *>(accS + (size_t)g.TH * SW);
+    uint8_t *tile = reinterpret_cast<uint8_t *>(cumR + 256);
+
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * SW, y0 = blockIdx.y * g.TH;
+    const int k0 = blockIdx.z * g.kg, k1 = min(d, k0 + g.kg);
+    const int x = x0 + t;
+    const int ty0 = y0 - r, tx0 = x0 - r;  // image coords of tile origin
+    for (int i = 0; i < g.TH; i++) accS[i * SW + t] = 0ull;
+
+    const int xl = max(0, x - r), xr = min(W - 1, x + r);
+    const int ncols = xr - xl + 1;
+    for (int k = k0; k < k1; k++) {
+        __syncthreads();
+        const uint8_t *bk = bins + (long)k * H * pitch;
+        for (int idx = t; idx < g.TR * g.TC; idx += SW) {
+            const int ty = idx / g.TC, tx = idx - ty * g.TC;
+            const int gy = ty0 + ty, gx = tx0 + tx;
+            int v = 0;
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = bk[(long)gy * pitch + gx];
+            tile[ty * g.TCp + tx] = (uint8_t)min(v, B - 1);  // out-of-range input bins clamp to B-1
+        }
+        if (t == 0) {
+            uint32_t c = 0;
+            for (int b = 0; b < B; b++) { c += ref_hist[(long)k * B + b]; cumR[b] = c; }
+        }
+        __syncthreads();
+        if (x >= W) continue;
+        for (int b = 0; b < B; b++) hist[b * SW + t] = 0;
+        // window of the band's first row
+        const int ya = max(0, y0 - r), yb = min(H - 1, y0 + r);
+        for (int yy = ya; yy <= yb; yy++) {
+            const uint8_t *row = tile + (yy - ty0) * g.TCp - tx0;
+            for (int xx = xl; xx <= xr; xx++) hist[row[xx] * SW + t] += 1u;
+        }
+        for (int i = 0; i < g.TH; i++) {
+            const int yy = y0 + i;
+            if (yy >= H) break;
+            if (i > 0) {
+                const int yo = yy - r - 1, yn = yy + r;
+                if (yo >= 0) {
+                    const uint8_t *row = tile + (yo - ty0) * g.TCp - tx0;
+                    for (int xx = xl; xx <= xr; xx++) hist[row[xx] * SW + t] -= 1u;
+                }
+                if (yn < H) {
+                    const uint8_t *row = tile + (yn - ty0) * g.TCp - tx0;
+                    for (int xx = xl; xx <= xr; xx++) hist[row[xx] * SW + t] += 1u;
+                }
+            }
+            const int nrows = min(H - 1, yy + r) - max(0, yy - r) + 1;
+            const unsigned long long Nloc = (unsigned long long)(nrows * ncols);
+            uint32_t cum = 0;
+            unsigned long long D = 0;
+            for (int b = 0; b < B; b++) {
+                cum += hist[b * SW + t];
+                const unsigned long long a = (unsigned long long)cum * Nref;
+                const unsigned long long c = (unsigned long long)cumR[b] * Nloc;
+                D += a > c ? a - c : c - a;
+            }
+            accS[i * SW + t] += D;
+            if (numer) numer[((long)k * H + yy) * W + x] = D;
+        }
+    }
+    __syncthreads();
+    if (x < W)
+        for (int i = 0; i < g.TH; i++) {
+            const int yy = y0 + i;
+            if (yy >= H) break;
+            if (g.n_kg == 1) acc[(long)yy * W + x] = accS[i * SW + t];
+            else atomicAdd(&acc[(long)yy * W + x], accS[i * SW + t]);
+        }
+}
+
+__global__ void k_finalize(const unsigned long long *__restrict__ acc, int H, int W, int r, int d, uint32_t Nref,
+                           float *__restrict__ score) {
+    const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (long)H * W) return;
+    const int y = (int)(p / W), x = (int)(p - (long)y * W);
+    const int nr = min(H - 1, y + r) - max(0, y - r) + 1;
+    const int nc = min(W - 1, x + r) - max(0, x - r) + 1;
+    const double den = (double)nr * (double)nc * (double)Nref * (double)d;
+    score[p] = (float)((double)acc[p] / den);
+}
+
+}  // namespace
+
+size_t score_workspace_bytes(int H, int W) { return align_up(sizeof(unsigned long long) * (size_t)H * W, 256); }
+
+cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d, int B, int r,
+                            const uint32_t *ref_hist, uint32_t ref_total, float *score, uint64_t *numer,
+                            void *ws, cudaStream_t st) {
+    const ScoreGeom g = score_geom(H, W, d, B, r);
+    if (g.smem > 200 * 1024) return cudaErrorNotSupported;  // nothing enqueued
+    unsigned long long *acc = (unsigned long long *)ws;
+    cudaError_t err = cudaSuccess;
+    if (g.n_kg > 1) err = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (size_t)H * W, st);
+    if (err != cudaSuccess) return err;
+    static bool attr_set = false;
+    if (!attr_set) {
+        err = cudaFuncSetAttribute(k_window_emd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (err != cudaSuccess) return err;
+        attr_set = true;
+    }
+    dim3 grid((W + g.SW - 1) / g.SW, (H + g.TH - 1) / g.TH, g.n_kg);
+    k_window_emd<<<grid, g.SW, g.smem, st>>>(bins, H, W, pitch, d, B, r, g, ref_hist, ref_total, acc, numer);
+    const long N = (long)H * W;
+    k_finalize<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(acc, H, W, r, d, ref_total, score);
+    return cudaGetLastError();
+}
+
+}  // namespace qfca

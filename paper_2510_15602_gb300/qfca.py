@@ -1,0 +1,232 @@
+"""Thin Python binding over libqfca.so (the C ABI of include/qfca.h).
+
+Argument marshalling only: tensors become device pointers, the current torch
+CUDA stream becomes the ``stream`` argument, and every step of the path runs
+in the library's CUDA kernels.  PyTorch provides device memory and streams.
+
+Importing this module loads ``libqfca.so`` and raises ImportError when the
+library has not been built -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqfca.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "qfca.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2510_15602_gb300/build.py "
+                      "(or __graft_entry__.build()); the QFCA path has no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# status codes and enums (include/qfca.h)
+OK, PENDING = 0, 1
+ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY = -1, -2, -3, -4, -5, -6
+NCHW, NHWC = 0, 1
+F32, BF16, FP8_E4M3 = 0, 1, 2
+RANGE_IMAGE, RANGE_FIXED = 0, 1
+_PREC = {"f32": F32, "fp32": F32, "bf16": BF16, "fp8": FP8_E4M3, F32: F32, BF16: BF16, FP8_E4M3: FP8_E4M3}
+
+
+class Fmap(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("C", ctypes.c_int), ("layout", ctypes.c_int)]
+
+
+class Basis(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_void_p), ("V", ctypes.c_void_p), ("eigvals", ctypes.c_void_p)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_lib.qfca_create.argtypes = [_I, ctypes.c_size_t, ctypes.POINTER(_P)]
+_lib.qfca_create.restype = _I
+_lib.qfca_destroy.argtypes = [_P]
+_lib.qfca_destroy.restype = _I
+_lib.qfca_status_string.argtypes = [_I]
+_lib.qfca_status_string.restype = ctypes.c_char_p
+_lib.qfca_last_error.argtypes = [_P]
+_lib.qfca_last_error.restype = ctypes.c_char_p
+_lib.qfca_version.argtypes = []
+_lib.qfca_version.restype = ctypes.c_char_p
+_lib.qfca_fit_pca.argtypes = [_P, _P, Fmap, _I, ctypes.POINTER(Basis), _P]
+_lib.qfca_fit_pca.restype = _I
+_lib.qfca_quantize.argtypes = [_P, _P, Fmap, ctypes.POINTER(Basis), _I, _I, _I, _I, _P, _P, _P, _I, _P, _P, _P,
+                               _P, _P]
+_lib.qfca_quantize.restype = _I
+_lib.qfca_score.argtypes = [_P, _P, _I, _I, _I, _I, _I, _I, _P, ctypes.c_uint32, _P, _P, _P]
+_lib.qfca_score.restype = _I
+
+
+class QfcaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_lib.qfca_status_string(status).decode()}: {msg}")
+        self.status = status
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/qfca.h."""
+    with open(HEADER) as f:
+        txt = f.read()
+    return sorted(set(re.findall(r"\b(qfca_[a-z0-9_]+)\s*\(", txt)))
+
+
+def version() -> str:
+    return _lib.qfca_version().decode()
+
+
+class Context:
+    """A libqfca context (owns the device workspace)."""
+
+    def __init__(self, device: int | None = None, workspace_bytes: int = 0):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = device
+        h = _P()
+        s = _lib.qfca_create(device, workspace_bytes, ctypes.byref(h))
+        if s != OK:
+            raise QfcaError(s, "qfca_create failed")
+        self.handle = h
+
+    def check(self, s: int):
+        if s != OK:
+            raise QfcaError(s, _lib.qfca_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.qfca_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_ctx_lock = threading.Lock()
+_default_ctx: dict[int, Context] = {}
+
+
+def default_context(device: int | None = None) -> Context:
+    if device is None:
+        device = torch.cuda.current_device()
+    with _ctx_lock:
+        if device not in _default_ctx:
+            _default_ctx[device] = Context(device)
+        return _default_ctx[device]
+
+
+def _stream_ptr(stream=None) -> int:
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return st.cuda_stream
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check_dev(t: torch.Tensor, name: str, dtype: torch.dtype):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def fmap_of(X: torch.Tensor, layout: int = NCHW) -> Fmap:
+    if X.dim() != 3:
+        raise ValueError("feature map must be 3-D: (C, H, W) for NCHW or (H, W, C) for NHWC")
+    if layout == NCHW:
+        C, H, W = X.shape
+    else:
+        H, W, C = X.shape
+    return Fmap(int(H), int(W), int(C), int(layout))
+
+
+def bins_pitch(W: int) -> int:
+    return (W + 15) // 16 * 16
+
+
+def fit_pca(X: torch.Tensor, d: int, layout: int = NCHW, ctx: Context | None = None, stream=None, out=None):
+    """qfca_fit_pca: returns (mean[C], V[C, d], eigvals[d]) FP64 device tensors."""
+    _check_dev(X, "X", torch.float32)
+    ctx = ctx or default_context(X.device.index)
+    fm = fmap_of(X, layout)
+    if out is None:
+        mean = torch.empty(fm.C, dtype=torch.float64, device=X.device)
+        V = torch.empty(fm.C, d, dtype=torch.float64, device=X.device)
+        ev = torch.empty(d, dtype=torch.float64, device=X.device)
+    else:
+        mean, V, ev = out
+    b = Basis(mean.data_ptr(), V.data_ptr(), ev.data_ptr())
+    ctx.check(_lib.qfca_fit_pca(ctx.handle, _ptr(X), fm, d, ctypes.byref(b), _P(_stream_ptr(stream))))
+    return mean, V, ev
+
+
+def quantize(X: torch.Tensor, basis, B: int, precision="f32", layout: int = NCHW, lo=None, hi=None,
+             want_Y: bool = False, want_hist: bool = True, ctx: Context | None = None, stream=None, out=None):
+    """qfca_quantize: projection + quantisation (+ reference histogram).
+
+    ``basis`` = (mean, V[, eigvals]).  ``lo``/``hi`` (f32 [d] device) select the
+    fixed-range mode.  Returns a dict with bins (u8 [d, H, pitch]), lo, hi,
+    hist (u32 [d, B]) and optionally Y (f32 [d, H, W]).
+    """
+    _check_dev(X, "X", torch.float32)
+    mean, V = basis[0], basis[1]
+    _check_dev(mean, "mean", torch.float64)
+    _check_dev(V, "V", torch.float64)
+    ctx = ctx or default_context(X.device.index)
+    fm = fmap_of(X, layout)
+    d = V.shape[1]
+    pitch = bins_pitch(fm.W)
+    dev = X.device
+    if out is None:
+        bins = torch.empty(d, fm.H, pitch, dtype=torch.uint8, device=dev)
+        lo_o = torch.empty(d, dtype=torch.float32, device=dev)
+        hi_o = torch.empty(d, dtype=torch.float32, device=dev)
+        hist = torch.empty(d, B, dtype=torch.int32, device=dev) if want_hist else None
+        Y = torch.empty(d, fm.H, fm.W, dtype=torch.float32, device=dev) if want_Y else None
+    else:
+        bins, lo_o, hi_o, hist, Y = out
+    rmode = RANGE_IMAGE if lo is None else RANGE_FIXED
+    b = Basis(mean.data_ptr(), V.data_ptr(), None)
+    ctx.check(_lib.qfca_quantize(ctx.handle, _ptr(X), fm, ctypes.byref(b), d, B, _PREC[precision], rmode,
+                                 _ptr(lo), _ptr(hi), _ptr(bins), pitch, _ptr(lo_o), _ptr(hi_o), _ptr(hist),
+                                 _ptr(Y), _P(_stream_ptr(stream))))
+    return dict(bins=bins, lo=lo_o, hi=hi_o, hist=hist, Y=Y, pitch=pitch)
+
+
+def score(bins: torch.Tensor, W: int, B: int, r: int, ref_hist: torch.Tensor, ref_total: int,
+          want_numer: bool = False, ctx: Context | None = None, stream=None, out=None):
+    """qfca_score: window histograms + 1-D EMD + component mean -> f32 [H, W] score map."""
+    _check_dev(bins, "bins", torch.uint8)
+    if ref_hist.dtype not in (torch.int32, torch.uint32) or not ref_hist.is_cuda:
+        raise ValueError("ref_hist must be a CUDA int32/uint32 tensor")
+    d, H, pitch = bins.shape
+    ctx = ctx or default_context(bins.device.index)
+    if out is None:
+        s = torch.empty(H, W, dtype=torch.float32, device=bins.device)
+    else:
+        s = out
+    numer = torch.empty(d, H, W, dtype=torch.int64, device=bins.device) if want_numer else None
+    ctx.check(_lib.qfca_score(ctx.handle, _ptr(bins), H, W, pitch, d, B, r, _ptr(ref_hist), int(ref_total),
+                              _ptr(s), _ptr(numer), _P(_stream_ptr(stream))))
+    return (s, numer) if want_numer else s
+
+
+def run_image(X: torch.Tensor, d: int, B: int, r: int, precision="f32", layout: int = NCHW,
+              ctx: Context | None = None, stream=None):
+    """The whole path on one image: fit, project + quantize, window EMD score."""
+    basis = fit_pca(X, d, layout, ctx=ctx, stream=stream)
+    q = quantize(X, basis, B, precision, layout, ctx=ctx, stream=stream)
+    fm = fmap_of(X, layout)
+    s = score(q["bins"], fm.W, B, r, q["hist"], fm.H * fm.W, ctx=ctx, stream=stream)
+    return s, basis, q

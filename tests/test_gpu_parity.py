@@ -1,0 +1,221 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances:
+  * integer stages (window histograms, EMD numerators, reference histogram,
+    bins given identical inputs): bit-exact;
+  * FP32 projection: |Y_gpu - Y_oracle| <= 1e-5 * max_p |Y_oracle[k]| per
+    component; a bin may differ from the oracle's only where the oracle value
+    lies within 1e-5 * range of a bin edge;
+  * bins from the GPU's own Y: identical to the oracle's FP32-precision
+    decision on the same values (both decide in FP32);
+  * score: the GPU rounds the exact sum_k D_k / (d N_loc N_ref) once to FP32,
+    so it is within one FP32 rounding (2^-23 relative) of the FP64 oracle;
+  * fit (FP64 on both sides, different algorithms): eigenvalues within 1e-11
+    relative, eigenvectors within 1e-9 (max abs), i.e. far inside the 1e-5
+    projection tolerance;
+  * BF16 projection: <= 1% bin flips and pixel AUROC within 0.005.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2510_15602_gb300 import synth
+from paper_2510_15602_gb300.metrics import auroc
+from tests.gpu_helpers import bins_np, edge_distance, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2510_15602_gb300 import qfca
+    assert torch.cuda.is_available()
+    return qfca
+
+
+# ------------------------------------------------------------------ window histogram + EMD (integer, bit-exact)
+
+@pytest.mark.parametrize("d,H,W,B,r,seed", [
+    (3, 70, 150, 16, 4, 0),     # several tiles, ragged in both directions
+    (2, 33, 129, 32, 7, 1),     # one row past a band, one column past a strip
+    (1, 5, 7, 8, 4, 2),         # window larger than the image
+    (2, 1, 40, 16, 3, 3),       # a single row
+    (2, 40, 1, 16, 3, 4),       # a single column
+    (4, 64, 96, 64, 12, 5),     # B=64, r=12
+    (2, 50, 60, 255, 2, 6),     # maximum bin count
+])
+def test_score_bit_exact_numerators(q, d, H, W, B, r, seed):
+    rng = np.random.default_rng(seed)
+    qb = synth.random_bins(rng, d, H, W, B, smooth=(seed % 2 == 0))
+    R = oracle.ref_hist(qb, B)
+    s_o, num_o, _ = oracle.score(qb, B, r, R, H * W)
+    pitch = q.bins_pitch(W)
+    bins = torch.zeros(d, H, pitch, dtype=torch.uint8, device="cuda")
+    bins[:, :, :W] = to_dev(qb)
+    s_g, num_g = q.score(bins, W, B, r, to_dev(R.astype(np.int32)), H * W, want_numer=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(num_g.cpu().numpy(), num_o)
+    np.testing.assert_allclose(s_g.cpu().numpy(), s_o, rtol=2.0 ** -23, atol=1e-12)
+
+
+def test_score_external_reference_point_masses(q):
+    # reference = point mass at bin 9 (mass 1000), map = constant bin 2: EMD = 7 everywhere
+    d, H, W, B, r = 2, 20, 30, 16, 3
+    bins = torch.full((d, H, q.bins_pitch(W)), 2, dtype=torch.uint8, device="cuda")
+    R = torch.zeros(d, B, dtype=torch.int32, device="cuda")
+    R[:, 9] = 1000
+    s = q.score(bins, W, B, r, R, 1000)
+    torch.cuda.synchronize()
+    assert torch.all(s == 7.0)
+
+
+# ------------------------------------------------------------------ projection + quantisation (oracle basis fed in)
+
+def _case(C, H, W, seed):
+    return synth.small_case(C=C, H=H, W=W, sigma=2.0, seed=seed, n_square=2, side=8, nch=6)
+
+
+@pytest.mark.parametrize("C,H,W,d,B,layout", [
+    (64, 128, 128, 16, 16, 0),
+    (256, 45, 77, 32, 32, 0),   # ragged pixel count
+    (40, 30, 50, 8, 16, 1),     # NHWC, C not a multiple of 32
+    (512, 24, 40, 32, 64, 0),
+])
+def test_project_quantize_against_oracle(q, C, H, W, d, B, layout):
+    img = _case(C, H, W, seed=C + H)
+    X = img.X if layout == 0 else np.ascontiguousarray(np.transpose(img.X, (1, 2, 0)))
+    mean, V, ev, _ = oracle.fit(img.X, d)
+    Y_o = oracle.project(img.X, mean, V)
+    qb_o, lo_o, hi_o = oracle.quantize(Y_o, B)
+    Xd = to_dev(X)
+    out = q.quantize(Xd, (to_dev(mean), to_dev(V)), B, "f32", layout=layout, want_Y=True)
+    torch.cuda.synchronize()
+    Y_g = out["Y"].cpu().numpy().astype(np.float64)
+    scale = np.abs(Y_o).reshape(d, -1).max(axis=1)
+    err = np.abs(Y_g - Y_o).reshape(d, -1).max(axis=1)
+    assert np.all(err <= 1e-5 * scale), (err / scale).max()
+    qb_g = bins_np(out["bins"], W)
+    # same-precision decision on the GPU's own Y: bit-exact
+    qb_f32, lo_f, hi_f = oracle.quantize(Y_g, B, fp32_decision=True)
+    np.testing.assert_array_equal(qb_g, qb_f32)
+    np.testing.assert_array_equal(out["lo"].cpu().numpy(), lo_f.astype(np.float32))
+    np.testing.assert_array_equal(out["hi"].cpu().numpy(), hi_f.astype(np.float32))
+    # against the FP64 oracle: flips only next to a bin edge
+    flip = qb_g != qb_o
+    if flip.any():
+        dist = edge_distance(Y_o, lo_o, hi_o, B)
+        assert np.all(dist[flip] <= 1e-5), dist[flip].max()
+    # reference histogram: bit-exact on the GPU's bins
+    np.testing.assert_array_equal(out["hist"].cpu().numpy().astype(np.uint32), oracle.ref_hist(qb_g, B))
+
+
+def test_quantize_fixed_range_clamps(q):
+    img = _case(32, 20, 24, seed=3)
+    mean, V, _, _ = oracle.fit(img.X, 4)
+    Y_o = oracle.project(img.X, mean, V)
+    lo = np.quantile(Y_o.reshape(4, -1), 0.1, axis=1).astype(np.float32)
+    hi = np.quantile(Y_o.reshape(4, -1), 0.9, axis=1).astype(np.float32)
+    out = q.quantize(to_dev(img.X), (to_dev(mean), to_dev(V)), 16, "f32", lo=to_dev(lo), hi=to_dev(hi),
+                     want_Y=True)
+    torch.cuda.synchronize()
+    Y_g = out["Y"].cpu().numpy().astype(np.float64)
+    exp, _, _ = oracle.quantize(Y_g, 16, lo=lo.astype(np.float64), hi=hi.astype(np.float64), fp32_decision=True)
+    np.testing.assert_array_equal(bins_np(out["bins"], 24), exp)
+    assert (exp == 0).any() and (exp == 15).any()
+
+
+# ------------------------------------------------------------------ PCA fit (FP64)
+
+@pytest.mark.parametrize("C,H,W,d,layout", [
+    (64, 128, 128, 16, 0),
+    (256, 40, 52, 32, 0),
+    (48, 30, 33, 12, 1),
+    (2, 9, 7, 2, 0),
+])
+def test_fit_against_oracle(q, C, H, W, d, layout):
+    img = _case(C, H, W, seed=7 * C + d)
+    X = img.X if layout == 0 else np.ascontiguousarray(np.transpose(img.X, (1, 2, 0)))
+    mean_o, V_o, ev_o, all_o = oracle.fit(img.X, d)
+    mean_g, V_g, ev_g = q.fit_pca(to_dev(X), d, layout=layout)
+    torch.cuda.synchronize()
+    mean_g, V_g, ev_g = mean_g.cpu().numpy(), V_g.cpu().numpy(), ev_g.cpu().numpy()
+    np.testing.assert_allclose(mean_g, mean_o, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(ev_g, ev_o, rtol=1e-11, atol=1e-13 * ev_o[0])
+    gaps = np.abs(np.diff(all_o))
+    for k in range(d):
+        gap = min(gaps[k - 1] if k > 0 else np.inf, gaps[k] if k < C - 1 else np.inf)
+        err = np.max(np.abs(V_g[:, k] - V_o[:, k]))
+        assert err < max(1e-9, 1e-13 / gap), (k, err, gap)
+
+
+# ------------------------------------------------------------------ the whole path
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_pipeline_fp32_config1(q, layout):
+    img = synth.make_image("plain_128_c64", 0)
+    d, B, r = 16, 16, 4
+    ref = oracle.pipeline(img.X, d, B, r)
+    X = img.X if layout == 0 else np.ascontiguousarray(np.transpose(img.X, (1, 2, 0)))
+    Xd = to_dev(X)
+    basis = q.fit_pca(Xd, d, layout=layout)
+    out = q.quantize(Xd, basis, B, "f32", layout=layout, want_Y=True)
+    s, num = q.score(out["bins"], 128, B, r, out["hist"], 128 * 128, want_numer=True)
+    torch.cuda.synchronize()
+    Y_g = out["Y"].cpu().numpy().astype(np.float64)
+    scale = np.abs(ref["Y"]).reshape(d, -1).max(axis=1)
+    assert np.all(np.abs(Y_g - ref["Y"]).reshape(d, -1).max(axis=1) <= 1e-5 * scale)
+    qb_g = bins_np(out["bins"], 128)
+    flip = qb_g != ref["q"]
+    if flip.any():
+        assert np.all(edge_distance(ref["Y"], ref["lo"], ref["hi"], B)[flip] <= 1e-5)
+    # integer stages bit-exact on the GPU's bins
+    R_g = oracle.ref_hist(qb_g, B)
+    s_o, num_o, _ = oracle.score(qb_g, B, r, R_g, 128 * 128)
+    np.testing.assert_array_equal(num.cpu().numpy(), num_o)
+    np.testing.assert_allclose(s.cpu().numpy(), s_o, rtol=2.0 ** -23, atol=1e-12)
+    a_g, a_o = auroc(s.cpu().numpy(), img.mask), auroc(ref["score"], img.mask)
+    assert abs(a_g - a_o) < 1e-3 and a_g > 0.9
+
+
+def test_pipeline_full_size_256_c256_sampled(q):
+    # one full-size image of the 16 x 256^2 x C256 workload
+    img = synth.make_image("batch16_256_c256", 0)
+    d, B, r = 32, 32, 7
+    mean_o, V_o, ev_o, _ = oracle.fit(img.X, d)
+    Xd = to_dev(img.X)
+    mean_g, V_g, ev_g = q.fit_pca(Xd, d)
+    out = q.quantize(Xd, (mean_g, V_g), B, "f32", want_Y=True)
+    s = q.score(out["bins"], 256, B, r, out["hist"], 256 * 256)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(ev_g.cpu().numpy(), ev_o, rtol=1e-11)
+    assert np.max(np.abs(V_g.cpu().numpy() - V_o)) < 1e-9
+    # projection at 4096 sampled pixels, computed one by one by the oracle
+    rng = np.random.default_rng(0)
+    idx = rng.choice(256 * 256, 4096, replace=False)
+    Xs = img.X.reshape(256, -1)[:, idx].reshape(256, 64, 64)
+    Y_o = oracle.project(Xs, mean_o, V_o).reshape(d, -1)
+    Y_g = out["Y"].reshape(d, -1)[:, torch.from_numpy(idx).cuda()].cpu().numpy()
+    scale = np.abs(Y_o).max(axis=1)
+    assert np.all(np.abs(Y_g - Y_o).max(axis=1) <= 1e-5 * scale)
+    # integer stages: the oracle's window EMD on the GPU's bins, full image
+    qb = bins_np(out["bins"], 256)
+    R = oracle.ref_hist(qb, B)
+    np.testing.assert_array_equal(out["hist"].cpu().numpy().astype(np.uint32), R)
+    s_o, _, _ = oracle.score(qb, B, r, R, 256 * 256)
+    np.testing.assert_allclose(s.cpu().numpy(), s_o, rtol=2.0 ** -23, atol=1e-12)
+
+
+# ------------------------------------------------------------------ argument validation through the ABI
+
+def test_invalid_arguments_rejected(q):
+    X = torch.zeros(8, 4, 4, device="cuda")
+    with pytest.raises(q.QfcaError) as e:
+        q.fit_pca(X, 9)  # d > C
+    assert e.value.status == q.ERR_INVALID_ARG
+    bins = torch.zeros(2, 4, 16, dtype=torch.uint8, device="cuda")
+    R = torch.zeros(2, 8, dtype=torch.int32, device="cuda")
+    with pytest.raises(q.QfcaError):
+        q.score(bins, 4, 8, 0, R, 16)  # r = 0
+    with pytest.raises(q.QfcaError):
+        q.score(bins, 4, 1, 1, R, 16)  # B = 1
