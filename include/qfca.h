@@ -149,6 +149,26 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
                        int r, const uint32_t *ref_hist, uint32_t ref_total, float *score,
                        uint64_t *numer_out, void *stream);
 
+/* ---------------------------------------------------------------- tracing */
+
+/* Number of kernels the library has launched through `ctx` since creation
+ * (every entry point counts its own launches; memsets are not counted). */
+qfca_status qfca_launch_count(qfca_ctx *ctx, uint64_t *out);
+
+/* Start timing kernel launches on `ctx`: every launch whose kernel name
+ * contains `filter` (all kernels when filter is "" or NULL) is bracketed by
+ * two CUDA events recorded on the launch's stream.  Clears earlier records. */
+qfca_status qfca_trace_start(qfca_ctx *ctx, const char *filter);
+
+/* Stop recording (records are kept until the next qfca_trace_start). */
+qfca_status qfca_trace_stop(qfca_ctx *ctx);
+
+/* Entry i (0-based) of the trace, aggregated per kernel name: name (copied
+ * into name_out, at most 63 chars + NUL), total device time in ms and launch
+ * count.  Synchronises on the recorded events.  Returns QFCA_ERR_INVALID_ARG
+ * when i is past the last entry. */
+qfca_status qfca_trace_get(qfca_ctx *ctx, int i, char *name_out, double *total_ms, uint64_t *launches);
+
 #ifdef __cplusplus
 }
 #endif

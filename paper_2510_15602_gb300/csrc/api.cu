@@ -6,10 +6,99 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <string.h>
+
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "internal.cuh"
+
+namespace qfca {
+thread_local LaunchHook *tl_hook = nullptr;
+}
+
+namespace {
+
+// Counts every launch; brackets launches whose kernel name matches the filter
+// with CUDA events on the launch stream.
+struct Tracer final : qfca::LaunchHook {
+    uint64_t launches = 0;
+    bool active = false;
+    bool pending = false;
+    std::string filter;
+    struct Rec {
+        const char *name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    // aggregated view (filled by trace_get)
+    std::vector<std::string> agg_name;
+    std::vector<double> agg_ms;
+    std::vector<uint64_t> agg_n;
+    bool agg_valid = false;
+
+    cudaEvent_t take() {
+        if (pool_used == pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool.push_back(e);
+        }
+        return pool[pool_used++];
+    }
+    void before(const char *k, cudaStream_t st) override {
+        launches++;
+        pending = false;
+        if (!active) return;
+        if (!filter.empty() && !strstr(k, filter.c_str())) return;
+        Rec r{k, take(), take()};
+        if (!r.a || !r.b) return;
+        cudaEventRecord(r.a, st);
+        recs.push_back(r);
+        pending = true;
+        agg_valid = false;
+    }
+    void after(const char *, cudaStream_t st) override {
+        if (pending) cudaEventRecord(recs.back().b, st);
+        pending = false;
+    }
+    void reset() {
+        recs.clear();
+        pool_used = 0;
+        agg_valid = false;
+    }
+    cudaError_t aggregate() {
+        if (agg_valid) return cudaSuccess;
+        agg_name.clear();
+        agg_ms.clear();
+        agg_n.clear();
+        for (const Rec &r : recs) {
+            cudaError_t e = cudaEventSynchronize(r.b);
+            if (e != cudaSuccess) return e;
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, r.a, r.b);
+            if (e != cudaSuccess) return e;
+            size_t i = 0;
+            while (i < agg_name.size() && agg_name[i] != r.name) i++;
+            if (i == agg_name.size()) {
+                agg_name.emplace_back(r.name);
+                agg_ms.push_back(0.0);
+                agg_n.push_back(0);
+            }
+            agg_ms[i] += ms;
+            agg_n[i] += 1;
+        }
+        agg_valid = true;
+        return cudaSuccess;
+    }
+    ~Tracer() override {
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace
 
 struct qfca_ctx {
     int device = 0;
@@ -18,11 +107,19 @@ struct qfca_ctx {
     bool sticky = false;
     std::string err;
     std::mutex mu;
+    Tracer tracer;
 };
 
 namespace {
 
 using namespace qfca;
+
+// Installs the context's tracer as the launch hook for the current call.
+struct HookScope {
+    qfca::LaunchHook *prev;
+    explicit HookScope(qfca_ctx *ctx) : prev(qfca::tl_hook) { qfca::tl_hook = &ctx->tracer; }
+    ~HookScope() { qfca::tl_hook = prev; }
+};
 
 struct DeviceGuard {
     int prev = -1;
@@ -167,6 +264,7 @@ qfca_status qfca_fit_pca(qfca_ctx *ctx, const float *X, qfca_fmap desc, int d, c
     if (!out || !out->mean || !out->V || !out->eigvals) return fail(ctx, QFCA_ERR_INVALID_ARG, "basis pointers NULL");
     if (d < 1 || d > desc.C || d > kMaxD) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, min(C, %d)]", d, kMaxD);
     DeviceGuard g(ctx->device);
+    HookScope hs(ctx);
     const long N = (long)desc.H * desc.W;
     if ((s = ensure_ws(ctx, fit_workspace_bytes(desc.C, N, d)))) return s;
     cudaError_t e = launch_fit(X, desc.layout, desc.H, desc.W, desc.C, d, out->mean, out->V, out->eigvals, ctx->ws,
@@ -196,6 +294,7 @@ qfca_status qfca_quantize(qfca_ctx *ctx, const float *X, qfca_fmap desc, const q
     if (!bins) return fail(ctx, QFCA_ERR_INVALID_ARG, "bins NULL");
     if (pitch < desc.W || pitch % 16 != 0) return fail(ctx, QFCA_ERR_INVALID_ARG, "pitch %d must be >= W and a multiple of 16", pitch);
     DeviceGuard g(ctx->device);
+    HookScope hs(ctx);
     const long N = (long)desc.H * desc.W;
     const size_t o_mm = 0;
     const size_t o_y = o_mm + bytes_mmkeys(d);
@@ -232,12 +331,53 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
     if (r < 1 || 2 * r + 1 > 127) return fail(ctx, QFCA_ERR_INVALID_ARG, "r = %d outside [1, 63]", r);
     if (ref_total < 1) return fail(ctx, QFCA_ERR_INVALID_ARG, "ref_total must be >= 1");
     DeviceGuard g(ctx->device);
+    HookScope hs(ctx);
     if ((s = ensure_ws(ctx, score_workspace_bytes(H, W)))) return s;
     cudaError_t e = launch_score_ws(bins, H, W, pitch, d, B, r, ref_hist, ref_total, score, numer_out, ctx->ws,
                                     (cudaStream_t)stream);
     if (e == cudaErrorNotSupported)
         return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d needs more shared memory than a CTA has", B, r);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_score");
+    return QFCA_OK;
+}
+
+qfca_status qfca_launch_count(qfca_ctx *ctx, uint64_t *out) {
+    if (!ctx || !out) return QFCA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    *out = ctx->tracer.launches;
+    return QFCA_OK;
+}
+
+qfca_status qfca_trace_start(qfca_ctx *ctx, const char *filter) {
+    if (!ctx) return QFCA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    ctx->tracer.reset();
+    ctx->tracer.filter = filter ? filter : "";
+    ctx->tracer.active = true;
+    return QFCA_OK;
+}
+
+qfca_status qfca_trace_stop(qfca_ctx *ctx) {
+    if (!ctx) return QFCA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->tracer.active = false;
+    return QFCA_OK;
+}
+
+qfca_status qfca_trace_get(qfca_ctx *ctx, int i, char *name_out, double *total_ms, uint64_t *launches) {
+    if (!ctx) return QFCA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    cudaError_t e = ctx->tracer.aggregate();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_trace_get");
+    if (i < 0 || (size_t)i >= ctx->tracer.agg_name.size()) return QFCA_ERR_INVALID_ARG;
+    if (name_out) {
+        strncpy(name_out, ctx->tracer.agg_name[i].c_str(), 63);
+        name_out[63] = 0;
+    }
+    if (total_ms) *total_ms = ctx->tracer.agg_ms[i];
+    if (launches) *launches = ctx->tracer.agg_n[i];
     return QFCA_OK;
 }
 

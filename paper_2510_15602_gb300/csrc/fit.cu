@@ -477,9 +477,10 @@ cudaError_t launch_fit(const float *X, int layout, int H, int W, int C, int d, d
     double *part = (double *)(base + L.off_part);
     double *cov = (double *)(base + L.off_cov);
     const int nt = (C + kTile - 1) / kTile;
-    k_mean<<<C, 256, 0, st>>>(X, layout, C, N, mean);
-    k_cov_tile<<<L.n_pairs * L.n_split, 256, 0, st>>>(X, layout, C, N, mean, nt, L.n_pairs, L.chunk, part);
-    k_cov_reduce<<<L.n_pairs, 256, 0, st>>>(part, nt, L.n_pairs, L.n_split, C, N, cov);
+    QFCA_LAUNCH("k_mean", st, k_mean<<<C, 256, 0, st>>>(X, layout, C, N, mean));
+    QFCA_LAUNCH("k_cov_tile_f64", st,
+                k_cov_tile<<<L.n_pairs * L.n_split, 256, 0, st>>>(X, layout, C, N, mean, nt, L.n_pairs, L.chunk, part));
+    QFCA_LAUNCH("k_cov_reduce", st, k_cov_reduce<<<L.n_pairs, 256, 0, st>>>(part, nt, L.n_pairs, L.n_split, C, N, cov));
     // eigensolver scratch
     char *e = base + L.off_eig;
     EigScratch s;
@@ -498,7 +499,7 @@ cudaError_t launch_fit(const float *X, int layout, int H, int W, int C, int d, d
     s.e232 = (float *)e; e += n * sizeof(float);
     s.order = (int *)e; e += d * sizeof(int);
     s.piv = (uint8_t *)e;
-    k_eig<<<1, kEigThreads, 0, st>>>(cov, C, d, s, V, eigvals);
+    QFCA_LAUNCH("k_eig", st, k_eig<<<1, kEigThreads, 0, st>>>(cov, C, d, s, V, eigvals));
     return cudaGetLastError();
 }
 

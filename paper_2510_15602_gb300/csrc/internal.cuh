@@ -76,4 +76,21 @@ __host__ __device__ inline float key2f(uint32_t k) {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// ------------------------------------------------------------------ launch hook (tracing)
+
+// Called around every kernel launch while an entry point runs on a context.
+struct LaunchHook {
+    virtual void before(const char *kernel, cudaStream_t st) = 0;
+    virtual void after(const char *kernel, cudaStream_t st) = 0;
+    virtual ~LaunchHook() = default;
+};
+extern thread_local LaunchHook *tl_hook;
+
+#define QFCA_LAUNCH(kname, st, ...)                            \
+    do {                                                       \
+        if (::qfca::tl_hook) ::qfca::tl_hook->before(kname, st); \
+        __VA_ARGS__;                                           \
+        if (::qfca::tl_hook) ::qfca::tl_hook->after(kname, st);  \
+    } while (0)
+
 }  // namespace qfca

@@ -132,12 +132,12 @@ cudaError_t launch_project(const float *X, int layout, int H, int W, int C, cons
     const int DT = pick_dt(d);
     float *mean32 = (float *)ws;
     float *V32 = mean32 + align_up(C, 64);
-    k_prep_f32<<<(C * DT + 255) / 256, 256, 0, st>>>(mean, V, C, d, DT, mean32, V32);
+    QFCA_LAUNCH("k_prep_f32", st, k_prep_f32<<<(C * DT + 255) / 256, 256, 0, st>>>(mean, V, C, d, DT, mean32, V32));
     const unsigned grid = (unsigned)((N + kPix - 1) / kPix);
     switch (DT) {
-        case 16: k_project_f32<16><<<grid, kPix, 0, st>>>(X, layout, C, N, mean32, V32, d, Y, mm_keys); break;
-        case 32: k_project_f32<32><<<grid, kPix, 0, st>>>(X, layout, C, N, mean32, V32, d, Y, mm_keys); break;
-        default: k_project_f32<64><<<grid, kPix, 0, st>>>(X, layout, C, N, mean32, V32, d, Y, mm_keys); break;
+        case 16: QFCA_LAUNCH("k_project_f32", st, k_project_f32<16><<<grid, kPix, 0, st>>>(X, layout, C, N, mean32, V32, d, Y, mm_keys)); break;
+        case 32: QFCA_LAUNCH("k_project_f32", st, k_project_f32<32><<<grid, kPix, 0, st>>>(X, layout, C, N, mean32, V32, d, Y, mm_keys)); break;
+        default: QFCA_LAUNCH("k_project_f32", st, k_project_f32<64><<<grid, kPix, 0, st>>>(X, layout, C, N, mean32, V32, d, Y, mm_keys)); break;
     }
     return cudaGetLastError();
 }

@@ -76,8 +76,9 @@ cudaError_t launch_quantize(const float *Y, long N, int H, int W, int d, int B, 
         if (err != cudaSuccess) return err;
     }
     dim3 grid((H + kRowsPerCta - 1) / kRowsPerCta, d);
-    k_quantize<<<grid, kThreads, 0, st>>>(Y, N, H, W, d, B, range_mode, mm_keys, lo_in, hi_in, bins, pitch,
-                                          lo_out, hi_out, hist);
+    QFCA_LAUNCH("k_quantize", st,
+                k_quantize<<<grid, kThreads, 0, st>>>(Y, N, H, W, d, B, range_mode, mm_keys, lo_in, hi_in, bins,
+                                                      pitch, lo_out, hi_out, hist));
     return cudaGetLastError();
 }
 

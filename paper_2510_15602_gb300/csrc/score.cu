@@ -160,9 +160,10 @@ cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d,
         attr_set = true;
     }
     dim3 grid((W + g.SW - 1) / g.SW, (H + g.TH - 1) / g.TH, g.n_kg);
-    k_window_emd<<<grid, g.SW, g.smem, st>>>(bins, H, W, pitch, d, B, r, g, ref_hist, ref_total, acc, numer);
+    QFCA_LAUNCH("k_window_emd", st,
+                k_window_emd<<<grid, g.SW, g.smem, st>>>(bins, H, W, pitch, d, B, r, g, ref_hist, ref_total, acc, numer));
     const long N = (long)H * W;
-    k_finalize<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(acc, H, W, r, d, ref_total, score);
+    QFCA_LAUNCH("k_finalize", st, k_finalize<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(acc, H, W, r, d, ref_total, score));
     return cudaGetLastError();
 }
 

@@ -62,6 +62,15 @@ _lib.qfca_quantize.argtypes = [_P, _P, Fmap, ctypes.POINTER(Basis), _I, _I, _I, 
 _lib.qfca_quantize.restype = _I
 _lib.qfca_score.argtypes = [_P, _P, _I, _I, _I, _I, _I, _I, _P, ctypes.c_uint32, _P, _P, _P]
 _lib.qfca_score.restype = _I
+_lib.qfca_launch_count.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64)]
+_lib.qfca_launch_count.restype = _I
+_lib.qfca_trace_start.argtypes = [_P, ctypes.c_char_p]
+_lib.qfca_trace_start.restype = _I
+_lib.qfca_trace_stop.argtypes = [_P]
+_lib.qfca_trace_stop.restype = _I
+_lib.qfca_trace_get.argtypes = [_P, _I, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_uint64)]
+_lib.qfca_trace_get.restype = _I
 
 
 class QfcaError(RuntimeError):
@@ -97,6 +106,29 @@ class Context:
     def check(self, s: int):
         if s != OK:
             raise QfcaError(s, _lib.qfca_last_error(self.handle).decode())
+
+    def launch_count(self) -> int:
+        n = ctypes.c_uint64()
+        self.check(_lib.qfca_launch_count(self.handle, ctypes.byref(n)))
+        return int(n.value)
+
+    def trace_start(self, kernel_filter: str = ""):
+        self.check(_lib.qfca_trace_start(self.handle, kernel_filter.encode()))
+
+    def trace_stop(self):
+        self.check(_lib.qfca_trace_stop(self.handle))
+
+    def trace(self) -> dict:
+        """{kernel name: (total device ms, launches)} of the current trace."""
+        out = {}
+        i = 0
+        buf = ctypes.create_string_buffer(64)
+        ms = ctypes.c_double()
+        n = ctypes.c_uint64()
+        while _lib.qfca_trace_get(self.handle, i, buf, ctypes.byref(ms), ctypes.byref(n)) == OK:
+            out[buf.value.decode()] = (ms.value, int(n.value))
+            i += 1
+        return out
 
     def close(self):
         if getattr(self, "handle", None):
