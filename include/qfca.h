@@ -149,6 +149,12 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
                        int r, const uint32_t *ref_hist, uint32_t ref_total, float *score,
                        uint64_t *numer_out, void *stream);
 
+/* Synchronise the device and read-and-clear the context's device status
+ * word.  Kernels whose bounded waits (on tensor-core completion, on a peer
+ * stage) run out set a bit there and return early instead of hanging.
+ * *out receives the word; returns QFCA_ERR_TIMEOUT when it was non-zero. */
+qfca_status qfca_device_status(qfca_ctx *ctx, int *out);
+
 /* ---------------------------------------------------------------- tracing */
 
 /* Number of kernels the library has launched through `ctx` since creation

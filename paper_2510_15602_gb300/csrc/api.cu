@@ -104,6 +104,7 @@ struct qfca_ctx {
     int device = 0;
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    int *status_dev = nullptr;  // device status word (bits set by kernels)
     bool sticky = false;
     std::string err;
     std::mutex mu;
@@ -238,6 +239,12 @@ qfca_status qfca_create(int device, size_t workspace_bytes, qfca_ctx **out) {
         delete ctx;
         return s;
     }
+    if (cudaMalloc(&ctx->status_dev, 256) != cudaSuccess || cudaMemset(ctx->status_dev, 0, 256) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ctx->ws);
+        delete ctx;
+        return QFCA_ERR_OOM;
+    }
     *out = ctx;
     return QFCA_OK;
 }
@@ -246,10 +253,9 @@ qfca_status qfca_destroy(qfca_ctx *ctx) {
     if (!ctx) return QFCA_ERR_INVALID_ARG;
     {
         DeviceGuard g(ctx->device);
-        if (ctx->ws) {
-            cudaDeviceSynchronize();
-            cudaFree(ctx->ws);
-        }
+        if (ctx->ws || ctx->status_dev) cudaDeviceSynchronize();
+        if (ctx->ws) cudaFree(ctx->ws);
+        if (ctx->status_dev) cudaFree(ctx->status_dev);
     }
     delete ctx;
     return QFCA_OK;
@@ -305,7 +311,7 @@ qfca_status qfca_quantize(qfca_ctx *ctx, const float *X, qfca_fmap desc, const q
     float *Y = Y_out ? Y_out : (float *)(base + o_y);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = launch_project(X, desc.layout, desc.H, desc.W, desc.C, basis->mean, basis->V, d, precision, Y, mm,
-                                   base + o_p, st);
+                                   base + o_p, ctx->status_dev, st);
     if (e == cudaErrorNotSupported) {
         cudaGetLastError();
         return fail(ctx, QFCA_ERR_UNSUPPORTED, "projection precision %d not supported for this shape", precision);
@@ -339,6 +345,17 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
         return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d needs more shared memory than a CTA has", B, r);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_score");
     return QFCA_OK;
+}
+
+qfca_status qfca_device_status(qfca_ctx *ctx, int *out) {
+    if (!ctx || !out) return QFCA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(out, ctx->status_dev, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ctx->status_dev, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_device_status");
+    return *out ? QFCA_ERR_TIMEOUT : QFCA_OK;
 }
 
 qfca_status qfca_launch_count(qfca_ctx *ctx, uint64_t *out) {

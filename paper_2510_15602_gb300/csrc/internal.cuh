@@ -34,7 +34,10 @@ size_t project_workspace_bytes(int C, long N, int d);
 // (as order-preserving u32 keys in mm_keys[2*d]).
 cudaError_t launch_project(const float *X, int layout, int H, int W, int C, const double *mean,
                            const double *V, int d, int precision, float *Y, uint32_t *mm_keys,
-                           void *ws, cudaStream_t st);
+                           void *ws, int *status, cudaStream_t st);
+
+// Device status word bits (set by kernels; read by qfca_device_status).
+constexpr int kStatusMmaTimeout = 1;
 
 // ------------------------------------------------------------------ quantize (quantize.cu)
 

@@ -17,7 +17,7 @@ namespace qfca {
 
 // tcgen05 BF16 projection (project_tc.cu)
 cudaError_t launch_project_bf16(const float *X, int layout, int H, int W, int C, const double *mean,
-                                const double *V, int d, float *Y, uint32_t *mm_keys, void *ws,
+                                const double *V, int d, float *Y, uint32_t *mm_keys, void *ws, int *status,
                                 cudaStream_t st);
 size_t project_bf16_workspace_bytes(int C, long N, int d);
 
@@ -121,14 +121,14 @@ size_t project_workspace_bytes(int C, long N, int d) {
 
 cudaError_t launch_project(const float *X, int layout, int H, int W, int C, const double *mean,
                            const double *V, int d, int precision, float *Y, uint32_t *mm_keys, void *ws,
-                           cudaStream_t st) {
+                           int *status, cudaStream_t st) {
     const long N = (long)H * W;
     // min keys start at the largest key, max keys at the smallest
     cudaError_t err = cudaMemsetAsync(mm_keys, 0xff, sizeof(uint32_t) * d, st);
     if (err == cudaSuccess) err = cudaMemsetAsync(mm_keys + d, 0x00, sizeof(uint32_t) * d, st);
     if (err != cudaSuccess) return err;
     if (precision == QFCA_BF16)
-        return launch_project_bf16(X, layout, H, W, C, mean, V, d, Y, mm_keys, ws, st);
+        return launch_project_bf16(X, layout, H, W, C, mean, V, d, Y, mm_keys, ws, status, st);
     const int DT = pick_dt(d);
     float *mean32 = (float *)ws;
     float *V32 = mean32 + align_up(C, 64);

@@ -62,6 +62,8 @@ _lib.qfca_quantize.argtypes = [_P, _P, Fmap, ctypes.POINTER(Basis), _I, _I, _I, 
 _lib.qfca_quantize.restype = _I
 _lib.qfca_score.argtypes = [_P, _P, _I, _I, _I, _I, _I, _I, _P, ctypes.c_uint32, _P, _P, _P]
 _lib.qfca_score.restype = _I
+_lib.qfca_device_status.argtypes = [_P, ctypes.POINTER(ctypes.c_int)]
+_lib.qfca_device_status.restype = _I
 _lib.qfca_launch_count.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64)]
 _lib.qfca_launch_count.restype = _I
 _lib.qfca_trace_start.argtypes = [_P, ctypes.c_char_p]
@@ -106,6 +108,14 @@ class Context:
     def check(self, s: int):
         if s != OK:
             raise QfcaError(s, _lib.qfca_last_error(self.handle).decode())
+
+    def device_status(self) -> int:
+        """Synchronise and read-and-clear the device status word (0 = no kernel timed out)."""
+        v = ctypes.c_int()
+        s = _lib.qfca_device_status(self.handle, ctypes.byref(v))
+        if s not in (OK, ERR_TIMEOUT):
+            self.check(s)
+        return int(v.value)
 
     def launch_count(self) -> int:
         n = ctypes.c_uint64()

@@ -219,3 +219,81 @@ def test_invalid_arguments_rejected(q):
         q.score(bins, 4, 8, 0, R, 16)  # r = 0
     with pytest.raises(q.QfcaError):
         q.score(bins, 4, 1, 1, R, 16)  # B = 1
+
+
+# ------------------------------------------------------------------ BF16 projection on tcgen05
+
+def bf16_round(a):
+    """Round to the nearest BF16 (ties to even), returned as float32."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+@pytest.mark.parametrize("C,H,W,d,layout", [
+    (256, 45, 77, 32, 0),   # ragged pixel count (last tile partial)
+    (64, 128, 128, 16, 0),
+    (512, 24, 40, 64, 0),   # 8 K-chunks, N = 64
+    (40, 30, 50, 8, 1),     # NHWC, C padded to 64
+    (200, 16, 17, 32, 1),
+])
+def test_project_bf16_matches_rounded_operands(q, C, H, W, d, layout):
+    # the tensor-core result equals the FP64 sum of the same BF16-rounded
+    # operands up to FP32 accumulation: checks operand layouts, swizzle,
+    # descriptors and the TMEM read-back element by element
+    img = _case(C, H, W, seed=C * 3 + W)
+    X = img.X if layout == 0 else np.ascontiguousarray(np.transpose(img.X, (1, 2, 0)))
+    mean, V, _, _ = oracle.fit(img.X, d)
+    out = q.quantize(to_dev(X), (to_dev(mean), to_dev(V)), 16, "bf16", layout=layout, want_Y=True)
+    torch.cuda.synchronize()
+    Xc = bf16_round(img.X.reshape(C, -1) - mean.astype(np.float32)[:, None]).astype(np.float64)
+    Vb = bf16_round(V.astype(np.float32)).astype(np.float64)
+    Y_ref = (Vb.T @ Xc).reshape(d, H, W)
+    bound = (np.abs(Vb).T @ np.abs(Xc)).reshape(d, H, W) * 1e-6 + 1e-30
+    Y_g = out["Y"].cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(Y_g - Y_ref) <= bound), np.max(np.abs(Y_g - Y_ref) / bound)
+    # bins still decided in FP32 on the kernel's own Y
+    qb, _, _ = oracle.quantize(Y_g, 16, fp32_decision=True)
+    np.testing.assert_array_equal(bins_np(out["bins"], W), qb)
+
+
+def test_bf16_flips_and_auroc_config1(q):
+    img = synth.make_image("plain_128_c64", 0)
+    d, B, r = 16, 16, 4
+    ref = oracle.pipeline(img.X, d, B, r)
+    Xd = to_dev(img.X)
+    basis = q.fit_pca(Xd, d)
+    out = q.quantize(Xd, basis, B, "bf16", want_Y=True)
+    s = q.score(out["bins"], 128, B, r, out["hist"], 128 * 128)
+    torch.cuda.synchronize()
+    flips = float((bins_np(out["bins"], 128) != ref["q"]).mean())
+    assert flips <= 0.01, flips
+    a_g, a_o = auroc(s.cpu().numpy(), img.mask), auroc(ref["score"], img.mask)
+    assert abs(a_g - a_o) <= 0.005, (a_g, a_o)
+
+
+def test_bf16_flips_and_auroc_full_size_image(q):
+    img = synth.make_image("batch16_256_c256", 1)
+    d, B, r = 32, 32, 7
+    mean_o, V_o, _, _ = oracle.fit(img.X, d)
+    Y_o = oracle.project(img.X, mean_o, V_o)
+    qb_o, _, _ = oracle.quantize(Y_o, B)
+    R_o = oracle.ref_hist(qb_o, B)
+    s_o, _, _ = oracle.score(qb_o, B, r, R_o, 256 * 256)
+    Xd = to_dev(img.X)
+    basis = q.fit_pca(Xd, d)
+    out = q.quantize(Xd, basis, B, "bf16")
+    s = q.score(out["bins"], 256, B, r, out["hist"], 256 * 256)
+    torch.cuda.synchronize()
+    flips = float((bins_np(out["bins"], 256) != qb_o).mean())
+    assert flips <= 0.01, flips
+    a_g, a_o = auroc(s.cpu().numpy(), img.mask), auroc(s_o, img.mask)
+    assert abs(a_g - a_o) <= 0.005, (a_g, a_o)
+
+
+def test_device_status_clean_after_bf16(q):
+    ctx = q.default_context()
+    img = _case(64, 32, 32, seed=2)
+    mean, V, _, _ = oracle.fit(img.X, 16)
+    q.quantize(to_dev(img.X), (to_dev(mean), to_dev(V)), 16, "bf16", ctx=ctx)
+    assert ctx.device_status() == 0
