@@ -110,11 +110,21 @@ const char *qfca_version(void);
  *   d     number of components, 1 <= d <= min(C, 64).
  *   out   device pointers receiving mean[C], V[C][d], eigvals[d] (FP64).
  * Computes mu = (1/N) sum_p x_p and Sigma = (1/N) sum_p (x_p - mu)(x_p - mu)^T
- * with FP64 accumulation, then the top-d eigenpairs of Sigma in FP64
+ * as qfca_covariance does, then the top-d eigenpairs of Sigma in FP64
  * (Householder tridiagonalisation, bisection, inverse iteration).
  * Requires 2 <= C <= 512 and H*W >= 2. */
 qfca_status qfca_fit_pca(qfca_ctx *ctx, const float *X, qfca_fmap desc, int d,
                          const qfca_basis *out, void *stream);
+
+/* qfca_covariance -- mean[C] and covariance Sigma[C][C] (FP64, full symmetric
+ * storage, 1/N normalisation) of a feature map: the first half of the PCA fit
+ * (Sec. 3.3).  Computed with exact integer arithmetic on the BF16 tensor
+ * cores: each channel is scaled by a power of two and written as four signed
+ * 7-bit digits (a 27-bit fixed-point value, per-element error <= 2^-28 of the
+ * channel's power-of-two range), digit products are summed exactly, and the
+ * level sums are combined in int64.  Requires 2 <= C <= 512, H*W >= 2. */
+qfca_status qfca_covariance(qfca_ctx *ctx, const float *X, qfca_fmap desc, double *mean_out,
+                            double *cov_out, void *stream);
 
 /* qfca_quantize -- projection Y = (X - mean) V (Sec. 3.3) followed by uniform
  * quantisation of each component into B equally spaced bins (Sec. 3.1) and

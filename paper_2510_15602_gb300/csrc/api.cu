@@ -186,7 +186,7 @@ qfca_status check_fmap(qfca_ctx *ctx, const float *X, const qfca_fmap &m) {
     return QFCA_OK;
 }
 
-size_t bytes_mmkeys(int d) { return align_up(sizeof(uint32_t) * 2 * d, 256); }
+size_t bytes_mmkeys(int d) { return align_up(sizeof(uint32_t) * 2 * d * kKeyStride, 256); }
 
 }  // namespace
 
@@ -274,8 +274,25 @@ qfca_status qfca_fit_pca(qfca_ctx *ctx, const float *X, qfca_fmap desc, int d, c
     const long N = (long)desc.H * desc.W;
     if ((s = ensure_ws(ctx, fit_workspace_bytes(desc.C, N, d)))) return s;
     cudaError_t e = launch_fit(X, desc.layout, desc.H, desc.W, desc.C, d, out->mean, out->V, out->eigvals, ctx->ws,
-                               (cudaStream_t)stream);
+                               ctx->status_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_fit_pca");
+    return QFCA_OK;
+}
+
+qfca_status qfca_covariance(qfca_ctx *ctx, const float *X, qfca_fmap desc, double *mean_out, double *cov_out,
+                            void *stream) {
+    qfca_status s = check_ctx(ctx);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if ((s = check_fmap(ctx, X, desc))) return s;
+    if (!mean_out || !cov_out) return fail(ctx, QFCA_ERR_INVALID_ARG, "mean_out / cov_out NULL");
+    DeviceGuard g(ctx->device);
+    HookScope hs(ctx);
+    const long N = (long)desc.H * desc.W;
+    if ((s = ensure_ws(ctx, gram_workspace_bytes(desc.C, N)))) return s;
+    cudaError_t e = launch_gram_cov(X, desc.layout, desc.C, N, mean_out, cov_out, ctx->ws, ctx->status_dev,
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_covariance");
     return QFCA_OK;
 }
 

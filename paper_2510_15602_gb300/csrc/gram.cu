@@ -1,0 +1,364 @@
+// gram.cu -- the covariance of the single-image PCA fit (arXiv 2510.15602,
+// Sec. 3.3) with exact integer arithmetic on the BF16 tensor cores.
+//
+// GB300's FP64 pipe issues ~2 DFMA/clk/SM, so a plain FP64 Gram of a
+// 256x256xC256 map costs ~5 ms.  Instead:
+//   1. k_chan_absmax + k_chan_scale: per channel, the smallest e_c with |x_cp| < 2^e_c.
+//   2. k_gram: y = x * 2^-e_c (exact, |y| < 1) is written as four signed 7-bit
+//      digits, y ~= sum_i d_i 2^(-6-7i), d_i in [-64, 64] (round-to-nearest
+//      splitting in FP32, each step exact); each digit is an integer, exact in
+//      BF16.  For a 128x128 channel tile, tcgen05 accumulates in tensor memory
+//      the level sums  A_L = sum_{i+j=L} sum_p d_i(c1,p) d_j(c2,p),  L = 0..3,
+//      four FP32 accumulators of 128 columns.  Over a window of 256 pixels
+//      every partial sum is an integer of magnitude <= 4 * 64 * 64 * 256 =
+//      2^22, so the FP32 accumulation is exact; the window's sums are drained
+//      into int64 registers, T += sum_L A_L << 7(3-L), and the CTA's totals
+//      are added into a global int64 Gram with integer atomics
+//      (order-independent, so the result is deterministic).  Column sums of
+//      the digits give the channel means.  The only rounding is the 27-bit
+//      fixed-point representation of y (error <= 2^-28 2^e_c per element) and
+//      the dropped digit products of levels >= 4 (<= 3 * 2^-40 per product).
+//   3. k_cov_finalize (FP64): mu_c = 2^e_c S_c / N,
+//      Sigma_ij = 2^(e_i + e_j) T_ij 2^-33 / N - mu_i mu_j.
+//
+// One CTA (512 threads) = one 128x128 tile of the upper triangle x one range
+// of pixels; per 64-pixel sub-chunk all threads convert both channel blocks
+// into the 128-byte-swizzled K-major layout (channels are rows, pixels are K:
+// NCHW is already K-major), one thread issues the 40 MMAs (10 digit pairs x 4
+// K-steps of 16) and commits to an mbarrier (bounded wait).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+#include "tc.cuh"
+
+namespace qfca {
+namespace {
+
+constexpr int kTB = 128;         // channels per tile side
+constexpr int kSub = 64;         // pixels per sub-chunk (one 128-B swizzle row of BF16)
+constexpr int kWin = 256;        // pixels per exact accumulation window
+constexpr int kThreads = 512;
+constexpr int kSlices = 4;
+constexpr uint32_t kWaitTries = 1u << 26;
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: (v + kMagic) - kMagic rounds v to an integer
+
+__device__ __forceinline__ int tile_pair_idx(int p, int nt, int &j) {
+    int i = 0;
+    while (p >= nt - i) { p -= nt - i; i++; }
+    j = i + p;
+    return i;
+}
+
+// e_c = smallest exponent with max_p |x_cp| < 2^e_c  (stored as the max |x| bits first)
+__global__ void k_chan_absmax(const float *__restrict__ X, int layout, int C, long N, unsigned *__restrict__ amax) {
+    const int c = blockIdx.y;
+    unsigned m = 0;
+    if (layout == QFCA_NCHW) {
+        const float *row = X + (long)c * N;
+        for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < N; p += (long)gridDim.x * blockDim.x)
+            m = max(m, __float_as_uint(row[p]) & 0x7fffffffu);
+    } else {
+        for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < N; p += (long)gridDim.x * blockDim.x)
+            m = max(m, __float_as_uint(X[p * C + c]) & 0x7fffffffu);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&amax[c], m);
+}
+
+__device__ __forceinline__ float rint_exact(float v) { return __fsub_rn(__fadd_rn(v, kMagic), kMagic); }
+
+// four 7-bit digits of y (|y| < 1): y ~= d0/2^6 + d1/2^13 + d2/2^20 + d3/2^27
+__device__ __forceinline__ void digits4(float y, float &d0, float &d1, float &d2, float &d3) {
+    float t = __fmul_rn(y, 64.0f);
+    d0 = rint_exact(t);
+    float r = __fsub_rn(t, d0);
+    t = __fmul_rn(r, 128.0f);
+    d1 = rint_exact(t);
+    r = __fsub_rn(t, d1);
+    t = __fmul_rn(r, 128.0f);
+    d2 = rint_exact(t);
+    r = __fsub_rn(t, d2);
+    t = __fmul_rn(r, 128.0f);
+    d3 = rint_exact(t);
+}
+
+__device__ __forceinline__ uint32_t swz(int row, int chunk16) {
+    return (uint32_t)(row * 128 + ((chunk16 ^ (row & 7)) << 4));
+}
+
+// Convert one operand block (128 channels starting at c0) of pixels [q0, q0+64) into
+// 4 digit slices (K-major, 128-B swizzle).  Optionally accumulate per-row digit sums.
+__device__ __forceinline__ void stage_block(const float *__restrict__ X, int layout, int vec_ok, int C, long N, int c0,
+                                            long q0, long q1, const float *__restrict__ scale, uint8_t *slices,
+                                            int *__restrict__ dsum /* [4][128] or null */) {
+    // 128 rows x 8 chunks of 8 pixels = 1024 units; 2 per thread
+    for (int u = threadIdx.x; u < kTB * 8; u += kThreads) {
+        const int row = u >> 3, g = u & 7;
+        const int c = c0 + row;
+        const long p = q0 + g * 8;
+        float v[8];
+        if (vec_ok && c < C && p + 8 <= q1) {
+            const float4 a = __ldg(reinterpret_cast<const float4 *>(X + (long)c * N + p));
+            const float4 b = __ldg(reinterpret_cast<const float4 *>(X + (long)c * N + p + 4));
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                const long pe = p + e;
+                v[e] = (c < C && pe < q1) ? (layout == QFCA_NCHW ? X[(long)c * N + pe] : X[pe * C + c]) : 0.0f;
+            }
+        }
+        const float s = c < C ? scale[c] : 0.0f;
+        float dd[kSlices][8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) digits4(__fmul_rn(v[e], s), dd[0][e], dd[1][e], dd[2][e], dd[3][e]);
+#pragma unroll
+        for (int sl = 0; sl < kSlices; sl++) {
+            uint4 pk;
+            pk.x = tc::pack_bf16x2(dd[sl][0], dd[sl][1]);
+            pk.y = tc::pack_bf16x2(dd[sl][2], dd[sl][3]);
+            pk.z = tc::pack_bf16x2(dd[sl][4], dd[sl][5]);
+            pk.w = tc::pack_bf16x2(dd[sl][6], dd[sl][7]);
+            *reinterpret_cast<uint4 *>(slices + sl * (kTB * 128) + swz(row, g)) = pk;
+            if (dsum) {
+                const float t = ((dd[sl][0] + dd[sl][1]) + (dd[sl][2] + dd[sl][3])) +
+                                ((dd[sl][4] + dd[sl][5]) + (dd[sl][6] + dd[sl][7]));
+                atomicAdd(&dsum[sl * kTB + row], (int)t);
+            }
+        }
+    }
+}
+
+// Grid: n_pairs * n_split CTAs.  Gint: [C][C] int64 (upper tiles accumulated), Dsum: [4][C] int64.
+__global__ void __launch_bounds__(kThreads, 1) k_gram(const float *__restrict__ X, int layout, int vec_ok, int C, long N,
+                                                      const float *__restrict__ scale, int nt, int n_pairs,
+                                                      long chunk, unsigned long long *__restrict__ Gint,
+                                                      unsigned long long *__restrict__ Dsum,
+                                                      int *__restrict__ status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *As = smem;                                // 4 slices x 16 KB
+    uint8_t *Bs = smem + kSlices * kTB * 128;          // 4 slices x 16 KB
+    uint64_t *bar = (uint64_t *)(Bs + kSlices * kTB * 128);
+    uint32_t *tmem_slot = (uint32_t *)(bar + 1);
+    int *dsum = (int *)(tmem_slot + 4);                // [4][128]
+
+    const int pair = blockIdx.x % n_pairs, split = blockIdx.x / n_pairs;
+    int tj;
+    const int ti = tile_pair_idx(pair, nt, tj);
+    const bool diag = ti == tj;
+    const long p0 = (long)split * chunk, p1 = min(N, p0 + chunk);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_slot, 512);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_mbar_init();
+    }
+    for (int i = tid; i < kSlices * kTB; i += kThreads) dsum[i] = 0;
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = tc::idesc_bf16_f32(kTB, kTB);
+    const uint32_t a_base = tc::smem_u32(As);
+    const uint32_t b_base = diag ? a_base : tc::smem_u32(Bs);
+
+    long long tot[32];
+#pragma unroll
+    for (int j = 0; j < 32; j++) tot[j] = 0;
+    const int q = warp & 3, cg4 = warp >> 2;  // TMEM lane quarter, 32-column group
+    uint32_t phase = 0;
+    bool failed = false;
+    int in_win = 0;
+
+    for (long q0 = p0; q0 < p1; q0 += kSub) {
+        stage_block(X, layout, vec_ok, C, N, ti * kTB, q0, p1, scale, As, diag ? dsum : nullptr);
+        if (!diag) stage_block(X, layout, vec_ok, C, N, tj * kTB, q0, p1, scale, Bs, nullptr);
+        tc::fence_proxy_async_smem();
+        tc::tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc::tc_fence_after();
+            for (int L = 0; L < 4; L++) {
+                bool first = in_win == 0;
+                for (int i = 0; i <= L; i++) {
+                    const int j = L - i;
+                    for (int ks = 0; ks < 4; ks++) {
+                        const uint64_t ad = tc::sdesc_kmajor_sw128(a_base + i * kTB * 128 + ks * 32);
+                        const uint64_t bd = tc::sdesc_kmajor_sw128(b_base + j * kTB * 128 + ks * 32);
+                        tc::mma_bf16_ss(tmem + (uint32_t)(L * kTB), ad, bd, idesc, first ? 0u : 1u);
+                        first = false;
+                    }
+                }
+            }
+            tc::mma_commit(bar);
+        }
+        const bool ok = tc::mbar_wait(bar, phase, kWaitTries);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        in_win += kSub;
+        if (in_win >= kWin || q0 + kSub >= p1) {
+            // drain the window's exact level sums into int64
+            tc::tc_fence_after();
+#pragma unroll
+            for (int L = 0; L < 4; L++) {
+                uint32_t r0[16], r1[16];
+                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(L * kTB + 32 * cg4);
+                tc::tmem_ld16(ta, r0);
+                tc::tmem_ld16(ta + 16, r1);
+                tc::tmem_wait_ld();
+                const int sh = 7 * (3 - L);
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const int v0 = __float_as_int(__fadd_rn(__uint_as_float(r0[j]), kMagic)) - 0x4B400000;
+                    const int v1 = __float_as_int(__fadd_rn(__uint_as_float(r1[j]), kMagic)) - 0x4B400000;
+                    tot[j] += (long long)v0 << sh;
+                    tot[16 + j] += (long long)v1 << sh;
+                }
+            }
+            tc::tc_fence_before();
+            in_win = 0;
+        }
+        __syncthreads();  // operand buffers and accumulators free for the next sub-chunk
+    }
+    if (failed) {
+        if (tid == 0) atomicOr(status, kStatusMmaTimeout);
+        tc::mbar_wait(bar, phase ^ 1u, kWaitTries);
+    } else {
+        const int c1 = ti * kTB + 32 * q + lane;
+        if (c1 < C) {
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+                const int c2 = tj * kTB + 32 * cg4 + j;
+                if (c2 < C && tot[j] != 0) atomicAdd(&Gint[(long)c1 * C + c2], (unsigned long long)tot[j]);
+            }
+        }
+        if (diag)
+            for (int i = tid; i < kSlices * kTB; i += kThreads) {
+                const int sl = i / kTB, row = i % kTB, c = ti * kTB + row;
+                if (c < C && dsum[i] != 0) atomicAdd(&Dsum[(long)sl * C + c], (unsigned long long)(long long)dsum[i]);
+            }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, 512);
+    }
+}
+
+__global__ void k_chan_scale(const unsigned *__restrict__ amax, int C, float *__restrict__ scale, int *__restrict__ ex) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const unsigned b = amax[c];
+    int e = 0;
+    if (b != 0) {
+        int eb = (int)(b >> 23);           // biased exponent of max |x|
+        e = eb - 127 + 1;                  // max |x| < 2^(eb-127+1)
+        if (eb == 0) e = -126;             // subnormal maximum
+    }
+    ex[c] = e;
+    scale[c] = ldexpf(1.0f, -e);
+}
+
+// Sigma_ij = 2^(e_i+e_j) T_ij 2^-33 / N - mu_i mu_j ;  mu_c = 2^e_c S_c / N,
+// S_c = sum_i D_i,c 2^(-6-7i).  Writes mean[C] and the full symmetric cov[C][C].
+__global__ void k_cov_finalize(const unsigned long long *__restrict__ Gint, const unsigned long long *__restrict__ Dsum,
+                               const int *__restrict__ ex, int C, long N, double *__restrict__ mean,
+                               double *__restrict__ cov) {
+    const double invN = 1.0 / (double)N;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)C * C; e += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / C), j = (int)(e % C);
+        const int a = min(i, j), b = max(i, j);
+        auto mu = [&](int c) {
+            double s = 0.0;
+            for (int sl = 0; sl < kSlices; sl++) s += (double)(long long)Dsum[(long)sl * C + c] * ldexp(1.0, -6 - 7 * sl);
+            return ldexp(s, ex[c]) * invN;
+        };
+        const double mi = mu(a), mj = mu(b);
+        const double g = ldexp((double)(long long)Gint[(long)a * C + b], ex[a] + ex[b] - 33) * invN;
+        cov[e] = g - mi * mj;
+        if (i == j) mean[i] = mi;
+    }
+}
+
+}  // namespace
+
+struct GramPlan {
+    int nt, n_pairs, n_split;
+    long chunk;
+    size_t off_amax, off_scale, off_ex, off_G, off_D, total, smem;
+};
+
+static GramPlan gram_plan(int C, long N) {
+    GramPlan g{};
+    g.nt = (C + kTB - 1) / kTB;
+    g.n_pairs = g.nt * (g.nt + 1) / 2;
+    // about one CTA per SM per image-worth of tiles, chunks a multiple of the window
+    int want = (152 + g.n_pairs - 1) / g.n_pairs;
+    long chunk = (N + want - 1) / want;
+    chunk = (chunk + kWin - 1) / kWin * kWin;
+    if (chunk < kWin) chunk = kWin;
+    g.chunk = chunk;
+    g.n_split = (int)((N + chunk - 1) / chunk);
+    size_t o = 0;
+    auto take = [&](size_t b) { size_t at = o; o = align_up(o + b, 256); return at; };
+    g.off_amax = take(sizeof(unsigned) * C);
+    g.off_scale = take(sizeof(float) * C);
+    g.off_ex = take(sizeof(int) * C);
+    g.off_G = take(sizeof(unsigned long long) * (size_t)C * C);
+    g.off_D = take(sizeof(unsigned long long) * (size_t)kSlices * C);
+    g.total = o;
+    g.smem = 1024 + 2 * kSlices * kTB * 128 + 64 + sizeof(int) * kSlices * kTB;
+    return g;
+}
+
+size_t gram_workspace_bytes(int C, long N) { return gram_plan(C, N).total; }
+
+// mean[C] and cov[C][C] (FP64) of the feature map; ws: gram_workspace_bytes.
+cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, double *mean, double *cov, void *ws, int *status,
+                            cudaStream_t st) {
+    const GramPlan g = gram_plan(C, N);
+    char *b = (char *)ws;
+    unsigned *amax = (unsigned *)(b + g.off_amax);
+    float *scale = (float *)(b + g.off_scale);
+    int *ex = (int *)(b + g.off_ex);
+    unsigned long long *G = (unsigned long long *)(b + g.off_G);
+    unsigned long long *D = (unsigned long long *)(b + g.off_D);
+    cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned) * C, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, sizeof(unsigned long long) * (size_t)C * C, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D, 0, sizeof(unsigned long long) * kSlices * C, st);
+    if (e != cudaSuccess) return e;
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        e = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    // float4 loads need 16-B aligned rows: NCHW, N % 4 == 0, X 16-B aligned
+    const int vec_ok = layout == QFCA_NCHW && N % 4 == 0 && ((uintptr_t)X & 15) == 0;
+    const int xb = (int)((N + 256 * 64 - 1) / (256 * 64));
+    QFCA_LAUNCH("k_chan_absmax", st, k_chan_absmax<<<dim3(xb < 1 ? 1 : xb, C), 256, 0, st>>>(X, layout, C, N, amax));
+    QFCA_LAUNCH("k_chan_scale", st, k_chan_scale<<<(C + 127) / 128, 128, 0, st>>>(amax, C, scale, ex));
+    QFCA_LAUNCH("k_gram", st,
+                k_gram<<<g.n_pairs * g.n_split, kThreads, g.smem, st>>>(X, layout, vec_ok, C, N, scale, g.nt, g.n_pairs,
+                                                                       g.chunk, G, D, status));
+    const long cc = (long)C * C;
+    QFCA_LAUNCH("k_cov_finalize", st,
+                k_cov_finalize<<<(unsigned)((cc + 255) / 256), 256, 0, st>>>(G, D, ex, C, N, mean, cov));
+    return cudaGetLastError();
+}
+
+}  // namespace qfca

@@ -23,7 +23,17 @@ size_t fit_workspace_bytes(int C, long N, int d);
 
 // Enqueue the PCA fit of one image.  ws: device scratch of fit_workspace_bytes.
 cudaError_t launch_fit(const float *X, int layout, int H, int W, int C, int d, double *mean,
-                       double *V, double *eigvals, void *ws, cudaStream_t st);
+                       double *V, double *eigvals, void *ws, int *status, cudaStream_t st);
+
+// Mean and covariance of one feature map (gram.cu).
+size_t gram_workspace_bytes(int C, long N);
+cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, double *mean, double *cov, void *ws,
+                            int *status, cudaStream_t st);
+
+// Top-d eigenpairs of `mats` symmetric n x n matrices (eig.cu).
+size_t eig_workspace_bytes(int n, int d, int mats);
+cudaError_t launch_eig(const double *cov, int n, int d, int mats, double *V, double *eigvals, void *ws,
+                       cudaStream_t st);
 
 // ------------------------------------------------------------------ projection (project.cu)
 
@@ -35,6 +45,10 @@ size_t project_workspace_bytes(int C, long N, int d);
 cudaError_t launch_project(const float *X, int layout, int H, int W, int C, const double *mean,
                            const double *V, int d, int precision, float *Y, uint32_t *mm_keys,
                            void *ws, int *status, cudaStream_t st);
+
+// Per-component min/max keys live 128 B apart (one L2 line each):
+// min of component j at mm_keys[j * kKeyStride], max at mm_keys[(d + j) * kKeyStride].
+constexpr int kKeyStride = 32;
 
 // Device status word bits (set by kernels; read by qfca_device_status).
 constexpr int kStatusMmaTimeout = 1;

@@ -43,7 +43,9 @@ __global__ void __launch_bounds__(kPix) k_project_f32(const float *__restrict__ 
     __shared__ float Xs[kCh][kPix + 1];
     __shared__ __align__(16) float Vs[kCh][DT];
     __shared__ float Ms[kCh];
+    __shared__ uint32_t kmin[DT], kmax[DT];
     const int tid = threadIdx.x;
+    if (tid < DT) { kmin[tid] = 0xffffffffu; kmax[tid] = 0u; }
     const long p0 = (long)blockIdx.x * kPix;
     const long p = p0 + tid;
     float acc[DT];
@@ -103,9 +105,14 @@ __global__ void __launch_bounds__(kPix) k_project_f32(const float *__restrict__ 
             mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         }
         if (lane == 0) {
-            atomicMin(&mm_keys[j], f2key(mn));
-            atomicMax(&mm_keys[d + j], f2key(mx));
+            atomicMin(&kmin[j], f2key(mn));
+            atomicMax(&kmax[j], f2key(mx));
         }
+    }
+    __syncthreads();
+    if (tid < d) {
+        atomicMin(&mm_keys[tid * kKeyStride], kmin[tid]);
+        atomicMax(&mm_keys[(d + tid) * kKeyStride], kmax[tid]);
     }
 }
 
@@ -124,8 +131,8 @@ cudaError_t launch_project(const float *X, int layout, int H, int W, int C, cons
                            int *status, cudaStream_t st) {
     const long N = (long)H * W;
     // min keys start at the largest key, max keys at the smallest
-    cudaError_t err = cudaMemsetAsync(mm_keys, 0xff, sizeof(uint32_t) * d, st);
-    if (err == cudaSuccess) err = cudaMemsetAsync(mm_keys + d, 0x00, sizeof(uint32_t) * d, st);
+    cudaError_t err = cudaMemsetAsync(mm_keys, 0xff, sizeof(uint32_t) * d * kKeyStride, st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(mm_keys + d * kKeyStride, 0x00, sizeof(uint32_t) * d * kKeyStride, st);
     if (err != cudaSuccess) return err;
     if (precision == QFCA_BF16)
         return launch_project_bf16(X, layout, H, W, C, mean, V, d, Y, mm_keys, ws, status, st);

@@ -45,7 +45,7 @@ TcShape tc_shape(int C, int d) {
     s.nk = s.Cp / kKc;
     s.a_bytes = (size_t)s.nk * kM * 128;
     s.b_bytes = (size_t)s.nk * s.DT * 128;
-    s.smem = 1024 + s.a_bytes + s.b_bytes + 64;
+    s.smem = 1024 + s.a_bytes + s.b_bytes + 64 + 8 * 64;
     return s;
 }
 
@@ -78,6 +78,8 @@ __global__ void __launch_bounds__(kThreads) k_project_bf16(const float *__restri
     uint8_t *Bs = smem + (size_t)nk * kM * 128;
     uint64_t *bar = (uint64_t *)(Bs + (size_t)nk * DT * 128);
     uint32_t *tmem_slot = (uint32_t *)(bar + 1);
+    uint32_t *kmin = tmem_slot + 1;  // [DT]
+    uint32_t *kmax = kmin + DT;      // [DT]
     constexpr uint32_t kCols = DT < 32 ? 32 : DT;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -89,6 +91,7 @@ __global__ void __launch_bounds__(kThreads) k_project_bf16(const float *__restri
         tc::mbar_init(bar, 1);
         tc::fence_mbar_init();
     }
+    if (tid < DT) { kmin[tid] = 0xffffffffu; kmax[tid] = 0u; }
     // resident Bt: DT rows x Cp channels, 16-B chunks of 8 channels
     for (int e = tid; e < DT * (Cp / 8); e += kThreads) {
         const int j = e / (Cp / 8), c8 = e % (Cp / 8);
@@ -184,8 +187,8 @@ __global__ void __launch_bounds__(kThreads) k_project_bf16(const float *__restri
                 mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             }
             if (lane == 0) {
-                atomicMin(&mm_keys[j], f2key(mn));
-                atomicMax(&mm_keys[d + j], f2key(mx));
+                atomicMin(&kmin[j], f2key(mn));
+                atomicMax(&kmax[j], f2key(mx));
             }
         }
         tc::tc_fence_before();
@@ -199,6 +202,10 @@ __global__ void __launch_bounds__(kThreads) k_project_bf16(const float *__restri
     if (warp == 0) {
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem, kCols);
+    }
+    if (!failed && tid < d) {
+        atomicMin(&mm_keys[tid * kKeyStride], kmin[tid]);
+        atomicMax(&mm_keys[(d + tid) * kKeyStride], kmax[tid]);
     }
 }
 

@@ -36,8 +36,8 @@ __global__ void __launch_bounds__(kThreads) k_quantize(const float *__restrict__
     const int k = blockIdx.y;
     float lo, hi;
     if (range_mode == QFCA_RANGE_IMAGE) {
-        lo = key2f(mm_keys[k]);
-        hi = key2f(mm_keys[d + k]);
+        lo = key2f(mm_keys[k * kKeyStride]);
+        hi = key2f(mm_keys[(d + k) * kKeyStride]);
     } else {
         lo = lo_in[k];
         hi = hi_in[k];

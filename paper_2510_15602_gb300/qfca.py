@@ -57,6 +57,8 @@ _lib.qfca_version.argtypes = []
 _lib.qfca_version.restype = ctypes.c_char_p
 _lib.qfca_fit_pca.argtypes = [_P, _P, Fmap, _I, ctypes.POINTER(Basis), _P]
 _lib.qfca_fit_pca.restype = _I
+_lib.qfca_covariance.argtypes = [_P, _P, Fmap, _P, _P, _P]
+_lib.qfca_covariance.restype = _I
 _lib.qfca_quantize.argtypes = [_P, _P, Fmap, ctypes.POINTER(Basis), _I, _I, _I, _I, _P, _P, _P, _I, _P, _P, _P,
                                _P, _P]
 _lib.qfca_quantize.restype = _I
@@ -211,6 +213,17 @@ def fit_pca(X: torch.Tensor, d: int, layout: int = NCHW, ctx: Context | None = N
     b = Basis(mean.data_ptr(), V.data_ptr(), ev.data_ptr())
     ctx.check(_lib.qfca_fit_pca(ctx.handle, _ptr(X), fm, d, ctypes.byref(b), _P(_stream_ptr(stream))))
     return mean, V, ev
+
+
+def covariance(X: torch.Tensor, layout: int = NCHW, ctx: Context | None = None, stream=None):
+    """qfca_covariance: returns (mean[C], Sigma[C, C]) FP64 device tensors."""
+    _check_dev(X, "X", torch.float32)
+    ctx = ctx or default_context(X.device.index)
+    fm = fmap_of(X, layout)
+    mean = torch.empty(fm.C, dtype=torch.float64, device=X.device)
+    cov = torch.empty(fm.C, fm.C, dtype=torch.float64, device=X.device)
+    ctx.check(_lib.qfca_covariance(ctx.handle, _ptr(X), fm, _ptr(mean), _ptr(cov), _P(_stream_ptr(stream))))
+    return mean, cov
 
 
 def quantize(X: torch.Tensor, basis, B: int, precision="f32", layout: int = NCHW, lo=None, hi=None,
