@@ -112,7 +112,7 @@ const char *qfca_version(void);
  * Computes mu = (1/N) sum_p x_p and Sigma = (1/N) sum_p (x_p - mu)(x_p - mu)^T
  * as qfca_covariance does, then the top-d eigenpairs of Sigma in FP64
  * (Householder tridiagonalisation, bisection, inverse iteration).
- * Requires 2 <= C <= 512 and H*W >= 2. */
+ * Requires 2 <= C <= 512 and 2 <= H*W <= 2^23. */
 qfca_status qfca_fit_pca(qfca_ctx *ctx, const float *X, qfca_fmap desc, int d,
                          const qfca_basis *out, void *stream);
 
@@ -122,7 +122,8 @@ qfca_status qfca_fit_pca(qfca_ctx *ctx, const float *X, qfca_fmap desc, int d,
  * cores: each channel is scaled by a power of two and written as four signed
  * 7-bit digits (a 27-bit fixed-point value, per-element error <= 2^-28 of the
  * channel's power-of-two range), digit products are summed exactly, and the
- * level sums are combined in int64.  Requires 2 <= C <= 512, H*W >= 2. */
+ * level sums are combined in int64 (which bounds H*W to 2^23 pixels).
+ * Requires 2 <= C <= 512, 2 <= H*W <= 2^23. */
 qfca_status qfca_covariance(qfca_ctx *ctx, const float *X, qfca_fmap desc, double *mean_out,
                             double *cov_out, void *stream);
 

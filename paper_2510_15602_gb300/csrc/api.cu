@@ -181,7 +181,7 @@ qfca_status check_fmap(qfca_ctx *ctx, const float *X, const qfca_fmap &m) {
     if (!X) return fail(ctx, QFCA_ERR_INVALID_ARG, "X is NULL");
     if (m.layout != QFCA_NCHW && m.layout != QFCA_NHWC) return fail(ctx, QFCA_ERR_INVALID_ARG, "bad layout %d", m.layout);
     if (m.H < 1 || m.W < 1 || (long)m.H * m.W < 2) return fail(ctx, QFCA_ERR_INVALID_ARG, "bad H x W = %d x %d", m.H, m.W);
-    if ((long)m.H * m.W > (1L << 31) - 1) return fail(ctx, QFCA_ERR_UNSUPPORTED, "H*W too large");
+    if ((long)m.H * m.W > (1L << 23)) return fail(ctx, QFCA_ERR_UNSUPPORTED, "H*W = %ld > 2^23 pixels", (long)m.H * m.W);
     if (m.C < 2 || m.C > kMaxC) return fail(ctx, QFCA_ERR_UNSUPPORTED, "C = %d outside [2, %d]", m.C, kMaxC);
     return QFCA_OK;
 }

@@ -12,14 +12,17 @@
 //      four FP32 accumulators of 128 columns.  Over a window of 256 pixels
 //      every partial sum is an integer of magnitude <= 4 * 64 * 64 * 256 =
 //      2^22, so the FP32 accumulation is exact; the window's sums are drained
-//      into int64 registers, T += sum_L A_L << 7(3-L), and the CTA's totals
-//      are added into a global int64 Gram with integer atomics
-//      (order-independent, so the result is deterministic).  Column sums of
-//      the digits give the channel means.  The only rounding is the 27-bit
-//      fixed-point representation of y (error <= 2^-28 2^e_c per element) and
-//      the dropped digit products of levels >= 4 (<= 3 * 2^-40 per product).
+//      into int64 registers, T += sum_L A_L << 7(4-L) (units of 2^-40), and
+//      the CTA's totals are added into a global int64 Gram with integer
+//      atomics (order-independent, so the result is deterministic).  Column
+//      sums of the digits give the channel means.  On the diagonal the level-4
+//      products sum_p (2 d1 d3 + d2^2) are added exactly as well (d2^2 >= 0
+//      would otherwise bias every variance low); off the diagonal the dropped
+//      level >= 4 products are zero-mean (<= 3 * 64^2 * 2^-40 each).  The
+//      other rounding is the 27-bit fixed-point representation of y
+//      (error <= 2^-28 2^e_c per element, round to nearest).
 //   3. k_cov_finalize (FP64): mu_c = 2^e_c S_c / N,
-//      Sigma_ij = 2^(e_i + e_j) T_ij 2^-33 / N - mu_i mu_j.
+//      Sigma_ij = 2^(e_i + e_j) T_ij 2^-40 / N - mu_i mu_j.
 //
 // One CTA (512 threads) = one 128x128 tile of the upper triangle x one range
 // of pixels; per 64-pixel sub-chunk all threads convert both channel blocks
@@ -93,7 +96,8 @@ __device__ __forceinline__ uint32_t swz(int row, int chunk16) {
 // 4 digit slices (K-major, 128-B swizzle).  Optionally accumulate per-row digit sums.
 __device__ __forceinline__ void stage_block(const float *__restrict__ X, int layout, int vec_ok, int C, long N, int c0,
                                             long q0, long q1, const float *__restrict__ scale, uint8_t *slices,
-                                            int *__restrict__ dsum /* [4][128] or null */) {
+                                            int *__restrict__ dsum /* [4][128] or null */,
+                                            unsigned long long *__restrict__ dsq /* [128] level-4 diagonal */) {
     // 128 rows x 8 chunks of 8 pixels = 1024 units; 2 per thread
     for (int u = threadIdx.x; u < kTB * 8; u += kThreads) {
         const int row = u >> 3, g = u & 7;
@@ -129,6 +133,15 @@ __device__ __forceinline__ void stage_block(const float *__restrict__ X, int lay
                 atomicAdd(&dsum[sl * kTB + row], (int)t);
             }
         }
+        if (dsq) {
+            int t4 = 0;  // exact: |2 d1 d3 + d2^2| <= 3 * 2^12 per pixel
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                const int d1 = (int)dd[1][e], d2 = (int)dd[2][e], d3 = (int)dd[3][e];
+                t4 += 2 * d1 * d3 + d2 * d2;
+            }
+            atomicAdd(&dsq[row], (unsigned long long)(long long)t4);
+        }
     }
 }
 
@@ -144,7 +157,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const float *__restrict__ 
     uint8_t *Bs = smem + kSlices * kTB * 128;          // 4 slices x 16 KB
     uint64_t *bar = (uint64_t *)(Bs + kSlices * kTB * 128);
     uint32_t *tmem_slot = (uint32_t *)(bar + 1);
-    int *dsum = (int *)(tmem_slot + 4);                // [4][128]
+    unsigned long long *dsq = (unsigned long long *)(tmem_slot + 4);  // [128] (8-B aligned: bar is)
+    int *dsum = (int *)(dsq + kTB);                                    // [4][128]
 
     const int pair = blockIdx.x % n_pairs, split = blockIdx.x / n_pairs;
     int tj;
@@ -162,6 +176,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const float *__restrict__ 
         tc::fence_mbar_init();
     }
     for (int i = tid; i < kSlices * kTB; i += kThreads) dsum[i] = 0;
+    for (int i = tid; i < kTB; i += kThreads) dsq[i] = 0ull;
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -179,8 +194,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const float *__restrict__ 
     int in_win = 0;
 
     for (long q0 = p0; q0 < p1; q0 += kSub) {
-        stage_block(X, layout, vec_ok, C, N, ti * kTB, q0, p1, scale, As, diag ? dsum : nullptr);
-        if (!diag) stage_block(X, layout, vec_ok, C, N, tj * kTB, q0, p1, scale, Bs, nullptr);
+        stage_block(X, layout, vec_ok, C, N, ti * kTB, q0, p1, scale, As, diag ? dsum : nullptr,
+                    diag ? dsq : nullptr);
+        if (!diag) stage_block(X, layout, vec_ok, C, N, tj * kTB, q0, p1, scale, Bs, nullptr, nullptr);
         tc::fence_proxy_async_smem();
         tc::tc_fence_before();
         __syncthreads();
@@ -217,7 +233,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const float *__restrict__ 
                 tc::tmem_ld16(ta, r0);
                 tc::tmem_ld16(ta + 16, r1);
                 tc::tmem_wait_ld();
-                const int sh = 7 * (3 - L);
+                const int sh = 7 * (4 - L);
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
                     const int v0 = __float_as_int(__fadd_rn(__uint_as_float(r0[j]), kMagic)) - 0x4B400000;
@@ -243,11 +259,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const float *__restrict__ 
                 if (c2 < C && tot[j] != 0) atomicAdd(&Gint[(long)c1 * C + c2], (unsigned long long)tot[j]);
             }
         }
-        if (diag)
+        if (diag) {
             for (int i = tid; i < kSlices * kTB; i += kThreads) {
                 const int sl = i / kTB, row = i % kTB, c = ti * kTB + row;
                 if (c < C && dsum[i] != 0) atomicAdd(&Dsum[(long)sl * C + c], (unsigned long long)(long long)dsum[i]);
             }
+            for (int row = tid; row < kTB; row += kThreads) {
+                const int c = ti * kTB + row;
+                if (c < C && dsq[row] != 0ull) atomicAdd(&Gint[(long)c * C + c], dsq[row]);
+            }
+        }
     }
     tc::tc_fence_before();
     __syncthreads();
@@ -271,7 +292,7 @@ __global__ void k_chan_scale(const unsigned *__restrict__ amax, int C, float *__
     scale[c] = ldexpf(1.0f, -e);
 }
 
-// Sigma_ij = 2^(e_i+e_j) T_ij 2^-33 / N - mu_i mu_j ;  mu_c = 2^e_c S_c / N,
+// Sigma_ij = 2^(e_i+e_j) T_ij 2^-40 / N - mu_i mu_j ;  mu_c = 2^e_c S_c / N,
 // S_c = sum_i D_i,c 2^(-6-7i).  Writes mean[C] and the full symmetric cov[C][C].
 __global__ void k_cov_finalize(const unsigned long long *__restrict__ Gint, const unsigned long long *__restrict__ Dsum,
                                const int *__restrict__ ex, int C, long N, double *__restrict__ mean,
@@ -286,7 +307,7 @@ __global__ void k_cov_finalize(const unsigned long long *__restrict__ Gint, cons
             return ldexp(s, ex[c]) * invN;
         };
         const double mi = mu(a), mj = mu(b);
-        const double g = ldexp((double)(long long)Gint[(long)a * C + b], ex[a] + ex[b] - 33) * invN;
+        const double g = ldexp((double)(long long)Gint[(long)a * C + b], ex[a] + ex[b] - 40) * invN;
         cov[e] = g - mi * mj;
         if (i == j) mean[i] = mi;
     }
@@ -319,7 +340,7 @@ static GramPlan gram_plan(int C, long N) {
     g.off_G = take(sizeof(unsigned long long) * (size_t)C * C);
     g.off_D = take(sizeof(unsigned long long) * (size_t)kSlices * C);
     g.total = o;
-    g.smem = 1024 + 2 * kSlices * kTB * 128 + 64 + sizeof(int) * kSlices * kTB;
+    g.smem = 1024 + 2 * kSlices * kTB * 128 + 64 + sizeof(int) * kSlices * kTB + sizeof(unsigned long long) * kTB;
     return g;
 }
 
