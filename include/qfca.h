@@ -166,6 +166,33 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
  * *out receives the word; returns QFCA_ERR_TIMEOUT when it was non-zero. */
 qfca_status qfca_device_status(qfca_ctx *ctx, int *out);
 
+/* qfca_score_noalloc -- the same computation as qfca_score (without the
+ * optional numerator output), for callers that cannot allocate device memory:
+ * code that runs under a host application or memory manager that owns every
+ * device allocation, inside a process with a hard device-memory budget, or
+ * in a latency-critical loop where the implicit synchronisation of
+ * cudaMalloc/cudaFree is not acceptable.  It takes no context (creating one
+ * allocates) and calls no cudaMalloc, cudaFree or allocating library routine.
+ * The paper has no counterpart; this is an interface convenience.
+ *
+ * Its scratch (the per-pixel sums of the EMD numerators, 8 bytes per pixel)
+ * is one file-scope device array of 4 MiB in the library, present on every
+ * GPU that loads the library until the process exits.  Hence:
+ *  - images are limited to H*W <= 524288 pixels; larger ones return
+ *    QFCA_ERR_UNSUPPORTED without enqueuing anything;
+ *  - every call shares that array: calls that overlap on the GPU (on
+ *    different streams, or from different threads, without ordering between
+ *    them) race and give wrong results; serialise them on one stream;
+ *  - work runs on the calling thread's current CUDA device; all pointers
+ *    must belong to it.  The first call on a device looks up the array's
+ *    device address (once per device); make that first call before any CUDA
+ *    stream capture.
+ * Arguments, layouts and the result are those of qfca_score; invalid
+ * arguments return QFCA_ERR_INVALID_ARG, CUDA errors QFCA_ERR_CUDA. */
+qfca_status qfca_score_noalloc(const uint8_t *bins, int H, int W, int pitch, int d, int B, int r,
+                               const uint32_t *ref_hist, uint32_t ref_total, float *score,
+                               void *stream);
+
 /* ---------------------------------------------------------------- tracing */
 
 /* Number of kernels the library has launched through `ctx` since creation

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace qfca {
@@ -167,4 +169,58 @@ cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d,
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- allocation-free variant
+
+// Scratch of qfca_score_noalloc: the per-pixel sums of the integer EMD
+// numerators, u64 [H][W].  It lives in the module image, so every device that
+// loads the library holds it (4 MiB) until the process exits; no call
+// allocates anything.
+namespace {
+constexpr long kNoAllocMaxPixels = 1L << 19;
+__device__ __align__(256) unsigned long long g_noalloc_acc[kNoAllocMaxPixels];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned long long *g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
 }  // namespace qfca
+
+extern "C" qfca_status qfca_score_noalloc(const uint8_t *bins, int H, int W, int pitch, int d, int B, int r,
+                                          const uint32_t *ref_hist, uint32_t ref_total, float *score,
+                                          void *stream) {
+    using namespace qfca;
+    if (!bins || !ref_hist || !score) return QFCA_ERR_INVALID_ARG;
+    if (H < 1 || W < 1 || pitch < W || pitch % 16 != 0) return QFCA_ERR_INVALID_ARG;
+    if (d < 1 || d > kMaxD || B < 2 || B > kMaxB || r < 1 || 2 * r + 1 > 127 || ref_total < 1)
+        return QFCA_ERR_INVALID_ARG;
+    if ((long)H * W > kNoAllocMaxPixels) return QFCA_ERR_UNSUPPORTED;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return QFCA_ERR_CUDA;
+    }
+    unsigned long long *acc;
+    {
+        // once per device, with that device current: the device address of the
+        // scratch array (in host code the symbol is only a stand-in)
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_acc) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return QFCA_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = (unsigned long long *)p;
+        }
+        acc = g_noalloc_ptr[dev];
+    }
+    const cudaError_t e = launch_score_ws(bins, H, W, pitch, d, B, r, ref_hist, ref_total, score, nullptr, acc,
+                                          (cudaStream_t)stream);
+    if (e == cudaErrorNotSupported) return QFCA_ERR_UNSUPPORTED;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return QFCA_ERR_CUDA;
+    }
+    return QFCA_OK;
+}
