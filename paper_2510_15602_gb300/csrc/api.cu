@@ -275,6 +275,7 @@ qfca_status qfca_fit_pca(qfca_ctx *ctx, const float *X, qfca_fmap desc, int d, c
     if ((s = ensure_ws(ctx, fit_workspace_bytes(desc.C, N, d)))) return s;
     cudaError_t e = launch_fit(X, desc.layout, desc.H, desc.W, desc.C, d, out->mean, out->V, out->eigvals, ctx->ws,
                                ctx->status_dev, (cudaStream_t)stream);
+    if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "eigensolver shape C=%d d=%d", desc.C, d);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_fit_pca");
     return QFCA_OK;
 }
@@ -290,7 +291,7 @@ qfca_status qfca_covariance(qfca_ctx *ctx, const float *X, qfca_fmap desc, doubl
     HookScope hs(ctx);
     const long N = (long)desc.H * desc.W;
     if ((s = ensure_ws(ctx, gram_workspace_bytes(desc.C, N)))) return s;
-    cudaError_t e = launch_gram_cov(X, desc.layout, desc.C, N, mean_out, cov_out, ctx->ws, ctx->status_dev,
+    cudaError_t e = launch_gram_cov(X, desc.layout, desc.C, N, mean_out, cov_out, nullptr, ctx->ws, ctx->status_dev,
                                     (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_covariance");
     return QFCA_OK;

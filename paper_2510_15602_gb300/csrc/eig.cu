@@ -1,30 +1,35 @@
-// eig.cu -- top-d eigenpairs of a symmetric C x C covariance in FP64 (the
-// eigendecomposition of the single-image PCA fit, arXiv 2510.15602, Sec. 3.3).
+// eig.cu -- top-d eigenpairs of a symmetric C x C covariance (the eigen-
+// decomposition of the single-image PCA fit, arXiv 2510.15602, Sec. 3.3) to
+// FP64-class accuracy, with the O(C^3) work on the FP32 pipe.
 //
-// One thread-block cluster of kR = 8 CTAs per matrix (GB300's FP64 pipe is
-// ~2 DFMA/clk/SM, so one matrix is spread over 8 SMs):
-//   1. Householder tridiagonalisation A = Q T Q^T.  Row i of the trailing
-//      matrix lives in CTA (i mod 8) -- in shared memory when it fits, else in
-//      global memory.  Step k: every CTA reads row k (= column k) from its
-//      owner through distributed shared memory and forms the reflector
-//      (v, tau) redundantly; each CTA computes p = tau A v for its own rows
-//      and broadcasts them into every CTA's p vector (DSMEM stores); cluster
-//      barrier; w = p - (tau/2)(p.v) v; each CTA applies the rank-2 update
-//      A -= v w^T + w v^T to its own rows; cluster barrier.
-//   2. Shifts: each eigenvalue of T by warp-wide multisection on the FP32
-//      Sturm count (33 points per round);  inverse iteration in FP64 on T
-//      (LU with partial pivoting, three solves) gives the eigenvector of T;
-//      vectors whose shifts lie within 1e-3 ||T|| of each other are
-//      re-orthogonalised (Gram-Schmidt); FP64 Rayleigh quotients give the
-//      eigenvalues, sorted descending.
-//   3. Back-transformation V = H_0 ... H_{n-3} Z, each CTA for its own
-//      columns; sign normalisation (largest-magnitude entry positive).
-// All waits are cluster barriers (hardware), so no spin loop can hang.
+// GB300's SIMT FP64 issues well under one DFMA per clock per SM (measured),
+// so the Householder reduction runs in float-float arithmetic (ff.cuh: ~48
+// significant bits from error-free FP32 transformations, 128 lanes/clk/SM).
+// One thread-block cluster of R CTAs per matrix (R = 2 for C <= 256, up to 8),
+// the lower triangle packed in shared memory, rows distributed cyclically:
+//   1. Householder tridiagonalisation A = Q T Q^T.  Step k: every CTA holds
+//      x = A[k+1.., k] (gathered through distributed shared memory at the end
+//      of step k-1) and forms (v, tau) (scalars in FP64 by one thread); each
+//      CTA computes its partial q of A v from the elements it stores (row part
+//      and column part of the symmetric product) and pushes it into every
+//      CTA; cluster barrier; p = tau sum_r q_r (fixed order),
+//      w = p - (tau/2)(p.v) v; each CTA applies A -= v w^T + w v^T to its
+//      lower-triangle rows and pushes the new column k+1 into every CTA;
+//      cluster barrier.
+//   2. Shifts by warp multisection on the FP32 Sturm count; FP64 inverse
+//      iteration on T (LU with partial pivoting, three solves); selective
+//      Gram-Schmidt for shifts within 1e-3 ||T||; FP64 Rayleigh quotients;
+//      stable descending order.
+//   3. Back-transformation V = H_0 ... H_{n-3} Z in float-float, columns
+//      distributed over the cluster; sign normalisation (largest-magnitude
+//      entry positive); FP64 output.
+// Every wait is a hardware barrier (cluster or CTA): no spin loop.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
+#include "ff.cuh"
 #include "internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -32,17 +37,17 @@ namespace cg = cooperative_groups;
 namespace qfca {
 namespace {
 
-constexpr int kR = 8;
+using ffa::ff;
 constexpr int kT = 512;
 constexpr int kNW = kT / 32;
-constexpr size_t kRowsSmemMax = 150 * 1024;
+constexpr size_t kSmemMax = 200 * 1024;
 
 struct EigArgs {
-    const double *cov;  // [mats][n][n]
-    int n, d;
-    int rows_in_smem;
-    double *rows_g;     // [mats][kR][rows_per][n]   (when rows are not in smem)
+    const ff *cov;  // [mats][n][n] float-float covariance
+    int n, d, R;
+    long region0;   // ff elements of the first shared region (packed rows; reused by phases 2/3)
     double *dg, *ed, *tau, *v0;  // [mats][n]
+    ff *Vh;                      // [mats][n][n]  Householder vectors (row k: v_k, length n-k-1)
     double *Z;                   // [mats][d][n]
     double *lu;                  // [mats][d][5][n]
     uint8_t *piv;                // [mats][d][n]
@@ -53,25 +58,50 @@ struct EigArgs {
     double *eig;                 // [mats][d]
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+__host__ __device__ inline long row_off(int l, int r, int R) {
+    return (long)l * (r + 1) + (long)R * l * (l - 1) / 2;
 }
 
-__device__ double block_sum(double v, double *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_sum(v);
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        double t = lane < kNW ? red[lane] : 0.0;
-        t = warp_sum(t);
-        if (lane == 0) red[0] = t;
+__host__ __device__ inline long rows_elems(int n, int R) {
+    long mx = 0;
+    for (int r = 0; r < R; r++) {
+        const int L = r < n ? (n - r + R - 1) / R : 0;
+        const long e = row_off(L, r, R);
+        if (e > mx) mx = e;
     }
+    return mx;
+}
+
+__device__ __forceinline__ void acc_down(ffa::acc &A, int o) {
+    ffa::acc B;
+    B.s = __shfl_down_sync(0xffffffffu, A.s, o);
+    B.c = __shfl_down_sync(0xffffffffu, A.c, o);
+    ffa::acc_merge(A, B);
+}
+
+// Deterministic block reduction; every thread gets the same value.
+__device__ ff block_acc(ffa::acc A, ffa::acc *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc_down(A, o);
     __syncthreads();
-    const double t = red[0];
+    if (lane == 0) red[warp] = A;
+    __syncthreads();
+    ffa::acc T = red[0];
+    for (int w = 1; w < kNW; w++) ffa::acc_merge(T, red[w]);
+    __syncthreads();
+    return ffa::acc_value(T);
+}
+
+__device__ double block_sum_d(double v, double *redd) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) redd[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < kNW; w++) t += redd[w];
     __syncthreads();
     return t;
 }
@@ -89,8 +119,7 @@ __device__ int sturm_count(const float *dg, const float *e2, int n, float x) {
     return cnt;
 }
 
-// LU factorisation with partial pivoting of the tridiagonal T - sigma I (FP64).
-// u0i: reciprocal pivots, u1/u2: first/second super-diagonals of U, lm: multipliers.
+// LU with partial pivoting of the tridiagonal T - sigma I (FP64); u0i: reciprocal pivots.
 __device__ void tri_factor(const double *dg, const double *ed, int n, double sigma, double tiny, double *u0i,
                            double *u1, double *u2, double *lm, uint8_t *piv) {
     double r0 = dg[0] - sigma, r1 = n > 1 ? ed[0] : 0.0;
@@ -126,126 +155,206 @@ __device__ void tri_solve(int n, const double *u0i, const double *u1, const doub
     for (int i = n - 3; i >= 0; i--) x[i] = (x[i] - u1[i] * x[i + 1] - u2[i] * x[i + 2]) * u0i[i];
 }
 
-__global__ void __cluster_dims__(kR, 1, 1) __launch_bounds__(kT, 1) k_eig_cluster(EigArgs a) {
+__global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
     cg::cluster_group cl = cg::this_cluster();
+    const int R = a.R;
     const int r = (int)cl.block_rank();
-    const int mat = blockIdx.x / kR;
+    const int mat = blockIdx.x / R;
     const int n = a.n, d = a.d;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int rows_per = (n + kR - 1) / kR;
-    const int ncol = d > r ? (d - r + kR - 1) / kR : 0;  // own output columns j = r, r+kR, ...
+    const int nloc = r < n ? (n - r + R - 1) / R : 0;  // own rows i = r + l R
 
-    extern __shared__ __align__(16) double sm[];
-    double *rows = a.rows_in_smem ? sm : a.rows_g + ((long)mat * kR + r) * rows_per * n;
-    double *vsh = sm + (a.rows_in_smem ? (size_t)rows_per * n : 0);
-    double *psh = vsh + n;
-    double *wsh = psh + n;
-    double *red = wsh + n;
-    double *coef = red + 32;
-    double *Wo = coef + 64;  // [n][ncol]
+    extern __shared__ __align__(16) unsigned char smraw[];
+    ff *rows = reinterpret_cast<ff *>(smraw);        // region 0
+    ff *qbuf = rows + a.region0;                     // [R][n] partial products pushed by every CTA
+    ff *xa = qbuf + (size_t)R * n;                   // [n] current column (x)
+    ff *xb = xa + n;                                 // [n] next column
+    ff *pbuf = xb + n;                               // [n]
+    ff *wbuf = pbuf + n;                             // [n]
+    ffa::acc *red = reinterpret_cast<ffa::acc *>(wbuf + n);  // [kNW]
+    ff *fsc = reinterpret_cast<ff *>(red + kNW);             // [4] step scalars in ff
+    double *scal = reinterpret_cast<double *>(fsc + 4);      // [4]
 
-    const double *S = a.cov + (long)mat * n * n;
+    const ff *S = a.cov + (long)mat * n * n;
     double *dg = a.dg + (long)mat * n, *ed = a.ed + (long)mat * n;
     double *tau_g = a.tau + (long)mat * n, *v0_g = a.v0 + (long)mat * n;
+    ff *Vh = a.Vh + (long)mat * n * n;
 
-    // rows of CTA `who` (local row lr): pointer valid cluster-wide
-    auto row_of = [&](int who, int lr) -> double * {
-        if (a.rows_in_smem) return cl.map_shared_rank(sm, who) + (size_t)lr * n;
-        return a.rows_g + (((long)mat * kR + who) * rows_per + lr) * n;
-    };
-
-    for (int lr = 0; lr * kR + r < n; lr++)
-        for (int j = tid; j < n; j += kT) rows[(size_t)lr * n + j] = S[(long)(lr * kR + r) * n + j];
+    // ---- own lower-triangle rows; column 0 below the diagonal into every CTA
+    for (int l = 0; l < nloc; l++) {
+        const int i = r + l * R;
+        ff *row = rows + row_off(l, r, R);
+        for (int j = tid; j <= i; j += kT) row[j] = S[(long)i * n + j];
+    }
+    __syncthreads();
+    for (int l = tid; l < nloc; l += kT) {
+        const int i = r + l * R;
+        if (i >= 1) {
+            const ff x = rows[row_off(l, r, R)];  // A[i][0]
+            for (int dst = 0; dst < R; dst++) cl.map_shared_rank(xa, dst)[i - 1] = x;
+        } else {
+            dg[0] = ffa::to_double(rows[0]);
+        }
+    }
     cl.sync();
 
+    ff *xcur = xa, *xnext = xb;
     // ---------------------------------------------------------------- 1. tridiagonalisation
     for (int k = 0; k + 2 < n; k++) {
         const int m = n - k - 1;
-        const int owner = k % kR;
-        const double *rk = row_of(owner, k / kR);
-        double part = 0.0;
-        for (int i = tid; i < m; i += kT) {
-            const double x = rk[k + 1 + i];
-            vsh[i] = x;
-            if (i >= 1) part += x * x;
+        ffa::acc A = ffa::acc_zero();
+        for (int j = 1 + tid; j < m; j += kT) ffa::acc_fma(A, xcur[j], xcur[j]);
+        const ff sig = block_acc(A, red);  // identical in every CTA of the cluster
+        if (tid == 0) {
+            const double alpha = ffa::to_double(xcur[0]);
+            const double sigma = ffa::to_double(sig);
+            double tau = 0.0, ek = alpha, v0 = alpha;
+            if (sigma > 0.0) {
+                const double mu = sqrt(alpha * alpha + sigma);
+                v0 = alpha >= 0.0 ? alpha + mu : alpha - mu;
+                ek = alpha >= 0.0 ? -mu : mu;
+                tau = 2.0 / (v0 * v0 + sigma);
+            }
+            scal[0] = tau;
+            fsc[0] = ffa::from_double(tau);
+            fsc[1] = ffa::from_double(v0);
+            fsc[2] = ffa::from_double(0.5 * tau);
+            if (r == 0) { tau_g[k] = tau; v0_g[k] = v0; ed[k] = ek; }
         }
-        const double sigma = block_sum(part, red);
-        const double alpha = vsh[0];
-        double tau = 0.0, ek = alpha, v0 = alpha;
-        if (sigma > 0.0) {
-            const double mu = sqrt(alpha * alpha + sigma);
-            v0 = alpha >= 0.0 ? alpha + mu : alpha - mu;
-            ek = alpha >= 0.0 ? -mu : mu;
-            tau = 2.0 / (v0 * v0 + sigma);
-        }
-        __syncthreads();  // every thread has read alpha = vsh[0]
-        if (tid == 0) vsh[0] = v0;
-        if (r == 0 && tid == 0) { tau_g[k] = tau; v0_g[k] = v0; ed[k] = ek; }
-        if (r == owner && tid == 0) dg[k] = rk[k];
         __syncthreads();
-        if (tau == 0.0) continue;  // identical in every CTA of the cluster
-        // first own row index >= k+1
-        const int i0 = (k + 1) + ((r - (k + 1)) % kR + kR) % kR;
-        for (int i = i0 + warp * kR; i < n; i += kNW * kR) {
-            const double *row = rows + (size_t)(i / kR) * n + (k + 1);
-            double acc = 0.0;
-            for (int j = lane; j < m; j += 32) acc = fma(row[j], vsh[j], acc);
-            acc = warp_sum(acc) * tau;
-            if (lane < kR) cl.map_shared_rank(psh, lane)[i - k - 1] = acc;
+        const double tau_d = scal[0];
+        const ff tau = fsc[0], v0 = fsc[1], htau = fsc[2];
+        if (r == 0)
+            for (int j = tid; j < m; j += kT) Vh[(long)k * n + j] = j == 0 ? v0 : xcur[j];
+        int l0 = (k + 1 - r + R - 1) / R;  // first own row with i >= k+1
+        if (l0 < 0) l0 = 0;
+        if (tau_d != 0.0) {
+            // ---- column part of the own partial product: sum over own rows i > jc of A[i][jc] v_i
+            for (int jc = k + 1 + tid; jc < n; jc += kT) {
+                ffa::acc Q = ffa::acc_zero();
+                int lc = (jc + 1 - r + R - 1) / R;
+                if (lc < 0) lc = 0;
+                for (int l = lc; l < nloc; l++) {
+                    const int i = r + l * R;  // i >= jc + 1 >= k + 2: v_i = x_{i-k-1}
+                    ffa::acc_fma(Q, rows[row_off(l, r, R) + jc], xcur[i - k - 1]);
+                }
+                pbuf[jc - k - 1] = ffa::acc_value(Q);
+            }
+            __syncthreads();
+            // ---- plus the row part for own rows i >= k+1: sum_{j=k+1..i} A[i][j] v_j
+            for (int l = l0 + warp; l < nloc; l += kNW) {
+                const int i = r + l * R;
+                const ff *row = rows + row_off(l, r, R);
+                ffa::acc Q = ffa::acc_zero();
+                for (int j = k + 1 + lane; j <= i; j += 32) ffa::acc_fma(Q, row[j], j == k + 1 ? v0 : xcur[j - k - 1]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc_down(Q, o);
+                if (lane == 0) {
+                    ffa::acc_add(Q, pbuf[i - k - 1]);
+                    pbuf[i - k - 1] = ffa::acc_value(Q);
+                }
+            }
+            __syncthreads();
+            for (int j = tid; j < m; j += kT) {
+                const ff q = pbuf[j];
+                for (int dst = 0; dst < R; dst++) cl.map_shared_rank(qbuf, dst)[(size_t)r * n + j] = q;
+            }
+            cl.sync();
+            // ---- p = tau sum_r q_r ; w = p - (tau/2)(p.v) v
+            ffa::acc PV = ffa::acc_zero();
+            for (int j = tid; j < m; j += kT) {
+                ffa::acc P = ffa::acc_zero();
+                for (int s = 0; s < R; s++) ffa::acc_add(P, qbuf[(size_t)s * n + j]);
+                const ff p = ffa::mul(tau, ffa::acc_value(P));
+                pbuf[j] = p;
+                ffa::acc_fma(PV, p, j == 0 ? v0 : xcur[j]);
+            }
+            const ff pv = block_acc(PV, red);
+            const ff K = ffa::mul(htau, pv);
+            for (int j = tid; j < m; j += kT) wbuf[j] = ffa::sub(pbuf[j], ffa::mul(K, j == 0 ? v0 : xcur[j]));
+            __syncthreads();
+            // ---- rank-2 update of own rows (lower part); push the new column k+1
+            for (int l = l0 + warp; l < nloc; l += kNW) {
+                const int i = r + l * R;
+                ff *row = rows + row_off(l, r, R);
+                const int ii = i - k - 1;
+                const ff vi = ii == 0 ? v0 : xcur[ii];
+                const ff wi = wbuf[ii];
+                for (int j = k + 1 + lane; j <= i; j += 32) {
+                    const int jj = j - k - 1;
+                    const ff t = ffa::add(ffa::mul(vi, wbuf[jj]), ffa::mul(wi, jj == 0 ? v0 : xcur[jj]));
+                    const ff nv = ffa::sub(row[j], t);
+                    row[j] = nv;
+                    if (jj == 0 && i >= k + 2)
+                        for (int dst = 0; dst < R; dst++) cl.map_shared_rank(xnext, dst)[i - k - 2] = nv;
+                }
+            }
+        } else {
+            // no reflection: only gather the next column
+            int lg = (k + 2 - r + R - 1) / R;
+            if (lg < 0) lg = 0;
+            for (int l = lg + tid; l < nloc; l += kT) {
+                const int i = r + l * R;
+                const ff nv = rows[row_off(l, r, R) + k + 1];
+                for (int dst = 0; dst < R; dst++) cl.map_shared_rank(xnext, dst)[i - k - 2] = nv;
+            }
         }
-        cl.sync();
-        double pv = 0.0;
-        for (int i = tid; i < m; i += kT) pv += psh[i] * vsh[i];
-        const double K = 0.5 * tau * block_sum(pv, red);
-        for (int i = tid; i < m; i += kT) wsh[i] = psh[i] - K * vsh[i];
         __syncthreads();
-        for (int i = i0 + warp * kR; i < n; i += kNW * kR) {
-            double *row = rows + (size_t)(i / kR) * n + (k + 1);
-            const double vi = vsh[i - k - 1], wi = wsh[i - k - 1];
-            for (int j = lane; j < m; j += 32) row[j] = row[j] - vi * wsh[j] - wi * vsh[j];
-        }
+        if (tid == 0 && (k + 1) % R == r) dg[k + 1] = ffa::to_double(rows[row_off((k + 1) / R, r, R) + k + 1]);
         cl.sync();
+        ff *t = xcur;
+        xcur = xnext;
+        xnext = t;
     }
     if (tid == 0) {
-        if (n >= 2) {
-            if (r == (n - 2) % kR) dg[n - 2] = rows[(size_t)((n - 2) / kR) * n + (n - 2)];
-            if (r == (n - 1) % kR) ed[n - 2] = rows[(size_t)((n - 1) / kR) * n + (n - 2)];
-            if (r == 0) { tau_g[n - 2] = 0.0; v0_g[n - 2] = 0.0; }
+        if (r == 0) {
+            ed[n - 1] = 0.0;
+            tau_g[n - 1] = 0.0;
+            v0_g[n - 1] = 0.0;
+            if (n >= 2) { tau_g[n - 2] = 0.0; v0_g[n - 2] = 0.0; }
         }
-        if (r == (n - 1) % kR) dg[n - 1] = rows[(size_t)((n - 1) / kR) * n + (n - 1)];
-        if (r == 0) { ed[n - 1] = 0.0; tau_g[n - 1] = 0.0; v0_g[n - 1] = 0.0; }
+        if (n >= 2 && (n - 1) % R == r) {
+            const ff *row = rows + row_off((n - 1) / R, r, R);
+            ed[n - 2] = ffa::to_double(row[n - 2]);
+            dg[n - 1] = ffa::to_double(row[n - 1]);
+        }
     }
     cl.sync();
 
     // ---------------------------------------------------------------- 2. eigenpairs of T
-    float *dg32 = reinterpret_cast<float *>(psh);
+    double *dgs = reinterpret_cast<double *>(rows);  // region 0 reused
+    double *eds = dgs + n;
+    double *redd = eds + n;                           // [2 * kNW]
+    float *dg32 = reinterpret_cast<float *>(redd + 2 * kNW);
     float *e232 = dg32 + n;
     for (int i = tid; i < n; i += kT) {
+        dgs[i] = dg[i];
+        eds[i] = ed[i];
         dg32[i] = (float)dg[i];
         e232[i] = (float)(ed[i] * ed[i]);
     }
+    __syncthreads();
     double glo = 1e300, ghi = -1e300;
     for (int i = tid; i < n; i += kT) {
-        const double rr = (i > 0 ? fabs(ed[i - 1]) : 0.0) + (i < n - 1 ? fabs(ed[i]) : 0.0);
-        glo = fmin(glo, dg[i] - rr);
-        ghi = fmax(ghi, dg[i] + rr);
+        const double rr = (i > 0 ? fabs(eds[i - 1]) : 0.0) + (i < n - 1 ? fabs(eds[i]) : 0.0);
+        glo = fmin(glo, dgs[i] - rr);
+        ghi = fmax(ghi, dgs[i] + rr);
     }
-    // block min / max
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, o));
         ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
     }
+    if (lane == 0) { redd[warp] = glo; redd[kNW + warp] = ghi; }
     __syncthreads();
-    if (lane == 0) { red[warp] = glo; coef[warp] = ghi; }
-    __syncthreads();
-    glo = red[0];
-    ghi = coef[0];
-    for (int w = 1; w < kNW; w++) { glo = fmin(glo, red[w]); ghi = fmax(ghi, coef[w]); }
+    glo = redd[0];
+    ghi = redd[kNW];
+    for (int w = 1; w < kNW; w++) { glo = fmin(glo, redd[w]); ghi = fmax(ghi, redd[kNW + w]); }
     __syncthreads();
     const double tnorm = fmax(fabs(glo), fabs(ghi)) + 1e-300;
     double *Zm = a.Z + (long)mat * d * n;
-    for (int t = r + warp * kR; t < d; t += kNW * kR) {
-        const int target = n - 1 - t;  // ascending index of the (t+1)-th largest eigenvalue
+    for (int t = r + warp * R; t < d; t += kNW * R) {
+        const int target = n - 1 - t;
         const float span = (float)(ghi - glo);
         float lo = (float)glo - 1e-3f * span - 1e-30f, hi = (float)ghi + 1e-3f * span + 1e-30f;
         for (int round = 0; round < 12; round++) {
@@ -269,7 +378,7 @@ __global__ void __cluster_dims__(kR, 1, 1) __launch_bounds__(kT, 1) k_eig_cluste
             a.sig[(long)mat * d + t] = (float)sigma;
             double *lu = a.lu + ((long)mat * d + t) * 5 * n;
             uint8_t *pv = a.piv + ((long)mat * d + t) * n;
-            tri_factor(dg, ed, n, sigma, 2.2e-16 * tnorm, lu, lu + n, lu + 2 * n, lu + 3 * n, pv);
+            tri_factor(dgs, eds, n, sigma, 2.2e-16 * tnorm, lu, lu + n, lu + 2 * n, lu + 3 * n, pv);
             double *z = Zm + (long)t * n;
             for (int i = 0; i < n; i++) z[i] = 1.0 + 0.5 * sin(0.7 * (double)(i + 1) + 1.3 * (double)(t + 1));
             for (int it = 0; it < 3; it++) {
@@ -282,7 +391,6 @@ __global__ void __cluster_dims__(kR, 1, 1) __launch_bounds__(kT, 1) k_eig_cluste
         }
     }
     cl.sync();
-    // selective re-orthogonalisation, Rayleigh quotients and ordering (rank 0)
     if (r == 0) {
         const float *sg = a.sig + (long)mat * d;
         for (int t = 1; t < d; t++) {
@@ -291,17 +399,17 @@ __global__ void __cluster_dims__(kR, 1, 1) __launch_bounds__(kT, 1) k_eig_cluste
             for (int s = 0; s < t; s++) {
                 if (fabs((double)sg[s] - (double)sg[t]) >= 1e-3 * tnorm) continue;
                 const double *zs = Zm + (long)s * n;
-                double part2 = 0.0;
-                for (int i = tid; i < n; i += kT) part2 += zs[i] * zt[i];
-                const double c = block_sum(part2, red);
+                double part = 0.0;
+                for (int i = tid; i < n; i += kT) part += zs[i] * zt[i];
+                const double c = block_sum_d(part, redd);
                 for (int i = tid; i < n; i += kT) zt[i] -= c * zs[i];
                 __syncthreads();
                 any = true;
             }
             if (any) {
-                double part2 = 0.0;
-                for (int i = tid; i < n; i += kT) part2 += zt[i] * zt[i];
-                const double inv = 1.0 / sqrt(block_sum(part2, red));
+                double part = 0.0;
+                for (int i = tid; i < n; i += kT) part += zt[i] * zt[i];
+                const double inv = 1.0 / sqrt(block_sum_d(part, redd));
                 for (int i = tid; i < n; i += kT) zt[i] *= inv;
                 __syncthreads();
             }
@@ -312,9 +420,9 @@ __global__ void __cluster_dims__(kR, 1, 1) __launch_bounds__(kT, 1) k_eig_cluste
             const double *z = Zm + (long)tid * n;
             double acc = 0.0;
             for (int i = 0; i < n; i++) {
-                double tz = dg[i] * z[i];
-                if (i > 0) tz += ed[i - 1] * z[i - 1];
-                if (i < n - 1) tz += ed[i] * z[i + 1];
+                double tz = dgs[i] * z[i];
+                if (i > 0) tz += eds[i - 1] * z[i - 1];
+                if (i < n - 1) tz += eds[i] * z[i + 1];
                 acc = fma(z[i], tz, acc);
             }
             lam[tid] = acc;
@@ -333,83 +441,105 @@ __global__ void __cluster_dims__(kR, 1, 1) __launch_bounds__(kT, 1) k_eig_cluste
     }
     cl.sync();
 
-    // ---------------------------------------------------------------- 3. back-transformation of own columns
+    // ---------------------------------------------------------------- 3. back-transformation (ff)
+    const int ncol = d > r ? (d - r + R - 1) / R : 0;
     const int *order = a.order + (long)mat * d;
+    ff *Wo = rows;  // [n][ncol], region 0 reused
+    ff *vk = qbuf;  // [n]
+    ff *coef = pbuf;
     for (int e = tid; e < n * ncol; e += kT) {
         const int i = e / ncol, c = e % ncol;
-        Wo[e] = Zm[(long)order[r + c * kR] * n + i];
+        Wo[e] = ffa::from_double(Zm[(long)order[r + c * R] * n + i]);
     }
     __syncthreads();
     for (int k = n - 3; k >= 0; k--) {
-        const double tau = tau_g[k];
-        if (tau == 0.0) continue;
+        const double td = tau_g[k];
+        if (td == 0.0) continue;
         const int m = n - k - 1;
-        const double *rk = row_of(k % kR, k / kR);
-        for (int i = tid; i < m; i += kT) vsh[i] = (i == 0) ? v0_g[k] : rk[k + 1 + i];
+        if (tid == 0) fsc[3] = ffa::from_double(td);
+        for (int i = tid; i < m; i += kT) vk[i] = Vh[(long)k * n + i];
         __syncthreads();
+        const ff tk = fsc[3];
         for (int c = warp; c < ncol; c += kNW) {
-            double acc = 0.0;
-            for (int i = lane; i < m; i += 32) acc = fma(vsh[i], Wo[(size_t)(k + 1 + i) * ncol + c], acc);
-            acc = warp_sum(acc);
-            if (lane == 0) coef[c] = tau * acc;
+            ffa::acc Q = ffa::acc_zero();
+            for (int i = lane; i < m; i += 32) ffa::acc_fma(Q, vk[i], Wo[(size_t)(k + 1 + i) * ncol + c]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc_down(Q, o);
+            if (lane == 0) coef[c] = ffa::mul(tk, ffa::acc_value(Q));
         }
         __syncthreads();
         for (int e = tid; e < m * ncol; e += kT) {
             const int i = e / ncol, c = e % ncol;
-            Wo[(size_t)(k + 1 + i) * ncol + c] -= coef[c] * vsh[i];
+            ff &w = Wo[(size_t)(k + 1 + i) * ncol + c];
+            w = ffa::sub(w, ffa::mul(coef[c], vk[i]));
         }
         __syncthreads();
     }
     // sign: largest-magnitude entry positive (first on ties)
+    double *sgn = reinterpret_cast<double *>(wbuf);
     for (int c = warp; c < ncol; c += kNW) {
-        double best = -1.0;
+        float best = -1.0f;
         int bi = 0x7fffffff;
         for (int i = lane; i < n; i += 32) {
-            const double v = fabs(Wo[(size_t)i * ncol + c]);
+            const float v = fabsf(Wo[(size_t)i * ncol + c].hi);
             if (v > best) { best = v; bi = i; }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        if (lane == 0) coef[c] = Wo[(size_t)bi * ncol + c] < 0.0 ? -1.0 : 1.0;
+        if (lane == 0) sgn[c] = Wo[(size_t)bi * ncol + c].hi < 0.0f ? -1.0 : 1.0;
     }
     __syncthreads();
     double *V = a.V + (long)mat * n * d;
     for (int e = tid; e < n * ncol; e += kT) {
         const int i = e / ncol, c = e % ncol;
-        V[(long)i * d + (r + c * kR)] = coef[c] * Wo[e];
+        V[(long)i * d + (r + c * R)] = sgn[c] * ffa::to_double(Wo[e]);
     }
-    cl.sync();  // no CTA leaves while others may still read its shared memory
+    cl.sync();  // no CTA leaves while others may still write into its shared memory
+}
+
+// Shared-memory plan of one CTA for cluster size R.
+size_t smem_plan(int n, int d, int R, long *region0) {
+    long reg = rows_elems(n, R);
+    const int ncol = (d + R - 1) / R;
+    const long p2 = (long)((2 * sizeof(double) * n + 2 * sizeof(double) * kNW + 2 * sizeof(float) * n + 7) / sizeof(ff));
+    const long p3 = (long)n * ncol;
+    if (p2 > reg) reg = p2;
+    if (p3 > reg) reg = p3;
+    *region0 = reg;
+    return sizeof(ff) * ((size_t)reg + (size_t)R * n + 4 * (size_t)n) + sizeof(ffa::acc) * kNW + sizeof(ff) * 4 +
+           sizeof(double) * 4;
+}
+
+int pick_R(int n, int d) {
+    for (int R = 2; R <= 8; R *= 2) {
+        long reg;
+        if (smem_plan(n, d, R, &reg) <= kSmemMax) return R;
+    }
+    return 0;
 }
 
 }  // namespace
 
 struct EigPlan {
-    size_t rows_g, dg, ed, tau, v0, Z, lu, piv, sig, lam, order, total;
-    int rows_in_smem;
-    size_t smem;
+    size_t dg, ed, tau, v0, Vh, Z, lu, piv, sig, lam, order, total;
 };
 
 static EigPlan eig_plan(int n, int d, int mats) {
     EigPlan p{};
-    const int rows_per = (n + kR - 1) / kR;
-    const size_t rows_bytes = sizeof(double) * (size_t)rows_per * n;
-    p.rows_in_smem = rows_bytes <= kRowsSmemMax;
-    const int ncol_max = (d + kR - 1) / kR;
-    p.smem = (p.rows_in_smem ? rows_bytes : 0) + sizeof(double) * (3 * (size_t)n + 32 + 64 + (size_t)n * ncol_max);
     size_t o = 0;
     auto take = [&](size_t bytes) {
         const size_t at = o;
         o = align_up(o + bytes, 256);
         return at;
     };
-    p.rows_g = take(p.rows_in_smem ? 0 : sizeof(double) * (size_t)mats * kR * rows_per * n);
     p.dg = take(sizeof(double) * (size_t)mats * n);
     p.ed = take(sizeof(double) * (size_t)mats * n);
     p.tau = take(sizeof(double) * (size_t)mats * n);
     p.v0 = take(sizeof(double) * (size_t)mats * n);
+    p.Vh = take(sizeof(ff) * (size_t)mats * n * n);
     p.Z = take(sizeof(double) * (size_t)mats * d * n);
     p.lu = take(sizeof(double) * (size_t)mats * d * 5 * n);
     p.piv = take((size_t)mats * d * n);
@@ -422,29 +552,34 @@ static EigPlan eig_plan(int n, int d, int mats) {
 
 size_t eig_workspace_bytes(int n, int d, int mats) { return eig_plan(n, d, mats).total; }
 
-cudaError_t launch_eig(const double *cov, int n, int d, int mats, double *V, double *eigvals, void *ws,
+// cov_ff: [mats][n][n] float-float pairs (hi, lo) of the covariance.
+cudaError_t launch_eig(const void *cov_ff, int n, int d, int mats, double *V, double *eigvals, void *ws,
                        cudaStream_t st) {
-    const EigPlan p = eig_plan(n, d, mats);
-    if (p.smem > 227 * 1024) return cudaErrorNotSupported;
+    const int R = pick_R(n, d);
+    if (R == 0) return cudaErrorNotSupported;
+    long region0 = 0;
+    const size_t smem = smem_plan(n, d, R, &region0);
     static int attr_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_eig_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(k_eig_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
+    const EigPlan p = eig_plan(n, d, mats);
     char *b = (char *)ws;
     EigArgs a;
-    a.cov = cov;
+    a.cov = (const ff *)cov_ff;
     a.n = n;
     a.d = d;
-    a.rows_in_smem = p.rows_in_smem;
-    a.rows_g = (double *)(b + p.rows_g);
+    a.R = R;
+    a.region0 = region0;
     a.dg = (double *)(b + p.dg);
     a.ed = (double *)(b + p.ed);
     a.tau = (double *)(b + p.tau);
     a.v0 = (double *)(b + p.v0);
+    a.Vh = (ff *)(b + p.Vh);
     a.Z = (double *)(b + p.Z);
     a.lu = (double *)(b + p.lu);
     a.piv = (uint8_t *)(b + p.piv);
@@ -453,7 +588,21 @@ cudaError_t launch_eig(const double *cov, int n, int d, int mats, double *V, dou
     a.order = (int *)(b + p.order);
     a.V = V;
     a.eig = eigvals;
-    QFCA_LAUNCH("k_eig_cluster", st, k_eig_cluster<<<kR * mats, kT, p.smem, st>>>(a));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(R * mats);
+    cfg.blockDim = dim3(kT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = R;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaSuccess;
+    QFCA_LAUNCH("k_eig_ff", st, e = cudaLaunchKernelEx(&cfg, k_eig_ff, a));
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

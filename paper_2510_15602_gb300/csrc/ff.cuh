@@ -1,0 +1,100 @@
+// ff.cuh -- float-float ("double-single") arithmetic on the FP32 pipe.
+//
+// A value is hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits.  The
+// building blocks are the error-free transformations TwoSum (Knuth),
+// FastTwoSum (Dekker) and TwoProd via FMA; every operation uses explicitly
+// rounded intrinsics so the compiler cannot re-associate or contract them.
+// Used where GB300's FP64 pipe (a few DFMA per clock per SM) would be the
+// bottleneck and FP32 (128 lanes per clock per SM) is not accurate enough.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace qfca {
+namespace ffa {
+
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff make(float hi, float lo) { return ff{hi, lo}; }
+__device__ __forceinline__ ff zero() { return ff{0.0f, 0.0f}; }
+
+// s + e == a + b exactly
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return ff{s, e};
+}
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float e = __fsub_rn(b, __fsub_rn(s, a));
+    return ff{s, e};
+}
+
+__device__ __forceinline__ ff add(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    const float t = __fadd_rn(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t);
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff neg(ff a) { return ff{-a.hi, -a.lo}; }
+__device__ __forceinline__ ff sub(ff a, ff b) { return add(a, neg(b)); }
+
+__device__ __forceinline__ ff mul(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+
+// Compensated dot-product accumulator: s carries the running sum of the
+// leading products, c the (small) compensation.
+struct acc {
+    float s, c;
+};
+__device__ __forceinline__ acc acc_zero() { return acc{0.0f, 0.0f}; }
+__device__ __forceinline__ void acc_fma(acc &A, ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const ff t = two_sum(A.s, p);
+    A.s = t.hi;
+    A.c = __fadd_rn(A.c, __fadd_rn(t.lo, e));
+}
+__device__ __forceinline__ void acc_add(acc &A, ff a) {
+    const ff t = two_sum(A.s, a.hi);
+    A.s = t.hi;
+    A.c = __fadd_rn(A.c, __fadd_rn(t.lo, a.lo));
+}
+__device__ __forceinline__ void acc_merge(acc &A, acc B) {
+    const ff t = two_sum(A.s, B.s);
+    A.s = t.hi;
+    A.c = __fadd_rn(A.c, __fadd_rn(t.lo, B.c));
+}
+__device__ __forceinline__ ff acc_value(acc A) { return two_sum(A.s, A.c); }
+
+__device__ __forceinline__ acc warp_sum(acc A) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc B;
+        B.s = __shfl_xor_sync(0xffffffffu, A.s, o);
+        B.c = __shfl_xor_sync(0xffffffffu, A.c, o);
+        acc_merge(A, B);
+    }
+    return A;
+}
+
+// conversions (FP64 only at the edges)
+__device__ __forceinline__ ff from_double(double x) {
+    const float h = (float)x;
+    return ff{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+}  // namespace ffa
+}  // namespace qfca

@@ -1,8 +1,8 @@
 // fit.cu -- single-image PCA fit (arXiv 2510.15602, Sec. 3.3) on the GPU:
 // the mean and covariance of the C channels over the H*W pixels (exact
 // integer-sliced Gram on the tensor cores, gram.cu) followed by the top-d
-// eigenpairs of the covariance in FP64 (eig.cu, one thread-block cluster per
-// matrix).
+// eigenpairs of the covariance (eig.cu: float-float Householder reduction on a
+// thread-block cluster, FP64 tridiagonal eigenvectors).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -13,7 +13,7 @@ namespace qfca {
 namespace {
 
 struct FitLayout {
-    size_t off_gram, off_cov, off_eig, total;
+    size_t off_gram, off_cov, off_covff, off_eig, total;
 };
 
 FitLayout fit_layout(int C, long N, int d) {
@@ -23,6 +23,8 @@ FitLayout fit_layout(int C, long N, int d) {
     o = align_up(o + gram_workspace_bytes(C, N), 256);
     L.off_cov = o;
     o = align_up(o + sizeof(double) * (size_t)C * C, 256);
+    L.off_covff = o;
+    o = align_up(o + 2 * sizeof(float) * (size_t)C * C, 256);
     L.off_eig = o;
     o = align_up(o + eig_workspace_bytes(C, d, 1), 256);
     L.total = o;
@@ -39,9 +41,10 @@ cudaError_t launch_fit(const float *X, int layout, int H, int W, int C, int d, d
     const FitLayout L = fit_layout(C, N, d);
     char *base = (char *)ws;
     double *cov = (double *)(base + L.off_cov);
-    cudaError_t e = launch_gram_cov(X, layout, C, N, mean, cov, base + L.off_gram, status, st);
+    void *cov_ff = base + L.off_covff;
+    cudaError_t e = launch_gram_cov(X, layout, C, N, mean, cov, cov_ff, base + L.off_gram, status, st);
     if (e != cudaSuccess) return e;
-    return launch_eig(cov, C, d, 1, V, eigvals, base + L.off_eig, st);
+    return launch_eig(cov_ff, C, d, 1, V, eigvals, base + L.off_eig, st);
 }
 
 }  // namespace qfca

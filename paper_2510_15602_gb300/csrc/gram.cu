@@ -296,7 +296,7 @@ __global__ void k_chan_scale(const unsigned *__restrict__ amax, int C, float *__
 // S_c = sum_i D_i,c 2^(-6-7i).  Writes mean[C] and the full symmetric cov[C][C].
 __global__ void k_cov_finalize(const unsigned long long *__restrict__ Gint, const unsigned long long *__restrict__ Dsum,
                                const int *__restrict__ ex, int C, long N, double *__restrict__ mean,
-                               double *__restrict__ cov) {
+                               double *__restrict__ cov, float2 *__restrict__ cov_ff) {
     const double invN = 1.0 / (double)N;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)C * C; e += (long)gridDim.x * blockDim.x) {
         const int i = (int)(e / C), j = (int)(e % C);
@@ -308,7 +308,12 @@ __global__ void k_cov_finalize(const unsigned long long *__restrict__ Gint, cons
         };
         const double mi = mu(a), mj = mu(b);
         const double g = ldexp((double)(long long)Gint[(long)a * C + b], ex[a] + ex[b] - 40) * invN;
-        cov[e] = g - mi * mj;
+        const double v = g - mi * mj;
+        cov[e] = v;
+        if (cov_ff) {
+            const float h = (float)v;
+            cov_ff[e] = make_float2(h, (float)(v - (double)h));
+        }
         if (i == j) mean[i] = mi;
     }
 }
@@ -347,8 +352,8 @@ static GramPlan gram_plan(int C, long N) {
 size_t gram_workspace_bytes(int C, long N) { return gram_plan(C, N).total; }
 
 // mean[C] and cov[C][C] (FP64) of the feature map; ws: gram_workspace_bytes.
-cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, double *mean, double *cov, void *ws, int *status,
-                            cudaStream_t st) {
+cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, double *mean, double *cov, void *cov_ff, void *ws,
+                            int *status, cudaStream_t st) {
     const GramPlan g = gram_plan(C, N);
     char *b = (char *)ws;
     unsigned *amax = (unsigned *)(b + g.off_amax);
@@ -378,7 +383,8 @@ cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, double *m
                                                                        g.chunk, G, D, status));
     const long cc = (long)C * C;
     QFCA_LAUNCH("k_cov_finalize", st,
-                k_cov_finalize<<<(unsigned)((cc + 255) / 256), 256, 0, st>>>(G, D, ex, C, N, mean, cov));
+                k_cov_finalize<<<(unsigned)((cc + 255) / 256), 256, 0, st>>>(G, D, ex, C, N, mean, cov,
+                                                                             (float2 *)cov_ff));
     return cudaGetLastError();
 }
 

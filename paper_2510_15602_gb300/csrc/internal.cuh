@@ -27,12 +27,14 @@ cudaError_t launch_fit(const float *X, int layout, int H, int W, int C, int d, d
 
 // Mean and covariance of one feature map (gram.cu).
 size_t gram_workspace_bytes(int C, long N);
-cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, double *mean, double *cov, void *ws,
-                            int *status, cudaStream_t st);
+// cov_ff (may be NULL): the covariance also as float-float pairs (float2 [C][C]).
+cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, double *mean, double *cov, void *cov_ff,
+                            void *ws, int *status, cudaStream_t st);
 
-// Top-d eigenpairs of `mats` symmetric n x n matrices (eig.cu).
+// Top-d eigenpairs of `mats` symmetric n x n matrices given as float-float
+// pairs (float2 [mats][n][n]) (eig.cu).
 size_t eig_workspace_bytes(int n, int d, int mats);
-cudaError_t launch_eig(const double *cov, int n, int d, int mats, double *V, double *eigvals, void *ws,
+cudaError_t launch_eig(const void *cov_ff, int n, int d, int mats, double *V, double *eigvals, void *ws,
                        cudaStream_t st);
 
 // ------------------------------------------------------------------ projection (project.cu)

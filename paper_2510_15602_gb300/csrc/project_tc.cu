@@ -219,6 +219,9 @@ cudaError_t launch_dt(const float *X, int layout, int C, const TcShape &sh, long
     if (attr_dev != dev) {
         cudaError_t e = cudaFuncSetAttribute(k_project_bf16<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_project_bf16<DT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
