@@ -9,17 +9,19 @@
 // the lower triangle packed in shared memory, rows distributed cyclically:
 //   1. Householder tridiagonalisation A = Q T Q^T.  Step k: every CTA holds
 //      x = A[k+1.., k] (gathered through distributed shared memory at the end
-//      of step k-1) and forms (v, tau) (scalars in FP64 by one thread); each
+//      of step k-1) and forms (v, tau) (float-float scalars, one thread); each
 //      CTA computes its partial q of A v from the elements it stores (row part
 //      and column part of the symmetric product) and pushes it into every
 //      CTA; cluster barrier; p = tau sum_r q_r (fixed order),
 //      w = p - (tau/2)(p.v) v; each CTA applies A -= v w^T + w v^T to its
 //      lower-triangle rows and pushes the new column k+1 into every CTA;
 //      cluster barrier.
-//   2. Shifts by warp multisection on the FP32 Sturm count; FP64 inverse
-//      iteration on T (LU with partial pivoting, three solves); selective
-//      Gram-Schmidt for shifts within 1e-3 ||T||; FP64 Rayleigh quotients;
-//      stable descending order.
+//   2. Shifts by warp multisection on the FP32 Sturm count; float-float
+//      inverse iteration on T (LU with partial pivoting, three solves, scratch
+//      per warp in shared memory); selective Gram-Schmidt for shifts within
+//      1e-3 ||T||; float-float Rayleigh quotients; stable descending order.
+//      (Single-lane FP64 code would issue warp-wide FP64 instructions at the
+//      FP64 pipe's rate: it cost milliseconds here.)
 //   3. Back-transformation V = H_0 ... H_{n-3} Z in float-float, columns
 //      distributed over the cluster; sign normalisation (largest-magnitude
 //      entry positive); FP64 output.
@@ -46,16 +48,15 @@ struct EigArgs {
     const ff *cov;  // [mats][n][n] float-float covariance
     int n, d, R;
     long region0;   // ff elements of the first shared region (packed rows; reused by phases 2/3)
-    double *dg, *ed, *tau, *v0;  // [mats][n]
-    ff *Vh;                      // [mats][n][n]  Householder vectors (row k: v_k, length n-k-1)
-    double *Z;                   // [mats][d][n]
-    double *lu;                  // [mats][d][5][n]
-    uint8_t *piv;                // [mats][d][n]
-    float *sig;                  // [mats][d]
-    double *lam;                 // [mats][d]
-    int *order;                  // [mats][d]
-    double *V;                   // [mats][n][d]
-    double *eig;                 // [mats][d]
+    int nslots;     // warps that can hold an inverse-iteration scratch slot at once
+    ff *dg, *ed, *tau, *v0;  // [mats][n]  tridiagonal T and the reflectors' scalars
+    ff *Vh;                  // [mats][n][n]  Householder vectors (row k: v_k, length n-k-1)
+    ff *Z;                   // [mats][d][n]  eigenvectors of T
+    float *sig;              // [mats][d]
+    ff *lam;                 // [mats][d]
+    int *order;              // [mats][d]
+    double *V;               // [mats][n][d]
+    double *eig;             // [mats][d]
 };
 
 __host__ __device__ inline long row_off(int l, int r, int R) {
@@ -93,19 +94,6 @@ __device__ ff block_acc(ffa::acc A, ffa::acc *red) {
     return ffa::acc_value(T);
 }
 
-__device__ double block_sum_d(double v, double *redd) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if (lane == 0) redd[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < kNW; w++) t += redd[w];
-    __syncthreads();
-    return t;
-}
-
 __device__ int sturm_count(const float *dg, const float *e2, int n, float x) {
     int cnt = 0;
     float q = dg[0] - x;
@@ -119,40 +107,44 @@ __device__ int sturm_count(const float *dg, const float *e2, int n, float x) {
     return cnt;
 }
 
-// LU with partial pivoting of the tridiagonal T - sigma I (FP64); u0i: reciprocal pivots.
-__device__ void tri_factor(const double *dg, const double *ed, int n, double sigma, double tiny, double *u0i,
-                           double *u1, double *u2, double *lm, uint8_t *piv) {
-    double r0 = dg[0] - sigma, r1 = n > 1 ? ed[0] : 0.0;
+// LU with partial pivoting of the tridiagonal T - sigma I, in float-float.
+// u0i: reciprocal pivots, u1/u2: first/second super-diagonals of U, lm: multipliers.
+__device__ void tri_factor(const ff *dg, const ff *ed, int n, ff sigma, ff tiny, ff *u0i, ff *u1, ff *u2, ff *lm,
+                           uint8_t *piv) {
+    using namespace ffa;
+    const ff one = make(1.0f, 0.0f);
+    ff r0 = sub(dg[0], sigma), r1 = n > 1 ? ed[0] : zero();
     for (int i = 0; i < n - 1; i++) {
-        const double s0 = ed[i], s1 = dg[i + 1] - sigma, s2 = (i + 1 < n - 1) ? ed[i + 1] : 0.0;
-        if (fabs(r0) >= fabs(s0)) {
-            if (r0 == 0.0) r0 = tiny;
-            const double inv = 1.0 / r0;
-            const double l = s0 * inv;
-            u0i[i] = inv; u1[i] = r1; u2[i] = 0.0; lm[i] = l; piv[i] = 0;
-            r0 = s1 - l * r1;
+        const ff s0 = ed[i], s1 = sub(dg[i + 1], sigma), s2 = (i + 1 < n - 1) ? ed[i + 1] : zero();
+        if (!less(fabs_ff(r0), fabs_ff(s0))) {
+            if (r0.hi == 0.0f) r0 = tiny;
+            const ff inv = div(one, r0);
+            const ff l = mul(s0, inv);
+            u0i[i] = inv; u1[i] = r1; u2[i] = zero(); lm[i] = l; piv[i] = 0;
+            r0 = sub(s1, mul(l, r1));
             r1 = s2;
         } else {
-            const double inv = 1.0 / s0;
-            const double l = r0 * inv;
+            const ff inv = div(one, s0);
+            const ff l = mul(r0, inv);
             u0i[i] = inv; u1[i] = s1; u2[i] = s2; lm[i] = l; piv[i] = 1;
-            const double n0 = r1 - l * s1, n1 = -l * s2;
+            const ff n0 = sub(r1, mul(l, s1)), n1 = neg(mul(l, s2));
             r0 = n0; r1 = n1;
         }
     }
-    if (r0 == 0.0) r0 = tiny;
-    u0i[n - 1] = 1.0 / r0; u1[n - 1] = 0.0; u2[n - 1] = 0.0;
+    if (r0.hi == 0.0f) r0 = tiny;
+    u0i[n - 1] = div(one, r0); u1[n - 1] = zero(); u2[n - 1] = zero();
 }
 
-__device__ void tri_solve(int n, const double *u0i, const double *u1, const double *u2, const double *lm,
-                          const uint8_t *piv, double *x) {
+__device__ void tri_solve(int n, const ff *u0i, const ff *u1, const ff *u2, const ff *lm, const uint8_t *piv, ff *x) {
+    using namespace ffa;
     for (int i = 0; i < n - 1; i++) {
-        if (piv[i]) { const double t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
-        x[i + 1] -= lm[i] * x[i];
+        if (piv[i]) { const ff t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
+        x[i + 1] = sub(x[i + 1], mul(lm[i], x[i]));
     }
-    x[n - 1] *= u0i[n - 1];
-    if (n >= 2) x[n - 2] = (x[n - 2] - u1[n - 2] * x[n - 1]) * u0i[n - 2];
-    for (int i = n - 3; i >= 0; i--) x[i] = (x[i] - u1[i] * x[i + 1] - u2[i] * x[i + 2]) * u0i[i];
+    x[n - 1] = mul(x[n - 1], u0i[n - 1]);
+    if (n >= 2) x[n - 2] = mul(sub(x[n - 2], mul(u1[n - 2], x[n - 1])), u0i[n - 2]);
+    for (int i = n - 3; i >= 0; i--)
+        x[i] = mul(sub(sub(x[i], mul(u1[i], x[i + 1])), mul(u2[i], x[i + 2])), u0i[i]);
 }
 
 __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
@@ -172,12 +164,11 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
     ff *pbuf = xb + n;                               // [n]
     ff *wbuf = pbuf + n;                             // [n]
     ffa::acc *red = reinterpret_cast<ffa::acc *>(wbuf + n);  // [kNW]
-    ff *fsc = reinterpret_cast<ff *>(red + kNW);             // [4] step scalars in ff
-    double *scal = reinterpret_cast<double *>(fsc + 4);      // [4]
+    ff *fsc = reinterpret_cast<ff *>(red + kNW);             // [4] step scalars
 
     const ff *S = a.cov + (long)mat * n * n;
-    double *dg = a.dg + (long)mat * n, *ed = a.ed + (long)mat * n;
-    double *tau_g = a.tau + (long)mat * n, *v0_g = a.v0 + (long)mat * n;
+    ff *dg = a.dg + (long)mat * n, *ed = a.ed + (long)mat * n;
+    ff *tau_g = a.tau + (long)mat * n, *v0_g = a.v0 + (long)mat * n;
     ff *Vh = a.Vh + (long)mat * n * n;
 
     // ---- own lower-triangle rows; column 0 below the diagonal into every CTA
@@ -193,7 +184,7 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
             const ff x = rows[row_off(l, r, R)];  // A[i][0]
             for (int dst = 0; dst < R; dst++) cl.map_shared_rank(xa, dst)[i - 1] = x;
         } else {
-            dg[0] = ffa::to_double(rows[0]);
+            dg[0] = rows[0];
         }
     }
     cl.sync();
@@ -206,29 +197,27 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
         for (int j = 1 + tid; j < m; j += kT) ffa::acc_fma(A, xcur[j], xcur[j]);
         const ff sig = block_acc(A, red);  // identical in every CTA of the cluster
         if (tid == 0) {
-            const double alpha = ffa::to_double(xcur[0]);
-            const double sigma = ffa::to_double(sig);
-            double tau = 0.0, ek = alpha, v0 = alpha;
-            if (sigma > 0.0) {
-                const double mu = sqrt(alpha * alpha + sigma);
-                v0 = alpha >= 0.0 ? alpha + mu : alpha - mu;
-                ek = alpha >= 0.0 ? -mu : mu;
-                tau = 2.0 / (v0 * v0 + sigma);
+            const ff alpha = xcur[0];
+            ff tau = ffa::zero(), ek = alpha, v0 = alpha;
+            if (sig.hi > 0.0f) {
+                const ff mu = ffa::sqrt(ffa::add(ffa::mul(alpha, alpha), sig));
+                if (alpha.hi >= 0.0f) { v0 = ffa::add(alpha, mu); ek = ffa::neg(mu); }
+                else { v0 = ffa::sub(alpha, mu); ek = mu; }
+                tau = ffa::div(ffa::make(2.0f, 0.0f), ffa::add(ffa::mul(v0, v0), sig));
             }
-            scal[0] = tau;
-            fsc[0] = ffa::from_double(tau);
-            fsc[1] = ffa::from_double(v0);
-            fsc[2] = ffa::from_double(0.5 * tau);
+            fsc[0] = tau;
+            fsc[1] = v0;
+            fsc[2] = ffa::scale(tau, 0.5f);
             if (r == 0) { tau_g[k] = tau; v0_g[k] = v0; ed[k] = ek; }
         }
         __syncthreads();
-        const double tau_d = scal[0];
         const ff tau = fsc[0], v0 = fsc[1], htau = fsc[2];
+        const bool reflect = tau.hi != 0.0f;
         if (r == 0)
             for (int j = tid; j < m; j += kT) Vh[(long)k * n + j] = j == 0 ? v0 : xcur[j];
         int l0 = (k + 1 - r + R - 1) / R;  // first own row with i >= k+1
         if (l0 < 0) l0 = 0;
-        if (tau_d != 0.0) {
+        if (reflect) {
             // ---- column part of the own partial product: sum over own rows i > jc of A[i][jc] v_i
             for (int jc = k + 1 + tid; jc < n; jc += kT) {
                 ffa::acc Q = ffa::acc_zero();
@@ -300,7 +289,7 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
             }
         }
         __syncthreads();
-        if (tid == 0 && (k + 1) % R == r) dg[k + 1] = ffa::to_double(rows[row_off((k + 1) / R, r, R) + k + 1]);
+        if (tid == 0 && (k + 1) % R == r) dg[k + 1] = rows[row_off((k + 1) / R, r, R) + k + 1];
         cl.sync();
         ff *t = xcur;
         xcur = xnext;
@@ -308,124 +297,142 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
     }
     if (tid == 0) {
         if (r == 0) {
-            ed[n - 1] = 0.0;
-            tau_g[n - 1] = 0.0;
-            v0_g[n - 1] = 0.0;
-            if (n >= 2) { tau_g[n - 2] = 0.0; v0_g[n - 2] = 0.0; }
+            ed[n - 1] = ffa::zero();
+            tau_g[n - 1] = ffa::zero();
+            v0_g[n - 1] = ffa::zero();
+            if (n >= 2) { tau_g[n - 2] = ffa::zero(); v0_g[n - 2] = ffa::zero(); }
         }
         if (n >= 2 && (n - 1) % R == r) {
             const ff *row = rows + row_off((n - 1) / R, r, R);
-            ed[n - 2] = ffa::to_double(row[n - 2]);
-            dg[n - 1] = ffa::to_double(row[n - 1]);
+            ed[n - 2] = row[n - 2];
+            dg[n - 1] = row[n - 1];
         }
     }
     cl.sync();
 
     // ---------------------------------------------------------------- 2. eigenpairs of T
-    double *dgs = reinterpret_cast<double *>(rows);  // region 0 reused
-    double *eds = dgs + n;
-    double *redd = eds + n;                           // [2 * kNW]
-    float *dg32 = reinterpret_cast<float *>(redd + 2 * kNW);
+    ff *dgs = rows;  // region 0 reused: T (ff), FP32 Sturm data, then per-warp LU slots
+    ff *eds = dgs + n;
+    float *dg32 = reinterpret_cast<float *>(eds + n);
     float *e232 = dg32 + n;
+    float *redf = e232 + n;  // [2 * kNW]
+    ff *slots = reinterpret_cast<ff *>(redf + 2 * kNW + 2);
+    const size_t slot_ff = (size_t)5 * n + (n + 7) / 8;  // u0i, u1, u2, lm, z  + piv bytes
     for (int i = tid; i < n; i += kT) {
         dgs[i] = dg[i];
         eds[i] = ed[i];
-        dg32[i] = (float)dg[i];
-        e232[i] = (float)(ed[i] * ed[i]);
+        dg32[i] = dg[i].hi;
+        e232[i] = __fmul_rn(ed[i].hi, ed[i].hi);
     }
     __syncthreads();
-    double glo = 1e300, ghi = -1e300;
+    float glo = 3e38f, ghi = -3e38f;
     for (int i = tid; i < n; i += kT) {
-        const double rr = (i > 0 ? fabs(eds[i - 1]) : 0.0) + (i < n - 1 ? fabs(eds[i]) : 0.0);
-        glo = fmin(glo, dgs[i] - rr);
-        ghi = fmax(ghi, dgs[i] + rr);
+        const float rr = (i > 0 ? fabsf(eds[i - 1].hi) : 0.0f) + (i < n - 1 ? fabsf(eds[i].hi) : 0.0f);
+        glo = fminf(glo, dgs[i].hi - rr);
+        ghi = fmaxf(ghi, dgs[i].hi + rr);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, o));
-        ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
+        glo = fminf(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+        ghi = fmaxf(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
     }
-    if (lane == 0) { redd[warp] = glo; redd[kNW + warp] = ghi; }
+    if (lane == 0) { redf[warp] = glo; redf[kNW + warp] = ghi; }
     __syncthreads();
-    glo = redd[0];
-    ghi = redd[kNW];
-    for (int w = 1; w < kNW; w++) { glo = fmin(glo, redd[w]); ghi = fmax(ghi, redd[kNW + w]); }
-    __syncthreads();
-    const double tnorm = fmax(fabs(glo), fabs(ghi)) + 1e-300;
-    double *Zm = a.Z + (long)mat * d * n;
-    for (int t = r + warp * R; t < d; t += kNW * R) {
-        const int target = n - 1 - t;
-        const float span = (float)(ghi - glo);
-        float lo = (float)glo - 1e-3f * span - 1e-30f, hi = (float)ghi + 1e-3f * span + 1e-30f;
-        for (int round = 0; round < 12; round++) {
-            const float x = lo + (hi - lo) * (float)(lane + 1) / 33.0f;
-            const int c = sturm_count(dg32, e232, n, x);
-            const unsigned mask = __ballot_sync(0xffffffffu, c > target);
-            const float x31 = __shfl_sync(0xffffffffu, x, 31);
-            if (mask == 0u) {
-                lo = x31;
-            } else {
-                const int f = __ffs(mask) - 1;
-                const float xf = __shfl_sync(0xffffffffu, x, f);
-                const float xp = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
-                hi = xf;
-                if (f > 0) lo = xp;
+    glo = redf[0];
+    ghi = redf[kNW];
+    for (int w = 1; w < kNW; w++) { glo = fminf(glo, redf[w]); ghi = fmaxf(ghi, redf[kNW + w]); }
+    const float tnorm = fmaxf(fabsf(glo), fabsf(ghi)) + 1e-30f;
+    ff *Zm = a.Z + (long)mat * d * n;
+    // my eigenvalue indices: t = r + (warp + kNW * round) * R, one per warp per round
+    const int per_cta = d > r ? (d - r + R - 1) / R : 0;
+    for (int base = 0; base < per_cta; base += a.nslots) {
+        const int j = base + warp;
+        if (warp < a.nslots && j < per_cta) {
+            const int t = r + j * R;
+            const int target = n - 1 - t;
+            const float span = ghi - glo;
+            float lo = glo - 1e-3f * span - 1e-30f, hi = ghi + 1e-3f * span + 1e-30f;
+            for (int round = 0; round < 12; round++) {
+                const float x = lo + (hi - lo) * (float)(lane + 1) / 33.0f;
+                const int c = sturm_count(dg32, e232, n, x);
+                const unsigned mask = __ballot_sync(0xffffffffu, c > target);
+                const float x31 = __shfl_sync(0xffffffffu, x, 31);
+                if (mask == 0u) {
+                    lo = x31;
+                } else {
+                    const int f = __ffs(mask) - 1;
+                    const float xf = __shfl_sync(0xffffffffu, x, f);
+                    const float xp = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
+                    hi = xf;
+                    if (f > 0) lo = xp;
+                }
+                if (hi - lo <= 4.0f * 1.2e-7f * fmaxf(fabsf(lo), fabsf(hi)) + 1e-30f) break;
             }
-            if (hi - lo <= 4.0f * 1.2e-7f * fmaxf(fabsf(lo), fabsf(hi)) + 1e-30f) break;
-        }
-        if (lane == 0) {
-            const double sigma = 0.5 * ((double)lo + (double)hi);
-            a.sig[(long)mat * d + t] = (float)sigma;
-            double *lu = a.lu + ((long)mat * d + t) * 5 * n;
-            uint8_t *pv = a.piv + ((long)mat * d + t) * n;
-            tri_factor(dgs, eds, n, sigma, 2.2e-16 * tnorm, lu, lu + n, lu + 2 * n, lu + 3 * n, pv);
-            double *z = Zm + (long)t * n;
-            for (int i = 0; i < n; i++) z[i] = 1.0 + 0.5 * sin(0.7 * (double)(i + 1) + 1.3 * (double)(t + 1));
-            for (int it = 0; it < 3; it++) {
-                tri_solve(n, lu, lu + n, lu + 2 * n, lu + 3 * n, pv, z);
-                double nrm = 0.0;
-                for (int i = 0; i < n; i++) nrm = fma(z[i], z[i], nrm);
-                nrm = 1.0 / sqrt(nrm);
-                for (int i = 0; i < n; i++) z[i] *= nrm;
+            if (lane == 0) {
+                const ff sigma = ffa::two_sum(0.5f * lo, 0.5f * hi);
+                a.sig[(long)mat * d + t] = sigma.hi;
+                ff *sl = slots + (size_t)warp * slot_ff;
+                ff *u0i = sl, *u1 = sl + n, *u2 = sl + 2 * n, *lm = sl + 3 * n, *z = sl + 4 * n;
+                uint8_t *pv = reinterpret_cast<uint8_t *>(sl + 5 * n);
+                tri_factor(dgs, eds, n, sigma, ffa::make(3.6e-15f * tnorm, 0.0f), u0i, u1, u2, lm, pv);
+                // deterministic start vector from an integer hash
+                for (int i = 0; i < n; i++) {
+                    unsigned h = (unsigned)(i + 1) * 2654435761u ^ (unsigned)(t + 1) * 40503u;
+                    h ^= h >> 15;
+                    h *= 2246822519u;
+                    h ^= h >> 13;
+                    z[i] = ffa::make(1.0f + 0.5f * ((float)(h & 0xffffu) / 65536.0f - 0.5f), 0.0f);
+                }
+                for (int it = 0; it < 3; it++) {
+                    tri_solve(n, u0i, u1, u2, lm, pv, z);
+                    ffa::acc N2 = ffa::acc_zero();
+                    for (int i = 0; i < n; i++) ffa::acc_fma(N2, z[i], z[i]);
+                    const ff inv = ffa::div(ffa::make(1.0f, 0.0f), ffa::sqrt(ffa::acc_value(N2)));
+                    for (int i = 0; i < n; i++) z[i] = ffa::mul(z[i], inv);
+                }
+                ff *zg = Zm + (long)t * n;
+                for (int i = 0; i < n; i++) zg[i] = z[i];
             }
         }
+        __syncthreads();
     }
     cl.sync();
     if (r == 0) {
         const float *sg = a.sig + (long)mat * d;
         for (int t = 1; t < d; t++) {
-            double *zt = Zm + (long)t * n;
+            ff *zt = Zm + (long)t * n;
             bool any = false;
-            for (int s = 0; s < t; s++) {
-                if (fabs((double)sg[s] - (double)sg[t]) >= 1e-3 * tnorm) continue;
-                const double *zs = Zm + (long)s * n;
-                double part = 0.0;
-                for (int i = tid; i < n; i += kT) part += zs[i] * zt[i];
-                const double c = block_sum_d(part, redd);
-                for (int i = tid; i < n; i += kT) zt[i] -= c * zs[i];
+            for (int s2 = 0; s2 < t; s2++) {
+                if (fabsf(sg[s2] - sg[t]) >= 1e-3f * tnorm) continue;
+                const ff *zs = Zm + (long)s2 * n;
+                ffa::acc P = ffa::acc_zero();
+                for (int i = tid; i < n; i += kT) ffa::acc_fma(P, zs[i], zt[i]);
+                const ff c = block_acc(P, red);
+                for (int i = tid; i < n; i += kT) zt[i] = ffa::sub(zt[i], ffa::mul(c, zs[i]));
                 __syncthreads();
                 any = true;
             }
             if (any) {
-                double part = 0.0;
-                for (int i = tid; i < n; i += kT) part += zt[i] * zt[i];
-                const double inv = 1.0 / sqrt(block_sum_d(part, redd));
-                for (int i = tid; i < n; i += kT) zt[i] *= inv;
+                ffa::acc P = ffa::acc_zero();
+                for (int i = tid; i < n; i += kT) ffa::acc_fma(P, zt[i], zt[i]);
+                const ff inv = ffa::div(ffa::make(1.0f, 0.0f), ffa::sqrt(block_acc(P, red)));
+                for (int i = tid; i < n; i += kT) zt[i] = ffa::mul(zt[i], inv);
                 __syncthreads();
             }
         }
-        double *lam = a.lam + (long)mat * d;
+        ff *lam = a.lam + (long)mat * d;
         int *order = a.order + (long)mat * d;
         if (tid < d) {
-            const double *z = Zm + (long)tid * n;
-            double acc = 0.0;
+            const ff *z = Zm + (long)tid * n;
+            ffa::acc Q = ffa::acc_zero();
             for (int i = 0; i < n; i++) {
-                double tz = dgs[i] * z[i];
-                if (i > 0) tz += eds[i - 1] * z[i - 1];
-                if (i < n - 1) tz += eds[i] * z[i + 1];
-                acc = fma(z[i], tz, acc);
+                ffa::acc T = ffa::acc_zero();
+                ffa::acc_fma(T, dgs[i], z[i]);
+                if (i > 0) ffa::acc_fma(T, eds[i - 1], z[i - 1]);
+                if (i < n - 1) ffa::acc_fma(T, eds[i], z[i + 1]);
+                ffa::acc_fma(Q, z[i], ffa::acc_value(T));
             }
-            lam[tid] = acc;
+            lam[tid] = ffa::acc_value(Q);
         }
         __syncthreads();
         if (tid == 0) {
@@ -433,10 +440,10 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
             for (int x = 1; x < d; x++) {
                 const int v = order[x];
                 int y = x - 1;
-                while (y >= 0 && lam[order[y]] < lam[v]) { order[y + 1] = order[y]; y--; }
+                while (y >= 0 && ffa::less(lam[order[y]], lam[v])) { order[y + 1] = order[y]; y--; }
                 order[y + 1] = v;
             }
-            for (int t = 0; t < d; t++) a.eig[(long)mat * d + t] = lam[order[t]];
+            for (int t = 0; t < d; t++) a.eig[(long)mat * d + t] = ffa::to_double(lam[order[t]]);
         }
     }
     cl.sync();
@@ -449,17 +456,15 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
     ff *coef = pbuf;
     for (int e = tid; e < n * ncol; e += kT) {
         const int i = e / ncol, c = e % ncol;
-        Wo[e] = ffa::from_double(Zm[(long)order[r + c * R] * n + i]);
+        Wo[e] = Zm[(long)order[r + c * R] * n + i];
     }
     __syncthreads();
     for (int k = n - 3; k >= 0; k--) {
-        const double td = tau_g[k];
-        if (td == 0.0) continue;
+        const ff tk = tau_g[k];
+        if (tk.hi == 0.0f) continue;
         const int m = n - k - 1;
-        if (tid == 0) fsc[3] = ffa::from_double(td);
         for (int i = tid; i < m; i += kT) vk[i] = Vh[(long)k * n + i];
         __syncthreads();
-        const ff tk = fsc[3];
         for (int c = warp; c < ncol; c += kNW) {
             ffa::acc Q = ffa::acc_zero();
             for (int i = lane; i < m; i += 32) ffa::acc_fma(Q, vk[i], Wo[(size_t)(k + 1 + i) * ncol + c]);
@@ -500,23 +505,32 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
     cl.sync();  // no CTA leaves while others may still write into its shared memory
 }
 
-// Shared-memory plan of one CTA for cluster size R.
-size_t smem_plan(int n, int d, int R, long *region0) {
-    long reg = rows_elems(n, R);
+// Shared-memory plan of one CTA for cluster size R: region 0 holds the packed
+// rows (phase 1), then T and the per-warp inverse-iteration slots (phase 2),
+// then the CTA's columns of the eigenvectors (phase 3).
+size_t smem_plan(int n, int d, int R, long *region0, int *nslots) {
+    const long rows = rows_elems(n, R);
     const int ncol = (d + R - 1) / R;
-    const long p2 = (long)((2 * sizeof(double) * n + 2 * sizeof(double) * kNW + 2 * sizeof(float) * n + 7) / sizeof(ff));
-    const long p3 = (long)n * ncol;
-    if (p2 > reg) reg = p2;
-    if (p3 > reg) reg = p3;
+    const long t_part = 2L * n + (long)((2 * sizeof(float) * n + 2 * sizeof(float) * kNW + 8 + 7) / sizeof(ff));
+    const long slot = 5L * n + (n + 7) / 8;
+    const int per_cta = ncol;
+    int ns = kNW < per_cta ? kNW : per_cta;
+    if (ns < 1) ns = 1;
+    long reg = rows;
+    // as many slots as fit in the packed-row region, at least one
+    while (ns > 1 && t_part + ns * slot > reg) ns--;
+    if (t_part + ns * slot > reg) reg = t_part + ns * slot;
+    if ((long)n * ncol > reg) reg = (long)n * ncol;
     *region0 = reg;
-    return sizeof(ff) * ((size_t)reg + (size_t)R * n + 4 * (size_t)n) + sizeof(ffa::acc) * kNW + sizeof(ff) * 4 +
-           sizeof(double) * 4;
+    *nslots = ns;
+    return sizeof(ff) * ((size_t)reg + (size_t)R * n + 4 * (size_t)n) + sizeof(ffa::acc) * kNW + sizeof(ff) * 4;
 }
 
 int pick_R(int n, int d) {
     for (int R = 2; R <= 8; R *= 2) {
         long reg;
-        if (smem_plan(n, d, R, &reg) <= kSmemMax) return R;
+        int ns;
+        if (smem_plan(n, d, R, &reg, &ns) <= kSmemMax) return R;
     }
     return 0;
 }
@@ -524,7 +538,7 @@ int pick_R(int n, int d) {
 }  // namespace
 
 struct EigPlan {
-    size_t dg, ed, tau, v0, Vh, Z, lu, piv, sig, lam, order, total;
+    size_t dg, ed, tau, v0, Vh, Z, sig, lam, order, total;
 };
 
 static EigPlan eig_plan(int n, int d, int mats) {
@@ -535,16 +549,14 @@ static EigPlan eig_plan(int n, int d, int mats) {
         o = align_up(o + bytes, 256);
         return at;
     };
-    p.dg = take(sizeof(double) * (size_t)mats * n);
-    p.ed = take(sizeof(double) * (size_t)mats * n);
-    p.tau = take(sizeof(double) * (size_t)mats * n);
-    p.v0 = take(sizeof(double) * (size_t)mats * n);
+    p.dg = take(sizeof(ff) * (size_t)mats * n);
+    p.ed = take(sizeof(ff) * (size_t)mats * n);
+    p.tau = take(sizeof(ff) * (size_t)mats * n);
+    p.v0 = take(sizeof(ff) * (size_t)mats * n);
     p.Vh = take(sizeof(ff) * (size_t)mats * n * n);
-    p.Z = take(sizeof(double) * (size_t)mats * d * n);
-    p.lu = take(sizeof(double) * (size_t)mats * d * 5 * n);
-    p.piv = take((size_t)mats * d * n);
+    p.Z = take(sizeof(ff) * (size_t)mats * d * n);
     p.sig = take(sizeof(float) * (size_t)mats * d);
-    p.lam = take(sizeof(double) * (size_t)mats * d);
+    p.lam = take(sizeof(ff) * (size_t)mats * d);
     p.order = take(sizeof(int) * (size_t)mats * d);
     p.total = o;
     return p;
@@ -558,7 +570,8 @@ cudaError_t launch_eig(const void *cov_ff, int n, int d, int mats, double *V, do
     const int R = pick_R(n, d);
     if (R == 0) return cudaErrorNotSupported;
     long region0 = 0;
-    const size_t smem = smem_plan(n, d, R, &region0);
+    int nslots = 1;
+    const size_t smem = smem_plan(n, d, R, &region0, &nslots);
     static int attr_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -575,16 +588,15 @@ cudaError_t launch_eig(const void *cov_ff, int n, int d, int mats, double *V, do
     a.d = d;
     a.R = R;
     a.region0 = region0;
-    a.dg = (double *)(b + p.dg);
-    a.ed = (double *)(b + p.ed);
-    a.tau = (double *)(b + p.tau);
-    a.v0 = (double *)(b + p.v0);
+    a.nslots = nslots;
+    a.dg = (ff *)(b + p.dg);
+    a.ed = (ff *)(b + p.ed);
+    a.tau = (ff *)(b + p.tau);
+    a.v0 = (ff *)(b + p.v0);
     a.Vh = (ff *)(b + p.Vh);
-    a.Z = (double *)(b + p.Z);
-    a.lu = (double *)(b + p.lu);
-    a.piv = (uint8_t *)(b + p.piv);
+    a.Z = (ff *)(b + p.Z);
     a.sig = (float *)(b + p.sig);
-    a.lam = (double *)(b + p.lam);
+    a.lam = (ff *)(b + p.lam);
     a.order = (int *)(b + p.order);
     a.V = V;
     a.eig = eigvals;

@@ -51,6 +51,31 @@ __device__ __forceinline__ ff mul(ff a, ff b) {
     return fast_two_sum(p, e);
 }
 
+__device__ __forceinline__ ff two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return ff{p, __fmaf_rn(a, b, -p)};
+}
+
+// a / b (one correction step: ~47 bits)
+__device__ __forceinline__ ff div(ff a, ff b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const ff r = sub(a, mul(ff{q1, 0.0f}, b));
+    const float q2 = __fdiv_rn(r.hi, b.hi);
+    return fast_two_sum(q1, q2);
+}
+
+// sqrt(a) for a >= 0 (one Newton correction)
+__device__ __forceinline__ ff sqrt(ff a) {
+    if (!(a.hi > 0.0f)) return ff{0.0f, 0.0f};
+    const float s = sqrtf(a.hi);
+    const ff e = sub(a, two_prod(s, s));
+    return fast_two_sum(s, __fdiv_rn(e.hi, __fmul_rn(2.0f, s)));
+}
+
+__device__ __forceinline__ ff scale(ff a, float p2) { return ff{__fmul_rn(a.hi, p2), __fmul_rn(a.lo, p2)}; }
+__device__ __forceinline__ bool less(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ ff fabs_ff(ff a) { return a.hi < 0.0f ? ff{-a.hi, -a.lo} : a; }
+
 // Compensated dot-product accumulator: s carries the running sum of the
 // leading products, c the (small) compensation.
 struct acc {
