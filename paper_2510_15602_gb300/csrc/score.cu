@@ -24,56 +24,67 @@
 namespace qfca {
 namespace {
 
-constexpr int kTH = 32;
+constexpr int kSW = 128;  // output columns per CTA (one thread each)
+constexpr int kTH = 16;   // output rows per CTA band
 
 struct ScoreGeom {
-    int SW, TH, TR, TC, TCp, kg, n_kg;
+    int TH, TR, TC, TCp, kg, n_kg;
     size_t smem;
 };
 
 ScoreGeom score_geom(int H, int W, int d, int B, int r) {
     ScoreGeom g;
-    g.SW = W >= 128 ? 128 : 64;
     g.TH = kTH;
     g.TR = g.TH + 2 * r;
-    g.TC = g.SW + 2 * r;
+    g.TC = kSW + 2 * r;
     g.TCp = (int)align_up(g.TC, 16);
-    const long tiles = (long)((W + g.SW - 1) / g.SW) * ((H + g.TH - 1) / g.TH);
-    int n_kg = (int)((2 * 152 + tiles - 1) / tiles);
+    const long tiles = (long)((W + kSW - 1) / kSW) * ((H + g.TH - 1) / g.TH);
+    // enough CTAs for ~4 per SM over 152 SMs
+    int n_kg = (int)((4 * 152 + tiles - 1) / tiles);
     if (n_kg < 1) n_kg = 1;
     if (n_kg > d) n_kg = d;
     g.kg = (d + n_kg - 1) / n_kg;
     g.n_kg = (d + g.kg - 1) / g.kg;
-    g.smem = sizeof(uint32_t) * (size_t)B * g.SW               // histograms
-             + sizeof(unsigned long long) * (size_t)g.TH * g.SW  // per-pixel sums
-             + sizeof(uint32_t) * 256                            // cumR
-             + (size_t)g.TR * g.TCp;                             // bin tile
+    g.smem = sizeof(uint32_t) * (size_t)B * kSW                 // histograms [B][kSW]
+             + sizeof(unsigned long long) * (size_t)g.TH * kSW  // per-pixel sums
+             + 2 * sizeof(uint32_t) * 256                       // cumR, cumR * N_loc(interior)
+             + (size_t)g.TR * g.TCp;                            // bin tile
     return g;
 }
 
-__global__ void k_window_emd(const uint8_t *__restrict__ bins, int H, int W, int pitch, int d, int B, int r,
-                             ScoreGeom g, const uint32_t *__restrict__ ref_hist, uint32_t Nref,
-                             unsigned long long *__restrict__ acc, uint64_t *__restrict__ numer) {
+// Window histograms + exact EMD numerators for a band of kTH rows x kSW columns
+// and a group of components.  Thread t owns output column x0 + t: its window
+// histogram lives in shared memory at hist[b * kSW + t] (conflict-free), and
+// slides down the band (one row of 2r+1 bins leaves, one enters); increments
+// are shared-memory atomics without return, so no thread waits on them.
+// ACC is the type of the CDF walk: uint32_t when (B-1)(2r+1)^2 N_ref < 2^32
+// (the numerator D and every term then fit), else unsigned long long.
+template <typename ACC>
+__global__ void __launch_bounds__(kSW) k_window_emd(const uint8_t *__restrict__ bins, int H, int W, int pitch, int d,
+                                                     int B, int r, ScoreGeom g, const uint32_t *__restrict__ ref_hist,
+                                                     uint32_t Nref, unsigned long long *__restrict__ acc,
+                                                     uint64_t *__restrict__ numer) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int SW = g.SW;
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
-    unsigned long long *accS = reinterpret_cast<unsigned long long *>(hist + (size_t)B * SW);
-    uint32_t *cumR = reinterpret_cast<uint32_t *>(accS + (size_t)g.TH * SW);
-    uint8_t *tile = reinterpret_cast<uint8_t *>(cumR + 256);
+    unsigned long long *accS = reinterpret_cast<unsigned long long *>(hist + (size_t)B * kSW);
+    uint32_t *cumR = reinterpret_cast<uint32_t *>(accS + (size_t)g.TH * kSW);
+    uint32_t *cRi = cumR + 256;  // cumR[b] * N_loc for an interior window
+    uint8_t *tile = reinterpret_cast<uint8_t *>(cRi + 256);
 
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * SW, y0 = blockIdx.y * g.TH;
+    const int x0 = blockIdx.x * kSW, y0 = blockIdx.y * g.TH;
     const int k0 = blockIdx.z * g.kg, k1 = min(d, k0 + g.kg);
     const int x = x0 + t;
-    const int ty0 = y0 - r, tx0 = x0 - r;  // image coords of tile origin
-    for (int i = 0; i < g.TH; i++) accS[i * SW + t] = 0ull;
+    const int ty0 = y0 - r, tx0 = x0 - r;  // image coordinates of the tile origin
+    const uint32_t Nint = (uint32_t)((2 * r + 1) * (2 * r + 1));
+    for (int i = 0; i < g.TH; i++) accS[i * kSW + t] = 0ull;
 
     const int xl = max(0, x - r), xr = min(W - 1, x + r);
     const int ncols = xr - xl + 1;
     for (int k = k0; k < k1; k++) {
         __syncthreads();
         const uint8_t *bk = bins + (long)k * H * pitch;
-        for (int idx = t; idx < g.TR * g.TC; idx += SW) {
+        for (int idx = t; idx < g.TR * g.TC; idx += kSW) {
             const int ty = idx / g.TC, tx = idx - ty * g.TC;
             const int gy = ty0 + ty, gx = tx0 + tx;
             int v = 0;
@@ -82,43 +93,56 @@ __global__ void k_window_emd(const uint8_t *__restrict__ bins, int H, int W, int
         }
         if (t == 0) {
             uint32_t c = 0;
-            for (int b = 0; b < B; b++) { c += ref_hist[(long)k * B + b]; cumR[b] = c; }
-        }
-        __syncthreads();
-        if (x >= W) continue;
-        for (int b = 0; b < B; b++) hist[b * SW + t] = 0;
-        // window of the band's first row
-        const int ya = max(0, y0 - r), yb = min(H - 1, y0 + r);
-        for (int yy = ya; yy <= yb; yy++) {
-            const uint8_t *row = tile + (yy - ty0) * g.TCp - tx0;
-            for (int xx = xl; xx <= xr; xx++) hist[row[xx] * SW + t] += 1u;
-        }
-        for (int i = 0; i < g.TH; i++) {
-            const int yy = y0 + i;
-            if (yy >= H) break;
-            if (i > 0) {
-                const int yo = yy - r - 1, yn = yy + r;
-                if (yo >= 0) {
-                    const uint8_t *row = tile + (yo - ty0) * g.TCp - tx0;
-                    for (int xx = xl; xx <= xr; xx++) hist[row[xx] * SW + t] -= 1u;
-                }
-                if (yn < H) {
-                    const uint8_t *row = tile + (yn - ty0) * g.TCp - tx0;
-                    for (int xx = xl; xx <= xr; xx++) hist[row[xx] * SW + t] += 1u;
-                }
-            }
-            const int nrows = min(H - 1, yy + r) - max(0, yy - r) + 1;
-            const unsigned long long Nloc = (unsigned long long)(nrows * ncols);
-            uint32_t cum = 0;
-            unsigned long long D = 0;
             for (int b = 0; b < B; b++) {
-                cum += hist[b * SW + t];
-                const unsigned long long a = (unsigned long long)cum * Nref;
-                const unsigned long long c = (unsigned long long)cumR[b] * Nloc;
-                D += a > c ? a - c : c - a;
+                c += ref_hist[(long)k * B + b];
+                cumR[b] = c;
+                cRi[b] = c * Nint;
             }
-            accS[i * SW + t] += D;
-            if (numer) numer[((long)k * H + yy) * W + x] = D;
+        }
+        for (int b = 0; b < B; b++) hist[b * kSW + t] = 0;
+        __syncthreads();
+        if (x < W) {
+            // window of the band's first row
+            const int ya = max(0, y0 - r), yb = min(H - 1, y0 + r);
+            for (int yy = ya; yy <= yb; yy++) {
+                const uint8_t *row = tile + (yy - ty0) * g.TCp - tx0;
+                for (int xx = xl; xx <= xr; xx++) atomicAdd(&hist[row[xx] * kSW + t], 1u);
+            }
+            for (int i = 0; i < g.TH; i++) {
+                const int yy = y0 + i;
+                if (yy >= H) break;
+                if (i > 0) {
+                    const int yo = yy - r - 1, yn = yy + r;
+                    if (yo >= 0) {
+                        const uint8_t *row = tile + (yo - ty0) * g.TCp - tx0;
+                        for (int xx = xl; xx <= xr; xx++) atomicSub(&hist[row[xx] * kSW + t], 1u);
+                    }
+                    if (yn < H) {
+                        const uint8_t *row = tile + (yn - ty0) * g.TCp - tx0;
+                        for (int xx = xl; xx <= xr; xx++) atomicAdd(&hist[row[xx] * kSW + t], 1u);
+                    }
+                }
+                const int nrows = min(H - 1, yy + r) - max(0, yy - r) + 1;
+                const uint32_t Nloc = (uint32_t)(nrows * ncols);
+                ACC D = 0, a = 0;
+                if (Nloc == Nint) {
+#pragma unroll 4
+                    for (int b = 0; b < B; b++) {
+                        a += (ACC)hist[b * kSW + t] * (ACC)Nref;
+                        const ACC c = (ACC)cRi[b];
+                        D += a > c ? a - c : c - a;
+                    }
+                } else {
+#pragma unroll 4
+                    for (int b = 0; b < B; b++) {
+                        a += (ACC)hist[b * kSW + t] * (ACC)Nref;
+                        const ACC c = (ACC)cumR[b] * (ACC)Nloc;
+                        D += a > c ? a - c : c - a;
+                    }
+                }
+                accS[i * kSW + t] += (unsigned long long)D;
+                if (numer) numer[((long)k * H + yy) * W + x] = (uint64_t)D;
+            }
         }
     }
     __syncthreads();
@@ -126,8 +150,8 @@ __global__ void k_window_emd(const uint8_t *__restrict__ bins, int H, int W, int
         for (int i = 0; i < g.TH; i++) {
             const int yy = y0 + i;
             if (yy >= H) break;
-            if (g.n_kg == 1) acc[(long)yy * W + x] = accS[i * SW + t];
-            else atomicAdd(&acc[(long)yy * W + x], accS[i * SW + t]);
+            if (g.n_kg == 1) acc[(long)yy * W + x] = accS[i * kSW + t];
+            else atomicAdd(&acc[(long)yy * W + x], accS[i * kSW + t]);
         }
 }
 
@@ -155,15 +179,29 @@ cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d,
     cudaError_t err = cudaSuccess;
     if (g.n_kg > 1) err = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (size_t)H * W, st);
     if (err != cudaSuccess) return err;
-    static bool attr_set = false;
-    if (!attr_set) {
-        err = cudaFuncSetAttribute(k_window_emd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    // u32 walk when every partial and the numerator fit: (B-1) (2r+1)^2 N_ref < 2^32
+    const double bound = (double)(B - 1) * (double)((2 * r + 1) * (2 * r + 1)) * (double)ref_total;
+    const bool narrow = bound < 4294967295.0 && (double)(2 * r + 1) * (2 * r + 1) * ref_total < 4294967295.0;
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        err = cudaFuncSetAttribute(k_window_emd<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(k_window_emd<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024);
         if (err != cudaSuccess) return err;
-        attr_set = true;
+        attr_dev = dev;
     }
-    dim3 grid((W + g.SW - 1) / g.SW, (H + g.TH - 1) / g.TH, g.n_kg);
-    QFCA_LAUNCH("k_window_emd", st,
-                k_window_emd<<<grid, g.SW, g.smem, st>>>(bins, H, W, pitch, d, B, r, g, ref_hist, ref_total, acc, numer));
+    dim3 grid((W + kSW - 1) / kSW, (H + g.TH - 1) / g.TH, g.n_kg);
+    if (narrow)
+        QFCA_LAUNCH("k_window_emd", st,
+                    k_window_emd<uint32_t><<<grid, kSW, g.smem, st>>>(bins, H, W, pitch, d, B, r, g, ref_hist,
+                                                                       ref_total, acc, numer));
+    else
+        QFCA_LAUNCH("k_window_emd", st,
+                    k_window_emd<unsigned long long><<<grid, kSW, g.smem, st>>>(bins, H, W, pitch, d, B, r, g,
+                                                                                 ref_hist, ref_total, acc, numer));
     const long N = (long)H * W;
     QFCA_LAUNCH("k_finalize", st, k_finalize<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(acc, H, W, r, d, ref_total, score));
     return cudaGetLastError();
