@@ -166,6 +166,38 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
  * *out receives the word; returns QFCA_ERR_TIMEOUT when it was non-zero. */
 qfca_status qfca_device_status(qfca_ctx *ctx, int *out);
 
+/* Optional outputs of qfca_batch_run (each pointer may be NULL; the library
+ * then keeps that intermediate in its workspace).  Per-image blocks are packed
+ * image after image:
+ *   mean [nimg][C], V [nimg][C][d], eigvals [nimg][d]  (FP64, as qfca_fit_pca)
+ *   bins [nimg][d][H][pitch] with `pitch` (>= W, multiple of 16; ignored when
+ *        bins is NULL), ref_hist [nimg][d][B], lo/hi [nimg][d]. */
+typedef struct {
+    double *mean;
+    double *V;
+    double *eigvals;
+    uint8_t *bins;
+    int pitch;
+    uint32_t *ref_hist;
+    float *lo;
+    float *hi;
+} qfca_batch_outputs;
+
+/* qfca_batch_run -- the whole path (Sec. 3.3 fit and projection, Sec. 3.1
+ * quantisation, window histograms and EMD, channel mean) for nimg feature
+ * maps of one shape stored one after the other in X (image i starts at
+ * X + i*C*H*W), with each stage launched once for the whole batch: the
+ * covariance tiles, eigensolver clusters, projection tiles, quantisation bands
+ * and window tiles of every image share one grid.  Quantisation ranges are
+ * each component's image-wide min/max; the reference of each image is its
+ * own global histogram (N_ref = H*W).
+ *   scores  device f32 [nimg][H][W].
+ * Results equal nimg separate calls of qfca_fit_pca, qfca_quantize and
+ * qfca_score (same kernels, same arithmetic).  Requires 1 <= nimg <= 4096
+ * and the limits of those entry points. */
+qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int d, int B, int r,
+                           int precision, float *scores, const qfca_batch_outputs *extra, void *stream);
+
 /* qfca_score_noalloc -- the same computation as qfca_score (without the
  * optional numerator output), for callers that cannot allocate device memory:
  * code that runs under a host application or memory manager that owns every

@@ -272,8 +272,8 @@ qfca_status qfca_fit_pca(qfca_ctx *ctx, const float *X, qfca_fmap desc, int d, c
     DeviceGuard g(ctx->device);
     HookScope hs(ctx);
     const long N = (long)desc.H * desc.W;
-    if ((s = ensure_ws(ctx, fit_workspace_bytes(desc.C, N, d)))) return s;
-    cudaError_t e = launch_fit(X, desc.layout, desc.H, desc.W, desc.C, d, out->mean, out->V, out->eigvals, ctx->ws,
+    if ((s = ensure_ws(ctx, fit_workspace_bytes(desc.C, N, d, 1)))) return s;
+    cudaError_t e = launch_fit(X, desc.layout, desc.H, desc.W, desc.C, d, 1, out->mean, out->V, out->eigvals, ctx->ws,
                                ctx->status_dev, (cudaStream_t)stream);
     if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "eigensolver shape C=%d d=%d", desc.C, d);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_fit_pca");
@@ -290,8 +290,8 @@ qfca_status qfca_covariance(qfca_ctx *ctx, const float *X, qfca_fmap desc, doubl
     DeviceGuard g(ctx->device);
     HookScope hs(ctx);
     const long N = (long)desc.H * desc.W;
-    if ((s = ensure_ws(ctx, gram_workspace_bytes(desc.C, N)))) return s;
-    cudaError_t e = launch_gram_cov(X, desc.layout, desc.C, N, mean_out, cov_out, nullptr, ctx->ws, ctx->status_dev,
+    if ((s = ensure_ws(ctx, gram_workspace_bytes(desc.C, N, 1)))) return s;
+    cudaError_t e = launch_gram_cov(X, desc.layout, desc.C, N, 1, mean_out, cov_out, nullptr, ctx->ws, ctx->status_dev,
                                     (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_covariance");
     return QFCA_OK;
@@ -323,19 +323,19 @@ qfca_status qfca_quantize(qfca_ctx *ctx, const float *X, qfca_fmap desc, const q
     const size_t o_mm = 0;
     const size_t o_y = o_mm + bytes_mmkeys(d);
     const size_t o_p = o_y + (Y_out ? 0 : align_up(sizeof(float) * d * N, 256));
-    if ((s = ensure_ws(ctx, o_p + project_workspace_bytes(desc.C, N, d)))) return s;
+    if ((s = ensure_ws(ctx, o_p + project_workspace_bytes(desc.C, N, d, 1)))) return s;
     char *base = (char *)ctx->ws;
     uint32_t *mm = (uint32_t *)(base + o_mm);
     float *Y = Y_out ? Y_out : (float *)(base + o_y);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = launch_project(X, desc.layout, desc.H, desc.W, desc.C, basis->mean, basis->V, d, precision, Y, mm,
-                                   base + o_p, ctx->status_dev, st);
+    cudaError_t e = launch_project(X, desc.layout, desc.H, desc.W, desc.C, basis->mean, basis->V, d, 1, precision, Y,
+                                   mm, base + o_p, ctx->status_dev, st);
     if (e == cudaErrorNotSupported) {
         cudaGetLastError();
         return fail(ctx, QFCA_ERR_UNSUPPORTED, "projection precision %d not supported for this shape", precision);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_quantize/project");
-    e = launch_quantize(Y, N, desc.H, desc.W, d, B, range_mode, mm, lo_in, hi_in, bins, pitch, lo_out, hi_out,
+    e = launch_quantize(Y, N, desc.H, desc.W, d, 1, B, range_mode, mm, lo_in, hi_in, bins, pitch, lo_out, hi_out,
                         ref_hist_out, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_quantize/quantize");
     return QFCA_OK;
@@ -356,12 +356,77 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
     if (ref_total < 1) return fail(ctx, QFCA_ERR_INVALID_ARG, "ref_total must be >= 1");
     DeviceGuard g(ctx->device);
     HookScope hs(ctx);
-    if ((s = ensure_ws(ctx, score_workspace_bytes(H, W)))) return s;
-    cudaError_t e = launch_score_ws(bins, H, W, pitch, d, B, r, ref_hist, ref_total, score, numer_out, ctx->ws,
+    if ((s = ensure_ws(ctx, score_workspace_bytes(H, W, 1)))) return s;
+    cudaError_t e = launch_score_ws(bins, H, W, pitch, d, 1, B, r, ref_hist, ref_total, score, numer_out, ctx->ws,
                                     (cudaStream_t)stream);
     if (e == cudaErrorNotSupported)
         return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d needs more shared memory than a CTA has", B, r);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_score");
+    return QFCA_OK;
+}
+
+qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int d, int B, int r,
+                           int precision, float *scores, const qfca_batch_outputs *extra, void *stream) {
+    qfca_status s = check_ctx(ctx);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if ((s = check_fmap(ctx, X, desc))) return s;
+    if (nimg < 1 || nimg > 4096) return fail(ctx, QFCA_ERR_INVALID_ARG, "nimg = %d outside [1, 4096]", nimg);
+    if (!scores) return fail(ctx, QFCA_ERR_INVALID_ARG, "scores NULL");
+    if (d < 1 || d > desc.C || d > kMaxD) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, min(C, %d)]", d, kMaxD);
+    if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
+    if (r < 1 || 2 * r + 1 > 127) return fail(ctx, QFCA_ERR_INVALID_ARG, "r = %d outside [1, 63]", r);
+    if (precision != QFCA_F32 && precision != QFCA_BF16)
+        return fail(ctx, precision == QFCA_FP8_E4M3 ? QFCA_ERR_UNSUPPORTED : QFCA_ERR_INVALID_ARG,
+                    "precision %d not available", precision);
+    const int pitch_min = (desc.W + 15) / 16 * 16;
+    if (extra && extra->bins && (extra->pitch < desc.W || extra->pitch % 16 != 0))
+        return fail(ctx, QFCA_ERR_INVALID_ARG, "extra->pitch %d must be >= W and a multiple of 16", extra->pitch);
+    DeviceGuard g(ctx->device);
+    HookScope hs(ctx);
+    const long N = (long)desc.H * desc.W;
+    const int C = desc.C;
+    const int pitch = (extra && extra->bins) ? extra->pitch : pitch_min;
+    // workspace: [fit | basis | Y | keys | project | bins | hist | lo/hi | score]
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t at = o; o = align_up(o + bytes, 256); return at; };
+    const size_t o_fit = take(fit_workspace_bytes(C, N, d, nimg));
+    const size_t o_mean = take(sizeof(double) * (size_t)C * nimg);
+    const size_t o_V = take(sizeof(double) * (size_t)C * d * nimg);
+    const size_t o_ev = take(sizeof(double) * (size_t)d * nimg);
+    const size_t o_Y = take(sizeof(float) * (size_t)d * N * nimg);
+    const size_t o_mm = take(sizeof(uint32_t) * 2 * (size_t)d * kKeyStride * nimg);
+    const size_t o_pj = take(project_workspace_bytes(C, N, d, nimg));
+    const size_t o_bins = take((size_t)d * desc.H * pitch * nimg);
+    const size_t o_hist = take(sizeof(uint32_t) * (size_t)d * B * nimg);
+    const size_t o_lohi = take(sizeof(float) * 2 * (size_t)d * nimg);
+    const size_t o_sc = take(score_workspace_bytes(desc.H, desc.W, nimg));
+    if ((s = ensure_ws(ctx, o))) return s;
+    char *b = (char *)ctx->ws;
+    double *mean = (extra && extra->mean) ? extra->mean : (double *)(b + o_mean);
+    double *V = (extra && extra->V) ? extra->V : (double *)(b + o_V);
+    double *ev = (extra && extra->eigvals) ? extra->eigvals : (double *)(b + o_ev);
+    uint8_t *bins = (extra && extra->bins) ? extra->bins : (uint8_t *)(b + o_bins);
+    uint32_t *hist = (extra && extra->ref_hist) ? extra->ref_hist : (uint32_t *)(b + o_hist);
+    float *lo = (extra && extra->lo) ? extra->lo : (float *)(b + o_lohi);
+    float *hi = (extra && extra->hi) ? extra->hi : (float *)(b + o_lohi) + (size_t)d * nimg;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_fit(X, desc.layout, desc.H, desc.W, C, d, nimg, mean, V, ev, b + o_fit, ctx->status_dev, st);
+    if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "eigensolver shape C=%d d=%d", C, d);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run/fit");
+    float *Y = (float *)(b + o_Y);
+    uint32_t *mm = (uint32_t *)(b + o_mm);
+    e = launch_project(X, desc.layout, desc.H, desc.W, C, mean, V, d, nimg, precision, Y, mm, b + o_pj,
+                       ctx->status_dev, st);
+    if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "projection precision %d", precision);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run/project");
+    e = launch_quantize(Y, N, desc.H, desc.W, d, nimg, B, QFCA_RANGE_IMAGE, mm, nullptr, nullptr, bins, pitch, lo, hi,
+                        hist, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run/quantize");
+    e = launch_score_ws(bins, desc.H, desc.W, pitch, d, nimg, B, r, hist, (uint32_t)N, scores, nullptr, b + o_sc, st);
+    if (e == cudaErrorNotSupported)
+        return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d needs more shared memory than a CTA has", B, r);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run/score");
     return QFCA_OK;
 }
 

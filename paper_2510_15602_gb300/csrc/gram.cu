@@ -55,8 +55,11 @@ __device__ __forceinline__ int tile_pair_idx(int p, int nt, int &j) {
 }
 
 // e_c = smallest exponent with max_p |x_cp| < 2^e_c  (stored as the max |x| bits first)
+// Grid (x-chunks, C, images).
 __global__ void k_chan_absmax(const float *__restrict__ X, int layout, int C, long N, unsigned *__restrict__ amax) {
     const int c = blockIdx.y;
+    X += (long)blockIdx.z * C * N;
+    amax += (long)blockIdx.z * C;
     unsigned m = 0;
     if (layout == QFCA_NCHW) {
         const float *row = X + (long)c * N;
@@ -145,7 +148,8 @@ __device__ __forceinline__ void stage_block(const float *__restrict__ X, int lay
     }
 }
 
-// Grid: n_pairs * n_split CTAs.  Gint: [C][C] int64 (upper tiles accumulated), Dsum: [4][C] int64.
+// Grid: images * n_pairs * n_split CTAs.  Per image: Gint [C][C] int64 (upper
+// tiles accumulated), Dsum [4][C] int64, scale [C].
 __global__ void __launch_bounds__(kThreads, 1) k_gram(const float *__restrict__ X, int layout, int vec_ok, int C, long N,
                                                       const float *__restrict__ scale, int nt, int n_pairs,
                                                       long chunk, unsigned long long *__restrict__ Gint,
@@ -160,7 +164,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const float *__restrict__ 
     unsigned long long *dsq = (unsigned long long *)(tmem_slot + 4);  // [128] (8-B aligned: bar is)
     int *dsum = (int *)(dsq + kTB);                                    // [4][128]
 
-    const int pair = blockIdx.x % n_pairs, split = blockIdx.x / n_pairs;
+    const int per_img = n_pairs * (int)((N + chunk - 1) / chunk);
+    const int img = blockIdx.x / per_img, rem = blockIdx.x % per_img;
+    const int pair = rem % n_pairs, split = rem / n_pairs;
+    X += (long)img * C * N;
+    scale += (long)img * C;
+    Gint += (long)img * C * C;
+    Dsum += (long)img * kSlices * C;
     int tj;
     const int ti = tile_pair_idx(pair, nt, tj);
     const bool diag = ti == tj;
@@ -279,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const float *__restrict__ 
 }
 
 __global__ void k_chan_scale(const unsigned *__restrict__ amax, int C, float *__restrict__ scale, int *__restrict__ ex) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;  // over images * C
     if (c >= C) return;
     const unsigned b = amax[c];
     int e = 0;
@@ -293,11 +303,19 @@ __global__ void k_chan_scale(const unsigned *__restrict__ amax, int C, float *__
 }
 
 // Sigma_ij = 2^(e_i+e_j) T_ij 2^-40 / N - mu_i mu_j ;  mu_c = 2^e_c S_c / N,
-// S_c = sum_i D_i,c 2^(-6-7i).  Writes mean[C] and the full symmetric cov[C][C].
+// S_c = sum_i D_i,c 2^(-6-7i).  Writes mean[C] and the full symmetric cov[C][C]
+// of each image (grid.y = image).
 __global__ void k_cov_finalize(const unsigned long long *__restrict__ Gint, const unsigned long long *__restrict__ Dsum,
                                const int *__restrict__ ex, int C, long N, double *__restrict__ mean,
                                double *__restrict__ cov, float2 *__restrict__ cov_ff) {
     const double invN = 1.0 / (double)N;
+    const long img = blockIdx.y;
+    Gint += img * C * C;
+    Dsum += img * kSlices * C;
+    ex += img * C;
+    mean += img * C;
+    cov += img * C * C;
+    if (cov_ff) cov_ff += img * C * C;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)C * C; e += (long)gridDim.x * blockDim.x) {
         const int i = (int)(e / C), j = (int)(e % C);
         const int a = min(i, j), b = max(i, j);
@@ -326,12 +344,14 @@ struct GramPlan {
     size_t off_amax, off_scale, off_ex, off_G, off_D, total, smem;
 };
 
-static GramPlan gram_plan(int C, long N) {
+static GramPlan gram_plan(int C, long N, int nimg) {
     GramPlan g{};
     g.nt = (C + kTB - 1) / kTB;
     g.n_pairs = g.nt * (g.nt + 1) / 2;
-    // about one CTA per SM per image-worth of tiles, chunks a multiple of the window
-    int want = (152 + g.n_pairs - 1) / g.n_pairs;
+    // about two waves of one CTA per SM over the batch, chunks a multiple of the window
+    int want = (2 * 152 + g.n_pairs * nimg - 1) / (g.n_pairs * nimg);
+    if (nimg == 1) want = (152 + g.n_pairs - 1) / g.n_pairs;
+    if (want < 1) want = 1;
     long chunk = (N + want - 1) / want;
     chunk = (chunk + kWin - 1) / kWin * kWin;
     if (chunk < kWin) chunk = kWin;
@@ -339,31 +359,32 @@ static GramPlan gram_plan(int C, long N) {
     g.n_split = (int)((N + chunk - 1) / chunk);
     size_t o = 0;
     auto take = [&](size_t b) { size_t at = o; o = align_up(o + b, 256); return at; };
-    g.off_amax = take(sizeof(unsigned) * C);
-    g.off_scale = take(sizeof(float) * C);
-    g.off_ex = take(sizeof(int) * C);
-    g.off_G = take(sizeof(unsigned long long) * (size_t)C * C);
-    g.off_D = take(sizeof(unsigned long long) * (size_t)kSlices * C);
+    g.off_amax = take(sizeof(unsigned) * (size_t)C * nimg);
+    g.off_scale = take(sizeof(float) * (size_t)C * nimg);
+    g.off_ex = take(sizeof(int) * (size_t)C * nimg);
+    g.off_G = take(sizeof(unsigned long long) * (size_t)C * C * nimg);
+    g.off_D = take(sizeof(unsigned long long) * (size_t)kSlices * C * nimg);
     g.total = o;
     g.smem = 1024 + 2 * kSlices * kTB * 128 + 64 + sizeof(int) * kSlices * kTB + sizeof(unsigned long long) * kTB;
     return g;
 }
 
-size_t gram_workspace_bytes(int C, long N) { return gram_plan(C, N).total; }
+size_t gram_workspace_bytes(int C, long N, int nimg) { return gram_plan(C, N, nimg).total; }
 
-// mean[C] and cov[C][C] (FP64) of the feature map; ws: gram_workspace_bytes.
-cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, double *mean, double *cov, void *cov_ff, void *ws,
-                            int *status, cudaStream_t st) {
-    const GramPlan g = gram_plan(C, N);
+// mean[nimg][C] and cov[nimg][C][C] (FP64) of nimg feature maps stored one after
+// the other; ws: gram_workspace_bytes.
+cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, int nimg, double *mean, double *cov,
+                            void *cov_ff, void *ws, int *status, cudaStream_t st) {
+    const GramPlan g = gram_plan(C, N, nimg);
     char *b = (char *)ws;
     unsigned *amax = (unsigned *)(b + g.off_amax);
     float *scale = (float *)(b + g.off_scale);
     int *ex = (int *)(b + g.off_ex);
     unsigned long long *G = (unsigned long long *)(b + g.off_G);
     unsigned long long *D = (unsigned long long *)(b + g.off_D);
-    cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned) * C, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, sizeof(unsigned long long) * (size_t)C * C, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(D, 0, sizeof(unsigned long long) * kSlices * C, st);
+    cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned) * (size_t)C * nimg, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, sizeof(unsigned long long) * (size_t)C * C * nimg, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D, 0, sizeof(unsigned long long) * kSlices * (size_t)C * nimg, st);
     if (e != cudaSuccess) return e;
     static int attr_dev = -1;
     int dev = 0;
@@ -376,15 +397,17 @@ cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, double *m
     // float4 loads need 16-B aligned rows: NCHW, N % 4 == 0, X 16-B aligned
     const int vec_ok = layout == QFCA_NCHW && N % 4 == 0 && ((uintptr_t)X & 15) == 0;
     const int xb = (int)((N + 256 * 64 - 1) / (256 * 64));
-    QFCA_LAUNCH("k_chan_absmax", st, k_chan_absmax<<<dim3(xb < 1 ? 1 : xb, C), 256, 0, st>>>(X, layout, C, N, amax));
-    QFCA_LAUNCH("k_chan_scale", st, k_chan_scale<<<(C + 127) / 128, 128, 0, st>>>(amax, C, scale, ex));
+    QFCA_LAUNCH("k_chan_absmax", st,
+                k_chan_absmax<<<dim3(xb < 1 ? 1 : xb, C, nimg), 256, 0, st>>>(X, layout, C, N, amax));
+    QFCA_LAUNCH("k_chan_scale", st,
+                k_chan_scale<<<(unsigned)((C * nimg + 127) / 128), 128, 0, st>>>(amax, C * nimg, scale, ex));
     QFCA_LAUNCH("k_gram", st,
-                k_gram<<<g.n_pairs * g.n_split, kThreads, g.smem, st>>>(X, layout, vec_ok, C, N, scale, g.nt, g.n_pairs,
-                                                                       g.chunk, G, D, status));
+                k_gram<<<g.n_pairs * g.n_split * nimg, kThreads, g.smem, st>>>(X, layout, vec_ok, C, N, scale, g.nt,
+                                                                              g.n_pairs, g.chunk, G, D, status));
     const long cc = (long)C * C;
     QFCA_LAUNCH("k_cov_finalize", st,
-                k_cov_finalize<<<(unsigned)((cc + 255) / 256), 256, 0, st>>>(G, D, ex, C, N, mean, cov,
-                                                                             (float2 *)cov_ff));
+                k_cov_finalize<<<dim3((unsigned)((cc + 255) / 256), nimg), 256, 0, st>>>(G, D, ex, C, N, mean, cov,
+                                                                                        (float2 *)cov_ff));
     return cudaGetLastError();
 }
 

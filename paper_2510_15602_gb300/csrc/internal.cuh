@@ -18,18 +18,21 @@ constexpr int kMaxB = 255;   // bins
 
 // ------------------------------------------------------------------ fit (fit.cu)
 
-// Workspace bytes needed by one fit of a C-channel map of N pixels.
-size_t fit_workspace_bytes(int C, long N, int d);
+// Batched entry points take `nimg` images of one shape stored one after the
+// other (feature maps C*H*W floats apart; per-image outputs likewise packed).
 
-// Enqueue the PCA fit of one image.  ws: device scratch of fit_workspace_bytes.
-cudaError_t launch_fit(const float *X, int layout, int H, int W, int C, int d, double *mean,
-                       double *V, double *eigvals, void *ws, int *status, cudaStream_t st);
+// Workspace bytes needed by the fit of nimg C-channel maps of N pixels.
+size_t fit_workspace_bytes(int C, long N, int d, int nimg);
+
+// Enqueue the PCA fit of nimg images.  ws: device scratch of fit_workspace_bytes.
+cudaError_t launch_fit(const float *X, int layout, int H, int W, int C, int d, int nimg,
+                       double *mean, double *V, double *eigvals, void *ws, int *status, cudaStream_t st);
 
 // Mean and covariance of one feature map (gram.cu).
-size_t gram_workspace_bytes(int C, long N);
+size_t gram_workspace_bytes(int C, long N, int nimg);
 // cov_ff (may be NULL): the covariance also as float-float pairs (float2 [C][C]).
-cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, double *mean, double *cov, void *cov_ff,
-                            void *ws, int *status, cudaStream_t st);
+cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, int nimg, double *mean, double *cov,
+                            void *cov_ff, void *ws, int *status, cudaStream_t st);
 
 // Top-d eigenpairs of `mats` symmetric n x n matrices given as float-float
 // pairs (float2 [mats][n][n]) (eig.cu).
@@ -39,13 +42,14 @@ cudaError_t launch_eig(const void *cov_ff, int n, int d, int mats, double *V, do
 
 // ------------------------------------------------------------------ projection (project.cu)
 
-size_t project_workspace_bytes(int C, long N, int d);
+size_t project_workspace_bytes(int C, long N, int d, int nimg);
 
 // Y[k][p] = sum_c (x_cp - mean_c) V[c][k] in FP32 (precision QFCA_F32) or with
 // BF16 operands on tcgen05 (QFCA_BF16); also the per-component min/max
 // (as order-preserving u32 keys in mm_keys[2*d]).
+// Y [nimg][d][N]; mm_keys [nimg][2 d kKeyStride]; mean/V per image packed.
 cudaError_t launch_project(const float *X, int layout, int H, int W, int C, const double *mean,
-                           const double *V, int d, int precision, float *Y, uint32_t *mm_keys,
+                           const double *V, int d, int nimg, int precision, float *Y, uint32_t *mm_keys,
                            void *ws, int *status, cudaStream_t st);
 
 // Per-component min/max keys live 128 B apart (one L2 line each):
@@ -57,16 +61,18 @@ constexpr int kStatusMmaTimeout = 1;
 
 // ------------------------------------------------------------------ quantize (quantize.cu)
 
-cudaError_t launch_quantize(const float *Y, long N, int H, int W, int d, int B, int range_mode,
+// bins [nimg][d][H][pitch], hist [nimg][d][B], lo/hi out [nimg][d]; fixed ranges are shared.
+cudaError_t launch_quantize(const float *Y, long N, int H, int W, int d, int nimg, int B, int range_mode,
                             const uint32_t *mm_keys, const float *lo_in, const float *hi_in,
                             uint8_t *bins, int pitch, float *lo_out, float *hi_out,
                             uint32_t *hist, cudaStream_t st);
 
 // ------------------------------------------------------------------ score (score.cu)
 
-size_t score_workspace_bytes(int H, int W);
+size_t score_workspace_bytes(int H, int W, int nimg);
 
-cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d, int B, int r,
+// bins [nimg][d][H][pitch], ref_hist [nimg][d][B], score [nimg][H][W], numer [nimg][d][H][W].
+cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d, int nimg, int B, int r,
                             const uint32_t *ref_hist, uint32_t ref_total, float *score,
                             uint64_t *numer, void *ws, cudaStream_t st);
 

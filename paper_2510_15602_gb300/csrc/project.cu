@@ -17,18 +17,23 @@ namespace qfca {
 
 // tcgen05 BF16 projection (project_tc.cu)
 cudaError_t launch_project_bf16(const float *X, int layout, int H, int W, int C, const double *mean,
-                                const double *V, int d, float *Y, uint32_t *mm_keys, void *ws, int *status,
-                                cudaStream_t st);
-size_t project_bf16_workspace_bytes(int C, long N, int d);
+                                const double *V, int d, int nimg, float *Y, uint32_t *mm_keys, void *ws,
+                                int *status, cudaStream_t st);
+size_t project_bf16_workspace_bytes(int C, long N, int d, int nimg);
 
 namespace {
 
 constexpr int kPix = 128;
 constexpr int kCh = 32;
 
-// mean32[c] = (float)mean[c];  V32[c][j] = (float)V[c][j] for j < d, 0 for d <= j < DT.
+// Per image (grid.y): mean32[c] = (float)mean[c];  V32[c][j] = (float)V[c][j] for j < d, 0 for d <= j < DT.
 __global__ void k_prep_f32(const double *__restrict__ mean, const double *__restrict__ V, int C, int d, int DT,
-                           float *__restrict__ mean32, float *__restrict__ V32) {
+                           int Cs, float *__restrict__ mean32, float *__restrict__ V32) {
+    const long img = blockIdx.y;
+    mean += img * C;
+    V += img * C * d;
+    mean32 += img * Cs;
+    V32 += img * C * DT;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C * DT; e += gridDim.x * blockDim.x) {
         const int c = e / DT, j = e % DT;
         V32[e] = j < d ? (float)V[(long)c * d + j] : 0.0f;
@@ -36,17 +41,33 @@ __global__ void k_prep_f32(const double *__restrict__ mean, const double *__rest
     }
 }
 
+// min keys start at the largest key, max keys at the smallest (per image: d min keys, then d max keys)
+__global__ void k_init_keys(uint32_t *__restrict__ keys, int d, int nimg) {
+    const long total = (long)nimg * 2 * d * kKeyStride;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const long within = e % (2L * d * kKeyStride);
+        keys[e] = within < (long)d * kKeyStride ? 0xffffffffu : 0u;
+    }
+}
+
 template <int DT>
 __global__ void __launch_bounds__(kPix) k_project_f32(const float *__restrict__ X, int layout, int C, long N,
                                                      const float *__restrict__ mean32, const float *__restrict__ V32,
-                                                     int d, float *__restrict__ Y, uint32_t *__restrict__ mm_keys) {
+                                                     int d, int Cs, long tiles, float *__restrict__ Y,
+                                                     uint32_t *__restrict__ mm_keys) {
     __shared__ float Xs[kCh][kPix + 1];
     __shared__ __align__(16) float Vs[kCh][DT];
     __shared__ float Ms[kCh];
     __shared__ uint32_t kmin[DT], kmax[DT];
     const int tid = threadIdx.x;
     if (tid < DT) { kmin[tid] = 0xffffffffu; kmax[tid] = 0u; }
-    const long p0 = (long)blockIdx.x * kPix;
+    const long img = blockIdx.x / tiles;
+    X += img * C * N;
+    mean32 += img * Cs;
+    V32 += img * C * DT;
+    Y += img * d * N;
+    mm_keys += img * 2 * d * kKeyStride;
+    const long p0 = (blockIdx.x % tiles) * kPix;
     const long p = p0 + tid;
     float acc[DT];
 #pragma unroll
@@ -120,31 +141,42 @@ int pick_dt(int d) { return d <= 16 ? 16 : (d <= 32 ? 32 : 64); }
 
 }  // namespace
 
-size_t project_workspace_bytes(int C, long N, int d) {
-    const size_t f32 = align_up(sizeof(float) * (align_up(C, 64) + (size_t)C * 64), 256);
-    const size_t bf = project_bf16_workspace_bytes(C, N, d);
+size_t project_workspace_bytes(int C, long N, int d, int nimg) {
+    const size_t f32 = align_up(sizeof(float) * (align_up(C, 64) + (size_t)C * 64) * nimg, 256);
+    const size_t bf = project_bf16_workspace_bytes(C, N, d, nimg);
     return f32 > bf ? f32 : bf;
 }
 
 cudaError_t launch_project(const float *X, int layout, int H, int W, int C, const double *mean,
-                           const double *V, int d, int precision, float *Y, uint32_t *mm_keys, void *ws,
+                           const double *V, int d, int nimg, int precision, float *Y, uint32_t *mm_keys, void *ws,
                            int *status, cudaStream_t st) {
     const long N = (long)H * W;
-    // min keys start at the largest key, max keys at the smallest
-    cudaError_t err = cudaMemsetAsync(mm_keys, 0xff, sizeof(uint32_t) * d * kKeyStride, st);
-    if (err == cudaSuccess) err = cudaMemsetAsync(mm_keys + d * kKeyStride, 0x00, sizeof(uint32_t) * d * kKeyStride, st);
-    if (err != cudaSuccess) return err;
+    const long nkeys = (long)nimg * 2 * d * kKeyStride;
+    QFCA_LAUNCH("k_init_keys", st,
+                k_init_keys<<<(unsigned)((nkeys + 255) / 256), 256, 0, st>>>(mm_keys, d, nimg));
     if (precision == QFCA_BF16)
-        return launch_project_bf16(X, layout, H, W, C, mean, V, d, Y, mm_keys, ws, status, st);
+        return launch_project_bf16(X, layout, H, W, C, mean, V, d, nimg, Y, mm_keys, ws, status, st);
     const int DT = pick_dt(d);
+    const int Cs = (int)align_up(C, 64);
     float *mean32 = (float *)ws;
-    float *V32 = mean32 + align_up(C, 64);
-    QFCA_LAUNCH("k_prep_f32", st, k_prep_f32<<<(C * DT + 255) / 256, 256, 0, st>>>(mean, V, C, d, DT, mean32, V32));
-    const unsigned grid = (unsigned)((N + kPix - 1) / kPix);
+    float *V32 = mean32 + (size_t)Cs * nimg;
+    QFCA_LAUNCH("k_prep_f32", st,
+                k_prep_f32<<<dim3((C * DT + 255) / 256, nimg), 256, 0, st>>>(mean, V, C, d, DT, Cs, mean32, V32));
+    const long tiles = (N + kPix - 1) / kPix;
+    const unsigned grid = (unsigned)(tiles * nimg);
     switch (DT) {
-        case 16: QFCA_LAUNCH("k_project_f32", st, k_project_f32<16><<<grid, kPix, 0, st>>>(X, layout, C, N, mean32, V32, d, Y, mm_keys)); break;
-        case 32: QFCA_LAUNCH("k_project_f32", st, k_project_f32<32><<<grid, kPix, 0, st>>>(X, layout, C, N, mean32, V32, d, Y, mm_keys)); break;
-        default: QFCA_LAUNCH("k_project_f32", st, k_project_f32<64><<<grid, kPix, 0, st>>>(X, layout, C, N, mean32, V32, d, Y, mm_keys)); break;
+        case 16:
+            QFCA_LAUNCH("k_project_f32", st,
+                        k_project_f32<16><<<grid, kPix, 0, st>>>(X, layout, C, N, mean32, V32, d, Cs, tiles, Y, mm_keys));
+            break;
+        case 32:
+            QFCA_LAUNCH("k_project_f32", st,
+                        k_project_f32<32><<<grid, kPix, 0, st>>>(X, layout, C, N, mean32, V32, d, Cs, tiles, Y, mm_keys));
+            break;
+        default:
+            QFCA_LAUNCH("k_project_f32", st,
+                        k_project_f32<64><<<grid, kPix, 0, st>>>(X, layout, C, N, mean32, V32, d, Cs, tiles, Y, mm_keys));
+            break;
     }
     return cudaGetLastError();
 }

@@ -49,9 +49,14 @@ TcShape tc_shape(int C, int d) {
     return s;
 }
 
-// mean32[c] (c < Cp, zero padded) and Vt[j][c] = bf16(V[c][j]) (DT x Cp, zero padded).
+// Per image (grid.y): mean32[c] (c < Cp, zero padded) and Vt[j][c] = bf16(V[c][j]) (DT x Cp, zero padded).
 __global__ void k_prep_bf16(const double *__restrict__ mean, const double *__restrict__ V, int C, int d, int Cp,
                             int DT, float *__restrict__ mean32, __nv_bfloat16 *__restrict__ Vt) {
+    const long img = blockIdx.y;
+    mean += img * C;
+    V += img * C * d;
+    mean32 += img * Cp;
+    Vt += img * DT * Cp;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < DT * Cp; e += gridDim.x * blockDim.x) {
         const int j = e / Cp, c = e % Cp;
         const float v = (j < d && c < C) ? (float)V[(long)c * d + j] : 0.0f;
@@ -70,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) k_project_bf16(const float *__restri
                                                           long N, const float *__restrict__ mean32,
                                                           const __nv_bfloat16 *__restrict__ Vt, int d,
                                                           float *__restrict__ Y, uint32_t *__restrict__ mm_keys,
-                                                          int *__restrict__ status, long n_tiles) {
+                                                          int *__restrict__ status, long tiles_per_img, int nimg) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int nk = Cp / kKc;
@@ -92,14 +97,6 @@ __global__ void __launch_bounds__(kThreads) k_project_bf16(const float *__restri
         tc::fence_mbar_init();
     }
     if (tid < DT) { kmin[tid] = 0xffffffffu; kmax[tid] = 0u; }
-    // resident Bt: DT rows x Cp channels, 16-B chunks of 8 channels
-    for (int e = tid; e < DT * (Cp / 8); e += kThreads) {
-        const int j = e / (Cp / 8), c8 = e % (Cp / 8);
-        const int kc = c8 >> 3, g = c8 & 7;
-        const uint4 v = *reinterpret_cast<const uint4 *>(Vt + (long)j * Cp + c8 * 8);
-        *reinterpret_cast<uint4 *>(Bs + (size_t)kc * DT * 128 + swz_off(j, g)) = v;
-    }
-    tc::fence_proxy_async_smem();
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -108,9 +105,35 @@ __global__ void __launch_bounds__(kThreads) k_project_bf16(const float *__restri
     const uint32_t a_base = tc::smem_u32(As), b_base = tc::smem_u32(Bs);
     uint32_t phase = 0;
     bool failed = false;
+    int cur = -1;  // image whose Bt is resident and whose min/max kmin/kmax hold
+    const long n_tiles = tiles_per_img * nimg;
 
     for (long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const long p0 = tile * kM;
+        const int img = (int)(tile / tiles_per_img);
+        if (img != cur) {
+            if (cur >= 0) {  // flush the previous image's min/max, then reset
+                __syncthreads();
+                if (tid < d) {
+                    atomicMin(&mm_keys[((long)cur * 2 * d + tid) * kKeyStride], kmin[tid]);
+                    atomicMax(&mm_keys[((long)cur * 2 * d + d + tid) * kKeyStride], kmax[tid]);
+                }
+                __syncthreads();
+                if (tid < DT) { kmin[tid] = 0xffffffffu; kmax[tid] = 0u; }
+            }
+            // resident Bt of this image: DT rows x Cp channels, 16-B chunks of 8 channels
+            // (the MMAs that read the previous Bt completed before the last epilogue)
+            const __nv_bfloat16 *Vi = Vt + (long)img * DT * Cp;
+            for (int e = tid; e < DT * (Cp / 8); e += kThreads) {
+                const int j = e / (Cp / 8), c8 = e % (Cp / 8);
+                const int kc = c8 >> 3, g = c8 & 7;
+                const uint4 v = *reinterpret_cast<const uint4 *>(Vi + (long)j * Cp + c8 * 8);
+                *reinterpret_cast<uint4 *>(Bs + (size_t)kc * DT * 128 + swz_off(j, g)) = v;
+            }
+            cur = img;
+        }
+        const float *Xi = X + (long)img * C * N;
+        const float *mui = mean32 + (long)img * Cp;
+        const long p0 = (tile - (long)img * tiles_per_img) * kM;
         const int m = tid;
         const long p = p0 + m;
         const bool pv = p < N;
@@ -121,19 +144,19 @@ __global__ void __launch_bounds__(kThreads) k_project_bf16(const float *__restri
 #pragma unroll
                 for (int i = 0; i < kKc; i++) {
                     const int c = kc * kKc + i;
-                    v[i] = (pv && c < C) ? __ldg(X + (long)c * N + p) : 0.0f;
+                    v[i] = (pv && c < C) ? __ldg(Xi + (long)c * N + p) : 0.0f;
                 }
             } else {
 #pragma unroll
                 for (int i = 0; i < kKc; i++) {
                     const int c = kc * kKc + i;
-                    v[i] = (pv && c < C) ? __ldg(X + p * C + c) : 0.0f;
+                    v[i] = (pv && c < C) ? __ldg(Xi + p * C + c) : 0.0f;
                 }
             }
 #pragma unroll
             for (int g = 0; g < 8; g++) {
                 uint4 pk;
-                const float *mu = mean32 + kc * kKc + g * 8;
+                const float *mu = mui + kc * kKc + g * 8;
                 pk.x = tc::pack_bf16x2(v[g * 8 + 0] - mu[0], v[g * 8 + 1] - mu[1]);
                 pk.y = tc::pack_bf16x2(v[g * 8 + 2] - mu[2], v[g * 8 + 3] - mu[3]);
                 pk.z = tc::pack_bf16x2(v[g * 8 + 4] - mu[4], v[g * 8 + 5] - mu[5]);
@@ -175,10 +198,11 @@ __global__ void __launch_bounds__(kThreads) k_project_bf16(const float *__restri
         }
         const long pe = p0 + 32 * warp + lane;
         const bool valid = pe < N;
+        float *Yi = Y + (long)img * d * N;
 #pragma unroll
         for (int j = 0; j < DT; j++) {
             if (j >= d) break;
-            if (valid) Y[(long)j * N + pe] = acc[j];
+            if (valid) Yi[(long)j * N + pe] = acc[j];
             float mn = valid ? acc[j] : __int_as_float(0x7f800000);
             float mx = valid ? acc[j] : -__int_as_float(0x7f800000);
 #pragma unroll
@@ -203,14 +227,14 @@ __global__ void __launch_bounds__(kThreads) k_project_bf16(const float *__restri
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem, kCols);
     }
-    if (!failed && tid < d) {
-        atomicMin(&mm_keys[tid * kKeyStride], kmin[tid]);
-        atomicMax(&mm_keys[(d + tid) * kKeyStride], kmax[tid]);
+    if (!failed && cur >= 0 && tid < d) {
+        atomicMin(&mm_keys[((long)cur * 2 * d + tid) * kKeyStride], kmin[tid]);
+        atomicMax(&mm_keys[((long)cur * 2 * d + d + tid) * kKeyStride], kmax[tid]);
     }
 }
 
 template <int DT>
-cudaError_t launch_dt(const float *X, int layout, int C, const TcShape &sh, long N, const float *mean32,
+cudaError_t launch_dt(const float *X, int layout, int C, const TcShape &sh, long N, int nimg, const float *mean32,
                       const __nv_bfloat16 *Vt, int d, float *Y, uint32_t *mm_keys, int *status, cudaStream_t st) {
     static int attr_dev = -1;
     static int max_blocks = 0;
@@ -231,36 +255,39 @@ cudaError_t launch_dt(const float *X, int layout, int C, const TcShape &sh, long
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (per_sm < 1) return cudaErrorNotSupported;
     max_blocks = per_sm * sms;
-    const long n_tiles = (N + kM - 1) / kM;
+    const long tiles = (N + kM - 1) / kM;
+    const long n_tiles = tiles * nimg;
     const int grid = (int)(n_tiles < max_blocks ? n_tiles : max_blocks);
     QFCA_LAUNCH("k_project_bf16", st,
                 k_project_bf16<DT><<<grid, kThreads, sh.smem, st>>>(X, layout, C, sh.Cp, N, mean32, Vt, d, Y,
-                                                                    mm_keys, status, n_tiles));
+                                                                    mm_keys, status, tiles, nimg));
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t project_bf16_workspace_bytes(int C, long N, int d) {
+size_t project_bf16_workspace_bytes(int C, long N, int d, int nimg) {
     (void)N;
     const TcShape s = tc_shape(C, d);
-    return align_up(sizeof(float) * s.Cp, 256) + align_up(sizeof(__nv_bfloat16) * (size_t)s.DT * s.Cp, 256) + 256;
+    return align_up(sizeof(float) * s.Cp * nimg, 256) + align_up(sizeof(__nv_bfloat16) * (size_t)s.DT * s.Cp * nimg, 256) +
+           256;
 }
 
 cudaError_t launch_project_bf16(const float *X, int layout, int H, int W, int C, const double *mean,
-                                const double *V, int d, float *Y, uint32_t *mm_keys, void *ws, int *status,
-                                cudaStream_t st) {
+                                const double *V, int d, int nimg, float *Y, uint32_t *mm_keys, void *ws,
+                                int *status, cudaStream_t st) {
     const long N = (long)H * W;
     const TcShape sh = tc_shape(C, d);
     if (sh.smem > 227 * 1024) return cudaErrorNotSupported;
     float *mean32 = (float *)ws;
-    __nv_bfloat16 *Vt = (__nv_bfloat16 *)((char *)ws + align_up(sizeof(float) * sh.Cp, 256));
+    __nv_bfloat16 *Vt = (__nv_bfloat16 *)((char *)ws + align_up(sizeof(float) * sh.Cp * nimg, 256));
     QFCA_LAUNCH("k_prep_bf16", st,
-                k_prep_bf16<<<(sh.DT * sh.Cp + 255) / 256, 256, 0, st>>>(mean, V, C, d, sh.Cp, sh.DT, mean32, Vt));
+                k_prep_bf16<<<dim3((sh.DT * sh.Cp + 255) / 256, nimg), 256, 0, st>>>(mean, V, C, d, sh.Cp, sh.DT,
+                                                                                     mean32, Vt));
     switch (sh.DT) {
-        case 16: return launch_dt<16>(X, layout, C, sh, N, mean32, Vt, d, Y, mm_keys, status, st);
-        case 32: return launch_dt<32>(X, layout, C, sh, N, mean32, Vt, d, Y, mm_keys, status, st);
-        default: return launch_dt<64>(X, layout, C, sh, N, mean32, Vt, d, Y, mm_keys, status, st);
+        case 16: return launch_dt<16>(X, layout, C, sh, N, nimg, mean32, Vt, d, Y, mm_keys, status, st);
+        case 32: return launch_dt<32>(X, layout, C, sh, N, nimg, mean32, Vt, d, Y, mm_keys, status, st);
+        default: return launch_dt<64>(X, layout, C, sh, N, nimg, mean32, Vt, d, Y, mm_keys, status, st);
     }
 }
 

@@ -26,6 +26,7 @@ __device__ __forceinline__ int bin_of(float y, float lo, float hi, float fB, int
     return q > B - 1 ? B - 1 : q;
 }
 
+// Grid (row bands, d, images).
 __global__ void __launch_bounds__(kThreads) k_quantize(const float *__restrict__ Y, long N, int H, int W, int d,
                                                        int B, int range_mode, const uint32_t *__restrict__ mm_keys,
                                                        const float *__restrict__ lo_in,
@@ -34,6 +35,13 @@ __global__ void __launch_bounds__(kThreads) k_quantize(const float *__restrict__
                                                        float *__restrict__ hi_out, uint32_t *__restrict__ hist) {
     __shared__ uint32_t sh[256];
     const int k = blockIdx.y;
+    const long img = blockIdx.z;
+    Y += img * d * N;
+    mm_keys += img * 2 * d * kKeyStride;
+    bins += img * d * H * (long)pitch;
+    if (lo_out) lo_out += img * d;
+    if (hi_out) hi_out += img * d;
+    if (hist) hist += img * d * B;
     float lo, hi;
     if (range_mode == QFCA_RANGE_IMAGE) {
         lo = key2f(mm_keys[k * kKeyStride]);
@@ -68,14 +76,14 @@ __global__ void __launch_bounds__(kThreads) k_quantize(const float *__restrict__
 
 }  // namespace
 
-cudaError_t launch_quantize(const float *Y, long N, int H, int W, int d, int B, int range_mode,
+cudaError_t launch_quantize(const float *Y, long N, int H, int W, int d, int nimg, int B, int range_mode,
                             const uint32_t *mm_keys, const float *lo_in, const float *hi_in, uint8_t *bins,
                             int pitch, float *lo_out, float *hi_out, uint32_t *hist, cudaStream_t st) {
     if (hist) {
-        cudaError_t err = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * d * B, st);
+        cudaError_t err = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)d * B * nimg, st);
         if (err != cudaSuccess) return err;
     }
-    dim3 grid((H + kRowsPerCta - 1) / kRowsPerCta, d);
+    dim3 grid((H + kRowsPerCta - 1) / kRowsPerCta, d, nimg);
     QFCA_LAUNCH("k_quantize", st,
                 k_quantize<<<grid, kThreads, 0, st>>>(Y, N, H, W, d, B, range_mode, mm_keys, lo_in, hi_in, bins,
                                                       pitch, lo_out, hi_out, hist));

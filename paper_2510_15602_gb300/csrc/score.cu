@@ -32,13 +32,13 @@ struct ScoreGeom {
     size_t smem;
 };
 
-ScoreGeom score_geom(int H, int W, int d, int B, int r) {
+ScoreGeom score_geom(int H, int W, int d, int B, int r, int nimg) {
     ScoreGeom g;
     g.TH = kTH;
     g.TR = g.TH + 2 * r;
     g.TC = kSW + 2 * r;
     g.TCp = (int)align_up(g.TC, 16);
-    const long tiles = (long)((W + kSW - 1) / kSW) * ((H + g.TH - 1) / g.TH);
+    const long tiles = (long)((W + kSW - 1) / kSW) * ((H + g.TH - 1) / g.TH) * nimg;
     // enough CTAs for ~4 per SM over 152 SMs
     int n_kg = (int)((4 * 152 + tiles - 1) / tiles);
     if (n_kg < 1) n_kg = 1;
@@ -73,7 +73,12 @@ __global__ void __launch_bounds__(kSW) k_window_emd(const uint8_t *__restrict__ 
 
     const int t = threadIdx.x;
     const int x0 = blockIdx.x * kSW, y0 = blockIdx.y * g.TH;
-    const int k0 = blockIdx.z * g.kg, k1 = min(d, k0 + g.kg);
+    const long img = blockIdx.z / g.n_kg;
+    const int k0 = (blockIdx.z % g.n_kg) * g.kg, k1 = min(d, k0 + g.kg);
+    bins += img * d * H * (long)pitch;
+    ref_hist += img * d * B;
+    acc += img * H * (long)W;
+    if (numer) numer += img * d * H * (long)W;
     const int x = x0 + t;
     const int ty0 = y0 - r, tx0 = x0 - r;  // image coordinates of the tile origin
     const uint32_t Nint = (uint32_t)((2 * r + 1) * (2 * r + 1));
@@ -155,10 +160,13 @@ __global__ void __launch_bounds__(kSW) k_window_emd(const uint8_t *__restrict__ 
         }
 }
 
+// Grid (pixels, images).
 __global__ void k_finalize(const unsigned long long *__restrict__ acc, int H, int W, int r, int d, uint32_t Nref,
                            float *__restrict__ score) {
     const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= (long)H * W) return;
+    acc += (long)blockIdx.y * H * W;
+    score += (long)blockIdx.y * H * W;
     const int y = (int)(p / W), x = (int)(p - (long)y * W);
     const int nr = min(H - 1, y + r) - max(0, y - r) + 1;
     const int nc = min(W - 1, x + r) - max(0, x - r) + 1;
@@ -168,16 +176,18 @@ __global__ void k_finalize(const unsigned long long *__restrict__ acc, int H, in
 
 }  // namespace
 
-size_t score_workspace_bytes(int H, int W) { return align_up(sizeof(unsigned long long) * (size_t)H * W, 256); }
+size_t score_workspace_bytes(int H, int W, int nimg) {
+    return align_up(sizeof(unsigned long long) * (size_t)H * W * nimg, 256);
+}
 
-cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d, int B, int r,
+cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d, int nimg, int B, int r,
                             const uint32_t *ref_hist, uint32_t ref_total, float *score, uint64_t *numer,
                             void *ws, cudaStream_t st) {
-    const ScoreGeom g = score_geom(H, W, d, B, r);
+    const ScoreGeom g = score_geom(H, W, d, B, r, nimg);
     if (g.smem > 200 * 1024) return cudaErrorNotSupported;  // nothing enqueued
     unsigned long long *acc = (unsigned long long *)ws;
     cudaError_t err = cudaSuccess;
-    if (g.n_kg > 1) err = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (size_t)H * W, st);
+    if (g.n_kg > 1) err = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (size_t)H * W * nimg, st);
     if (err != cudaSuccess) return err;
     // u32 walk when every partial and the numerator fit: (B-1) (2r+1)^2 N_ref < 2^32
     const double bound = (double)(B - 1) * (double)((2 * r + 1) * (2 * r + 1)) * (double)ref_total;
@@ -193,7 +203,7 @@ cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d,
         if (err != cudaSuccess) return err;
         attr_dev = dev;
     }
-    dim3 grid((W + kSW - 1) / kSW, (H + g.TH - 1) / g.TH, g.n_kg);
+    dim3 grid((W + kSW - 1) / kSW, (H + g.TH - 1) / g.TH, g.n_kg * nimg);
     if (narrow)
         QFCA_LAUNCH("k_window_emd", st,
                     k_window_emd<uint32_t><<<grid, kSW, g.smem, st>>>(bins, H, W, pitch, d, B, r, g, ref_hist,
@@ -203,7 +213,8 @@ cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d,
                     k_window_emd<unsigned long long><<<grid, kSW, g.smem, st>>>(bins, H, W, pitch, d, B, r, g,
                                                                                  ref_hist, ref_total, acc, numer));
     const long N = (long)H * W;
-    QFCA_LAUNCH("k_finalize", st, k_finalize<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(acc, H, W, r, d, ref_total, score));
+    QFCA_LAUNCH("k_finalize", st,
+                k_finalize<<<dim3((unsigned)((N + 255) / 256), nimg), 256, 0, st>>>(acc, H, W, r, d, ref_total, score));
     return cudaGetLastError();
 }
 
@@ -253,7 +264,7 @@ extern "C" qfca_status qfca_score_noalloc(const uint8_t *bins, int H, int W, int
         }
         acc = g_noalloc_ptr[dev];
     }
-    const cudaError_t e = launch_score_ws(bins, H, W, pitch, d, B, r, ref_hist, ref_total, score, nullptr, acc,
+    const cudaError_t e = launch_score_ws(bins, H, W, pitch, d, 1, B, r, ref_hist, ref_total, score, nullptr, acc,
                                           (cudaStream_t)stream);
     if (e == cudaErrorNotSupported) return QFCA_ERR_UNSUPPORTED;
     if (e != cudaSuccess) {

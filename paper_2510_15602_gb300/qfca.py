@@ -77,6 +77,16 @@ _lib.qfca_trace_get.argtypes = [_P, _I, ctypes.c_char_p, ctypes.POINTER(ctypes.c
 _lib.qfca_trace_get.restype = _I
 
 
+class BatchOutputs(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_void_p), ("V", ctypes.c_void_p), ("eigvals", ctypes.c_void_p),
+                ("bins", ctypes.c_void_p), ("pitch", ctypes.c_int), ("ref_hist", ctypes.c_void_p),
+                ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p)]
+
+
+_lib.qfca_batch_run.argtypes = [_P, _P, _I, Fmap, _I, _I, _I, _I, _P, ctypes.POINTER(BatchOutputs), _P]
+_lib.qfca_batch_run.restype = _I
+
+
 class QfcaError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{_lib.qfca_status_string(status).decode()}: {msg}")
@@ -275,6 +285,41 @@ def score(bins: torch.Tensor, W: int, B: int, r: int, ref_hist: torch.Tensor, re
     ctx.check(_lib.qfca_score(ctx.handle, _ptr(bins), H, W, pitch, d, B, r, _ptr(ref_hist), int(ref_total),
                               _ptr(s), _ptr(numer), _P(_stream_ptr(stream))))
     return (s, numer) if want_numer else s
+
+
+def batch_run(X: torch.Tensor, d: int, B: int, r: int, precision="bf16", ctx: Context | None = None, stream=None,
+              scores: torch.Tensor | None = None, extras: bool = False):
+    """qfca_batch_run: the whole path for a batch X [nimg, C, H, W] (NCHW maps).
+
+    Returns scores [nimg, H, W] (f32), or (scores, dict of per-image mean, V,
+    eigvals, bins, ref_hist, lo, hi) when ``extras`` is set.
+    """
+    _check_dev(X, "X", torch.float32)
+    if X.dim() != 4:
+        raise ValueError("X must be [nimg, C, H, W]")
+    nimg, C, H, W = (int(v) for v in X.shape)
+    ctx = ctx or default_context(X.device.index)
+    dev = X.device
+    if scores is None:
+        scores = torch.empty(nimg, H, W, dtype=torch.float32, device=dev)
+    ext = None
+    ex = None
+    if extras:
+        pitch = bins_pitch(W)
+        ex = dict(mean=torch.empty(nimg, C, dtype=torch.float64, device=dev),
+                  V=torch.empty(nimg, C, d, dtype=torch.float64, device=dev),
+                  eigvals=torch.empty(nimg, d, dtype=torch.float64, device=dev),
+                  bins=torch.empty(nimg, d, H, pitch, dtype=torch.uint8, device=dev),
+                  ref_hist=torch.empty(nimg, d, B, dtype=torch.int32, device=dev),
+                  lo=torch.empty(nimg, d, dtype=torch.float32, device=dev),
+                  hi=torch.empty(nimg, d, dtype=torch.float32, device=dev))
+        ext = BatchOutputs(ex["mean"].data_ptr(), ex["V"].data_ptr(), ex["eigvals"].data_ptr(),
+                           ex["bins"].data_ptr(), pitch, ex["ref_hist"].data_ptr(), ex["lo"].data_ptr(),
+                           ex["hi"].data_ptr())
+    fm = Fmap(H, W, C, NCHW)
+    ctx.check(_lib.qfca_batch_run(ctx.handle, _ptr(X), nimg, fm, d, B, r, _PREC[precision], _ptr(scores),
+                                  ctypes.byref(ext) if ext is not None else None, _P(_stream_ptr(stream))))
+    return (scores, ex) if extras else scores
 
 
 def run_image(X: torch.Tensor, d: int, B: int, r: int, precision="f32", layout: int = NCHW,

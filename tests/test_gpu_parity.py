@@ -321,3 +321,41 @@ def test_device_status_clean_after_bf16(q):
     mean, V, _, _ = oracle.fit(img.X, 16)
     q.quantize(to_dev(img.X), (to_dev(mean), to_dev(V)), 16, "bf16", ctx=ctx)
     assert ctx.device_status() == 0
+
+
+# ------------------------------------------------------------------ batched entry point
+
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+def test_batch_run_equals_single_image_calls(q, precision):
+    # every stage of qfca_batch_run shares one grid across the batch; the
+    # results must equal per-image calls bit for bit (integer stages are exact
+    # and order-independent, the floating stages use the same per-image order)
+    C, H, W, d, B, r, n = 64, 48, 40, 16, 16, 4, 3
+    imgs = [synth.small_case(C=C, H=H, W=W, sigma=2.0, seed=50 + i, n_square=1, side=8, nch=6) for i in range(n)]
+    Xb = to_dev(np.stack([im.X for im in imgs]))
+    sb, ex = q.batch_run(Xb, d, B, r, precision, extras=True)
+    torch.cuda.synchronize()
+    for i in range(n):
+        basis = q.fit_pca(Xb[i], d)
+        out = q.quantize(Xb[i], basis, B, precision)
+        s1 = q.score(out["bins"], W, B, r, out["hist"], H * W)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ex["eigvals"][i].cpu().numpy(), basis[2].cpu().numpy())
+        np.testing.assert_array_equal(ex["V"][i].cpu().numpy(), basis[1].cpu().numpy())
+        np.testing.assert_array_equal(ex["bins"][i][:, :, :W].cpu().numpy(), out["bins"][:, :, :W].cpu().numpy())
+        np.testing.assert_array_equal(sb[i].cpu().numpy(), s1.cpu().numpy())
+
+
+def test_batch_run_full_size_against_oracle_integer_stages(q):
+    # two images of the 256^2 x C256 workload through the batch path; integer
+    # stages of each image checked bit-exactly against the oracle on the GPU bins
+    imgs = [synth.make_image("batch16_256_c256", i) for i in range(2)]
+    Xb = to_dev(np.stack([im.X for im in imgs]))
+    sb, ex = q.batch_run(Xb, 32, 32, 7, "bf16", extras=True)
+    torch.cuda.synchronize()
+    for i in range(2):
+        qb = ex["bins"][i][:, :, :256].cpu().numpy()
+        R = oracle.ref_hist(qb, 32)
+        np.testing.assert_array_equal(ex["ref_hist"][i].cpu().numpy().astype(np.uint32), R)
+        s_o, _, _ = oracle.score(qb, 32, 7, R, 256 * 256)
+        np.testing.assert_allclose(sb[i].cpu().numpy(), s_o, rtol=2.0 ** -23, atol=1e-12)
