@@ -257,65 +257,6 @@ def run_reference(args):
 # ------------------------------------------------------------------ our arm
 
 
-class Runner:
-    """Holds device inputs/outputs and runs the whole path over the batch."""
-
-    def __init__(self, X_dev, precision, n_streams, q, torch):
-        self.q, self.torch = q, torch
-        self.X = X_dev
-        self.precision = precision
-        self.n = len(X_dev)
-        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
-        self.ctxs = [q.Context() for _ in range(n_streams)]
-        dev = X_dev[0].device
-        pitch = q.bins_pitch(HW)
-        self.out = []
-        for _ in range(self.n):
-            self.out.append(dict(
-                mean=torch.empty(C, dtype=torch.float64, device=dev),
-                V=torch.empty(C, D, dtype=torch.float64, device=dev),
-                ev=torch.empty(D, dtype=torch.float64, device=dev),
-                bins=torch.empty(D, HW, pitch, dtype=torch.uint8, device=dev),
-                lo=torch.empty(D, dtype=torch.float32, device=dev),
-                hi=torch.empty(D, dtype=torch.float32, device=dev),
-                hist=torch.empty(D, B, dtype=torch.int32, device=dev),
-                score=torch.empty(HW, HW, dtype=torch.float32, device=dev)))
-
-    def image(self, i, stream, ctx, precision=None):
-        q, o = self.q, self.out[i]
-        prec = precision or self.precision
-        q.fit_pca(self.X[i], D, ctx=ctx, stream=stream, out=(o["mean"], o["V"], o["ev"]))
-        q.quantize(self.X[i], (o["mean"], o["V"]), B, prec, ctx=ctx, stream=stream,
-                   out=(o["bins"], o["lo"], o["hi"], o["hist"], None))
-        q.score(o["bins"], HW, B, R, o["hist"], HW * HW, ctx=ctx, stream=stream, out=o["score"])
-
-    def step(self, main, pre=None, post=None):
-        """Whole batch; side streams fork from and join into `main`."""
-        torch = self.torch
-        fork = torch.cuda.Event()
-        fork.record(main)
-        joins = []
-        for s in self.streams:
-            s.wait_event(fork)
-        for i in range(self.n):
-            k = i % len(self.streams)
-            st = self.streams[k]
-            if pre is not None:
-                pre(i, st)
-            self.image(i, st, self.ctxs[k])
-            if post is not None:
-                post(i, st)
-        for s in self.streams:
-            e = torch.cuda.Event()
-            e.record(s)
-            joins.append(e)
-        for e in joins:
-            main.wait_event(e)
-
-    def launches(self):
-        return sum(c.launch_count() for c in self.ctxs)
-
-
 def timed(torch, main, fn, steps):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -323,13 +264,63 @@ def timed(torch, main, fn, steps):
     barrier()
     e0.record(main)
     t0 = time.perf_counter()
-    for _ in range(steps):
-        fn()
+    for i in range(steps):
+        fn(i)
     e1.record(main)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     barrier()
     return e0.elapsed_time(e1) / 1e3, wall
+
+
+class BatchPipe:
+    """Two contexts on two streams; step i runs the whole path over the batch on
+    pipe i % 2 (a captured CUDA graph of one qfca_batch_run), so consecutive
+    steps overlap on the device.  Steps fork from and join into `main`."""
+
+    def __init__(self, q, torch, X, precision, use_graph=True):
+        self.q, self.torch, self.X = q, torch, X
+        self.precision = precision
+        nimg, C, H, W = X.shape
+        self.ctx = [q.Context(), q.Context()]
+        self.st = [torch.cuda.Stream(), torch.cuda.Stream()]
+        self.scores = [torch.empty(nimg, H, W, dtype=torch.float32, device=X.device) for _ in range(2)]
+        self.graphs = None
+        self.use_graph = use_graph
+
+    def run_direct(self, k):
+        self.q.batch_run(self.X, D, B, R, self.precision, ctx=self.ctx[k], stream=self.st[k], scores=self.scores[k])
+
+    def capture(self):
+        torch = self.torch
+        self.graphs = []
+        for k in range(2):
+            g = torch.cuda.CUDAGraph()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=self.st[k]):
+                self.run_direct(k)
+            self.graphs.append(g)
+        torch.cuda.synchronize()
+
+    def step(self, i, main, pre=None, post=None):
+        torch = self.torch
+        k = i % 2
+        st = self.st[k]
+        ev = torch.cuda.Event()
+        ev.record(main)
+        st.wait_event(ev)
+        with torch.cuda.stream(st):
+            if pre is not None:
+                pre(st)
+            if self.graphs is not None:
+                self.graphs[k].replay()
+            else:
+                self.run_direct(k)
+            if post is not None:
+                post(st, self.scores[k])
+        done = torch.cuda.Event()
+        done.record(st)
+        main.wait_event(done)
 
 
 def run_ours(args):
@@ -346,104 +337,118 @@ def run_ours(args):
     from paper_2510_15602_gb300.metrics import auroc
     main = torch.cuda.current_stream()
 
-    X_pin = [torch.from_numpy(x).pin_memory() for x, _ in host]
-    X_dev = [x.cuda() for x in X_pin]
+    X_pin = torch.from_numpy(np.stack([x for x, _ in host])).pin_memory()  # [16, C, H, W]
+    X_dev = X_pin.cuda()
     masks = [m for _, m in host]
-    run = Runner(X_dev, args.precision, args.streams, qfca, torch)
+    pipe = BatchPipe(qfca, torch, X_dev, args.precision)
 
-    # ---- warm-up (also grows the context workspaces once)
-    for _ in range(args.warmup):
-        run.step(main)
+    # ---- warm-up (grows both context workspaces, sets kernel attributes)
+    for i in range(args.warmup):
+        pipe.step(i, main)
     torch.cuda.synchronize()
 
-    # ---- which kernel dominates: one traced step over all kernels
-    for c in run.ctxs:
-        c.trace_start("")
-    run.step(main)
+    # ---- which kernel dominates: one traced direct step over all kernels
+    pipe.ctx[0].trace_start("")
+    pipe.step(0, main)
     torch.cuda.synchronize()
-    agg = {}
-    for c in run.ctxs:
-        for k, (ms, n) in c.trace().items():
-            a = agg.setdefault(k, [0.0, 0])
-            a[0] += ms
-            a[1] += n
-        c.trace_stop()
+    agg = {k: list(v) for k, v in pipe.ctx[0].trace().items()}
+    pipe.ctx[0].trace_stop()
     dominant = max(agg, key=lambda k: agg[k][0])
+    n0 = pipe.ctx[0].launch_count()
+    pipe.step(0, main)
+    torch.cuda.synchronize()
+    launches_per_step = pipe.ctx[0].launch_count() - n0
 
-    # ---- timed region: the dominant kernel bracketed by events on its own stream
-    for c in run.ctxs:
+    # ---- graphs (the dominant kernel's events are captured as graph nodes)
+    for c in pipe.ctx:
         c.trace_start(dominant)
+    if not args.no_graph:
+        pipe.capture()
+        for i in range(2):
+            pipe.step(i, main)
+        torch.cuda.synchronize()
+
+    # ---- timed region
     sampler = ClockSampler(gpu_id_for_smi(local))
     sampler.start()
-    n0 = run.launches()
-    dev_s, wall_s = timed(torch, main, lambda: run.step(main), args.steps)
-    n1 = run.launches()
+    dev_s, wall_s = timed(torch, main, lambda i: pipe.step(i, main), args.steps)
     clocks = sampler.stop()
     dom_ms, dom_n = 0.0, 0
-    for c in run.ctxs:
+    for c in pipe.ctx:
         t = c.trace()
         if dominant in t:
             dom_ms += t[dominant][0]
             dom_n += t[dominant][1]
         c.trace_stop()
     t_max = max_over_ranks(dev_s)
-    total_maps = N_IMG * ws * args.steps
-    value = total_maps / t_max
-    launches = n1 - n0
+    value = N_IMG * ws * args.steps / t_max
 
-    # ---- end to end through the public API with host buffers
-    score_pin = [torch.empty(HW, HW, dtype=torch.float32).pin_memory() for _ in range(N_IMG)]
+    # ---- end to end through the public API with host buffers (H2D of the batch, D2H of the maps)
+    score_pin = [torch.empty(N_IMG, HW, HW, dtype=torch.float32).pin_memory() for _ in range(2)]
 
-    def pre(i, st):
-        with torch.cuda.stream(st):
-            X_dev[i].copy_(X_pin[i], non_blocking=True)
+    def pre(st):
+        X_dev.copy_(X_pin, non_blocking=True)
 
-    def post(i, st):
-        with torch.cuda.stream(st):
-            score_pin[i].copy_(run.out[i]["score"], non_blocking=True)
+    def post_factory(i):
+        def post(st, scores):
+            score_pin[i % 2].copy_(scores, non_blocking=True)
+        return post
 
-    e2e_steps = max(1, args.steps // 2)
-    run.step(main, pre, post)
-    torch.cuda.synchronize()
-    e2e_dev, e2e_wall = timed(torch, main, lambda: run.step(main, pre, post), e2e_steps)
+    e2e_steps = max(2, args.steps // 2)
+    e2e_dev, e2e_wall = timed(torch, main, lambda i: pipe.step(i, main, pre, post_factory(i)), e2e_steps)
     e2e_t = max_over_ranks(max(e2e_dev, e2e_wall))
     e2e_value = N_IMG * ws * e2e_steps / e2e_t
-    h2d = sum(x.numel() * 4 for x in X_pin)
+    h2d = X_pin.numel() * 4
     d2h = N_IMG * HW * HW * 4
 
     # ---- plain FP32 single-image path (one stream, one image at a time)
     fp32 = None
     if not args.skip_fp32:
-        ctx1 = run.ctxs[0]
+        ctx1 = pipe.ctx[0]
+        outs = []
+        for i in range(N_IMG):
+            outs.append(dict(mean=torch.empty(C, dtype=torch.float64, device="cuda"),
+                             V=torch.empty(C, D, dtype=torch.float64, device="cuda"),
+                             ev=torch.empty(D, dtype=torch.float64, device="cuda"),
+                             bins=torch.empty(D, HW, qfca.bins_pitch(HW), dtype=torch.uint8, device="cuda"),
+                             lo=torch.empty(D, dtype=torch.float32, device="cuda"),
+                             hi=torch.empty(D, dtype=torch.float32, device="cuda"),
+                             hist=torch.empty(D, B, dtype=torch.int32, device="cuda"),
+                             score=torch.empty(HW, HW, dtype=torch.float32, device="cuda")))
 
-        def single_fp32():
+        def single_fp32(_i):
             for i in range(N_IMG):
-                run.image(i, main, ctx1, precision="f32")
+                o = outs[i]
+                qfca.fit_pca(X_dev[i], D, ctx=ctx1, stream=main, out=(o["mean"], o["V"], o["ev"]))
+                qfca.quantize(X_dev[i], (o["mean"], o["V"]), B, "f32", ctx=ctx1, stream=main,
+                              out=(o["bins"], o["lo"], o["hi"], o["hist"], None))
+                qfca.score(o["bins"], HW, B, R, o["hist"], HW * HW, ctx=ctx1, stream=main, out=o["score"])
 
-        single_fp32()
-        fs, _ = timed(torch, main, single_fp32, max(1, args.steps // 2))
+        single_fp32(0)
+        fs, _ = timed(torch, main, single_fp32, max(1, args.steps // 4))
         fs = max_over_ranks(fs)
-        fp32 = {"value": round(N_IMG * ws * max(1, args.steps // 2) / fs, 3), "unit": "maps/s",
-                "path": "FP32 projection, one image per launch sequence, one stream"}
+        fp32 = {"value": round(N_IMG * ws * max(1, args.steps // 4) / fs, 3), "unit": "maps/s",
+                "path": "FP32 projection, one image per call sequence (fit, quantize, score), one stream"}
 
-    # ---- quality: pixel AUROC of the GPU maps against the planted masks
-    run.step(main)
-    torch.cuda.synchronize()
-    scores = [run.out[i]["score"].cpu().numpy() for i in range(N_IMG)]
-    aurocs = [auroc(scores[i], masks[i]) for i in range(N_IMG)]
-    auroc_mean = float(np.nanmean(aurocs))
-
-    # per-image latency on an idle GPU (single stream)
+    # ---- single-image latency on an idle GPU (batch of one through the batched entry point)
     lat = []
+    s1 = torch.empty(1, HW, HW, dtype=torch.float32, device="cuda")
     for i in range(N_IMG):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(main)
-        run.image(i, main, run.ctxs[0])
+        qfca.batch_run(X_dev[i:i + 1], D, B, R, args.precision, ctx=pipe.ctx[0], stream=main, scores=s1)
         b.record(main)
         torch.cuda.synchronize()
         lat.append(a.elapsed_time(b))
     lat.sort()
+
+    # ---- quality: pixel AUROC of the GPU maps against the planted masks
+    pipe.step(0, main)
+    torch.cuda.synchronize()
+    scores = pipe.scores[0].cpu().numpy()
+    aurocs = [auroc(scores[i], masks[i]) for i in range(N_IMG)]
+    auroc_mean = float(np.nanmean(aurocs))
 
     peaks = measured_peaks()
     roof = roofline_entry(dominant, dom_ms, dom_n, peaks, HW, HW, C, D, B, R, traffic=args.traffic)
@@ -470,11 +475,13 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
             "data": "synthetic (seeded Gaussian random fields with planted anomalies)",
             "config": {"workload": WORKLOAD, "images_per_rank_step": N_IMG, "H": HW, "W": HW, "C": C, "d": D,
-                       "B": B, "r": R, "projection": args.precision, "fit": "fp64", "streams": args.streams,
+                       "B": B, "r": R, "projection": args.precision, "fit": "exact integer Gram + float-float eig",
+                       "path": "qfca_batch_run, CUDA graph, 2 steps in flight" if not args.no_graph
+                       else "qfca_batch_run, 2 steps in flight",
                        "l2": "inputs 1 GiB per step > L2 (no flush needed)"},
             "e2e": {"value": round(e2e_value, 3), "unit": "maps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches,
+            "gpu_launches": launches_per_step * args.steps,
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clocks,
@@ -500,8 +507,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f32", choices=["f32", "bf16"])
-    ap.add_argument("--streams", type=int, default=16)
+    ap.add_argument("--precision", default="bf16", choices=["f32", "bf16"])
+    ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,

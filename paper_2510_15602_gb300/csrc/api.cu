@@ -48,6 +48,15 @@ struct Tracer final : qfca::LaunchHook {
         }
         return pool[pool_used++];
     }
+    // While the stream is being captured into a CUDA graph the events must be
+    // recorded as graph nodes (external records), so each replay re-records them.
+    static void record(cudaEvent_t e, cudaStream_t st) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+            cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+        else
+            cudaEventRecord(e, st);
+    }
     void before(const char *k, cudaStream_t st) override {
         launches++;
         pending = false;
@@ -55,13 +64,13 @@ struct Tracer final : qfca::LaunchHook {
         if (!filter.empty() && !strstr(k, filter.c_str())) return;
         Rec r{k, take(), take()};
         if (!r.a || !r.b) return;
-        cudaEventRecord(r.a, st);
+        record(r.a, st);
         recs.push_back(r);
         pending = true;
         agg_valid = false;
     }
     void after(const char *, cudaStream_t st) override {
-        if (pending) cudaEventRecord(recs.back().b, st);
+        if (pending) record(recs.back().b, st);
         pending = false;
     }
     void reset() {
