@@ -257,15 +257,22 @@ def run_reference(args):
 # ------------------------------------------------------------------ our arm
 
 
-def timed(torch, main, fn, steps):
+def timed(torch, main, fn, steps, fork=None, join=None):
+    """Time `steps` calls of fn(i) with CUDA events on `main`: side streams
+    fork from main after the start event (`fork()`) and main waits for them
+    before the stop event (`join()`)."""
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     barrier()
     e0.record(main)
+    if fork is not None:
+        fork()
     t0 = time.perf_counter()
     for i in range(steps):
         fn(i)
+    if join is not None:
+        join()
     e1.record(main)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
@@ -276,20 +283,22 @@ def timed(torch, main, fn, steps):
 class BatchPipe:
     """Two contexts on two streams; step i runs the whole path over the batch on
     pipe i % 2 (a captured CUDA graph of one qfca_batch_run), so consecutive
-    steps overlap on the device.  Steps fork from and join into `main`."""
+    steps overlap on the device: each pipe waits only for its own previous step.
+    `fork()` makes both pipes wait for `main`; `join()` makes `main` wait for both."""
 
-    def __init__(self, q, torch, X, precision, use_graph=True):
-        self.q, self.torch, self.X = q, torch, X
+    def __init__(self, q, torch, X, precision):
+        self.q, self.torch = q, torch
+        self.X = [X, X.clone()]  # one input buffer per pipe (the end-to-end run refills them)
         self.precision = precision
         nimg, C, H, W = X.shape
         self.ctx = [q.Context(), q.Context()]
         self.st = [torch.cuda.Stream(), torch.cuda.Stream()]
         self.scores = [torch.empty(nimg, H, W, dtype=torch.float32, device=X.device) for _ in range(2)]
         self.graphs = None
-        self.use_graph = use_graph
 
     def run_direct(self, k):
-        self.q.batch_run(self.X, D, B, R, self.precision, ctx=self.ctx[k], stream=self.st[k], scores=self.scores[k])
+        self.q.batch_run(self.X[k], D, B, R, self.precision, ctx=self.ctx[k], stream=self.st[k],
+                         scores=self.scores[k])
 
     def capture(self):
         torch = self.torch
@@ -302,25 +311,31 @@ class BatchPipe:
             self.graphs.append(g)
         torch.cuda.synchronize()
 
-    def step(self, i, main, pre=None, post=None):
+    def fork(self, main):
+        ev = self.torch.cuda.Event()
+        ev.record(main)
+        for st in self.st:
+            st.wait_event(ev)
+
+    def join(self, main):
+        for st in self.st:
+            ev = self.torch.cuda.Event()
+            ev.record(st)
+            main.wait_event(ev)
+
+    def step(self, i, pre=None, post=None):
         torch = self.torch
         k = i % 2
         st = self.st[k]
-        ev = torch.cuda.Event()
-        ev.record(main)
-        st.wait_event(ev)
         with torch.cuda.stream(st):
             if pre is not None:
-                pre(st)
+                pre(k)
             if self.graphs is not None:
                 self.graphs[k].replay()
             else:
                 self.run_direct(k)
             if post is not None:
-                post(st, self.scores[k])
-        done = torch.cuda.Event()
-        done.record(st)
-        main.wait_event(done)
+                post(k, self.scores[k])
 
 
 def run_ours(args):
@@ -342,20 +357,25 @@ def run_ours(args):
     masks = [m for _, m in host]
     pipe = BatchPipe(qfca, torch, X_dev, args.precision)
 
+    def run_steps(n, pre=None, post=None):
+        pipe.fork(main)
+        for i in range(n):
+            pipe.step(i, pre, post)
+        pipe.join(main)
+
     # ---- warm-up (grows both context workspaces, sets kernel attributes)
-    for i in range(args.warmup):
-        pipe.step(i, main)
+    run_steps(max(2, args.warmup))
     torch.cuda.synchronize()
 
     # ---- which kernel dominates: one traced direct step over all kernels
     pipe.ctx[0].trace_start("")
-    pipe.step(0, main)
+    run_steps(1)
     torch.cuda.synchronize()
     agg = {k: list(v) for k, v in pipe.ctx[0].trace().items()}
     pipe.ctx[0].trace_stop()
     dominant = max(agg, key=lambda k: agg[k][0])
     n0 = pipe.ctx[0].launch_count()
-    pipe.step(0, main)
+    run_steps(1)
     torch.cuda.synchronize()
     launches_per_step = pipe.ctx[0].launch_count() - n0
 
@@ -364,14 +384,14 @@ def run_ours(args):
         c.trace_start(dominant)
     if not args.no_graph:
         pipe.capture()
-        for i in range(2):
-            pipe.step(i, main)
+        run_steps(2)
         torch.cuda.synchronize()
 
-    # ---- timed region
+    # ---- timed region: fork once, K steps alternating over the two pipes, join once
     sampler = ClockSampler(gpu_id_for_smi(local))
     sampler.start()
-    dev_s, wall_s = timed(torch, main, lambda i: pipe.step(i, main), args.steps)
+    dev_s, wall_s = timed(torch, main, lambda i: pipe.step(i), args.steps, fork=lambda: pipe.fork(main),
+                          join=lambda: pipe.join(main))
     clocks = sampler.stop()
     dom_ms, dom_n = 0.0, 0
     for c in pipe.ctx:
@@ -386,16 +406,15 @@ def run_ours(args):
     # ---- end to end through the public API with host buffers (H2D of the batch, D2H of the maps)
     score_pin = [torch.empty(N_IMG, HW, HW, dtype=torch.float32).pin_memory() for _ in range(2)]
 
-    def pre(st):
-        X_dev.copy_(X_pin, non_blocking=True)
+    def pre(k):
+        pipe.X[k].copy_(X_pin, non_blocking=True)
 
-    def post_factory(i):
-        def post(st, scores):
-            score_pin[i % 2].copy_(scores, non_blocking=True)
-        return post
+    def post(k, scores):
+        score_pin[k].copy_(scores, non_blocking=True)
 
     e2e_steps = max(2, args.steps // 2)
-    e2e_dev, e2e_wall = timed(torch, main, lambda i: pipe.step(i, main, pre, post_factory(i)), e2e_steps)
+    e2e_dev, e2e_wall = timed(torch, main, lambda i: pipe.step(i, pre, post), e2e_steps,
+                              fork=lambda: pipe.fork(main), join=lambda: pipe.join(main))
     e2e_t = max_over_ranks(max(e2e_dev, e2e_wall))
     e2e_value = N_IMG * ws * e2e_steps / e2e_t
     h2d = X_pin.numel() * 4
@@ -444,7 +463,8 @@ def run_ours(args):
     lat.sort()
 
     # ---- quality: pixel AUROC of the GPU maps against the planted masks
-    pipe.step(0, main)
+    pipe.X[0].copy_(X_pin)
+    run_steps(1)
     torch.cuda.synchronize()
     scores = pipe.scores[0].cpu().numpy()
     aurocs = [auroc(scores[i], masks[i]) for i in range(N_IMG)]

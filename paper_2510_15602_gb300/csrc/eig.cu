@@ -88,10 +88,16 @@ __device__ ff block_acc(ffa::acc A, ffa::acc *red) {
     __syncthreads();
     if (lane == 0) red[warp] = A;
     __syncthreads();
-    ffa::acc T = red[0];
-    for (int w = 1; w < kNW; w++) ffa::acc_merge(T, red[w]);
+    // pairwise tree over the 16 warp sums (same order in every thread and CTA)
+    ffa::acc T[kNW];
+#pragma unroll
+    for (int w = 0; w < kNW; w++) T[w] = red[w];
+#pragma unroll
+    for (int step = 1; step < kNW; step <<= 1)
+#pragma unroll
+        for (int w = 0; w + step < kNW; w += 2 * step) ffa::acc_merge(T[w], T[w + step]);
     __syncthreads();
-    return ffa::acc_value(T);
+    return ffa::acc_value(T[0]);
 }
 
 __device__ int sturm_count(const float *dg, const float *e2, int n, float x) {
@@ -220,14 +226,19 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
         if (reflect) {
             // ---- column part of the own partial product: sum over own rows i > jc of A[i][jc] v_i
             for (int jc = k + 1 + tid; jc < n; jc += kT) {
-                ffa::acc Q = ffa::acc_zero();
+                ffa::acc Q0 = ffa::acc_zero(), Q1 = ffa::acc_zero();  // two chains for ILP
                 int lc = (jc + 1 - r + R - 1) / R;
                 if (lc < 0) lc = 0;
-                for (int l = lc; l < nloc; l++) {
-                    const int i = r + l * R;  // i >= jc + 1 >= k + 2: v_i = x_{i-k-1}
-                    ffa::acc_fma(Q, rows[row_off(l, r, R) + jc], xcur[i - k - 1]);
+                int l = lc;
+                for (; l + 1 < nloc; l += 2) {
+                    const int i0 = r + l * R, i1 = i0 + R;  // i >= jc + 1 >= k + 2: v_i = x_{i-k-1}
+                    const ff a0 = rows[row_off(l, r, R) + jc], a1 = rows[row_off(l + 1, r, R) + jc];
+                    ffa::acc_fma(Q0, a0, xcur[i0 - k - 1]);
+                    ffa::acc_fma(Q1, a1, xcur[i1 - k - 1]);
                 }
-                pbuf[jc - k - 1] = ffa::acc_value(Q);
+                if (l < nloc) ffa::acc_fma(Q0, rows[row_off(l, r, R) + jc], xcur[r + l * R - k - 1]);
+                ffa::acc_merge(Q0, Q1);
+                pbuf[jc - k - 1] = ffa::acc_value(Q0);
             }
             __syncthreads();
             // ---- plus the row part for own rows i >= k+1: sum_{j=k+1..i} A[i][j] v_j
@@ -526,13 +537,19 @@ size_t smem_plan(int n, int d, int R, long *region0, int *nslots) {
     return sizeof(ff) * ((size_t)reg + (size_t)R * n + 4 * (size_t)n) + sizeof(ffa::acc) * kNW + sizeof(ff) * 4;
 }
 
-int pick_R(int n, int d) {
-    for (int R = 2; R <= 8; R *= 2) {
+// Cluster size: the smallest R whose shared-memory plan fits, raised for small
+// batches (a matrix's reduction is latency-bound, so idle SMs are better spent
+// on fewer rows per CTA): aim for about half of the 152 SMs across the batch.
+int pick_R(int n, int d, int mats) {
+    int R = 0;
+    for (int r = 2; r <= 8; r *= 2) {
         long reg;
         int ns;
-        if (smem_plan(n, d, R, &reg, &ns) <= kSmemMax) return R;
+        if (smem_plan(n, d, r, &reg, &ns) <= kSmemMax) { R = r; break; }
     }
-    return 0;
+    if (R == 0) return 0;
+    while (R < 8 && 2 * R * mats <= 76) R *= 2;
+    return R;
 }
 
 }  // namespace
@@ -567,7 +584,7 @@ size_t eig_workspace_bytes(int n, int d, int mats) { return eig_plan(n, d, mats)
 // cov_ff: [mats][n][n] float-float pairs (hi, lo) of the covariance.
 cudaError_t launch_eig(const void *cov_ff, int n, int d, int mats, double *V, double *eigvals, void *ws,
                        cudaStream_t st) {
-    const int R = pick_R(n, d);
+    const int R = pick_R(n, d, mats);
     if (R == 0) return cudaErrorNotSupported;
     long region0 = 0;
     int nslots = 1;
