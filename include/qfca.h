@@ -151,7 +151,9 @@ qfca_status qfca_quantize(qfca_ctx *ctx, const float *X, qfca_fmap desc, const q
  * the supplement).  For pixel p with clipped window of N_loc pixels:
  *   D_k(p) = sum_{b=0}^{B-1} |cumP_b * N_ref - cumR_b * N_loc|   (exact),
  *   score(p) = (sum_k D_k(p)) / (d * N_loc * N_ref)              (FP32 out).
- *   bins       device u8 [d][H][pitch]; values >= B are treated as B-1.
+ *   bins       device u8 [d][H][pitch], 16-byte aligned, pitch >= W and a
+ *              multiple of 16 (tiles are staged by TMA); values >= B are
+ *              treated as B-1.
  *   ref_hist   device u32 [d][B]; every row sums to ref_total = N_ref.
  *   score      device f32 [H][W].
  *   numer_out  device u64 [d][H][W] or NULL: the exact D_k(p).
@@ -170,7 +172,7 @@ qfca_status qfca_device_status(qfca_ctx *ctx, int *out);
  * then keeps that intermediate in its workspace).  Per-image blocks are packed
  * image after image:
  *   mean [nimg][C], V [nimg][C][d], eigvals [nimg][d]  (FP64, as qfca_fit_pca)
- *   bins [nimg][d][H][pitch] with `pitch` (>= W, multiple of 16; ignored when
+ *   bins [nimg][d][H][pitch], 16-byte aligned, `pitch` >= W and a multiple of 16 (ignored when
  *        bins is NULL), ref_hist [nimg][d][B], lo/hi [nimg][d]. */
 typedef struct {
     double *mean;

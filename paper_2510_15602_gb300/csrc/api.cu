@@ -359,6 +359,7 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
     if (!bins || !ref_hist || !score) return fail(ctx, QFCA_ERR_INVALID_ARG, "NULL pointer");
     if (H < 1 || W < 1) return fail(ctx, QFCA_ERR_INVALID_ARG, "bad H x W");
     if (pitch < W || pitch % 16 != 0) return fail(ctx, QFCA_ERR_INVALID_ARG, "pitch %d must be >= W and a multiple of 16", pitch);
+    if (((uintptr_t)bins & 15) != 0) return fail(ctx, QFCA_ERR_INVALID_ARG, "bins must be 16-byte aligned");
     if (d < 1 || d > kMaxD) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, %d]", d, kMaxD);
     if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
     if (r < 1 || 2 * r + 1 > 127) return fail(ctx, QFCA_ERR_INVALID_ARG, "r = %d outside [1, 63]", r);
@@ -367,7 +368,7 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
     HookScope hs(ctx);
     if ((s = ensure_ws(ctx, score_workspace_bytes(H, W, 1)))) return s;
     cudaError_t e = launch_score_ws(bins, H, W, pitch, d, 1, B, r, ref_hist, ref_total, score, numer_out, ctx->ws,
-                                    (cudaStream_t)stream);
+                                    ctx->status_dev, (cudaStream_t)stream);
     if (e == cudaErrorNotSupported)
         return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d needs more shared memory than a CTA has", B, r);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_score");
@@ -391,6 +392,8 @@ qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap de
     const int pitch_min = (desc.W + 15) / 16 * 16;
     if (extra && extra->bins && (extra->pitch < desc.W || extra->pitch % 16 != 0))
         return fail(ctx, QFCA_ERR_INVALID_ARG, "extra->pitch %d must be >= W and a multiple of 16", extra->pitch);
+    if (extra && extra->bins && ((uintptr_t)extra->bins & 15) != 0)
+        return fail(ctx, QFCA_ERR_INVALID_ARG, "extra->bins must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     HookScope hs(ctx);
     const long N = (long)desc.H * desc.W;
@@ -432,7 +435,8 @@ qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap de
     e = launch_quantize(Y, N, desc.H, desc.W, d, nimg, B, QFCA_RANGE_IMAGE, mm, nullptr, nullptr, bins, pitch, lo, hi,
                         hist, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run/quantize");
-    e = launch_score_ws(bins, desc.H, desc.W, pitch, d, nimg, B, r, hist, (uint32_t)N, scores, nullptr, b + o_sc, st);
+    e = launch_score_ws(bins, desc.H, desc.W, pitch, d, nimg, B, r, hist, (uint32_t)N, scores, nullptr, b + o_sc,
+                        ctx->status_dev, st);
     if (e == cudaErrorNotSupported)
         return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d needs more shared memory than a CTA has", B, r);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run/score");

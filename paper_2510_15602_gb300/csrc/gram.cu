@@ -28,7 +28,8 @@
 // of pixels; per 64-pixel sub-chunk all threads convert both channel blocks
 // into the 128-byte-swizzled K-major layout (channels are rows, pixels are K:
 // NCHW is already K-major), one thread issues the 40 MMAs (10 digit pairs x 4
-// K-steps of 16) and commits to an mbarrier (bounded wait).
+// K-steps of 16) and commits to an mbarrier (bounded wait); while the tensor
+// cores run, every thread fetches the next sub-chunk's features into registers.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -95,33 +96,46 @@ __device__ __forceinline__ uint32_t swz(int row, int chunk16) {
     return (uint32_t)(row * 128 + ((chunk16 ^ (row & 7)) << 4));
 }
 
-// Convert one operand block (128 channels starting at c0) of pixels [q0, q0+64) into
-// 4 digit slices (K-major, 128-B swizzle).  Optionally accumulate per-row digit sums.
-__device__ __forceinline__ void stage_block(const float *__restrict__ X, int layout, int vec_ok, int C, long N, int c0,
-                                            long q0, long q1, const float *__restrict__ scale, uint8_t *slices,
-                                            int *__restrict__ dsum /* [4][128] or null */,
-                                            unsigned long long *__restrict__ dsq /* [128] level-4 diagonal */) {
-    // 128 rows x 8 chunks of 8 pixels = 1024 units; 2 per thread
-    for (int u = threadIdx.x; u < kTB * 8; u += kThreads) {
+// Load one operand block (128 channels starting at c0) of pixels [q0, q0+64)
+// into registers: units u = threadIdx.x + i * kThreads (i = 0, 1), each one
+// channel row and 8 consecutive pixels.
+__device__ __forceinline__ void load_block(const float *__restrict__ X, int layout, int vec_ok, int C, long N, int c0,
+                                           long q0, long q1, float (&v)[2][8]) {
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const int u = threadIdx.x + i * kThreads;
         const int row = u >> 3, g = u & 7;
         const int c = c0 + row;
         const long p = q0 + g * 8;
-        float v[8];
         if (vec_ok && c < C && p + 8 <= q1) {
             const float4 a = __ldg(reinterpret_cast<const float4 *>(X + (long)c * N + p));
             const float4 b = __ldg(reinterpret_cast<const float4 *>(X + (long)c * N + p + 4));
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z; v[i][3] = a.w;
+            v[i][4] = b.x; v[i][5] = b.y; v[i][6] = b.z; v[i][7] = b.w;
         } else {
 #pragma unroll
             for (int e = 0; e < 8; e++) {
                 const long pe = p + e;
-                v[e] = (c < C && pe < q1) ? (layout == QFCA_NCHW ? X[(long)c * N + pe] : X[pe * C + c]) : 0.0f;
+                v[i][e] = (c < C && pe < q1) ? (layout == QFCA_NCHW ? X[(long)c * N + pe] : X[pe * C + c]) : 0.0f;
             }
         }
+    }
+}
+
+// Convert the loaded block into 4 digit slices (K-major, 128-B swizzle);
+// optionally accumulate per-row digit sums and the level-4 diagonal terms.
+__device__ __forceinline__ void convert_block(const float (&v)[2][8], int C, int c0, const float *__restrict__ scale,
+                                              uint8_t *slices, int *__restrict__ dsum /* [4][128] or null */,
+                                              unsigned long long *__restrict__ dsq /* [128] or null */) {
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const int u = threadIdx.x + i * kThreads;
+        const int row = u >> 3, g = u & 7;
+        const int c = c0 + row;
         const float s = c < C ? scale[c] : 0.0f;
         float dd[kSlices][8];
 #pragma unroll
-        for (int e = 0; e < 8; e++) digits4(__fmul_rn(v[e], s), dd[0][e], dd[1][e], dd[2][e], dd[3][e]);
+        for (int e = 0; e < 8; e++) digits4(__fmul_rn(v[i][e], s), dd[0][e], dd[1][e], dd[2][e], dd[3][e]);
 #pragma unroll
         for (int sl = 0; sl < kSlices; sl++) {
             uint4 pk;
@@ -203,10 +217,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const float *__restrict__ 
     bool failed = false;
     int in_win = 0;
 
+    float va[2][8], vb[2][8];
+    load_block(X, layout, vec_ok, C, N, ti * kTB, p0, p1, va);
+    if (!diag) load_block(X, layout, vec_ok, C, N, tj * kTB, p0, p1, vb);
     for (long q0 = p0; q0 < p1; q0 += kSub) {
-        stage_block(X, layout, vec_ok, C, N, ti * kTB, q0, p1, scale, As, diag ? dsum : nullptr,
-                    diag ? dsq : nullptr);
-        if (!diag) stage_block(X, layout, vec_ok, C, N, tj * kTB, q0, p1, scale, Bs, nullptr, nullptr);
+        convert_block(va, C, ti * kTB, scale, As, diag ? dsum : nullptr, diag ? dsq : nullptr);
+        if (!diag) convert_block(vb, C, tj * kTB, scale, Bs, nullptr, nullptr);
         tc::fence_proxy_async_smem();
         tc::tc_fence_before();
         __syncthreads();
@@ -225,6 +241,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const float *__restrict__ 
                 }
             }
             tc::mma_commit(bar);
+        }
+        // the next sub-chunk's features are fetched while the tensor cores run
+        if (q0 + kSub < p1) {
+            load_block(X, layout, vec_ok, C, N, ti * kTB, q0 + kSub, p1, va);
+            if (!diag) load_block(X, layout, vec_ok, C, N, tj * kTB, q0 + kSub, p1, vb);
         }
         const bool ok = tc::mbar_wait(bar, phase, kWaitTries);
         phase ^= 1u;

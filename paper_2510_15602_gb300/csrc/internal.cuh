@@ -2,6 +2,7 @@
 // Not part of the public ABI (include/qfca.h is).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -74,7 +75,14 @@ size_t score_workspace_bytes(int H, int W, int nimg);
 // bins [nimg][d][H][pitch], ref_hist [nimg][d][B], score [nimg][H][W], numer [nimg][d][H][W].
 cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d, int nimg, int B, int r,
                             const uint32_t *ref_hist, uint32_t ref_total, float *score,
-                            uint64_t *numer, void *ws, cudaStream_t st);
+                            uint64_t *numer, void *ws, int *status, cudaStream_t st);
+
+// ------------------------------------------------------------------ TMA (tmap.cu)
+
+// Encode a 3-D u8 tiled tensor map (no swizzle, zero fill out of bounds) into
+// the 128-byte CUtensorMap at tmap_out.  dim0 is innermost.
+cudaError_t make_tmap_u8_3d(void *tmap_out, const void *base, uint64_t dim0, uint64_t dim1, uint64_t dim2,
+                            uint64_t stride1_bytes, uint64_t stride2_bytes, uint32_t box0, uint32_t box1);
 
 // ------------------------------------------------------------------ helpers
 
