@@ -70,6 +70,8 @@ def _load():
             lib.orc_window_hist.restype = L
             lib.orc_score.argtypes = [P, I, I, I, I, I, P, ctypes.c_uint64, P, P, P]
             lib.orc_score.restype = I
+            lib.orc_score_at.argtypes = [P, I, I, I, I, I, P, ctypes.c_uint64, I, I, P]
+            lib.orc_score_at.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -193,6 +195,18 @@ def score(q: np.ndarray, B: int, r: int, R: np.ndarray, Nref: int | None = None)
     if rc < 0:
         raise MemoryError("oracle score")
     return s, numer, nloc
+
+
+def score_at(q: np.ndarray, B: int, r: int, R: np.ndarray, Nref: int, y: int, x: int):
+    """One pixel of `score`: (score float64, numer int64 [d]) at (y, x)."""
+    q = np.ascontiguousarray(q, np.uint8)
+    d, H, W = q.shape
+    R = np.ascontiguousarray(R, np.uint32)
+    numer = np.zeros(d, np.int64)
+    s = _load().orc_score_at(_p(q), d, H, W, B, r, _p(R), int(Nref), int(y), int(x), _p(numer))
+    if s < 0:
+        raise MemoryError("oracle score_at")
+    return s, numer
 
 
 def pipeline(X: np.ndarray, d: int, B: int, r: int, layout: int = NCHW):

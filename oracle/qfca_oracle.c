@@ -337,3 +337,32 @@ int orc_score(const uint8_t *q, int d, int H, int W, int B, int r, const uint32_
     free(L);
     return 0;
 }
+
+/* One pixel of orc_score: the window histogram of (y, x) per component
+ * (orc_window_hist), its EMD numerator D_k against R_k, and the mean over
+ * components of D_k / (N_loc N_ref) (Sec. 3.1, Sec. 3).  Writes numer[d]
+ * when non-NULL; returns the score, or -1 on allocation failure. */
+double orc_score_at(const uint8_t *q, int d, int H, int W, int B, int r, const uint32_t *R,
+                    uint64_t Nref, int y, int x, int64_t *numer)
+{
+    long N = (long)H * W;
+    int64_t *L = (int64_t *)malloc(sizeof(int64_t) * (B > 0 ? B : 1));
+    if (!L)
+        return -1.0;
+    double s = 0.0;
+    for (int k = 0; k < d; k++) {
+        long Nloc = orc_window_hist(q + (long)k * N, H, W, B, r, y, x, L);
+        int64_t cumL = 0, cumR = 0, D = 0;
+        for (int b = 0; b < B; b++) {
+            cumL += L[b];
+            cumR += (int64_t)R[(long)k * B + b];
+            int64_t diff = cumL * (int64_t)Nref - cumR * (int64_t)Nloc;
+            D += diff < 0 ? -diff : diff;
+        }
+        if (numer)
+            numer[k] = D;
+        s += (double)D / ((double)Nloc * (double)Nref);
+    }
+    free(L);
+    return s / (double)d;
+}

@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const float *__restrict__ 
                                                       unsigned long long *__restrict__ Dsum,
                                                       int *__restrict__ status) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *smem = tc::align_smem<1024>(smem_raw);
     uint8_t *As = smem;                                // 4 slices x 16 KB
     uint8_t *Bs = smem + kSlices * kTB * 128;          // 4 slices x 16 KB
     uint64_t *bar = (uint64_t *)(Bs + kSlices * kTB * 128);

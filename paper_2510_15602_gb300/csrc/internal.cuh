@@ -70,12 +70,23 @@ cudaError_t launch_quantize(const float *Y, long N, int H, int W, int d, int nim
 
 // ------------------------------------------------------------------ score (score.cu)
 
-size_t score_workspace_bytes(int H, int W, int nimg);
+// Workspace of launch_score_ws in per-component mode: the numerators D_k(p).
+size_t score_workspace_bytes(int H, int W, int d, int nimg);
 
-// bins [nimg][d][H][pitch], ref_hist [nimg][d][B], score [nimg][H][W], numer [nimg][d][H][W].
+// Tiling of the window-EMD kernel: strip width SW (64 or 128 threads), band
+// height TH (1..64 rows) and number of component groups n_kg.
+struct ScoreTiling {
+    int SW, TH, n_kg;
+};
+
+// bins [nimg][d][H][pitch], ref_hist [nimg][d][B], score [nimg][H][W], numer_out [nimg][d][H][W] (optional).
+// ws: the per-component numerators (score_workspace_bytes) or, when
+// ws_accumulates, their per-pixel sums u64 [nimg][H][W].  tiling NULL: the
+// built-in model picks one.  cudaErrorNotSupported: nothing was enqueued.
 cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d, int nimg, int B, int r,
-                            const uint32_t *ref_hist, uint32_t ref_total, float *score,
-                            uint64_t *numer, void *ws, int *status, cudaStream_t st);
+                            const uint32_t *ref_hist, uint32_t ref_total, float *score, uint64_t *numer_out,
+                            void *ws, bool ws_accumulates, int *status, cudaStream_t st,
+                            const ScoreTiling *tiling);
 
 // ------------------------------------------------------------------ TMA (tmap.cu)
 

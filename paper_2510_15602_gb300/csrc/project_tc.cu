@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kThreads) k_project_bf16(const float *__restri
                                                           float *__restrict__ Y, uint32_t *__restrict__ mm_keys,
                                                           int *__restrict__ status, long tiles_per_img, int nimg) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *smem = tc::align_smem<1024>(smem_raw);
     const int nk = Cp / kKc;
     uint8_t *As = smem;
     uint8_t *Bs = smem + (size_t)nk * kM * 128;

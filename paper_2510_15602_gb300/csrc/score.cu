@@ -7,13 +7,16 @@
 //     score(p) = sum_k D_k(p) / (d * N_loc * N_ref)
 //
 // k_window_emd: one CTA = a band of TH rows x a strip of SW columns x a group of
-// components.  The bin tile with an r-pixel halo is staged in shared memory;
-// each thread owns one output column and keeps its window histogram in shared
-// memory (bin-major, thread-minor: conflict-free), sliding it down the band:
-// one row of 2r+1 bins leaves and one enters per step (running window counts).
-// The CDF walk is sequential per thread.  The per-pixel integer sum over the
-// CTA's components goes to a u64 accumulator (atomic integer adds:
-// order-independent and exact); k_finalize divides once per pixel.
+// components.  Each component's bin tile (band plus an r-pixel halo) arrives
+// in shared memory as one TMA box; the CTA rewrites it in place so that
+// in-image pixels hold bin+1 and everything outside the image holds 0.  Each
+// thread owns one output column and keeps its window histogram in shared
+// memory (bin-major, thread-minor: conflict-free), row 0 counting the
+// outside pixels, so every window update touches exactly 2r+1 entries with no
+// clipping tests.  The histogram slides down the band (one row leaves, one
+// enters: running window counts); the CDF walk is sequential per thread over
+// the B bins.  Each numerator D_k(p) is written out (exact, u32 when it
+// fits), and k_finalize sums them over k and divides once per pixel.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,87 +28,73 @@
 namespace qfca {
 namespace {
 
-constexpr int kSW = 128;  // output columns per CTA (one thread each)
-constexpr int kTH = 16;   // output rows per CTA band
+constexpr int kMaxSW = 128;  // strip width limit (threads per CTA)
+constexpr uint32_t kTmaTries = 1u << 26;
 
 struct ScoreGeom {
-    int TH, TR, halo, TCp, kg, n_kg;  // TCp: TMA box width (bytes), halo: left margin (16-B aligned)
+    int SW, TH, TR, halo, TCp, kg, n_kg;  // TCp: TMA box width (bytes), halo: left margin (16-B aligned)
     size_t smem, tile_bytes;
 };
 
-constexpr uint32_t kTmaTries = 1u << 26;
-
-// `slots`: CTAs resident at once on the whole GPU (0: geometry only).  The
-// components are split into n_kg groups so that the waves of CTAs, each
-// costing its number of components plus a fixed setup share, finish soonest.
-ScoreGeom score_geom(int H, int W, int d, int B, int r, int nimg, long slots) {
+ScoreGeom make_geom(int H, int W, int d, int B, int r, int nimg, int SW, int TH, int n_kg) {
+    (void)H, (void)W, (void)nimg;
     ScoreGeom g;
-    g.TH = kTH;
-    g.TR = g.TH + 2 * r;
+    g.SW = SW;
+    g.TH = TH;
+    g.TR = TH + 2 * r;
     g.halo = (int)align_up(r, 16);
-    g.TCp = kSW + 2 * g.halo;
-    const long tiles = (long)((W + kSW - 1) / kSW) * ((H + g.TH - 1) / g.TH) * nimg;
-    int n_kg = 1;
-    if (slots > 0) {
-        double best = 1e300;
-        for (int n = 1; n <= d; n++) {
-            const int kg = (d + n - 1) / n;
-            if (n > 1 && (d + kg - 1) / kg != n) continue;  // same split as a smaller n
-            const double waves = (double)((tiles * n + slots - 1) / slots);
-            const double cost = waves * (kg + 0.5);
-            if (cost < best * 0.999) best = cost, n_kg = n;
-        }
-    }
+    g.TCp = SW + 2 * g.halo;
+    n_kg = n_kg < 1 ? 1 : (n_kg > d ? d : n_kg);
     g.kg = (d + n_kg - 1) / n_kg;
     g.n_kg = (d + g.kg - 1) / g.kg;
     g.tile_bytes = align_up((size_t)g.TR * g.TCp, 128);
-    g.smem = 128                                                // alignment slack
-             + 2 * g.tile_bytes                                 // bin tiles (double buffer, TMA)
-             + sizeof(uint32_t) * (size_t)B * kSW                 // histograms [B][kSW]
-             + sizeof(unsigned long long) * (size_t)g.TH * kSW  // per-pixel sums
-             + 2 * sizeof(uint32_t) * 256                       // cumR, cumR * N_loc(interior)
-             + 2 * sizeof(uint64_t);                            // mbarriers
+    g.smem = 128                                   // alignment slack
+             + 2 * g.tile_bytes                    // bin tiles (double buffer, TMA)
+             + sizeof(uint32_t) * (size_t)(B + 1) * SW  // histograms [B+1][SW], row 0 = outside
+             + sizeof(uint32_t) * 256              // cumR
+             + sizeof(uint64_t) * 256              // cumR * N_loc of an interior window
+             + 2 * sizeof(uint64_t);               // mbarriers
     return g;
 }
 
-// Window histograms + exact EMD numerators for a band of kTH rows x kSW columns
-// and a group of components.  Thread t owns output column x0 + t: its window
-// histogram lives in shared memory at hist[b * kSW + t] (conflict-free), and
-// slides down the band (one row of 2r+1 bins leaves, one enters); increments
-// are shared-memory atomics without return, so no thread waits on them.
-// ACC is the type of the CDF walk: uint32_t when (B-1)(2r+1)^2 N_ref < 2^32
-// (the numerator D and every term then fit), else unsigned long long.
-// The band's bin tile of each component (rows y0-r .. y0+TH-1+r, columns from
-// x0 - halo, halo = r rounded up to 16 bytes) is one 3-D TMA box of the bins
-// tensor [images*d][H][pitch]; boxes are double-buffered so the next
-// component's tile arrives while the current one is processed.  Waits are
-// bounded; a wait that runs out sets bit 0 of the status word and the CTA stops.
-template <typename ACC>
-__global__ void __launch_bounds__(kSW) k_window_emd(const __grid_constant__ CUtensorMap tmap, int H, int W, int d,
-                                                     int B, int r, ScoreGeom g, const uint32_t *__restrict__ ref_hist,
-                                                     uint32_t Nref, unsigned long long *__restrict__ acc,
-                                                     uint64_t *__restrict__ numer, int *__restrict__ status) {
+bool geom_ok(const ScoreGeom &g) { return g.smem <= 200 * 1024 && g.TCp <= 256 && g.TR <= 256; }
+
+// Window histograms + exact EMD numerators for a band of TH rows x SW columns
+// and a group of components.  Thread t owns output column x0 + t; its window
+// histogram lives at hist[b * SW + t].  Increments are shared-memory atomics
+// without return, so no thread waits on them.  ACC is the type of the CDF
+// walk (u32 when (B-1)(2r+1)^2 N_ref < 2^32), OUT the type of the stored
+// numerators; KB > 0 fixes B at compile time.
+template <typename ACC, typename OUT, int KB>
+__global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ CUtensorMap tmap, int H, int W, int d,
+                                                        int Bdyn, int r, ScoreGeom g,
+                                                        const uint32_t *__restrict__ ref_hist, uint32_t Nref,
+                                                        OUT *__restrict__ numer, unsigned long long *__restrict__ accum,
+                                                        int *__restrict__ status) {
+    const int B = KB > 0 ? KB : Bdyn;
+    const int SW = g.SW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    unsigned char *smem = tc::align_smem<128>(smem_raw);
     uint8_t *tiles = smem;
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem + 2 * g.tile_bytes);
-    unsigned long long *accS = reinterpret_cast<unsigned long long *>(hist + (size_t)B * kSW);
-    uint32_t *cumR = reinterpret_cast<uint32_t *>(accS + (size_t)g.TH * kSW);
-    uint32_t *cRi = cumR + 256;  // cumR[b] * N_loc for an interior window
-    uint64_t *bar = reinterpret_cast<uint64_t *>(cRi + 256);
+    uint32_t *cumR = hist + (size_t)(B + 1) * SW;
+    ACC *cRi = reinterpret_cast<ACC *>(cumR + 256);  // cumR[b] * N_loc for an interior window
+    uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(cumR + 256) + 256 * sizeof(uint64_t));
 
-    const int t = threadIdx.x;
-    const int x0 = blockIdx.x * kSW, y0 = blockIdx.y * g.TH;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = SW >> 5;
+    const int x0 = blockIdx.x * SW, y0 = blockIdx.y * g.TH;
+    const int x = x0 + t;
     const long img = blockIdx.z / g.n_kg;
     const int k0 = (blockIdx.z % g.n_kg) * g.kg, k1 = min(d, k0 + g.kg);
     ref_hist += img * d * B;
-    acc += img * H * (long)W;
-    if (numer) numer += img * d * H * (long)W;
-    const int x = x0 + t;
+    const long HW = (long)H * W;
+
     const int ty0 = y0 - r, tx0 = x0 - g.halo;  // image coordinates of the tile origin
-    const uint32_t Nint = (uint32_t)((2 * r + 1) * (2 * r + 1));
+    const int span = 2 * r + 1;
+    const uint32_t Nint = (uint32_t)(span * span);
     const uint32_t box_bytes = (uint32_t)(g.TR * g.TCp);
-    for (int i = 0; i < g.TH; i++) accS[i * kSW + t] = 0ull;
+    const int wpr = g.TCp >> 2;  // 32-bit words per tile row
+    const bool inner = tx0 >= 0 && tx0 + g.TCp <= W && ty0 >= 0 && ty0 + g.TR <= H;
     if (t == 0) {
         tc::mbar_init(&bar[0], 1);
         tc::mbar_init(&bar[1], 1);
@@ -119,8 +108,9 @@ __global__ void __launch_bounds__(kSW) k_window_emd(const __grid_constant__ CUte
     bool failed = false;
     int issued = k0 < k1 ? 1 : 0, waited = 0;
 
-    const int xl = max(0, x - r), xr = min(W - 1, x + r);
-    const int ncols = xr - xl + 1;
+    const int ncols = min(W - 1, x + r) - max(0, x - r) + 1;
+    const int c0 = t + g.halo - r;  // tile column of this thread's window's left edge
+    uint32_t *hc = hist + t;
     for (int k = k0; k < k1; k++) {
         __syncthreads();  // the buffer of component k-1 is free again
         const int buf = (k - k0) & 1;
@@ -130,7 +120,7 @@ __global__ void __launch_bounds__(kSW) k_window_emd(const __grid_constant__ CUte
                             &bar[buf ^ 1]);
         }
         if (k + 1 < k1) issued++;
-        // warp 0: lane l loads reference bins [8l, 8l+8) of component k (independent loads, in flight during the wait)
+        // warp 0: lane l loads reference bins [8l, 8l+8) of component k (in flight during the wait)
         uint32_t rv[8];
         if (t < 32) {
 #pragma unroll
@@ -146,11 +136,25 @@ __global__ void __launch_bounds__(kSW) k_window_emd(const __grid_constant__ CUte
             break;
         }
         uint8_t *tile = tiles + (size_t)buf * g.tile_bytes;
-        // clamp out-of-range input bins to B-1, four bytes at a time
+        // in-image bytes -> min(bin, B-1) + 1, everything else -> 0; a warp per tile row
         {
             uint32_t *tw = reinterpret_cast<uint32_t *>(tile);
             const uint32_t cap = 0x01010101u * (uint32_t)(B - 1);
-            for (int i = t; i < (int)(box_bytes >> 2); i += kSW) tw[i] = __vminu4(tw[i], cap);
+            for (int row = warp; row < g.TR; row += nwarps) {
+                const int gy = ty0 + row;
+                const bool rin = gy >= 0 && gy < H;
+                for (int j = lane; j < wpr; j += 32) {
+                    uint32_t w = __vadd4(__vminu4(tw[row * wpr + j], cap), 0x01010101u);
+                    if (!inner) {
+                        const int gx = tx0 + 4 * j;
+                        const int lo = max(0, -gx), hi = min(4, W - gx);  // bytes [lo, hi) lie in the image
+                        uint32_t m = 0;
+                        if (rin && hi > lo) m = (hi >= 4 ? 0xFFFFFFFFu : ((1u << (8 * hi)) - 1u)) & (0xFFFFFFFFu << (8 * lo));
+                        w &= m;
+                    }
+                    tw[row * wpr + j] = w;
+                }
+            }
         }
         if (t < 32) {  // whole warp 0: prefix sums of the reference histogram
             uint32_t part = 0;
@@ -169,138 +173,251 @@ __global__ void __launch_bounds__(kSW) k_window_emd(const __grid_constant__ CUte
                 c += rv[j];
                 if (b < B) {
                     cumR[b] = c;
-                    cRi[b] = c * Nint;
+                    cRi[b] = (ACC)c * (ACC)Nint;
                 }
             }
         }
-        for (int b = 0; b < B; b++) hist[b * kSW + t] = 0;
+        if (KB > 0) {
+#pragma unroll
+            for (int b = 0; b <= KB; b++) hc[b * SW] = 0;
+        } else {
+            for (int b = 0; b <= B; b++) hc[b * SW] = 0;
+        }
         __syncthreads();
         if (x < W) {
-            // window of the band's first row
-            const int ya = max(0, y0 - r), yb = min(H - 1, y0 + r);
-            for (int yy = ya; yy <= yb; yy++) {
-                const uint8_t *row = tile + (yy - ty0) * g.TCp - tx0;
-                for (int xx = xl; xx <= xr; xx++) atomicAdd(&hist[row[xx] * kSW + t], 1u);
+            // window of the band's first row: tile rows 0 .. 2r
+            for (int ry = 0; ry < span; ry++) {
+                const uint8_t *row = tile + ry * g.TCp + c0;
+#pragma unroll 4
+                for (int j = 0; j < span; j++) atomicAdd(hc + row[j] * SW, 1u);
             }
             for (int i = 0; i < g.TH; i++) {
                 const int yy = y0 + i;
                 if (yy >= H) break;
                 if (i > 0) {
-                    const int yo = yy - r - 1, yn = yy + r;
-                    if (yo >= 0) {
-                        const uint8_t *row = tile + (yo - ty0) * g.TCp - tx0;
-                        for (int xx = xl; xx <= xr; xx++) atomicSub(&hist[row[xx] * kSW + t], 1u);
-                    }
-                    if (yn < H) {
-                        const uint8_t *row = tile + (yn - ty0) * g.TCp - tx0;
-                        for (int xx = xl; xx <= xr; xx++) atomicAdd(&hist[row[xx] * kSW + t], 1u);
+                    const uint8_t *ro = tile + (i - 1) * g.TCp + c0;       // image row yy - r - 1
+                    const uint8_t *rn = tile + (i + 2 * r) * g.TCp + c0;   // image row yy + r
+#pragma unroll 4
+                    for (int j = 0; j < span; j++) {
+                        atomicSub(hc + ro[j] * SW, 1u);
+                        atomicAdd(hc + rn[j] * SW, 1u);
                     }
                 }
                 const int nrows = min(H - 1, yy + r) - max(0, yy - r) + 1;
                 const uint32_t Nloc = (uint32_t)(nrows * ncols);
-                ACC D = 0, a = 0;
+                ACC D = 0;
+                uint32_t cnt = 0;
+                const uint32_t *hb = hc + SW;  // bin 0
+                // the last bin's term is 0 (both CDFs reach 1), so the walk stops at B-2
                 if (Nloc == Nint) {
+                    if (KB > 0) {
+#pragma unroll
+                        for (int b = 0; b < KB - 1; b++) {
+                            cnt += hb[b * SW];
+                            const ACC a = (ACC)cnt * (ACC)Nref, c = cRi[b];
+                            D += max(a, c) - min(a, c);
+                        }
+                    } else {
 #pragma unroll 4
-                    for (int b = 0; b < B; b++) {
-                        a += (ACC)hist[b * kSW + t] * (ACC)Nref;
-                        const ACC c = (ACC)cRi[b];
-                        D += a > c ? a - c : c - a;
+                        for (int b = 0; b < B - 1; b++) {
+                            cnt += hb[b * SW];
+                            const ACC a = (ACC)cnt * (ACC)Nref, c = cRi[b];
+                            D += max(a, c) - min(a, c);
+                        }
                     }
                 } else {
 #pragma unroll 4
-                    for (int b = 0; b < B; b++) {
-                        a += (ACC)hist[b * kSW + t] * (ACC)Nref;
-                        const ACC c = (ACC)cumR[b] * (ACC)Nloc;
-                        D += a > c ? a - c : c - a;
+                    for (int b = 0; b < B - 1; b++) {
+                        cnt += hb[b * SW];
+                        const ACC a = (ACC)cnt * (ACC)Nref, c = (ACC)cumR[b] * (ACC)Nloc;
+                        D += max(a, c) - min(a, c);
                     }
                 }
-                accS[i * kSW + t] += (unsigned long long)D;
-                if (numer) numer[((long)k * H + yy) * W + x] = (uint64_t)D;
+                const long pix = (long)yy * W + x;
+                if (accum) atomicAdd(&accum[img * HW + pix], (unsigned long long)D);
+                else numer[(img * d + k) * HW + pix] = (OUT)D;
             }
         }
-        tc::fence_proxy_async_smem();  // the clamp's writes precede the next TMA write into this buffer
+        tc::fence_proxy_async_smem();  // this iteration's writes to the tile precede the next TMA write into it
     }
     if (failed) {
         if (t == 0) atomicOr(status, kStatusMmaTimeout);
         // let every issued copy (including the one whose wait ran out) land before the CTA leaves (bounded)
         for (int w = waited - 1; w < issued; w++) tc::mbar_wait(&bar[w & 1], (w >> 1) & 1, kTmaTries);
-        return;
     }
-    __syncthreads();
-    if (x < W)
-        for (int i = 0; i < g.TH; i++) {
-            const int yy = y0 + i;
-            if (yy >= H) break;
-            if (g.n_kg == 1) acc[(long)yy * W + x] = accS[i * kSW + t];
-            else atomicAdd(&acc[(long)yy * W + x], accS[i * kSW + t]);
-        }
 }
 
-// Grid (pixels, images).
-__global__ void k_finalize(const unsigned long long *__restrict__ acc, int H, int W, int r, int d, uint32_t Nref,
-                           float *__restrict__ score) {
+// Grid (pixels, images): s(p) = sum_k D_k(p) / (d * N_loc * N_ref), from the
+// per-component numerators or from their running sums.
+template <typename OUT>
+__global__ void k_finalize(const OUT *__restrict__ numer, const unsigned long long *__restrict__ accum, int H, int W,
+                           int r, int d, uint32_t Nref, float *__restrict__ score) {
     const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= (long)H * W) return;
-    acc += (long)blockIdx.y * H * W;
-    score += (long)blockIdx.y * H * W;
+    const long HW = (long)H * W;
+    if (p >= HW) return;
+    const long img = blockIdx.y;
+    unsigned long long s = 0;
+    if (accum) {
+        s = accum[img * HW + p];
+    } else {
+        const OUT *nk = numer + img * d * HW + p;
+        for (int k = 0; k < d; k++) s += (unsigned long long)__ldg(nk + (long)k * HW);
+    }
     const int y = (int)(p / W), x = (int)(p - (long)y * W);
     const int nr = min(H - 1, y + r) - max(0, y - r) + 1;
     const int nc = min(W - 1, x + r) - max(0, x - r) + 1;
     const double den = (double)nr * (double)nc * (double)Nref * (double)d;
-    score[p] = (float)((double)acc[p] / den);
+    score[img * HW + p] = (float)((double)s / den);
+}
+
+template <typename ACC, typename OUT>
+cudaError_t launch_emd_kb(int KB, const ScoreGeom &g, dim3 grid, cudaStream_t st, const CUtensorMap &tmap, int H,
+                          int W, int d, int B, int r, const uint32_t *ref_hist, uint32_t Nref, OUT *numer,
+                          unsigned long long *accum, int *status) {
+    if (KB == 32)
+        QFCA_LAUNCH("k_window_emd", st,
+                    (k_window_emd<ACC, OUT, 32><<<grid, g.SW, g.smem, st>>>(tmap, H, W, d, B, r, g, ref_hist, Nref,
+                                                                             numer, accum, status)));
+    else if (KB == 64)
+        QFCA_LAUNCH("k_window_emd", st,
+                    (k_window_emd<ACC, OUT, 64><<<grid, g.SW, g.smem, st>>>(tmap, H, W, d, B, r, g, ref_hist, Nref,
+                                                                             numer, accum, status)));
+    else
+        QFCA_LAUNCH("k_window_emd", st,
+                    (k_window_emd<ACC, OUT, 0><<<grid, g.SW, g.smem, st>>>(tmap, H, W, d, B, r, g, ref_hist, Nref,
+                                                                            numer, accum, status)));
+    return cudaSuccess;
+}
+
+template <typename ACC, typename OUT>
+cudaError_t emd_occupancy(int KB, size_t smem, int SW, int *per_sm) {
+    if (KB == 32) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_window_emd<ACC, OUT, 32>, SW, smem);
+    if (KB == 64) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_window_emd<ACC, OUT, 64>, SW, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_window_emd<ACC, OUT, 0>, SW, smem);
+}
+
+template <typename ACC, typename OUT>
+cudaError_t emd_set_smem_attr() {
+    cudaError_t e = cudaFuncSetAttribute(k_window_emd<ACC, OUT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_window_emd<ACC, OUT, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_window_emd<ACC, OUT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    return e;
+}
+
+enum class EmdKind { U32_U32, U32_U64, U64_U64 };
+
+cudaError_t emd_occupancy_kind(EmdKind kind, int KB, size_t smem, int SW, int *per_sm) {
+    switch (kind) {
+    case EmdKind::U32_U32: return emd_occupancy<uint32_t, uint32_t>(KB, smem, SW, per_sm);
+    case EmdKind::U32_U64: return emd_occupancy<uint32_t, unsigned long long>(KB, smem, SW, per_sm);
+    default: return emd_occupancy<unsigned long long, unsigned long long>(KB, smem, SW, per_sm);
+    }
+}
+
+// Modelled cost (in lane-instructions) of one CTA and the choice of strip
+// width, band height and component split that finishes the grid soonest.
+double cta_cost(const ScoreGeom &g, int B, int r) {
+    const int span = 2 * r + 1;
+    const double row = 2.0 * span * 3.0 + 5.0 * (B - 1) + 12.0;
+    const double setup = 3.0 * span * span + 6.0 * g.TR * g.TCp / (4.0 * g.SW) + 2.0 * B + 60.0;
+    return g.kg * (g.TH * row + setup) + 200.0;
 }
 
 }  // namespace
 
-size_t score_workspace_bytes(int H, int W, int nimg) {
-    return align_up(sizeof(unsigned long long) * (size_t)H * W * nimg, 256);
+size_t score_workspace_bytes(int H, int W, int d, int nimg) {
+    return align_up(sizeof(unsigned long long) * (size_t)H * W * d * nimg, 256);
 }
 
 cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d, int nimg, int B, int r,
-                            const uint32_t *ref_hist, uint32_t ref_total, float *score, uint64_t *numer,
-                            void *ws, int *status, cudaStream_t st) {
-    const ScoreGeom g0 = score_geom(H, W, d, B, r, nimg, 0);
-    if (g0.smem > 200 * 1024 || g0.TCp > 256 || g0.TR > 256) return cudaErrorNotSupported;  // nothing enqueued
-    alignas(64) CUtensorMap tmap;
-    cudaError_t err = make_tmap_u8_3d(&tmap, bins, (uint64_t)pitch, (uint64_t)H, (uint64_t)nimg * d, (uint64_t)pitch,
-                                      (uint64_t)H * pitch, (uint32_t)g0.TCp, (uint32_t)g0.TR);
-    if (err != cudaSuccess) return err;
+                            const uint32_t *ref_hist, uint32_t ref_total, float *score, uint64_t *numer_out,
+                            void *ws, bool ws_accumulates, int *status, cudaStream_t st, const ScoreTiling *tiling) {
     // u32 walk when every partial and the numerator fit: (B-1) (2r+1)^2 N_ref < 2^32
-    const double bound = (double)(B - 1) * (double)((2 * r + 1) * (2 * r + 1)) * (double)ref_total;
-    const bool narrow = bound < 4294967295.0 && (double)(2 * r + 1) * (2 * r + 1) * ref_total < 4294967295.0;
+    const double span2 = (double)(2 * r + 1) * (2 * r + 1);
+    const bool narrow = (double)(B - 1) * span2 * (double)ref_total < 4294967295.0 && span2 * ref_total < 4294967295.0;
+    const EmdKind kind = !narrow ? EmdKind::U64_U64
+                         : (numer_out || ws_accumulates) ? EmdKind::U32_U64 : EmdKind::U32_U32;
+    const int KB = (B == 32 || B == 64) ? B : 0;
     static int attr_dev = -1, n_sm = 0;
     int dev = 0;
-    cudaGetDevice(&dev);
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
     if (attr_dev != dev) {
-        err = cudaFuncSetAttribute(k_window_emd<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (err == cudaSuccess)
-            err = cudaFuncSetAttribute(k_window_emd<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       200 * 1024);
+        err = emd_set_smem_attr<uint32_t, uint32_t>();
+        if (err == cudaSuccess) err = emd_set_smem_attr<uint32_t, unsigned long long>();
+        if (err == cudaSuccess) err = emd_set_smem_attr<unsigned long long, unsigned long long>();
         if (err == cudaSuccess) err = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         if (err != cudaSuccess) return err;
         attr_dev = dev;
     }
-    int per_sm = 0;
-    err = narrow ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_window_emd<uint32_t>, kSW, g0.smem)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_window_emd<unsigned long long>, kSW,
-                                                                 g0.smem);
+    // geometry: the caller's tiling, else the modelled best over strip widths, band heights and splits
+    ScoreGeom g{};
+    bool have = false;
+    if (tiling && tiling->SW > 0) {
+        g = make_geom(H, W, d, B, r, nimg, tiling->SW, tiling->TH, tiling->n_kg);
+        have = geom_ok(g) && (g.SW == 64 || g.SW == 128) && g.TH >= 1 && g.TH <= 64 && (long)g.n_kg * nimg <= 65535;
+        if (!have) return cudaErrorNotSupported;
+    } else {
+        double best = 1e300;
+        for (int SW : {128, 64})
+            for (int TH : {16, 32, 8}) {
+                const ScoreGeom g0 = make_geom(H, W, d, B, r, nimg, SW, TH, 1);
+                if (!geom_ok(g0)) continue;
+                int per_sm = 0;
+                err = emd_occupancy_kind(kind, KB, g0.smem, SW, &per_sm);
+                if (err != cudaSuccess) return err;
+                if (per_sm < 1) continue;
+                const long slots = (long)per_sm * n_sm;
+                const long tiles = (long)((W + SW - 1) / SW) * ((H + TH - 1) / TH) * nimg;
+                for (int n = 1; n <= d && (long)n * nimg <= 65535; n++) {
+                    const ScoreGeom gn = make_geom(H, W, d, B, r, nimg, SW, TH, n);
+                    if (gn.n_kg != n) continue;
+                    const double waves = (double)((tiles * n + slots - 1) / slots);
+                    const double cost = waves * cta_cost(gn, B, r);
+                    if (cost < best * 0.999) best = cost, g = gn, have = true;
+                }
+            }
+        if (!have) return cudaErrorNotSupported;  // nothing enqueued
+    }
+    alignas(64) CUtensorMap tmap;
+    err = make_tmap_u8_3d(&tmap, bins, (uint64_t)pitch, (uint64_t)H, (uint64_t)nimg * d, (uint64_t)pitch,
+                          (uint64_t)H * pitch, (uint32_t)g.TCp, (uint32_t)g.TR);
     if (err != cudaSuccess) return err;
-    const ScoreGeom g = score_geom(H, W, d, B, r, nimg, (long)max(per_sm, 1) * n_sm);
-    unsigned long long *acc = (unsigned long long *)ws;
-    if (g.n_kg > 1) err = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (size_t)H * W * nimg, st);
+    unsigned long long *accum = ws_accumulates ? (unsigned long long *)ws : nullptr;
+    if (accum) err = cudaMemsetAsync(accum, 0, sizeof(unsigned long long) * (size_t)H * W * nimg, st);
     if (err != cudaSuccess) return err;
-    dim3 grid((W + kSW - 1) / kSW, (H + g.TH - 1) / g.TH, g.n_kg * nimg);
-    if (narrow)
-        QFCA_LAUNCH("k_window_emd", st,
-                    k_window_emd<uint32_t><<<grid, kSW, g.smem, st>>>(tmap, H, W, d, B, r, g, ref_hist, ref_total, acc,
-                                                                       numer, status));
-    else
-        QFCA_LAUNCH("k_window_emd", st,
-                    k_window_emd<unsigned long long><<<grid, kSW, g.smem, st>>>(tmap, H, W, d, B, r, g, ref_hist,
-                                                                                 ref_total, acc, numer, status));
+    const dim3 grid((W + g.SW - 1) / g.SW, (H + g.TH - 1) / g.TH, g.n_kg * nimg);
     const long N = (long)H * W;
-    QFCA_LAUNCH("k_finalize", st,
-                k_finalize<<<dim3((unsigned)((N + 255) / 256), nimg), 256, 0, st>>>(acc, H, W, r, d, ref_total, score));
+    const dim3 fgrid((unsigned)((N + 255) / 256), nimg);
+    switch (kind) {
+    case EmdKind::U32_U32: {
+        uint32_t *nm = (uint32_t *)ws;
+        launch_emd_kb<uint32_t, uint32_t>(KB, g, grid, st, tmap, H, W, d, B, r, ref_hist, ref_total, nm, nullptr,
+                                          status);
+        QFCA_LAUNCH("k_finalize", st,
+                    k_finalize<uint32_t><<<fgrid, 256, 0, st>>>(nm, nullptr, H, W, r, d, ref_total, score));
+        break;
+    }
+    case EmdKind::U32_U64: {
+        unsigned long long *nm = accum ? nullptr : (unsigned long long *)(numer_out ? (void *)numer_out : ws);
+        launch_emd_kb<uint32_t, unsigned long long>(KB, g, grid, st, tmap, H, W, d, B, r, ref_hist, ref_total, nm,
+                                                    accum, status);
+        QFCA_LAUNCH("k_finalize", st,
+                    k_finalize<unsigned long long><<<fgrid, 256, 0, st>>>(nm, accum, H, W, r, d, ref_total, score));
+        break;
+    }
+    default: {
+        unsigned long long *nm = accum ? nullptr : (unsigned long long *)(numer_out ? (void *)numer_out : ws);
+        launch_emd_kb<unsigned long long, unsigned long long>(KB, g, grid, st, tmap, H, W, d, B, r, ref_hist,
+                                                              ref_total, nm, accum, status);
+        QFCA_LAUNCH("k_finalize", st,
+                    k_finalize<unsigned long long><<<fgrid, 256, 0, st>>>(nm, accum, H, W, r, d, ref_total, score));
+        break;
+    }
+    }
     return cudaGetLastError();
 }
 
@@ -355,7 +472,7 @@ extern "C" qfca_status qfca_score_noalloc(const uint8_t *bins, int H, int W, int
         acc = g_noalloc_ptr[dev];
     }
     const cudaError_t e = launch_score_ws(bins, H, W, pitch, d, 1, B, r, ref_hist, ref_total, score, nullptr, acc,
-                                          g_noalloc_status[dev], (cudaStream_t)stream);
+                                          true, g_noalloc_status[dev], (cudaStream_t)stream, nullptr);
     if (e == cudaErrorNotSupported) return QFCA_ERR_UNSUPPORTED;
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -10,6 +10,14 @@ namespace tc {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Round a pointer into dynamic shared memory up to an A-byte boundary by
+// pointer arithmetic, so the compiler still knows it points to shared memory
+// (a round trip through an integer would turn every access into a generic one).
+template <int A>
+__device__ __forceinline__ unsigned char *align_smem(unsigned char *p) {
+    return p + ((A - (smem_u32(p) & (A - 1))) & (A - 1));
+}
+
 // ---------------------------------------------------------------- mbarrier
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {

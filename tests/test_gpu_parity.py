@@ -65,6 +65,47 @@ def test_score_bit_exact_numerators(q, d, H, W, B, r, seed):
     np.testing.assert_allclose(s_g.cpu().numpy(), s_o, rtol=2.0 ** -23, atol=1e-12)
 
 
+@pytest.mark.parametrize("d,H,W,B,r,seed", [
+    (2, 192, 200, 255, 12, 0),   # (B-1)(2r+1)^2 N_ref >= 2^32: 64-bit CDF walk
+    (1, 600, 610, 255, 63, 1),   # widest window; N_ref (2r+1)^2 >= 2^32; narrow strips
+    (3, 300, 260, 64, 9, 2),     # compile-time B = 64 path with ragged bands and strips
+])
+def test_score_wide_and_large_windows_sampled(q, d, H, W, B, r, seed):
+    # exact numerators at sampled pixels (corners, edges, interior), each
+    # computed one by one by the oracle
+    rng = np.random.default_rng(100 + seed)
+    qb = synth.random_bins(rng, d, H, W, B, smooth=True)
+    R = oracle.ref_hist(qb, B)
+    bins = torch.zeros(d, H, q.bins_pitch(W), dtype=torch.uint8, device="cuda")
+    bins[:, :, :W] = to_dev(qb)
+    s_g, num_g = q.score(bins, W, B, r, to_dev(R.astype(np.int32)), H * W, want_numer=True)
+    torch.cuda.synchronize()
+    s_g, num_g = s_g.cpu().numpy(), num_g.cpu().numpy()
+    pts = [(0, 0), (0, W - 1), (H - 1, 0), (H - 1, W - 1), (r, r), (H // 2, W // 2)]
+    pts += [(int(y), int(x)) for y, x in zip(rng.integers(0, H, 40), rng.integers(0, W, 40))]
+    for y, x in pts:
+        s_o, n_o = oracle.score_at(qb, B, r, R, H * W, y, x)
+        np.testing.assert_array_equal(num_g[:, y, x].astype(np.int64), n_o)
+        assert abs(s_g[y, x] - s_o) <= 2.0 ** -23 * abs(s_o) + 1e-12
+
+
+def test_score_bins_above_range_clamp_to_last_bin(q):
+    # input bins >= B count as bin B-1 (documented for qfca_score)
+    d, H, W, B, r = 2, 40, 70, 16, 3
+    rng = np.random.default_rng(7)
+    qb = synth.random_bins(rng, d, H, W, B, smooth=False)
+    raw = qb.copy()
+    hi = rng.random((d, H, W)) < 0.2
+    raw[hi & (qb == B - 1)] = rng.integers(B, 256, size=int(np.sum(hi & (qb == B - 1))))
+    R = oracle.ref_hist(qb, B)
+    _, num_o, _ = oracle.score(qb, B, r, R, H * W)
+    bins = torch.zeros(d, H, q.bins_pitch(W), dtype=torch.uint8, device="cuda")
+    bins[:, :, :W] = to_dev(raw)
+    _, num_g = q.score(bins, W, B, r, to_dev(R.astype(np.int32)), H * W, want_numer=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(num_g.cpu().numpy(), num_o)
+
+
 def test_score_external_reference_point_masses(q):
     # reference = point mass at bin 9 (mass 1000), map = constant bin 2: EMD = 7 everywhere
     d, H, W, B, r = 2, 20, 30, 16, 3

@@ -117,6 +117,31 @@ def test_brute_force_8x8_against_quantile_integral_and_scipy(seed):
             assert abs(s[y, x] - np.mean(emds)) < 1e-12
 
 
+@pytest.mark.parametrize("seed", [0, 1])
+def test_score_at_against_scipy_and_point_masses(seed):
+    # one pixel at a time: W1 of the clipped window against the image (scipy),
+    # and point masses at bin distance |a - b|
+    scipy_stats = pytest.importorskip("scipy.stats")
+    rng = np.random.default_rng(10 + seed)
+    d, H, W, B, r = 2, 9, 11, 7, 3
+    q = rng.integers(0, B, size=(d, H, W)).astype(np.uint8)
+    R = oracle.ref_hist(q, B)
+    for y, x in [(0, 0), (4, 5), (8, 10), (2, 9)]:
+        s, numer = oracle.score_at(q, B, r, R, H * W, y, x)
+        emds = []
+        for k in range(d):
+            win = brute_window(q[k], r, y, x)
+            w = scipy_stats.wasserstein_distance(win.astype(float), q[k].ravel().astype(float))
+            assert abs(numer[k] / (win.size * H * W) - w) < 1e-12
+            emds.append(w)
+        assert abs(s - np.mean(emds)) < 1e-12
+    qa = np.full((1, 5, 6), 2, np.uint8)
+    Rb = np.zeros((1, 16), np.uint32)
+    Rb[0, 11] = 77
+    s, numer = oracle.score_at(qa, 16, 2, Rb, 77, 0, 5)
+    assert s == 9.0 and numer[0] == 9 * (3 * 3) * 77
+
+
 def test_equal_mass_sort_and_match():
     # window of 81 pixels against an external reference of mass 81:
     # W1 = (1/81) sum_i |sorted(window)_i - sorted(ref)_i|  (textbook equal-mass form)
