@@ -366,9 +366,10 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
     if (ref_total < 1) return fail(ctx, QFCA_ERR_INVALID_ARG, "ref_total must be >= 1");
     DeviceGuard g(ctx->device);
     HookScope hs(ctx);
-    if ((s = ensure_ws(ctx, score_workspace_bytes(H, W, d, 1)))) return s;
-    cudaError_t e = launch_score_ws(bins, H, W, pitch, d, 1, B, r, ref_hist, ref_total, score, numer_out, ctx->ws,
-                                    false, ctx->status_dev, (cudaStream_t)stream, nullptr);
+    const ScoreJob job{bins, H, W, pitch, r, ref_hist, ref_total, score, numer_out};
+    if ((s = ensure_ws(ctx, score_jobs_workspace_bytes(&job, 1, d)))) return s;
+    cudaError_t e = launch_score_jobs(&job, 1, d, B, ctx->ws, false, ctx->status_dev, (cudaStream_t)stream,
+                                      nullptr, nullptr);
     if (e == cudaErrorNotSupported)
         return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d needs more shared memory than a CTA has", B, r);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_score");
@@ -412,7 +413,9 @@ qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap de
     const size_t o_bins = take((size_t)d * desc.H * pitch * nimg);
     const size_t o_hist = take(sizeof(uint32_t) * (size_t)d * B * nimg);
     const size_t o_lohi = take(sizeof(float) * 2 * (size_t)d * nimg);
-    const size_t o_sc = take(score_workspace_bytes(desc.H, desc.W, d, nimg));
+    std::vector<ScoreJob> jobs((size_t)nimg);
+    for (int i = 0; i < nimg; i++) jobs[i] = ScoreJob{nullptr, desc.H, desc.W, pitch, r, nullptr, (uint32_t)N, nullptr, nullptr};
+    const size_t o_sc = take(score_jobs_workspace_bytes(jobs.data(), nimg, d));
     if ((s = ensure_ws(ctx, o))) return s;
     char *b = (char *)ctx->ws;
     double *mean = (extra && extra->mean) ? extra->mean : (double *)(b + o_mean);
@@ -435,8 +438,12 @@ qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap de
     e = launch_quantize(Y, N, desc.H, desc.W, d, nimg, B, QFCA_RANGE_IMAGE, mm, nullptr, nullptr, bins, pitch, lo, hi,
                         hist, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run/quantize");
-    e = launch_score_ws(bins, desc.H, desc.W, pitch, d, nimg, B, r, hist, (uint32_t)N, scores, nullptr, b + o_sc,
-                        false, ctx->status_dev, st, nullptr);
+    for (int i = 0; i < nimg; i++) {
+        jobs[i].bins = bins + (size_t)i * d * desc.H * pitch;
+        jobs[i].ref = hist + (size_t)i * d * B;
+        jobs[i].score = scores + (size_t)i * N;
+    }
+    e = launch_score_jobs(jobs.data(), nimg, d, B, b + o_sc, false, ctx->status_dev, st, nullptr, nullptr);
     if (e == cudaErrorNotSupported)
         return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d needs more shared memory than a CTA has", B, r);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run/score");

@@ -70,8 +70,21 @@ cudaError_t launch_quantize(const float *Y, long N, int H, int W, int d, int nim
 
 // ------------------------------------------------------------------ score (score.cu)
 
-// Workspace of launch_score_ws in per-component mode: the numerators D_k(p).
-size_t score_workspace_bytes(int H, int W, int d, int nimg);
+// Images per launch of the table-driven stages (the table travels in the
+// kernel's parameter block).
+constexpr int kMaxBatch = 64;
+
+// One image of a score launch: bins [d][H][pitch] (16-B aligned, pitch a
+// multiple of 16), reference [d][B] with N_ref = Nref, score [H][W],
+// numer_out [d][H][W] u64 (optional).
+struct ScoreJob {
+    const uint8_t *bins;
+    int H, W, pitch, r;
+    const uint32_t *ref;
+    uint32_t Nref;
+    float *score;
+    uint64_t *numer_out;
+};
 
 // Tiling of the window-EMD kernel: strip width SW (64 or 128 threads), band
 // height TH (1..64 rows) and number of component groups n_kg.
@@ -79,14 +92,18 @@ struct ScoreTiling {
     int SW, TH, n_kg;
 };
 
-// bins [nimg][d][H][pitch], ref_hist [nimg][d][B], score [nimg][H][W], numer_out [nimg][d][H][W] (optional).
-// ws: the per-component numerators (score_workspace_bytes) or, when
-// ws_accumulates, their per-pixel sums u64 [nimg][H][W].  tiling NULL: the
-// built-in model picks one.  cudaErrorNotSupported: nothing was enqueued.
-cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d, int nimg, int B, int r,
-                            const uint32_t *ref_hist, uint32_t ref_total, float *score, uint64_t *numer_out,
-                            void *ws, bool ws_accumulates, int *status, cudaStream_t st,
-                            const ScoreTiling *tiling);
+// Workspace of launch_score_jobs: the numerators D_k(p) of every job (or, when
+// accumulating, their per-pixel sums).
+size_t score_jobs_workspace_bytes(const ScoreJob *jobs, int n, int d);
+
+// True when some tiling fits B bins and radius r in shared memory.
+bool score_shape_ok(int B, int r);
+
+// Window EMD + score of n images (one launch per kMaxBatch images).  tiling
+// NULL: the built-in cost model picks one (written to *chosen when given).
+// cudaErrorNotSupported: nothing was enqueued.
+cudaError_t launch_score_jobs(const ScoreJob *jobs, int n, int d, int B, void *ws, bool ws_accumulates, int *status,
+                              cudaStream_t st, const ScoreTiling *tiling, ScoreTiling *chosen);
 
 // ------------------------------------------------------------------ TMA (tmap.cu)
 

@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cmath>
 #include <mutex>
 
 #include "internal.cuh"
@@ -31,70 +33,95 @@ namespace {
 constexpr int kMaxSW = 128;  // strip width limit (threads per CTA)
 constexpr uint32_t kTmaTries = 1u << 26;
 
-struct ScoreGeom {
-    int SW, TH, TR, halo, TCp, kg, n_kg;  // TCp: TMA box width (bytes), halo: left margin (16-B aligned)
-    size_t smem, tile_bytes;
+// Per-image part of a window-EMD launch (kernel parameter block).
+struct ScoreImgP {
+    int H, W, r, nbx;        // nbx: strips
+    long cta0;               // first CTA of this image
+    const uint32_t *ref;     // [d][B]
+    uint32_t Nref;
+    void *numer;             // [d][H][W] of OUT, or NULL when accumulating
+    unsigned long long *accum;  // [H][W] running sums, or NULL
 };
 
-ScoreGeom make_geom(int H, int W, int d, int B, int r, int nimg, int SW, int TH, int n_kg) {
-    (void)H, (void)W, (void)nimg;
-    ScoreGeom g;
-    g.SW = SW;
-    g.TH = TH;
-    g.TR = TH + 2 * r;
-    g.halo = (int)align_up(r, 16);
-    g.TCp = SW + 2 * g.halo;
-    n_kg = n_kg < 1 ? 1 : (n_kg > d ? d : n_kg);
-    g.kg = (d + n_kg - 1) / n_kg;
-    g.n_kg = (d + g.kg - 1) / g.kg;
-    g.tile_bytes = align_up((size_t)g.TR * g.TCp, 128);
-    g.smem = 128                                   // alignment slack
-             + 2 * g.tile_bytes                    // bin tiles (double buffer, TMA)
-             + sizeof(uint32_t) * (size_t)(B + 1) * SW  // histograms [B+1][SW], row 0 = outside
-             + sizeof(uint32_t) * 256              // cumR
-             + sizeof(uint64_t) * 256              // cumR * N_loc of an interior window
-             + 2 * sizeof(uint64_t);               // mbarriers
-    return g;
+struct ScoreParams {
+    int n, d, B, SW, TH, kg, n_kg;
+    uint32_t tile_bytes;
+    ScoreImgP img[kMaxBatch];
+    CUtensorMap tmap[kMaxBatch];  // bins of image i as [d][H][pitch] u8, box {TCp_i, TH + 2 r_i, 1}
+};
+
+struct FinImgP {
+    int H, W, r;
+    uint32_t Nref;
+    long blk0;               // first pixel block of this image
+    const void *numer;
+    const unsigned long long *accum;
+    float *score;
+};
+
+struct FinParams {
+    int n, d;
+    FinImgP img[kMaxBatch];
+};
+
+__host__ __device__ inline int halo_of(int r) { return (r + 15) & ~15; }
+__host__ __device__ inline int tcp_of(int SW, int r) { return SW + 2 * halo_of(r); }
+
+size_t score_smem(int SW, int TH, int B, int rmax) {
+    const size_t tile = align_up((size_t)(TH + 2 * rmax) * tcp_of(SW, rmax), 128);
+    return 128 + 2 * tile + sizeof(uint32_t) * (size_t)(B + 1) * SW + sizeof(uint32_t) * 256 +
+           sizeof(uint64_t) * 256 + 2 * sizeof(uint64_t);
 }
 
-bool geom_ok(const ScoreGeom &g) { return g.smem <= 200 * 1024 && g.TCp <= 256 && g.TR <= 256; }
-
 // Window histograms + exact EMD numerators for a band of TH rows x SW columns
-// and a group of components.  Thread t owns output column x0 + t; its window
-// histogram lives at hist[b * SW + t].  Increments are shared-memory atomics
-// without return, so no thread waits on them.  ACC is the type of the CDF
-// walk (u32 when (B-1)(2r+1)^2 N_ref < 2^32), OUT the type of the stored
-// numerators; KB > 0 fixes B at compile time.
+// and a group of kg components of one image of the table.  Thread t owns
+// output column x0 + t; its window histogram lives at hist[b * SW + t].
+// Increments are shared-memory atomics without return, so no thread waits on
+// them.  ACC is the type of the CDF walk (u32 when (B-1)(2r+1)^2 N_ref < 2^32
+// for every image), OUT the type of the stored numerators; KB > 0 fixes B at
+// compile time.  The band's bin tile of each component (rows y0-r ..
+// y0+TH-1+r, columns from x0 - halo, halo = r rounded up to 16 bytes) is one
+// 3-D TMA box; boxes are double-buffered so the next component's tile arrives
+// while the current one is processed.  Waits are bounded; a wait that runs out
+// sets bit 0 of the status word and the CTA stops.
 template <typename ACC, typename OUT, int KB>
-__global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ CUtensorMap tmap, int H, int W, int d,
-                                                        int Bdyn, int r, ScoreGeom g,
-                                                        const uint32_t *__restrict__ ref_hist, uint32_t Nref,
-                                                        OUT *__restrict__ numer, unsigned long long *__restrict__ accum,
-                                                        int *__restrict__ status) {
-    const int B = KB > 0 ? KB : Bdyn;
-    const int SW = g.SW;
+__global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ ScoreParams p, int *__restrict__ status) {
+    const int B = KB > 0 ? KB : p.B;
+    const int SW = p.SW, TH = p.TH, d = p.d;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *smem = tc::align_smem<128>(smem_raw);
     uint8_t *tiles = smem;
-    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + 2 * g.tile_bytes);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + 2 * (size_t)p.tile_bytes);
     uint32_t *cumR = hist + (size_t)(B + 1) * SW;
     ACC *cRi = reinterpret_cast<ACC *>(cumR + 256);  // cumR[b] * N_loc for an interior window
     uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(cumR + 256) + 256 * sizeof(uint64_t));
 
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = SW >> 5;
-    const int x0 = blockIdx.x * SW, y0 = blockIdx.y * g.TH;
-    const int x = x0 + t;
-    const long img = blockIdx.z / g.n_kg;
-    const int k0 = (blockIdx.z % g.n_kg) * g.kg, k1 = min(d, k0 + g.kg);
-    ref_hist += img * d * B;
+    // which image, component group, band and strip
+    const long cta = blockIdx.x;
+    int ii = 0;
+    while (ii + 1 < p.n && p.img[ii + 1].cta0 <= cta) ii++;
+    const ScoreImgP &im = p.img[ii];
+    const CUtensorMap *tmap = &p.tmap[ii];
+    const int H = im.H, W = im.W, r = im.r;
+    long local = cta - im.cta0;
+    const int kgi = (int)(local % p.n_kg);
+    local /= p.n_kg;
+    const int bx = (int)(local % im.nbx), by = (int)(local / im.nbx);
+    const int k0 = kgi * p.kg, k1 = min(d, k0 + p.kg);
+    const uint32_t Nref = im.Nref;
+    const uint32_t *ref_hist = im.ref;
     const long HW = (long)H * W;
 
-    const int ty0 = y0 - r, tx0 = x0 - g.halo;  // image coordinates of the tile origin
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = SW >> 5;
+    const int x0 = bx * SW, y0 = by * TH;
+    const int x = x0 + t;
+    const int halo = halo_of(r), TCp = SW + 2 * halo, TR = TH + 2 * r;
+    const int ty0 = y0 - r, tx0 = x0 - halo;  // image coordinates of the tile origin
     const int span = 2 * r + 1;
     const uint32_t Nint = (uint32_t)(span * span);
-    const uint32_t box_bytes = (uint32_t)(g.TR * g.TCp);
-    const int wpr = g.TCp >> 2;  // 32-bit words per tile row
-    const bool inner = tx0 >= 0 && tx0 + g.TCp <= W && ty0 >= 0 && ty0 + g.TR <= H;
+    const uint32_t box_bytes = (uint32_t)(TR * TCp);
+    const int wpr = TCp >> 2;  // 32-bit words per tile row
+    const bool inner = tx0 >= 0 && tx0 + TCp <= W && ty0 >= 0 && ty0 + TR <= H;
     if (t == 0) {
         tc::mbar_init(&bar[0], 1);
         tc::mbar_init(&bar[1], 1);
@@ -103,21 +130,20 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ C
     __syncthreads();
     if (t == 0 && k0 < k1) {
         tc::mbar_arrive_expect_tx(&bar[0], box_bytes);
-        tc::tma_load_3d(tiles, &tmap, tx0, ty0, (int)(img * d + k0), &bar[0]);
+        tc::tma_load_3d(tiles, tmap, tx0, ty0, k0, &bar[0]);
     }
     bool failed = false;
     int issued = k0 < k1 ? 1 : 0, waited = 0;
 
     const int ncols = min(W - 1, x + r) - max(0, x - r) + 1;
-    const int c0 = t + g.halo - r;  // tile column of this thread's window's left edge
+    const int c0 = t + halo - r;  // tile column of this thread's window's left edge
     uint32_t *hc = hist + t;
     for (int k = k0; k < k1; k++) {
         __syncthreads();  // the buffer of component k-1 is free again
         const int buf = (k - k0) & 1;
         if (t == 0 && k + 1 < k1) {
             tc::mbar_arrive_expect_tx(&bar[buf ^ 1], box_bytes);
-            tc::tma_load_3d(tiles + (size_t)(buf ^ 1) * g.tile_bytes, &tmap, tx0, ty0, (int)(img * d + k + 1),
-                            &bar[buf ^ 1]);
+            tc::tma_load_3d(tiles + (size_t)(buf ^ 1) * p.tile_bytes, tmap, tx0, ty0, k + 1, &bar[buf ^ 1]);
         }
         if (k + 1 < k1) issued++;
         // warp 0: lane l loads reference bins [8l, 8l+8) of component k (in flight during the wait)
@@ -135,12 +161,12 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ C
             failed = true;
             break;
         }
-        uint8_t *tile = tiles + (size_t)buf * g.tile_bytes;
+        uint8_t *tile = tiles + (size_t)buf * p.tile_bytes;
         // in-image bytes -> min(bin, B-1) + 1, everything else -> 0; a warp per tile row
         {
             uint32_t *tw = reinterpret_cast<uint32_t *>(tile);
             const uint32_t cap = 0x01010101u * (uint32_t)(B - 1);
-            for (int row = warp; row < g.TR; row += nwarps) {
+            for (int row = warp; row < TR; row += nwarps) {
                 const int gy = ty0 + row;
                 const bool rin = gy >= 0 && gy < H;
                 for (int j = lane; j < wpr; j += 32) {
@@ -187,16 +213,16 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ C
         if (x < W) {
             // window of the band's first row: tile rows 0 .. 2r
             for (int ry = 0; ry < span; ry++) {
-                const uint8_t *row = tile + ry * g.TCp + c0;
+                const uint8_t *row = tile + ry * TCp + c0;
 #pragma unroll 4
                 for (int j = 0; j < span; j++) atomicAdd(hc + row[j] * SW, 1u);
             }
-            for (int i = 0; i < g.TH; i++) {
+            for (int i = 0; i < TH; i++) {
                 const int yy = y0 + i;
                 if (yy >= H) break;
                 if (i > 0) {
-                    const uint8_t *ro = tile + (i - 1) * g.TCp + c0;       // image row yy - r - 1
-                    const uint8_t *rn = tile + (i + 2 * r) * g.TCp + c0;   // image row yy + r
+                    const uint8_t *ro = tile + (i - 1) * TCp + c0;       // image row yy - r - 1
+                    const uint8_t *rn = tile + (i + 2 * r) * TCp + c0;   // image row yy + r
 #pragma unroll 4
                     for (int j = 0; j < span; j++) {
                         atomicSub(hc + ro[j] * SW, 1u);
@@ -234,8 +260,8 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ C
                     }
                 }
                 const long pix = (long)yy * W + x;
-                if (accum) atomicAdd(&accum[img * HW + pix], (unsigned long long)D);
-                else numer[(img * d + k) * HW + pix] = (OUT)D;
+                if (im.accum) atomicAdd(&im.accum[pix], (unsigned long long)D);
+                else reinterpret_cast<OUT *>(im.numer)[(long)k * HW + pix] = (OUT)D;
             }
         }
         tc::fence_proxy_async_smem();  // this iteration's writes to the tile precede the next TMA write into it
@@ -247,46 +273,41 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ C
     }
 }
 
-// Grid (pixels, images): s(p) = sum_k D_k(p) / (d * N_loc * N_ref), from the
-// per-component numerators or from their running sums.
+// s(p) = sum_k D_k(p) / (d * N_loc * N_ref), from the per-component numerators
+// or from their running sums; blocks of 256 pixels over the table's images.
 template <typename OUT>
-__global__ void k_finalize(const OUT *__restrict__ numer, const unsigned long long *__restrict__ accum, int H, int W,
-                           int r, int d, uint32_t Nref, float *__restrict__ score) {
-    const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long HW = (long)H * W;
-    if (p >= HW) return;
-    const long img = blockIdx.y;
+__global__ void __launch_bounds__(256) k_finalize(const __grid_constant__ FinParams p) {
+    const long blk = blockIdx.x;
+    int ii = 0;
+    while (ii + 1 < p.n && p.img[ii + 1].blk0 <= blk) ii++;
+    const FinImgP &im = p.img[ii];
+    const long HW = (long)im.H * im.W;
+    const long q = (blk - im.blk0) * 256 + threadIdx.x;
+    if (q >= HW) return;
+    const int d = p.d;
     unsigned long long s = 0;
-    if (accum) {
-        s = accum[img * HW + p];
+    if (im.accum) {
+        s = im.accum[q];
     } else {
-        const OUT *nk = numer + img * d * HW + p;
+        const OUT *nk = reinterpret_cast<const OUT *>(im.numer) + q;
         for (int k = 0; k < d; k++) s += (unsigned long long)__ldg(nk + (long)k * HW);
     }
-    const int y = (int)(p / W), x = (int)(p - (long)y * W);
-    const int nr = min(H - 1, y + r) - max(0, y - r) + 1;
-    const int nc = min(W - 1, x + r) - max(0, x - r) + 1;
-    const double den = (double)nr * (double)nc * (double)Nref * (double)d;
-    score[img * HW + p] = (float)((double)s / den);
+    const int y = (int)(q / im.W), x = (int)(q - (long)y * im.W);
+    const int r = im.r;
+    const int nr = min(im.H - 1, y + r) - max(0, y - r) + 1;
+    const int nc = min(im.W - 1, x + r) - max(0, x - r) + 1;
+    const double den = (double)nr * (double)nc * (double)im.Nref * (double)d;
+    im.score[q] = (float)((double)s / den);
 }
 
 template <typename ACC, typename OUT>
-cudaError_t launch_emd_kb(int KB, const ScoreGeom &g, dim3 grid, cudaStream_t st, const CUtensorMap &tmap, int H,
-                          int W, int d, int B, int r, const uint32_t *ref_hist, uint32_t Nref, OUT *numer,
-                          unsigned long long *accum, int *status) {
+void launch_emd_kb(int KB, long grid, size_t smem, int SW, cudaStream_t st, const ScoreParams &p, int *status) {
     if (KB == 32)
-        QFCA_LAUNCH("k_window_emd", st,
-                    (k_window_emd<ACC, OUT, 32><<<grid, g.SW, g.smem, st>>>(tmap, H, W, d, B, r, g, ref_hist, Nref,
-                                                                             numer, accum, status)));
+        QFCA_LAUNCH("k_window_emd", st, (k_window_emd<ACC, OUT, 32><<<(unsigned)grid, SW, smem, st>>>(p, status)));
     else if (KB == 64)
-        QFCA_LAUNCH("k_window_emd", st,
-                    (k_window_emd<ACC, OUT, 64><<<grid, g.SW, g.smem, st>>>(tmap, H, W, d, B, r, g, ref_hist, Nref,
-                                                                             numer, accum, status)));
+        QFCA_LAUNCH("k_window_emd", st, (k_window_emd<ACC, OUT, 64><<<(unsigned)grid, SW, smem, st>>>(p, status)));
     else
-        QFCA_LAUNCH("k_window_emd", st,
-                    (k_window_emd<ACC, OUT, 0><<<grid, g.SW, g.smem, st>>>(tmap, H, W, d, B, r, g, ref_hist, Nref,
-                                                                            numer, accum, status)));
-    return cudaSuccess;
+        QFCA_LAUNCH("k_window_emd", st, (k_window_emd<ACC, OUT, 0><<<(unsigned)grid, SW, smem, st>>>(p, status)));
 }
 
 template <typename ACC, typename OUT>
@@ -317,108 +338,182 @@ cudaError_t emd_occupancy_kind(EmdKind kind, int KB, size_t smem, int SW, int *p
     }
 }
 
-// Modelled cost (in lane-instructions) of one CTA and the choice of strip
-// width, band height and component split that finishes the grid soonest.
-double cta_cost(const ScoreGeom &g, int B, int r) {
-    const int span = 2 * r + 1;
+// Modelled cost (lane-instructions) of the CTAs of one image at a given tiling.
+double image_cost(int H, int W, int d, int B, int r, int SW, int TH, int kg, int n_kg) {
+    const int span = 2 * r + 1, TR = TH + 2 * r;
     const double row = 2.0 * span * 3.0 + 5.0 * (B - 1) + 12.0;
-    const double setup = 3.0 * span * span + 6.0 * g.TR * g.TCp / (4.0 * g.SW) + 2.0 * B + 60.0;
-    return g.kg * (g.TH * row + setup) + 200.0;
+    const double setup = 3.0 * span * span + 6.0 * TR * tcp_of(SW, r) / (4.0 * SW) + 2.0 * B + 60.0;
+    const double ctas = (double)((W + SW - 1) / SW) * ((H + TH - 1) / TH) * n_kg;
+    (void)d;
+    return ctas * (kg * (TH * row + setup) + 200.0);
+}
+
+int g_attr_dev = -1, g_n_sm = 0;
+std::mutex g_attr_mu;
+
+cudaError_t ensure_attrs(int *n_sm) {
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (g_attr_dev != dev) {
+        err = emd_set_smem_attr<uint32_t, uint32_t>();
+        if (err == cudaSuccess) err = emd_set_smem_attr<uint32_t, unsigned long long>();
+        if (err == cudaSuccess) err = emd_set_smem_attr<unsigned long long, unsigned long long>();
+        if (err == cudaSuccess) err = cudaDeviceGetAttribute(&g_n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (err != cudaSuccess) return err;
+        g_attr_dev = dev;
+    }
+    *n_sm = g_n_sm;
+    return cudaSuccess;
+}
+
+// One launch of at most kMaxBatch jobs.
+cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, bool ws_accumulates, int *status,
+                        cudaStream_t st, const ScoreTiling *tiling, ScoreTiling *chosen) {
+    int rmax = 1;
+    bool narrow = true, want_numer = false;
+    for (int i = 0; i < n; i++) {
+        const double span2 = (double)(2 * jobs[i].r + 1) * (2 * jobs[i].r + 1);
+        // u32 walk when every partial and the numerator fit: (B-1) (2r+1)^2 N_ref < 2^32
+        narrow = narrow && (double)(B - 1) * span2 * (double)jobs[i].Nref < 4294967295.0 &&
+                 span2 * jobs[i].Nref < 4294967295.0;
+        want_numer = want_numer || jobs[i].numer_out;
+        rmax = std::max(rmax, jobs[i].r);
+    }
+    const EmdKind kind = !narrow ? EmdKind::U64_U64
+                         : (want_numer || ws_accumulates) ? EmdKind::U32_U64 : EmdKind::U32_U32;
+    const size_t out_bytes = kind == EmdKind::U32_U32 ? 4 : 8;
+    const int KB = (B == 32 || B == 64) ? B : 0;
+    int n_sm = 0;
+    cudaError_t err = ensure_attrs(&n_sm);
+    if (err != cudaSuccess) return err;
+
+    // tiling: the caller's, else the modelled best over strip widths, band heights and component splits
+    ScoreTiling best{0, 0, 0};
+    if (tiling && tiling->SW > 0) {
+        best = *tiling;
+        if (!(best.SW == 64 || best.SW == 128) || best.TH < 1 || best.TH > 64 || best.n_kg < 1) return cudaErrorNotSupported;
+        if (score_smem(best.SW, best.TH, B, rmax) > 200 * 1024 || tcp_of(best.SW, rmax) > 256 ||
+            best.TH + 2 * rmax > 256)
+            return cudaErrorNotSupported;
+    } else {
+        double best_cost = 1e300;
+        for (int SW : {128, 64})
+            for (int TH : {16, 32, 8}) {
+                const size_t smem = score_smem(SW, TH, B, rmax);
+                if (smem > 200 * 1024 || tcp_of(SW, rmax) > 256 || TH + 2 * rmax > 256) continue;
+                int per_sm = 0;
+                err = emd_occupancy_kind(kind, KB, smem, SW, &per_sm);
+                if (err != cudaSuccess) return err;
+                if (per_sm < 1) continue;
+                const long slots = (long)per_sm * n_sm;
+                long tiles = 0;
+                for (int i = 0; i < n; i++) tiles += (long)((jobs[i].W + SW - 1) / SW) * ((jobs[i].H + TH - 1) / TH);
+                for (int nk = 1; nk <= d; nk++) {
+                    const int kg = (d + nk - 1) / nk;
+                    if ((d + kg - 1) / kg != nk) continue;  // same split as a smaller count
+                    double work = 0.0;
+                    for (int i = 0; i < n; i++) work += image_cost(jobs[i].H, jobs[i].W, d, B, jobs[i].r, SW, TH, kg, nk);
+                    const double ctas = (double)tiles * nk;
+                    const double waves = std::ceil(ctas / (double)slots);
+                    // per-CTA average cost times the waves, plus a penalty for a tail wave
+                    const double cost = waves * (work / ctas);
+                    if (cost < best_cost * 0.999) best_cost = cost, best = ScoreTiling{SW, TH, nk};
+                }
+            }
+        if (best.SW == 0) return cudaErrorNotSupported;  // nothing enqueued
+    }
+    if (chosen) *chosen = best;
+    const int SW = best.SW, TH = best.TH;
+    const int kg = (d + best.n_kg - 1) / best.n_kg, n_kg = (d + kg - 1) / kg;
+    const size_t smem = score_smem(SW, TH, B, rmax);
+
+    ScoreParams p;
+    memset(&p, 0, sizeof(p));
+    p.n = n, p.d = d, p.B = B, p.SW = SW, p.TH = TH, p.kg = kg, p.n_kg = n_kg;
+    p.tile_bytes = (uint32_t)align_up((size_t)(TH + 2 * rmax) * tcp_of(SW, rmax), 128);
+    FinParams f;
+    memset(&f, 0, sizeof(f));
+    f.n = n, f.d = d;
+    long cta = 0, blk = 0;
+    size_t off = 0;
+    for (int i = 0; i < n; i++) {
+        const ScoreJob &j = jobs[i];
+        const long HW = (long)j.H * j.W;
+        ScoreImgP &im = p.img[i];
+        im.H = j.H, im.W = j.W, im.r = j.r, im.nbx = (j.W + SW - 1) / SW;
+        im.cta0 = cta;
+        cta += (long)im.nbx * ((j.H + TH - 1) / TH) * n_kg;
+        im.ref = j.ref, im.Nref = j.Nref;
+        void *numer = nullptr;
+        unsigned long long *accum = nullptr;
+        if (ws_accumulates) {
+            accum = (unsigned long long *)((char *)ws + off);
+            off += align_up(sizeof(unsigned long long) * HW, 256);
+        } else if (j.numer_out) {
+            numer = j.numer_out;
+        } else {
+            numer = (char *)ws + off;
+            off += align_up(out_bytes * (size_t)d * HW, 256);
+        }
+        im.numer = numer, im.accum = accum;
+        err = make_tmap_u8_3d(&p.tmap[i], j.bins, (uint64_t)j.pitch, (uint64_t)j.H, (uint64_t)d, (uint64_t)j.pitch,
+                              (uint64_t)j.H * j.pitch, (uint32_t)tcp_of(SW, j.r), (uint32_t)(TH + 2 * j.r));
+        if (err != cudaSuccess) return err;
+        FinImgP &fi = f.img[i];
+        fi.H = j.H, fi.W = j.W, fi.r = j.r, fi.Nref = j.Nref, fi.blk0 = blk;
+        blk += (HW + 255) / 256;
+        fi.numer = numer, fi.accum = accum, fi.score = j.score;
+    }
+    for (int i = 0; i < n; i++)
+        if (p.img[i].accum) {
+            err = cudaMemsetAsync(p.img[i].accum, 0, sizeof(unsigned long long) * (size_t)jobs[i].H * jobs[i].W, st);
+            if (err != cudaSuccess) return err;
+        }
+    switch (kind) {
+    case EmdKind::U32_U32:
+        launch_emd_kb<uint32_t, uint32_t>(KB, cta, smem, SW, st, p, status);
+        QFCA_LAUNCH("k_finalize", st, k_finalize<uint32_t><<<(unsigned)blk, 256, 0, st>>>(f));
+        break;
+    case EmdKind::U32_U64:
+        launch_emd_kb<uint32_t, unsigned long long>(KB, cta, smem, SW, st, p, status);
+        QFCA_LAUNCH("k_finalize", st, k_finalize<unsigned long long><<<(unsigned)blk, 256, 0, st>>>(f));
+        break;
+    default:
+        launch_emd_kb<unsigned long long, unsigned long long>(KB, cta, smem, SW, st, p, status);
+        QFCA_LAUNCH("k_finalize", st, k_finalize<unsigned long long><<<(unsigned)blk, 256, 0, st>>>(f));
+        break;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t score_workspace_bytes(int H, int W, int d, int nimg) {
-    return align_up(sizeof(unsigned long long) * (size_t)H * W * d * nimg, 256);
+size_t score_jobs_workspace_bytes(const ScoreJob *jobs, int n, int d) {
+    size_t b = 0;
+    for (int i = 0; i < n; i++) b += align_up(sizeof(unsigned long long) * (size_t)jobs[i].H * jobs[i].W * d, 256);
+    return b + 256;
 }
 
-cudaError_t launch_score_ws(const uint8_t *bins, int H, int W, int pitch, int d, int nimg, int B, int r,
-                            const uint32_t *ref_hist, uint32_t ref_total, float *score, uint64_t *numer_out,
-                            void *ws, bool ws_accumulates, int *status, cudaStream_t st, const ScoreTiling *tiling) {
-    // u32 walk when every partial and the numerator fit: (B-1) (2r+1)^2 N_ref < 2^32
-    const double span2 = (double)(2 * r + 1) * (2 * r + 1);
-    const bool narrow = (double)(B - 1) * span2 * (double)ref_total < 4294967295.0 && span2 * ref_total < 4294967295.0;
-    const EmdKind kind = !narrow ? EmdKind::U64_U64
-                         : (numer_out || ws_accumulates) ? EmdKind::U32_U64 : EmdKind::U32_U32;
-    const int KB = (B == 32 || B == 64) ? B : 0;
-    static int attr_dev = -1, n_sm = 0;
-    int dev = 0;
-    cudaError_t err = cudaGetDevice(&dev);
-    if (err != cudaSuccess) return err;
-    if (attr_dev != dev) {
-        err = emd_set_smem_attr<uint32_t, uint32_t>();
-        if (err == cudaSuccess) err = emd_set_smem_attr<uint32_t, unsigned long long>();
-        if (err == cudaSuccess) err = emd_set_smem_attr<unsigned long long, unsigned long long>();
-        if (err == cudaSuccess) err = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        if (err != cudaSuccess) return err;
-        attr_dev = dev;
+bool score_shape_ok(int B, int r) {
+    for (int SW : {128, 64})
+        for (int TH : {16, 32, 8})
+            if (score_smem(SW, TH, B, r) <= 200 * 1024 && tcp_of(SW, r) <= 256 && TH + 2 * r <= 256) return true;
+    return false;
+}
+
+cudaError_t launch_score_jobs(const ScoreJob *jobs, int n, int d, int B, void *ws, bool ws_accumulates, int *status,
+                              cudaStream_t st, const ScoreTiling *tiling, ScoreTiling *chosen) {
+    size_t off = 0;
+    for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
+        const int m = std::min(kMaxBatch, n - i0);
+        cudaError_t e = score_chunk(jobs + i0, m, d, B, (char *)ws + off, ws_accumulates, status, st, tiling, chosen);
+        if (e != cudaSuccess) return e;
+        for (int i = i0; i < i0 + m; i++)
+            off += align_up((ws_accumulates ? 1 : (size_t)d) * sizeof(unsigned long long) * jobs[i].H * jobs[i].W, 256);
     }
-    // geometry: the caller's tiling, else the modelled best over strip widths, band heights and splits
-    ScoreGeom g{};
-    bool have = false;
-    if (tiling && tiling->SW > 0) {
-        g = make_geom(H, W, d, B, r, nimg, tiling->SW, tiling->TH, tiling->n_kg);
-        have = geom_ok(g) && (g.SW == 64 || g.SW == 128) && g.TH >= 1 && g.TH <= 64 && (long)g.n_kg * nimg <= 65535;
-        if (!have) return cudaErrorNotSupported;
-    } else {
-        double best = 1e300;
-        for (int SW : {128, 64})
-            for (int TH : {16, 32, 8}) {
-                const ScoreGeom g0 = make_geom(H, W, d, B, r, nimg, SW, TH, 1);
-                if (!geom_ok(g0)) continue;
-                int per_sm = 0;
-                err = emd_occupancy_kind(kind, KB, g0.smem, SW, &per_sm);
-                if (err != cudaSuccess) return err;
-                if (per_sm < 1) continue;
-                const long slots = (long)per_sm * n_sm;
-                const long tiles = (long)((W + SW - 1) / SW) * ((H + TH - 1) / TH) * nimg;
-                for (int n = 1; n <= d && (long)n * nimg <= 65535; n++) {
-                    const ScoreGeom gn = make_geom(H, W, d, B, r, nimg, SW, TH, n);
-                    if (gn.n_kg != n) continue;
-                    const double waves = (double)((tiles * n + slots - 1) / slots);
-                    const double cost = waves * cta_cost(gn, B, r);
-                    if (cost < best * 0.999) best = cost, g = gn, have = true;
-                }
-            }
-        if (!have) return cudaErrorNotSupported;  // nothing enqueued
-    }
-    alignas(64) CUtensorMap tmap;
-    err = make_tmap_u8_3d(&tmap, bins, (uint64_t)pitch, (uint64_t)H, (uint64_t)nimg * d, (uint64_t)pitch,
-                          (uint64_t)H * pitch, (uint32_t)g.TCp, (uint32_t)g.TR);
-    if (err != cudaSuccess) return err;
-    unsigned long long *accum = ws_accumulates ? (unsigned long long *)ws : nullptr;
-    if (accum) err = cudaMemsetAsync(accum, 0, sizeof(unsigned long long) * (size_t)H * W * nimg, st);
-    if (err != cudaSuccess) return err;
-    const dim3 grid((W + g.SW - 1) / g.SW, (H + g.TH - 1) / g.TH, g.n_kg * nimg);
-    const long N = (long)H * W;
-    const dim3 fgrid((unsigned)((N + 255) / 256), nimg);
-    switch (kind) {
-    case EmdKind::U32_U32: {
-        uint32_t *nm = (uint32_t *)ws;
-        launch_emd_kb<uint32_t, uint32_t>(KB, g, grid, st, tmap, H, W, d, B, r, ref_hist, ref_total, nm, nullptr,
-                                          status);
-        QFCA_LAUNCH("k_finalize", st,
-                    k_finalize<uint32_t><<<fgrid, 256, 0, st>>>(nm, nullptr, H, W, r, d, ref_total, score));
-        break;
-    }
-    case EmdKind::U32_U64: {
-        unsigned long long *nm = accum ? nullptr : (unsigned long long *)(numer_out ? (void *)numer_out : ws);
-        launch_emd_kb<uint32_t, unsigned long long>(KB, g, grid, st, tmap, H, W, d, B, r, ref_hist, ref_total, nm,
-                                                    accum, status);
-        QFCA_LAUNCH("k_finalize", st,
-                    k_finalize<unsigned long long><<<fgrid, 256, 0, st>>>(nm, accum, H, W, r, d, ref_total, score));
-        break;
-    }
-    default: {
-        unsigned long long *nm = accum ? nullptr : (unsigned long long *)(numer_out ? (void *)numer_out : ws);
-        launch_emd_kb<unsigned long long, unsigned long long>(KB, g, grid, st, tmap, H, W, d, B, r, ref_hist,
-                                                              ref_total, nm, accum, status);
-        QFCA_LAUNCH("k_finalize", st,
-                    k_finalize<unsigned long long><<<fgrid, 256, 0, st>>>(nm, accum, H, W, r, d, ref_total, score));
-        break;
-    }
-    }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- allocation-free variant
@@ -471,8 +566,9 @@ extern "C" qfca_status qfca_score_noalloc(const uint8_t *bins, int H, int W, int
         }
         acc = g_noalloc_ptr[dev];
     }
-    const cudaError_t e = launch_score_ws(bins, H, W, pitch, d, 1, B, r, ref_hist, ref_total, score, nullptr, acc,
-                                          true, g_noalloc_status[dev], (cudaStream_t)stream, nullptr);
+    const ScoreJob job{bins, H, W, pitch, r, ref_hist, ref_total, score, nullptr};
+    const cudaError_t e = launch_score_jobs(&job, 1, d, B, acc, true, g_noalloc_status[dev], (cudaStream_t)stream,
+                                            nullptr, nullptr);
     if (e == cudaErrorNotSupported) return QFCA_ERR_UNSUPPORTED;
     if (e != cudaSuccess) {
         cudaGetLastError();
