@@ -16,6 +16,9 @@ namespace qfca {
 constexpr int kMaxC = 512;   // channels supported by the fit and projection
 constexpr int kMaxD = 64;    // components
 constexpr int kMaxB = 255;   // bins
+// Images per launch of the table-driven stages (the table travels in the
+// kernel's parameter block).
+constexpr int kMaxBatch = 64;
 
 // ------------------------------------------------------------------ fit (fit.cu)
 
@@ -54,6 +57,20 @@ cudaError_t launch_project(const float *X, int layout, int H, int W, int C, cons
                            void *ws, int *status, cudaStream_t st);
 
 // Per-component min/max keys live 128 B apart (one L2 line each):
+// One image of the TMA-fed BF16 projection: X NCHW [C][N] (16-B aligned,
+// N % 4 == 0), prepared operands mean32 [Cp] and Vt [DT][Cp] (BF16), Y [d][N],
+// min/max keys mm [2 d kKeyStride] (initialised by the caller).
+struct ProjJob {
+    const float *X;
+    long N;
+    const float *mean32;
+    const void *Vt;
+    float *Y;
+    uint32_t *mm;
+};
+bool project_tma_ok(const float *X, long N, int layout);
+cudaError_t launch_project_tma(const ProjJob *jobs, int n, int C, int d, int *status, cudaStream_t st);
+
 // min of component j at mm_keys[j * kKeyStride], max at mm_keys[(d + j) * kKeyStride].
 constexpr int kKeyStride = 32;
 
@@ -68,11 +85,23 @@ cudaError_t launch_quantize(const float *Y, long N, int H, int W, int d, int nim
                             uint8_t *bins, int pitch, float *lo_out, float *hi_out,
                             uint32_t *hist, cudaStream_t st);
 
-// ------------------------------------------------------------------ score (score.cu)
+// One image of a table-driven quantisation: Y [d][H*W]; image range from the
+// min/max keys mm (or, when mm is NULL, the fixed range lo_in/hi_in [d]);
+// bins [d][H][pitch]; lo_out/hi_out [d] and hist [d][B] optional.
+struct QuantJob {
+    const float *Y;
+    int H, W;
+    const uint32_t *mm;
+    const float *lo_in, *hi_in;
+    uint8_t *bins;
+    int pitch;
+    float *lo_out, *hi_out;
+    uint32_t *hist;
+};
+// zero_hist: clear each job's hist first (else the caller has).
+cudaError_t launch_quantize_jobs(const QuantJob *jobs, int n, int d, int B, bool zero_hist, cudaStream_t st);
 
-// Images per launch of the table-driven stages (the table travels in the
-// kernel's parameter block).
-constexpr int kMaxBatch = 64;
+// ------------------------------------------------------------------ score (score.cu)
 
 // One image of a score launch: bins [d][H][pitch] (16-B aligned, pitch a
 // multiple of 16), reference [d][B] with N_ref = Nref, score [H][W],
@@ -111,6 +140,10 @@ cudaError_t launch_score_jobs(const ScoreJob *jobs, int n, int d, int B, void *w
 // the 128-byte CUtensorMap at tmap_out.  dim0 is innermost.
 cudaError_t make_tmap_u8_3d(void *tmap_out, const void *base, uint64_t dim0, uint64_t dim1, uint64_t dim2,
                             uint64_t stride1_bytes, uint64_t stride2_bytes, uint32_t box0, uint32_t box1);
+
+// 2-D FP32 tiled tensor map (no swizzle, zero fill out of bounds); dim0 innermost.
+cudaError_t make_tmap_f32_2d(void *tmap_out, const void *base, uint64_t dim0, uint64_t dim1, uint64_t stride1_bytes,
+                             uint32_t box0, uint32_t box1);
 
 // ------------------------------------------------------------------ helpers
 

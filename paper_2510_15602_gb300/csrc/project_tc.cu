@@ -284,6 +284,21 @@ cudaError_t launch_project_bf16(const float *X, int layout, int H, int W, int C,
     QFCA_LAUNCH("k_prep_bf16", st,
                 k_prep_bf16<<<dim3((sh.DT * sh.Cp + 255) / 256, nimg), 256, 0, st>>>(mean, V, C, d, sh.Cp, sh.DT,
                                                                                      mean32, Vt));
+    if (project_tma_ok(X, N, layout)) {
+        // NCHW with 16-B aligned rows: the TMA-fed pipeline
+        ProjJob jobs[kMaxBatch];
+        for (int i0 = 0; i0 < nimg; i0 += kMaxBatch) {
+            const int m = nimg - i0 < kMaxBatch ? nimg - i0 : kMaxBatch;
+            for (int i = 0; i < m; i++) {
+                const long img = i0 + i;
+                jobs[i] = ProjJob{X + img * C * N, N, mean32 + img * sh.Cp, Vt + img * sh.DT * sh.Cp, Y + img * d * N,
+                                  mm_keys + img * 2 * d * kKeyStride};
+            }
+            cudaError_t e = launch_project_tma(jobs, m, C, d, status, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     switch (sh.DT) {
         case 16: return launch_dt<16>(X, layout, C, sh, N, nimg, mean32, Vt, d, Y, mm_keys, status, st);
         case 32: return launch_dt<32>(X, layout, C, sh, N, nimg, mean32, Vt, d, Y, mm_keys, status, st);

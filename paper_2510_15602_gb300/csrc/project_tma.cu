@@ -1,0 +1,399 @@
+// project_tma.cu -- BF16 principal-component projection Y = (X - mean) V
+// (arXiv 2510.15602, Sec. 3.3) as a warp-specialised TMA / tcgen05 pipeline
+// over a table of images of any size (one launch for up to 64 images).
+//
+// The projection reads each FP32 feature once and does 2d flops per byte, so
+// it is bound by HBM bandwidth; the design keeps HBM busy.  One persistent CTA
+// per SM owns a contiguous range of the table's 128-pixel tiles; a tile is
+// processed in K-chunks of 64 channels.  Roles (10 warps), synchronised only
+// through mbarriers:
+//   - warp 0 (one thread): TMA producer.  Keeps a ring of `stages` 32 KB boxes
+//     (64 channels x 128 pixels of FP32, zero-filled beyond the image and
+//     beyond C) in flight; a stage is refilled once the converters release it.
+//   - warp 1 (one thread): MMA issuer.  For each converted chunk, 4
+//     tcgen05.mma (M=128, N=DT, K=16) into the tensor-memory accumulator,
+//     then tcgen05.commit to release the operand buffer; after a tile's last
+//     chunk, a commit signals the accumulator.
+//   - warps 2-9: converters and epilogue.  Centre each landed box by the
+//     mean, convert to BF16 into the 128-byte swizzled K-major operand layout
+//     (two operand buffers), release the stage, hand the chunk to the MMA
+//     warp; after a tile, read the accumulator back (tcgen05.ld), write Y
+//     [d][N] coalesced and keep running per-component min/max in registers,
+//     flushed per image as u32 keys.  At an image change they reload V^T
+//     (BF16, DT x Cp) and the FP32 mean into shared memory.
+// Every wait is bounded and also watches a CTA-wide abort flag; a wait that
+// runs out sets bit 0 of the status word and the abort flag, every role
+// leaves its loop, the copies and MMAs in flight drain (bounded), tensor
+// memory is freed and the CTA returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+#include "tc.cuh"
+
+namespace qfca {
+namespace {
+
+constexpr int kM = 128;        // pixels per tile (MMA M)
+constexpr int kKc = 64;        // channels per K-chunk / TMA box (one 128-B swizzle row of BF16)
+constexpr int kConv = 256;     // converter threads (warps 2-9)
+constexpr int kThreads = 64 + kConv;
+constexpr int kMaxStages = 5;
+constexpr uint32_t kStageBytes = kKc * kM * 4;  // 32 KB of FP32
+constexpr uint32_t kAChunk = kM * 128;           // 16 KB of BF16
+constexpr uint32_t kTries = 1u << 26;
+
+struct ProjImgP {
+    long N, tile0;
+    const float *mean32;            // [Cp]
+    const __nv_bfloat16 *Vt;        // [DT][Cp]
+    float *Y;                       // [d][N]
+    uint32_t *mm;                   // [2 d kKeyStride]
+};
+
+struct ProjParams {
+    int n, C, Cp, nk, d, stages;
+    long total_tiles;
+    ProjImgP img[kMaxBatch];
+    CUtensorMap tmap[kMaxBatch];    // X of image i as [C][N] FP32, box {128 pixels, 64 channels}
+};
+
+__device__ __forceinline__ uint32_t swz_off(int row, int chunk16) {
+    return (uint32_t)(row * 128 + ((chunk16 ^ (row & 7)) << 4));
+}
+
+__device__ __forceinline__ int find_img(const ProjParams &p, long w) {
+    int i = 0;
+    while (i + 1 < p.n && p.img[i + 1].tile0 <= w) i++;
+    return i;
+}
+
+// Bounded wait that also gives up when another role has aborted; a wait that
+// runs out raises the abort flag itself.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    for (uint32_t i = 0; i < kTries; i++) {
+        if (tc::mbar_try_wait(bar, parity)) return true;
+        if ((i & 255) == 255 && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+}
+
+__device__ __forceinline__ void conv_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConv) : "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+struct SmemLayout {
+    size_t stage, a, b, mean, bar, total;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int stages, int Cp, int DT) {
+    SmemLayout L;
+    size_t o = 0;
+    L.stage = o;
+    o += (size_t)stages * kStageBytes;
+    L.a = o;
+    o += 2 * (size_t)kAChunk;
+    L.b = o;
+    o += (size_t)(Cp / kKc) * DT * 128;
+    L.mean = o;
+    o += sizeof(float) * (size_t)Cp;
+    L.bar = o;
+    o += 8 * (2 * kMaxStages + 6) + 16 + 2 * 4 * 64;  // barriers, tmem slot + abort flag, kmin/kmax
+    L.total = o + 1024;                                // alignment slack
+    return L;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_constant__ ProjParams p,
+                                                            int *__restrict__ status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = tc::align_smem<1024>(smem_raw);
+    const SmemLayout L = smem_layout(p.stages, p.Cp, DT);
+    uint8_t *stage = smem + L.stage;
+    uint8_t *As = smem + L.a;
+    uint8_t *Bs = smem + L.b;
+    float *mean_s = reinterpret_cast<float *>(smem + L.mean);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bar);  // [kMaxStages] TMA landed
+    uint64_t *empty = full + kMaxStages;                            // [kMaxStages] converters done with a stage
+    uint64_t *a_full = empty + kMaxStages;                          // [2] operand chunk converted
+    uint64_t *a_empty = a_full + 2;                                 // [2] MMAs of a chunk complete
+    uint64_t *acc_full = a_empty + 2;                               // tile's MMAs complete
+    uint64_t *acc_empty = acc_full + 1;                             // accumulator read back
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    uint32_t *kmin = tmem_slot + 4;  // [64]
+    uint32_t *kmax = kmin + 64;      // [64]
+    constexpr uint32_t kCols = DT < 32 ? 32 : DT;
+
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int nk = p.nk, S = p.stages, d = p.d;
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_slot, kCols);
+        tc::tmem_relinquish();
+    }
+    if (t == 32) {
+        for (int s = 0; s < kMaxStages; s++) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], kConv / 32);
+        }
+        for (int b = 0; b < 2; b++) {
+            tc::mbar_init(&a_full[b], kConv / 32);
+            tc::mbar_init(&a_empty[b], 1);
+        }
+        tc::mbar_init(acc_full, 1);
+        tc::mbar_init(acc_empty, kConv / 32);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (t < 64) { kmin[t] = 0xffffffffu; kmax[t] = 0u; }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    // this CTA's contiguous range of tiles
+    const long T = p.total_tiles, G = gridDim.x;
+    const long w0 = T * blockIdx.x / G, w1 = T * (blockIdx.x + 1) / G;
+    const long n_chunks = (w1 - w0) * nk;
+
+    // Every role keeps its whole warp converged (one lane issues), and after an
+    // abort the converters still pass every named barrier, so no thread can be
+    // left waiting at a barrier or a .sync.aligned instruction.
+    constexpr unsigned kFull = 0xffffffffu;
+    if (warp == 0) {
+        // ---------------------------------------------------------------- TMA producer
+        long q = 0;
+        for (; q < n_chunks; q++) {
+            const int s = (int)(q % S);
+            bool ok = q < S || wait_or_abort(&empty[s], (uint32_t)((q / S - 1) & 1), abort_flag);
+            if (!__all_sync(kFull, ok)) break;
+            if (lane == 0) {
+                const long w = w0 + q / nk;
+                const int kc = (int)(q % nk);
+                const int i = find_img(p, w);
+                tc::mbar_arrive_expect_tx(&full[s], kStageBytes);
+                tc::tma_load_2d(stage + (size_t)s * kStageBytes, &p.tmap[i], (int)((w - p.img[i].tile0) * kM),
+                                kc * kKc, &full[s]);
+            }
+            __syncwarp();
+        }
+        if (*abort_flag && lane == 0) {
+            // bounded drain of the copies that may still be landing
+            for (long r = (q > S ? q - S : 0); r < q; r++) tc::mbar_wait(&full[r % S], (uint32_t)((r / S) & 1), kTries);
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- MMA issuer
+        const uint32_t idesc = tc::idesc_bf16_f32(kM, DT);
+        const uint32_t a_base = tc::smem_u32(As), b_base = tc::smem_u32(Bs);
+        long q = 0, last_commit = -1;
+        bool ok = true;
+        for (long tile = 0; ok && tile < w1 - w0; tile++) {
+            if (tile >= 1) ok = __all_sync(kFull, wait_or_abort(acc_empty, (uint32_t)((tile - 1) & 1), abort_flag));
+            for (int kc = 0; ok && kc < nk; kc++, q++) {
+                const int ab = (int)(q & 1);
+                ok = __all_sync(kFull, wait_or_abort(&a_full[ab], (uint32_t)((q >> 1) & 1), abort_flag));
+                if (!ok) break;
+                tc::tc_fence_after();
+                if (lane == 0) {
+                    const uint32_t a0 = a_base + (uint32_t)ab * kAChunk, b0 = b_base + (uint32_t)kc * DT * 128;
+#pragma unroll
+                    for (int ks = 0; ks < 4; ks++)
+                        tc::mma_bf16_ss(tmem, tc::sdesc_kmajor_sw128(a0 + ks * 32), tc::sdesc_kmajor_sw128(b0 + ks * 32),
+                                        idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+                    tc::mma_commit(&a_empty[ab]);
+                    if (kc == nk - 1) tc::mma_commit(acc_full);
+                }
+                __syncwarp();
+                last_commit = q;
+            }
+        }
+        if (*abort_flag && last_commit >= 0 && lane == 0)  // bounded drain of the MMAs in flight
+            tc::mbar_wait(&a_empty[last_commit & 1], (uint32_t)((last_commit >> 1) & 1), kTries);
+    } else {
+        // ---------------------------------------------------------------- converters + epilogue
+        const int ct = t - 64, cw = warp - 2;
+        const int m = ct & (kM - 1), h = ct >> 7;        // pixel row m, channels [32 h, 32 h + 32) of a chunk
+        const int quarter = warp & 3, chalf = cw >> 2;   // TMEM lane quarter (warp id % 4), column half
+        constexpr int CW = DT >= 32 ? DT / 2 : 16;
+        const bool epi = DT >= 32 || chalf == 0;
+        const int jbase = DT >= 32 ? chalf * CW : 0;
+        float rmn[CW], rmx[CW];
+#pragma unroll
+        for (int i = 0; i < CW; i++) { rmn[i] = __int_as_float(0x7f800000); rmx[i] = -__int_as_float(0x7f800000); }
+        auto flush = [&](int img) {  // all converter threads
+            if (epi) {
+#pragma unroll
+                for (int i = 0; i < CW; i++) {
+                    float mn = rmn[i], mx = rmx[i];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        mn = fminf(mn, __shfl_xor_sync(kFull, mn, o));
+                        mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+                    }
+                    const int j = jbase + i;
+                    if (lane == 0 && j < d) {
+                        atomicMin(&kmin[j], f2key(mn));
+                        atomicMax(&kmax[j], f2key(mx));
+                    }
+                    rmn[i] = __int_as_float(0x7f800000);
+                    rmx[i] = -__int_as_float(0x7f800000);
+                }
+            }
+            conv_sync();
+            if (ct < d) {
+                uint32_t *mm = p.img[img].mm;
+                atomicMin(&mm[ct * kKeyStride], kmin[ct]);
+                atomicMax(&mm[(d + ct) * kKeyStride], kmax[ct]);
+                kmin[ct] = 0xffffffffu;
+                kmax[ct] = 0u;
+            }
+        };
+        int cur = -1;
+        long q = 0;
+        bool ok = true;  // warp-uniform; once false the warp only keeps passing the named barriers
+        for (long tile = 0; tile < w1 - w0; tile++) {
+            const long w = w0 + tile;
+            const int img = find_img(p, w);
+            const ProjImgP &im = p.img[img];
+            if (img != cur) {
+                // image change: the previous tile's MMAs completed (its epilogue waited for them)
+                if (cur >= 0) flush(cur);
+                conv_sync();
+                for (int c = ct; c < p.Cp; c += kConv) mean_s[c] = im.mean32[c];
+                for (int e = ct; e < DT * (p.Cp / 8); e += kConv) {
+                    const int j = e / (p.Cp / 8), c8 = e % (p.Cp / 8);
+                    const uint4 v = *reinterpret_cast<const uint4 *>(im.Vt + (long)j * p.Cp + c8 * 8);
+                    *reinterpret_cast<uint4 *>(Bs + (size_t)(c8 >> 3) * DT * 128 + swz_off(j, c8 & 7)) = v;
+                }
+                tc::fence_proxy_async_smem();
+                conv_sync();
+                cur = img;
+            }
+            for (int kc = 0; kc < nk; kc++, q++) {
+                const int s = (int)(q % S), ab = (int)(q & 1);
+                if (ok) ok = __all_sync(kFull, wait_or_abort(&full[s], (uint32_t)((q / S) & 1), abort_flag));
+                if (ok && q >= 2)
+                    ok = __all_sync(kFull, wait_or_abort(&a_empty[ab], (uint32_t)(((q - 2) >> 1) & 1), abort_flag));
+                if (!ok) continue;
+                const float *xs = reinterpret_cast<const float *>(stage + (size_t)s * kStageBytes) + (32 * h) * kM + m;
+                const float4 *mu4 = reinterpret_cast<const float4 *>(mean_s + kc * kKc + 32 * h);
+                uint8_t *arow = As + (size_t)ab * kAChunk;
+#pragma unroll
+                for (int g = 0; g < 4; g++) {
+                    const float4 ma = mu4[2 * g], mb = mu4[2 * g + 1];
+                    const float *x8 = xs + (8 * g) * kM;
+                    uint4 pk;
+                    pk.x = tc::pack_bf16x2(x8[0 * kM] - ma.x, x8[1 * kM] - ma.y);
+                    pk.y = tc::pack_bf16x2(x8[2 * kM] - ma.z, x8[3 * kM] - ma.w);
+                    pk.z = tc::pack_bf16x2(x8[4 * kM] - mb.x, x8[5 * kM] - mb.y);
+                    pk.w = tc::pack_bf16x2(x8[6 * kM] - mb.z, x8[7 * kM] - mb.w);
+                    *reinterpret_cast<uint4 *>(arow + swz_off(m, 4 * h + g)) = pk;
+                }
+                tc::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&empty[s]);
+                    mbar_arrive(&a_full[ab]);
+                }
+            }
+            // epilogue: this warp's 32 accumulator lanes, its half of the columns
+            if (ok) ok = __all_sync(kFull, wait_or_abort(acc_full, (uint32_t)(tile & 1), abort_flag));
+            if (!ok) continue;
+            tc::tc_fence_after();
+            if (epi) {
+                const long pe = (w - im.tile0) * kM + 32 * quarter + lane;
+                const bool valid = pe < im.N;
+#pragma unroll
+                for (int j0 = 0; j0 < CW; j0 += 16) {
+                    uint32_t r[16];
+                    tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(jbase + j0), r);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        const int j = jbase + j0 + i;
+                        const float v = __uint_as_float(r[i]);
+                        if (j < d && valid) {
+                            im.Y[(long)j * im.N + pe] = v;
+                            rmn[j0 + i] = fminf(rmn[j0 + i], v);
+                            rmx[j0 + i] = fmaxf(rmx[j0 + i], v);
+                        }
+                    }
+                }
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty);
+        }
+        if (cur >= 0) flush(cur);  // unconditional: every converter thread passes the same barriers
+    }
+    if (t == 0 && *abort_flag) atomicOr(status, kStatusMmaTimeout);
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, kCols);
+    }
+}
+
+template <int DT>
+cudaError_t launch_dt(const ProjParams &p, int *status, cudaStream_t st) {
+    static int attr_dev = -1, n_sm = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (attr_dev != dev) {
+        e = cudaFuncSetAttribute(k_project_tma<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    const size_t smem = smem_layout(p.stages, p.Cp, DT).total;
+    const long grid = p.total_tiles < n_sm ? p.total_tiles : n_sm;
+    QFCA_LAUNCH("k_project_tma", st, k_project_tma<DT><<<(unsigned)grid, kThreads, smem, st>>>(p, status));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool project_tma_ok(const float *X, long N, int layout) {
+    return layout == QFCA_NCHW && N % 4 == 0 && ((uintptr_t)X & 15) == 0;
+}
+
+cudaError_t launch_project_tma(const ProjJob *jobs, int n, int C, int d, int *status, cudaStream_t st) {
+    const int DT = d <= 16 ? 16 : (d <= 32 ? 32 : 64);
+    const int Cp = (C + kKc - 1) / kKc * kKc;
+    int stages = kMaxStages;
+    while (stages > 2 && smem_layout(stages, Cp, DT).total > 227 * 1024) stages--;
+    if (smem_layout(stages, Cp, DT).total > 227 * 1024) return cudaErrorNotSupported;
+    for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
+        const int m = n - i0 < kMaxBatch ? n - i0 : kMaxBatch;
+        ProjParams p;
+        memset(&p, 0, sizeof(p));
+        p.n = m, p.C = C, p.Cp = Cp, p.nk = Cp / kKc, p.d = d, p.stages = stages;
+        long tiles = 0;
+        for (int i = 0; i < m; i++) {
+            const ProjJob &j = jobs[i0 + i];
+            if (!project_tma_ok(j.X, j.N, QFCA_NCHW)) return cudaErrorNotSupported;
+            ProjImgP &im = p.img[i];
+            im.N = j.N, im.tile0 = tiles, im.mean32 = j.mean32, im.Vt = (const __nv_bfloat16 *)j.Vt, im.Y = j.Y, im.mm = j.mm;
+            tiles += (j.N + kM - 1) / kM;
+            cudaError_t e = make_tmap_f32_2d(&p.tmap[i], j.X, (uint64_t)j.N, (uint64_t)C, (uint64_t)j.N * 4, kM, kKc);
+            if (e != cudaSuccess) return e;
+        }
+        p.total_tiles = tiles;
+        cudaError_t e;
+        switch (DT) {
+            case 16: e = launch_dt<16>(p, status, st); break;
+            case 32: e = launch_dt<32>(p, status, st); break;
+            default: e = launch_dt<64>(p, status, st); break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace qfca

@@ -26,55 +26,93 @@ __device__ __forceinline__ int bin_of(float y, float lo, float hi, float fB, int
     return q > B - 1 ? B - 1 : q;
 }
 
-// Grid (row bands, d, images).
-__global__ void __launch_bounds__(kThreads) k_quantize(const float *__restrict__ Y, long N, int H, int W, int d,
-                                                       int B, int range_mode, const uint32_t *__restrict__ mm_keys,
-                                                       const float *__restrict__ lo_in,
-                                                       const float *__restrict__ hi_in, uint8_t *__restrict__ bins,
-                                                       int pitch, float *__restrict__ lo_out,
-                                                       float *__restrict__ hi_out, uint32_t *__restrict__ hist) {
+struct QuantImgP {
+    const float *Y;           // [d][N]
+    int H, W;
+    long cta0;                // first CTA of this image
+    const uint32_t *mm;       // min/max keys (image range) or NULL
+    const float *lo_in, *hi_in;  // fixed range [d] when mm is NULL
+    uint8_t *bins;            // [d][H][pitch]
+    int pitch;
+    float *lo_out, *hi_out;   // [d] or NULL
+    uint32_t *hist;           // [d][B] or NULL
+};
+
+struct QuantParams {
+    int n, d, B;
+    QuantImgP img[kMaxBatch];
+};
+
+// One CTA = one component x a band of rows of one image of the table.
+__global__ void __launch_bounds__(kThreads) k_quantize(const __grid_constant__ QuantParams p) {
     __shared__ uint32_t sh[256];
-    const int k = blockIdx.y;
-    const long img = blockIdx.z;
-    Y += img * d * N;
-    mm_keys += img * 2 * d * kKeyStride;
-    bins += img * d * H * (long)pitch;
-    if (lo_out) lo_out += img * d;
-    if (hi_out) hi_out += img * d;
-    if (hist) hist += img * d * B;
+    const long cta = blockIdx.x;
+    int ii = 0;
+    while (ii + 1 < p.n && p.img[ii + 1].cta0 <= cta) ii++;
+    const QuantImgP &im = p.img[ii];
+    const int d = p.d, B = p.B, H = im.H, W = im.W;
+    const long N = (long)H * W;
+    const long local = cta - im.cta0;
+    const int k = (int)(local % d), band = (int)(local / d);
     float lo, hi;
-    if (range_mode == QFCA_RANGE_IMAGE) {
-        lo = key2f(mm_keys[k * kKeyStride]);
-        hi = key2f(mm_keys[(d + k) * kKeyStride]);
+    if (im.mm) {
+        lo = key2f(im.mm[k * kKeyStride]);
+        hi = key2f(im.mm[(d + k) * kKeyStride]);
     } else {
-        lo = lo_in[k];
-        hi = hi_in[k];
+        lo = im.lo_in[k];
+        hi = im.hi_in[k];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (lo_out) lo_out[k] = lo;
-        if (hi_out) hi_out[k] = hi;
+    if (band == 0 && threadIdx.x == 0) {
+        if (im.lo_out) im.lo_out[k] = lo;
+        if (im.hi_out) im.hi_out[k] = hi;
     }
     for (int b = threadIdx.x; b < B; b += kThreads) sh[b] = 0;
     __syncthreads();
     const float fB = (float)B;
-    const float *yk = Y + (long)k * N;
-    uint8_t *bk = bins + (long)k * H * pitch;
-    const int y0 = blockIdx.x * kRowsPerCta;
+    const float *yk = im.Y + (long)k * N;
+    uint8_t *bk = im.bins + (long)k * H * im.pitch;
+    const int y0 = band * kRowsPerCta;
     const int y1 = min(H, y0 + kRowsPerCta);
     for (int yy = y0; yy < y1; yy++) {
         for (int x = threadIdx.x; x < W; x += kThreads) {
             const int q = bin_of(yk[(long)yy * W + x], lo, hi, fB, B);
-            bk[(long)yy * pitch + x] = (uint8_t)q;
-            if (hist) atomicAdd(&sh[q], 1u);
+            bk[(long)yy * im.pitch + x] = (uint8_t)q;
+            if (im.hist) atomicAdd(&sh[q], 1u);
         }
     }
     __syncthreads();
-    if (hist)
+    if (im.hist)
         for (int b = threadIdx.x; b < B; b += kThreads)
-            if (sh[b]) atomicAdd(&hist[(long)k * B + b], sh[b]);
+            if (sh[b]) atomicAdd(&im.hist[(long)k * B + b], sh[b]);
 }
 
 }  // namespace
+
+cudaError_t launch_quantize_jobs(const QuantJob *jobs, int n, int d, int B, bool zero_hist, cudaStream_t st) {
+    for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
+        const int m = n - i0 < kMaxBatch ? n - i0 : kMaxBatch;
+        QuantParams p;
+        memset(&p, 0, sizeof(p));
+        p.n = m, p.d = d, p.B = B;
+        long cta = 0;
+        for (int i = 0; i < m; i++) {
+            const QuantJob &j = jobs[i0 + i];
+            QuantImgP &im = p.img[i];
+            im.Y = j.Y, im.H = j.H, im.W = j.W, im.cta0 = cta;
+            cta += (long)((j.H + kRowsPerCta - 1) / kRowsPerCta) * d;
+            im.mm = j.mm, im.lo_in = j.lo_in, im.hi_in = j.hi_in;
+            im.bins = j.bins, im.pitch = j.pitch, im.lo_out = j.lo_out, im.hi_out = j.hi_out, im.hist = j.hist;
+            if (j.hist && zero_hist) {
+                cudaError_t err = cudaMemsetAsync(j.hist, 0, sizeof(uint32_t) * (size_t)d * B, st);
+                if (err != cudaSuccess) return err;
+            }
+        }
+        QFCA_LAUNCH("k_quantize", st, k_quantize<<<(unsigned)cta, kThreads, 0, st>>>(p));
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
 
 cudaError_t launch_quantize(const float *Y, long N, int H, int W, int d, int nimg, int B, int range_mode,
                             const uint32_t *mm_keys, const float *lo_in, const float *hi_in, uint8_t *bins,
@@ -83,11 +121,25 @@ cudaError_t launch_quantize(const float *Y, long N, int H, int W, int d, int nim
         cudaError_t err = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)d * B * nimg, st);
         if (err != cudaSuccess) return err;
     }
-    dim3 grid((H + kRowsPerCta - 1) / kRowsPerCta, d, nimg);
-    QFCA_LAUNCH("k_quantize", st,
-                k_quantize<<<grid, kThreads, 0, st>>>(Y, N, H, W, d, B, range_mode, mm_keys, lo_in, hi_in, bins,
-                                                      pitch, lo_out, hi_out, hist));
-    return cudaGetLastError();
+    QuantJob jobs[kMaxBatch];
+    for (int i0 = 0; i0 < nimg; i0 += kMaxBatch) {
+        const int m = nimg - i0 < kMaxBatch ? nimg - i0 : kMaxBatch;
+        for (int i = 0; i < m; i++) {
+            const long img = i0 + i;
+            QuantJob &j = jobs[i];
+            j.Y = Y + img * d * N;
+            j.H = H, j.W = W;
+            j.mm = range_mode == QFCA_RANGE_IMAGE ? mm_keys + img * 2 * d * kKeyStride : nullptr;
+            j.lo_in = lo_in, j.hi_in = hi_in;
+            j.bins = bins + img * d * H * (long)pitch, j.pitch = pitch;
+            j.lo_out = lo_out ? lo_out + img * d : nullptr;
+            j.hi_out = hi_out ? hi_out + img * d : nullptr;
+            j.hist = hist ? hist + img * d * B : nullptr;
+        }
+        cudaError_t e = launch_quantize_jobs(jobs, m, d, B, false, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace qfca
