@@ -200,6 +200,39 @@ typedef struct {
 qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int d, int B, int r,
                            int precision, float *scores, const qfca_batch_outputs *extra, void *stream);
 
+/* One image of an uneven batch (qfca_score_batch). */
+typedef struct {
+    const float *X; /* device feature map, C channels in the batch's layout,
+                       16-byte aligned for the TMA-fed BF16 projection */
+    int H, W;       /* size, H*W >= 2 */
+    int r;          /* window radius of this image, 1 <= r <= 63 */
+    float *score;   /* device f32 [H][W], written */
+} qfca_image;
+
+/* qfca_score_batch -- the whole path of qfca_batch_run for n images of
+ * different sizes and window radii (same C, layout, d, B, precision): each
+ * image gets its own PCA fit (Sec. 3.3), image-wide quantisation ranges and
+ * its own global histogram as reference (Sec. 3.1).  Every stage is one
+ * persistent launch over a table of up to 64 images (more images: one launch
+ * per 64), so the whole batch can be captured in one CUDA graph.  Results
+ * equal n separate single-image calls (same kernels, same arithmetic).  With
+ * autotuning on (qfca_set_autotune), the first call for a new set of shapes
+ * outside stream capture times the window stage's candidate tilings and
+ * keeps the fastest for later calls.  Requires 1 <= n <= 4096 and the limits
+ * of the single-image entry points. */
+qfca_status qfca_score_batch(qfca_ctx *ctx, const qfca_image *imgs, int n, int C, int layout, int d, int B,
+                             int precision, void *stream);
+
+/* Autotuning of the window stage's tiling (strip width, band height,
+ * components per CTA) for qfca_score_batch and qfca_batch_run: 0 = the built-in
+ * cost model (default), 1 = measure candidates once per shape set (blocking,
+ * never under stream capture) and reuse the fastest. */
+qfca_status qfca_set_autotune(qfca_ctx *ctx, int mode);
+
+/* The window-stage tiling used by the context's most recent score launch:
+ * strip width (threads), band height (rows), component groups. */
+qfca_status qfca_last_tiling(qfca_ctx *ctx, int *strip_width, int *band_height, int *component_groups);
+
 /* qfca_score_noalloc -- the same computation as qfca_score (without the
  * optional numerator output), for callers that cannot allocate device memory:
  * code that runs under a host application or memory manager that owns every

@@ -8,6 +8,8 @@
 
 #include <string.h>
 
+#include <algorithm>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -118,6 +120,9 @@ struct qfca_ctx {
     std::string err;
     std::mutex mu;
     Tracer tracer;
+    int autotune = 0;                                   // window-stage tiling: 0 model, 1 measured
+    std::map<std::string, qfca::ScoreTiling> tuned;     // measured tilings per shape set
+    qfca::ScoreTiling last_tiling{0, 0, 0};
 };
 
 namespace {
@@ -196,6 +201,82 @@ qfca_status check_fmap(qfca_ctx *ctx, const float *X, const qfca_fmap &m) {
 }
 
 size_t bytes_mmkeys(int d) { return align_up(sizeof(uint32_t) * 2 * d * kKeyStride, 256); }
+
+bool capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// The window stage of a batch, with the context's tiling policy: the cost
+// model, or (autotune) the fastest of the candidate tilings measured once per
+// shape set on this stream (outside capture), reused afterwards.
+qfca_status run_score(qfca_ctx *ctx, const ScoreJob *jobs, int n, int d, int B, void *ws, cudaStream_t st,
+                      const char *where) {
+    const ScoreTiling *use = nullptr;
+    ScoreTiling chosen{0, 0, 0};
+    if (ctx->autotune) {
+        std::string key = std::to_string(n) + ":" + std::to_string(d) + ":" + std::to_string(B);
+        for (int i = 0; i < n; i++)
+            key += ":" + std::to_string(jobs[i].H) + "x" + std::to_string(jobs[i].W) + "r" + std::to_string(jobs[i].r);
+        auto it = ctx->tuned.find(key);
+        if (it != ctx->tuned.end()) {
+            chosen = it->second;
+            use = &chosen;
+        } else if (!capturing(st)) {
+            cudaEvent_t a = nullptr, b = nullptr;
+            if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+                return cuda_fail(ctx, cudaGetLastError(), "autotune events");
+            float best_ms = 1e30f;
+            ScoreTiling best{0, 0, 0};
+            std::vector<ScoreTiling> cands;
+            ScoreTiling model{0, 0, 0};
+            cudaError_t e = launch_score_jobs(jobs, n, d, B, ws, false, ctx->status_dev, st, nullptr, &model);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(a), cudaEventDestroy(b);
+                return e == cudaErrorNotSupported ? fail(ctx, QFCA_ERR_UNSUPPORTED, "%s: no tiling fits", where)
+                                                  : cuda_fail(ctx, e, where);
+            }
+            cands.push_back(model);
+            for (int SW : {128, 64})
+                for (int TH : {8, 16, 32})
+                    for (int nk : {1, 2, 4, 8, 16, 32})
+                        if (nk <= d) cands.push_back(ScoreTiling{SW, TH, nk});
+            for (const ScoreTiling &c : cands) {
+                float tot = 0.0f;
+                bool okc = true;
+                for (int rep = 0; rep < 3 && okc; rep++) {
+                    cudaEventRecord(a, st);
+                    e = launch_score_jobs(jobs, n, d, B, ws, false, ctx->status_dev, st, &c, nullptr);
+                    if (e == cudaErrorNotSupported) {
+                        okc = false;
+                        break;
+                    }
+                    if (e != cudaSuccess) {
+                        cudaEventDestroy(a), cudaEventDestroy(b);
+                        return cuda_fail(ctx, e, where);
+                    }
+                    cudaEventRecord(b, st);
+                    if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
+                        cudaEventDestroy(a), cudaEventDestroy(b);
+                        return cuda_fail(ctx, e, where);
+                    }
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, a, b);
+                    if (rep > 0) tot += ms;  // the first run warms up
+                }
+                if (okc && tot < best_ms) best_ms = tot, best = c;
+            }
+            cudaEventDestroy(a), cudaEventDestroy(b);
+            ctx->tuned[key] = best;
+            chosen = best;
+            use = &chosen;
+        }
+    }
+    cudaError_t e = launch_score_jobs(jobs, n, d, B, ws, false, ctx->status_dev, st, use, &ctx->last_tiling);
+    if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "%s: no window tiling fits B = %d", where, B);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, where);
+    return QFCA_OK;
+}
 
 }  // namespace
 
@@ -443,10 +524,127 @@ qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap de
         jobs[i].ref = hist + (size_t)i * d * B;
         jobs[i].score = scores + (size_t)i * N;
     }
-    e = launch_score_jobs(jobs.data(), nimg, d, B, b + o_sc, false, ctx->status_dev, st, nullptr, nullptr);
-    if (e == cudaErrorNotSupported)
-        return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d needs more shared memory than a CTA has", B, r);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run/score");
+    return run_score(ctx, jobs.data(), nimg, d, B, b + o_sc, st, "qfca_batch_run/score");
+}
+
+qfca_status qfca_score_batch(qfca_ctx *ctx, const qfca_image *imgs, int n, int C, int layout, int d, int B,
+                             int precision, void *stream) {
+    qfca_status s = check_ctx(ctx);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!imgs) return fail(ctx, QFCA_ERR_INVALID_ARG, "imgs is NULL");
+    if (n < 1 || n > 4096) return fail(ctx, QFCA_ERR_INVALID_ARG, "n = %d outside [1, 4096]", n);
+    if (layout != QFCA_NCHW && layout != QFCA_NHWC) return fail(ctx, QFCA_ERR_INVALID_ARG, "bad layout %d", layout);
+    if (C < 2 || C > kMaxC) return fail(ctx, QFCA_ERR_UNSUPPORTED, "C = %d outside [2, %d]", C, kMaxC);
+    if (d < 1 || d > C || d > kMaxD) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, min(C, %d)]", d, kMaxD);
+    if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
+    if (precision != QFCA_F32 && precision != QFCA_BF16)
+        return fail(ctx, precision == QFCA_FP8_E4M3 ? QFCA_ERR_UNSUPPORTED : QFCA_ERR_INVALID_ARG,
+                    "precision %d not available", precision);
+    for (int i = 0; i < n; i++) {
+        const qfca_image &im = imgs[i];
+        if (!im.X || !im.score) return fail(ctx, QFCA_ERR_INVALID_ARG, "image %d: NULL pointer", i);
+        if (im.H < 1 || im.W < 1 || (long)im.H * im.W < 2)
+            return fail(ctx, QFCA_ERR_INVALID_ARG, "image %d: bad H x W = %d x %d", i, im.H, im.W);
+        if ((long)im.H * im.W > (1L << 23)) return fail(ctx, QFCA_ERR_UNSUPPORTED, "image %d: H*W > 2^23", i);
+        if (im.r < 1 || 2 * im.r + 1 > 127) return fail(ctx, QFCA_ERR_INVALID_ARG, "image %d: r = %d outside [1, 63]", i, im.r);
+        if (!score_shape_ok(B, im.r))
+            return fail(ctx, QFCA_ERR_UNSUPPORTED, "image %d: B = %d with r = %d does not fit shared memory", i, B, im.r);
+    }
+    DeviceGuard g(ctx->device);
+    HookScope hs(ctx);
+    cudaStream_t st = (cudaStream_t)stream;
+    // workspace: [fit | mean | V | ev | prep | keys | per image: Y, bins, hist, lo/hi | score]
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t at = o; o = align_up(o + bytes, 256); return at; };
+    const size_t o_fit = take(fit_workspace_bytes(C, 1, d, n));
+    const size_t o_mean = take(sizeof(double) * (size_t)C * n);
+    const size_t o_V = take(sizeof(double) * (size_t)C * d * n);
+    const size_t o_ev = take(sizeof(double) * (size_t)d * n);
+    long maxN = 0;
+    for (int i = 0; i < n; i++) maxN = std::max(maxN, (long)imgs[i].H * imgs[i].W);
+    const size_t o_pj = take(std::max(project_bf16_workspace_bytes(C, maxN, d, n), project_workspace_bytes(C, maxN, d, 1)));
+    const size_t o_mm = take(bytes_mmkeys(d) * (size_t)n);
+    std::vector<size_t> o_Y(n), o_bins(n), o_hist(n), o_lohi(n);
+    std::vector<int> pitch(n);
+    for (int i = 0; i < n; i++) {
+        const long N = (long)imgs[i].H * imgs[i].W;
+        pitch[i] = (imgs[i].W + 15) / 16 * 16;
+        o_Y[i] = take(sizeof(float) * (size_t)d * N);
+        o_bins[i] = take((size_t)d * imgs[i].H * pitch[i]);
+        o_hist[i] = take(sizeof(uint32_t) * (size_t)d * B);
+        o_lohi[i] = take(sizeof(float) * 2 * (size_t)d);
+    }
+    std::vector<ScoreJob> sjobs(n);
+    for (int i = 0; i < n; i++)
+        sjobs[i] = ScoreJob{nullptr, imgs[i].H, imgs[i].W, pitch[i], imgs[i].r, nullptr,
+                            (uint32_t)((long)imgs[i].H * imgs[i].W), imgs[i].score, nullptr};
+    const size_t o_sc = take(score_jobs_workspace_bytes(sjobs.data(), n, d));
+    if ((s = ensure_ws(ctx, o))) return s;
+    char *b = (char *)ctx->ws;
+    double *mean = (double *)(b + o_mean), *V = (double *)(b + o_V), *ev = (double *)(b + o_ev);
+    uint32_t *mm = (uint32_t *)(b + o_mm);
+    const size_t mm_stride = bytes_mmkeys(d) / sizeof(uint32_t);
+
+    // fit: one launch per stage for the table
+    std::vector<FitJob> fjobs(n);
+    for (int i = 0; i < n; i++) fjobs[i] = FitJob{imgs[i].X, (long)imgs[i].H * imgs[i].W};
+    cudaError_t e = launch_fit_jobs(fjobs.data(), n, layout, C, d, mean, V, ev, b + o_fit, ctx->status_dev, st);
+    if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "eigensolver shape C=%d d=%d", C, d);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_score_batch/fit");
+    // projection: the TMA-fed table kernel when every image allows it, else one call per image
+    bool tma = precision == QFCA_BF16;
+    for (int i = 0; i < n && tma; i++) tma = project_tma_ok(imgs[i].X, (long)imgs[i].H * imgs[i].W, layout);
+    if (mm_stride != (size_t)2 * d * kKeyStride) return fail(ctx, QFCA_ERR_UNSUPPORTED, "key layout");
+    if (tma) {
+        float *mean32 = nullptr;
+        void *Vt = nullptr;
+        int Cp = 0, DT = 0;
+        e = launch_prep_bf16(mean, V, C, d, n, b + o_pj, &mean32, &Vt, &Cp, &DT, st);
+        if (e == cudaSuccess) e = launch_init_keys(mm, d, n, st);
+        std::vector<ProjJob> pjobs(n);
+        for (int i = 0; i < n; i++)
+            pjobs[i] = ProjJob{imgs[i].X, (long)imgs[i].H * imgs[i].W, mean32 + (size_t)i * Cp,
+                               (const char *)Vt + sizeof(uint16_t) * (size_t)i * DT * Cp, (float *)(b + o_Y[i]),
+                               mm + (size_t)i * mm_stride};
+        if (e == cudaSuccess) e = launch_project_tma(pjobs.data(), n, C, d, ctx->status_dev, st);
+    } else {
+        for (int i = 0; i < n && e == cudaSuccess; i++)
+            e = launch_project(imgs[i].X, layout, imgs[i].H, imgs[i].W, C, mean + (size_t)i * C, V + (size_t)i * C * d, d,
+                               1, precision, (float *)(b + o_Y[i]), mm + (size_t)i * mm_stride, b + o_pj,
+                               ctx->status_dev, st);
+    }
+    if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "projection shape C=%d d=%d", C, d);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_score_batch/project");
+    // quantisation: image-wide ranges, each image's own reference histogram
+    std::vector<QuantJob> qjobs(n);
+    for (int i = 0; i < n; i++) {
+        float *lo = (float *)(b + o_lohi[i]);
+        qjobs[i] = QuantJob{(const float *)(b + o_Y[i]), imgs[i].H, imgs[i].W, mm + (size_t)i * mm_stride, nullptr,
+                            nullptr, (uint8_t *)(b + o_bins[i]), pitch[i], lo, lo + d, (uint32_t *)(b + o_hist[i])};
+    }
+    e = launch_quantize_jobs(qjobs.data(), n, d, B, true, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_score_batch/quantize");
+    for (int i = 0; i < n; i++) {
+        sjobs[i].bins = (const uint8_t *)(b + o_bins[i]);
+        sjobs[i].ref = (const uint32_t *)(b + o_hist[i]);
+    }
+    return run_score(ctx, sjobs.data(), n, d, B, b + o_sc, st, "qfca_score_batch/score");
+}
+
+qfca_status qfca_set_autotune(qfca_ctx *ctx, int mode) {
+    if (!ctx || (mode != 0 && mode != 1)) return QFCA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->autotune = mode;
+    return QFCA_OK;
+}
+
+qfca_status qfca_last_tiling(qfca_ctx *ctx, int *strip_width, int *band_height, int *component_groups) {
+    if (!ctx || !strip_width || !band_height || !component_groups) return QFCA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    *strip_width = ctx->last_tiling.SW;
+    *band_height = ctx->last_tiling.TH;
+    *component_groups = ctx->last_tiling.n_kg;
     return QFCA_OK;
 }
 

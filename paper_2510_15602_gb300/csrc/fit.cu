@@ -35,6 +35,17 @@ FitLayout fit_layout(int C, long N, int d, int nimg) {
 
 size_t fit_workspace_bytes(int C, long N, int d, int nimg) { return fit_layout(C, N, d, nimg).total; }
 
+cudaError_t launch_fit_jobs(const FitJob *jobs, int n, int layout, int C, int d, double *mean, double *V,
+                            double *eigvals, void *ws, int *status, cudaStream_t st) {
+    const FitLayout L = fit_layout(C, 1, d, n);
+    char *base = (char *)ws;
+    double *cov = (double *)(base + L.off_cov);
+    void *cov_ff = base + L.off_covff;
+    cudaError_t e = launch_gram_cov_jobs(jobs, n, layout, C, mean, cov, cov_ff, base + L.off_gram, status, st);
+    if (e != cudaSuccess) return e;
+    return launch_eig(cov_ff, C, d, n, V, eigvals, base + L.off_eig, st);
+}
+
 cudaError_t launch_fit(const float *X, int layout, int H, int W, int C, int d, int nimg, double *mean, double *V,
                        double *eigvals, void *ws, int *status, cudaStream_t st) {
     const long N = (long)H * W;

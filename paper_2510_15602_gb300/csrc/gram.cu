@@ -55,24 +55,40 @@ __device__ __forceinline__ int tile_pair_idx(int p, int nt, int &j) {
     return i;
 }
 
+// Per-image part of a table-driven fit launch.
+struct FitImgP {
+    const float *X;   // [C][N] (NCHW) or [N][C] (NHWC)
+    long N;
+    long chunk;       // pixels per Gram CTA (a multiple of the exact-accumulation window)
+    int n_split;      // pixel ranges of this image
+    long cta0;        // first Gram CTA of this image
+};
+
+struct FitParams {
+    int n, C, layout, vec_ok, nt, n_pairs;
+    FitImgP img[kMaxBatch];
+};
+
 // e_c = smallest exponent with max_p |x_cp| < 2^e_c  (stored as the max |x| bits first)
-// Grid (x-chunks, C, images).
-__global__ void k_chan_absmax(const float *__restrict__ X, int layout, int C, long N, unsigned *__restrict__ amax) {
-    const int c = blockIdx.y;
-    X += (long)blockIdx.z * C * N;
+// Grid (x-chunks, C, images of the table).
+__global__ void k_chan_absmax(const __grid_constant__ FitParams p, unsigned *__restrict__ amax) {
+    const int c = blockIdx.y, C = p.C;
+    const FitImgP &im = p.img[blockIdx.z];
+    const float *X = im.X;
+    const long N = im.N;
     amax += (long)blockIdx.z * C;
     unsigned m = 0;
-    if (layout == QFCA_NCHW) {
+    if (p.layout == QFCA_NCHW) {
         const float *row = X + (long)c * N;
-        for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < N; p += (long)gridDim.x * blockDim.x)
-            m = max(m, __float_as_uint(row[p]) & 0x7fffffffu);
+        for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < N; q += (long)gridDim.x * blockDim.x)
+            m = max(m, __float_as_uint(row[q]) & 0x7fffffffu);
     } else {
-        for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < N; p += (long)gridDim.x * blockDim.x)
-            m = max(m, __float_as_uint(X[p * C + c]) & 0x7fffffffu);
+        for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < N; q += (long)gridDim.x * blockDim.x)
+            m = max(m, __float_as_uint(X[q * C + c]) & 0x7fffffffu);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(&amax[c], m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&amax[c], m);
 }
 
 __device__ __forceinline__ float rint_exact(float v) { return __fsub_rn(__fadd_rn(v, kMagic), kMagic); }
@@ -164,9 +180,9 @@ __device__ __forceinline__ void convert_block(const float (&v)[2][8], int C, int
 
 // Grid: images * n_pairs * n_split CTAs.  Per image: Gint [C][C] int64 (upper
 // tiles accumulated), Dsum [4][C] int64, scale [C].
-__global__ void __launch_bounds__(kThreads, 1) k_gram(const float *__restrict__ X, int layout, int vec_ok, int C, long N,
-                                                      const float *__restrict__ scale, int nt, int n_pairs,
-                                                      long chunk, unsigned long long *__restrict__ Gint,
+__global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ FitParams p,
+                                                      const float *__restrict__ scale,
+                                                      unsigned long long *__restrict__ Gint,
                                                       unsigned long long *__restrict__ Dsum,
                                                       int *__restrict__ status) {
     extern __shared__ uint8_t smem_raw[];
@@ -178,10 +194,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const float *__restrict__ 
     unsigned long long *dsq = (unsigned long long *)(tmem_slot + 4);  // [128] (8-B aligned: bar is)
     int *dsum = (int *)(dsq + kTB);                                    // [4][128]
 
-    const int per_img = n_pairs * (int)((N + chunk - 1) / chunk);
-    const int img = blockIdx.x / per_img, rem = blockIdx.x % per_img;
+    const long cta = blockIdx.x;
+    int img = 0;
+    while (img + 1 < p.n && p.img[img + 1].cta0 <= cta) img++;
+    const FitImgP &im = p.img[img];
+    const int C = p.C, layout = p.layout, vec_ok = p.vec_ok, nt = p.nt, n_pairs = p.n_pairs;
+    const long N = im.N, chunk = im.chunk;
+    const float *X = im.X;
+    const int rem = (int)(cta - im.cta0);
     const int pair = rem % n_pairs, split = rem / n_pairs;
-    X += (long)img * C * N;
     scale += (long)img * C;
     Gint += (long)img * C * C;
     Dsum += (long)img * kSlices * C;
@@ -326,11 +347,12 @@ __global__ void k_chan_scale(const unsigned *__restrict__ amax, int C, float *__
 // Sigma_ij = 2^(e_i+e_j) T_ij 2^-40 / N - mu_i mu_j ;  mu_c = 2^e_c S_c / N,
 // S_c = sum_i D_i,c 2^(-6-7i).  Writes mean[C] and the full symmetric cov[C][C]
 // of each image (grid.y = image).
-__global__ void k_cov_finalize(const unsigned long long *__restrict__ Gint, const unsigned long long *__restrict__ Dsum,
-                               const int *__restrict__ ex, int C, long N, double *__restrict__ mean,
-                               double *__restrict__ cov, float2 *__restrict__ cov_ff) {
-    const double invN = 1.0 / (double)N;
+__global__ void k_cov_finalize(const __grid_constant__ FitParams p, const unsigned long long *__restrict__ Gint,
+                               const unsigned long long *__restrict__ Dsum, const int *__restrict__ ex,
+                               double *__restrict__ mean, double *__restrict__ cov, float2 *__restrict__ cov_ff) {
     const long img = blockIdx.y;
+    const int C = p.C;
+    const double invN = 1.0 / (double)p.img[img].N;
     Gint += img * C * C;
     Dsum += img * kSlices * C;
     ex += img * C;
@@ -360,24 +382,14 @@ __global__ void k_cov_finalize(const unsigned long long *__restrict__ Gint, cons
 }  // namespace
 
 struct GramPlan {
-    int nt, n_pairs, n_split;
-    long chunk;
+    int nt, n_pairs;
     size_t off_amax, off_scale, off_ex, off_G, off_D, total, smem;
 };
 
-static GramPlan gram_plan(int C, long N, int nimg) {
+static GramPlan gram_plan(int C, int nimg) {
     GramPlan g{};
     g.nt = (C + kTB - 1) / kTB;
     g.n_pairs = g.nt * (g.nt + 1) / 2;
-    // about two waves of one CTA per SM over the batch, chunks a multiple of the window
-    int want = (2 * 152 + g.n_pairs * nimg - 1) / (g.n_pairs * nimg);
-    if (nimg == 1) want = (152 + g.n_pairs - 1) / g.n_pairs;
-    if (want < 1) want = 1;
-    long chunk = (N + want - 1) / want;
-    chunk = (chunk + kWin - 1) / kWin * kWin;
-    if (chunk < kWin) chunk = kWin;
-    g.chunk = chunk;
-    g.n_split = (int)((N + chunk - 1) / chunk);
     size_t o = 0;
     auto take = [&](size_t b) { size_t at = o; o = align_up(o + b, 256); return at; };
     g.off_amax = take(sizeof(unsigned) * (size_t)C * nimg);
@@ -390,22 +402,25 @@ static GramPlan gram_plan(int C, long N, int nimg) {
     return g;
 }
 
-size_t gram_workspace_bytes(int C, long N, int nimg) { return gram_plan(C, N, nimg).total; }
+size_t gram_workspace_bytes(int C, long N, int nimg) {
+    (void)N;
+    return gram_plan(C, nimg).total;
+}
 
-// mean[nimg][C] and cov[nimg][C][C] (FP64) of nimg feature maps stored one after
-// the other; ws: gram_workspace_bytes.
-cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, int nimg, double *mean, double *cov,
-                            void *cov_ff, void *ws, int *status, cudaStream_t st) {
-    const GramPlan g = gram_plan(C, N, nimg);
+// mean[n][C] and cov[n][C][C] (FP64) of the n feature maps of `jobs` (one
+// launch per stage for up to kMaxBatch images); ws: gram_workspace_bytes(C, *, n).
+cudaError_t launch_gram_cov_jobs(const FitJob *jobs, int n, int layout, int C, double *mean, double *cov, void *cov_ff,
+                                 void *ws, int *status, cudaStream_t st) {
+    const GramPlan g = gram_plan(C, n);
     char *b = (char *)ws;
     unsigned *amax = (unsigned *)(b + g.off_amax);
     float *scale = (float *)(b + g.off_scale);
     int *ex = (int *)(b + g.off_ex);
     unsigned long long *G = (unsigned long long *)(b + g.off_G);
     unsigned long long *D = (unsigned long long *)(b + g.off_D);
-    cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned) * (size_t)C * nimg, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, sizeof(unsigned long long) * (size_t)C * C * nimg, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(D, 0, sizeof(unsigned long long) * kSlices * (size_t)C * nimg, st);
+    cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned) * (size_t)C * n, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, sizeof(unsigned long long) * (size_t)C * C * n, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D, 0, sizeof(unsigned long long) * kSlices * (size_t)C * n, st);
     if (e != cudaSuccess) return e;
     static int attr_dev = -1;
     int dev = 0;
@@ -415,21 +430,68 @@ cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, int nimg,
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
-    // float4 loads need 16-B aligned rows: NCHW, N % 4 == 0, X 16-B aligned
-    const int vec_ok = layout == QFCA_NCHW && N % 4 == 0 && ((uintptr_t)X & 15) == 0;
-    const int xb = (int)((N + 256 * 64 - 1) / (256 * 64));
-    QFCA_LAUNCH("k_chan_absmax", st,
-                k_chan_absmax<<<dim3(xb < 1 ? 1 : xb, C, nimg), 256, 0, st>>>(X, layout, C, N, amax));
-    QFCA_LAUNCH("k_chan_scale", st,
-                k_chan_scale<<<(unsigned)((C * nimg + 127) / 128), 128, 0, st>>>(amax, C * nimg, scale, ex));
-    QFCA_LAUNCH("k_gram", st,
-                k_gram<<<g.n_pairs * g.n_split * nimg, kThreads, g.smem, st>>>(X, layout, vec_ok, C, N, scale, g.nt,
-                                                                              g.n_pairs, g.chunk, G, D, status));
-    const long cc = (long)C * C;
-    QFCA_LAUNCH("k_cov_finalize", st,
-                k_cov_finalize<<<dim3((unsigned)((cc + 255) / 256), nimg), 256, 0, st>>>(G, D, ex, C, N, mean, cov,
-                                                                                        (float2 *)cov_ff));
-    return cudaGetLastError();
+    for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
+        const int m = n - i0 < kMaxBatch ? n - i0 : kMaxBatch;
+        FitParams p;
+        memset(&p, 0, sizeof(p));
+        p.n = m, p.C = C, p.layout = layout, p.nt = g.nt, p.n_pairs = g.n_pairs;
+        // float4 loads need 16-B aligned rows: NCHW, N % 4 == 0, X 16-B aligned (every image)
+        int vec_ok = layout == QFCA_NCHW;
+        long total_px = 0, max_n = 1;
+        for (int i = 0; i < m; i++) {
+            const FitJob &j = jobs[i0 + i];
+            vec_ok = vec_ok && j.N % 4 == 0 && ((uintptr_t)j.X & 15) == 0;
+            total_px += j.N;
+            max_n = j.N > max_n ? j.N : max_n;
+        }
+        p.vec_ok = vec_ok;
+        // about two waves of one CTA per SM (one for a single image), chunks a multiple of the window
+        const long target = m == 1 ? 152 : 2 * 152;
+        long chunk = (total_px * g.n_pairs + target - 1) / target;
+        chunk = (chunk + kWin - 1) / kWin * kWin;
+        if (chunk < kWin) chunk = kWin;
+        long cta = 0;
+        for (int i = 0; i < m; i++) {
+            const FitJob &j = jobs[i0 + i];
+            FitImgP &im = p.img[i];
+            im.X = j.X, im.N = j.N, im.chunk = chunk;
+            im.n_split = (int)((j.N + chunk - 1) / chunk);
+            im.cta0 = cta;
+            cta += (long)im.n_split * g.n_pairs;
+        }
+        unsigned *am = amax + (size_t)i0 * C;
+        float *sc = scale + (size_t)i0 * C;
+        int *exi = ex + (size_t)i0 * C;
+        unsigned long long *Gi = G + (size_t)i0 * C * C;
+        unsigned long long *Di = D + (size_t)i0 * kSlices * C;
+        const int xb = (int)((max_n + 256 * 64 - 1) / (256 * 64));
+        QFCA_LAUNCH("k_chan_absmax", st, k_chan_absmax<<<dim3(xb < 1 ? 1 : xb, C, m), 256, 0, st>>>(p, am));
+        QFCA_LAUNCH("k_chan_scale", st,
+                    k_chan_scale<<<(unsigned)((C * m + 127) / 128), 128, 0, st>>>(am, C * m, sc, exi));
+        QFCA_LAUNCH("k_gram", st, k_gram<<<(unsigned)cta, kThreads, g.smem, st>>>(p, sc, Gi, Di, status));
+        const long cc = (long)C * C;
+        QFCA_LAUNCH("k_cov_finalize", st,
+                    k_cov_finalize<<<dim3((unsigned)((cc + 255) / 256), m), 256, 0, st>>>(
+                        p, Gi, Di, exi, mean + (size_t)i0 * C, cov + (size_t)i0 * C * C,
+                        cov_ff ? (float2 *)cov_ff + (size_t)i0 * C * C : nullptr));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, int nimg, double *mean, double *cov,
+                            void *cov_ff, void *ws, int *status, cudaStream_t st) {
+    // chunks of kMaxBatch images reuse the workspace in stream order
+    FitJob jobs[kMaxBatch];
+    for (int i0 = 0; i0 < nimg; i0 += kMaxBatch) {
+        const int m = nimg - i0 < kMaxBatch ? nimg - i0 : kMaxBatch;
+        for (int i = 0; i < m; i++) jobs[i] = FitJob{X + (long)(i0 + i) * C * N, N};
+        cudaError_t e = launch_gram_cov_jobs(jobs, m, layout, C, mean + (size_t)i0 * C, cov + (size_t)i0 * C * C,
+                                             cov_ff ? (float2 *)cov_ff + (size_t)i0 * C * C : nullptr, ws, status, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace qfca

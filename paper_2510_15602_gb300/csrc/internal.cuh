@@ -26,6 +26,16 @@ constexpr int kMaxBatch = 64;
 // other (feature maps C*H*W floats apart; per-image outputs likewise packed).
 
 // Workspace bytes needed by the fit of nimg C-channel maps of N pixels.
+// One image of a table-driven fit: feature map X (layout of the launch), N pixels.
+struct FitJob {
+    const float *X;
+    long N;
+};
+cudaError_t launch_gram_cov_jobs(const FitJob *jobs, int n, int layout, int C, double *mean, double *cov, void *cov_ff,
+                                 void *ws, int *status, cudaStream_t st);
+cudaError_t launch_fit_jobs(const FitJob *jobs, int n, int layout, int C, int d, double *mean, double *V,
+                            double *eigvals, void *ws, int *status, cudaStream_t st);
+
 size_t fit_workspace_bytes(int C, long N, int d, int nimg);
 
 // Enqueue the PCA fit of nimg images.  ws: device scratch of fit_workspace_bytes.
@@ -69,6 +79,11 @@ struct ProjJob {
     uint32_t *mm;
 };
 bool project_tma_ok(const float *X, long N, int layout);
+size_t project_bf16_workspace_bytes(int C, long N, int d, int nimg);
+cudaError_t launch_prep_bf16(const double *mean, const double *V, int C, int d, int n, void *ws, float **mean32_out,
+                             void **Vt_out, int *Cp_out, int *DT_out, cudaStream_t st);
+// min/max keys of nimg images (contiguous [nimg][2 d kKeyStride]) to their start values
+cudaError_t launch_init_keys(uint32_t *mm_keys, int d, int nimg, cudaStream_t st);
 cudaError_t launch_project_tma(const ProjJob *jobs, int n, int C, int d, int *status, cudaStream_t st);
 
 // min of component j at mm_keys[j * kKeyStride], max at mm_keys[(d + j) * kKeyStride].

@@ -141,6 +141,12 @@ int pick_dt(int d) { return d <= 16 ? 16 : (d <= 32 ? 32 : 64); }
 
 }  // namespace
 
+cudaError_t launch_init_keys(uint32_t *mm_keys, int d, int nimg, cudaStream_t st) {
+    const long nkeys = (long)nimg * 2 * d * kKeyStride;
+    QFCA_LAUNCH("k_init_keys", st, k_init_keys<<<(unsigned)((nkeys + 255) / 256), 256, 0, st>>>(mm_keys, d, nimg));
+    return cudaGetLastError();
+}
+
 size_t project_workspace_bytes(int C, long N, int d, int nimg) {
     const size_t f32 = align_up(sizeof(float) * (align_up(C, 64) + (size_t)C * 64) * nimg, 256);
     const size_t bf = project_bf16_workspace_bytes(C, N, d, nimg);

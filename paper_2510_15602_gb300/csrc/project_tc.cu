@@ -273,6 +273,23 @@ size_t project_bf16_workspace_bytes(int C, long N, int d, int nimg) {
            256;
 }
 
+// Prepared BF16 operands of n bases (packed mean [n][C], V [n][C][d]): mean32
+// [n][Cp] and Vt [n][DT][Cp] at the start of ws (project_bf16_workspace_bytes).
+cudaError_t launch_prep_bf16(const double *mean, const double *V, int C, int d, int n, void *ws, float **mean32_out,
+                             void **Vt_out, int *Cp_out, int *DT_out, cudaStream_t st) {
+    const TcShape sh = tc_shape(C, d);
+    float *mean32 = (float *)ws;
+    __nv_bfloat16 *Vt = (__nv_bfloat16 *)((char *)ws + align_up(sizeof(float) * sh.Cp * n, 256));
+    QFCA_LAUNCH("k_prep_bf16", st,
+                k_prep_bf16<<<dim3((sh.DT * sh.Cp + 255) / 256, n), 256, 0, st>>>(mean, V, C, d, sh.Cp, sh.DT, mean32,
+                                                                                  Vt));
+    *mean32_out = mean32;
+    *Vt_out = Vt;
+    *Cp_out = sh.Cp;
+    *DT_out = sh.DT;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_project_bf16(const float *X, int layout, int H, int W, int C, const double *mean,
                                 const double *V, int d, int nimg, float *Y, uint32_t *mm_keys, void *ws,
                                 int *status, cudaStream_t st) {

@@ -5,25 +5,31 @@
 // The projection reads each FP32 feature once and does 2d flops per byte, so
 // it is bound by HBM bandwidth; the design keeps HBM busy.  One persistent CTA
 // per SM owns a contiguous range of the table's 128-pixel tiles; a tile is
-// processed in K-chunks of 64 channels.  Roles (10 warps), synchronised only
+// processed in K-chunks of 64 channels.  Roles (14 warps), synchronised only
 // through mbarriers:
-//   - warp 0 (one thread): TMA producer.  Keeps a ring of `stages` 32 KB boxes
-//     (64 channels x 128 pixels of FP32, zero-filled beyond the image and
-//     beyond C) in flight; a stage is refilled once the converters release it.
-//   - warp 1 (one thread): MMA issuer.  For each converted chunk, 4
-//     tcgen05.mma (M=128, N=DT, K=16) into the tensor-memory accumulator,
-//     then tcgen05.commit to release the operand buffer; after a tile's last
-//     chunk, a commit signals the accumulator.
-//   - warps 2-9: converters and epilogue.  Centre each landed box by the
-//     mean, convert to BF16 into the 128-byte swizzled K-major operand layout
-//     (two operand buffers), release the stage, hand the chunk to the MMA
-//     warp; after a tile, read the accumulator back (tcgen05.ld), write Y
-//     [d][N] coalesced and keep running per-component min/max in registers,
-//     flushed per image as u32 keys.  At an image change they reload V^T
-//     (BF16, DT x Cp) and the FP32 mean into shared memory.
-// Every wait is bounded and also watches a CTA-wide abort flag; a wait that
-// runs out sets bit 0 of the status word and the abort flag, every role
-// leaves its loop, the copies and MMAs in flight drain (bounded), tensor
+//   - warp 0: TMA producer.  Keeps a ring of `stages` 32 KB boxes (64 channels
+//     x 128 pixels of FP32, zero-filled beyond the image and beyond C) in
+//     flight; a stage is refilled once the converters have read it.
+//   - warp 1: MMA issuer.  For each converted chunk, 4 tcgen05.mma (M=128,
+//     N=DT, K=16) into one of two tensor-memory accumulators (tiles
+//     alternate), then tcgen05.commit to release the operand buffer; after a
+//     tile's last chunk, a commit hands the accumulator to the epilogue.
+//   - warps 2-9: converters.  Read a landed box, release the stage, centre by
+//     the mean, convert to BF16 into the 128-byte swizzled K-major operand
+//     layout (a ring of operand buffers), hand the chunk to the MMA warp.  At
+//     an image change they wait for the MMAs in flight and reload V^T (BF16,
+//     DT x Cp) and the FP32 mean into shared memory.
+//   - warps 10-13: epilogue, one per accumulator lane quarter: read the
+//     accumulator back (tcgen05.ld, 16 columns at a time), write Y [d][N]
+//     coalesced, fold each 16-column group's min/max over the warp's 32
+//     pixels with a halving shuffle reduction (lane L ends up owning column
+//     (L >> 1) & 15 of the group), keep running values per lane and flush
+//     them once per image as u32 keys, and release the accumulator; this
+//     overlaps the next tile's conversion and MMAs.
+// Every role keeps its warps converged (one lane issues) and every wait is
+// bounded and watches a CTA-wide abort flag; a wait that runs out sets bit 0
+// of the status word and the flag, every role leaves its loop (still passing
+// its named barriers), the copies and MMAs in flight drain (bounded), tensor
 // memory is freed and the CTA returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -38,8 +44,10 @@ namespace {
 constexpr int kM = 128;        // pixels per tile (MMA M)
 constexpr int kKc = 64;        // channels per K-chunk / TMA box (one 128-B swizzle row of BF16)
 constexpr int kConv = 256;     // converter threads (warps 2-9)
-constexpr int kThreads = 64 + kConv;
+constexpr int kEpi = 128;      // epilogue threads (warps 10-13)
+constexpr int kThreads = 64 + kConv + kEpi;
 constexpr int kMaxStages = 5;
+constexpr int kMaxA = 4;       // operand buffers (chunks converted ahead of the MMAs)
 constexpr uint32_t kStageBytes = kKc * kM * 4;  // 32 KB of FP32
 constexpr uint32_t kAChunk = kM * 128;           // 16 KB of BF16
 constexpr uint32_t kTries = 1u << 26;
@@ -53,7 +61,7 @@ struct ProjImgP {
 };
 
 struct ProjParams {
-    int n, C, Cp, nk, d, stages;
+    int n, C, Cp, nk, d, stages, na;
     long total_tiles;
     ProjImgP img[kMaxBatch];
     CUtensorMap tmap[kMaxBatch];    // X of image i as [C][N] FP32, box {128 pixels, 64 channels}
@@ -80,7 +88,35 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
     return false;
 }
 
+// Warp-wide bounded wait: every lane probes (and so acquires the completed
+// phase); the result is agreed across the warp.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    return __all_sync(0xffffffffu, wait_or_abort(bar, parity, abort_flag));
+}
+
+// Min (or max) of 16 values per lane over the 32 lanes of a warp, halving
+// the data at each exchange: on return v[0] of lane L holds the reduction of
+// value (L >> 1) & 15 over all lanes.  NaN inputs are ignored (fminf/fmaxf).
+template <bool kMin>
+__device__ __forceinline__ void warp_reduce16(float (&v)[16]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16, h = 8; o >= 2; o >>= 1, h >>= 1) {
+        const bool up = (lane & o) != 0;  // this lane keeps the upper half of its values
+#pragma unroll
+        for (int i = 0; i < h; i++) {
+            const float send = up ? v[i] : v[i + h];
+            const float keep = up ? v[i + h] : v[i];
+            const float recv = __shfl_xor_sync(0xffffffffu, send, o);
+            v[i] = kMin ? fminf(keep, recv) : fmaxf(keep, recv);
+        }
+    }
+    const float recv = __shfl_xor_sync(0xffffffffu, v[0], 1);
+    v[0] = kMin ? fminf(v[0], recv) : fmaxf(v[0], recv);
+}
+
 __device__ __forceinline__ void conv_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConv) : "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 2, %0;" ::"n"(kEpi) : "memory"); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
@@ -90,19 +126,19 @@ struct SmemLayout {
     size_t stage, a, b, mean, bar, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int stages, int Cp, int DT) {
+__host__ __device__ inline SmemLayout smem_layout(int stages, int na, int Cp, int DT) {
     SmemLayout L;
     size_t o = 0;
     L.stage = o;
     o += (size_t)stages * kStageBytes;
     L.a = o;
-    o += 2 * (size_t)kAChunk;
+    o += (size_t)na * kAChunk;
     L.b = o;
     o += (size_t)(Cp / kKc) * DT * 128;
     L.mean = o;
     o += sizeof(float) * (size_t)Cp;
     L.bar = o;
-    o += 8 * (2 * kMaxStages + 6) + 16 + 2 * 4 * 64;  // barriers, tmem slot + abort flag, kmin/kmax
+    o += 8 * (2 * kMaxStages + 2 * kMaxA + 4) + 16 + 2 * 4 * 64;  // barriers, tmem slot + abort flag, kmin/kmax
     L.total = o + 1024;                                // alignment slack
     return L;
 }
@@ -112,25 +148,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
                                                             int *__restrict__ status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = tc::align_smem<1024>(smem_raw);
-    const SmemLayout L = smem_layout(p.stages, p.Cp, DT);
+    const SmemLayout L = smem_layout(p.stages, p.na, p.Cp, DT);
     uint8_t *stage = smem + L.stage;
     uint8_t *As = smem + L.a;
     uint8_t *Bs = smem + L.b;
     float *mean_s = reinterpret_cast<float *>(smem + L.mean);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bar);  // [kMaxStages] TMA landed
     uint64_t *empty = full + kMaxStages;                            // [kMaxStages] converters done with a stage
-    uint64_t *a_full = empty + kMaxStages;                          // [2] operand chunk converted
-    uint64_t *a_empty = a_full + 2;                                 // [2] MMAs of a chunk complete
-    uint64_t *acc_full = a_empty + 2;                               // tile's MMAs complete
-    uint64_t *acc_empty = acc_full + 1;                             // accumulator read back
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 1);
+    uint64_t *a_full = empty + kMaxStages;                          // [kMaxA] operand chunk converted
+    uint64_t *a_empty = a_full + kMaxA;                             // [kMaxA] MMAs of a chunk complete
+    uint64_t *acc_full = a_empty + kMaxA;                           // [2] tile's MMAs complete
+    uint64_t *acc_empty = acc_full + 2;                             // [2] accumulator read back
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     uint32_t *kmin = tmem_slot + 4;  // [64]
     uint32_t *kmax = kmin + 64;      // [64]
-    constexpr uint32_t kCols = DT < 32 ? 32 : DT;
+    constexpr uint32_t kCols = 2 * DT < 32 ? 32 : 2 * DT;  // two accumulators
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int nk = p.nk, S = p.stages, d = p.d;
+    const int nk = p.nk, S = p.stages, NA = p.na, d = p.d;
     if (warp == 0) {
         tc::tmem_alloc(tmem_slot, kCols);
         tc::tmem_relinquish();
@@ -140,12 +176,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], kConv / 32);
         }
-        for (int b = 0; b < 2; b++) {
+        for (int b = 0; b < kMaxA; b++) {
             tc::mbar_init(&a_full[b], kConv / 32);
             tc::mbar_init(&a_empty[b], 1);
         }
-        tc::mbar_init(acc_full, 1);
-        tc::mbar_init(acc_empty, kConv / 32);
+        for (int b = 0; b < 2; b++) {
+            tc::mbar_init(&acc_full[b], 1);
+            tc::mbar_init(&acc_empty[b], kEpi / 32);
+        }
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -169,8 +207,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
         long q = 0;
         for (; q < n_chunks; q++) {
             const int s = (int)(q % S);
-            bool ok = q < S || wait_or_abort(&empty[s], (uint32_t)((q / S - 1) & 1), abort_flag);
-            if (!__all_sync(kFull, ok)) break;
+            const bool ok = q < S || warp_wait(&empty[s], (uint32_t)((q / S - 1) & 1), abort_flag);
+            if (!ok) break;
             if (lane == 0) {
                 const long w = w0 + q / nk;
                 const int kc = (int)(q % nk);
@@ -192,77 +230,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
         long q = 0, last_commit = -1;
         bool ok = true;
         for (long tile = 0; ok && tile < w1 - w0; tile++) {
-            if (tile >= 1) ok = __all_sync(kFull, wait_or_abort(acc_empty, (uint32_t)((tile - 1) & 1), abort_flag));
+            const int ac = (int)(tile & 1);
+            if (tile >= 2) ok = warp_wait(&acc_empty[ac], (uint32_t)((tile / 2 - 1) & 1), abort_flag);
             for (int kc = 0; ok && kc < nk; kc++, q++) {
-                const int ab = (int)(q & 1);
-                ok = __all_sync(kFull, wait_or_abort(&a_full[ab], (uint32_t)((q >> 1) & 1), abort_flag));
+                const int ab = (int)(q % NA);
+                ok = warp_wait(&a_full[ab], (uint32_t)((q / NA) & 1), abort_flag);
                 if (!ok) break;
                 tc::tc_fence_after();
                 if (lane == 0) {
                     const uint32_t a0 = a_base + (uint32_t)ab * kAChunk, b0 = b_base + (uint32_t)kc * DT * 128;
 #pragma unroll
                     for (int ks = 0; ks < 4; ks++)
-                        tc::mma_bf16_ss(tmem, tc::sdesc_kmajor_sw128(a0 + ks * 32), tc::sdesc_kmajor_sw128(b0 + ks * 32),
-                                        idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+                        tc::mma_bf16_ss(tmem + (uint32_t)(ac * DT), tc::sdesc_kmajor_sw128(a0 + ks * 32),
+                                        tc::sdesc_kmajor_sw128(b0 + ks * 32), idesc, (kc > 0 || ks > 0) ? 1u : 0u);
                     tc::mma_commit(&a_empty[ab]);
-                    if (kc == nk - 1) tc::mma_commit(acc_full);
+                    if (kc == nk - 1) tc::mma_commit(&acc_full[ac]);
                 }
                 __syncwarp();
                 last_commit = q;
             }
         }
         if (*abort_flag && last_commit >= 0 && lane == 0)  // bounded drain of the MMAs in flight
-            tc::mbar_wait(&a_empty[last_commit & 1], (uint32_t)((last_commit >> 1) & 1), kTries);
-    } else {
-        // ---------------------------------------------------------------- converters + epilogue
-        const int ct = t - 64, cw = warp - 2;
-        const int m = ct & (kM - 1), h = ct >> 7;        // pixel row m, channels [32 h, 32 h + 32) of a chunk
-        const int quarter = warp & 3, chalf = cw >> 2;   // TMEM lane quarter (warp id % 4), column half
-        constexpr int CW = DT >= 32 ? DT / 2 : 16;
-        const bool epi = DT >= 32 || chalf == 0;
-        const int jbase = DT >= 32 ? chalf * CW : 0;
-        float rmn[CW], rmx[CW];
-#pragma unroll
-        for (int i = 0; i < CW; i++) { rmn[i] = __int_as_float(0x7f800000); rmx[i] = -__int_as_float(0x7f800000); }
-        auto flush = [&](int img) {  // all converter threads
-            if (epi) {
-#pragma unroll
-                for (int i = 0; i < CW; i++) {
-                    float mn = rmn[i], mx = rmx[i];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        mn = fminf(mn, __shfl_xor_sync(kFull, mn, o));
-                        mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
-                    }
-                    const int j = jbase + i;
-                    if (lane == 0 && j < d) {
-                        atomicMin(&kmin[j], f2key(mn));
-                        atomicMax(&kmax[j], f2key(mx));
-                    }
-                    rmn[i] = __int_as_float(0x7f800000);
-                    rmx[i] = -__int_as_float(0x7f800000);
-                }
-            }
-            conv_sync();
-            if (ct < d) {
-                uint32_t *mm = p.img[img].mm;
-                atomicMin(&mm[ct * kKeyStride], kmin[ct]);
-                atomicMax(&mm[(d + ct) * kKeyStride], kmax[ct]);
-                kmin[ct] = 0xffffffffu;
-                kmax[ct] = 0u;
-            }
-        };
+            tc::mbar_wait(&a_empty[last_commit % NA], (uint32_t)((last_commit / NA) & 1), kTries);
+    } else if (warp < 10) {
+        // ---------------------------------------------------------------- converters
+        const int ct = t - 64;
+        const int m = ct & (kM - 1), h = ct >> 7;  // pixel row m, channels [32 h, 32 h + 32) of a chunk
         int cur = -1;
         long q = 0;
         bool ok = true;  // warp-uniform; once false the warp only keeps passing the named barriers
         for (long tile = 0; tile < w1 - w0; tile++) {
             const long w = w0 + tile;
             const int img = find_img(p, w);
-            const ProjImgP &im = p.img[img];
             if (img != cur) {
-                // image change: the previous tile's MMAs completed (its epilogue waited for them)
-                if (cur >= 0) flush(cur);
+                // image change: wait for the MMAs in flight (they read the old V^T), then reload
+                if (ok && q >= 1)
+                    ok = warp_wait(&a_empty[(q - 1) % NA], (uint32_t)(((q - 1) / NA) & 1), abort_flag);
                 conv_sync();
+                const ProjImgP &im = p.img[img];
                 for (int c = ct; c < p.Cp; c += kConv) mean_s[c] = im.mean32[c];
                 for (int e = ct; e < DT * (p.Cp / 8); e += kConv) {
                     const int j = e / (p.Cp / 8), c8 = e % (p.Cp / 8);
@@ -274,61 +279,106 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
                 cur = img;
             }
             for (int kc = 0; kc < nk; kc++, q++) {
-                const int s = (int)(q % S), ab = (int)(q & 1);
-                if (ok) ok = __all_sync(kFull, wait_or_abort(&full[s], (uint32_t)((q / S) & 1), abort_flag));
-                if (ok && q >= 2)
-                    ok = __all_sync(kFull, wait_or_abort(&a_empty[ab], (uint32_t)(((q - 2) >> 1) & 1), abort_flag));
+                const int s = (int)(q % S), ab = (int)(q % NA);
+                if (ok) ok = warp_wait(&full[s], (uint32_t)((q / S) & 1), abort_flag);
                 if (!ok) continue;
+                // read the 32 features first and release the stage, then wait for the operand buffer
                 const float *xs = reinterpret_cast<const float *>(stage + (size_t)s * kStageBytes) + (32 * h) * kM + m;
+                float xv[32];
+#pragma unroll
+                for (int i = 0; i < 32; i++) xv[i] = xs[i * kM];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+                if (q >= NA) ok = warp_wait(&a_empty[ab], (uint32_t)((q / NA - 1) & 1), abort_flag);
+                if (!ok) continue;
                 const float4 *mu4 = reinterpret_cast<const float4 *>(mean_s + kc * kKc + 32 * h);
                 uint8_t *arow = As + (size_t)ab * kAChunk;
 #pragma unroll
                 for (int g = 0; g < 4; g++) {
                     const float4 ma = mu4[2 * g], mb = mu4[2 * g + 1];
-                    const float *x8 = xs + (8 * g) * kM;
+                    const float *x8 = xv + 8 * g;
                     uint4 pk;
-                    pk.x = tc::pack_bf16x2(x8[0 * kM] - ma.x, x8[1 * kM] - ma.y);
-                    pk.y = tc::pack_bf16x2(x8[2 * kM] - ma.z, x8[3 * kM] - ma.w);
-                    pk.z = tc::pack_bf16x2(x8[4 * kM] - mb.x, x8[5 * kM] - mb.y);
-                    pk.w = tc::pack_bf16x2(x8[6 * kM] - mb.z, x8[7 * kM] - mb.w);
+                    pk.x = tc::pack_bf16x2(x8[0] - ma.x, x8[1] - ma.y);
+                    pk.y = tc::pack_bf16x2(x8[2] - ma.z, x8[3] - ma.w);
+                    pk.z = tc::pack_bf16x2(x8[4] - mb.x, x8[5] - mb.y);
+                    pk.w = tc::pack_bf16x2(x8[6] - mb.z, x8[7] - mb.w);
                     *reinterpret_cast<uint4 *>(arow + swz_off(m, 4 * h + g)) = pk;
                 }
                 tc::fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(&empty[s]);
-                    mbar_arrive(&a_full[ab]);
-                }
+                if (lane == 0) mbar_arrive(&a_full[ab]);
             }
-            // epilogue: this warp's 32 accumulator lanes, its half of the columns
-            if (ok) ok = __all_sync(kFull, wait_or_abort(acc_full, (uint32_t)(tile & 1), abort_flag));
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int et = t - 64 - kConv;
+        const int quarter = warp & 3;  // TMEM lane quarter (warp id % 4)
+        constexpr int NG = DT / 16;    // 16-column groups
+        const int own = (lane >> 1) & 15;  // column of each group this lane accumulates
+        float rmn[NG], rmx[NG];
+#pragma unroll
+        for (int g = 0; g < NG; g++) { rmn[g] = __int_as_float(0x7f800000); rmx[g] = -__int_as_float(0x7f800000); }
+        auto flush = [&](int img) {  // all epilogue threads
+#pragma unroll
+            for (int g = 0; g < NG; g++) {
+                const int j = 16 * g + own;
+                if ((lane & 1) == 0 && j < d) {
+                    atomicMin(&kmin[j], f2key(rmn[g]));
+                    atomicMax(&kmax[j], f2key(rmx[g]));
+                }
+                rmn[g] = __int_as_float(0x7f800000);
+                rmx[g] = -__int_as_float(0x7f800000);
+            }
+            epi_sync();
+            if (et < d) {
+                uint32_t *mm = p.img[img].mm;
+                atomicMin(&mm[et * kKeyStride], kmin[et]);
+                atomicMax(&mm[(d + et) * kKeyStride], kmax[et]);
+                kmin[et] = 0xffffffffu;
+                kmax[et] = 0u;
+            }
+            epi_sync();
+        };
+        int cur = -1;
+        bool ok = true;
+        for (long tile = 0; tile < w1 - w0; tile++) {
+            const long w = w0 + tile;
+            const int img = find_img(p, w);
+            if (img != cur) {
+                if (cur >= 0) flush(cur);
+                cur = img;
+            }
+            const ProjImgP &im = p.img[img];
+            const int ac = (int)(tile & 1);
+            if (ok) ok = warp_wait(&acc_full[ac], (uint32_t)((tile / 2) & 1), abort_flag);
             if (!ok) continue;
             tc::tc_fence_after();
-            if (epi) {
-                const long pe = (w - im.tile0) * kM + 32 * quarter + lane;
-                const bool valid = pe < im.N;
+            const long pe = (w - im.tile0) * kM + 32 * quarter + lane;
+            const bool valid = pe < im.N;
 #pragma unroll
-                for (int j0 = 0; j0 < CW; j0 += 16) {
-                    uint32_t r[16];
-                    tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(jbase + j0), r);
-                    tc::tmem_wait_ld();
+            for (int g = 0; g < NG; g++) {
+                uint32_t r[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(ac * DT + 16 * g), r);
+                tc::tmem_wait_ld();
+                float vmn[16], vmx[16];
 #pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        const int j = jbase + j0 + i;
-                        const float v = __uint_as_float(r[i]);
-                        if (j < d && valid) {
-                            im.Y[(long)j * im.N + pe] = v;
-                            rmn[j0 + i] = fminf(rmn[j0 + i], v);
-                            rmx[j0 + i] = fmaxf(rmx[j0 + i], v);
-                        }
-                    }
+                for (int i = 0; i < 16; i++) {
+                    const int j = 16 * g + i;
+                    const float v = __uint_as_float(r[i]);
+                    if (j < d && valid) im.Y[(long)j * im.N + pe] = v;
+                    vmn[i] = valid ? v : __int_as_float(0x7fc00000);  // NaN: ignored by the reduction
+                    vmx[i] = vmn[i];
                 }
+                warp_reduce16<true>(vmn);
+                warp_reduce16<false>(vmx);
+                rmn[g] = fminf(rmn[g], vmn[0]);
+                rmx[g] = fmaxf(rmx[g], vmx[0]);
             }
             tc::tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty);
+            if (lane == 0) mbar_arrive(&acc_empty[ac]);
         }
-        if (cur >= 0) flush(cur);  // unconditional: every converter thread passes the same barriers
+        if (cur >= 0) flush(cur);  // unconditional: every epilogue thread passes the same barriers
     }
     if (t == 0 && *abort_flag) atomicOr(status, kStatusMmaTimeout);
     tc::tc_fence_before();
@@ -351,7 +401,7 @@ cudaError_t launch_dt(const ProjParams &p, int *status, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
-    const size_t smem = smem_layout(p.stages, p.Cp, DT).total;
+    const size_t smem = smem_layout(p.stages, p.na, p.Cp, DT).total;
     const long grid = p.total_tiles < n_sm ? p.total_tiles : n_sm;
     QFCA_LAUNCH("k_project_tma", st, k_project_tma<DT><<<(unsigned)grid, kThreads, smem, st>>>(p, status));
     return cudaGetLastError();
@@ -366,14 +416,20 @@ bool project_tma_ok(const float *X, long N, int layout) {
 cudaError_t launch_project_tma(const ProjJob *jobs, int n, int C, int d, int *status, cudaStream_t st) {
     const int DT = d <= 16 ? 16 : (d <= 32 ? 32 : 64);
     const int Cp = (C + kKc - 1) / kKc * kKc;
-    int stages = kMaxStages;
-    while (stages > 2 && smem_layout(stages, Cp, DT).total > 227 * 1024) stages--;
-    if (smem_layout(stages, Cp, DT).total > 227 * 1024) return cudaErrorNotSupported;
+    // deepest TMA ring first (bytes in flight), then the deepest operand ring
+    int stages = 0, na = 0;
+    for (int sg = kMaxStages; sg >= 3 && !stages; sg--)
+        for (int a = kMaxA; a >= 2; a--)
+            if (smem_layout(sg, a, Cp, DT).total <= 227 * 1024) { stages = sg, na = a; break; }
+    if (!stages) {
+        stages = 2, na = 2;
+        if (smem_layout(stages, na, Cp, DT).total > 227 * 1024) return cudaErrorNotSupported;
+    }
     for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
         const int m = n - i0 < kMaxBatch ? n - i0 : kMaxBatch;
         ProjParams p;
         memset(&p, 0, sizeof(p));
-        p.n = m, p.C = C, p.Cp = Cp, p.nk = Cp / kKc, p.d = d, p.stages = stages;
+        p.n = m, p.C = C, p.Cp = Cp, p.nk = Cp / kKc, p.d = d, p.stages = stages, p.na = na;
         long tiles = 0;
         for (int i = 0; i < m; i++) {
             const ProjJob &j = jobs[i0 + i];

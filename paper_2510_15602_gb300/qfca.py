@@ -87,6 +87,19 @@ _lib.qfca_batch_run.argtypes = [_P, _P, _I, Fmap, _I, _I, _I, _I, _P, ctypes.POI
 _lib.qfca_batch_run.restype = _I
 
 
+class Image(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int), ("r", ctypes.c_int),
+                ("score", ctypes.c_void_p)]
+
+
+_lib.qfca_score_batch.argtypes = [_P, ctypes.POINTER(Image), _I, _I, _I, _I, _I, _I, _P]
+_lib.qfca_score_batch.restype = _I
+_lib.qfca_set_autotune.argtypes = [_P, _I]
+_lib.qfca_set_autotune.restype = _I
+_lib.qfca_last_tiling.argtypes = [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]
+_lib.qfca_last_tiling.restype = _I
+
+
 class QfcaError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{_lib.qfca_status_string(status).decode()}: {msg}")
@@ -128,6 +141,16 @@ class Context:
         if s not in (OK, ERR_TIMEOUT):
             self.check(s)
         return int(v.value)
+
+    def set_autotune(self, on: bool):
+        """Measure the window stage's tilings once per shape set (True) or use the cost model (False)."""
+        self.check(_lib.qfca_set_autotune(self.handle, 1 if on else 0))
+
+    def last_tiling(self) -> tuple[int, int, int]:
+        """(strip width, band height, component groups) of the most recent window-stage launch."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self.check(_lib.qfca_last_tiling(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return int(a.value), int(b.value), int(c.value)
 
     def launch_count(self) -> int:
         n = ctypes.c_uint64()
@@ -320,6 +343,31 @@ def batch_run(X: torch.Tensor, d: int, B: int, r: int, precision="bf16", ctx: Co
     ctx.check(_lib.qfca_batch_run(ctx.handle, _ptr(X), nimg, fm, d, B, r, _PREC[precision], _ptr(scores),
                                   ctypes.byref(ext) if ext is not None else None, _P(_stream_ptr(stream))))
     return (scores, ex) if extras else scores
+
+
+def score_batch(Xs, rs, d: int, B: int, precision="bf16", layout: int = NCHW, ctx: Context | None = None,
+                stream=None, scores=None):
+    """qfca_score_batch: the whole path for images of different sizes and radii.
+
+    Xs: list of device FP32 maps [C, H_i, W_i] (NCHW) or [H_i, W_i, C] (NHWC);
+    rs: one window radius per image.  Returns the list of score maps [H_i, W_i].
+    """
+    if len(Xs) != len(rs) or not Xs:
+        raise ValueError("one radius per image, at least one image")
+    ctx = ctx or default_context(Xs[0].device.index)
+    fms = [fmap_of(X, layout) for X in Xs]
+    C = fms[0].C
+    if any(fm.C != C for fm in fms):
+        raise ValueError("every image needs the same channel count")
+    if scores is None:
+        scores = [torch.empty(fm.H, fm.W, dtype=torch.float32, device=X.device) for fm, X in zip(fms, Xs)]
+    arr = (Image * len(Xs))()
+    for i, (X, fm, r, sc) in enumerate(zip(Xs, fms, rs, scores)):
+        _check_dev(X, f"Xs[{i}]", torch.float32)
+        arr[i] = Image(_ptr(X), fm.H, fm.W, int(r), _ptr(sc))
+    ctx.check(_lib.qfca_score_batch(ctx.handle, arr, len(Xs), C, layout, d, B, _PREC[precision],
+                                    _P(_stream_ptr(stream))))
+    return scores
 
 
 def run_image(X: torch.Tensor, d: int, B: int, r: int, precision="f32", layout: int = NCHW,

@@ -400,3 +400,85 @@ def test_batch_run_full_size_against_oracle_integer_stages(q):
         np.testing.assert_array_equal(ex["ref_hist"][i].cpu().numpy().astype(np.uint32), R)
         s_o, _, _ = oracle.score(qb, 32, 7, R, 256 * 256)
         np.testing.assert_allclose(sb[i].cpu().numpy(), s_o, rtol=2.0 ** -23, atol=1e-12)
+
+
+# ------------------------------------------------------------------ uneven batch (one launch per stage over an image table)
+
+def _uneven_images(C, sizes, seed0):
+    return [synth.small_case(C=C, H=h, W=w, sigma=2.0, seed=seed0 + i, n_square=1, side=8, nch=6)
+            for i, (h, w) in enumerate(sizes)]
+
+
+@pytest.mark.parametrize("precision", ["bf16", "f32"])
+def test_score_batch_uneven_equals_single_image_calls(q, precision):
+    # sizes and radii differ per image; the table-driven launches must give
+    # each image exactly what the single-image entry points give it
+    C, d, B = 64, 16, 64
+    sizes = [(96, 104), (64, 72), (120, 88), (48, 160)]
+    rs = [5, 7, 9, 12]
+    imgs = _uneven_images(C, sizes, 70)
+    Xs = [to_dev(im.X) for im in imgs]
+    ctx = q.Context()
+    sb = q.score_batch(Xs, rs, d, B, precision, ctx=ctx)
+    torch.cuda.synchronize()
+    for i, (X, (H, W), r) in enumerate(zip(Xs, sizes, rs)):
+        basis = q.fit_pca(X, d, ctx=ctx)
+        out = q.quantize(X, basis, B, precision, ctx=ctx)
+        s1 = q.score(out["bins"], W, B, r, out["hist"], H * W, ctx=ctx)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(sb[i].cpu().numpy(), s1.cpu().numpy())
+    assert ctx.device_status() == 0
+
+
+def test_score_batch_uneven_integer_stages_against_oracle(q):
+    # one image of the batch checked end to end: eigenvalues against the
+    # oracle's fit, and the oracle's window EMD on the GPU's own bins
+    C, d, B = 64, 16, 64
+    sizes = [(72, 80), (104, 96)]
+    rs = [7, 5]
+    imgs = _uneven_images(C, sizes, 90)
+    Xs = [to_dev(im.X) for im in imgs]
+    sb = q.score_batch(Xs, rs, d, B, "f32")
+    torch.cuda.synchronize()
+    for i, (X, (H, W), r) in enumerate(zip(Xs, sizes, rs)):
+        basis = q.fit_pca(X, d)
+        out = q.quantize(X, basis, B, "f32")
+        torch.cuda.synchronize()
+        qb = bins_np(out["bins"], W)
+        R = oracle.ref_hist(qb, B)
+        s_o, _, _ = oracle.score(qb, B, r, R, H * W)
+        np.testing.assert_allclose(sb[i].cpu().numpy(), s_o, rtol=2.0 ** -23, atol=1e-12)
+
+
+def test_score_batch_autotune_keeps_results(q):
+    C, d, B = 64, 16, 32
+    sizes = [(80, 96), (96, 64), (64, 64)]
+    rs = [7, 5, 9]
+    imgs = _uneven_images(C, sizes, 110)
+    Xs = [to_dev(im.X) for im in imgs]
+    ctx = q.Context()
+    s_model = [s.clone() for s in q.score_batch(Xs, rs, d, B, "bf16", ctx=ctx)]
+    model_tiling = ctx.last_tiling()
+    ctx.set_autotune(True)
+    s_tuned = q.score_batch(Xs, rs, d, B, "bf16", ctx=ctx)
+    tuned = ctx.last_tiling()
+    s_again = q.score_batch(Xs, rs, d, B, "bf16", ctx=ctx)
+    torch.cuda.synchronize()
+    assert tuned[0] in (64, 128) and 1 <= tuned[1] <= 64 and 1 <= tuned[2] <= d
+    assert ctx.last_tiling() == tuned  # cached for the same shapes
+    assert model_tiling[0] in (64, 128)
+    for a, b, c in zip(s_model, s_tuned, s_again):
+        np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+        np.testing.assert_array_equal(a.cpu().numpy(), c.cpu().numpy())
+
+
+def test_score_batch_rejects_bad_arguments(q):
+    X = to_dev(synth.small_case(C=16, H=16, W=16, sigma=1.0, seed=1, n_square=0, side=4, nch=2).X)
+    with pytest.raises(q.QfcaError):
+        q.score_batch([X], [0], 4, 16)          # r < 1
+    with pytest.raises(q.QfcaError):
+        q.score_batch([X], [64], 4, 16)         # 2r+1 > 127
+    with pytest.raises(q.QfcaError):
+        q.score_batch([X], [3], 4, 1)           # B < 2
+    with pytest.raises(ValueError):
+        q.score_batch([X], [3, 4], 4, 16)       # one radius per image
