@@ -260,6 +260,81 @@ qfca_status qfca_score_noalloc(const uint8_t *bins, int H, int W, int pitch, int
                                const uint32_t *ref_hist, uint32_t ref_total, float *score,
                                void *stream);
 
+/* ---------------------------------------------------------------- serving
+ *
+ * A serving session keeps per-class PCA bases, quantisation ranges and
+ * reference histograms resident on the device and scores single images as
+ * they arrive (the paper's per-texture setting of Sec. 4: one reference per
+ * texture class, fitted once).  Requests wait in a FIFO queue; a scheduler
+ * thread admits them to the GPU as device memory (a fixed arena) and stream
+ * slots free up, packs the admitted ones into one table-driven batch (one
+ * launch per stage for up to max_batch images of mixed sizes and radii) and
+ * keeps several batches in flight on separate streams, so requests that
+ * arrive while others run start as soon as resources allow (continuous
+ * batching).  A request's result does not depend on what it was batched with.
+ * Per image: projection with the class basis (BF16 or FP32), quantisation
+ * with the class's fixed range (values outside clamp to the end bins), the
+ * window EMD against the class reference (N_ref = its total), the component
+ * mean. */
+
+typedef struct {
+    int C, d, B;               /* shared by every class and request of the session */
+    int precision;             /* QFCA_F32 or QFCA_BF16 */
+    int max_batch;             /* images per launched batch, 1..64 */
+    int streams;               /* batches in flight at once, 1..8 */
+    int max_queue;             /* pending requests before submit answers QFCA_ERR_BUSY */
+    size_t arena_bytes;        /* device memory for in-flight requests (admission budget) */
+} qfca_serve_config;
+
+#define QFCA_REQ_HOST_INPUT 1  /* X is pinned host memory (copied in on the batch's stream) */
+#define QFCA_REQ_HOST_OUTPUT 2 /* score is pinned host memory (copied out on the batch's stream) */
+
+typedef struct {
+    int class_id;
+    const float *X;            /* [C][H][W] FP32, NCHW; device unless QFCA_REQ_HOST_INPUT */
+    int H, W;
+    int r;                     /* window radius, 1..63 */
+    float *score;              /* [H][W] FP32 out; device unless QFCA_REQ_HOST_OUTPUT */
+    int flags;
+} qfca_request;
+
+typedef struct {
+    int status;                /* qfca_status of the request */
+    int batch_size;            /* images in the batch it ran in */
+    double t_submit_us;        /* host steady-clock stamps, microseconds since the session started */
+    double t_start_us;         /* batch launched */
+    double t_done_us;          /* batch completed on the GPU (stream callback) */
+} qfca_result;
+
+/* Start the session's scheduler (one per context).  Allocates the arena and
+ * the streams; QFCA_ERR_OOM when the arena cannot be allocated. */
+qfca_status qfca_serve_start(qfca_ctx *ctx, const qfca_serve_config *cfg);
+
+/* Copy a class into the session: mean [C] and V [C][d] (FP64, column k =
+ * component k, as qfca_fit_pca writes them), the fixed range lo/hi [d] and the
+ * reference histogram ref_hist [d][B] with N_ref = ref_total; all device
+ * pointers, read before the call returns.  Re-registering an id replaces it
+ * (requests already admitted keep the old copy until they finish). */
+qfca_status qfca_register_class(qfca_ctx *ctx, int class_id, const double *mean, const double *V,
+                                const float *lo, const float *hi, const uint32_t *ref_hist,
+                                uint32_t ref_total);
+
+/* Queue one request (non-blocking).  *ticket identifies it for qfca_poll.
+ * QFCA_ERR_BUSY: the queue is full (retry later); QFCA_ERR_UNSUPPORTED: the
+ * request can never fit the arena; QFCA_ERR_INVALID_ARG: bad request or
+ * unknown class.  The caller keeps X and score alive until poll returns OK. */
+qfca_status qfca_submit(qfca_ctx *ctx, const qfca_request *req, uint64_t *ticket);
+
+/* Wait up to timeout_us (0: just look) for a request.  QFCA_OK: done, *out
+ * filled and the ticket retired; QFCA_PENDING: not yet; QFCA_ERR_INVALID_ARG:
+ * unknown ticket. */
+qfca_status qfca_poll(qfca_ctx *ctx, uint64_t ticket, int timeout_us, qfca_result *out);
+
+/* Drain every queued and in-flight request, then stop the scheduler and free
+ * the session's device memory.  Unpolled results are discarded.  No other
+ * serving call on the context may run concurrently with this one. */
+qfca_status qfca_serve_stop(qfca_ctx *ctx);
+
 /* ---------------------------------------------------------------- tracing */
 
 /* Number of kernels the library has launched through `ctx` since creation

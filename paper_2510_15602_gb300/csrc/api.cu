@@ -123,7 +123,21 @@ struct qfca_ctx {
     int autotune = 0;                                   // window-stage tiling: 0 model, 1 measured
     std::map<std::string, qfca::ScoreTiling> tuned;     // measured tilings per shape set
     qfca::ScoreTiling last_tiling{0, 0, 0};
+    qfca::ServeState *serve = nullptr;                  // serving session (serve.cu)
 };
+
+namespace qfca {
+ServeState *&ctx_serve(qfca_ctx *ctx) { return ctx->serve; }
+int ctx_device(qfca_ctx *ctx) { return ctx->device; }
+int *ctx_status_dev(qfca_ctx *ctx) { return ctx->status_dev; }
+std::mutex &ctx_mutex(qfca_ctx *ctx) { return ctx->mu; }
+qfca_status ctx_set_error(qfca_ctx *ctx, qfca_status s, const std::string &msg) {
+    ctx->err = msg;
+    if (s == QFCA_ERR_CUDA) ctx->sticky = true;
+    return s;
+}
+bool ctx_sticky(qfca_ctx *ctx) { return ctx->sticky; }
+}  // namespace qfca
 
 namespace {
 
@@ -341,6 +355,7 @@ qfca_status qfca_create(int device, size_t workspace_bytes, qfca_ctx **out) {
 
 qfca_status qfca_destroy(qfca_ctx *ctx) {
     if (!ctx) return QFCA_ERR_INVALID_ARG;
+    if (ctx->serve) qfca_serve_stop(ctx);
     {
         DeviceGuard g(ctx->device);
         if (ctx->ws || ctx->status_dev) cudaDeviceSynchronize();

@@ -7,6 +7,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
 
 #include "../../include/qfca.h"
@@ -148,6 +149,16 @@ bool score_shape_ok(int B, int r);
 // cudaErrorNotSupported: nothing was enqueued.
 cudaError_t launch_score_jobs(const ScoreJob *jobs, int n, int d, int B, void *ws, bool ws_accumulates, int *status,
                               cudaStream_t st, const ScoreTiling *tiling, ScoreTiling *chosen);
+
+// ------------------------------------------------------------------ context access (api.cu) for serve.cu
+
+struct ServeState;
+ServeState *&ctx_serve(qfca_ctx *ctx);
+int ctx_device(qfca_ctx *ctx);
+int *ctx_status_dev(qfca_ctx *ctx);
+std::mutex &ctx_mutex(qfca_ctx *ctx);
+qfca_status ctx_set_error(qfca_ctx *ctx, qfca_status s, const std::string &msg);
+bool ctx_sticky(qfca_ctx *ctx);
 
 // ------------------------------------------------------------------ TMA (tmap.cu)
 

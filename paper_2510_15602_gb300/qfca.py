@@ -100,6 +100,35 @@ _lib.qfca_last_tiling.argtypes = [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ct
 _lib.qfca_last_tiling.restype = _I
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_int), ("d", ctypes.c_int), ("B", ctypes.c_int), ("precision", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("streams", ctypes.c_int), ("max_queue", ctypes.c_int),
+                ("arena_bytes", ctypes.c_size_t)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("class_id", ctypes.c_int), ("X", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("r", ctypes.c_int), ("score", ctypes.c_void_p), ("flags", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("batch_size", ctypes.c_int), ("t_submit_us", ctypes.c_double),
+                ("t_start_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+
+
+REQ_HOST_INPUT, REQ_HOST_OUTPUT = 1, 2
+_lib.qfca_serve_start.argtypes = [_P, ctypes.POINTER(ServeConfig)]
+_lib.qfca_serve_start.restype = _I
+_lib.qfca_register_class.argtypes = [_P, _I, _P, _P, _P, _P, _P, ctypes.c_uint32]
+_lib.qfca_register_class.restype = _I
+_lib.qfca_submit.argtypes = [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+_lib.qfca_submit.restype = _I
+_lib.qfca_poll.argtypes = [_P, ctypes.c_uint64, _I, ctypes.POINTER(Result)]
+_lib.qfca_poll.restype = _I
+_lib.qfca_serve_stop.argtypes = [_P]
+_lib.qfca_serve_stop.restype = _I
+
+
 class QfcaError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{_lib.qfca_status_string(status).decode()}: {msg}")
@@ -368,6 +397,65 @@ def score_batch(Xs, rs, d: int, B: int, precision="bf16", layout: int = NCHW, ct
     ctx.check(_lib.qfca_score_batch(ctx.handle, arr, len(Xs), C, layout, d, B, _PREC[precision],
                                     _P(_stream_ptr(stream))))
     return scores
+
+
+class Server:
+    """A serving session on a context (qfca_serve_start ... qfca_serve_stop).
+
+    Classes carry resident bases, fixed ranges and reference histograms;
+    requests are single NCHW feature maps [C, H, W] scored against their
+    class.  submit() queues a request and returns its ticket (None when the
+    queue is full); poll() returns a Result once it has finished.
+    """
+
+    def __init__(self, C: int, d: int, B: int, precision="bf16", max_batch: int = 16, streams: int = 2,
+                 max_queue: int = 4096, arena_bytes: int = 4 << 30, ctx: Context | None = None):
+        self.ctx = ctx or Context()
+        self.C, self.d, self.B = C, d, B
+        cfg = ServeConfig(C, d, B, _PREC[precision], max_batch, streams, max_queue, arena_bytes)
+        self.ctx.check(_lib.qfca_serve_start(self.ctx.handle, ctypes.byref(cfg)))
+        self._keep = {}  # ticket -> tensors the GPU reads or writes until the request is polled
+
+    def register_class(self, class_id: int, mean, V, lo, hi, ref_hist, ref_total: int):
+        _check_dev(mean, "mean", torch.float64)
+        _check_dev(V, "V", torch.float64)
+        self.ctx.check(_lib.qfca_register_class(self.ctx.handle, int(class_id), _ptr(mean), _ptr(V), _ptr(lo),
+                                                _ptr(hi), _ptr(ref_hist), int(ref_total)))
+
+    def submit(self, class_id: int, X: torch.Tensor, r: int, score: torch.Tensor | None = None):
+        C, H, W = (int(v) for v in X.shape)
+        if C != self.C:
+            raise ValueError(f"X has {C} channels, the session {self.C}")
+        host_in = not X.is_cuda
+        if score is None:
+            score = torch.empty(H, W, dtype=torch.float32, device="cpu" if host_in else X.device,
+                                pin_memory=host_in)
+        flags = (REQ_HOST_INPUT if host_in else 0) | (REQ_HOST_OUTPUT if not score.is_cuda else 0)
+        req = Request(int(class_id), X.data_ptr(), H, W, int(r), score.data_ptr(), flags)
+        t = ctypes.c_uint64()
+        s = _lib.qfca_submit(self.ctx.handle, ctypes.byref(req), ctypes.byref(t))
+        if s == ERR_BUSY:
+            return None
+        if s != OK:
+            raise QfcaError(s, "qfca_submit")
+        self._keep[int(t.value)] = (X, score)
+        return int(t.value)
+
+    def poll(self, ticket: int, timeout_us: int = 0):
+        """(Result, score tensor) when the request is done, else None."""
+        res = Result()
+        s = _lib.qfca_poll(self.ctx.handle, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(res))
+        if s == PENDING:
+            return None
+        if s != OK:
+            raise QfcaError(s, "qfca_poll")
+        _, score = self._keep.pop(ticket)
+        return res, score
+
+    def stop(self):
+        if self.ctx is not None and getattr(self.ctx, "handle", None):
+            self.ctx.check(_lib.qfca_serve_stop(self.ctx.handle))
+        self._keep.clear()
 
 
 def run_image(X: torch.Tensor, d: int, B: int, r: int, precision="f32", layout: int = NCHW,
