@@ -36,6 +36,11 @@ if ROOT not in sys.path:
 METRIC = "score maps/s @256²×C256 vs plain FP32; p50/p99 latency; AUROC within 0.005"
 WORKLOAD = "batch16_256_c256"
 N_IMG, C, HW, D, B, R = 16, 256, 256, 32, 32, 7
+# uneven batch: 64 images 96..320 (multiples of 8) x C512, d=32, B=64, radii {5,7,9,12}
+UNEVEN, UNEVEN_N, UNEVEN_C, UNEVEN_B = "uneven64_c512", 64, 512, 64
+# serving: sizes {128,224,320,448} x C256, d=32, B=32, r=7, 32 classes, Poisson arrivals
+SERVE, SERVE_SIZES, SERVE_CLASSES, SERVE_TRAIN_SIDE = "serve_c256", (128, 224, 320, 448), 32, 128
+SERVE_RATES = (50, 200, 500, 1000, 2000)
 
 # ------------------------------------------------------------------ distributed helpers (CPU-testable)
 
@@ -77,15 +82,41 @@ def _gen(idx):
     return img.X, img.mask
 
 
-def make_inputs(indices):
-    """Seeded synthetic images, drawn in a spawn pool (before any CUDA call)."""
+def _gen_uneven(idx):
+    from paper_2510_15602_gb300 import synth
+    img = synth.make_image(UNEVEN, idx)
+    return img.X, img.mask, img.r
+
+
+def _gen_serve_field(job):
+    # a unit-covariance field of one serving size; the class's channel mixing is applied on the device
+    from paper_2510_15602_gb300 import synth
+    side, j = job
+    img = synth.make_image(SERVE, 100 * side + j, side=side)
+    return img.X
+
+
+def _gen_serve_class(k):
+    # the training image of class k (its own channel covariance) and the class's mixing matrix
+    from paper_2510_15602_gb300 import synth
+    Q = synth.class_mixing(k, C)
+    img = synth.make_image(SERVE, 50000 + k, side=SERVE_TRAIN_SIDE, class_id=k, class_mix=Q)
+    return img.X, Q
+
+
+def _pool_map(fn, items):
     import multiprocessing as mp
-    n = len(indices)
+    n = len(items)
     workers = max(1, min(n, (os.cpu_count() or 2) - 1, 8))
     if workers == 1:
-        return [_gen(i) for i in indices]
+        return [fn(i) for i in items]
     with mp.get_context("spawn").Pool(workers) as pool:
-        return pool.map(_gen, indices)
+        return pool.map(fn, items)
+
+
+def make_inputs(indices):
+    """Seeded synthetic images, drawn in a spawn pool (before any CUDA call)."""
+    return _pool_map(_gen, list(indices))
 
 
 # ------------------------------------------------------------------ clocks
@@ -338,10 +369,148 @@ class BatchPipe:
                 post(k, self.scores[k])
 
 
+def run_uneven(qfca, torch, host, args):
+    """Uneven batch: one table-driven launch per stage over 64 images of their
+    own size and radius, autotuned window tiling, replayed as one CUDA graph."""
+    import numpy as np
+    from paper_2510_15602_gb300.metrics import auroc
+    Xs = [torch.from_numpy(x).cuda() for x, _, _ in host]
+    rs = [r for _, _, r in host]
+    ctx = qfca.Context()
+    ctx.set_autotune(True)
+    st = torch.cuda.Stream()
+    scores = [torch.empty(x.shape[1], x.shape[2], dtype=torch.float32, device="cuda") for x in Xs]
+
+    def run():
+        qfca.score_batch(Xs, rs, D, UNEVEN_B, "bf16", ctx=ctx, stream=st, scores=scores)
+
+    with torch.cuda.stream(st):
+        run()  # tunes the window tiling (outside capture)
+        run()
+    torch.cuda.synchronize()
+    ctx.trace_start("")
+    with torch.cuda.stream(st):
+        run()
+    torch.cuda.synchronize()
+    kern = {k: round(v[0], 3) for k, v in sorted(ctx.trace().items(), key=lambda kv: -kv[1][0])}
+    ctx.trace_stop()
+    n0 = ctx.launch_count()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        run()
+    launches = ctx.launch_count() - n0
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    reps = max(3, args.steps // 2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        with torch.cuda.stream(st):
+            g.replay()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    aur = [auroc(s.cpu().numpy(), m) for s, (_, m, _) in zip(scores, host)]
+    px = sum(int(x.shape[1]) * int(x.shape[2]) for x in Xs)
+    return {"workload": UNEVEN, "images": len(Xs), "C": UNEVEN_C, "d": D, "B": UNEVEN_B,
+            "radii": sorted(set(rs)), "pixels": px, "projection": "bf16",
+            "path": "qfca_score_batch: one launch per stage over the image table, one CUDA graph",
+            "value": round(len(Xs) * 1e3 / ms, 3), "unit": "maps/s", "ms_per_batch": round(ms, 3),
+            "launches_per_batch": launches, "tiling": list(ctx.last_tiling()),
+            "auroc_mean": round(float(np.nanmean(aur)), 5), "kernel_ms_per_batch": kern}
+
+
+def run_serving(qfca, torch, fields, classes, args):
+    """Serving: 32 resident classes, Poisson arrivals of single images of mixed
+    sizes at several rates, continuous batching; p50/p99 of submit-to-done."""
+    import numpy as np
+    srv = qfca.Server(C, D, B, "bf16", max_batch=16, streams=3, max_queue=1 << 15, arena_bytes=8 << 30)
+    try:
+        # classes: fit on the training image, image-wide ranges, global histogram as reference
+        Qs = []
+        for k, (Xt, Q) in enumerate(classes):
+            Xd = torch.from_numpy(Xt).cuda()
+            mean, V, _ = qfca.fit_pca(Xd, D, ctx=srv.ctx)
+            out = qfca.quantize(Xd, (mean, V), B, "bf16", ctx=srv.ctx)
+            srv.register_class(k, mean, V, out["lo"], out["hi"], out["hist"], Xt.shape[1] * Xt.shape[2])
+            Qs.append(torch.from_numpy(Q).cuda())
+        # request pool: (class, size) combinations, the class mixing applied on the device
+        rng = np.random.default_rng(77)
+        pool = []
+        for i in range(48):
+            side, fx = fields[i % len(fields)]
+            k = int(rng.integers(0, len(classes)))
+            X = (Qs[k] @ torch.from_numpy(fx).cuda().reshape(C, -1)).reshape(C, side, side).contiguous()
+            pool.append((k, X, side))
+        torch.cuda.synchronize()
+        # warm-up: every size once
+        for k, X, side in pool[:8]:
+            t = srv.submit(k, X, R)
+            while srv.poll(t, 100000) is None:
+                pass
+        points = []
+        for rate in SERVE_RATES:
+            n = int(min(600, max(100, rate * 1.5)))
+            gaps = rng.exponential(1.0 / rate, size=n)
+            arrive = np.cumsum(gaps)
+            tickets = [None] * n
+            done = [None] * n
+            stop = threading.Event()
+
+            def poller():
+                i = 0
+                while i < n:
+                    t = tickets[i]
+                    if t is None:
+                        time.sleep(0.0001)
+                        continue
+                    res = srv.poll(t, 2000)
+                    if res is not None:
+                        done[i] = res[0]
+                        i += 1
+                    elif stop.is_set():
+                        break
+
+            th = threading.Thread(target=poller, daemon=True)
+            th.start()
+            t0 = time.perf_counter()
+            for i in range(n):
+                while time.perf_counter() - t0 < arrive[i]:
+                    pass
+                k, X, side = pool[i % len(pool)]
+                t = srv.submit(k, X, R)
+                while t is None:  # queue full: retry (the wait counts in the latency via t_submit)
+                    t = srv.submit(k, X, R)
+                tickets[i] = t
+            th.join(timeout=120)
+            stop.set()
+            res = [r for r in done if r is not None]
+            lat = sorted((r.t_done_us - r.t_submit_us) / 1e3 for r in res)
+            span_s = (max(r.t_done_us for r in res) - min(r.t_submit_us for r in res)) / 1e6
+            points.append({"rate": rate, "requests": n, "completed": len(res),
+                           "p50_ms": round(lat[len(lat) // 2], 3),
+                           "p99_ms": round(lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)], 3),
+                           "maps_per_s": round(len(res) / span_s, 1),
+                           "mean_batch": round(float(np.mean([r.batch_size for r in res])), 2)})
+        return {"workload": SERVE, "classes": len(classes), "sizes": list(SERVE_SIZES), "C": C, "d": D, "B": B,
+                "r": R, "projection": "bf16", "max_batch": 16, "streams": 3,
+                "latency": "submit to GPU completion (library stamps)", "points": points}
+    finally:
+        srv.stop()
+
+
 def run_ours(args):
     ws, rank, local = dist_env()
     indices = shard_indices(rank, ws, N_IMG)
     host = make_inputs(indices)  # before the first CUDA call (spawn pool)
+    extra = rank == 0 and ws == 1
+    host_uneven = _pool_map(_gen_uneven, list(range(UNEVEN_N))) if extra and not args.skip_uneven else None
+    serve_fields = serve_classes = None
+    if extra and not args.skip_serving:
+        jobs = [(side, j) for side in SERVE_SIZES for j in range(3)]
+        serve_fields = list(zip([sd for sd, _ in jobs], _pool_map(_gen_serve_field, jobs)))
+        serve_classes = _pool_map(_gen_serve_class, list(range(SERVE_CLASSES)))
     import numpy as np
     import torch
     if ws > 1:
@@ -488,6 +657,9 @@ def run_ours(args):
                "sample": "image 0 of the batch: fit + project + quantize + window EMD, FP64, single thread"}
         auroc_oracle = auroc(ref["score"], masks[0])
 
+    uneven = run_uneven(qfca, torch, host_uneven, args) if host_uneven is not None else None
+    serving = run_serving(qfca, torch, serve_fields, serve_classes, args) if serve_fields is not None else None
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "maps/s", "n_gpus": ws, "steps": args.steps,
@@ -512,6 +684,8 @@ def run_ours(args):
                       "oracle_image0": None if auroc_oracle is None else round(auroc_oracle, 5),
                       "delta_image0": None if auroc_oracle is None else round(abs(aurocs[0] - auroc_oracle), 6)},
             "kernel_ms_per_step": {k: round(v[0], 3) for k, v in sorted(agg.items(), key=lambda kv: -kv[1][0])},
+            "uneven_batch": uneven,
+            "serving": serving,
             "wall_s_timed": round(wall_s, 3),
         }
         print(json.dumps(line), flush=True)
@@ -531,6 +705,8 @@ def main(argv=None):
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp32", action="store_true")
+    ap.add_argument("--skip-uneven", action="store_true", help="skip the 64-image uneven batch measurement")
+    ap.add_argument("--skip-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args(argv)
