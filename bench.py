@@ -312,19 +312,21 @@ def timed(torch, main, fn, steps, fork=None, join=None):
 
 
 class BatchPipe:
-    """Two contexts on two streams; step i runs the whole path over the batch on
-    pipe i % 2 (a captured CUDA graph of one qfca_batch_run), so consecutive
-    steps overlap on the device: each pipe waits only for its own previous step.
+    """`pipes` contexts on as many streams; step i runs the whole path over the
+    batch on pipe i % pipes (a captured CUDA graph of one qfca_batch_run), so
+    consecutive steps overlap on the device: each pipe waits only for its own
+    previous step.
     `fork()` makes both pipes wait for `main`; `join()` makes `main` wait for both."""
 
-    def __init__(self, q, torch, X, precision):
+    def __init__(self, q, torch, X, precision, pipes=2):
         self.q, self.torch = q, torch
-        self.X = [X, X.clone()]  # one input buffer per pipe (the end-to-end run refills them)
+        self.n = pipes
+        self.X = [X] + [X.clone() for _ in range(pipes - 1)]  # one input buffer per pipe (the e2e run refills them)
         self.precision = precision
         nimg, C, H, W = X.shape
-        self.ctx = [q.Context(), q.Context()]
-        self.st = [torch.cuda.Stream(), torch.cuda.Stream()]
-        self.scores = [torch.empty(nimg, H, W, dtype=torch.float32, device=X.device) for _ in range(2)]
+        self.ctx = [q.Context() for _ in range(pipes)]
+        self.st = [torch.cuda.Stream() for _ in range(pipes)]
+        self.scores = [torch.empty(nimg, H, W, dtype=torch.float32, device=X.device) for _ in range(pipes)]
         self.graphs = None
 
     def run_direct(self, k):
@@ -334,7 +336,7 @@ class BatchPipe:
     def capture(self):
         torch = self.torch
         self.graphs = []
-        for k in range(2):
+        for k in range(self.n):
             g = torch.cuda.CUDAGraph()
             torch.cuda.synchronize()
             with torch.cuda.graph(g, stream=self.st[k]):
@@ -356,7 +358,7 @@ class BatchPipe:
 
     def step(self, i, pre=None, post=None):
         torch = self.torch
-        k = i % 2
+        k = i % self.n
         st = self.st[k]
         with torch.cuda.stream(st):
             if pre is not None:
@@ -524,7 +526,7 @@ def run_ours(args):
     X_pin = torch.from_numpy(np.stack([x for x, _ in host])).pin_memory()  # [16, C, H, W]
     X_dev = X_pin.cuda()
     masks = [m for _, m in host]
-    pipe = BatchPipe(qfca, torch, X_dev, args.precision)
+    pipe = BatchPipe(qfca, torch, X_dev, args.precision, args.pipes)
 
     def run_steps(n, pre=None, post=None):
         pipe.fork(main)
@@ -533,7 +535,7 @@ def run_ours(args):
         pipe.join(main)
 
     # ---- warm-up (grows both context workspaces, sets kernel attributes)
-    run_steps(max(2, args.warmup))
+    run_steps(max(args.pipes, args.warmup))
     torch.cuda.synchronize()
 
     # ---- which kernel dominates: one traced direct step over all kernels
@@ -573,7 +575,7 @@ def run_ours(args):
     value = N_IMG * ws * args.steps / t_max
 
     # ---- end to end through the public API with host buffers (H2D of the batch, D2H of the maps)
-    score_pin = [torch.empty(N_IMG, HW, HW, dtype=torch.float32).pin_memory() for _ in range(2)]
+    score_pin = [torch.empty(N_IMG, HW, HW, dtype=torch.float32).pin_memory() for _ in range(args.pipes)]
 
     def pre(k):
         pipe.X[k].copy_(X_pin, non_blocking=True)
@@ -668,8 +670,8 @@ def run_ours(args):
             "data": "synthetic (seeded Gaussian random fields with planted anomalies)",
             "config": {"workload": WORKLOAD, "images_per_rank_step": N_IMG, "H": HW, "W": HW, "C": C, "d": D,
                        "B": B, "r": R, "projection": args.precision, "fit": "exact integer Gram + float-float eig",
-                       "path": "qfca_batch_run, CUDA graph, 2 steps in flight" if not args.no_graph
-                       else "qfca_batch_run, 2 steps in flight",
+                       "path": f"qfca_batch_run, CUDA graph, {args.pipes} steps in flight" if not args.no_graph
+                       else f"qfca_batch_run, {args.pipes} steps in flight",
                        "l2": "inputs 1 GiB per step > L2 (no flush needed)"},
             "e2e": {"value": round(e2e_value, 3), "unit": "maps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -703,6 +705,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["f32", "bf16"])
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--pipes", type=int, default=3, help="batches in flight (one context, stream and graph each)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-uneven", action="store_true", help="skip the 64-image uneven batch measurement")

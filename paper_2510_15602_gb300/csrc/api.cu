@@ -178,9 +178,16 @@ qfca_status cuda_fail(qfca_ctx *ctx, cudaError_t e, const char *where) {
     return fail(ctx, QFCA_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
-// Grow the context workspace to at least `need` bytes (blocking; frees the old one).
-qfca_status ensure_ws(qfca_ctx *ctx, size_t need) {
+// Grow the context workspace to at least `need` bytes (blocking; frees the old
+// one).  Growing is not possible while `st` is being captured into a graph:
+// the caller must run the same call once outside capture first.
+qfca_status ensure_ws(qfca_ctx *ctx, size_t need, cudaStream_t st = nullptr) {
     if (need <= ctx->ws_bytes) return QFCA_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (st && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return fail(ctx, QFCA_ERR_INVALID_ARG,
+                    "the workspace must grow to %zu bytes during stream capture: run the call once before capturing",
+                    need);
     if (ctx->ws) {
         cudaError_t e = cudaFree(ctx->ws);
         ctx->ws = nullptr;
@@ -377,7 +384,7 @@ qfca_status qfca_fit_pca(qfca_ctx *ctx, const float *X, qfca_fmap desc, int d, c
     DeviceGuard g(ctx->device);
     HookScope hs(ctx);
     const long N = (long)desc.H * desc.W;
-    if ((s = ensure_ws(ctx, fit_workspace_bytes(desc.C, N, d, 1)))) return s;
+    if ((s = ensure_ws(ctx, fit_workspace_bytes(desc.C, N, d, 1), (cudaStream_t)stream))) return s;
     cudaError_t e = launch_fit(X, desc.layout, desc.H, desc.W, desc.C, d, 1, out->mean, out->V, out->eigvals, ctx->ws,
                                ctx->status_dev, (cudaStream_t)stream);
     if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "eigensolver shape C=%d d=%d", desc.C, d);
@@ -395,7 +402,7 @@ qfca_status qfca_covariance(qfca_ctx *ctx, const float *X, qfca_fmap desc, doubl
     DeviceGuard g(ctx->device);
     HookScope hs(ctx);
     const long N = (long)desc.H * desc.W;
-    if ((s = ensure_ws(ctx, gram_workspace_bytes(desc.C, N, 1)))) return s;
+    if ((s = ensure_ws(ctx, gram_workspace_bytes(desc.C, N, 1), (cudaStream_t)stream))) return s;
     cudaError_t e = launch_gram_cov(X, desc.layout, desc.C, N, 1, mean_out, cov_out, nullptr, ctx->ws, ctx->status_dev,
                                     (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_covariance");
@@ -428,7 +435,7 @@ qfca_status qfca_quantize(qfca_ctx *ctx, const float *X, qfca_fmap desc, const q
     const size_t o_mm = 0;
     const size_t o_y = o_mm + bytes_mmkeys(d);
     const size_t o_p = o_y + (Y_out ? 0 : align_up(sizeof(float) * d * N, 256));
-    if ((s = ensure_ws(ctx, o_p + project_workspace_bytes(desc.C, N, d, 1)))) return s;
+    if ((s = ensure_ws(ctx, o_p + project_workspace_bytes(desc.C, N, d, 1), (cudaStream_t)stream))) return s;
     char *base = (char *)ctx->ws;
     uint32_t *mm = (uint32_t *)(base + o_mm);
     float *Y = Y_out ? Y_out : (float *)(base + o_y);
@@ -463,7 +470,7 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
     DeviceGuard g(ctx->device);
     HookScope hs(ctx);
     const ScoreJob job{bins, H, W, pitch, r, ref_hist, ref_total, score, numer_out};
-    if ((s = ensure_ws(ctx, score_jobs_workspace_bytes(&job, 1, d)))) return s;
+    if ((s = ensure_ws(ctx, score_jobs_workspace_bytes(&job, 1, d), (cudaStream_t)stream))) return s;
     cudaError_t e = launch_score_jobs(&job, 1, d, B, ctx->ws, false, ctx->status_dev, (cudaStream_t)stream,
                                       nullptr, nullptr);
     if (e == cudaErrorNotSupported)
@@ -512,7 +519,7 @@ qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap de
     std::vector<ScoreJob> jobs((size_t)nimg);
     for (int i = 0; i < nimg; i++) jobs[i] = ScoreJob{nullptr, desc.H, desc.W, pitch, r, nullptr, (uint32_t)N, nullptr, nullptr};
     const size_t o_sc = take(score_jobs_workspace_bytes(jobs.data(), nimg, d));
-    if ((s = ensure_ws(ctx, o))) return s;
+    if ((s = ensure_ws(ctx, o, (cudaStream_t)stream))) return s;
     char *b = (char *)ctx->ws;
     double *mean = (extra && extra->mean) ? extra->mean : (double *)(b + o_mean);
     double *V = (extra && extra->V) ? extra->V : (double *)(b + o_V);
@@ -595,7 +602,7 @@ qfca_status qfca_score_batch(qfca_ctx *ctx, const qfca_image *imgs, int n, int C
         sjobs[i] = ScoreJob{nullptr, imgs[i].H, imgs[i].W, pitch[i], imgs[i].r, nullptr,
                             (uint32_t)((long)imgs[i].H * imgs[i].W), imgs[i].score, nullptr};
     const size_t o_sc = take(score_jobs_workspace_bytes(sjobs.data(), n, d));
-    if ((s = ensure_ws(ctx, o))) return s;
+    if ((s = ensure_ws(ctx, o, (cudaStream_t)stream))) return s;
     char *b = (char *)ctx->ws;
     double *mean = (double *)(b + o_mean), *V = (double *)(b + o_V), *ev = (double *)(b + o_ev);
     uint32_t *mm = (uint32_t *)(b + o_mm);
