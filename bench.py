@@ -204,51 +204,78 @@ def measured_peaks() -> dict:
 # Nominal ALU peaks from unit counts and the maximum SM clock (152 SMs x 2070 MHz):
 #   FP32 FFMA: 128 lanes/SM -> 152*128*2*2.07e9 = 80.5 TFLOP/s
 #   INT32:     128 lanes/SM -> 152*128*2.07e9   = 40.3 Tops
-#   FP64:      the recipe's nominal GB300 figure, 1.25 TFLOP/s
+#   float-float on the FP32 pipe: one multiply-add of two (hi, lo) pairs into a
+#   compensated accumulator is 12 FP32 instructions (product, 3 FMA corrections,
+#   TwoSum, 2 adds) for 2 FP64-equivalent flops -> 40.3e12 / 6 = 6.7 TFLOP/s
 ALU_PEAKS = {"fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "int32_tops": 152 * 128 * 2.07e9 / 1e12,
-             "fp64_tflops": 1.25}
+             "ff_tflops": 152 * 128 * 2.07e9 / 6 / 1e12}
 
 
-def kernel_work(name: str, H: int, W: int, C: int, d: int, B: int, r: int) -> dict:
-    """Algorithmic work of ONE launch of kernel `name` on one image (per-unit figure x units)."""
+def kernel_work(name: str, H: int, W: int, C: int, d: int, B: int, r: int, nimg: int = 1) -> dict:
+    """Algorithmic work of ONE launch of kernel `name` covering `nimg` images (per-unit figure x units)."""
     N = H * W
-    if name.startswith("k_cov"):
-        # symmetric covariance: C(C+1)/2 entries x N pixels x 2 flop
-        return {"bound": "alu", "unit": "TFLOP/s", "work": C * (C + 1) * N, "peak_key": "fp64_tflops",
-                "per_unit": "C(C+1) flop per pixel"}
+    nt = (C + 127) // 128
     if name.startswith("k_gram"):
-        return {"bound": "hbm", "unit": "GB/s", "work": 4 * N * C, "peak_key": "hbm",
-                "per_unit": "4C bytes per pixel (X read once)"}
+        # exact Gram from 10 digit-pair BF16 products per 128x128 channel tile pair
+        return {"bound": "tensor", "unit": "TFLOP/s", "work": nimg * N * (nt * (nt + 1) // 2) * 10 * 2 * 128 * 128,
+                "peak_key": "bf16_sustained",
+                "per_unit": "10 x 2 x 128^2 BF16 flop per pixel per channel-tile pair (exact digit products)"}
     if name.startswith("k_eig"):
-        return {"bound": "alu", "unit": "TFLOP/s", "work": int(4 * C ** 3 / 3 + 2 * C * C * d),
-                "peak_key": "fp64_tflops", "per_unit": "4C^3/3 + 2C^2 d flop per image"}
+        return {"bound": "alu", "unit": "TFLOP/s", "work": nimg * int(4 * C ** 3 / 3 + 2 * C * C * d),
+                "peak_key": "ff_tflops",
+                "per_unit": "4C^3/3 + 2C^2 d FP64-equivalent flop per image, run as float-float on the FP32 pipe"}
     if name.startswith("k_project"):
-        return {"bound": "hbm", "unit": "GB/s", "work": 4 * N * C + 4 * N * d, "peak_key": "hbm",
+        return {"bound": "hbm", "unit": "GB/s", "work": nimg * (4 * N * C + 4 * N * d), "peak_key": "hbm",
                 "per_unit": "4C + 4d bytes per pixel"}
     if name.startswith("k_quantize"):
-        return {"bound": "hbm", "unit": "GB/s", "work": 5 * N * d, "peak_key": "hbm",
+        return {"bound": "hbm", "unit": "GB/s", "work": nimg * 5 * N * d, "peak_key": "hbm",
                 "per_unit": "5d bytes per pixel"}
+    if name.startswith("k_chan_absmax"):
+        return {"bound": "hbm", "unit": "GB/s", "work": nimg * 4 * N * C, "peak_key": "hbm",
+                "per_unit": "4C bytes per pixel"}
     if name.startswith("k_window_emd"):
-        ops = min(2 * B, 2 * (2 * r + 1)) + 4 * B
-        return {"bound": "alu", "unit": "Tops", "work": N * d * ops, "peak_key": "int32_tops",
-                "per_unit": f"{ops} int ops per (pixel, component)"}
-    return {"bound": "hbm", "unit": "GB/s", "work": 4 * N, "peak_key": "hbm", "per_unit": "4 bytes per pixel"}
+        ops = 2 * (2 * r + 1) + 4 * (B - 1)
+        return {"bound": "alu", "unit": "Tops", "work": nimg * N * d * ops, "peak_key": "int32_tops",
+                "per_unit": f"{ops} int ops per (pixel, component): 2(2r+1) window updates + 4(B-1) CDF-walk ops"}
+    if name.startswith("k_finalize"):
+        return {"bound": "hbm", "unit": "GB/s", "work": nimg * N * (4 * d + 4), "peak_key": "hbm",
+                "per_unit": "4d + 4 bytes per pixel"}
+    if name.startswith("k_cov_finalize"):
+        return {"bound": "hbm", "unit": "GB/s", "work": nimg * C * C * 24, "peak_key": "hbm",
+                "per_unit": "24 bytes per covariance entry"}
+    return {"bound": "hbm", "unit": "GB/s", "work": nimg * 4 * C, "peak_key": "hbm", "per_unit": "4C bytes per image"}
 
 
-def roofline_entry(name, total_ms, launches, peaks, H, W, C, d, B, r, traffic=None):
-    kw = kernel_work(name, H, W, C, d, B, r)
+# DRAM bytes (read + write) per launch over the 16-image batch, from the ncu
+# captures summarised in profiles/<kernel>_batch16_256_c256.md; an entry is
+# removed whenever its kernel changes after the capture.
+NCU_TRAFFIC = {
+    "k_eig_ff": 4840960,
+    "k_gram": 1685346000 + 17843968,
+    "k_project_tma": 1074424000 + 125305600,
+    "k_window_emd": 33648384 + 73858816,
+    "k_quantize": 134446336 + 19018240,
+}
+
+
+def roofline_entry(name, total_ms, launches, peaks, H, W, C, d, B, r, nimg=1, traffic=None):
+    kw = kernel_work(name, H, W, C, d, B, r, nimg)
+    if traffic is None and nimg == N_IMG and H == HW and C == globals()["C"]:
+        traffic = NCU_TRAFFIC.get(name)
     avg_s = total_ms / 1e3 / max(1, launches)
     if kw["peak_key"] == "hbm":
         achieved = kw["work"] / avg_s / 1e9
-        peak = peaks["hbm_gbs"]
+        peak, src = peaks["hbm_gbs"], peaks["source"] + " (copy, burst)"
+    elif kw["peak_key"] == "bf16_sustained":
+        achieved = kw["work"] / avg_s / 1e12
+        peak, src = peaks["bf16_tflops_sustained"], peaks["source"] + " (cuBLAS bf16, sustained)"
     else:
         achieved = kw["work"] / avg_s / 1e12
-        peak = ALU_PEAKS[kw["peak_key"]]
+        peak, src = ALU_PEAKS[kw["peak_key"]], "derived from unit counts and the 2070 MHz clock"
     return {"kernel": name, "bound": kw["bound"], "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": kw["unit"], "frac": round(achieved / peak, 4), "traffic": traffic,
-            "avg_launch_us": round(avg_s * 1e6, 2), "launches": launches, "work_per_launch": kw["work"],
-            "per_unit": kw["per_unit"], "peak_source": "measured" if kw["peak_key"] == "hbm" and
-            peaks["source"] == "measured" else ("measured" if kw["peak_key"] == "hbm" else "nominal")}
+            "avg_launch_us": round(avg_s * 1e6, 2), "launches": launches, "images_per_launch": nimg,
+            "work_per_launch": kw["work"], "per_unit": kw["per_unit"], "peak_source": src}
 
 
 # ------------------------------------------------------------------ reference arm (CPU oracle)
@@ -555,7 +582,7 @@ def run_ours(args):
         c.trace_start(dominant)
     if not args.no_graph:
         pipe.capture()
-        run_steps(2)
+        run_steps(args.pipes)  # replay every pipe's graph once
         torch.cuda.synchronize()
 
     # ---- timed region: fork once, K steps alternating over the two pipes, join once
@@ -642,9 +669,9 @@ def run_ours(args):
     auroc_mean = float(np.nanmean(aurocs))
 
     peaks = measured_peaks()
-    roof = roofline_entry(dominant, dom_ms, dom_n, peaks, HW, HW, C, D, B, R, traffic=args.traffic)
-    if roof["bound"] == "hbm":
-        roof["peak_source"] = peaks["source"]
+    roof = roofline_entry(dominant, dom_ms, dom_n, peaks, HW, HW, C, D, B, R, nimg=N_IMG, traffic=args.traffic)
+    kernels_roof = {k: roofline_entry(k, v[0], v[1], peaks, HW, HW, C, D, B, R, nimg=N_IMG)
+                    for k, v in agg.items() if v[0] >= 0.02}
 
     # ---- CPU baseline: the oracle on one image (rank 0, N = 1 only)
     cpu = None
@@ -677,6 +704,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roof,
+            "roofline_by_kernel": {k: {kk: v[kk] for kk in ("bound", "achieved", "peak", "unit", "frac")}
+                                   for k, v in kernels_roof.items()},
             "cpu_baseline": cpu,
             "clocks": clocks,
             "fp32_single_image": fp32,
@@ -697,6 +726,22 @@ def run_ours(args):
     return 0
 
 
+def run_profile_batch(args):
+    """A short fixed run for profilers: `args.profile_batch` calls of
+    qfca_batch_run on one context over the 16-image batch (no timing, no output)."""
+    host = make_inputs(range(N_IMG))
+    import numpy as np
+    import torch
+    from paper_2510_15602_gb300 import qfca
+    X = torch.from_numpy(np.stack([x for x, _ in host])).cuda()
+    ctx = qfca.Context()
+    scores = torch.empty(N_IMG, HW, HW, dtype=torch.float32, device="cuda")
+    for _ in range(args.profile_batch):
+        qfca.batch_run(X, D, B, R, args.precision, ctx=ctx, scores=scores)
+    torch.cuda.synchronize()
+    return 0 if ctx.device_status() == 0 else 1
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -710,6 +755,8 @@ def main(argv=None):
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-uneven", action="store_true", help="skip the 64-image uneven batch measurement")
     ap.add_argument("--skip-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="only run this many batches through qfca_batch_run (for profilers), then exit")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args(argv)
@@ -717,6 +764,8 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_batch:
+        return run_profile_batch(args)
     return run_ours(args)
 
 

@@ -90,6 +90,11 @@ struct Tracer final : qfca::LaunchHook {
             if (e != cudaSuccess) return e;
             float ms = 0.f;
             e = cudaEventElapsedTime(&ms, r.a, r.b);
+            if (e == cudaErrorInvalidResourceHandle || e == cudaErrorNotReady) {
+                // events captured into a graph that has not been replayed yet were never recorded
+                cudaGetLastError();
+                continue;
+            }
             if (e != cudaSuccess) return e;
             size_t i = 0;
             while (i < agg_name.size() && agg_name[i] != r.name) i++;
