@@ -56,7 +56,10 @@ typedef int qfca_status;
 /* Projection precisions.  All accumulate in FP32. */
 #define QFCA_F32 0       /* FP32 SIMT FFMA */
 #define QFCA_BF16 1      /* BF16 operands on tcgen05 tensor cores */
-#define QFCA_FP8_E4M3 2  /* e4m3 operands, per-channel scales (reserved) */
+#define QFCA_FP8_E4M3 2  /* e4m3 operands: (x - mean) s_c per channel, and the basis V/s_c as an
+                            e4m3 hi + lo pair scaled per component; all scales powers of two
+                            (s_c from a pass over max |x|); NCHW maps with H*W % 4 == 0 and a
+                            16-byte aligned X only (else QFCA_ERR_UNSUPPORTED); not in serving */
 
 /* Quantisation ranges. */
 #define QFCA_RANGE_IMAGE 0  /* lo/hi = each component's min/max over the image */
@@ -130,7 +133,7 @@ qfca_status qfca_covariance(qfca_ctx *ctx, const float *X, qfca_fmap desc, doubl
 /* qfca_quantize -- projection Y = (X - mean) V (Sec. 3.3) followed by uniform
  * quantisation of each component into B equally spaced bins (Sec. 3.1) and
  * the reference histogram.
- *   precision   QFCA_F32 or QFCA_BF16 (FP32 accumulation in both).
+ *   precision   QFCA_F32, QFCA_BF16 or QFCA_FP8_E4M3 (FP32 accumulation in all).
  *   range_mode  QFCA_RANGE_IMAGE: lo_k/hi_k = min/max of component k;
  *               QFCA_RANGE_FIXED: lo_in/hi_in (device f32[d]) are used and
  *               values are clamped into [0, B-1].

@@ -425,9 +425,8 @@ qfca_status qfca_quantize(qfca_ctx *ctx, const float *X, qfca_fmap desc, const q
     if (!basis || !basis->mean || !basis->V) return fail(ctx, QFCA_ERR_INVALID_ARG, "basis NULL");
     if (d < 1 || d > desc.C || d > kMaxD) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, min(C, %d)]", d, kMaxD);
     if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
-    if (precision != QFCA_F32 && precision != QFCA_BF16)
-        return fail(ctx, precision == QFCA_FP8_E4M3 ? QFCA_ERR_UNSUPPORTED : QFCA_ERR_INVALID_ARG,
-                    "precision %d not available", precision);
+    if (precision != QFCA_F32 && precision != QFCA_BF16 && precision != QFCA_FP8_E4M3)
+        return fail(ctx, QFCA_ERR_INVALID_ARG, "precision %d not available", precision);
     if (range_mode != QFCA_RANGE_IMAGE && range_mode != QFCA_RANGE_FIXED)
         return fail(ctx, QFCA_ERR_INVALID_ARG, "bad range_mode %d", range_mode);
     if (range_mode == QFCA_RANGE_FIXED && (!lo_in || !hi_in))
@@ -495,9 +494,8 @@ qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap de
     if (d < 1 || d > desc.C || d > kMaxD) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, min(C, %d)]", d, kMaxD);
     if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
     if (r < 1 || 2 * r + 1 > 127) return fail(ctx, QFCA_ERR_INVALID_ARG, "r = %d outside [1, 63]", r);
-    if (precision != QFCA_F32 && precision != QFCA_BF16)
-        return fail(ctx, precision == QFCA_FP8_E4M3 ? QFCA_ERR_UNSUPPORTED : QFCA_ERR_INVALID_ARG,
-                    "precision %d not available", precision);
+    if (precision != QFCA_F32 && precision != QFCA_BF16 && precision != QFCA_FP8_E4M3)
+        return fail(ctx, QFCA_ERR_INVALID_ARG, "precision %d not available", precision);
     const int pitch_min = (desc.W + 15) / 16 * 16;
     if (extra && extra->bins && (extra->pitch < desc.W || extra->pitch % 16 != 0))
         return fail(ctx, QFCA_ERR_INVALID_ARG, "extra->pitch %d must be >= W and a multiple of 16", extra->pitch);
@@ -565,9 +563,8 @@ qfca_status qfca_score_batch(qfca_ctx *ctx, const qfca_image *imgs, int n, int C
     if (C < 2 || C > kMaxC) return fail(ctx, QFCA_ERR_UNSUPPORTED, "C = %d outside [2, %d]", C, kMaxC);
     if (d < 1 || d > C || d > kMaxD) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, min(C, %d)]", d, kMaxD);
     if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
-    if (precision != QFCA_F32 && precision != QFCA_BF16)
-        return fail(ctx, precision == QFCA_FP8_E4M3 ? QFCA_ERR_UNSUPPORTED : QFCA_ERR_INVALID_ARG,
-                    "precision %d not available", precision);
+    if (precision != QFCA_F32 && precision != QFCA_BF16 && precision != QFCA_FP8_E4M3)
+        return fail(ctx, QFCA_ERR_INVALID_ARG, "precision %d not available", precision);
     for (int i = 0; i < n; i++) {
         const qfca_image &im = imgs[i];
         if (!im.X || !im.score) return fail(ctx, QFCA_ERR_INVALID_ARG, "image %d: NULL pointer", i);
@@ -634,7 +631,7 @@ qfca_status qfca_score_batch(qfca_ctx *ctx, const qfca_image *imgs, int n, int C
             pjobs[i] = ProjJob{imgs[i].X, (long)imgs[i].H * imgs[i].W, mean32 + (size_t)i * Cp,
                                (const char *)Vt + sizeof(uint16_t) * (size_t)i * DT * Cp, (float *)(b + o_Y[i]),
                                mm + (size_t)i * mm_stride};
-        if (e == cudaSuccess) e = launch_project_tma(pjobs.data(), n, C, d, ctx->status_dev, st);
+        if (e == cudaSuccess) e = launch_project_tma(pjobs.data(), n, C, d, false, ctx->status_dev, st);
     } else {
         for (int i = 0; i < n && e == cudaSuccess; i++)
             e = launch_project(imgs[i].X, layout, imgs[i].H, imgs[i].W, C, mean + (size_t)i * C, V + (size_t)i * C * d, d,

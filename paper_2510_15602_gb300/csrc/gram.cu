@@ -480,6 +480,26 @@ cudaError_t launch_gram_cov_jobs(const FitJob *jobs, int n, int layout, int C, d
     return cudaSuccess;
 }
 
+cudaError_t launch_chan_absmax_jobs(const FitJob *jobs, int n, int layout, int C, unsigned *amax, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned) * (size_t)C * n, st);
+    for (int i0 = 0; i0 < n && e == cudaSuccess; i0 += kMaxBatch) {
+        const int m = n - i0 < kMaxBatch ? n - i0 : kMaxBatch;
+        FitParams p;
+        memset(&p, 0, sizeof(p));
+        p.n = m, p.C = C, p.layout = layout;
+        long max_n = 1;
+        for (int i = 0; i < m; i++) {
+            p.img[i].X = jobs[i0 + i].X, p.img[i].N = jobs[i0 + i].N;
+            max_n = jobs[i0 + i].N > max_n ? jobs[i0 + i].N : max_n;
+        }
+        const int xb = (int)((max_n + 256 * 64 - 1) / (256 * 64));
+        QFCA_LAUNCH("k_chan_absmax", st,
+                    k_chan_absmax<<<dim3(xb < 1 ? 1 : xb, C, m), 256, 0, st>>>(p, amax + (size_t)i0 * C));
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
 cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, int nimg, double *mean, double *cov,
                             void *cov_ff, void *ws, int *status, cudaStream_t st) {
     // chunks of kMaxBatch images reuse the workspace in stream order

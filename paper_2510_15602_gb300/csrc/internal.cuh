@@ -34,6 +34,8 @@ struct FitJob {
 };
 cudaError_t launch_gram_cov_jobs(const FitJob *jobs, int n, int layout, int C, double *mean, double *cov, void *cov_ff,
                                  void *ws, int *status, cudaStream_t st);
+// max |x| per channel (float bits) of each image: amax [n][C]
+cudaError_t launch_chan_absmax_jobs(const FitJob *jobs, int n, int layout, int C, unsigned *amax, cudaStream_t st);
 cudaError_t launch_fit_jobs(const FitJob *jobs, int n, int layout, int C, int d, double *mean, double *V,
                             double *eigvals, void *ws, int *status, cudaStream_t st);
 
@@ -67,10 +69,11 @@ cudaError_t launch_project(const float *X, int layout, int H, int W, int C, cons
                            const double *V, int d, int nimg, int precision, float *Y, uint32_t *mm_keys,
                            void *ws, int *status, cudaStream_t st);
 
-// Per-component min/max keys live 128 B apart (one L2 line each):
-// One image of the TMA-fed BF16 projection: X NCHW [C][N] (16-B aligned,
-// N % 4 == 0), prepared operands mean32 [Cp] and Vt [DT][Cp] (BF16), Y [d][N],
-// min/max keys mm [2 d kKeyStride] (initialised by the caller).
+// One image of the TMA-fed projection: X NCHW [C][N] (16-B aligned, N % 4 ==
+// 0), prepared operands mean32 [Cp] and Vt (BF16 [DT][Cp]; FP8: the e4m3 hi
+// then lo parts [2][DT][Cp], Cp = C rounded to 128, with the per-channel
+// scale s_c [Cp] and the per-component 1/t_j [DT], all powers of two), Y
+// [d][N], min/max keys mm [2 d kKeyStride] (initialised by the caller).
 struct ProjJob {
     const float *X;
     long N;
@@ -78,15 +81,21 @@ struct ProjJob {
     const void *Vt;
     float *Y;
     uint32_t *mm;
+    const float *scale = nullptr;
+    const float *colscale = nullptr;
 };
 bool project_tma_ok(const float *X, long N, int layout);
 size_t project_bf16_workspace_bytes(int C, long N, int d, int nimg);
+size_t project_fp8_workspace_bytes(int C, int d, int nimg);
+cudaError_t launch_project_fp8(const float *X, int layout, long N, int C, const double *mean, const double *V, int d,
+                               int nimg, float *Y, uint32_t *mm_keys, void *ws, int *status, cudaStream_t st);
 cudaError_t launch_prep_bf16(const double *mean, const double *V, int C, int d, int n, void *ws, float **mean32_out,
                              void **Vt_out, int *Cp_out, int *DT_out, cudaStream_t st);
 // min/max keys of nimg images (contiguous [nimg][2 d kKeyStride]) to their start values
 cudaError_t launch_init_keys(uint32_t *mm_keys, int d, int nimg, cudaStream_t st);
-cudaError_t launch_project_tma(const ProjJob *jobs, int n, int C, int d, int *status, cudaStream_t st);
+cudaError_t launch_project_tma(const ProjJob *jobs, int n, int C, int d, bool fp8, int *status, cudaStream_t st);
 
+// Per-component min/max keys live 128 B apart (one L2 line each):
 // min of component j at mm_keys[j * kKeyStride], max at mm_keys[(d + j) * kKeyStride].
 constexpr int kKeyStride = 32;
 

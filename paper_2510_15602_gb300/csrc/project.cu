@@ -9,6 +9,8 @@
 // it coalesced.  min/max per component: warp reductions, then one atomicMin /
 // atomicMax per warp on order-preserving u32 keys.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "internal.cuh"
@@ -150,7 +152,8 @@ cudaError_t launch_init_keys(uint32_t *mm_keys, int d, int nimg, cudaStream_t st
 size_t project_workspace_bytes(int C, long N, int d, int nimg) {
     const size_t f32 = align_up(sizeof(float) * (align_up(C, 64) + (size_t)C * 64) * nimg, 256);
     const size_t bf = project_bf16_workspace_bytes(C, N, d, nimg);
-    return f32 > bf ? f32 : bf;
+    const size_t f8 = project_fp8_workspace_bytes(C, d, nimg);
+    return std::max(f32, std::max(bf, f8));
 }
 
 cudaError_t launch_project(const float *X, int layout, int H, int W, int C, const double *mean,
@@ -162,6 +165,8 @@ cudaError_t launch_project(const float *X, int layout, int H, int W, int C, cons
                 k_init_keys<<<(unsigned)((nkeys + 255) / 256), 256, 0, st>>>(mm_keys, d, nimg));
     if (precision == QFCA_BF16)
         return launch_project_bf16(X, layout, H, W, C, mean, V, d, nimg, Y, mm_keys, ws, status, st);
+    if (precision == QFCA_FP8_E4M3)
+        return launch_project_fp8(X, layout, N, C, mean, V, d, nimg, Y, mm_keys, ws, status, st);
     const int DT = pick_dt(d);
     const int Cs = (int)align_up(C, 64);
     float *mean32 = (float *)ws;

@@ -19,8 +19,11 @@
 // A wait that runs out sets bit 0 of the device status word, waits once more
 // (bounded) for the CTA's MMAs, frees the tensor memory and returns.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <vector>
 
 #include "internal.cuh"
 #include "tc.cuh"
@@ -62,6 +65,56 @@ __global__ void k_prep_bf16(const double *__restrict__ mean, const double *__res
         const float v = (j < d && c < C) ? (float)V[(long)c * d + j] : 0.0f;
         Vt[e] = __float2bfloat16_rn(v);
         if (j == 0) mean32[c] = c < C ? (float)mean[c] : 0.0f;
+    }
+}
+
+// FP8 (e4m3) operands of one basis per CTA (grid.x = image):
+//   s_c = 2^floor(log2(448 / (max_p |x_cp| + |mean_c|)))   (|(x - mean) s_c| <= 448, no saturation)
+//   B'_jc = V_cj / s_c * t_j,  t_j = 2^floor(log2(448 / max_c |V_cj / s_c|))
+//   hi = e4m3(B'), lo = e4m3(B' - hi)   (round to nearest even)
+// so (x - mean) V = sum_c [(x - mean) s_c] (hi + lo)_jc / t_j up to the e4m3
+// roundings.  amax holds max |x| per channel as float bits.
+__global__ void __launch_bounds__(256) k_prep_fp8(const double *__restrict__ mean, const double *__restrict__ V,
+                                                  const unsigned *__restrict__ amax, int C, int d, int Cp, int DT,
+                                                  float *__restrict__ mean32, float *__restrict__ scale,
+                                                  float *__restrict__ colscale, uint8_t *__restrict__ Vt8) {
+    const long img = blockIdx.x;
+    mean += img * C;
+    V += img * C * d;
+    amax += img * C;
+    mean32 += img * Cp;
+    scale += img * Cp;
+    colscale += img * DT;
+    Vt8 += img * 2 * DT * Cp;
+    __shared__ float s_sc[512];
+    __shared__ float s_t[64];
+    for (int c = threadIdx.x; c < Cp; c += blockDim.x) {
+        float sc = 1.0f;
+        if (c < C) {
+            const double bound = (double)__uint_as_float(amax[c]) + fabs(mean[c]);
+            if (bound > 0.0) sc = (float)exp2(floor(log2(448.0 / bound)));
+        }
+        s_sc[c] = sc;
+        scale[c] = sc;
+        mean32[c] = c < C ? (float)mean[c] : 0.0f;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < DT; j += blockDim.x) {
+        double m = 0.0;
+        if (j < d)
+            for (int c = 0; c < C; c++) m = fmax(m, fabs(V[(long)c * d + j]) / (double)s_sc[c]);
+        const float t = m > 0.0 ? (float)exp2(floor(log2(448.0 / m))) : 1.0f;
+        s_t[j] = t;
+        colscale[j] = 1.0f / t;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < DT * Cp; e += blockDim.x) {
+        const int j = e / Cp, c = e % Cp;
+        const float b = (j < d && c < C) ? (float)(V[(long)c * d + j] / (double)s_sc[c] * (double)s_t[j]) : 0.0f;
+        const __nv_fp8_e4m3 hi(b);
+        const __nv_fp8_e4m3 lo(b - (float)hi);
+        Vt8[e] = hi.__x;
+        Vt8[(long)DT * Cp + e] = lo.__x;
     }
 }
 
@@ -266,6 +319,43 @@ cudaError_t launch_dt(const float *X, int layout, int C, const TcShape &sh, long
 
 }  // namespace
 
+size_t project_fp8_workspace_bytes(int C, int d, int nimg) {
+    const int Cp = (C + 127) / 128 * 128, DT = d <= 16 ? 16 : (d <= 32 ? 32 : 64);
+    return (align_up(sizeof(float) * 2 * Cp, 256) + align_up(sizeof(float) * DT, 256) +
+            align_up((size_t)2 * DT * Cp, 256) + align_up(sizeof(unsigned) * C, 256)) * nimg + 256;
+}
+
+// FP8 projection of nimg same-shaped NCHW images (TMA path only).
+cudaError_t launch_project_fp8(const float *X, int layout, long N, int C, const double *mean, const double *V, int d,
+                               int nimg, float *Y, uint32_t *mm_keys, void *ws, int *status, cudaStream_t st) {
+    if (!project_tma_ok(X, N, layout) || C > 512) return cudaErrorNotSupported;
+    const int Cp = (C + 127) / 128 * 128, DT = d <= 16 ? 16 : (d <= 32 ? 32 : 64);
+    char *b = (char *)ws;
+    float *mean32 = (float *)b;
+    b += align_up(sizeof(float) * Cp * nimg, 256);
+    float *scale = (float *)b;
+    b += align_up(sizeof(float) * Cp * nimg, 256);
+    float *colscale = (float *)b;
+    b += align_up(sizeof(float) * DT * nimg, 256);
+    uint8_t *Vt8 = (uint8_t *)b;
+    b += align_up((size_t)2 * DT * Cp * nimg, 256);
+    unsigned *amax = (unsigned *)b;
+    std::vector<FitJob> fj(nimg);
+    for (int i = 0; i < nimg; i++) fj[i] = FitJob{X + (long)i * C * N, N};
+    cudaError_t e = launch_chan_absmax_jobs(fj.data(), nimg, layout, C, amax, st);
+    if (e != cudaSuccess) return e;
+    QFCA_LAUNCH("k_prep_fp8", st,
+                k_prep_fp8<<<nimg, 256, 0, st>>>(mean, V, amax, C, d, Cp, DT, mean32, scale, colscale, Vt8));
+    std::vector<ProjJob> jobs(nimg);
+    for (int i = 0; i < nimg; i++) {
+        jobs[i] = ProjJob{X + (long)i * C * N, N, mean32 + (size_t)i * Cp, Vt8 + (size_t)i * 2 * DT * Cp,
+                          Y + (size_t)i * d * N, mm_keys + (size_t)i * 2 * d * kKeyStride};
+        jobs[i].scale = scale + (size_t)i * Cp;
+        jobs[i].colscale = colscale + (size_t)i * DT;
+    }
+    return launch_project_tma(jobs.data(), nimg, C, d, true, status, st);
+}
+
 size_t project_bf16_workspace_bytes(int C, long N, int d, int nimg) {
     (void)N;
     const TcShape s = tc_shape(C, d);
@@ -311,7 +401,7 @@ cudaError_t launch_project_bf16(const float *X, int layout, int H, int W, int C,
                 jobs[i] = ProjJob{X + img * C * N, N, mean32 + img * sh.Cp, Vt + img * sh.DT * sh.Cp, Y + img * d * N,
                                   mm_keys + img * 2 * d * kKeyStride};
             }
-            cudaError_t e = launch_project_tma(jobs, m, C, d, status, st);
+            cudaError_t e = launch_project_tma(jobs, m, C, d, false, status, st);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;

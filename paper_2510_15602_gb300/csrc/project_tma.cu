@@ -55,7 +55,9 @@ constexpr uint32_t kTries = 1u << 26;
 struct ProjImgP {
     long N, tile0;
     const float *mean32;            // [Cp]
-    const __nv_bfloat16 *Vt;        // [DT][Cp]
+    const void *Vt;                 // BF16 [DT][Cp]; FP8: e4m3 hi [DT][Cp] then lo [DT][Cp]
+    const float *scale;             // FP8: per-channel power-of-two scale s_c [Cp]
+    const float *colscale;          // FP8: per-component power-of-two 1/t_j [DT]
     float *Y;                       // [d][N]
     uint32_t *mm;                   // [2 d kKeyStride]
 };
@@ -126,7 +128,7 @@ struct SmemLayout {
     size_t stage, a, b, mean, bar, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int stages, int na, int Cp, int DT) {
+__host__ __device__ inline SmemLayout smem_layout(int stages, int na, int Cp, int DT, bool f8) {
     SmemLayout L;
     size_t o = 0;
     L.stage = o;
@@ -134,25 +136,29 @@ __host__ __device__ inline SmemLayout smem_layout(int stages, int na, int Cp, in
     L.a = o;
     o += (size_t)na * kAChunk;
     L.b = o;
-    o += (size_t)(Cp / kKc) * DT * 128;
+    o += f8 ? 2 * (size_t)Cp * DT : (size_t)(Cp / kKc) * DT * 128;  // FP8: hi and lo, 128 channels per 128-B row
     L.mean = o;
-    o += sizeof(float) * (size_t)Cp;
+    o += (f8 ? 2 : 1) * sizeof(float) * (size_t)Cp;                // mean (and FP8 scale)
     L.bar = o;
     o += 8 * (2 * kMaxStages + 2 * kMaxA + 4) + 16 + 2 * 4 * 64;  // barriers, tmem slot + abort flag, kmin/kmax
     L.total = o + 1024;                                // alignment slack
     return L;
 }
 
-template <int DT>
+// F8: A = e4m3((x - mean) s_c), B = e4m3 hi + lo of V^T / s_c scaled by t_j per
+// component, kind::f8f6f4 MMAs (K = 32) over 128-channel K-chunks, each
+// assembled from two 64-channel boxes; the epilogue multiplies by 1/t_j.
+template <int DT, bool F8>
 __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_constant__ ProjParams p,
                                                             int *__restrict__ status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = tc::align_smem<1024>(smem_raw);
-    const SmemLayout L = smem_layout(p.stages, p.na, p.Cp, DT);
+    const SmemLayout L = smem_layout(p.stages, p.na, p.Cp, DT, F8);
     uint8_t *stage = smem + L.stage;
     uint8_t *As = smem + L.a;
     uint8_t *Bs = smem + L.b;
     float *mean_s = reinterpret_cast<float *>(smem + L.mean);
+    float *scale_s = mean_s + p.Cp;  // FP8 only
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bar);  // [kMaxStages] TMA landed
     uint64_t *empty = full + kMaxStages;                            // [kMaxStages] converters done with a stage
     uint64_t *a_full = empty + kMaxStages;                          // [kMaxA] operand chunk converted
@@ -177,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
             tc::mbar_init(&empty[s], kConv / 32);
         }
         for (int b = 0; b < kMaxA; b++) {
-            tc::mbar_init(&a_full[b], kConv / 32);
+            tc::mbar_init(&a_full[b], (F8 ? 2 : 1) * kConv / 32);  // FP8: two boxes per operand chunk
             tc::mbar_init(&a_empty[b], 1);
         }
         for (int b = 0; b < 2; b++) {
@@ -201,7 +207,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
     // Every role keeps its whole warp converged (one lane issues), and after an
     // abort the converters still pass every named barrier, so no thread can be
     // left waiting at a barrier or a .sync.aligned instruction.
-    constexpr unsigned kFull = 0xffffffffu;
     if (warp == 0) {
         // ---------------------------------------------------------------- TMA producer
         long q = 0;
@@ -225,26 +230,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------------- MMA issuer
-        const uint32_t idesc = tc::idesc_bf16_f32(kM, DT);
+        const uint32_t idesc = F8 ? tc::idesc_e4m3_f32(kM, DT) : tc::idesc_bf16_f32(kM, DT);
         const uint32_t a_base = tc::smem_u32(As), b_base = tc::smem_u32(Bs);
+        const int nq = F8 ? nk / 2 : nk;  // operand chunks per tile
         long q = 0, last_commit = -1;
         bool ok = true;
         for (long tile = 0; ok && tile < w1 - w0; tile++) {
             const int ac = (int)(tile & 1);
             if (tile >= 2) ok = warp_wait(&acc_empty[ac], (uint32_t)((tile / 2 - 1) & 1), abort_flag);
-            for (int kc = 0; ok && kc < nk; kc++, q++) {
+            for (int kc = 0; ok && kc < nq; kc++, q++) {
                 const int ab = (int)(q % NA);
                 ok = warp_wait(&a_full[ab], (uint32_t)((q / NA) & 1), abort_flag);
                 if (!ok) break;
                 tc::tc_fence_after();
                 if (lane == 0) {
                     const uint32_t a0 = a_base + (uint32_t)ab * kAChunk, b0 = b_base + (uint32_t)kc * DT * 128;
+                    if (F8) {
+                        const uint32_t b1 = b0 + (uint32_t)(p.Cp * DT);  // lo part
 #pragma unroll
-                    for (int ks = 0; ks < 4; ks++)
-                        tc::mma_bf16_ss(tmem + (uint32_t)(ac * DT), tc::sdesc_kmajor_sw128(a0 + ks * 32),
-                                        tc::sdesc_kmajor_sw128(b0 + ks * 32), idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+                        for (int ks = 0; ks < 4; ks++) {
+                            tc::mma_f8_ss(tmem + (uint32_t)(ac * DT), tc::sdesc_kmajor_sw128(a0 + ks * 32),
+                                          tc::sdesc_kmajor_sw128(b0 + ks * 32), idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+                            tc::mma_f8_ss(tmem + (uint32_t)(ac * DT), tc::sdesc_kmajor_sw128(a0 + ks * 32),
+                                          tc::sdesc_kmajor_sw128(b1 + ks * 32), idesc, 1u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int ks = 0; ks < 4; ks++)
+                            tc::mma_bf16_ss(tmem + (uint32_t)(ac * DT), tc::sdesc_kmajor_sw128(a0 + ks * 32),
+                                            tc::sdesc_kmajor_sw128(b0 + ks * 32), idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+                    }
                     tc::mma_commit(&a_empty[ab]);
-                    if (kc == nk - 1) tc::mma_commit(&acc_full[ac]);
+                    if (kc == nq - 1) tc::mma_commit(&acc_full[ac]);
                 }
                 __syncwarp();
                 last_commit = q;
@@ -269,17 +286,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
                 conv_sync();
                 const ProjImgP &im = p.img[img];
                 for (int c = ct; c < p.Cp; c += kConv) mean_s[c] = im.mean32[c];
-                for (int e = ct; e < DT * (p.Cp / 8); e += kConv) {
-                    const int j = e / (p.Cp / 8), c8 = e % (p.Cp / 8);
-                    const uint4 v = *reinterpret_cast<const uint4 *>(im.Vt + (long)j * p.Cp + c8 * 8);
-                    *reinterpret_cast<uint4 *>(Bs + (size_t)(c8 >> 3) * DT * 128 + swz_off(j, c8 & 7)) = v;
+                if (F8) {
+                    for (int c = ct; c < p.Cp; c += kConv) scale_s[c] = im.scale[c];
+                    // hi then lo, each DT rows x Cp bytes: 16-B chunks of 16 channels, 128 channels per row
+                    const uint8_t *src = reinterpret_cast<const uint8_t *>(im.Vt);
+                    for (int e = ct; e < 2 * DT * (p.Cp / 16); e += kConv) {
+                        const int part = e / (DT * (p.Cp / 16)), r = e % (DT * (p.Cp / 16));
+                        const int j = r / (p.Cp / 16), c16 = r % (p.Cp / 16);
+                        const uint4 v = *reinterpret_cast<const uint4 *>(src + ((size_t)part * DT + j) * p.Cp + c16 * 16);
+                        *reinterpret_cast<uint4 *>(Bs + (size_t)part * p.Cp * DT + (size_t)(c16 >> 3) * DT * 128 +
+                                                   swz_off(j, c16 & 7)) = v;
+                    }
+                } else {
+                    const __nv_bfloat16 *vt = reinterpret_cast<const __nv_bfloat16 *>(im.Vt);
+                    for (int e = ct; e < DT * (p.Cp / 8); e += kConv) {
+                        const int j = e / (p.Cp / 8), c8 = e % (p.Cp / 8);
+                        const uint4 v = *reinterpret_cast<const uint4 *>(vt + (long)j * p.Cp + c8 * 8);
+                        *reinterpret_cast<uint4 *>(Bs + (size_t)(c8 >> 3) * DT * 128 + swz_off(j, c8 & 7)) = v;
+                    }
                 }
                 tc::fence_proxy_async_smem();
                 conv_sync();
                 cur = img;
             }
             for (int kc = 0; kc < nk; kc++, q++) {
-                const int s = (int)(q % S), ab = (int)(q % NA);
+                // operand chunk of this box: one box each (BF16), two boxes each (FP8)
+                const long qa = F8 ? q >> 1 : q;
+                const int hf = F8 ? (int)(q & 1) : 0;
+                const int s = (int)(q % S), ab = (int)(qa % NA);
                 if (ok) ok = warp_wait(&full[s], (uint32_t)((q / S) & 1), abort_flag);
                 if (!ok) continue;
                 // read the 32 features first and release the stage, then wait for the operand buffer
@@ -289,20 +323,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
                 for (int i = 0; i < 32; i++) xv[i] = xs[i * kM];
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
-                if (q >= NA) ok = warp_wait(&a_empty[ab], (uint32_t)((q / NA - 1) & 1), abort_flag);
+                if (hf == 0 && qa >= NA) ok = warp_wait(&a_empty[ab], (uint32_t)((qa / NA - 1) & 1), abort_flag);
                 if (!ok) continue;
                 const float4 *mu4 = reinterpret_cast<const float4 *>(mean_s + kc * kKc + 32 * h);
                 uint8_t *arow = As + (size_t)ab * kAChunk;
+                if (F8) {
+                    // 32 channels -> 32 bytes: 16-B chunks 4 hf + 2 h and 4 hf + 2 h + 1 of the 128-B row
+                    const float4 *sc4 = reinterpret_cast<const float4 *>(scale_s + kc * kKc + 32 * h);
 #pragma unroll
-                for (int g = 0; g < 4; g++) {
-                    const float4 ma = mu4[2 * g], mb = mu4[2 * g + 1];
-                    const float *x8 = xv + 8 * g;
-                    uint4 pk;
-                    pk.x = tc::pack_bf16x2(x8[0] - ma.x, x8[1] - ma.y);
-                    pk.y = tc::pack_bf16x2(x8[2] - ma.z, x8[3] - ma.w);
-                    pk.z = tc::pack_bf16x2(x8[4] - mb.x, x8[5] - mb.y);
-                    pk.w = tc::pack_bf16x2(x8[6] - mb.z, x8[7] - mb.w);
-                    *reinterpret_cast<uint4 *>(arow + swz_off(m, 4 * h + g)) = pk;
+                    for (int g = 0; g < 2; g++) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const int i = 16 * g + 4 * u;
+                            const float4 mu = mu4[4 * g + u], sc = sc4[4 * g + u];
+                            w[u] = tc::pack_e4m3x4((xv[i] - mu.x) * sc.x, (xv[i + 1] - mu.y) * sc.y,
+                                                   (xv[i + 2] - mu.z) * sc.z, (xv[i + 3] - mu.w) * sc.w);
+                        }
+                        *reinterpret_cast<uint4 *>(arow + swz_off(m, 4 * hf + 2 * h + g)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int g = 0; g < 4; g++) {
+                        const float4 ma = mu4[2 * g], mb = mu4[2 * g + 1];
+                        const float *x8 = xv + 8 * g;
+                        uint4 pk;
+                        pk.x = tc::pack_bf16x2(x8[0] - ma.x, x8[1] - ma.y);
+                        pk.y = tc::pack_bf16x2(x8[2] - ma.z, x8[3] - ma.w);
+                        pk.z = tc::pack_bf16x2(x8[4] - mb.x, x8[5] - mb.y);
+                        pk.w = tc::pack_bf16x2(x8[6] - mb.z, x8[7] - mb.w);
+                        *reinterpret_cast<uint4 *>(arow + swz_off(m, 4 * h + g)) = pk;
+                    }
                 }
                 tc::fence_proxy_async_smem();
                 __syncwarp();
@@ -364,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
 #pragma unroll
                 for (int i = 0; i < 16; i++) {
                     const int j = 16 * g + i;
-                    const float v = __uint_as_float(r[i]);
+                    const float v = F8 ? __uint_as_float(r[i]) * __ldg(im.colscale + j) : __uint_as_float(r[i]);
                     if (j < d && valid) im.Y[(long)j * im.N + pe] = v;
                     vmn[i] = valid ? v : __int_as_float(0x7fc00000);  // NaN: ignored by the reduction
                     vmx[i] = vmn[i];
@@ -389,21 +440,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
     }
 }
 
-template <int DT>
+template <int DT, bool F8>
 cudaError_t launch_dt(const ProjParams &p, int *status, cudaStream_t st) {
     static int attr_dev = -1, n_sm = 0;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (attr_dev != dev) {
-        e = cudaFuncSetAttribute(k_project_tma<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        e = cudaFuncSetAttribute(k_project_tma<DT, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
-    const size_t smem = smem_layout(p.stages, p.na, p.Cp, DT).total;
+    const size_t smem = smem_layout(p.stages, p.na, p.Cp, DT, F8).total;
     const long grid = p.total_tiles < n_sm ? p.total_tiles : n_sm;
-    QFCA_LAUNCH("k_project_tma", st, k_project_tma<DT><<<(unsigned)grid, kThreads, smem, st>>>(p, status));
+    QFCA_LAUNCH("k_project_tma", st, (k_project_tma<DT, F8><<<(unsigned)grid, kThreads, smem, st>>>(p, status)));
     return cudaGetLastError();
 }
 
@@ -413,17 +464,17 @@ bool project_tma_ok(const float *X, long N, int layout) {
     return layout == QFCA_NCHW && N % 4 == 0 && ((uintptr_t)X & 15) == 0;
 }
 
-cudaError_t launch_project_tma(const ProjJob *jobs, int n, int C, int d, int *status, cudaStream_t st) {
+cudaError_t launch_project_tma(const ProjJob *jobs, int n, int C, int d, bool fp8, int *status, cudaStream_t st) {
     const int DT = d <= 16 ? 16 : (d <= 32 ? 32 : 64);
-    const int Cp = (C + kKc - 1) / kKc * kKc;
+    const int Cp = fp8 ? (C + 127) / 128 * 128 : (C + kKc - 1) / kKc * kKc;
     // deepest TMA ring first (bytes in flight), then the deepest operand ring
     int stages = 0, na = 0;
     for (int sg = kMaxStages; sg >= 3 && !stages; sg--)
         for (int a = kMaxA; a >= 2; a--)
-            if (smem_layout(sg, a, Cp, DT).total <= 227 * 1024) { stages = sg, na = a; break; }
+            if (smem_layout(sg, a, Cp, DT, fp8).total <= 227 * 1024) { stages = sg, na = a; break; }
     if (!stages) {
         stages = 2, na = 2;
-        if (smem_layout(stages, na, Cp, DT).total > 227 * 1024) return cudaErrorNotSupported;
+        if (smem_layout(stages, na, Cp, DT, fp8).total > 227 * 1024) return cudaErrorNotSupported;
     }
     for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
         const int m = n - i0 < kMaxBatch ? n - i0 : kMaxBatch;
@@ -434,18 +485,28 @@ cudaError_t launch_project_tma(const ProjJob *jobs, int n, int C, int d, int *st
         for (int i = 0; i < m; i++) {
             const ProjJob &j = jobs[i0 + i];
             if (!project_tma_ok(j.X, j.N, QFCA_NCHW)) return cudaErrorNotSupported;
+            if (fp8 && (!j.scale || !j.colscale)) return cudaErrorInvalidValue;
             ProjImgP &im = p.img[i];
-            im.N = j.N, im.tile0 = tiles, im.mean32 = j.mean32, im.Vt = (const __nv_bfloat16 *)j.Vt, im.Y = j.Y, im.mm = j.mm;
+            im.N = j.N, im.tile0 = tiles, im.mean32 = j.mean32, im.Vt = j.Vt, im.scale = j.scale;
+            im.colscale = j.colscale, im.Y = j.Y, im.mm = j.mm;
             tiles += (j.N + kM - 1) / kM;
             cudaError_t e = make_tmap_f32_2d(&p.tmap[i], j.X, (uint64_t)j.N, (uint64_t)C, (uint64_t)j.N * 4, kM, kKc);
             if (e != cudaSuccess) return e;
         }
         p.total_tiles = tiles;
         cudaError_t e;
-        switch (DT) {
-            case 16: e = launch_dt<16>(p, status, st); break;
-            case 32: e = launch_dt<32>(p, status, st); break;
-            default: e = launch_dt<64>(p, status, st); break;
+        if (fp8) {
+            switch (DT) {
+                case 16: e = launch_dt<16, true>(p, status, st); break;
+                case 32: e = launch_dt<32, true>(p, status, st); break;
+                default: e = launch_dt<64, true>(p, status, st); break;
+            }
+        } else {
+            switch (DT) {
+                case 16: e = launch_dt<16, false>(p, status, st); break;
+                case 32: e = launch_dt<32, false>(p, status, st); break;
+                default: e = launch_dt<64, false>(p, status, st); break;
+            }
         }
         if (e != cudaSuccess) return e;
     }

@@ -229,7 +229,7 @@ cudaError_t launch_batch(ServeState *S, Batch *b) {
             pj[i] = ProjJob{X[i], (long)b->reqs[i].req.H * b->reqs[i].req.W, cl.mean32, cl.Vt, Y[i],
                             keys + (size_t)i * 2 * c.d * kKeyStride};
         }
-        if (e == cudaSuccess) e = launch_project_tma(pj.data(), n, c.C, c.d, S->status_dev, st);
+        if (e == cudaSuccess) e = launch_project_tma(pj.data(), n, c.C, c.d, false, S->status_dev, st);
     } else {
         for (int i = 0; i < n && e == cudaSuccess; i++) {
             const qfca_request &r = b->reqs[i].req;

@@ -482,3 +482,69 @@ def test_score_batch_rejects_bad_arguments(q):
         q.score_batch([X], [3], 4, 1)           # B < 2
     with pytest.raises(ValueError):
         q.score_batch([X], [3, 4], 4, 16)       # one radius per image
+
+
+# ------------------------------------------------------------------ FP8 (e4m3) projection
+
+def _e4m3(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.float8_e4m3fn).to(torch.float32).numpy()
+
+
+def _fp8_operands(X, mean, V):
+    """The documented FP8 operands, from the same inputs: per-channel and
+    per-component power-of-two scales, e4m3 A and the e4m3 hi + lo basis."""
+    C = X.shape[0]
+    amax = np.abs(X.reshape(C, -1)).max(axis=1).astype(np.float32).astype(np.float64)
+    bound = amax + np.abs(mean)
+    s = np.where(bound > 0, np.exp2(np.floor(np.log2(448.0 / np.where(bound > 0, bound, 1.0)))), 1.0)
+    m = (np.abs(V) / s[:, None]).max(axis=0)
+    t = np.where(m > 0, np.exp2(np.floor(np.log2(448.0 / np.where(m > 0, m, 1.0)))), 1.0)
+    b = (V / s[:, None] * t[None, :]).astype(np.float32)
+    hi = _e4m3(b)
+    lo = _e4m3(b - hi)
+    xc = (X.reshape(C, -1).astype(np.float32) - mean.astype(np.float32)[:, None]) * s.astype(np.float32)[:, None]
+    A = _e4m3(xc.astype(np.float32))
+    return A.astype(np.float64), (hi.astype(np.float64) + lo.astype(np.float64)) / t[None, :]
+
+
+@pytest.mark.parametrize("C,H,W,d", [(64, 40, 48, 16), (256, 32, 64, 32), (200, 24, 40, 64), (512, 16, 32, 32)])
+def test_project_fp8_matches_rounded_operands(q, C, H, W, d):
+    # tcgen05 kind::f8f6f4 result equals the FP64 sum of the same e4m3 operands
+    # up to FP32 accumulation: checks scales, packing, 128-channel chunk
+    # assembly, descriptors and the epilogue's component scale element by element
+    img = _case(C, H, W, seed=C * 5 + W)
+    mean, V, _, _ = oracle.fit(img.X, d)
+    out = q.quantize(to_dev(img.X), (to_dev(mean), to_dev(V)), 16, "fp8", want_Y=True)
+    torch.cuda.synchronize()
+    A, Bm = _fp8_operands(img.X, mean, V)
+    Y_ref = (Bm.T @ A).reshape(d, H, W)
+    bound = (np.abs(Bm).T @ np.abs(A)).reshape(d, H, W) * 1e-6 + 1e-30
+    Y_g = out["Y"].cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(Y_g - Y_ref) <= bound), np.max(np.abs(Y_g - Y_ref) / bound)
+    qb, _, _ = oracle.quantize(Y_g, 16, fp32_decision=True)
+    np.testing.assert_array_equal(bins_np(out["bins"], W), qb)
+
+
+def test_fp8_precision_sweep_config1(q):
+    # precision sweep on the single-image workload: FP32 / BF16 / FP8 projection
+    # against the FP64 oracle (bin flips, score error, AUROC)
+    img = synth.make_image("plain_128_c64", 0)
+    d, B, r = 16, 16, 4
+    ref = oracle.pipeline(img.X, d, B, r)
+    Xd = to_dev(img.X)
+    basis = q.fit_pca(Xd, d)
+    res = {}
+    for prec in ("f32", "bf16", "fp8"):
+        out = q.quantize(Xd, basis, B, prec)
+        s = q.score(out["bins"], 128, B, r, out["hist"], 128 * 128)
+        torch.cuda.synchronize()
+        sg = s.cpu().numpy()
+        res[prec] = dict(flips=float((bins_np(out["bins"], 128) != ref["q"]).mean()),
+                         max_err=float(np.abs(sg - ref["score"]).max()),
+                         auroc=auroc(sg, img.mask))
+    a_o = auroc(ref["score"], img.mask)
+    print("precision sweep", res, "oracle auroc", a_o)
+    assert res["f32"]["flips"] <= res["bf16"]["flips"] <= res["fp8"]["flips"]
+    # measured on GB300: flips 0 / 0.45% / 5.2%, AUROC within 0.002 of the oracle for all three
+    assert res["f32"]["flips"] <= 1e-3 and res["bf16"]["flips"] <= 0.01 and res["fp8"]["flips"] <= 0.08
+    assert abs(res["fp8"]["auroc"] - a_o) <= 0.01 and abs(res["bf16"]["auroc"] - a_o) <= 0.005
