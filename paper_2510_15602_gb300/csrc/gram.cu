@@ -178,6 +178,34 @@ __device__ __forceinline__ void convert_block(const float (&v)[2][8], int C, int
     }
 }
 
+// The level sums of one 64-pixel sub-chunk: A_L += sum_{i+j=L} D_i E_j^T for
+// L = 0..3 (D: the A block's digit slices, E: the B block's).  The B slices
+// lie back to back in shared memory (128 rows each, the same 1024-B row-group
+// stride), so slices j..j+1 form one 256-row operand: A_i times slices
+// j0..j0+1 fills the accumulators of levels i+j0 and i+j0+1 (TMEM columns
+// 128 (i+j0) .. +256) in one N = 256 instruction.  Per K-step: A_0 x E_0..1
+// and A_0 x E_2..3 (issued first: they start all four levels of a window),
+// A_1 x E_0..1, A_1 x E_2, A_2 x E_0..1, A_3 x E_0 -- 6 MMAs instead of 10.
+__device__ __forceinline__ void issue_level_mmas(uint32_t tmem, uint32_t a_addr, uint32_t b_addr, bool first) {
+    const uint64_t ad0 = tc::sdesc_kmajor_sw128(a_addr), bd0 = tc::sdesc_kmajor_sw128(b_addr);
+    constexpr uint32_t id256 = tc::idesc_bf16_f32(kTB, 256), id128 = tc::idesc_bf16_f32(kTB, 128);
+    constexpr int kSl = kTB * 128;  // bytes of one digit slice
+    const uint32_t acc0 = first ? 0u : 1u;
+#pragma unroll
+    for (int ks = 0; ks < 4; ks++) {
+        // descriptors differ only in the start-address field (bytes >> 4)
+        auto A = [&](int i) { return ad0 + (uint64_t)((i * kSl + ks * 32) >> 4); };
+        auto E = [&](int j) { return bd0 + (uint64_t)((j * kSl + ks * 32) >> 4); };
+        const uint32_t a0 = ks == 0 ? acc0 : 1u;
+        tc::mma_bf16_ss(tmem + 0 * kTB, A(0), E(0), id256, a0);  // levels 0, 1
+        tc::mma_bf16_ss(tmem + 2 * kTB, A(0), E(2), id256, a0);  // levels 2, 3
+        tc::mma_bf16_ss(tmem + 1 * kTB, A(1), E(0), id256, 1u);  // levels 1, 2
+        tc::mma_bf16_ss(tmem + 3 * kTB, A(1), E(2), id128, 1u);  // level 3
+        tc::mma_bf16_ss(tmem + 2 * kTB, A(2), E(0), id256, 1u);  // levels 2, 3
+        tc::mma_bf16_ss(tmem + 3 * kTB, A(3), E(0), id128, 1u);  // level 3
+    }
+}
+
 // Grid: images * n_pairs * n_split CTAs.  Per image: Gint [C][C] int64 (upper
 // tiles accumulated), Dsum [4][C] int64, scale [C].
 __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ FitParams p,
@@ -226,7 +254,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = tc::idesc_bf16_f32(kTB, kTB);
     const uint32_t a_base = tc::smem_u32(As);
     const uint32_t b_base = diag ? a_base : tc::smem_u32(Bs);
 
@@ -249,18 +276,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
         __syncthreads();
         if (tid == 0) {
             tc::tc_fence_after();
-            for (int L = 0; L < 4; L++) {
-                bool first = in_win == 0;
-                for (int i = 0; i <= L; i++) {
-                    const int j = L - i;
-                    for (int ks = 0; ks < 4; ks++) {
-                        const uint64_t ad = tc::sdesc_kmajor_sw128(a_base + i * kTB * 128 + ks * 32);
-                        const uint64_t bd = tc::sdesc_kmajor_sw128(b_base + j * kTB * 128 + ks * 32);
-                        tc::mma_bf16_ss(tmem + (uint32_t)(L * kTB), ad, bd, idesc, first ? 0u : 1u);
-                        first = false;
-                    }
-                }
-            }
+            issue_level_mmas(tmem, a_base, b_base, in_win == 0);
             tc::mma_commit(bar);
         }
         // the next sub-chunk's features are fetched while the tensor cores run

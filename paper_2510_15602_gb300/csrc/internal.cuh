@@ -176,9 +176,11 @@ bool ctx_sticky(qfca_ctx *ctx);
 cudaError_t make_tmap_u8_3d(void *tmap_out, const void *base, uint64_t dim0, uint64_t dim1, uint64_t dim2,
                             uint64_t stride1_bytes, uint64_t stride2_bytes, uint32_t box0, uint32_t box1);
 
-// 2-D FP32 tiled tensor map (no swizzle, zero fill out of bounds); dim0 innermost.
+// 2-D FP32 tiled tensor map (zero fill out of bounds); dim0 innermost.
+// swizzle128: 128-byte swizzle in shared memory (the box's inner extent must
+// be 128 bytes; 16-B chunk c of box row r lands at chunk c ^ (r & 7)).
 cudaError_t make_tmap_f32_2d(void *tmap_out, const void *base, uint64_t dim0, uint64_t dim1, uint64_t stride1_bytes,
-                             uint32_t box0, uint32_t box1);
+                             uint32_t box0, uint32_t box1, bool swizzle128 = false);
 
 // ------------------------------------------------------------------ helpers
 

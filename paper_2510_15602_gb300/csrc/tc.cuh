@@ -84,6 +84,18 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows of
+// 64 B, 8-row atoms 512 B apart (stride byte offset), base 512-B aligned.
+__device__ __forceinline__ uint64_t sdesc_kmajor_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address >> 4
+    d |= (uint64_t)1u << 16;                  // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512u >> 4) << 32;         // stride byte offset >> 4
+    d |= (uint64_t)1u << 46;                  // descriptor version (tcgen05)
+    d |= (uint64_t)4u << 61;                  // 64-byte swizzle
+    return d;
+}
+
 // Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 accumulator, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4)                          // D format: F32

@@ -39,7 +39,7 @@ cudaError_t make_tmap_u8_3d(void *tmap_out, const void *base, uint64_t dim0, uin
 }
 
 cudaError_t make_tmap_f32_2d(void *tmap_out, const void *base, uint64_t dim0, uint64_t dim1, uint64_t stride1_bytes,
-                             uint32_t box0, uint32_t box1) {
+                             uint32_t box0, uint32_t box1, bool swizzle128) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_tmap_mu);
@@ -57,7 +57,8 @@ cudaError_t make_tmap_f32_2d(void *tmap_out, const void *base, uint64_t dim0, ui
     const cuuint32_t box[2] = {box0, box1};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = enc((CUtensorMap *)tmap_out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims,
-                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
