@@ -73,6 +73,10 @@ __host__ __device__ inline long rows_elems(int n, int R) {
     return mx;
 }
 
+// The two halves of a cluster barrier (all threads of every CTA take part).
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
+
 __device__ __forceinline__ void acc_down(ffa::acc &A, int o) {
     ffa::acc B;
     B.s = __shfl_down_sync(0xffffffffu, A.s, o);
@@ -167,10 +171,14 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
     ff *qbuf = rows + a.region0;                     // [R][n] partial products pushed by every CTA
     ff *xa = qbuf + (size_t)R * n;                   // [n] current column (x)
     ff *xb = xa + n;                                 // [n] next column
-    ff *pbuf = xb + n;                               // [n]
+    ff *pbuf = xb + n;                               // [n] column part of the own partial product, then p
     ff *wbuf = pbuf + n;                             // [n]
-    ffa::acc *red = reinterpret_cast<ffa::acc *>(wbuf + n);  // [kNW]
-    ff *fsc = reinterpret_cast<ff *>(red + kNW);             // [4] step scalars
+    ff *pbuf2 = wbuf + n;                            // [n] row part (own rows)
+    ff *colb = pbuf2 + n;                            // [n] column k+1 before the update, gathered from every CTA
+    ffa::acc *red = reinterpret_cast<ffa::acc *>(colb + n);  // [kNW]
+    ffa::acc *wsq = red + kNW;                                // [kNW] per-warp squared norms of the next column
+    ff *fsc = reinterpret_cast<ff *>(wsq + kNW);              // [4] step scalars
+    ff *dpart = fsc + 4;                                      // [8] per-CTA partial products q_r . v
 
     const ff *S = a.cov + (long)mat * n * n;
     ff *dg = a.dg + (long)mat * n, *ed = a.ed + (long)mat * n;
@@ -197,11 +205,21 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
 
     ff *xcur = xa, *xnext = xb;
     // ---------------------------------------------------------------- 1. tridiagonalisation
+    // One cluster exchange per step: with its partial product q_r each CTA pushes
+    // its own rows' entries of column k+1 (before the update); after the barrier
+    // every CTA forms w and the updated column k+1 itself, with the same
+    // float-float expression the row update uses, so the next step needs no
+    // second exchange. The buffers that receive the pushes (qbuf, colb, dpart)
+    // are released by a split barrier: each CTA arrives once it has read them and
+    // waits just before its next push, so the wait is normally already satisfied.
+    ff sig;
+    {
+        ffa::acc A = ffa::acc_zero();
+        for (int j = 1 + tid; j < n - 1; j += kT) ffa::acc_fma(A, xcur[j], xcur[j]);
+        sig = block_acc(A, red);
+    }
     for (int k = 0; k + 2 < n; k++) {
         const int m = n - k - 1;
-        ffa::acc A = ffa::acc_zero();
-        for (int j = 1 + tid; j < m; j += kT) ffa::acc_fma(A, xcur[j], xcur[j]);
-        const ff sig = block_acc(A, red);  // identical in every CTA of the cluster
         if (tid == 0) {
             const ff alpha = xcur[0];
             ff tau = ffa::zero(), ek = alpha, v0 = alpha;
@@ -215,6 +233,7 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
             fsc[1] = v0;
             fsc[2] = ffa::scale(tau, 0.5f);
             if (r == 0) { tau_g[k] = tau; v0_g[k] = v0; ed[k] = ek; }
+            if (k >= 1 && k % R == r) dg[k] = rows[row_off(k / R, r, R) + k];  // updated by step k-1
         }
         __syncthreads();
         const ff tau = fsc[0], v0 = fsc[1], htau = fsc[2];
@@ -223,6 +242,8 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
             for (int j = tid; j < m; j += kT) Vh[(long)k * n + j] = j == 0 ? v0 : xcur[j];
         int l0 = (k + 1 - r + R - 1) / R;  // first own row with i >= k+1
         if (l0 < 0) l0 = 0;
+        int l2 = (k + 2 - r + R - 1) / R;  // first own row with i >= k+2
+        if (l2 < 0) l2 = 0;
         if (reflect) {
             // ---- column part of the own partial product: sum over own rows i > jc of A[i][jc] v_i
             for (int jc = k + 1 + tid; jc < n; jc += kT) {
@@ -240,8 +261,7 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
                 ffa::acc_merge(Q0, Q1);
                 pbuf[jc - k - 1] = ffa::acc_value(Q0);
             }
-            __syncthreads();
-            // ---- plus the row part for own rows i >= k+1: sum_{j=k+1..i} A[i][j] v_j
+            // ---- the row part for own rows i >= k+1 (sum_{j=k+1..i} A[i][j] v_j), into its own buffer
             for (int l = l0 + warp; l < nloc; l += kNW) {
                 const int i = r + l * R;
                 const ff *row = rows + row_off(l, r, R);
@@ -249,31 +269,61 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
                 for (int j = k + 1 + lane; j <= i; j += 32) ffa::acc_fma(Q, row[j], j == k + 1 ? v0 : xcur[j - k - 1]);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc_down(Q, o);
-                if (lane == 0) {
-                    ffa::acc_add(Q, pbuf[i - k - 1]);
-                    pbuf[i - k - 1] = ffa::acc_value(Q);
-                }
+                if (lane == 0) pbuf2[i - k - 1] = ffa::acc_value(Q);
             }
             __syncthreads();
+            if (k > 0) cluster_wait();  // every CTA has read the previous step's pushes
+            // ---- push q_r and this CTA's entries of column k+1 to every CTA, with q_r . v
+            ffa::acc D = ffa::acc_zero();
             for (int j = tid; j < m; j += kT) {
-                const ff q = pbuf[j];
+                const int i = j + k + 1;
+                const ff q = (i >= r && (i - r) % R == 0) ? ffa::add(pbuf[j], pbuf2[j]) : pbuf[j];
                 for (int dst = 0; dst < R; dst++) cl.map_shared_rank(qbuf, dst)[(size_t)r * n + j] = q;
+                ffa::acc_fma(D, q, j == 0 ? v0 : xcur[j]);
+            }
+            for (int l = l2 + tid; l < nloc; l += kT) {
+                const int i = r + l * R;
+                const ff c = rows[row_off(l, r, R) + k + 1];
+                for (int dst = 0; dst < R; dst++) cl.map_shared_rank(colb, dst)[i - k - 2] = c;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc_down(D, o);
+            if (lane == 0) red[warp] = D;
+            __syncthreads();
+            if (tid == 0) {
+                ffa::acc T = red[0];
+                for (int w = 1; w < kNW; w++) ffa::acc_merge(T, red[w]);
+                const ff dr = ffa::acc_value(T);
+                for (int dst = 0; dst < R; dst++) cl.map_shared_rank(dpart, dst)[r] = dr;
             }
             cl.sync();
-            // ---- p = tau sum_r q_r ; w = p - (tau/2)(p.v) v
+            // ---- p = tau sum_r q_r ;  p.v = tau sum_r (q_r . v) ;  w = p - (tau/2)(p.v) v
             ffa::acc PV = ffa::acc_zero();
+            for (int s2 = 0; s2 < R; s2++) ffa::acc_add(PV, dpart[s2]);
+            const ff pv = ffa::mul(tau, ffa::acc_value(PV));
+            const ff K = ffa::mul(htau, pv);
             for (int j = tid; j < m; j += kT) {
                 ffa::acc P = ffa::acc_zero();
-                for (int s = 0; s < R; s++) ffa::acc_add(P, qbuf[(size_t)s * n + j]);
-                const ff p = ffa::mul(tau, ffa::acc_value(P));
-                pbuf[j] = p;
-                ffa::acc_fma(PV, p, j == 0 ? v0 : xcur[j]);
+                for (int s2 = 0; s2 < R; s2++) ffa::acc_add(P, qbuf[(size_t)s2 * n + j]);
+                const ff pj = ffa::mul(tau, ffa::acc_value(P));
+                wbuf[j] = ffa::sub(pj, ffa::mul(K, j == 0 ? v0 : xcur[j]));
             }
-            const ff pv = block_acc(PV, red);
-            const ff K = ffa::mul(htau, pv);
-            for (int j = tid; j < m; j += kT) wbuf[j] = ffa::sub(pbuf[j], ffa::mul(K, j == 0 ? v0 : xcur[j]));
             __syncthreads();
-            // ---- rank-2 update of own rows (lower part); push the new column k+1
+            // ---- the updated column k+1 (all of it, in every CTA) and its squared norm
+            ffa::acc SQ = ffa::acc_zero();
+            const ff w0 = wbuf[0];
+            for (int jn = tid; jn < m - 1; jn += kT) {  // row i = k + 2 + jn, ii = i - k - 1 = jn + 1
+                const ff vi = xcur[jn + 1], wi = wbuf[jn + 1];
+                const ff t = ffa::add(ffa::mul(vi, w0), ffa::mul(wi, v0));
+                const ff nv = ffa::sub(colb[jn], t);
+                xnext[jn] = nv;
+                if (jn >= 1) ffa::acc_fma(SQ, nv, nv);
+            }
+            cluster_arrive();  // done with qbuf, colb and dpart of this step
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc_down(SQ, o);
+            if (lane == 0) wsq[warp] = SQ;
+            // ---- rank-2 update of own rows (lower part, from column k+1)
             for (int l = l0 + warp; l < nloc; l += kNW) {
                 const int i = r + l * R;
                 ff *row = rows + row_off(l, r, R);
@@ -283,29 +333,40 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
                 for (int j = k + 1 + lane; j <= i; j += 32) {
                     const int jj = j - k - 1;
                     const ff t = ffa::add(ffa::mul(vi, wbuf[jj]), ffa::mul(wi, jj == 0 ? v0 : xcur[jj]));
-                    const ff nv = ffa::sub(row[j], t);
-                    row[j] = nv;
-                    if (jj == 0 && i >= k + 2)
-                        for (int dst = 0; dst < R; dst++) cl.map_shared_rank(xnext, dst)[i - k - 2] = nv;
+                    row[j] = ffa::sub(row[j], t);
                 }
             }
         } else {
-            // no reflection: only gather the next column
-            int lg = (k + 2 - r + R - 1) / R;
-            if (lg < 0) lg = 0;
-            for (int l = lg + tid; l < nloc; l += kT) {
+            // no reflection: the next column is column k+1 as it stands
+            if (k > 0) cluster_wait();
+            for (int l = l2 + tid; l < nloc; l += kT) {
                 const int i = r + l * R;
-                const ff nv = rows[row_off(l, r, R) + k + 1];
-                for (int dst = 0; dst < R; dst++) cl.map_shared_rank(xnext, dst)[i - k - 2] = nv;
+                const ff c = rows[row_off(l, r, R) + k + 1];
+                for (int dst = 0; dst < R; dst++) cl.map_shared_rank(colb, dst)[i - k - 2] = c;
             }
+            cl.sync();
+            ffa::acc SQ = ffa::acc_zero();
+            for (int jn = tid; jn < m - 1; jn += kT) {
+                xnext[jn] = colb[jn];
+                if (jn >= 1) ffa::acc_fma(SQ, colb[jn], colb[jn]);
+            }
+            cluster_arrive();
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc_down(SQ, o);
+            if (lane == 0) wsq[warp] = SQ;
         }
         __syncthreads();
-        if (tid == 0 && (k + 1) % R == r) dg[k + 1] = rows[row_off((k + 1) / R, r, R) + k + 1];
-        cl.sync();
+        {   // squared norm of the next column's x[1..]: the warps' sums merged in a fixed order
+            ffa::acc T = wsq[0];
+            for (int w = 1; w < kNW; w++) ffa::acc_merge(T, wsq[w]);
+            sig = ffa::acc_value(T);
+        }
         ff *t = xcur;
         xcur = xnext;
         xnext = t;
     }
+    if (n >= 3) cluster_wait();  // completes the last step's arrive
+    __syncthreads();
     if (tid == 0) {
         if (r == 0) {
             ed[n - 1] = ffa::zero();
@@ -313,6 +374,7 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
             v0_g[n - 1] = ffa::zero();
             if (n >= 2) { tau_g[n - 2] = ffa::zero(); v0_g[n - 2] = ffa::zero(); }
         }
+        if (n >= 3 && (n - 2) % R == r) dg[n - 2] = rows[row_off((n - 2) / R, r, R) + n - 2];
         if (n >= 2 && (n - 1) % R == r) {
             const ff *row = rows + row_off((n - 1) / R, r, R);
             ed[n - 2] = row[n - 2];
@@ -534,7 +596,8 @@ size_t smem_plan(int n, int d, int R, long *region0, int *nslots) {
     if ((long)n * ncol > reg) reg = (long)n * ncol;
     *region0 = reg;
     *nslots = ns;
-    return sizeof(ff) * ((size_t)reg + (size_t)R * n + 4 * (size_t)n) + sizeof(ffa::acc) * kNW + sizeof(ff) * 4;
+    return sizeof(ff) * ((size_t)reg + (size_t)R * n + 6 * (size_t)n) + 2 * sizeof(ffa::acc) * kNW +
+           sizeof(ff) * (4 + 8);
 }
 
 // Cluster size: the smallest R whose shared-memory plan fits, raised for small
