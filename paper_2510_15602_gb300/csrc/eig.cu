@@ -84,6 +84,35 @@ __device__ __forceinline__ void acc_down(ffa::acc &A, int o) {
     ffa::acc_merge(A, B);
 }
 
+// Pairwise tree over the 16 per-warp sums (same order in every thread and CTA).
+__device__ __forceinline__ ff tree16(const ffa::acc *red) {
+    ffa::acc T[kNW];
+#pragma unroll
+    for (int w = 0; w < kNW; w++) T[w] = red[w];
+#pragma unroll
+    for (int step = 1; step < kNW; step <<= 1)
+#pragma unroll
+        for (int w = 0; w + step < kNW; w += 2 * step) ffa::acc_merge(T[w], T[w + step]);
+    return ffa::acc_value(T[0]);
+}
+
+// One entry of the symmetric rank-2 update: a - (vi wj + wi vj), float-float,
+// both products kept exact to their FMA error terms and summed into a once.
+__device__ __forceinline__ ff rank2(ff a, ff vi, ff wj, ff wi, ff vj) {
+    const float p1 = __fmul_rn(vi.hi, wj.hi);
+    float e1 = __fmaf_rn(vi.hi, wj.hi, -p1);
+    e1 = __fmaf_rn(vi.hi, wj.lo, e1);
+    e1 = __fmaf_rn(vi.lo, wj.hi, e1);
+    const float p2 = __fmul_rn(wi.hi, vj.hi);
+    float e2 = __fmaf_rn(wi.hi, vj.hi, -p2);
+    e2 = __fmaf_rn(wi.hi, vj.lo, e2);
+    e2 = __fmaf_rn(wi.lo, vj.hi, e2);
+    const ff s1 = ffa::two_sum(a.hi, -p1);
+    const ff s2 = ffa::two_sum(s1.hi, -p2);
+    const float lo = __fadd_rn(__fadd_rn(__fsub_rn(a.lo, __fadd_rn(e1, e2)), s1.lo), s2.lo);
+    return ffa::fast_two_sum(s2.hi, lo);
+}
+
 // Deterministic block reduction; every thread gets the same value.
 __device__ ff block_acc(ffa::acc A, ffa::acc *red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -168,14 +197,16 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
 
     extern __shared__ __align__(16) unsigned char smraw[];
     ff *rows = reinterpret_cast<ff *>(smraw);        // region 0
-    ff *qbuf = rows + a.region0;                     // [R][n] partial products pushed by every CTA
-    ff *xa = qbuf + (size_t)R * n;                   // [n] current column (x)
+    const int nq = (n + 1) & ~1;                     // qbuf row stride (16-byte rows)
+    ff *qbuf = rows + a.region0;                     // [R][nq] partial products pushed by every CTA
+    ff *xa = qbuf + (size_t)R * nq;                  // [n] current column (x)
     ff *xb = xa + n;                                 // [n] next column
     ff *pbuf = xb + n;                               // [n] column part of the own partial product, then p
     ff *wbuf = pbuf + n;                             // [n]
     ff *pbuf2 = wbuf + n;                            // [n] row part (own rows)
     ff *colb = pbuf2 + n;                            // [n] column k+1 before the update, gathered from every CTA
-    ffa::acc *red = reinterpret_cast<ffa::acc *>(colb + n);  // [kNW]
+    ff *pcol1 = colb + n;                            // [n] column part of the second row group
+    ffa::acc *red = reinterpret_cast<ffa::acc *>(pcol1 + n);  // [kNW]
     ffa::acc *wsq = red + kNW;                                // [kNW] per-warp squared norms of the next column
     ff *fsc = reinterpret_cast<ff *>(wsq + kNW);              // [4] step scalars
     ff *dpart = fsc + 4;                                      // [8] per-CTA partial products q_r . v
@@ -220,14 +251,15 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
     }
     for (int k = 0; k + 2 < n; k++) {
         const int m = n - k - 1;
+        // ---- the reflector (one thread, while the others start on the product)
         if (tid == 0) {
             const ff alpha = xcur[0];
             ff tau = ffa::zero(), ek = alpha, v0 = alpha;
             if (sig.hi > 0.0f) {
-                const ff mu = ffa::sqrt(ffa::add(ffa::mul(alpha, alpha), sig));
+                const ff mu = ffa::sqrt_newton(ffa::add(ffa::mul(alpha, alpha), sig));
                 if (alpha.hi >= 0.0f) { v0 = ffa::add(alpha, mu); ek = ffa::neg(mu); }
                 else { v0 = ffa::sub(alpha, mu); ek = mu; }
-                tau = ffa::div(ffa::make(2.0f, 0.0f), ffa::add(ffa::mul(v0, v0), sig));
+                tau = ffa::div_newton(ffa::make(2.0f, 0.0f), ffa::add(ffa::mul(v0, v0), sig));
             }
             fsc[0] = tau;
             fsc[1] = v0;
@@ -235,51 +267,87 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
             if (r == 0) { tau_g[k] = tau; v0_g[k] = v0; ed[k] = ek; }
             if (k >= 1 && k % R == r) dg[k] = rows[row_off(k / R, r, R) + k];  // updated by step k-1
         }
+        int l0 = (k + 1 - r + R - 1) / R;  // first own row with i >= k+1
+        if (l0 < 0) l0 = 0;
+        int l2 = (k + 2 - r + R - 1) / R;  // first own row with i >= k+2
+        if (l2 < 0) l2 = 0;
+        // ---- own partial product of A with x (x_0 = alpha in place of v_0; the
+        // difference (v_0 - alpha) A e_0 touches only own rows and is added below):
+        // column part (sum over own rows i > jc of A[i][jc] x_i): thread (g, c) takes
+        // column k+1+c and every other own row below it (row group g), the longest
+        // columns on the last warps (warp 0 also forms the reflector);
+        // row part (sum over j <= i of A[i][j] x_j): 8 lanes per own row, 4 rows per warp.
+        {
+            const int g = tid >> 8;
+            for (int c = 255 - (tid & 255); c < m; c += 256) {
+                const int jc = k + 1 + c;
+                ffa::acc Q0 = ffa::acc_zero(), Q1 = ffa::acc_zero();  // two chains for ILP
+                int lc = (jc + 1 - r + R - 1) / R;
+                if (lc < 0) lc = 0;
+                int l = lc + g;
+                for (; l + 2 < nloc; l += 4) {
+                    const int i0 = r + l * R, i1 = i0 + 2 * R;  // i >= jc + 1 >= k + 2
+                    ffa::acc_fma(Q0, rows[row_off(l, r, R) + jc], xcur[i0 - k - 1]);
+                    ffa::acc_fma(Q1, rows[row_off(l + 2, r, R) + jc], xcur[i1 - k - 1]);
+                }
+                if (l < nloc) ffa::acc_fma(Q0, rows[row_off(l, r, R) + jc], xcur[r + l * R - k - 1]);
+                ffa::acc_merge(Q0, Q1);
+                (g ? pcol1 : pbuf)[c] = ffa::acc_value(Q0);
+            }
+        }
+        {
+            const int s8 = lane & 7;
+            for (int base = l0 + warp * 4; base < nloc; base += 4 * kNW) {  // warp-uniform
+                const int l = base + (lane >> 3);
+                ffa::acc Q0 = ffa::acc_zero(), Q1 = ffa::acc_zero();
+                int i = -1;
+                if (l < nloc) {
+                    i = r + l * R;
+                    const ff *row = rows + row_off(l, r, R);
+                    int j = k + 1 + s8;
+                    for (; j + 8 <= i; j += 16) {
+                        ffa::acc_fma(Q0, row[j], xcur[j - k - 1]);
+                        ffa::acc_fma(Q1, row[j + 8], xcur[j + 8 - k - 1]);
+                    }
+                    if (j <= i) ffa::acc_fma(Q0, row[j], xcur[j - k - 1]);
+                    ffa::acc_merge(Q0, Q1);
+                }
+#pragma unroll
+                for (int o = 4; o > 0; o >>= 1) {
+                    ffa::acc B;
+                    B.s = __shfl_xor_sync(0xffffffffu, Q0.s, o);
+                    B.c = __shfl_xor_sync(0xffffffffu, Q0.c, o);
+                    ffa::acc_merge(Q0, B);
+                }
+                if (i >= 0 && s8 == 0) pbuf2[i - k - 1] = ffa::acc_value(Q0);
+            }
+        }
         __syncthreads();
         const ff tau = fsc[0], v0 = fsc[1], htau = fsc[2];
         const bool reflect = tau.hi != 0.0f;
         if (r == 0)
             for (int j = tid; j < m; j += kT) Vh[(long)k * n + j] = j == 0 ? v0 : xcur[j];
-        int l0 = (k + 1 - r + R - 1) / R;  // first own row with i >= k+1
-        if (l0 < 0) l0 = 0;
-        int l2 = (k + 2 - r + R - 1) / R;  // first own row with i >= k+2
-        if (l2 < 0) l2 = 0;
         if (reflect) {
-            // ---- column part of the own partial product: sum over own rows i > jc of A[i][jc] v_i
-            for (int jc = k + 1 + tid; jc < n; jc += kT) {
-                ffa::acc Q0 = ffa::acc_zero(), Q1 = ffa::acc_zero();  // two chains for ILP
-                int lc = (jc + 1 - r + R - 1) / R;
-                if (lc < 0) lc = 0;
-                int l = lc;
-                for (; l + 1 < nloc; l += 2) {
-                    const int i0 = r + l * R, i1 = i0 + R;  // i >= jc + 1 >= k + 2: v_i = x_{i-k-1}
-                    const ff a0 = rows[row_off(l, r, R) + jc], a1 = rows[row_off(l + 1, r, R) + jc];
-                    ffa::acc_fma(Q0, a0, xcur[i0 - k - 1]);
-                    ffa::acc_fma(Q1, a1, xcur[i1 - k - 1]);
-                }
-                if (l < nloc) ffa::acc_fma(Q0, rows[row_off(l, r, R) + jc], xcur[r + l * R - k - 1]);
-                ffa::acc_merge(Q0, Q1);
-                pbuf[jc - k - 1] = ffa::acc_value(Q0);
-            }
-            // ---- the row part for own rows i >= k+1 (sum_{j=k+1..i} A[i][j] v_j), into its own buffer
-            for (int l = l0 + warp; l < nloc; l += kNW) {
-                const int i = r + l * R;
-                const ff *row = rows + row_off(l, r, R);
-                ffa::acc Q = ffa::acc_zero();
-                for (int j = k + 1 + lane; j <= i; j += 32) ffa::acc_fma(Q, row[j], j == k + 1 ? v0 : xcur[j - k - 1]);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc_down(Q, o);
-                if (lane == 0) pbuf2[i - k - 1] = ffa::acc_value(Q);
-            }
-            __syncthreads();
             if (k > 0) cluster_wait();  // every CTA has read the previous step's pushes
             // ---- push q_r and this CTA's entries of column k+1 to every CTA, with q_r . v
             ffa::acc D = ffa::acc_zero();
-            for (int j = tid; j < m; j += kT) {
-                const int i = j + k + 1;
-                const ff q = (i >= r && (i - r) % R == 0) ? ffa::add(pbuf[j], pbuf2[j]) : pbuf[j];
-                for (int dst = 0; dst < R; dst++) cl.map_shared_rank(qbuf, dst)[(size_t)r * n + j] = q;
-                ffa::acc_fma(D, q, j == 0 ? v0 : xcur[j]);
+            const ff dv = ffa::sub(v0, xcur[0]);  // v_0 - alpha
+            for (int j = 2 * tid; j < m; j += 2 * kT) {  // two entries per 16-byte remote store
+                float4 q2;
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int jj = j + h, i = jj + k + 1;
+                    ff q = ffa::zero();
+                    if (jj < m) {
+                        q = ffa::add(pbuf[jj], pcol1[jj]);
+                        if (i >= r && (i - r) % R == 0)
+                            q = ffa::add(q, ffa::add(pbuf2[jj], ffa::mul(dv, rows[row_off((i - r) / R, r, R) + k + 1])));
+                        ffa::acc_fma(D, q, jj == 0 ? v0 : xcur[jj]);
+                    }
+                    if (h == 0) { q2.x = q.hi; q2.y = q.lo; } else { q2.z = q.hi; q2.w = q.lo; }
+                }
+                for (int dst = 0; dst < R; dst++)
+                    *reinterpret_cast<float4 *>(cl.map_shared_rank(qbuf, dst) + (size_t)r * nq + j) = q2;
             }
             for (int l = l2 + tid; l < nloc; l += kT) {
                 const int i = r + l * R;
@@ -290,11 +358,9 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
             for (int o = 16; o > 0; o >>= 1) acc_down(D, o);
             if (lane == 0) red[warp] = D;
             __syncthreads();
-            if (tid == 0) {
-                ffa::acc T = red[0];
-                for (int w = 1; w < kNW; w++) ffa::acc_merge(T, red[w]);
-                const ff dr = ffa::acc_value(T);
-                for (int dst = 0; dst < R; dst++) cl.map_shared_rank(dpart, dst)[r] = dr;
+            if (warp == 0) {
+                const ff dr = tree16(red);
+                if (lane < R) cl.map_shared_rank(dpart, lane)[r] = dr;
             }
             cl.sync();
             // ---- p = tau sum_r q_r ;  p.v = tau sum_r (q_r . v) ;  w = p - (tau/2)(p.v) v
@@ -304,7 +370,7 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
             const ff K = ffa::mul(htau, pv);
             for (int j = tid; j < m; j += kT) {
                 ffa::acc P = ffa::acc_zero();
-                for (int s2 = 0; s2 < R; s2++) ffa::acc_add(P, qbuf[(size_t)s2 * n + j]);
+                for (int s2 = 0; s2 < R; s2++) ffa::acc_add(P, qbuf[(size_t)s2 * nq + j]);
                 const ff pj = ffa::mul(tau, ffa::acc_value(P));
                 wbuf[j] = ffa::sub(pj, ffa::mul(K, j == 0 ? v0 : xcur[j]));
             }
@@ -313,9 +379,7 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
             ffa::acc SQ = ffa::acc_zero();
             const ff w0 = wbuf[0];
             for (int jn = tid; jn < m - 1; jn += kT) {  // row i = k + 2 + jn, ii = i - k - 1 = jn + 1
-                const ff vi = xcur[jn + 1], wi = wbuf[jn + 1];
-                const ff t = ffa::add(ffa::mul(vi, w0), ffa::mul(wi, v0));
-                const ff nv = ffa::sub(colb[jn], t);
+                const ff nv = rank2(colb[jn], xcur[jn + 1], w0, wbuf[jn + 1], v0);
                 xnext[jn] = nv;
                 if (jn >= 1) ffa::acc_fma(SQ, nv, nv);
             }
@@ -332,8 +396,7 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
                 const ff wi = wbuf[ii];
                 for (int j = k + 1 + lane; j <= i; j += 32) {
                     const int jj = j - k - 1;
-                    const ff t = ffa::add(ffa::mul(vi, wbuf[jj]), ffa::mul(wi, jj == 0 ? v0 : xcur[jj]));
-                    row[j] = ffa::sub(row[j], t);
+                    row[j] = rank2(row[j], vi, wbuf[jj], wi, jj == 0 ? v0 : xcur[jj]);
                 }
             }
         } else {
@@ -356,11 +419,7 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
             if (lane == 0) wsq[warp] = SQ;
         }
         __syncthreads();
-        {   // squared norm of the next column's x[1..]: the warps' sums merged in a fixed order
-            ffa::acc T = wsq[0];
-            for (int w = 1; w < kNW; w++) ffa::acc_merge(T, wsq[w]);
-            sig = ffa::acc_value(T);
-        }
+        sig = tree16(wsq);  // squared norm of the next column's x[1..], the same in every thread
         ff *t = xcur;
         xcur = xnext;
         xnext = t;
@@ -594,9 +653,10 @@ size_t smem_plan(int n, int d, int R, long *region0, int *nslots) {
     while (ns > 1 && t_part + ns * slot > reg) ns--;
     if (t_part + ns * slot > reg) reg = t_part + ns * slot;
     if ((long)n * ncol > reg) reg = (long)n * ncol;
+    reg = (reg + 1) & ~1L;  // qbuf starts on a 16-byte boundary
     *region0 = reg;
     *nslots = ns;
-    return sizeof(ff) * ((size_t)reg + (size_t)R * n + 6 * (size_t)n) + 2 * sizeof(ffa::acc) * kNW +
+    return sizeof(ff) * ((size_t)reg + (size_t)R * ((n + 1) & ~1) + 7 * (size_t)n) + 2 * sizeof(ffa::acc) * kNW +
            sizeof(ff) * (4 + 8);
 }
 

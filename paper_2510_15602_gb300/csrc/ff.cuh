@@ -72,6 +72,38 @@ __device__ __forceinline__ ff sqrt(ff a) {
     return fast_two_sum(s, __fdiv_rn(e.hi, __fmul_rn(2.0f, s)));
 }
 
+// The same two operations from the hardware's approximate reciprocal and
+// reciprocal square root (PTX rcp.approx / rsqrt.approx, about 2^-23
+// relative) refined by two Newton corrections in float-float (each squares the
+// relative error, down to float-float rounding).  Shorter dependency chains than
+// the correctly rounded FP32 divide and square root, for scalar chains on the
+// critical path.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ ff div_newton(ff a, ff b) {
+    const float y = rcp_approx(b.hi);
+    const float q1 = __fmul_rn(a.hi, y);
+    const ff r1 = sub(a, mul(ff{q1, 0.0f}, b));
+    const ff q = fast_two_sum(q1, __fmul_rn(r1.hi, y));
+    const ff r2 = sub(a, mul(q, b));
+    return add(q, ff{__fmul_rn(r2.hi, y), 0.0f});
+}
+__device__ __forceinline__ ff sqrt_newton(ff a) {
+    if (!(a.hi > 0.0f)) return ff{0.0f, 0.0f};
+    const float hy = __fmul_rn(0.5f, rsqrt_approx(a.hi));  // 1 / (2 sqrt(a))
+    const float s0 = __fmul_rn(a.hi, __fmul_rn(2.0f, hy));
+    const ff s1 = fast_two_sum(s0, __fmul_rn(sub(a, two_prod(s0, s0)).hi, hy));
+    return add(s1, ff{__fmul_rn(sub(a, mul(s1, s1)).hi, hy), 0.0f});
+}
+
 __device__ __forceinline__ ff scale(ff a, float p2) { return ff{__fmul_rn(a.hi, p2), __fmul_rn(a.lo, p2)}; }
 __device__ __forceinline__ bool less(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 __device__ __forceinline__ ff fabs_ff(ff a) { return a.hi < 0.0f ? ff{-a.hi, -a.lo} : a; }
