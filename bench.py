@@ -252,7 +252,6 @@ def kernel_work(name: str, H: int, W: int, C: int, d: int, B: int, r: int, nimg:
 # captures summarised in profiles/<kernel>_batch16_256_c256.md; an entry is
 # removed whenever its kernel changes after the capture.
 NCU_TRAFFIC = {
-    "k_eig_ff": 4840960,
     "k_project_tma": 1074424000 + 125305600,
     "k_window_emd": 33648384 + 73858816,
     "k_quantize": 134446336 + 19018240,
