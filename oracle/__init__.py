@@ -12,8 +12,10 @@ arXiv 2510.15602 it follows.
 
 Parity status: ``fit`` (Sec. 3.3), ``project`` (Sec. 3.3), ``quantize``
 (Sec. 3.1), ``ref_hist`` and ``score`` (Sec. 3.1, supplement's Wasserstein
-closed form) are each pinned by tests against closed forms, library routines
-or brute force (tests/test_oracle_pins.py).
+closed form), ``alg1`` (Algorithm 1; the supplement's correctness proof) and
+``assoc`` (Sec. 3.1's error-to-pixel association, the final blur) are each
+pinned by tests against closed forms, library routines or brute force
+(tests/test_oracle_pins.py).
 """
 from __future__ import annotations
 
@@ -72,6 +74,12 @@ def _load():
             lib.orc_score.restype = I
             lib.orc_score_at.argtypes = [P, I, I, I, I, I, P, ctypes.c_uint64, I, I, P]
             lib.orc_score_at.restype = ctypes.c_double
+            lib.orc_alg1.argtypes = [P, P, I, ctypes.c_int64, ctypes.c_int64, P]
+            lib.orc_alg1.restype = I
+            lib.orc_assoc.argtypes = [P, I, I, I, I, I, P, ctypes.c_uint64, ctypes.c_double, P, P, P]
+            lib.orc_assoc.restype = I
+            lib.orc_blur.argtypes = [P, I, I, ctypes.c_double, P]
+            lib.orc_blur.restype = I
             _lib = lib
     return _lib
 
@@ -207,6 +215,59 @@ def score_at(q: np.ndarray, B: int, r: int, R: np.ndarray, Nref: int, y: int, x:
     if s < 0:
         raise MemoryError("oracle score_at")
     return s, numer
+
+
+def alg1(P: np.ndarray, R: np.ndarray, Nloc: int | None = None, Nref: int | None = None):
+    """Algorithm 1 (Sec. 3.1) on one window histogram P against the reference R.
+
+    Masses are made equal by scaling (P * N_ref, R * N_loc).  Returns
+    (Enum int64 [B], steps): Enum[i] is the mass-weighted transport distance
+    charged to bin i (bin units); E_i = Enum[i] / (P[i] * N_ref).
+    """
+    P = np.ascontiguousarray(P, np.int64)
+    R = np.ascontiguousarray(R, np.int64)
+    B = P.shape[0]
+    Nloc = int(P.sum()) if Nloc is None else int(Nloc)
+    Nref = int(R.sum()) if Nref is None else int(Nref)
+    En = np.zeros(B, np.int64)
+    steps = _load().orc_alg1(_p(P), _p(R), B, Nloc, Nref, _p(En))
+    if steps < 0:
+        raise MemoryError("oracle alg1")
+    return En, int(steps)
+
+
+def blur(a: np.ndarray, sigma: float) -> np.ndarray:
+    """Gaussian smoothing of a map (the final low-pass step with sigma_s): separable,
+    taps |t| <= ceil(4 sigma), weights renormalised over the taps inside the image."""
+    a = np.ascontiguousarray(a, np.float64)
+    H, W = a.shape
+    out = np.zeros_like(a)
+    if _load().orc_blur(_p(a), H, W, float(sigma), _p(out)) < 0:
+        raise MemoryError("oracle blur")
+    return out
+
+
+def assoc(q: np.ndarray, B: int, r: int, R: np.ndarray, Nref: int | None = None, sigma_s: float = 1.0):
+    """The paper's scoring: Algorithm 1 per window and component, error-to-pixel
+    association (each pixel averages its own bin's error over the windows that
+    contain it, sigma_p = infinity), mean over components, Gaussian blur sigma_s
+    (Sec. 3.1 and its association paragraph; smoothing as in the sigma_s study).
+
+    Returns (score float64 [H,W], raw float64 [H,W] before the blur,
+    comp float64 [d,H,W] per-component associated errors).
+    """
+    q = np.ascontiguousarray(q, np.uint8)
+    d, H, W = q.shape
+    R = np.ascontiguousarray(R, np.uint32)
+    if Nref is None:
+        Nref = int(R[0].sum())
+    s = np.zeros((H, W), np.float64)
+    raw = np.zeros((H, W), np.float64)
+    comp = np.zeros((d, H, W), np.float64)
+    rc = _load().orc_assoc(_p(q), d, H, W, B, r, _p(R), int(Nref), float(sigma_s), _p(raw), _p(s), _p(comp))
+    if rc < 0:
+        raise MemoryError("oracle assoc")
+    return s, raw, comp
 
 
 def pipeline(X: np.ndarray, d: int, B: int, r: int, layout: int = NCHW):

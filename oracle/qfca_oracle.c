@@ -366,3 +366,168 @@ double orc_score_at(const uint8_t *q, int d, int H, int W, int B, int r, const u
     free(L);
     return s / (double)d;
 }
+
+/* ------------------------------------------------- Algorithm 1 + association */
+
+/* Algorithm 1 (Sec. 3.1, quantized patch mismatch score) for one window and one
+ * component.  The patch histogram P (N_loc pixels) and the reference R (N_ref
+ * pixels) have different masses; both are scaled to the common mass
+ * N_loc * N_ref first (P'_i = P_i N_ref, R'_j = R_j N_loc), so the two-pointer
+ * walk transports whole integers.  Each step compares the current bins: if
+ * P'_i < R'_j the whole remainder of P'_i goes to bin j (charged to E_i at
+ * distance |i - j|, bin units), R'_j shrinks and i advances; otherwise R'_j
+ * goes, P'_i shrinks and j advances.  Enum[i] receives the mass-weighted
+ * distance charged to bin i (an exact integer; the paper's E_i before its
+ * final division is Enum[i], and E_i = Enum[i] / P'_i).  Returns the number of
+ * steps (at most 2B - 1). */
+int orc_alg1(const int64_t *P, const int64_t *R, int B, int64_t Nloc, int64_t Nref, int64_t *Enum)
+{
+    int64_t *Pw = (int64_t *)malloc(sizeof(int64_t) * (B > 0 ? B : 1));
+    int64_t *Rw = (int64_t *)malloc(sizeof(int64_t) * (B > 0 ? B : 1));
+    if (!Pw || !Rw) {
+        free(Pw);
+        free(Rw);
+        return -1;
+    }
+    for (int b = 0; b < B; b++) {
+        Pw[b] = P[b] * Nref;
+        Rw[b] = R[b] * Nloc;
+        Enum[b] = 0;
+    }
+    int i = 0, j = 0, steps = 0;
+    while (i < B && j < B) {
+        int64_t dist = i > j ? i - j : j - i;
+        steps++;
+        if (Pw[i] < Rw[j]) {
+            Enum[i] += Pw[i] * dist;
+            Rw[j] -= Pw[i];
+            i++;
+        } else {
+            Enum[i] += Rw[j] * dist;
+            Pw[i] -= Rw[j];
+            j++;
+        }
+    }
+    free(Pw);
+    free(Rw);
+    return steps;
+}
+
+/* Gaussian smoothing of an H x W map with standard deviation sigma (the final
+ * low-pass step, sigma_s): separable, taps |t| <= ceil(4 sigma) with weights
+ * exp(-t^2 / (2 sigma^2)), renormalised over the taps that fall inside the
+ * image.  sigma <= 0 copies.  Returns 0, or -1 on allocation failure. */
+int orc_blur(const double *in, int H, int W, double sigma, double *out)
+{
+    long N = (long)H * W;
+    if (!(sigma > 0.0)) {
+        for (long p = 0; p < N; p++)
+            out[p] = in[p];
+        return 0;
+    }
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    if (!tmp)
+        return -1;
+    int R4 = (int)ceil(4.0 * sigma);
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            double s = 0.0, w = 0.0;
+            for (int t = -R4; t <= R4; t++)
+                if (x + t >= 0 && x + t < W) {
+                    double g = exp(-(double)t * t / (2.0 * sigma * sigma));
+                    s += g * in[(long)y * W + x + t];
+                    w += g;
+                }
+            tmp[(long)y * W + x] = s / w;
+        }
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            double s = 0.0, w = 0.0;
+            for (int t = -R4; t <= R4; t++)
+                if (y + t >= 0 && y + t < H) {
+                    double g = exp(-(double)t * t / (2.0 * sigma * sigma));
+                    s += g * tmp[(long)(y + t) * W + x];
+                    w += g;
+                }
+            out[(long)y * W + x] = s / w;
+        }
+    free(tmp);
+    return 0;
+}
+
+/* The paper's scoring (Sec. 3.1 and the error-to-pixel association): for each
+ * component k and each window centre p, Algorithm 1 gives the per-bin errors
+ * E_{k,p}[b] = Enum[b] / (P_b N_ref) (0 for empty bins).  A pixel q takes,
+ * from every window that contains it, the error of its own bin b_k(q), and
+ * averages them (the association with sigma_p = infinity: a box average over
+ * the window centres p with |p - q|_inf <= r inside the image); the score
+ * before smoothing is the mean over components:
+ *     raw(q) = (1/d) sum_k (1/n(q)) sum_{p in box(q)} E_{k,p}[b_k(q)].
+ * Then the Gaussian smoothing orc_blur with standard deviation sigma_s.  Writes raw[H][W], score[H][W] and, when
+ * non-NULL, comp[d][H][W] = the per-component averages.  Returns 0, or -1 on
+ * allocation failure. */
+int orc_assoc(const uint8_t *q, int d, int H, int W, int B, int r, const uint32_t *R, uint64_t Nref,
+              double sigma_s, double *raw, double *score, double *comp)
+{
+    long N = (long)H * W;
+    double *E = (double *)malloc(sizeof(double) * (size_t)N * (B > 0 ? B : 1));
+    int64_t *L = (int64_t *)malloc(sizeof(int64_t) * (B > 0 ? B : 1));
+    int64_t *Rk = (int64_t *)malloc(sizeof(int64_t) * (B > 0 ? B : 1));
+    int64_t *En = (int64_t *)malloc(sizeof(int64_t) * (B > 0 ? B : 1));
+    if (!E || !L || !Rk || !En) {
+        free(E);
+        free(L);
+        free(Rk);
+        free(En);
+        return -1;
+    }
+    for (long p = 0; p < N; p++)
+        raw[p] = 0.0;
+    for (int k = 0; k < d; k++) {
+        const uint8_t *qk = q + (long)k * N;
+        for (int b = 0; b < B; b++)
+            Rk[b] = (int64_t)R[(long)k * B + b];
+        /* per-bin errors of every window of component k */
+        for (int y = 0; y < H; y++)
+            for (int x = 0; x < W; x++) {
+                long Nloc = orc_window_hist(qk, H, W, B, r, y, x, L);
+                if (orc_alg1(L, Rk, B, Nloc, (int64_t)Nref, En) < 0)
+                    goto oom;
+                double *e = E + ((long)y * W + x) * B;
+                for (int b = 0; b < B; b++)
+                    e[b] = L[b] > 0 ? (double)En[b] / ((double)L[b] * (double)Nref) : 0.0;
+            }
+        /* association: each pixel averages its own bin's error over the windows that contain it */
+        for (int y = 0; y < H; y++)
+            for (int x = 0; x < W; x++) {
+                int bq = qk[(long)y * W + x];
+                double s = 0.0;
+                long n = 0;
+                for (int py = y - r; py <= y + r; py++)
+                    for (int px = x - r; px <= x + r; px++)
+                        if (py >= 0 && py < H && px >= 0 && px < W) {
+                            s += E[((long)py * W + px) * B + bq];
+                            n++;
+                        }
+                double a = s / (double)n;
+                if (comp)
+                    comp[(long)k * N + (long)y * W + x] = a;
+                raw[(long)y * W + x] += a;
+            }
+    }
+    for (long p = 0; p < N; p++)
+        raw[p] /= (double)d;
+    if (orc_blur(raw, H, W, sigma_s, score) < 0)
+        goto oom;
+    free(E);
+    free(L);
+    free(Rk);
+    free(En);
+    return 0;
+oom:
+    free(E);
+    free(L);
+    free(Rk);
+    free(En);
+    return -1;
+}
