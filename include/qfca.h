@@ -165,6 +165,52 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
                        int r, const uint32_t *ref_hist, uint32_t ref_total, float *score,
                        uint64_t *numer_out, void *stream);
 
+/* qfca_score_assoc -- the paper's own per-pixel scoring (Sec. 3.1):
+ *   1. Algorithm 1 for every window and component: the window histogram P
+ *      (clipped (2r+1)^2 window, N_loc pixels) is transported onto the
+ *      reference R at the common mass N_loc * N_ref by the two-pointer walk
+ *      over the bins; E_i = (mass moved out of bin i x bin distance) /
+ *      (P_i N_ref), in bin units (0 for empty bins);
+ *   2. the error-to-pixel association with sigma_p = infinity: pixel q of bin
+ *      b takes E_i[b] from every window that contains it and averages them
+ *      (a box average over the window centres within r of q);
+ *   3. the mean over the d components, then a Gaussian smoothing with
+ *      standard deviation sigma_s (separable, taps |t| <= ceil(4 sigma_s),
+ *      weights renormalised over the taps inside the image).
+ * The per-bin errors are rounded to a fixed point 2^-s (s <= 20, the largest
+ * with (2r+1)^2 (B-1) 2^s < 2^32) so the association sums are exact; the one
+ * rounding of each E_i is the only error before the final division.
+ *   bins       device u8 [d][H][pitch], pitch >= W; values >= B count as B-1.
+ *   ref_hist   device u32 [d][B]; every row sums to ref_total = N_ref.
+ *   sigma_s    0 <= sigma_s <= 4 (0: no smoothing; the paper uses 1).
+ *   score      device f32 [H][W].
+ *   raw_out    device f32 [H][W] or NULL: the map before smoothing.
+ *   comp_out   device f32 [d][H][W] or NULL: each component's associated
+ *              error (the map before the mean over components).
+ * Requires 1 <= r, 2 <= B <= 255, d <= 64, 2r <= 248 (B <= 32), 2r <= 120
+ * (B <= 128), 2r <= 56 (B <= 255), and a shared-memory plan (histograms and
+ * running sums for the window columns, (2r+1)^2 reciprocals) within 200 KB
+ * (r <= 31 always fits for B <= 64); QFCA_ERR_UNSUPPORTED otherwise. */
+qfca_status qfca_score_assoc(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pitch, int d, int B,
+                             int r, const uint32_t *ref_hist, uint32_t ref_total, float sigma_s,
+                             float *score, float *raw_out, float *comp_out, void *stream);
+
+/* One image of qfca_score_assoc_batch (fields as in qfca_score_assoc). */
+typedef struct {
+    const uint8_t *bins;       /* device u8 [d][H][pitch] */
+    int H, W, pitch, r;
+    const uint32_t *ref_hist;  /* device u32 [d][B] */
+    uint32_t ref_total;
+    float *score;              /* device f32 [H][W], written */
+    float *raw;                /* device f32 [H][W] or NULL */
+} qfca_assoc_image;
+
+/* qfca_score_assoc_batch -- qfca_score_assoc for n images (own sizes and
+ * radii, common d, B and sigma_s), each stage one launch per 64 images.
+ * Results equal n single-image calls.  Requires 1 <= n <= 4096. */
+qfca_status qfca_score_assoc_batch(qfca_ctx *ctx, const qfca_assoc_image *imgs, int n, int d, int B,
+                                   float sigma_s, void *stream);
+
 /* Synchronise the device and read-and-clear the context's device status
  * word.  Kernels whose bounded waits (on tensor-core completion, on a peer
  * stage) run out set a bit there and return early instead of hanging.

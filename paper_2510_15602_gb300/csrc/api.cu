@@ -483,6 +483,54 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
     return QFCA_OK;
 }
 
+static qfca_status run_assoc(qfca_ctx *ctx, const AssocJob *jobs, int n, int d, int B, cudaStream_t st) {
+    for (int i = 0; i < n; i++) {
+        const AssocJob &j = jobs[i];
+        if (!j.bins || !j.ref || !j.score) return fail(ctx, QFCA_ERR_INVALID_ARG, "image %d: NULL pointer", i);
+        if (j.H < 1 || j.W < 1) return fail(ctx, QFCA_ERR_INVALID_ARG, "image %d: bad H x W", i);
+        if (j.pitch < j.W) return fail(ctx, QFCA_ERR_INVALID_ARG, "image %d: pitch %d < W", i, j.pitch);
+        if (j.r < 1) return fail(ctx, QFCA_ERR_INVALID_ARG, "image %d: r = %d < 1", i, j.r);
+        if (j.Nref < 1) return fail(ctx, QFCA_ERR_INVALID_ARG, "image %d: ref_total must be >= 1", i);
+        if (!assoc_shape_ok(B, j.r))
+            return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d does not fit the association kernel", B, j.r);
+    }
+    if (d < 1 || d > kMaxD) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, %d]", d, kMaxD);
+    if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
+    if (!(jobs[0].sigma_s >= 0.0f && jobs[0].sigma_s <= 4.0f))
+        return fail(ctx, QFCA_ERR_INVALID_ARG, "sigma_s = %g outside [0, 4]", (double)jobs[0].sigma_s);
+    DeviceGuard g(ctx->device);
+    HookScope hs(ctx);
+    qfca_status s;
+    if ((s = ensure_ws(ctx, assoc_jobs_workspace_bytes(jobs, n, d), st))) return s;
+    const cudaError_t e = launch_assoc_jobs(jobs, n, d, B, ctx->ws, st);
+    if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "shape does not fit the association kernel");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_score_assoc");
+    return QFCA_OK;
+}
+
+qfca_status qfca_score_assoc(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pitch, int d, int B, int r,
+                             const uint32_t *ref_hist, uint32_t ref_total, float sigma_s, float *score,
+                             float *raw_out, float *comp_out, void *stream) {
+    qfca_status s = check_ctx(ctx);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const AssocJob job{bins, H, W, pitch, r, ref_hist, ref_total, sigma_s, score, raw_out, comp_out};
+    return run_assoc(ctx, &job, 1, d, B, (cudaStream_t)stream);
+}
+
+qfca_status qfca_score_assoc_batch(qfca_ctx *ctx, const qfca_assoc_image *imgs, int n, int d, int B,
+                                   float sigma_s, void *stream) {
+    qfca_status s = check_ctx(ctx);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!imgs || n < 1 || n > 4096) return fail(ctx, QFCA_ERR_INVALID_ARG, "n = %d outside [1, 4096]", n);
+    std::vector<AssocJob> jobs(n);
+    for (int i = 0; i < n; i++)
+        jobs[i] = AssocJob{imgs[i].bins, imgs[i].H, imgs[i].W, imgs[i].pitch, imgs[i].r, imgs[i].ref_hist,
+                           imgs[i].ref_total, sigma_s, imgs[i].score, imgs[i].raw, nullptr};
+    return run_assoc(ctx, jobs.data(), n, d, B, (cudaStream_t)stream);
+}
+
 qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int d, int B, int r,
                            int precision, float *scores, const qfca_batch_outputs *extra, void *stream) {
     qfca_status s = check_ctx(ctx);

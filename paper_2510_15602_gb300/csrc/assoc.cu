@@ -1,0 +1,460 @@
+// assoc.cu -- the paper's own per-pixel scoring (arXiv 2510.15602, Sec. 3.1):
+// Algorithm 1 per window and component, the error-to-pixel association, the
+// mean over components and the final Gaussian smoothing.
+//
+// For component k and window centre p (clipped (2r+1)^2 window, N_loc
+// pixels, histogram P), Algorithm 1 transports P onto the reference R at the
+// common mass N_loc N_ref (P'_i = P_i N_ref, R'_j = R_j N_loc) with two
+// pointers; the mass-weighted distance charged to bin i, Enum_i, is an exact
+// integer and E_i = Enum_i / P'_i.  A pixel q of bin b takes E_{k,p}[b] from
+// every window p that contains it and averages (sigma_p = infinity: a box
+// average over the window centres within r of q):
+//     raw(q) = (1/d) sum_k (1/n(q)) sum_{|p-q|_inf <= r} E_{k,p}[b_k(q)]
+// and score = Gaussian(sigma_s) * raw, renormalised at the border.
+//
+// k_assoc: one CTA = one component of one image x a strip of output columns,
+// all rows.  Thread c owns window column c (the strip plus r on each side);
+// it slides two window histograms down the image, packed in one u32 per bin
+// (low half: the leading window, centre row y + r; high half: the trailing
+// window, centre row y - r - 1, the same window 2r+1 rows later), and runs
+// Algorithm 1 on both.  The leading window adds its per-bin errors to a
+// running column sum V[b][c] (fixed point, 2^s), the trailing one subtracts
+// the identical values, so V holds the sum over the 2r+1 window rows around
+// the output row exactly.  Output pixel x then sums V[b(x)][c] over the 2r+1
+// window columns around it.  The per-component sums go to the workspace;
+// k_assoc_fin adds them over components (exact, u64) and divides once;
+// k_blur smooths.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace qfca {
+namespace {
+
+constexpr int kMaxTaps = 33;  // 2 ceil(4 sigma_s) + 1 for sigma_s <= 4
+
+struct AssocImgP {
+    const uint8_t *bins;   // [d][H][pitch]
+    int H, W, pitch, r;
+    int sw, nstrip;        // output columns per strip, strips
+    int shift;             // fixed-point scale 2^shift of the per-bin errors
+    long cta0;             // first CTA of this image
+    const uint32_t *ref;   // [d][B]
+    uint32_t Nref;
+    uint32_t *F;           // [d][H][W] per-component sums of fixed-point errors
+};
+
+struct AssocParams {
+    int n, d, B, nt;       // nt: threads per CTA (window columns)
+    AssocImgP img[kMaxBatch];
+};
+
+struct FinImg {
+    int H, W, r, shift;
+    long blk0;
+    const uint32_t *F;
+    float *raw, *comp;
+};
+
+struct AssocFinParams {
+    int n, d;
+    FinImg img[kMaxBatch];
+};
+
+struct BlurImg {
+    int H, W;
+    long blk0;
+    const float *in;
+    float *out;
+};
+
+struct BlurParams {
+    int n, R4, copy;
+    float w[kMaxTaps];
+    BlurImg img[kMaxBatch];
+};
+
+// Threads (window columns) per CTA for B bins: the histogram and the running
+// sums take (2B + 1) words per column.
+inline int max_cols(int B) { return B <= 32 ? 256 : (B <= 128 ? 128 : 64); }
+
+__host__ __device__ inline int ring_rows(int r) { return 4 * r + 4; }
+
+size_t assoc_smem(int nt, int B, int r) {
+    const int span = 2 * r + 1;
+    const int rw = (nt + 2 * r + 15) & ~15;
+    return sizeof(uint32_t) * ((size_t)(B + 1) * nt + (size_t)B * nt + B + span * span + 1) +
+           (size_t)ring_rows(r) * rw;
+}
+
+// Fixed-point scale: a window-column sum over 2r+1 rows and the output sum over
+// (2r+1)^2 windows of errors <= B-1 must stay below 2^32.
+int assoc_shift(int B, int r) {
+    const double span2 = (double)(2 * r + 1) * (2 * r + 1);
+    int s = (int)std::floor(std::log2(4294967295.0 / (span2 * (B - 1))));
+    return std::min(20, std::max(0, s));
+}
+
+template <typename ACC>
+__device__ __forceinline__ void alg1_column(const uint32_t *hist, int nt, int c, int B, int half, uint32_t Nloc,
+                                            uint32_t Nref, const uint32_t *ref, const float *recip, uint32_t *V,
+                                            bool add) {
+    // Algorithm 1 with P'_i = P_i N_ref and R'_j = R_j N_loc; the bin-i errors are
+    // flushed into V when bin i is used up (or empty).
+    int i = 0, j = 0;
+    uint32_t cnt = (hist[(size_t)1 * nt + c] >> half) & 0xffffu;
+    ACC pr = (ACC)cnt * Nref, rr = (ACC)ref[0] * Nloc, en = 0;
+    while (i < B && j < B) {
+        const ACC m = pr < rr ? pr : rr;
+        en += m * (ACC)(i > j ? i - j : j - i);
+        pr -= m;
+        rr -= m;
+        if (pr == 0) {
+            if (cnt) {
+                float e;
+                if (sizeof(ACC) == 4) e = __uint2float_rn((uint32_t)en) * recip[cnt];
+                else e = __ull2float_rn((unsigned long long)en) * recip[cnt];
+                const uint32_t fx = __float2uint_rn(e);
+                uint32_t *v = V + (size_t)i * nt + c;
+                *v = add ? *v + fx : *v - fx;
+            }
+            en = 0;
+            if (++i < B) {
+                cnt = (hist[(size_t)(i + 1) * nt + c] >> half) & 0xffffu;
+                pr = (ACC)cnt * Nref;
+            }
+        } else {
+            if (++j < B) rr = (ACC)ref[j] * Nloc;
+        }
+    }
+}
+
+template <typename ACC>
+__global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocParams p) {
+    const int B = p.B, nt = p.nt;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const long cta = blockIdx.x;
+    int ii = 0;
+    while (ii + 1 < p.n && p.img[ii + 1].cta0 <= cta) ii++;
+    const AssocImgP &im = p.img[ii];
+    const int H = im.H, W = im.W, r = im.r, span = 2 * r + 1;
+    long local = cta - im.cta0;
+    const int strip = (int)(local % im.nstrip), k = (int)(local / im.nstrip);
+    const int x0 = strip * im.sw;           // first output column
+    const int c0 = x0 - r;                  // image column of window column 0
+    const int px0 = x0 - 2 * r;             // image column of ring column 0
+    const int rw = (nt + 2 * r + 15) & ~15; // ring row width
+    const int RR = ring_rows(r);
+
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem_raw);  // [B+1][nt], row 0: outside pixels
+    uint32_t *V = hist + (size_t)(B + 1) * nt;                 // [B][nt]
+    uint32_t *ref = V + (size_t)B * nt;                        // [B]
+    float *recip = reinterpret_cast<float *>(ref + B);         // [span^2 + 1]: 2^s / (n N_ref)
+    uint8_t *ring = reinterpret_cast<uint8_t *>(recip + span * span + 1);  // [RR][rw]: bin+1, 0 outside
+
+    const int t = threadIdx.x;
+    const uint8_t *plane = im.bins + (size_t)k * H * im.pitch;
+    const uint32_t Nref = im.Nref;
+    for (int e = t; e < (B + 1) * nt + B * nt; e += nt) hist[e] = 0;  // hist and V
+    for (int b = t; b < B; b += nt) ref[b] = im.ref[(size_t)k * B + b];
+    const float scale = ldexpf(1.0f, im.shift);
+    for (int n = t; n <= span * span; n += nt) recip[n] = n ? scale / ((float)n * (float)Nref) : 0.0f;
+    auto load_row = [&](int yy) {
+        uint8_t *dst = ring + (size_t)(((yy % RR) + RR) % RR) * rw;
+        for (int col = t; col < rw; col += nt) {
+            const int x = px0 + col;
+            uint8_t v = 0;
+            if (yy >= 0 && yy < H && x >= 0 && x < W) v = (uint8_t)(min((int)plane[(size_t)yy * im.pitch + x], B - 1) + 1);
+            dst[col] = v;
+        }
+    };
+    // rows needed by the first step: y0 - 2r - 2 .. y0 + 2r with y0 = -2r
+    const int ys = -2 * r;
+    for (int yy = ys - 2 * r - 2; yy <= ys + 2 * r; yy++) load_row(yy);
+    __syncthreads();
+
+    const int c = c0 + t;                   // this thread's window column (image coordinates)
+    const bool col_ok = c >= 0 && c < W;
+    const int wx0 = max(0, c - r), wx1 = min(W - 1, c + r);
+    const uint32_t wcols = col_ok ? (uint32_t)(wx1 - wx0 + 1) : 0u;
+    const int sw_here = min(im.sw, W - x0);
+    uint32_t *Fk = im.F + (size_t)k * H * W;
+
+    for (int y = ys; y < H; y++) {
+        // ---- slide the two histograms: row y+2r enters the leading window,
+        // row y-1 leaves it and enters the trailing one, row y-2r-2 leaves the trailing one
+        {
+            const uint8_t *ra = ring + (size_t)((((y + 2 * r) % RR) + RR) % RR) * rw + t;
+            const uint8_t *rb = ring + (size_t)((((y - 1) % RR) + RR) % RR) * rw + t;
+            const uint8_t *rc = ring + (size_t)((((y - 2 * r - 2) % RR) + RR) % RR) * rw + t;
+#pragma unroll 4
+            for (int u = 0; u < span; u++) {
+                atomicAdd(&hist[(size_t)ra[u] * nt + t], 1u);
+                atomicAdd(&hist[(size_t)rb[u] * nt + t], 0xffffu);  // -1 low half, +1 high half
+                atomicAdd(&hist[(size_t)rc[u] * nt + t], 0xffff0000u);  // -1 high half
+            }
+        }
+        // ---- Algorithm 1 on the leading window (centre y+r) and the trailing one (centre y-r-1)
+        if (col_ok) {
+            const int a = y + r, bq = y - r - 1;
+            if (a >= 0 && a < H) {
+                const uint32_t Nloc = (uint32_t)(min(H - 1, a + r) - max(0, a - r) + 1) * wcols;
+                alg1_column<ACC>(hist, nt, t, B, 0, Nloc, Nref, ref, recip, V, true);
+            }
+            if (bq >= 0) {
+                const uint32_t Nloc = (uint32_t)(min(H - 1, bq + r) - max(0, bq - r) + 1) * wcols;
+                alg1_column<ACC>(hist, nt, t, B, 16, Nloc, Nref, ref, recip, V, false);
+            }
+        }
+        __syncthreads();
+        // ---- output row y: each pixel sums its own bin over the 2r+1 window columns around it
+        if (y >= 0 && t < sw_here) {
+            const int x = x0 + t;
+            const int b = (int)ring[(size_t)(y % RR) * rw + (x - px0)] - 1;
+            const uint32_t *vb = V + (size_t)b * nt + t;  // window columns x-r .. x+r are t .. t+2r
+            uint32_t s = 0;
+            for (int u = 0; u < span; u++) s += vb[u];
+            Fk[(size_t)y * W + x] = s;
+        }
+        if (y + 1 < H) load_row(y + 1 + 2 * r);
+        __syncthreads();
+    }
+}
+
+// raw(q) = sum_k F_k(q) / (d n(q) 2^s); comp_k(q) = F_k(q) / (n(q) 2^s) when asked.
+__global__ void __launch_bounds__(256) k_assoc_fin(const __grid_constant__ AssocFinParams p) {
+    const long blk = blockIdx.x;
+    int ii = 0;
+    while (ii + 1 < p.n && p.img[ii + 1].blk0 <= blk) ii++;
+    const FinImg &im = p.img[ii];
+    const long HW = (long)im.H * im.W;
+    const long q = (blk - im.blk0) * 256 + threadIdx.x;
+    if (q >= HW) return;
+    const int y = (int)(q / im.W), x = (int)(q % im.W);
+    const int r = im.r;
+    const double n = (double)(min(im.H - 1, y + r) - max(0, y - r) + 1) * (double)(min(im.W - 1, x + r) - max(0, x - r) + 1);
+    const double unit = n * ldexp(1.0, im.shift);
+    unsigned long long s = 0;
+    for (int k = 0; k < p.d; k++) {
+        const uint32_t f = im.F[(size_t)k * HW + q];
+        s += f;
+        if (im.comp) im.comp[(size_t)k * HW + q] = (float)((double)f / unit);
+    }
+    im.raw[q] = (float)((double)s / (unit * p.d));
+}
+
+// Separable Gaussian on a 32 x 32 tile with a halo of R4, weights renormalised
+// over the taps inside the image.
+__global__ void __launch_bounds__(256) k_blur(const __grid_constant__ BlurParams p) {
+    __shared__ float tile[32 + 2 * 16][32 + 2 * 16 + 1];
+    __shared__ float mid[32 + 2 * 16][33];
+    const long blk = blockIdx.x;
+    int ii = 0;
+    while (ii + 1 < p.n && p.img[ii + 1].blk0 <= blk) ii++;
+    const BlurImg &im = p.img[ii];
+    const int H = im.H, W = im.W, R4 = p.R4;
+    const int nbx = (W + 31) / 32;
+    const long local = blk - im.blk0;
+    const int tx0 = (int)(local % nbx) * 32, ty0 = (int)(local / nbx) * 32;
+    const int TW = 32 + 2 * R4;
+    for (int e = threadIdx.x; e < TW * TW; e += 256) {
+        const int yy = e / TW, xx = e % TW;
+        const int gy = ty0 - R4 + yy, gx = tx0 - R4 + xx;
+        tile[yy][xx] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? im.in[(size_t)gy * W + gx] : 0.0f;
+    }
+    __syncthreads();
+    if (p.copy) {
+        for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+            const int gy = ty0 + e / 32, gx = tx0 + e % 32;
+            if (gy < H && gx < W) im.out[(size_t)gy * W + gx] = tile[e / 32 + R4][e % 32 + R4];
+        }
+        return;
+    }
+    // horizontal pass over all tile rows (the halo rows too)
+    for (int e = threadIdx.x; e < TW * 32; e += 256) {
+        const int yy = e / 32, xo = e % 32;
+        const int gx = tx0 + xo;
+        float s = 0.0f, w = 0.0f;
+        for (int u = -R4; u <= R4; u++) {
+            if (gx + u < 0 || gx + u >= W) continue;
+            s = fmaf(p.w[u + R4], tile[yy][xo + R4 + u], s);
+            w += p.w[u + R4];
+        }
+        mid[yy][xo] = s / w;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+        const int yo = e / 32, xo = e % 32;
+        const int gy = ty0 + yo, gx = tx0 + xo;
+        if (gy >= H || gx >= W) continue;
+        float s = 0.0f, w = 0.0f;
+        for (int u = -R4; u <= R4; u++) {
+            if (gy + u < 0 || gy + u >= H) continue;
+            s = fmaf(p.w[u + R4], mid[yo + R4 + u][xo], s);
+            w += p.w[u + R4];
+        }
+        im.out[(size_t)gy * W + gx] = s / w;
+    }
+}
+
+int g_attr_dev_assoc = -1;
+
+}  // namespace
+
+bool assoc_shape_ok(int B, int r) {
+    const int nt = max_cols(B);
+    if (nt - 2 * r < 8) return false;
+    const int ntp = std::min(nt, 256);
+    return assoc_smem(ntp, B, r) <= 200 * 1024;
+}
+
+size_t assoc_jobs_workspace_bytes(const AssocJob *jobs, int n, int d) {
+    size_t b = 0;
+    for (int i = 0; i < n; i++) {
+        const size_t HW = (size_t)jobs[i].H * jobs[i].W;
+        b += align_up(sizeof(uint32_t) * HW * d, 256);
+        if (jobs[i].sigma_s > 0.0f || !jobs[i].raw) b += align_up(sizeof(float) * HW, 256);
+    }
+    return b;
+}
+
+cudaError_t launch_assoc_jobs(const AssocJob *jobs, int n, int d, int B, void *ws, cudaStream_t st) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int rmax = 0;
+    bool wide = false;
+    for (int i = 0; i < n; i++) {
+        rmax = std::max(rmax, jobs[i].r);
+        const double span2 = (double)(2 * jobs[i].r + 1) * (2 * jobs[i].r + 1);
+        if ((double)(B - 1) * span2 * jobs[i].Nref >= 4294967296.0) wide = true;
+        if (!(jobs[i].sigma_s <= 4.0f)) return cudaErrorInvalidValue;
+    }
+    if (!assoc_shape_ok(B, rmax)) return cudaErrorNotSupported;
+    const int ntmax = max_cols(B);
+    // threads per CTA: the widest strip any image needs, rounded to warps
+    int nt = 32;
+    std::vector<int> sw(n), ns(n);
+    for (int i = 0; i < n; i++) {
+        const int r = jobs[i].r, W = jobs[i].W;
+        const int cap = ntmax - 2 * r;
+        ns[i] = (W + cap - 1) / cap;
+        sw[i] = (W + ns[i] - 1) / ns[i];
+        nt = std::max(nt, (sw[i] + 2 * r + 31) & ~31);
+    }
+    nt = std::min(nt, ntmax);
+    const size_t smem = assoc_smem(nt, B, rmax);
+    if (g_attr_dev_assoc != dev) {
+        cudaFuncSetAttribute(k_assoc<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_assoc<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        g_attr_dev_assoc = dev;
+    }
+    // workspace carve: F per image, then the unblurred map where the caller gave none (or a blur follows)
+    std::vector<uint32_t *> F(n);
+    std::vector<float *> rawp(n);
+    unsigned char *w = static_cast<unsigned char *>(ws);
+    for (int i = 0; i < n; i++) {
+        const size_t HW = (size_t)jobs[i].H * jobs[i].W;
+        F[i] = reinterpret_cast<uint32_t *>(w);
+        w += align_up(sizeof(uint32_t) * HW * d, 256);
+    }
+    for (int i = 0; i < n; i++) {
+        const size_t HW = (size_t)jobs[i].H * jobs[i].W;
+        if (jobs[i].sigma_s > 0.0f || !jobs[i].raw) {
+            rawp[i] = reinterpret_cast<float *>(w);
+            w += align_up(sizeof(float) * HW, 256);
+        } else {
+            rawp[i] = jobs[i].raw;
+        }
+    }
+    for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
+        const int m = std::min(kMaxBatch, n - i0);
+        AssocParams ap{};
+        ap.n = m;
+        ap.d = d;
+        ap.B = B;
+        ap.nt = nt;
+        long ctas = 0;
+        for (int i = 0; i < m; i++) {
+            const AssocJob &j = jobs[i0 + i];
+            AssocImgP &q = ap.img[i];
+            q.bins = j.bins;
+            q.H = j.H;
+            q.W = j.W;
+            q.pitch = j.pitch;
+            q.r = j.r;
+            q.sw = sw[i0 + i];
+            q.nstrip = ns[i0 + i];
+            q.shift = assoc_shift(B, j.r);
+            q.cta0 = ctas;
+            q.ref = j.ref;
+            q.Nref = j.Nref;
+            q.F = F[i0 + i];
+            ctas += (long)q.nstrip * d;
+        }
+        if (wide) QFCA_LAUNCH("k_assoc", st, (k_assoc<unsigned long long><<<(unsigned)ctas, nt, smem, st>>>(ap)));
+        else QFCA_LAUNCH("k_assoc", st, (k_assoc<uint32_t><<<(unsigned)ctas, nt, smem, st>>>(ap)));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+
+        AssocFinParams fp{};
+        fp.n = m;
+        fp.d = d;
+        long blks = 0;
+        for (int i = 0; i < m; i++) {
+            const AssocJob &j = jobs[i0 + i];
+            FinImg &q = fp.img[i];
+            q.H = j.H;
+            q.W = j.W;
+            q.r = j.r;
+            q.shift = ap.img[i].shift;
+            q.blk0 = blks;
+            q.F = F[i0 + i];
+            q.raw = rawp[i0 + i];
+            q.comp = j.comp;
+            blks += ((long)j.H * j.W + 255) / 256;
+        }
+        QFCA_LAUNCH("k_assoc_fin", st, (k_assoc_fin<<<(unsigned)blks, 256, 0, st>>>(fp)));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+        // smoothing (or a copy into the caller's raw map / the score); images of one launch share sigma_s
+        for (int i = 0; i < m;) {
+            const float sg = jobs[i0 + i].sigma_s;
+            int i1 = i + 1;
+            while (i1 < m && jobs[i0 + i1].sigma_s == sg) i1++;
+            BlurParams bp{};
+            bp.n = i1 - i;
+            bp.copy = sg > 0.0f ? 0 : 1;
+            bp.R4 = sg > 0.0f ? (int)std::ceil(4.0 * sg) : 0;
+            for (int u = -bp.R4; u <= bp.R4; u++) bp.w[u + bp.R4] = (float)std::exp(-(double)u * u / (2.0 * sg * sg));
+            long bb = 0;
+            for (int q = i; q < i1; q++) {
+                const AssocJob &j = jobs[i0 + q];
+                BlurImg &b = bp.img[q - i];
+                b.H = j.H;
+                b.W = j.W;
+                b.blk0 = bb;
+                b.in = rawp[i0 + q];
+                b.out = j.score;
+                bb += (long)((j.W + 31) / 32) * ((j.H + 31) / 32);
+            }
+            QFCA_LAUNCH("k_blur", st, (k_blur<<<(unsigned)bb, 256, 0, st>>>(bp)));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (sg > 0.0f)
+                for (int q = i; q < i1; q++)
+                    if (jobs[i0 + q].raw)
+                        if ((e = cudaMemcpyAsync(jobs[i0 + q].raw, rawp[i0 + q],
+                                                 sizeof(float) * jobs[i0 + q].H * jobs[i0 + q].W,
+                                                 cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+                            return e;
+            i = i1;
+        }
+    }
+    return cudaSuccess;
+}
+
+}  // namespace qfca

@@ -159,6 +159,27 @@ bool score_shape_ok(int B, int r);
 cudaError_t launch_score_jobs(const ScoreJob *jobs, int n, int d, int B, void *ws, bool ws_accumulates, int *status,
                               cudaStream_t st, const ScoreTiling *tiling, ScoreTiling *chosen);
 
+// One image of the paper's scoring (assoc.cu): bins [d][H][pitch], reference
+// [d][B] with N_ref = Nref, window radius r, final smoothing sigma_s (<= 0:
+// none, at most 4); score [H][W]; raw [H][W] (before smoothing) and comp
+// [d][H][W] (per-component associated errors) optional.
+struct AssocJob {
+    const uint8_t *bins;
+    int H, W, pitch, r;
+    const uint32_t *ref;
+    uint32_t Nref;
+    float sigma_s;
+    float *score, *raw, *comp;
+};
+
+// True when B bins and radius r fit the association kernel.
+bool assoc_shape_ok(int B, int r);
+size_t assoc_jobs_workspace_bytes(const AssocJob *jobs, int n, int d);
+// Algorithm 1 + association + mean + smoothing for n images.  Returns
+// cudaErrorNotSupported (nothing enqueued) when the shape does not fit and
+// cudaErrorInvalidValue for sigma_s > 4.
+cudaError_t launch_assoc_jobs(const AssocJob *jobs, int n, int d, int B, void *ws, cudaStream_t st);
+
 // ------------------------------------------------------------------ context access (api.cu) for serve.cu
 
 struct ServeState;

@@ -94,6 +94,18 @@ class Image(ctypes.Structure):
 
 _lib.qfca_score_batch.argtypes = [_P, ctypes.POINTER(Image), _I, _I, _I, _I, _I, _I, _P]
 _lib.qfca_score_batch.restype = _I
+_lib.qfca_score_assoc.argtypes = [_P, _P, _I, _I, _I, _I, _I, _I, _P, ctypes.c_uint32, ctypes.c_float, _P, _P, _P, _P]
+_lib.qfca_score_assoc.restype = _I
+
+
+class AssocImage(ctypes.Structure):
+    _fields_ = [("bins", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int), ("pitch", ctypes.c_int),
+                ("r", ctypes.c_int), ("ref_hist", ctypes.c_void_p), ("ref_total", ctypes.c_uint32),
+                ("score", ctypes.c_void_p), ("raw", ctypes.c_void_p)]
+
+
+_lib.qfca_score_assoc_batch.argtypes = [_P, ctypes.POINTER(AssocImage), _I, _I, _I, ctypes.c_float, _P]
+_lib.qfca_score_assoc_batch.restype = _I
 _lib.qfca_set_autotune.argtypes = [_P, _I]
 _lib.qfca_set_autotune.restype = _I
 _lib.qfca_last_tiling.argtypes = [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]
@@ -337,6 +349,49 @@ def score(bins: torch.Tensor, W: int, B: int, r: int, ref_hist: torch.Tensor, re
     ctx.check(_lib.qfca_score(ctx.handle, _ptr(bins), H, W, pitch, d, B, r, _ptr(ref_hist), int(ref_total),
                               _ptr(s), _ptr(numer), _P(_stream_ptr(stream))))
     return (s, numer) if want_numer else s
+
+
+def score_assoc(bins: torch.Tensor, W: int, B: int, r: int, ref_hist: torch.Tensor, ref_total: int,
+                sigma_s: float = 1.0, want_raw: bool = False, want_comp: bool = False, ctx: Context | None = None,
+                stream=None, out=None):
+    """qfca_score_assoc: the paper's scoring (Algorithm 1, error-to-pixel association,
+    component mean, Gaussian smoothing) -> f32 [H, W] score map; with want_raw /
+    want_comp also the map before smoothing [H, W] and the per-component maps [d, H, W]."""
+    _check_dev(bins, "bins", torch.uint8)
+    if ref_hist.dtype not in (torch.int32, torch.uint32) or not ref_hist.is_cuda:
+        raise ValueError("ref_hist must be a CUDA int32/uint32 tensor")
+    d, H, pitch = bins.shape
+    ctx = ctx or default_context(bins.device.index)
+    s = torch.empty(H, W, dtype=torch.float32, device=bins.device) if out is None else out
+    raw = torch.empty(H, W, dtype=torch.float32, device=bins.device) if want_raw else None
+    comp = torch.empty(d, H, W, dtype=torch.float32, device=bins.device) if want_comp else None
+    ctx.check(_lib.qfca_score_assoc(ctx.handle, _ptr(bins), H, W, pitch, d, B, r, _ptr(ref_hist), int(ref_total),
+                                    float(sigma_s), _ptr(s), _ptr(raw), _ptr(comp), _P(_stream_ptr(stream))))
+    if not (want_raw or want_comp):
+        return s
+    return (s,) + ((raw,) if want_raw else ()) + ((comp,) if want_comp else ())
+
+
+def score_assoc_batch(bins_list, Ws, rs, B: int, refs, ref_totals, sigma_s: float = 1.0,
+                      ctx: Context | None = None, stream=None, scores=None):
+    """qfca_score_assoc_batch: qfca_score_assoc for several images (bins [d, H_i, pitch_i])
+    in one launch per stage.  Returns the list of score maps [H_i, W_i]."""
+    n = len(bins_list)
+    if not (n == len(Ws) == len(rs) == len(refs) == len(ref_totals)) or n == 0:
+        raise ValueError("one width, radius, reference and total per image")
+    ctx = ctx or default_context(bins_list[0].device.index)
+    d = int(bins_list[0].shape[0])
+    if scores is None:
+        scores = [torch.empty(int(b.shape[1]), int(w), dtype=torch.float32, device=b.device)
+                  for b, w in zip(bins_list, Ws)]
+    arr = (AssocImage * n)()
+    for i, (b, w, r, R, nt, sc) in enumerate(zip(bins_list, Ws, rs, refs, ref_totals, scores)):
+        _check_dev(b, f"bins_list[{i}]", torch.uint8)
+        if int(b.shape[0]) != d:
+            raise ValueError("every image needs the same number of components")
+        arr[i] = AssocImage(_ptr(b), int(b.shape[1]), int(w), int(b.shape[2]), int(r), _ptr(R), int(nt), _ptr(sc), None)
+    ctx.check(_lib.qfca_score_assoc_batch(ctx.handle, arr, n, d, B, float(sigma_s), _P(_stream_ptr(stream))))
+    return scores
 
 
 def batch_run(X: torch.Tensor, d: int, B: int, r: int, precision="bf16", ctx: Context | None = None, stream=None,
