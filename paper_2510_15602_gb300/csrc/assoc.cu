@@ -16,8 +16,10 @@
 // all rows.  Thread c owns window column c (the strip plus r on each side);
 // it slides two window histograms down the image, packed in one u32 per bin
 // (low half: the leading window, centre row y + r; high half: the trailing
-// window, centre row y - r - 1, the same window 2r+1 rows later), and runs
-// Algorithm 1 on both.  The leading window adds its per-bin errors to a
+// window, centre row y - r - 1, the same window 2r+1 rows later), and forms
+// Algorithm 1's per-bin integers for both in one pass over the bins (a closed
+// form of the walk from prefix-sum tables of the reference for B <= 64, the
+// two-pointer walk itself above).  The leading window adds its per-bin errors to a
 // running column sum V[b][c] (fixed point, 2^s), the trailing one subtracts
 // the identical values, so V holds the sum over the 2r+1 window rows around
 // the output row exactly.  Output pixel x then sums V[b(x)][c] over the 2r+1
@@ -85,11 +87,17 @@ inline int max_cols(int B) { return B <= 32 ? 256 : (B <= 128 ? 128 : 64); }
 
 __host__ __device__ inline int ring_rows(int r) { return 4 * r + 4; }
 
-size_t assoc_smem(int nt, int B, int r) {
+// Closed-form per-bin errors (tables of B (B+1) prefix sums) up to this many bins;
+// above it the two-pointer walk itself runs.
+constexpr int kClosedMaxB = 64;
+
+size_t assoc_smem(int nt, int B, int r, bool wide) {
     const int span = 2 * r + 1;
     const int rw = (nt + 2 * r + 15) & ~15;
-    return sizeof(uint32_t) * ((size_t)(B + 1) * nt + (size_t)B * nt + B + span * span + 1) +
-           (size_t)ring_rows(r) * rw;
+    size_t tab = sizeof(uint32_t) * (B + 1);  // reference (walk) or its exclusive prefix (closed form)
+    if (B <= kClosedMaxB) tab += align_up((wide ? 8 : 4) * (size_t)B * (B + 1), 16) + align_up((size_t)span * span + 1, 16);
+    return sizeof(uint32_t) * ((size_t)(B + 1) * nt + (size_t)B * nt) + align_up(tab, 16) +
+           sizeof(float) * (span * span + 1) + (size_t)ring_rows(r) * rw + 64;
 }
 
 // Fixed-point scale: a window-column sum over 2r+1 rows and the output sum over
@@ -134,7 +142,92 @@ __device__ __forceinline__ void alg1_column(const uint32_t *hist, int nt, int c,
     }
 }
 
+// J(t) = max{x in [0, B-1] : N_loc cumRx[x] <= t}: the reference bin at
+// position t of the common mass axis (any bin whose closed interval holds t
+// serves, the transport integral being continuous).
 template <typename ACC>
+__device__ __forceinline__ int ref_bin_at(const uint32_t *cumRx, int B, uint32_t Nloc, ACC t) {
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((ACC)Nloc * cumRx[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Algorithm 1's per-bin integers in closed form.  The mass of window bin i
+// occupies [a, b) = [N_ref cumP_{i-1}, N_ref cumP_i) of the common mass axis;
+// the walk moves each unit at t to reference bin J(t), so
+//   Enum_i = F_i(b) - F_i(a),  F_i(t) = int_0^t |i - J(s)| ds
+//          = N_loc T[i][J] + |i - J| (t - N_loc cumRx[J]),  J = J(t),
+// with T[i][x] = sum_{j<x} |i - j| R_j and cumRx[x] = sum_{j<x} R_j: the same
+// integers as the two-pointer walk.  Each boundary's J comes from Jtab (J at
+// N_ref m for the interior window size) or a binary search; consecutive bins
+// share a boundary.
+// One window's running state in the closed form: cumulative count so far, the
+// reference bin J(a) at the current boundary a = N_ref cumP, the window size
+// and its boundary table (NULL: binary search).
+template <typename ACC>
+struct Walk {
+    uint32_t cumP, Nloc;
+    int Ja;
+    ACC a;
+    const uint8_t *Jtab;
+};
+
+// Fixed-point error of window bin i (count cnt): when the bin's mass lies in a
+// single reference bin J the error is exactly |i - J|; otherwise
+// E_i = (F_i(b) - F_i(a)) / (cnt N_ref) with the closed form above.
+template <typename ACC>
+__device__ __forceinline__ uint32_t bin_error(Walk<ACC> &w, int i, uint32_t cnt, int B, uint32_t Nref, int shift,
+                                              const uint32_t *cumRx, const ACC *Trow, const float *recip) {
+    w.cumP += cnt;
+    const ACC b = (ACC)Nref * w.cumP;
+    const int Jb = w.Jtab ? (int)w.Jtab[w.cumP] : ref_bin_at<ACC>(cumRx, B, w.Nloc, b);
+    uint32_t fx;
+    if (Jb == w.Ja) {
+        fx = (uint32_t)(i > Jb ? i - Jb : Jb - i) << shift;
+    } else {
+        const int Ja = w.Ja;
+        const ACC Fa = (ACC)w.Nloc * Trow[Ja] + (ACC)(i > Ja ? i - Ja : Ja - i) * (w.a - (ACC)w.Nloc * cumRx[Ja]);
+        const ACC Fb = (ACC)w.Nloc * Trow[Jb] + (ACC)(i > Jb ? i - Jb : Jb - i) * (b - (ACC)w.Nloc * cumRx[Jb]);
+        const ACC en = Fb - Fa;
+        float e;
+        if (sizeof(ACC) == 4) e = __uint2float_rn((uint32_t)en) * recip[cnt];
+        else e = __ull2float_rn((unsigned long long)en) * recip[cnt];
+        fx = __float2uint_rn(e);
+    }
+    w.Ja = Jb;
+    w.a = b;
+    return fx;
+}
+
+// Both windows of a window column in one pass over the bins (one load of the
+// packed counts per bin): V[i] += E_lead,i - E_trail,i.
+template <typename ACC>
+__device__ __forceinline__ void alg1_pair(const uint32_t *hist, int nt, int c, int B, bool lead_on, bool trail_on,
+                                          uint32_t Nl, uint32_t Nt, uint32_t Nint, uint32_t Nref, int shift,
+                                          const uint32_t *cumRx, const ACC *T, const uint8_t *Jtab,
+                                          const float *recip, uint32_t *V) {
+    Walk<ACC> wl{0u, Nl, 0, (ACC)0, Nl == Nint ? Jtab : nullptr};
+    Walk<ACC> wt{0u, Nt, 0, (ACC)0, Nt == Nint ? Jtab : nullptr};
+    const uint32_t ml = lead_on ? 0xffffu : 0u, mt = trail_on ? 0xffffu : 0u;
+    const uint32_t *h = hist + nt + c;
+    uint32_t *v = V + c;
+    for (int i = 0; i < B; i++, h += nt, v += nt) {
+        const uint32_t word = *h;
+        const uint32_t cl = word & ml, ct = (word >> 16) & mt;
+        if (!(cl | ct)) continue;
+        const ACC *Trow = T + (size_t)i * (B + 1);
+        uint32_t delta = 0;
+        if (cl) delta += bin_error<ACC>(wl, i, cl, B, Nref, shift, cumRx, Trow, recip);
+        if (ct) delta -= bin_error<ACC>(wt, i, ct, B, Nref, shift, cumRx, Trow, recip);
+        *v += delta;
+    }
+}
+
+template <typename ACC, bool CLOSED>
 __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocParams p) {
     const int B = p.B, nt = p.nt;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -153,15 +246,45 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
 
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem_raw);  // [B+1][nt], row 0: outside pixels
     uint32_t *V = hist + (size_t)(B + 1) * nt;                 // [B][nt]
-    uint32_t *ref = V + (size_t)B * nt;                        // [B]
-    float *recip = reinterpret_cast<float *>(ref + B);         // [span^2 + 1]: 2^s / (n N_ref)
+    uint32_t *ref = V + (size_t)B * nt;                        // [B+1]: R_j (walk) or cumRx[x] (closed form)
+    unsigned char *tp = reinterpret_cast<unsigned char *>(ref + B + 1);
+    ACC *T = nullptr;
+    uint8_t *Jtab = nullptr;
+    if (CLOSED) {
+        tp = reinterpret_cast<unsigned char *>(((uintptr_t)tp + 15) & ~(uintptr_t)15);
+        T = reinterpret_cast<ACC *>(tp);                       // [B][B+1]
+        Jtab = reinterpret_cast<uint8_t *>(T + (size_t)B * (B + 1));  // [span^2 + 1]
+        tp = Jtab + ((span * span + 1 + 15) & ~15);
+    }
+    float *recip = reinterpret_cast<float *>(((uintptr_t)tp + 15) & ~(uintptr_t)15);  // [span^2 + 1]: 2^s / (n N_ref)
     uint8_t *ring = reinterpret_cast<uint8_t *>(recip + span * span + 1);  // [RR][rw]: bin+1, 0 outside
 
     const int t = threadIdx.x;
     const uint8_t *plane = im.bins + (size_t)k * H * im.pitch;
     const uint32_t Nref = im.Nref;
+    const uint32_t *Rk = im.ref + (size_t)k * B;
     for (int e = t; e < (B + 1) * nt + B * nt; e += nt) hist[e] = 0;  // hist and V
-    for (int b = t; b < B; b += nt) ref[b] = im.ref[(size_t)k * B + b];
+    if (CLOSED) {
+        if (t == 0) {
+            uint32_t acc = 0;
+            for (int x = 0; x <= B; x++) {
+                ref[x] = acc;
+                if (x < B) acc += Rk[x];
+            }
+        }
+        for (int i = t; i < B; i += nt) {
+            ACC acc = 0;
+            for (int x = 0; x <= B; x++) {
+                T[i * (B + 1) + x] = acc;
+                if (x < B) acc += (ACC)(i > x ? i - x : x - i) * Rk[x];
+            }
+        }
+        __syncthreads();
+        const uint32_t Nint = (uint32_t)(span * span);
+        for (int m = t; m <= span * span; m += nt) Jtab[m] = (uint8_t)ref_bin_at<ACC>(ref, B, Nint, (ACC)Nref * (uint32_t)m);
+    } else {
+        for (int b = t; b < B; b += nt) ref[b] = Rk[b];
+    }
     const float scale = ldexpf(1.0f, im.shift);
     for (int n = t; n <= span * span; n += nt) recip[n] = n ? scale / ((float)n * (float)Nref) : 0.0f;
     auto load_row = [&](int yy) {
@@ -186,6 +309,16 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
     uint32_t *Fk = im.F + (size_t)k * H * W;
 
     for (int y = ys; y < H; y++) {
+        // ---- the bins of row y+2r+1 (needed next step) are fetched now and stored
+        // after the window work, so their latency hides behind it
+        const int yn = y + 1 + 2 * r;
+        uint8_t pf[3];
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const int col = t + q * nt, x = px0 + col;
+            pf[q] = 0;
+            if (col < rw && yn < H && x >= 0 && x < W) pf[q] = (uint8_t)(min((int)plane[(size_t)yn * im.pitch + x], B - 1) + 1);
+        }
         // ---- slide the two histograms: row y+2r enters the leading window,
         // row y-1 leaves it and enters the trailing one, row y-2r-2 leaves the trailing one
         {
@@ -200,7 +333,15 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
             }
         }
         // ---- Algorithm 1 on the leading window (centre y+r) and the trailing one (centre y-r-1)
-        if (col_ok) {
+        if (CLOSED && col_ok) {
+            const int a = y + r, bq = y - r - 1;
+            const bool lead_on = a >= 0 && a < H, trail_on = bq >= 0;
+            const uint32_t Nl = lead_on ? (uint32_t)(min(H - 1, a + r) - max(0, a - r) + 1) * wcols : 0u;
+            const uint32_t Ntr = trail_on ? (uint32_t)(min(H - 1, bq + r) - max(0, bq - r) + 1) * wcols : 0u;
+            if (lead_on || trail_on)
+                alg1_pair<ACC>(hist, nt, t, B, lead_on, trail_on, Nl, Ntr, (uint32_t)(span * span), Nref, im.shift,
+                               ref, T, Jtab, recip, V);
+        } else if (col_ok) {
             const int a = y + r, bq = y - r - 1;
             if (a >= 0 && a < H) {
                 const uint32_t Nloc = (uint32_t)(min(H - 1, a + r) - max(0, a - r) + 1) * wcols;
@@ -210,6 +351,12 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
                 const uint32_t Nloc = (uint32_t)(min(H - 1, bq + r) - max(0, bq - r) + 1) * wcols;
                 alg1_column<ACC>(hist, nt, t, B, 16, Nloc, Nref, ref, recip, V, false);
             }
+        }
+        {
+            uint8_t *dst = ring + (size_t)(yn % RR) * rw;  // the slot of row y-2r-3, read by no one this step
+#pragma unroll
+            for (int q = 0; q < 3; q++)
+                if (t + q * nt < rw) dst[t + q * nt] = pf[q];
         }
         __syncthreads();
         // ---- output row y: each pixel sums its own bin over the 2r+1 window columns around it
@@ -221,7 +368,6 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
             for (int u = 0; u < span; u++) s += vb[u];
             Fk[(size_t)y * W + x] = s;
         }
-        if (y + 1 < H) load_row(y + 1 + 2 * r);
         __syncthreads();
     }
 }
@@ -309,8 +455,7 @@ int g_attr_dev_assoc = -1;
 bool assoc_shape_ok(int B, int r) {
     const int nt = max_cols(B);
     if (nt - 2 * r < 8) return false;
-    const int ntp = std::min(nt, 256);
-    return assoc_smem(ntp, B, r) <= 200 * 1024;
+    return assoc_smem(nt, B, r, true) <= 200 * 1024;
 }
 
 size_t assoc_jobs_workspace_bytes(const AssocJob *jobs, int n, int d) {
@@ -347,10 +492,13 @@ cudaError_t launch_assoc_jobs(const AssocJob *jobs, int n, int d, int B, void *w
         nt = std::max(nt, (sw[i] + 2 * r + 31) & ~31);
     }
     nt = std::min(nt, ntmax);
-    const size_t smem = assoc_smem(nt, B, rmax);
+    const size_t smem = assoc_smem(nt, B, rmax, wide);
+    const bool closed = B <= kClosedMaxB;
     if (g_attr_dev_assoc != dev) {
-        cudaFuncSetAttribute(k_assoc<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_assoc<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_assoc<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_assoc<unsigned long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_assoc<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_assoc<unsigned long long, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         g_attr_dev_assoc = dev;
     }
     // workspace carve: F per image, then the unblurred map where the caller gave none (or a blur follows)
@@ -396,8 +544,10 @@ cudaError_t launch_assoc_jobs(const AssocJob *jobs, int n, int d, int B, void *w
             q.F = F[i0 + i];
             ctas += (long)q.nstrip * d;
         }
-        if (wide) QFCA_LAUNCH("k_assoc", st, (k_assoc<unsigned long long><<<(unsigned)ctas, nt, smem, st>>>(ap)));
-        else QFCA_LAUNCH("k_assoc", st, (k_assoc<uint32_t><<<(unsigned)ctas, nt, smem, st>>>(ap)));
+        if (wide && closed) QFCA_LAUNCH("k_assoc", st, (k_assoc<unsigned long long, true><<<(unsigned)ctas, nt, smem, st>>>(ap)));
+        else if (closed) QFCA_LAUNCH("k_assoc", st, (k_assoc<uint32_t, true><<<(unsigned)ctas, nt, smem, st>>>(ap)));
+        else if (wide) QFCA_LAUNCH("k_assoc", st, (k_assoc<unsigned long long, false><<<(unsigned)ctas, nt, smem, st>>>(ap)));
+        else QFCA_LAUNCH("k_assoc", st, (k_assoc<uint32_t, false><<<(unsigned)ctas, nt, smem, st>>>(ap)));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
 
