@@ -239,6 +239,17 @@ def kernel_work(name: str, H: int, W: int, C: int, d: int, B: int, r: int, nimg:
         ops = 2 * (2 * r + 1) + 4 * (B - 1)
         return {"bound": "alu", "unit": "Tops", "work": nimg * N * d * ops, "peak_key": "int32_tops",
                 "per_unit": f"{ops} int ops per (pixel, component): 2(2r+1) window updates + 4(B-1) CDF-walk ops"}
+    if name.startswith("k_assoc_fin"):
+        return {"bound": "hbm", "unit": "GB/s", "work": nimg * N * (4 * d + 4), "peak_key": "hbm",
+                "per_unit": "4d + 4 bytes per pixel"}
+    if name.startswith("k_assoc"):
+        ops = 3 * (2 * r + 1) + 4 * (2 * B - 1) + 2 * B
+        return {"bound": "alu", "unit": "Tops", "work": nimg * N * d * ops, "peak_key": "int32_tops",
+                "per_unit": f"{ops} int ops per (pixel, component): 2(2r+1) window updates + 4(2B-1) for "
+                            "Algorithm 1's at most 2B-1 steps + 2B running-sum updates + (2r+1) association adds"}
+    if name.startswith("k_blur"):
+        return {"bound": "hbm", "unit": "GB/s", "work": nimg * N * 8, "peak_key": "hbm",
+                "per_unit": "8 bytes per pixel"}
     if name.startswith("k_finalize"):
         return {"bound": "hbm", "unit": "GB/s", "work": nimg * N * (4 * d + 4), "peak_key": "hbm",
                 "per_unit": "4d + 4 bytes per pixel"}
@@ -252,6 +263,8 @@ def kernel_work(name: str, H: int, W: int, C: int, d: int, B: int, r: int, nimg:
 # captures summarised in profiles/<kernel>_batch16_256_c256.md; an entry is
 # removed whenever its kernel changes after the capture.
 NCU_TRAFFIC = {
+    "k_eig_ff": 4851456,
+    "k_assoc": 33908480 + 75129856,
     "k_project_tma": 1074424000 + 125305600,
     "k_window_emd": 33648384 + 73858816,
     "k_quantize": 134446336 + 19018240,
@@ -529,6 +542,45 @@ def run_serving(qfca, torch, fields, classes, args):
         srv.stop()
 
 
+def run_paper_scoring(qfca, torch, pipe, masks, args):
+    """The paper's own scoring (Algorithm 1, error-to-pixel association, component
+    mean, sigma_s = 1 smoothing) on the batch's bins and references, one launch
+    per stage for the 16 images, CUDA-event timed on its stream."""
+    import numpy as np
+    from paper_2510_15602_gb300.metrics import auroc
+    ctx = qfca.Context()  # its own workspace: the pipes' captured graphs keep theirs
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        _, ex = qfca.batch_run(pipe.X[0], D, B, R, args.precision, ctx=ctx, stream=st, extras=True)
+    st.synchronize()
+    bl = [ex["bins"][i] for i in range(N_IMG)]
+    refs = [ex["ref_hist"][i] for i in range(N_IMG)]
+    outs = [torch.empty(HW, HW, dtype=torch.float32, device="cuda") for _ in range(N_IMG)]
+
+    def step(_i):
+        qfca.score_assoc_batch(bl, [HW] * N_IMG, [R] * N_IMG, B, refs, [HW * HW] * N_IMG, sigma_s=1.0, ctx=ctx,
+                               stream=st, scores=outs)
+
+    for i in range(3):
+        step(i)
+    st.synchronize()
+    ctx.trace_start("")
+    step(0)
+    st.synchronize()
+    tr = {k: list(v) for k, v in ctx.trace().items()}
+    ctx.trace_stop()
+    n = max(2, args.steps // 2)
+    dev_s, _ = timed(torch, st, step, n)
+    a = [auroc(outs[i].cpu().numpy(), masks[i]) for i in range(N_IMG)]
+    peaks = measured_peaks()
+    roof = roofline_entry("k_assoc", tr["k_assoc"][0], tr["k_assoc"][1], peaks, HW, HW, C, D, B, R, nimg=N_IMG)
+    return {"value": round(N_IMG * n / dev_s, 3), "unit": "maps/s", "ms_per_batch": round(1e3 * dev_s / n, 3),
+            "path": "qfca_score_assoc_batch on the batch's bins and global references (sigma_s = 1), "
+                    "one launch per stage for the 16 images",
+            "kernel_ms_per_batch": {k: round(v[0], 3) for k, v in sorted(tr.items(), key=lambda kv: -kv[1][0])},
+            "roofline": roof, "auroc_mean": round(float(np.nanmean(a)), 5)}
+
+
 def run_ours(args):
     ws, rank, local = dist_env()
     indices = shard_indices(rank, ws, N_IMG)
@@ -686,6 +738,7 @@ def run_ours(args):
                "sample": "image 0 of the batch: fit + project + quantize + window EMD, FP64, single thread"}
         auroc_oracle = auroc(ref["score"], masks[0])
 
+    paper = run_paper_scoring(qfca, torch, pipe, masks, args) if extra and not args.skip_paper else None
     uneven = run_uneven(qfca, torch, host_uneven, args) if host_uneven is not None else None
     serving = run_serving(qfca, torch, serve_fields, serve_classes, args) if serve_fields is not None else None
 
@@ -715,6 +768,7 @@ def run_ours(args):
                       "oracle_image0": None if auroc_oracle is None else round(auroc_oracle, 5),
                       "delta_image0": None if auroc_oracle is None else round(abs(aurocs[0] - auroc_oracle), 6)},
             "kernel_ms_per_step": {k: round(v[0], 3) for k, v in sorted(agg.items(), key=lambda kv: -kv[1][0])},
+            "paper_scoring": paper,
             "uneven_batch": uneven,
             "serving": serving,
             "wall_s_timed": round(wall_s, 3),
@@ -738,6 +792,13 @@ def run_profile_batch(args):
     scores = torch.empty(N_IMG, HW, HW, dtype=torch.float32, device="cuda")
     for _ in range(args.profile_batch):
         qfca.batch_run(X, D, B, R, args.precision, ctx=ctx, scores=scores)
+    if args.profile_paper:
+        # then the paper's scoring on the batch's bins, `args.profile_paper` calls
+        _, ex = qfca.batch_run(X, D, B, R, args.precision, ctx=ctx, scores=scores, extras=True)
+        bl = [ex["bins"][i] for i in range(N_IMG)]
+        refs = [ex["ref_hist"][i] for i in range(N_IMG)]
+        for _ in range(args.profile_paper):
+            qfca.score_assoc_batch(bl, [HW] * N_IMG, [R] * N_IMG, B, refs, [HW * HW] * N_IMG, sigma_s=1.0, ctx=ctx)
     torch.cuda.synchronize()
     return 0 if ctx.device_status() == 0 else 1
 
@@ -755,6 +816,9 @@ def main(argv=None):
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-uneven", action="store_true", help="skip the 64-image uneven batch measurement")
     ap.add_argument("--skip-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--skip-paper", action="store_true", help="skip the paper-scoring (Algorithm 1) measurement")
+    ap.add_argument("--profile-paper", type=int, default=0,
+                    help="profiling mode: after --profile-batch calls, N calls of the paper's scoring on the batch")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="only run this many batches through qfca_batch_run (for profilers), then exit")
     ap.add_argument("--traffic", type=float, default=None,
@@ -764,7 +828,7 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
-    if args.profile_batch:
+    if args.profile_batch or args.profile_paper:
         return run_profile_batch(args)
     return run_ours(args)
 
