@@ -571,14 +571,18 @@ def run_paper_scoring(qfca, torch, pipe, masks, args):
     ctx.trace_stop()
     n = max(2, args.steps // 2)
     dev_s, _ = timed(torch, st, step, n)
-    a = [auroc(outs[i].cpu().numpy(), masks[i]) for i in range(N_IMG)]
+    maps = [outs[i].cpu().numpy() for i in range(N_IMG)]
+    a = [auroc(maps[i], masks[i]) for i in range(N_IMG)]
+    from paper_2510_15602_gb300.metrics import aupro, f1_max
     peaks = measured_peaks()
     roof = roofline_entry("k_assoc", tr["k_assoc"][0], tr["k_assoc"][1], peaks, HW, HW, C, D, B, R, nimg=N_IMG)
     return {"value": round(N_IMG * n / dev_s, 3), "unit": "maps/s", "ms_per_batch": round(1e3 * dev_s / n, 3),
             "path": "qfca_score_assoc_batch on the batch's bins and global references (sigma_s = 1), "
                     "one launch per stage for the 16 images",
             "kernel_ms_per_batch": {k: round(v[0], 3) for k, v in sorted(tr.items(), key=lambda kv: -kv[1][0])},
-            "roofline": roof, "auroc_mean": round(float(np.nanmean(a)), 5)}
+            "roofline": roof, "auroc_mean": round(float(np.nanmean(a)), 5),
+            "aupro_30": round(aupro(maps, masks, 0.3, border=R), 5),
+            "f1_max": round(f1_max(np.stack(maps), np.stack(masks), border=R), 5)}
 
 
 def run_ours(args):
@@ -719,6 +723,13 @@ def run_ours(args):
     scores = pipe.scores[0].cpu().numpy()
     aurocs = [auroc(scores[i], masks[i]) for i in range(N_IMG)]
     auroc_mean = float(np.nanmean(aurocs))
+    from paper_2510_15602_gb300.metrics import aupro, f1_max
+    mstack = np.stack(masks)
+    quality = {"pixel_auroc_border_r": round(auroc(scores, mstack, border=R), 5),
+               "aupro_30": round(aupro(list(scores), masks, 0.3, border=R), 5),
+               "f1_max": round(f1_max(scores, mstack, border=R), 5),
+               "note": "pooled over the 16 maps, r-pixel border discarded; every image of the batch is anomalous, "
+                       "so the image-level AUROC is undefined here"}
 
     peaks = measured_peaks()
     roof = roofline_entry(dominant, dom_ms, dom_n, peaks, HW, HW, C, D, B, R, nimg=N_IMG, traffic=args.traffic)
@@ -767,6 +778,7 @@ def run_ours(args):
             "auroc": {"gpu_mean": round(auroc_mean, 5), "gpu_image0": round(aurocs[0], 5),
                       "oracle_image0": None if auroc_oracle is None else round(auroc_oracle, 5),
                       "delta_image0": None if auroc_oracle is None else round(abs(aurocs[0] - auroc_oracle), 6)},
+            "metrics": quality,
             "kernel_ms_per_step": {k: round(v[0], 3) for k, v in sorted(agg.items(), key=lambda kv: -kv[1][0])},
             "paper_scoring": paper,
             "uneven_batch": uneven,
