@@ -13,7 +13,8 @@ arXiv 2510.15602 it follows.
 Parity status: ``fit`` (Sec. 3.3), ``project`` (Sec. 3.3), ``quantize``
 (Sec. 3.1), ``ref_hist`` and ``score`` (Sec. 3.1, supplement's Wasserstein
 closed form), ``alg1`` (Algorithm 1; the supplement's correctness proof) and
-``assoc`` (Sec. 3.1's error-to-pixel association, the final blur) are each
+``assoc`` (Sec. 3.1's error-to-pixel association, the final blur) and
+``median_ref`` (Sec. 3.2's median reference) are each
 pinned by tests against closed forms, library routines or brute force
 (tests/test_oracle_pins.py).
 """
@@ -80,6 +81,8 @@ def _load():
             lib.orc_assoc.restype = I
             lib.orc_blur.argtypes = [P, I, I, ctypes.c_double, P]
             lib.orc_blur.restype = I
+            lib.orc_median_ref.argtypes = [P, I, I, I, I, I, P]
+            lib.orc_median_ref.restype = I
             _lib = lib
     return _lib
 
@@ -234,6 +237,20 @@ def alg1(P: np.ndarray, R: np.ndarray, Nloc: int | None = None, Nref: int | None
     if steps < 0:
         raise MemoryError("oracle alg1")
     return En, int(steps)
+
+
+def median_ref(q: np.ndarray, B: int, r: int) -> np.ndarray:
+    """The median reference (Sec. 3.2): per component, the lower median over all
+    full windows of each rank's value, as a histogram R [d, B] with N_ref = (2r+1)^2."""
+    q = np.ascontiguousarray(q, np.uint8)
+    d, H, W = q.shape
+    R = np.zeros((d, B), np.uint32)
+    rc = _load().orc_median_ref(_p(q), d, H, W, B, r, _p(R))
+    if rc == -2:
+        raise ValueError("no full window: H and W must exceed 2r")
+    if rc < 0:
+        raise MemoryError("oracle median_ref")
+    return R
 
 
 def blur(a: np.ndarray, sigma: float) -> np.ndarray:

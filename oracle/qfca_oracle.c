@@ -531,3 +531,60 @@ oom:
     free(En);
     return -1;
 }
+
+/* ------------------------------------------------------------ median reference */
+
+static int cmp_u8(const void *a, const void *b)
+{
+    return (int)*(const uint8_t *)a - (int)*(const uint8_t *)b;
+}
+
+/* The median reference (Sec. 3.2): for each component, every full window
+ * (centre at least r from each border, T^2 = (2r+1)^2 pixels) is sorted, and
+ * for each rank m the reference's m-th value is the median over the windows of
+ * their m-th smallest value; the reference is then the histogram of those T^2
+ * values (R[k][b], N_ref = T^2).  The median is the lower median (the
+ * ceil(Np/2)-th smallest of the Np windows' values).  Works on bin indices:
+ * a non-decreasing quantiser commutes with order statistics, so the median of
+ * the quantised values is the quantised median of the values.  Returns 0, -1 on
+ * allocation failure, -2 when no full window exists (H or W <= 2r). */
+int orc_median_ref(const uint8_t *q, int d, int H, int W, int B, int r, uint32_t *R)
+{
+    if (H <= 2 * r || W <= 2 * r)
+        return -2;
+    long N = (long)H * W;
+    int T = 2 * r + 1, T2 = T * T;
+    long Np = (long)(H - 2 * r) * (W - 2 * r);
+    uint8_t *o = (uint8_t *)malloc((size_t)Np * T2);
+    uint8_t *col = (uint8_t *)malloc((size_t)Np);
+    if (!o || !col) {
+        free(o);
+        free(col);
+        return -1;
+    }
+    for (int k = 0; k < d; k++) {
+        const uint8_t *qk = q + (long)k * N;
+        long p = 0;
+        for (int y = r; y < H - r; y++)
+            for (int x = r; x < W - r; x++, p++) {
+                uint8_t *w = o + p * T2;
+                int n = 0;
+                for (int yy = y - r; yy <= y + r; yy++)
+                    for (int xx = x - r; xx <= x + r; xx++)
+                        w[n++] = qk[(long)yy * W + xx];
+                qsort(w, (size_t)T2, 1, cmp_u8);
+            }
+        for (int b = 0; b < B; b++)
+            R[(long)k * B + b] = 0;
+        for (int m = 0; m < T2; m++) {
+            for (long i = 0; i < Np; i++)
+                col[i] = o[i * T2 + m];
+            qsort(col, (size_t)Np, 1, cmp_u8);
+            int med = col[(Np + 1) / 2 - 1];
+            R[(long)k * B + med]++;
+        }
+    }
+    free(o);
+    free(col);
+    return 0;
+}
