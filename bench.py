@@ -247,6 +247,12 @@ def kernel_work(name: str, H: int, W: int, C: int, d: int, B: int, r: int, nimg:
         return {"bound": "alu", "unit": "Tops", "work": nimg * N * d * ops, "peak_key": "int32_tops",
                 "per_unit": f"{ops} int ops per (pixel, component): 2(2r+1) window updates + 4(2B-1) for "
                             "Algorithm 1's at most 2B-1 steps + 2B running-sum updates + (2r+1) association adds"}
+    if name.startswith("k_median_ref"):
+        ops = 2 * (2 * r + 1) + 2 * B
+        return {"bound": "alu", "unit": "Tops", "work": nimg * (H - 2 * r) * (W - 2 * r) * d * ops,
+                "peak_key": "int32_tops",
+                "per_unit": f"{ops} int ops per (full window, component): 2(2r+1) window updates + B cumulative "
+                            "counts and B table increments"}
     if name.startswith("k_blur"):
         return {"bound": "hbm", "unit": "GB/s", "work": nimg * N * 8, "peak_key": "hbm",
                 "per_unit": "8 bytes per pixel"}
@@ -585,6 +591,48 @@ def run_paper_scoring(qfca, torch, pipe, masks, args):
             "f1_max": round(f1_max(np.stack(maps), np.stack(masks), border=R), 5)}
 
 
+def run_median_reference(qfca, torch, pipe, masks, args):
+    """The median reference (per-rank lower median over the full windows) of the
+    batch's bins, one launch per stage for the 16 images, CUDA-event timed; and the
+    pixel AUROC of the plain EMD scored against it."""
+    import numpy as np
+    from paper_2510_15602_gb300.metrics import auroc
+    ctx = qfca.Context()
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        _, ex = qfca.batch_run(pipe.X[0], D, B, R, args.precision, ctx=ctx, stream=st, extras=True)
+    st.synchronize()
+    bl = [ex["bins"][i] for i in range(N_IMG)]
+    outs = [torch.empty(D, B, dtype=torch.int32, device="cuda") for _ in range(N_IMG)]
+
+    def step(_i):
+        qfca.median_reference_batch(bl, [HW] * N_IMG, [R] * N_IMG, B, ctx=ctx, stream=st, outs=outs)
+
+    for i in range(3):
+        step(i)
+    st.synchronize()
+    ctx.trace_start("")
+    step(0)
+    st.synchronize()
+    tr = {k: list(v) for k, v in ctx.trace().items()}
+    ctx.trace_stop()
+    n = max(2, args.steps // 2)
+    dev_s, _ = timed(torch, st, step, n)
+    T2 = (2 * R + 1) ** 2
+    a = []
+    for i in range(N_IMG):
+        sc = qfca.score(bl[i], HW, B, R, outs[i], T2, ctx=ctx, stream=st)
+        st.synchronize()
+        a.append(auroc(sc.cpu().numpy(), masks[i]))
+    peaks = measured_peaks()
+    roof = roofline_entry("k_median_ref", tr["k_median_ref"][0], tr["k_median_ref"][1], peaks, HW, HW, C, D, B, R,
+                          nimg=N_IMG)
+    return {"value": round(N_IMG * n / dev_s, 3), "unit": "references/s", "ms_per_batch": round(1e3 * dev_s / n, 3),
+            "path": "qfca_median_reference_batch on the batch's bins, one launch per stage for the 16 images",
+            "kernel_ms_per_batch": {k: round(v[0], 3) for k, v in sorted(tr.items(), key=lambda kv: -kv[1][0])},
+            "roofline": roof, "emd_auroc_mean": round(float(np.nanmean(a)), 5)}
+
+
 def run_ours(args):
     ws, rank, local = dist_env()
     indices = shard_indices(rank, ws, N_IMG)
@@ -750,6 +798,7 @@ def run_ours(args):
         auroc_oracle = auroc(ref["score"], masks[0])
 
     paper = run_paper_scoring(qfca, torch, pipe, masks, args) if extra and not args.skip_paper else None
+    median = run_median_reference(qfca, torch, pipe, masks, args) if extra and not args.skip_paper else None
     uneven = run_uneven(qfca, torch, host_uneven, args) if host_uneven is not None else None
     serving = run_serving(qfca, torch, serve_fields, serve_classes, args) if serve_fields is not None else None
 
@@ -781,6 +830,7 @@ def run_ours(args):
             "metrics": quality,
             "kernel_ms_per_step": {k: round(v[0], 3) for k, v in sorted(agg.items(), key=lambda kv: -kv[1][0])},
             "paper_scoring": paper,
+            "median_reference": median,
             "uneven_batch": uneven,
             "serving": serving,
             "wall_s_timed": round(wall_s, 3),
@@ -811,6 +861,8 @@ def run_profile_batch(args):
         refs = [ex["ref_hist"][i] for i in range(N_IMG)]
         for _ in range(args.profile_paper):
             qfca.score_assoc_batch(bl, [HW] * N_IMG, [R] * N_IMG, B, refs, [HW * HW] * N_IMG, sigma_s=1.0, ctx=ctx)
+        for _ in range(args.profile_paper):
+            qfca.median_reference_batch(bl, [HW] * N_IMG, [R] * N_IMG, B, ctx=ctx)
     torch.cuda.synchronize()
     return 0 if ctx.device_status() == 0 else 1
 
@@ -828,7 +880,8 @@ def main(argv=None):
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-uneven", action="store_true", help="skip the 64-image uneven batch measurement")
     ap.add_argument("--skip-serving", action="store_true", help="skip the serving measurement")
-    ap.add_argument("--skip-paper", action="store_true", help="skip the paper-scoring (Algorithm 1) measurement")
+    ap.add_argument("--skip-paper", action="store_true",
+                    help="skip the paper-scoring (Algorithm 1) and median-reference measurements")
     ap.add_argument("--profile-paper", type=int, default=0,
                     help="profiling mode: after --profile-batch calls, N calls of the paper's scoring on the batch")
     ap.add_argument("--profile-batch", type=int, default=0,

@@ -211,6 +211,36 @@ typedef struct {
 qfca_status qfca_score_assoc_batch(qfca_ctx *ctx, const qfca_assoc_image *imgs, int n, int d, int B,
                                    float sigma_s, void *stream);
 
+/* qfca_median_reference -- the median reference (Sec. 3.2): for each component,
+ * every full window (centre at least r from each border, T^2 = (2r+1)^2
+ * pixels) is sorted, and the reference's m-th value, m = 1..T^2, is the lower
+ * median over the windows (the ceil(Np/2)-th smallest of the Np windows'
+ * m-th values).  The result is their histogram, ref_out[k][b] (each row sums
+ * to T^2: pass ref_total = (2r+1)^2 to qfca_score / qfca_score_assoc).  Bin
+ * indices are used directly: a non-decreasing quantiser commutes with order
+ * statistics, so this equals quantising the median of the unquantised values.
+ *   bins     device u8 [d][H][pitch], pitch >= W; values >= B count as B-1.
+ *   ref_out  device u32 [d][B], written.
+ * Requires H > 2r, W > 2r, 1 <= r, 2 <= B <= 255, d <= 64, and the count table
+ * of B x (T^2 + 1) words plus 32 window histograms within 200 KB of shared
+ * memory (r <= 19 for B = 32, r <= 13 for B = 64, r <= 5 for B = 255);
+ * QFCA_ERR_UNSUPPORTED otherwise.  Exact (integer). */
+qfca_status qfca_median_reference(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pitch, int d, int B,
+                                  int r, uint32_t *ref_out, void *stream);
+
+/* One image of qfca_median_reference_batch (fields as in qfca_median_reference). */
+typedef struct {
+    const uint8_t *bins;  /* device u8 [d][H][pitch] */
+    int H, W, pitch, r;
+    uint32_t *ref_out;    /* device u32 [d][B], written */
+} qfca_median_image;
+
+/* qfca_median_reference_batch -- qfca_median_reference for n images (own sizes
+ * and radii, common d and B), one launch per stage per 64 images.
+ * Requires 1 <= n <= 4096. */
+qfca_status qfca_median_reference_batch(qfca_ctx *ctx, const qfca_median_image *imgs, int n, int d, int B,
+                                        void *stream);
+
 /* Synchronise the device and read-and-clear the context's device status
  * word.  Kernels whose bounded waits (on tensor-core completion, on a peer
  * stage) run out set a bit there and return early instead of hanging.

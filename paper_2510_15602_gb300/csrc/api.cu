@@ -531,6 +531,50 @@ qfca_status qfca_score_assoc_batch(qfca_ctx *ctx, const qfca_assoc_image *imgs, 
     return run_assoc(ctx, jobs.data(), n, d, B, (cudaStream_t)stream);
 }
 
+static qfca_status run_median(qfca_ctx *ctx, const MedianJob *jobs, int n, int d, int B, cudaStream_t st) {
+    if (d < 1 || d > kMaxD) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, %d]", d, kMaxD);
+    if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
+    for (int i = 0; i < n; i++) {
+        const MedianJob &j = jobs[i];
+        if (!j.bins || !j.ref_out) return fail(ctx, QFCA_ERR_INVALID_ARG, "image %d: NULL pointer", i);
+        if (j.r < 1) return fail(ctx, QFCA_ERR_INVALID_ARG, "image %d: r = %d < 1", i, j.r);
+        if (j.H <= 2 * j.r || j.W <= 2 * j.r)
+            return fail(ctx, QFCA_ERR_INVALID_ARG, "image %d: %d x %d has no full window of radius %d", i, j.H, j.W, j.r);
+        if (j.pitch < j.W) return fail(ctx, QFCA_ERR_INVALID_ARG, "image %d: pitch %d < W", i, j.pitch);
+        if (!median_shape_ok(B, j.r))
+            return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d: the count table does not fit", B, j.r);
+    }
+    DeviceGuard g(ctx->device);
+    HookScope hs(ctx);
+    qfca_status s;
+    if ((s = ensure_ws(ctx, median_jobs_workspace_bytes(jobs, n, d, B), st))) return s;
+    const cudaError_t e = launch_median_jobs(jobs, n, d, B, ctx->ws, st);
+    if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "shape does not fit the median kernel");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_median_reference");
+    return QFCA_OK;
+}
+
+qfca_status qfca_median_reference(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pitch, int d, int B,
+                                  int r, uint32_t *ref_out, void *stream) {
+    qfca_status s = check_ctx(ctx);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const MedianJob job{bins, H, W, pitch, r, ref_out};
+    return run_median(ctx, &job, 1, d, B, (cudaStream_t)stream);
+}
+
+qfca_status qfca_median_reference_batch(qfca_ctx *ctx, const qfca_median_image *imgs, int n, int d, int B,
+                                        void *stream) {
+    qfca_status s = check_ctx(ctx);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!imgs || n < 1 || n > 4096) return fail(ctx, QFCA_ERR_INVALID_ARG, "n = %d outside [1, 4096]", n);
+    std::vector<MedianJob> jobs(n);
+    for (int i = 0; i < n; i++)
+        jobs[i] = MedianJob{imgs[i].bins, imgs[i].H, imgs[i].W, imgs[i].pitch, imgs[i].r, imgs[i].ref_out};
+    return run_median(ctx, jobs.data(), n, d, B, (cudaStream_t)stream);
+}
+
 qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int d, int B, int r,
                            int precision, float *scores, const qfca_batch_outputs *extra, void *stream) {
     qfca_status s = check_ctx(ctx);

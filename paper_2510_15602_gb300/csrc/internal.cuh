@@ -180,6 +180,21 @@ size_t assoc_jobs_workspace_bytes(const AssocJob *jobs, int n, int d);
 // cudaErrorInvalidValue for sigma_s > 4.
 cudaError_t launch_assoc_jobs(const AssocJob *jobs, int n, int d, int B, void *ws, cudaStream_t st);
 
+// One image of the median reference (median.cu): bins [d][H][pitch], window
+// radius r (H, W > 2r); ref_out [d][B] receives the histogram of the per-rank
+// lower medians over the full windows (N_ref = (2r+1)^2).
+struct MedianJob {
+    const uint8_t *bins;
+    int H, W, pitch, r;
+    uint32_t *ref_out;
+};
+
+bool median_shape_ok(int B, int r);
+size_t median_jobs_workspace_bytes(const MedianJob *jobs, int n, int d, int B);
+// cudaErrorNotSupported (nothing enqueued) when B and r do not fit;
+// cudaErrorInvalidValue when an image has no full window.
+cudaError_t launch_median_jobs(const MedianJob *jobs, int n, int d, int B, void *ws, cudaStream_t st);
+
 // ------------------------------------------------------------------ context access (api.cu) for serve.cu
 
 struct ServeState;

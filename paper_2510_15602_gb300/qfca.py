@@ -106,6 +106,17 @@ class AssocImage(ctypes.Structure):
 
 _lib.qfca_score_assoc_batch.argtypes = [_P, ctypes.POINTER(AssocImage), _I, _I, _I, ctypes.c_float, _P]
 _lib.qfca_score_assoc_batch.restype = _I
+_lib.qfca_median_reference.argtypes = [_P, _P, _I, _I, _I, _I, _I, _I, _P, _P]
+_lib.qfca_median_reference.restype = _I
+
+
+class MedianImage(ctypes.Structure):
+    _fields_ = [("bins", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int), ("pitch", ctypes.c_int),
+                ("r", ctypes.c_int), ("ref_out", ctypes.c_void_p)]
+
+
+_lib.qfca_median_reference_batch.argtypes = [_P, ctypes.POINTER(MedianImage), _I, _I, _I, _P]
+_lib.qfca_median_reference_batch.restype = _I
 _lib.qfca_set_autotune.argtypes = [_P, _I]
 _lib.qfca_set_autotune.restype = _I
 _lib.qfca_last_tiling.argtypes = [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]
@@ -392,6 +403,35 @@ def score_assoc_batch(bins_list, Ws, rs, B: int, refs, ref_totals, sigma_s: floa
         arr[i] = AssocImage(_ptr(b), int(b.shape[1]), int(w), int(b.shape[2]), int(r), _ptr(R), int(nt), _ptr(sc), None)
     ctx.check(_lib.qfca_score_assoc_batch(ctx.handle, arr, n, d, B, float(sigma_s), _P(_stream_ptr(stream))))
     return scores
+
+
+def median_reference(bins: torch.Tensor, W: int, B: int, r: int, ctx: Context | None = None, stream=None, out=None):
+    """qfca_median_reference: the per-rank median reference of bins [d, H, pitch] as a
+    histogram int32 [d, B] (each row sums to (2r+1)^2)."""
+    _check_dev(bins, "bins", torch.uint8)
+    d, H, pitch = bins.shape
+    ctx = ctx or default_context(bins.device.index)
+    R = torch.empty(d, B, dtype=torch.int32, device=bins.device) if out is None else out
+    ctx.check(_lib.qfca_median_reference(ctx.handle, _ptr(bins), H, W, pitch, d, B, r, _ptr(R),
+                                         _P(_stream_ptr(stream))))
+    return R
+
+
+def median_reference_batch(bins_list, Ws, rs, B: int, ctx: Context | None = None, stream=None, outs=None):
+    """qfca_median_reference_batch over several images; returns the list of int32 [d, B]."""
+    n = len(bins_list)
+    if not (n == len(Ws) == len(rs)) or n == 0:
+        raise ValueError("one width and radius per image")
+    ctx = ctx or default_context(bins_list[0].device.index)
+    d = int(bins_list[0].shape[0])
+    if outs is None:
+        outs = [torch.empty(d, B, dtype=torch.int32, device=b.device) for b in bins_list]
+    arr = (MedianImage * n)()
+    for i, (b, w, r, o) in enumerate(zip(bins_list, Ws, rs, outs)):
+        _check_dev(b, f"bins_list[{i}]", torch.uint8)
+        arr[i] = MedianImage(_ptr(b), int(b.shape[1]), int(w), int(b.shape[2]), int(r), _ptr(o))
+    ctx.check(_lib.qfca_median_reference_batch(ctx.handle, arr, n, d, B, _P(_stream_ptr(stream))))
+    return outs
 
 
 def batch_run(X: torch.Tensor, d: int, B: int, r: int, precision="bf16", ctx: Context | None = None, stream=None,

@@ -1,0 +1,84 @@
+"""GPU parity of the median reference (arXiv 2510.15602, Sec. 3.2) through the
+C ABI against the oracle: integer work, bit-exact; and the EMD / paper scoring
+against it, bit-exact numerators and within the association bound."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2510_15602_gb300 import synth
+from tests.gpu_helpers import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2510_15602_gb300 import qfca
+    assert torch.cuda.is_available()
+    return qfca
+
+
+def dev_bins(q, qb):
+    d, H, W = qb.shape
+    bins = torch.zeros(d, H, q.bins_pitch(W), dtype=torch.uint8, device="cuda")
+    bins[:, :, :W] = to_dev(qb)
+    return bins
+
+
+@pytest.mark.parametrize("d,H,W,B,r,seed", [
+    (3, 40, 300, 16, 4, 0),     # two strips of centres, ragged
+    (2, 33, 65, 32, 7, 1),
+    (2, 3, 5, 8, 1, 2),         # a single full window
+    (2, 60, 9, 16, 4, 3),       # a single column of centres
+    (2, 50, 70, 64, 12, 4),     # B = 64, r = 12
+    (2, 20, 24, 255, 3, 5),     # maximum bin count
+])
+def test_median_reference_bit_exact(q, d, H, W, B, r, seed):
+    rng = np.random.default_rng(400 + seed)
+    qb = synth.random_bins(rng, d, H, W, B, smooth=(seed % 2 == 0))
+    R_o = oracle.median_ref(qb, B, r)
+    R_g = q.median_reference(dev_bins(q, qb), W, B, r).cpu().numpy().astype(np.uint32)
+    np.testing.assert_array_equal(R_g, R_o)
+    assert (R_g.sum(axis=1) == (2 * r + 1) ** 2).all()
+
+
+def test_median_reference_clamps_and_batches(q):
+    rng = np.random.default_rng(410)
+    B = 10
+    shapes = [(30, 41, 3), (25, 25, 5), (64, 33, 2)]
+    bl, Ws, rs, ro = [], [], [], []
+    for H, W, r in shapes:
+        qb = synth.random_bins(rng, 3, H, W, 14, smooth=True)  # values up to 13 with B = 10
+        bl.append(dev_bins(q, qb))
+        Ws.append(W)
+        rs.append(r)
+        ro.append(oracle.median_ref(np.minimum(qb, B - 1), B, r))
+    outs = q.median_reference_batch(bl, Ws, rs, B)
+    for o, R in zip(outs, ro):
+        np.testing.assert_array_equal(o.cpu().numpy().astype(np.uint32), R)
+
+
+def test_scores_against_the_median_reference(q):
+    # the full path of Table 3's median reference: reference -> plain EMD and the paper's scoring
+    rng = np.random.default_rng(420)
+    d, H, W, B, r = 4, 48, 72, 16, 4
+    qb = synth.random_bins(rng, d, H, W, B, smooth=True)
+    bins = dev_bins(q, qb)
+    Rg = q.median_reference(bins, W, B, r)
+    R = Rg.cpu().numpy().astype(np.uint32)
+    T2 = (2 * r + 1) ** 2
+    _, num_o, _ = oracle.score(qb, B, r, R, T2)
+    _, num_g = q.score(bins, W, B, r, Rg, T2, want_numer=True)
+    np.testing.assert_array_equal(num_g.cpu().numpy(), num_o)
+    s_o, _, _ = oracle.assoc(qb, B, r, R, T2, sigma_s=1.0)
+    s_g = q.score_assoc(bins, W, B, r, Rg, T2, sigma_s=1.0).cpu().numpy()
+    np.testing.assert_allclose(s_g, s_o, rtol=2.0 ** -20, atol=4 * 2.0 ** -24 * (B - 1) + 2.0 ** -21)
+
+
+def test_median_reference_rejects_bad_arguments(q):
+    bins = torch.zeros(1, 8, 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(RuntimeError):
+        q.median_reference(bins, 8, 8, 4)   # 8 x 8 has no full 9 x 9 window
+    with pytest.raises(RuntimeError):
+        q.median_reference(torch.zeros(1, 64, 64, dtype=torch.uint8, device="cuda"), 64, 255, 20)  # table too large
