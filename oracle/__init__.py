@@ -14,7 +14,8 @@ Parity status: ``fit`` (Sec. 3.3), ``project`` (Sec. 3.3), ``quantize``
 (Sec. 3.1), ``ref_hist`` and ``score`` (Sec. 3.1, supplement's Wasserstein
 closed form), ``alg1`` (Algorithm 1; the supplement's correctness proof) and
 ``assoc`` (Sec. 3.1's error-to-pixel association, the final blur) and
-``median_ref`` (Sec. 3.2's median reference) are each
+``median_ref`` (Sec. 3.2's median reference) and ``residual`` (Sec. 3.3's
+QFCA+ features) are each
 pinned by tests against closed forms, library routines or brute force
 (tests/test_oracle_pins.py).
 """
@@ -83,6 +84,8 @@ def _load():
             lib.orc_blur.restype = I
             lib.orc_median_ref.argtypes = [P, I, I, I, I, I, P]
             lib.orc_median_ref.restype = I
+            lib.orc_residual.argtypes = [P, I, I, I, I, P, P, I, P]
+            lib.orc_residual.restype = None
             _lib = lib
     return _lib
 
@@ -237,6 +240,30 @@ def alg1(P: np.ndarray, R: np.ndarray, Nloc: int | None = None, Nref: int | None
     if steps < 0:
         raise MemoryError("oracle alg1")
     return En, int(steps)
+
+
+def residual(X: np.ndarray, mean: np.ndarray, V: np.ndarray, layout: int = NCHW) -> np.ndarray:
+    """QFCA+ features (Sec. 3.3): X minus its PCA reconstruction from the columns
+    of V, F[c, y, x] = (x_c - mean_c) - sum_k V[c, k] y_k, in FP64."""
+    X, C, H, W = _fmap(X, layout)
+    mean = np.ascontiguousarray(mean, np.float64)
+    V = np.ascontiguousarray(V, np.float64)
+    dres = V.shape[1]
+    F = np.zeros((C, H, W), np.float64)
+    _load().orc_residual(_p(X), layout, H, W, C, _p(mean), _p(V), dres, _p(F))
+    return F
+
+
+def pipeline_plus(X: np.ndarray, dres: int, B: int, r: int, layout: int = NCHW):
+    """QFCA+ on one image: fit dres components, residual features over all C
+    channels, per-channel quantisation, global histograms, window EMD."""
+    mean, V, ev, allev = fit(X, dres, layout)
+    F = residual(X, mean, V, layout)
+    q, lo, hi = quantize(F, B)
+    R = ref_hist(q, B)
+    H, W = q.shape[1:]
+    s, numer, nloc = score(q, B, r, R, H * W)
+    return dict(mean=mean, V=V, all_eigvals=allev, F=F, q=q, lo=lo, hi=hi, R=R, score=s, numer=numer)
 
 
 def median_ref(q: np.ndarray, B: int, r: int) -> np.ndarray:

@@ -588,3 +588,34 @@ int orc_median_ref(const uint8_t *q, int d, int H, int W, int B, int r, uint32_t
     free(col);
     return 0;
 }
+
+/* ------------------------------------------------------------ QFCA+ residual */
+
+/* The QFCA+ feature preprocessing (Sec. 3.3): the features minus their PCA
+ * reconstruction from the top dres components,
+ *     F(X) = X - PCA^-1(PCA(X)) = (X - mean) - (X - mean) V V^T,
+ * computed channel by channel in FP64 (the mean cancels: the reconstruction
+ * adds it back).  V is [C][dres] (columns orthonormal).  Writes Fres[C][N]. */
+void orc_residual(const float *X, int layout, int H, int W, int C, const double *mean, const double *V, int dres,
+                  double *Fres)
+{
+    long N = (long)H * W;
+    double *y = (double *)malloc(sizeof(double) * (dres > 0 ? dres : 1));
+    if (!y)
+        return;
+    for (long p = 0; p < N; p++) {
+        for (int k = 0; k < dres; k++) {
+            double s = 0.0;
+            for (int c = 0; c < C; c++)
+                s += (feat(X, layout, C, N, c, p) - mean[c]) * V[(long)c * dres + k];
+            y[k] = s;
+        }
+        for (int c = 0; c < C; c++) {
+            double rec = 0.0;
+            for (int k = 0; k < dres; k++)
+                rec += V[(long)c * dres + k] * y[k];
+            Fres[(long)c * N + p] = (feat(X, layout, C, N, c, p) - mean[c]) - rec;
+        }
+    }
+    free(y);
+}
