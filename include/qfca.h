@@ -149,6 +149,24 @@ qfca_status qfca_quantize(qfca_ctx *ctx, const float *X, qfca_fmap desc, const q
                           const float *hi_in, uint8_t *bins, int pitch, float *lo_out,
                           float *hi_out, uint32_t *ref_hist_out, float *Y_out, void *stream);
 
+/* qfca_quantize_residual -- the QFCA+ features (Sec. 3.3) and their per-channel
+ * quantisation: with the basis of qfca_fit_pca fitted with dres components,
+ *   F = (X - mean) - (X - mean) V V^T        (all C channels, FP32),
+ * the input minus its PCA reconstruction; then each channel is quantised into
+ * B equally spaced bins between its image-wide min and max (as qfca_quantize,
+ * range mode IMAGE) with its global histogram as reference.  Score the result
+ * with qfca_score / qfca_score_assoc with d = C.
+ *   basis          mean f64[C], V f64[C][dres] (column k = component k).
+ *   bins           device u8 [C][H][pitch], 16-byte aligned, pitch >= W and a
+ *                  multiple of 16.
+ *   lo_out, hi_out device f32 [C] (may be NULL): the channel ranges.
+ *   ref_hist_out   device u32 [C][B] (may be NULL).
+ *   F_out          device f32 [C][H*W] (may be NULL): the residual features.
+ * Requires 0 <= dres <= min(C, 32), C <= 512, 2 <= B <= 255. */
+qfca_status qfca_quantize_residual(qfca_ctx *ctx, const float *X, qfca_fmap desc, const qfca_basis *basis,
+                                   int dres, int B, uint8_t *bins, int pitch, float *lo_out, float *hi_out,
+                                   uint32_t *ref_hist_out, float *F_out, void *stream);
+
 /* qfca_score -- per-pixel window histogram and 1-D EMD against the
  * reference, averaged over the d components (Sec. 3.1; W1 closed form in
  * the supplement).  For pixel p with clipped window of N_loc pixels:
@@ -160,7 +178,8 @@ qfca_status qfca_quantize(qfca_ctx *ctx, const float *X, qfca_fmap desc, const q
  *   ref_hist   device u32 [d][B]; every row sums to ref_total = N_ref.
  *   score      device f32 [H][W].
  *   numer_out  device u64 [d][H][W] or NULL: the exact D_k(p).
- * Requires 1 <= r, 2 <= B <= 255, (2r+1) <= 127, d <= 64. */
+ * Requires 1 <= r, 2 <= B <= 255, (2r+1) <= 127, d <= 512 (d planes: the
+ * components, or all C channels of qfca_quantize_residual). */
 qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pitch, int d, int B,
                        int r, const uint32_t *ref_hist, uint32_t ref_total, float *score,
                        uint64_t *numer_out, void *stream);
@@ -187,7 +206,7 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
  *   raw_out    device f32 [H][W] or NULL: the map before smoothing.
  *   comp_out   device f32 [d][H][W] or NULL: each component's associated
  *              error (the map before the mean over components).
- * Requires 1 <= r, 2 <= B <= 255, d <= 64, 2r <= 248 (B <= 32), 2r <= 120
+ * Requires 1 <= r, 2 <= B <= 255, d <= 512, 2r <= 248 (B <= 32), 2r <= 120
  * (B <= 128), 2r <= 56 (B <= 255), and a shared-memory plan (histograms and
  * running sums for the window columns, (2r+1)^2 reciprocals) within 200 KB
  * (r <= 31 always fits for B <= 64); QFCA_ERR_UNSUPPORTED otherwise. */
@@ -221,7 +240,7 @@ qfca_status qfca_score_assoc_batch(qfca_ctx *ctx, const qfca_assoc_image *imgs, 
  * statistics, so this equals quantising the median of the unquantised values.
  *   bins     device u8 [d][H][pitch], pitch >= W; values >= B count as B-1.
  *   ref_out  device u32 [d][B], written.
- * Requires H > 2r, W > 2r, 1 <= r, 2 <= B <= 255, d <= 64, and the count table
+ * Requires H > 2r, W > 2r, 1 <= r, 2 <= B <= 255, d <= 512, and the count table
  * of B x (T^2 + 1) words plus 32 window histograms within 200 KB of shared
  * memory (r <= 19 for B = 32, r <= 13 for B = 64, r <= 5 for B = 255);
  * QFCA_ERR_UNSUPPORTED otherwise.  Exact (integer). */

@@ -467,7 +467,7 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
     if (H < 1 || W < 1) return fail(ctx, QFCA_ERR_INVALID_ARG, "bad H x W");
     if (pitch < W || pitch % 16 != 0) return fail(ctx, QFCA_ERR_INVALID_ARG, "pitch %d must be >= W and a multiple of 16", pitch);
     if (((uintptr_t)bins & 15) != 0) return fail(ctx, QFCA_ERR_INVALID_ARG, "bins must be 16-byte aligned");
-    if (d < 1 || d > kMaxD) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, %d]", d, kMaxD);
+    if (d < 1 || d > kMaxPlanes) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, %d]", d, kMaxPlanes);
     if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
     if (r < 1 || 2 * r + 1 > 127) return fail(ctx, QFCA_ERR_INVALID_ARG, "r = %d outside [1, 63]", r);
     if (ref_total < 1) return fail(ctx, QFCA_ERR_INVALID_ARG, "ref_total must be >= 1");
@@ -483,6 +483,38 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
     return QFCA_OK;
 }
 
+qfca_status qfca_quantize_residual(qfca_ctx *ctx, const float *X, qfca_fmap desc, const qfca_basis *basis, int dres,
+                                   int B, uint8_t *bins, int pitch, float *lo_out, float *hi_out,
+                                   uint32_t *ref_hist_out, float *F_out, void *stream) {
+    qfca_status s = check_ctx(ctx);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if ((s = check_fmap(ctx, X, desc))) return s;
+    if (!basis || !basis->mean || (dres > 0 && !basis->V)) return fail(ctx, QFCA_ERR_INVALID_ARG, "basis NULL");
+    if (dres < 0 || dres > desc.C || dres > kMaxResidual)
+        return fail(ctx, QFCA_ERR_INVALID_ARG, "dres = %d outside [0, min(C, %d)]", dres, kMaxResidual);
+    if (desc.C > kMaxPlanes) return fail(ctx, QFCA_ERR_INVALID_ARG, "C = %d above %d", desc.C, kMaxPlanes);
+    if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
+    if (!bins) return fail(ctx, QFCA_ERR_INVALID_ARG, "bins NULL");
+    if (pitch < desc.W || pitch % 16 != 0) return fail(ctx, QFCA_ERR_INVALID_ARG, "pitch %d must be >= W and a multiple of 16", pitch);
+    DeviceGuard g(ctx->device);
+    HookScope hs(ctx);
+    const long N = (long)desc.H * desc.W;
+    const int C = desc.C;
+    const size_t o_f = bytes_mmkeys(C);
+    if ((s = ensure_ws(ctx, o_f + (F_out ? 0 : align_up(sizeof(float) * C * N, 256)), (cudaStream_t)stream))) return s;
+    char *base = (char *)ctx->ws;
+    uint32_t *mm = (uint32_t *)base;
+    float *F = F_out ? F_out : (float *)(base + o_f);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_residual(X, desc.layout, desc.H, desc.W, C, basis->mean, basis->V, dres, F, mm, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_quantize_residual/residual");
+    e = launch_quantize(F, N, desc.H, desc.W, C, 1, B, QFCA_RANGE_IMAGE, mm, nullptr, nullptr, bins, pitch, lo_out,
+                        hi_out, ref_hist_out, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_quantize_residual/quantize");
+    return QFCA_OK;
+}
+
 static qfca_status run_assoc(qfca_ctx *ctx, const AssocJob *jobs, int n, int d, int B, cudaStream_t st) {
     for (int i = 0; i < n; i++) {
         const AssocJob &j = jobs[i];
@@ -494,7 +526,7 @@ static qfca_status run_assoc(qfca_ctx *ctx, const AssocJob *jobs, int n, int d, 
         if (!assoc_shape_ok(B, j.r))
             return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d does not fit the association kernel", B, j.r);
     }
-    if (d < 1 || d > kMaxD) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, %d]", d, kMaxD);
+    if (d < 1 || d > kMaxPlanes) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, %d]", d, kMaxPlanes);
     if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
     if (!(jobs[0].sigma_s >= 0.0f && jobs[0].sigma_s <= 4.0f))
         return fail(ctx, QFCA_ERR_INVALID_ARG, "sigma_s = %g outside [0, 4]", (double)jobs[0].sigma_s);
@@ -532,7 +564,7 @@ qfca_status qfca_score_assoc_batch(qfca_ctx *ctx, const qfca_assoc_image *imgs, 
 }
 
 static qfca_status run_median(qfca_ctx *ctx, const MedianJob *jobs, int n, int d, int B, cudaStream_t st) {
-    if (d < 1 || d > kMaxD) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, %d]", d, kMaxD);
+    if (d < 1 || d > kMaxPlanes) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, %d]", d, kMaxPlanes);
     if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
     for (int i = 0; i < n; i++) {
         const MedianJob &j = jobs[i];

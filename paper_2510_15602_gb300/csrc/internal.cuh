@@ -15,7 +15,9 @@
 namespace qfca {
 
 constexpr int kMaxC = 512;   // channels supported by the fit and projection
-constexpr int kMaxD = 64;    // components
+constexpr int kMaxD = 64;    // components of a PCA projection
+constexpr int kMaxPlanes = 512;  // bin planes scored per image (components, or all channels for QFCA+)
+constexpr int kMaxResidual = 32;  // components removed by the QFCA+ residual
 constexpr int kMaxB = 255;   // bins
 // Images per launch of the table-driven stages (the table travels in the
 // kernel's parameter block).
@@ -194,6 +196,12 @@ size_t median_jobs_workspace_bytes(const MedianJob *jobs, int n, int d, int B);
 // cudaErrorNotSupported (nothing enqueued) when B and r do not fit;
 // cudaErrorInvalidValue when an image has no full window.
 cudaError_t launch_median_jobs(const MedianJob *jobs, int n, int d, int B, void *ws, cudaStream_t st);
+
+// QFCA+ residual features F = (X - mean) - (X - mean) V V^T over all C
+// channels (residual.cu): F [C][N] f32, per-channel min/max keys mm
+// [2 C kKeyStride] (initialised here).  0 <= dres <= kMaxResidual.
+cudaError_t launch_residual(const float *X, int layout, int H, int W, int C, const double *mean, const double *V,
+                            int dres, float *F, uint32_t *mm, cudaStream_t st);
 
 // ------------------------------------------------------------------ context access (api.cu) for serve.cu
 

@@ -106,6 +106,8 @@ class AssocImage(ctypes.Structure):
 
 _lib.qfca_score_assoc_batch.argtypes = [_P, ctypes.POINTER(AssocImage), _I, _I, _I, ctypes.c_float, _P]
 _lib.qfca_score_assoc_batch.restype = _I
+_lib.qfca_quantize_residual.argtypes = [_P, _P, Fmap, ctypes.POINTER(Basis), _I, _I, _P, _I, _P, _P, _P, _P, _P]
+_lib.qfca_quantize_residual.restype = _I
 _lib.qfca_median_reference.argtypes = [_P, _P, _I, _I, _I, _I, _I, _I, _P, _P]
 _lib.qfca_median_reference.restype = _I
 
@@ -342,6 +344,32 @@ def quantize(X: torch.Tensor, basis, B: int, precision="f32", layout: int = NCHW
                                  _ptr(lo), _ptr(hi), _ptr(bins), pitch, _ptr(lo_o), _ptr(hi_o), _ptr(hist),
                                  _ptr(Y), _P(_stream_ptr(stream))))
     return dict(bins=bins, lo=lo_o, hi=hi_o, hist=hist, Y=Y, pitch=pitch)
+
+
+def quantize_residual(X: torch.Tensor, basis, B: int, layout: int = NCHW, want_F: bool = False,
+                      ctx: Context | None = None, stream=None):
+    """qfca_quantize_residual: QFCA+ features (X minus its PCA reconstruction from the
+    basis' dres components) quantised per channel.  Returns a dict with bins (u8
+    [C, H, pitch]), lo, hi (f32 [C]), hist (u32 [C, B]) and optionally F (f32 [C, H, W])."""
+    _check_dev(X, "X", torch.float32)
+    mean, V = basis[0], basis[1]
+    _check_dev(mean, "mean", torch.float64)
+    _check_dev(V, "V", torch.float64)
+    ctx = ctx or default_context(X.device.index)
+    fm = fmap_of(X, layout)
+    dres = V.shape[1]
+    pitch = bins_pitch(fm.W)
+    dev = X.device
+    C = fm.C
+    bins = torch.empty(C, fm.H, pitch, dtype=torch.uint8, device=dev)
+    lo_o = torch.empty(C, dtype=torch.float32, device=dev)
+    hi_o = torch.empty(C, dtype=torch.float32, device=dev)
+    hist = torch.empty(C, B, dtype=torch.int32, device=dev)
+    F = torch.empty(C, fm.H, fm.W, dtype=torch.float32, device=dev) if want_F else None
+    b = Basis(mean.data_ptr(), V.data_ptr() if V.numel() else None, None)
+    ctx.check(_lib.qfca_quantize_residual(ctx.handle, _ptr(X), fm, ctypes.byref(b), dres, B, _ptr(bins), pitch,
+                                          _ptr(lo_o), _ptr(hi_o), _ptr(hist), _ptr(F), _P(_stream_ptr(stream))))
+    return dict(bins=bins, lo=lo_o, hi=hi_o, hist=hist, F=F, pitch=pitch)
 
 
 def score(bins: torch.Tensor, W: int, B: int, r: int, ref_hist: torch.Tensor, ref_total: int,

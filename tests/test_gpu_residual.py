@@ -1,0 +1,86 @@
+"""GPU parity of the QFCA+ path (arXiv 2510.15602, Sec. 3.3): residual
+features over all C channels, per-channel quantisation, scoring of all C
+planes, through the C ABI against the FP64 oracle.
+
+Tolerance of the residual: FP32 sums of C products for each y_k and dres+1
+terms for each f_c, so |f_gpu - f_oracle| <= (C + dres + 2) 2^-24 (max|x - mean|
++ sum_k |V_ck y_k|) -- well inside 1e-5 * max|x - mean| for the C used here.
+Bins: bit-exact against the oracle's FP32 decision on the GPU's own features;
+against the oracle's FP64 features a bin may differ only where the value lies
+within the tolerance of an edge.  Scores of identical bins: bit-exact
+numerators."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2510_15602_gb300 import synth
+from tests.gpu_helpers import edge_distance, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2510_15602_gb300 import qfca
+    assert torch.cuda.is_available()
+    return qfca
+
+
+@pytest.mark.parametrize("C,H,W,dres,B,layout,seed", [
+    (40, 33, 70, 5, 16, 0, 0),
+    (24, 17, 300, 1, 32, 1, 1),     # NHWC, one component removed
+    (80, 20, 21, 12, 16, 0, 2),     # more than 64 channels
+    (16, 9, 9, 0, 8, 0, 3),         # nothing removed: centred features
+])
+def test_residual_features_and_bins(q, C, H, W, dres, B, layout, seed):
+    img = synth.small_case(C, H, W, 2.0, seed=500 + seed)
+    X = img.X
+    mean, V, _, _ = oracle.fit(X, max(dres, 1))
+    V = V[:, :dres]
+    F_o = oracle.residual(X, mean, V)
+    Xd = to_dev(X if layout == 0 else np.ascontiguousarray(X.transpose(1, 2, 0)))
+    out = q.quantize_residual(Xd, (to_dev(mean), to_dev(np.ascontiguousarray(V))), B, layout=layout, want_F=True)
+    torch.cuda.synchronize()
+    F_g = out["F"].cpu().numpy().astype(np.float64)
+    scale = np.abs(X.astype(np.float64) - mean[:, None, None]).max()
+    assert np.abs(F_g - F_o).max() <= 1e-5 * scale
+    qb_f32, lo_f, hi_f = oracle.quantize(F_g, B, fp32_decision=True)
+    bins = out["bins"][:, :, :W].cpu().numpy()
+    np.testing.assert_array_equal(bins, qb_f32)
+    np.testing.assert_array_equal(out["hist"].cpu().numpy().astype(np.uint32), oracle.ref_hist(qb_f32, B))
+    np.testing.assert_array_equal(out["lo"].cpu().numpy(), F_g.reshape(C, -1).min(axis=1).astype(np.float32))
+    np.testing.assert_array_equal(out["hi"].cpu().numpy(), F_g.reshape(C, -1).max(axis=1).astype(np.float32))
+    # against the FP64 features: differences only next to a bin edge
+    qb_o, lo_o, hi_o = oracle.quantize(F_o, B)
+    diff = bins != qb_o
+    if diff.any():
+        assert edge_distance(F_o, lo_o, hi_o, B)[diff].max() <= 2e-5
+
+
+def test_qfca_plus_end_to_end(q):
+    # fit (dres components) + residual over all C = 72 channels + scoring of the 72 planes
+    C, H, W, dres, B, r = 72, 40, 44, 6, 16, 3
+    img = synth.small_case(C, H, W, 2.0, seed=520)
+    Xd = to_dev(img.X)
+    mean, V, ev = q.fit_pca(Xd, dres)
+    out = q.quantize_residual(Xd, (mean, V), B)
+    bins, hist = out["bins"], out["hist"]
+    s_g, num_g = q.score(bins, W, B, r, hist, H * W, want_numer=True)
+    torch.cuda.synchronize()
+    qb = bins[:, :, :W].cpu().numpy()
+    s_o, num_o, _ = oracle.score(qb, B, r, hist.cpu().numpy().astype(np.uint32), H * W)
+    np.testing.assert_array_equal(num_g.cpu().numpy(), num_o)
+    np.testing.assert_allclose(s_g.cpu().numpy(), s_o, rtol=2.0 ** -23, atol=0)
+    ref = oracle.pipeline_plus(img.X, dres, B, r)
+    flips = (qb != ref["q"]).mean()
+    assert flips < 1e-3
+    assert abs(float(s_g.cpu().numpy().mean()) - float(ref["score"].mean())) < 1e-3 * float(ref["score"].mean())
+
+
+def test_residual_rejects_bad_arguments(q):
+    X = torch.zeros(8, 16, 16, device="cuda")
+    mean = torch.zeros(8, dtype=torch.float64, device="cuda")
+    V = torch.zeros(8, 40, dtype=torch.float64, device="cuda")
+    with pytest.raises(RuntimeError):
+        q.quantize_residual(X, (mean, V), 16)  # dres > C
