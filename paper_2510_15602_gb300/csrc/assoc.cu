@@ -95,7 +95,7 @@ size_t assoc_smem(int nt, int B, int r, bool wide) {
     const int span = 2 * r + 1;
     const int rw = (nt + 2 * r + 15) & ~15;
     size_t tab = sizeof(uint32_t) * (B + 1);  // reference (walk) or its exclusive prefix (closed form)
-    if (B <= kClosedMaxB) tab += align_up((wide ? 8 : 4) * (size_t)B * (B + 1), 16) + align_up((size_t)span * span + 1, 16);
+    if (B <= kClosedMaxB) tab += align_up((wide ? 8 : 4) * (size_t)B * (2 * B + 1), 16) + align_up((size_t)span * span + 1, 16);
     return sizeof(uint32_t) * ((size_t)(B + 1) * nt + (size_t)B * nt) + align_up(tab, 16) +
            sizeof(float) * (span * span + 1) + (size_t)ring_rows(r) * rw + 64;
 }
@@ -173,42 +173,46 @@ struct Walk {
     uint32_t cumP, Nloc;
     int Ja;
     ACC a;
-    const uint8_t *Jtab;
+    const uint8_t *Jtab;  // J at N_ref m for the full window size, or NULL
 };
 
-// Fixed-point error of window bin i (count cnt): when the bin's mass lies in a
-// single reference bin J the error is exactly |i - J|; otherwise
-// E_i = (F_i(b) - F_i(a)) / (cnt N_ref) with the closed form above.
+// Fixed-point error of window bin i (count cnt): E_i = (F_i(b) - F_i(a)) /
+// (cnt N_ref) with the closed form above.  For the full window size the two
+// terms of F_i fold into one table, F_i(t) = U[i][J] + |i - J| t with
+// U[i][J] = N T[i][J] - |i - J| N cumRx[J] (N = (2r+1)^2; taken modulo the
+// word size: the difference is exact and non-negative).
 template <typename ACC>
-__device__ __forceinline__ uint32_t bin_error(Walk<ACC> &w, int i, uint32_t cnt, int B, uint32_t Nref, int shift,
-                                              const uint32_t *cumRx, const ACC *Trow, const float *recip) {
+__device__ __forceinline__ uint32_t bin_error(Walk<ACC> &w, int i, uint32_t cnt, int B, uint32_t Nref,
+                                              const uint32_t *cumRx, const ACC *Trow, const ACC *Urow,
+                                              const float *recip) {
     w.cumP += cnt;
     const ACC b = (ACC)Nref * w.cumP;
-    const int Jb = w.Jtab ? (int)w.Jtab[w.cumP] : ref_bin_at<ACC>(cumRx, B, w.Nloc, b);
-    uint32_t fx;
-    if (Jb == w.Ja) {
-        fx = (uint32_t)(i > Jb ? i - Jb : Jb - i) << shift;
+    const int Ja = w.Ja;
+    ACC en;
+    if (w.Jtab) {
+        const int Jb = (int)w.Jtab[w.cumP];
+        en = (Urow[Jb] + (ACC)(i > Jb ? i - Jb : Jb - i) * b) - (Urow[Ja] + (ACC)(i > Ja ? i - Ja : Ja - i) * w.a);
+        w.Ja = Jb;
     } else {
-        const int Ja = w.Ja;
+        const int Jb = ref_bin_at<ACC>(cumRx, B, w.Nloc, b);
         const ACC Fa = (ACC)w.Nloc * Trow[Ja] + (ACC)(i > Ja ? i - Ja : Ja - i) * (w.a - (ACC)w.Nloc * cumRx[Ja]);
         const ACC Fb = (ACC)w.Nloc * Trow[Jb] + (ACC)(i > Jb ? i - Jb : Jb - i) * (b - (ACC)w.Nloc * cumRx[Jb]);
-        const ACC en = Fb - Fa;
-        float e;
-        if (sizeof(ACC) == 4) e = __uint2float_rn((uint32_t)en) * recip[cnt];
-        else e = __ull2float_rn((unsigned long long)en) * recip[cnt];
-        fx = __float2uint_rn(e);
+        en = Fb - Fa;
+        w.Ja = Jb;
     }
-    w.Ja = Jb;
     w.a = b;
-    return fx;
+    float e;
+    if (sizeof(ACC) == 4) e = __uint2float_rn((uint32_t)en) * recip[cnt];
+    else e = __ull2float_rn((unsigned long long)en) * recip[cnt];
+    return __float2uint_rn(e);
 }
 
 // Both windows of a window column in one pass over the bins (one load of the
 // packed counts per bin): V[i] += E_lead,i - E_trail,i.
 template <typename ACC>
 __device__ __forceinline__ void alg1_pair(const uint32_t *hist, int nt, int c, int B, bool lead_on, bool trail_on,
-                                          uint32_t Nl, uint32_t Nt, uint32_t Nint, uint32_t Nref, int shift,
-                                          const uint32_t *cumRx, const ACC *T, const uint8_t *Jtab,
+                                          uint32_t Nl, uint32_t Nt, uint32_t Nint, uint32_t Nref,
+                                          const uint32_t *cumRx, const ACC *T, const ACC *U, const uint8_t *Jtab,
                                           const float *recip, uint32_t *V) {
     Walk<ACC> wl{0u, Nl, 0, (ACC)0, Nl == Nint ? Jtab : nullptr};
     Walk<ACC> wt{0u, Nt, 0, (ACC)0, Nt == Nint ? Jtab : nullptr};
@@ -220,9 +224,10 @@ __device__ __forceinline__ void alg1_pair(const uint32_t *hist, int nt, int c, i
         const uint32_t cl = word & ml, ct = (word >> 16) & mt;
         if (!(cl | ct)) continue;
         const ACC *Trow = T + (size_t)i * (B + 1);
+        const ACC *Urow = U + (size_t)i * B;
         uint32_t delta = 0;
-        if (cl) delta += bin_error<ACC>(wl, i, cl, B, Nref, shift, cumRx, Trow, recip);
-        if (ct) delta -= bin_error<ACC>(wt, i, ct, B, Nref, shift, cumRx, Trow, recip);
+        if (cl) delta += bin_error<ACC>(wl, i, cl, B, Nref, cumRx, Trow, Urow, recip);
+        if (ct) delta -= bin_error<ACC>(wt, i, ct, B, Nref, cumRx, Trow, Urow, recip);
         *v += delta;
     }
 }
@@ -248,12 +253,13 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
     uint32_t *V = hist + (size_t)(B + 1) * nt;                 // [B][nt]
     uint32_t *ref = V + (size_t)B * nt;                        // [B+1]: R_j (walk) or cumRx[x] (closed form)
     unsigned char *tp = reinterpret_cast<unsigned char *>(ref + B + 1);
-    ACC *T = nullptr;
+    ACC *T = nullptr, *U = nullptr;
     uint8_t *Jtab = nullptr;
     if (CLOSED) {
         tp = reinterpret_cast<unsigned char *>(((uintptr_t)tp + 15) & ~(uintptr_t)15);
         T = reinterpret_cast<ACC *>(tp);                       // [B][B+1]
-        Jtab = reinterpret_cast<uint8_t *>(T + (size_t)B * (B + 1));  // [span^2 + 1]
+        U = T + (size_t)B * (B + 1);                           // [B][B]
+        Jtab = reinterpret_cast<uint8_t *>(U + (size_t)B * B);  // [span^2 + 1]
         tp = Jtab + ((span * span + 1 + 15) & ~15);
     }
     float *recip = reinterpret_cast<float *>(((uintptr_t)tp + 15) & ~(uintptr_t)15);  // [span^2 + 1]: 2^s / (n N_ref)
@@ -282,6 +288,10 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
         __syncthreads();
         const uint32_t Nint = (uint32_t)(span * span);
         for (int m = t; m <= span * span; m += nt) Jtab[m] = (uint8_t)ref_bin_at<ACC>(ref, B, Nint, (ACC)Nref * (uint32_t)m);
+        for (int e = t; e < B * B; e += nt) {
+            const int i = e / B, J = e % B;
+            U[e] = (ACC)Nint * T[i * (B + 1) + J] - (ACC)(i > J ? i - J : J - i) * ((ACC)Nint * ref[J]);
+        }
     } else {
         for (int b = t; b < B; b += nt) ref[b] = Rk[b];
     }
@@ -339,8 +349,8 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
             const uint32_t Nl = lead_on ? (uint32_t)(min(H - 1, a + r) - max(0, a - r) + 1) * wcols : 0u;
             const uint32_t Ntr = trail_on ? (uint32_t)(min(H - 1, bq + r) - max(0, bq - r) + 1) * wcols : 0u;
             if (lead_on || trail_on)
-                alg1_pair<ACC>(hist, nt, t, B, lead_on, trail_on, Nl, Ntr, (uint32_t)(span * span), Nref, im.shift,
-                               ref, T, Jtab, recip, V);
+                alg1_pair<ACC>(hist, nt, t, B, lead_on, trail_on, Nl, Ntr, (uint32_t)(span * span), Nref, ref, T, U,
+                               Jtab, recip, V);
         } else if (col_ok) {
             const int a = y + r, bq = y - r - 1;
             if (a >= 0 && a < H) {

@@ -54,7 +54,22 @@ __global__ void __launch_bounds__(kResThreads) k_residual(const __grid_constant_
     float y[kMaxResidual];
 #pragma unroll
     for (int k = 0; k < kMaxResidual; k++) y[k] = 0.0f;
-    for (int c = 0; c < C; c++) {
+    // eight channels' loads in flight at a time (few warps per SM: latency, not bandwidth, is the limit)
+    int c = 0;
+    for (; c + 8 <= C; c += 8) {
+        float xs[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) xs[u] = xval(c + u);
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const float xc = xs[u] - mu[c + u];
+            const float *v = Vs + (size_t)(c + u) * dr;
+#pragma unroll
+            for (int k = 0; k < kMaxResidual; k++)
+                if (k < dr) y[k] = fmaf(xc, v[k], y[k]);
+        }
+    }
+    for (; c < C; c++) {
         const float xc = xval(c) - mu[c];
         const float *v = Vs + (size_t)c * dr;
 #pragma unroll
@@ -62,21 +77,30 @@ __global__ void __launch_bounds__(kResThreads) k_residual(const __grid_constant_
             if (k < dr) y[k] = fmaf(xc, v[k], y[k]);
     }
     const int lane = threadIdx.x & 31;
-    for (int c = 0; c < C; c++) {
-        float f = xval(c) - mu[c];
-        const float *v = Vs + (size_t)c * dr;
+    auto emit = [&](int cc, float xv) {
+        float f = xv - mu[cc];
+        const float *v = Vs + (size_t)cc * dr;
 #pragma unroll
         for (int k = 0; k < kMaxResidual; k++)
             if (k < dr) f = fmaf(-v[k], y[k], f);
         const uint32_t key = f2key(f);
-        if (ok) p.F[(size_t)c * N + px] = f;
+        if (ok) p.F[(size_t)cc * N + px] = f;
         const uint32_t kmin = __reduce_min_sync(0xffffffffu, ok ? key : 0xffffffffu);
         const uint32_t kmax = __reduce_max_sync(0xffffffffu, ok ? key : 0u);
         if (lane == 0) {
-            atomicMin(&mn[c], kmin);
-            atomicMax(&mx[c], kmax);
+            atomicMin(&mn[cc], kmin);
+            atomicMax(&mx[cc], kmax);
         }
+    };
+    c = 0;
+    for (; c + 8 <= C; c += 8) {
+        float xs[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) xs[u] = xval(c + u);
+#pragma unroll
+        for (int u = 0; u < 8; u++) emit(c + u, xs[u]);
     }
+    for (; c < C; c++) emit(c, xval(c));
     __syncthreads();
     for (int c = threadIdx.x; c < C; c += kResThreads) {
         atomicMin(&p.mm[(size_t)c * kKeyStride], mn[c]);
