@@ -298,6 +298,22 @@ typedef struct {
 qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int d, int B, int r,
                            int precision, float *scores, const qfca_batch_outputs *extra, void *stream);
 
+/* qfca_batch_run_plus -- QFCA+ (Sec. 3.3) for nimg feature maps of one shape
+ * stored one after the other in X: each image's PCA fitted with dres
+ * components (Sec. 3.3 fit), its residual features over all C channels (the
+ * input minus its PCA reconstruction, qfca_quantize_residual), each channel
+ * quantised between its image-wide min and max with its global histogram as
+ * reference (Sec. 3.1), and the window EMD averaged over all C channels; each
+ * stage is one launch for the batch (the residual features of the batch are
+ * kept in the workspace: 4 C H W bytes per image).
+ *   scores  device f32 [nimg][H][W].
+ *   extra   as qfca_batch_run with d = dres for mean, V, eigvals and d = C for
+ *           bins [nimg][C][H][pitch], ref_hist [nimg][C][B], lo/hi [nimg][C].
+ * Requires 1 <= dres <= min(C, 32), C <= 512, 2 <= B <= 255, 1 <= r <= 63,
+ * 1 <= nimg <= 4096. */
+qfca_status qfca_batch_run_plus(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int dres, int B, int r,
+                                float *scores, const qfca_batch_outputs *extra, void *stream);
+
 /* One image of an uneven batch (qfca_score_batch). */
 typedef struct {
     const float *X; /* device feature map, C channels in the batch's layout,

@@ -507,7 +507,7 @@ qfca_status qfca_quantize_residual(qfca_ctx *ctx, const float *X, qfca_fmap desc
     uint32_t *mm = (uint32_t *)base;
     float *F = F_out ? F_out : (float *)(base + o_f);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = launch_residual(X, desc.layout, desc.H, desc.W, C, basis->mean, basis->V, dres, F, mm, st);
+    cudaError_t e = launch_residual(X, desc.layout, desc.H, desc.W, C, basis->mean, basis->V, dres, 1, F, mm, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_quantize_residual/residual");
     e = launch_quantize(F, N, desc.H, desc.W, C, 1, B, QFCA_RANGE_IMAGE, mm, nullptr, nullptr, bins, pitch, lo_out,
                         hi_out, ref_hist_out, st);
@@ -605,6 +605,71 @@ qfca_status qfca_median_reference_batch(qfca_ctx *ctx, const qfca_median_image *
     for (int i = 0; i < n; i++)
         jobs[i] = MedianJob{imgs[i].bins, imgs[i].H, imgs[i].W, imgs[i].pitch, imgs[i].r, imgs[i].ref_out};
     return run_median(ctx, jobs.data(), n, d, B, (cudaStream_t)stream);
+}
+
+qfca_status qfca_batch_run_plus(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int dres, int B, int r,
+                                float *scores, const qfca_batch_outputs *extra, void *stream) {
+    qfca_status s = check_ctx(ctx);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if ((s = check_fmap(ctx, X, desc))) return s;
+    if (nimg < 1 || nimg > 4096) return fail(ctx, QFCA_ERR_INVALID_ARG, "nimg = %d outside [1, 4096]", nimg);
+    if (!scores) return fail(ctx, QFCA_ERR_INVALID_ARG, "scores NULL");
+    if (dres < 1 || dres > desc.C || dres > kMaxResidual)
+        return fail(ctx, QFCA_ERR_INVALID_ARG, "dres = %d outside [1, min(C, %d)]", dres, kMaxResidual);
+    if (desc.C > kMaxPlanes) return fail(ctx, QFCA_ERR_INVALID_ARG, "C = %d above %d", desc.C, kMaxPlanes);
+    if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
+    if (r < 1 || 2 * r + 1 > 127) return fail(ctx, QFCA_ERR_INVALID_ARG, "r = %d outside [1, 63]", r);
+    if (extra && extra->bins && (extra->pitch < desc.W || extra->pitch % 16 != 0))
+        return fail(ctx, QFCA_ERR_INVALID_ARG, "extra->pitch %d must be >= W and a multiple of 16", extra->pitch);
+    if (extra && extra->bins && ((uintptr_t)extra->bins & 15) != 0)
+        return fail(ctx, QFCA_ERR_INVALID_ARG, "extra->bins must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    HookScope hs(ctx);
+    const long N = (long)desc.H * desc.W;
+    const int C = desc.C;
+    const int pitch = (extra && extra->bins) ? extra->pitch : (desc.W + 15) / 16 * 16;
+    // workspace: [fit | basis | residual features | keys | bins | hist | lo/hi | score]
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t at = o; o = align_up(o + bytes, 256); return at; };
+    const size_t o_fit = take(fit_workspace_bytes(C, N, dres, nimg));
+    const size_t o_mean = take(sizeof(double) * (size_t)C * nimg);
+    const size_t o_V = take(sizeof(double) * (size_t)C * dres * nimg);
+    const size_t o_ev = take(sizeof(double) * (size_t)dres * nimg);
+    const size_t o_F = take(sizeof(float) * (size_t)C * N * nimg);
+    const size_t o_mm = take(sizeof(uint32_t) * 2 * (size_t)C * kKeyStride * nimg);
+    const size_t o_bins = take((size_t)C * desc.H * pitch * nimg);
+    const size_t o_hist = take(sizeof(uint32_t) * (size_t)C * B * nimg);
+    const size_t o_lohi = take(sizeof(float) * 2 * (size_t)C * nimg);
+    std::vector<ScoreJob> jobs((size_t)nimg);
+    for (int i = 0; i < nimg; i++) jobs[i] = ScoreJob{nullptr, desc.H, desc.W, pitch, r, nullptr, (uint32_t)N, nullptr, nullptr};
+    const size_t o_sc = take(score_jobs_workspace_bytes(jobs.data(), nimg, C));
+    if ((s = ensure_ws(ctx, o, (cudaStream_t)stream))) return s;
+    char *b = (char *)ctx->ws;
+    double *mean = (extra && extra->mean) ? extra->mean : (double *)(b + o_mean);
+    double *V = (extra && extra->V) ? extra->V : (double *)(b + o_V);
+    double *ev = (extra && extra->eigvals) ? extra->eigvals : (double *)(b + o_ev);
+    uint8_t *bins = (extra && extra->bins) ? extra->bins : (uint8_t *)(b + o_bins);
+    uint32_t *hist = (extra && extra->ref_hist) ? extra->ref_hist : (uint32_t *)(b + o_hist);
+    float *lo = (extra && extra->lo) ? extra->lo : (float *)(b + o_lohi);
+    float *hi = (extra && extra->hi) ? extra->hi : (float *)(b + o_lohi) + (size_t)C * nimg;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_fit(X, desc.layout, desc.H, desc.W, C, dres, nimg, mean, V, ev, b + o_fit, ctx->status_dev, st);
+    if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "eigensolver shape C=%d d=%d", C, dres);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run_plus/fit");
+    float *F = (float *)(b + o_F);
+    uint32_t *mm = (uint32_t *)(b + o_mm);
+    e = launch_residual(X, desc.layout, desc.H, desc.W, C, mean, V, dres, nimg, F, mm, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run_plus/residual");
+    e = launch_quantize(F, N, desc.H, desc.W, C, nimg, B, QFCA_RANGE_IMAGE, mm, nullptr, nullptr, bins, pitch, lo, hi,
+                        hist, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run_plus/quantize");
+    for (int i = 0; i < nimg; i++) {
+        jobs[i].bins = bins + (size_t)i * C * desc.H * pitch;
+        jobs[i].ref = hist + (size_t)i * C * B;
+        jobs[i].score = scores + (size_t)i * N;
+    }
+    return run_score(ctx, jobs.data(), nimg, C, B, b + o_sc, st, "qfca_batch_run_plus/score");
 }
 
 qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int d, int B, int r,

@@ -198,10 +198,11 @@ size_t median_jobs_workspace_bytes(const MedianJob *jobs, int n, int d, int B);
 cudaError_t launch_median_jobs(const MedianJob *jobs, int n, int d, int B, void *ws, cudaStream_t st);
 
 // QFCA+ residual features F = (X - mean) - (X - mean) V V^T over all C
-// channels (residual.cu): F [C][N] f32, per-channel min/max keys mm
-// [2 C kKeyStride] (initialised here).  0 <= dres <= kMaxResidual.
+// channels of nimg same-shaped images (residual.cu): per image X [C][N],
+// mean [C], V [C][dres], F [C][N] f32 and min/max keys [2 C kKeyStride]
+// (initialised here), packed image after image.  0 <= dres <= kMaxResidual.
 cudaError_t launch_residual(const float *X, int layout, int H, int W, int C, const double *mean, const double *V,
-                            int dres, float *F, uint32_t *mm, cudaStream_t st);
+                            int dres, int nimg, float *F, uint32_t *mm, cudaStream_t st);
 
 // ------------------------------------------------------------------ context access (api.cu) for serve.cu
 

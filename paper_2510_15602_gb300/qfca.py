@@ -85,6 +85,8 @@ class BatchOutputs(ctypes.Structure):
 
 _lib.qfca_batch_run.argtypes = [_P, _P, _I, Fmap, _I, _I, _I, _I, _P, ctypes.POINTER(BatchOutputs), _P]
 _lib.qfca_batch_run.restype = _I
+_lib.qfca_batch_run_plus.argtypes = [_P, _P, _I, Fmap, _I, _I, _I, _P, ctypes.POINTER(BatchOutputs), _P]
+_lib.qfca_batch_run_plus.restype = _I
 
 
 class Image(ctypes.Structure):
@@ -494,6 +496,39 @@ def batch_run(X: torch.Tensor, d: int, B: int, r: int, precision="bf16", ctx: Co
     fm = Fmap(H, W, C, NCHW)
     ctx.check(_lib.qfca_batch_run(ctx.handle, _ptr(X), nimg, fm, d, B, r, _PREC[precision], _ptr(scores),
                                   ctypes.byref(ext) if ext is not None else None, _P(_stream_ptr(stream))))
+    return (scores, ex) if extras else scores
+
+
+def batch_run_plus(X: torch.Tensor, dres: int, B: int, r: int, ctx: Context | None = None, stream=None,
+                   scores: torch.Tensor | None = None, extras: bool = False):
+    """qfca_batch_run_plus: QFCA+ for a batch X [nimg, C, H, W] (NCHW maps): fit of dres
+    components, residual features of all C channels, per-channel quantisation, EMD over
+    the C planes.  Returns scores [nimg, H, W], or (scores, dict of mean, V, eigvals,
+    bins [nimg, C, H, pitch], ref_hist [nimg, C, B], lo, hi) when ``extras`` is set."""
+    _check_dev(X, "X", torch.float32)
+    if X.dim() != 4:
+        raise ValueError("X must be [nimg, C, H, W]")
+    nimg, C, H, W = (int(v) for v in X.shape)
+    ctx = ctx or default_context(X.device.index)
+    dev = X.device
+    if scores is None:
+        scores = torch.empty(nimg, H, W, dtype=torch.float32, device=dev)
+    ext = None
+    ex = None
+    if extras:
+        pitch = bins_pitch(W)
+        ex = dict(mean=torch.empty(nimg, C, dtype=torch.float64, device=dev),
+                  V=torch.empty(nimg, C, dres, dtype=torch.float64, device=dev),
+                  eigvals=torch.empty(nimg, dres, dtype=torch.float64, device=dev),
+                  bins=torch.empty(nimg, C, H, pitch, dtype=torch.uint8, device=dev),
+                  ref_hist=torch.empty(nimg, C, B, dtype=torch.int32, device=dev),
+                  lo=torch.empty(nimg, C, dtype=torch.float32, device=dev),
+                  hi=torch.empty(nimg, C, dtype=torch.float32, device=dev))
+        ext = BatchOutputs(_ptr(ex["mean"]), _ptr(ex["V"]), _ptr(ex["eigvals"]), _ptr(ex["bins"]), pitch,
+                           _ptr(ex["ref_hist"]), _ptr(ex["lo"]), _ptr(ex["hi"]))
+    fm = Fmap(H, W, C, NCHW)
+    ctx.check(_lib.qfca_batch_run_plus(ctx.handle, _ptr(X), nimg, fm, dres, B, r, _ptr(scores),
+                                       ctypes.byref(ext) if ext is not None else None, _P(_stream_ptr(stream))))
     return (scores, ex) if extras else scores
 
 

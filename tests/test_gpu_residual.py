@@ -84,3 +84,19 @@ def test_residual_rejects_bad_arguments(q):
     V = torch.zeros(8, 40, dtype=torch.float64, device="cuda")
     with pytest.raises(RuntimeError):
         q.quantize_residual(X, (mean, V), 16)  # dres > C
+
+
+def test_batch_run_plus_equals_single_calls(q):
+    C, H, W, dres, B, r = 40, 36, 50, 4, 16, 3
+    X = np.stack([synth.small_case(C, H, W, 2.0, seed=530 + i).X for i in range(3)])
+    Xd = to_dev(X)
+    s_b, ex = q.batch_run_plus(Xd, dres, B, r, extras=True)
+    for i in range(3):
+        mean, V, ev = q.fit_pca(Xd[i], dres)
+        o = q.quantize_residual(Xd[i], (mean, V), B)
+        s1 = q.score(o["bins"], W, B, r, o["hist"], H * W)
+        torch.cuda.synchronize()
+        torch.testing.assert_close(ex["V"][i], V, rtol=0, atol=0)
+        torch.testing.assert_close(ex["bins"][i][:, :, :W], o["bins"][:, :, :W], rtol=0, atol=0)
+        torch.testing.assert_close(ex["ref_hist"][i], o["hist"], rtol=0, atol=0)
+        torch.testing.assert_close(s_b[i], s1, rtol=0, atol=0)
