@@ -232,6 +232,49 @@ __device__ __forceinline__ void alg1_pair(const uint32_t *hist, int nt, int c, i
     }
 }
 
+// The same pass when every window of the warp that is on is full-size: no
+// branch per bin (an empty bin gives en = 0 and recip[0] = 0), so the bins'
+// table lookups pipeline; J at each boundary comes from Jtab and F from U.
+template <typename ACC>
+__device__ __forceinline__ void alg1_pair_full(const uint32_t *hist, int nt, int c, int B, bool lead_on,
+                                               bool trail_on, uint32_t Nref, const ACC *U, const uint8_t *Jtab,
+                                               const float *recip, uint32_t *V) {
+    const uint32_t ml = lead_on ? 0xffffu : 0u, mt = trail_on ? 0xffffu : 0u;
+    uint32_t cl_sum = 0, ct_sum = 0;
+    int JaL = 0, JaT = 0;
+    ACC aL = 0, aT = 0;
+    const uint32_t *h = hist + nt + c;
+    uint32_t *v = V + c;
+    const ACC *Urow = U;
+#pragma unroll 4
+    for (int i = 0; i < B; i++, h += nt, v += nt, Urow += B) {
+        const uint32_t word = *h;
+        const uint32_t cl = word & ml, ct = (word >> 16) & mt;
+        cl_sum += cl;
+        ct_sum += ct;
+        const ACC bL = (ACC)Nref * cl_sum, bT = (ACC)Nref * ct_sum;
+        const int JbL = Jtab[cl_sum], JbT = Jtab[ct_sum];
+        const ACC enL = (Urow[JbL] + (ACC)(i > JbL ? i - JbL : JbL - i) * bL) -
+                        (Urow[JaL] + (ACC)(i > JaL ? i - JaL : JaL - i) * aL);
+        const ACC enT = (Urow[JbT] + (ACC)(i > JbT ? i - JbT : JbT - i) * bT) -
+                        (Urow[JaT] + (ACC)(i > JaT ? i - JaT : JaT - i) * aT);
+        float eL, eT;
+        if (sizeof(ACC) == 4) {
+            eL = __uint2float_rn((uint32_t)enL) * recip[cl];
+            eT = __uint2float_rn((uint32_t)enT) * recip[ct];
+        } else {
+            eL = __ull2float_rn((unsigned long long)enL) * recip[cl];
+            eT = __ull2float_rn((unsigned long long)enT) * recip[ct];
+        }
+        const uint32_t delta = __float2uint_rn(eL) - __float2uint_rn(eT);
+        if (delta) *v += delta;
+        JaL = JbL;
+        JaT = JbT;
+        aL = bL;
+        aT = bT;
+    }
+}
+
 template <typename ACC, bool CLOSED>
 __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocParams p) {
     const int B = p.B, nt = p.nt;
@@ -343,14 +386,20 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
             }
         }
         // ---- Algorithm 1 on the leading window (centre y+r) and the trailing one (centre y-r-1)
-        if (CLOSED && col_ok) {
+        if (CLOSED) {
             const int a = y + r, bq = y - r - 1;
-            const bool lead_on = a >= 0 && a < H, trail_on = bq >= 0;
+            const bool lead_on = col_ok && a >= 0 && a < H, trail_on = col_ok && bq >= 0;
+            const uint32_t Nint = (uint32_t)(span * span);
             const uint32_t Nl = lead_on ? (uint32_t)(min(H - 1, a + r) - max(0, a - r) + 1) * wcols : 0u;
             const uint32_t Ntr = trail_on ? (uint32_t)(min(H - 1, bq + r) - max(0, bq - r) + 1) * wcols : 0u;
-            if (lead_on || trail_on)
-                alg1_pair<ACC>(hist, nt, t, B, lead_on, trail_on, Nl, Ntr, (uint32_t)(span * span), Nref, ref, T, U,
-                               Jtab, recip, V);
+            const bool full = (!lead_on || Nl == Nint) && (!trail_on || Ntr == Nint);
+            const bool warp_full = __all_sync(0xffffffffu, full);
+            if (lead_on || trail_on) {
+                if (warp_full)
+                    alg1_pair_full<ACC>(hist, nt, t, B, lead_on, trail_on, Nref, U, Jtab, recip, V);
+                else
+                    alg1_pair<ACC>(hist, nt, t, B, lead_on, trail_on, Nl, Ntr, Nint, Nref, ref, T, U, Jtab, recip, V);
+            }
         } else if (col_ok) {
             const int a = y + r, bq = y - r - 1;
             if (a >= 0 && a < H) {
