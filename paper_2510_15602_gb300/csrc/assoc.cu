@@ -53,7 +53,21 @@ struct AssocImgP {
 
 struct AssocParams {
     int n, d, B, nt;       // nt: threads per CTA (window columns)
+    int p8;                // histogram bytes: 1 = 8-bit counts, two columns per word (r <= 7)
     AssocImgP img[kMaxBatch];
+};
+
+// Where window column c's packed counts live: 32-bit words per bin row
+// (stride), the word of column c (col), the shift of its 16-bit pair (sh), and
+// within the pair the leading count's mask (lm) and the trailing count's shift
+// (ts).  Layout 16: one word per column, leading | trailing << 16.  Layout 8:
+// two columns per word, each pair leading | trailing << 8 (counts <= 255).
+struct HistView {
+    int stride, col, sh, ts;
+    uint32_t lm;
+    __device__ __forceinline__ HistView(int nt, int c, bool p8)
+        : stride(p8 ? nt / 2 : nt), col(p8 ? c >> 1 : c), sh(p8 ? 16 * (c & 1) : 0), ts(p8 ? 8 : 16),
+          lm(p8 ? 0xffu : 0xffffu) {}
 };
 
 struct FinImg {
@@ -91,12 +105,29 @@ __host__ __device__ inline int ring_rows(int r) { return 4 * r + 4; }
 // above it the two-pointer walk itself runs.
 constexpr int kClosedMaxB = 64;
 
+// Boundary tables of the column-border window sizes (2r+1 rows x cols, cols =
+// r+1 .. 2r), packed one after another; not kept when they would take more than
+// kColTabMax bytes (those windows then search the reference bins).
+constexpr size_t kColTabMax = 8192;
+__host__ __device__ inline int coltab_off(int r, int cols) {
+    const int span = 2 * r + 1;
+    return span * ((cols - 1) * cols / 2 - r * (r + 1) / 2) + (cols - r - 1);
+}
+__host__ __device__ inline size_t coltab_bytes(int r) {
+    const size_t b = (size_t)coltab_off(r, 2 * r + 1);
+    return b <= kColTabMax ? (b + 15) & ~(size_t)15 : 0;
+}
+
 size_t assoc_smem(int nt, int B, int r, bool wide) {
     const int span = 2 * r + 1;
     const int rw = (nt + 2 * r + 15) & ~15;
     size_t tab = sizeof(uint32_t) * (B + 1);  // reference (walk) or its exclusive prefix (closed form)
-    if (B <= kClosedMaxB) tab += align_up((wide ? 8 : 4) * (size_t)B * (2 * B + 1), 16) + align_up((size_t)span * span + 1, 16);
-    return sizeof(uint32_t) * ((size_t)(B + 1) * nt + (size_t)B * nt) + align_up(tab, 16) +
+    size_t coltab = 0;  // images of a launch have radii <= r: the largest of their column tables
+    for (int rr = 1; rr <= r; rr++) coltab = std::max(coltab, coltab_bytes(rr));
+    if (B <= kClosedMaxB)
+        tab += align_up((wide ? 8 : 4) * (size_t)B * (2 * B + 1), 16) + align_up((size_t)span * span + 1, 16) + coltab;
+    const size_t hist_words = (size_t)(B + 1) * (r <= 7 && B <= kClosedMaxB ? nt / 2 : nt);
+    return sizeof(uint32_t) * (hist_words + (size_t)B * nt) + align_up(tab, 16) +
            sizeof(float) * (span * span + 1) + (size_t)ring_rows(r) * rw + 64;
 }
 
@@ -173,7 +204,8 @@ struct Walk {
     uint32_t cumP, Nloc;
     int Ja;
     ACC a;
-    const uint8_t *Jtab;  // J at N_ref m for the full window size, or NULL
+    const uint8_t *Jtab;  // J at N_ref m for this window's size, or NULL (search)
+    bool full;            // full-size window: the folded table U applies
 };
 
 // Fixed-point error of window bin i (count cnt): E_i = (F_i(b) - F_i(a)) /
@@ -188,18 +220,16 @@ __device__ __forceinline__ uint32_t bin_error(Walk<ACC> &w, int i, uint32_t cnt,
     w.cumP += cnt;
     const ACC b = (ACC)Nref * w.cumP;
     const int Ja = w.Ja;
+    const int Jb = w.Jtab ? (int)w.Jtab[w.cumP] : ref_bin_at<ACC>(cumRx, B, w.Nloc, b);
     ACC en;
-    if (w.Jtab) {
-        const int Jb = (int)w.Jtab[w.cumP];
+    if (w.full) {
         en = (Urow[Jb] + (ACC)(i > Jb ? i - Jb : Jb - i) * b) - (Urow[Ja] + (ACC)(i > Ja ? i - Ja : Ja - i) * w.a);
-        w.Ja = Jb;
     } else {
-        const int Jb = ref_bin_at<ACC>(cumRx, B, w.Nloc, b);
         const ACC Fa = (ACC)w.Nloc * Trow[Ja] + (ACC)(i > Ja ? i - Ja : Ja - i) * (w.a - (ACC)w.Nloc * cumRx[Ja]);
         const ACC Fb = (ACC)w.Nloc * Trow[Jb] + (ACC)(i > Jb ? i - Jb : Jb - i) * (b - (ACC)w.Nloc * cumRx[Jb]);
         en = Fb - Fa;
-        w.Ja = Jb;
     }
+    w.Ja = Jb;
     w.a = b;
     float e;
     if (sizeof(ACC) == 4) e = __uint2float_rn((uint32_t)en) * recip[cnt];
@@ -210,18 +240,19 @@ __device__ __forceinline__ uint32_t bin_error(Walk<ACC> &w, int i, uint32_t cnt,
 // Both windows of a window column in one pass over the bins (one load of the
 // packed counts per bin): V[i] += E_lead,i - E_trail,i.
 template <typename ACC>
-__device__ __forceinline__ void alg1_pair(const uint32_t *hist, int nt, int c, int B, bool lead_on, bool trail_on,
+__device__ __forceinline__ void alg1_pair(const uint32_t *hist, int nt, int c, bool p8, int B, bool lead_on, bool trail_on,
                                           uint32_t Nl, uint32_t Nt, uint32_t Nint, uint32_t Nref,
-                                          const uint32_t *cumRx, const ACC *T, const ACC *U, const uint8_t *Jtab,
-                                          const float *recip, uint32_t *V) {
-    Walk<ACC> wl{0u, Nl, 0, (ACC)0, Nl == Nint ? Jtab : nullptr};
-    Walk<ACC> wt{0u, Nt, 0, (ACC)0, Nt == Nint ? Jtab : nullptr};
+                                          const uint32_t *cumRx, const ACC *T, const ACC *U, const uint8_t *JtL,
+                                          const uint8_t *JtT, const float *recip, uint32_t *V) {
+    Walk<ACC> wl{0u, Nl, 0, (ACC)0, JtL, Nl == Nint};
+    Walk<ACC> wt{0u, Nt, 0, (ACC)0, JtT, Nt == Nint};
     const uint32_t ml = lead_on ? 0xffffu : 0u, mt = trail_on ? 0xffffu : 0u;
-    const uint32_t *h = hist + nt + c;
+    const HistView hv(nt, c, p8);
+    const uint32_t *h = hist + hv.stride + hv.col;
     uint32_t *v = V + c;
-    for (int i = 0; i < B; i++, h += nt, v += nt) {
-        const uint32_t word = *h;
-        const uint32_t cl = word & ml, ct = (word >> 16) & mt;
+    for (int i = 0; i < B; i++, h += hv.stride, v += nt) {
+        const uint32_t word = *h >> hv.sh;
+        const uint32_t cl = word & hv.lm & ml, ct = (word >> hv.ts) & hv.lm & mt;
         if (!(cl | ct)) continue;
         const ACC *Trow = T + (size_t)i * (B + 1);
         const ACC *Urow = U + (size_t)i * B;
@@ -236,20 +267,21 @@ __device__ __forceinline__ void alg1_pair(const uint32_t *hist, int nt, int c, i
 // branch per bin (an empty bin gives en = 0 and recip[0] = 0), so the bins'
 // table lookups pipeline; J at each boundary comes from Jtab and F from U.
 template <typename ACC>
-__device__ __forceinline__ void alg1_pair_full(const uint32_t *hist, int nt, int c, int B, bool lead_on,
+__device__ __forceinline__ void alg1_pair_full(const uint32_t *hist, int nt, int c, bool p8, int B, bool lead_on,
                                                bool trail_on, uint32_t Nref, const ACC *U, const uint8_t *Jtab,
                                                const float *recip, uint32_t *V) {
     const uint32_t ml = lead_on ? 0xffffu : 0u, mt = trail_on ? 0xffffu : 0u;
     uint32_t cl_sum = 0, ct_sum = 0;
     int JaL = 0, JaT = 0;
     ACC aL = 0, aT = 0;
-    const uint32_t *h = hist + nt + c;
+    const HistView hv(nt, c, p8);
+    const uint32_t *h = hist + hv.stride + hv.col;
     uint32_t *v = V + c;
     const ACC *Urow = U;
 #pragma unroll 4
-    for (int i = 0; i < B; i++, h += nt, v += nt, Urow += B) {
-        const uint32_t word = *h;
-        const uint32_t cl = word & ml, ct = (word >> 16) & mt;
+    for (int i = 0; i < B; i++, h += hv.stride, v += nt, Urow += B) {
+        const uint32_t word = *h >> hv.sh;
+        const uint32_t cl = word & hv.lm & ml, ct = (word >> hv.ts) & hv.lm & mt;
         cl_sum += cl;
         ct_sum += ct;
         const ACC bL = (ACC)Nref * cl_sum, bT = (ACC)Nref * ct_sum;
@@ -258,6 +290,52 @@ __device__ __forceinline__ void alg1_pair_full(const uint32_t *hist, int nt, int
                         (Urow[JaL] + (ACC)(i > JaL ? i - JaL : JaL - i) * aL);
         const ACC enT = (Urow[JbT] + (ACC)(i > JbT ? i - JbT : JbT - i) * bT) -
                         (Urow[JaT] + (ACC)(i > JaT ? i - JaT : JaT - i) * aT);
+        float eL, eT;
+        if (sizeof(ACC) == 4) {
+            eL = __uint2float_rn((uint32_t)enL) * recip[cl];
+            eT = __uint2float_rn((uint32_t)enT) * recip[ct];
+        } else {
+            eL = __ull2float_rn((unsigned long long)enL) * recip[cl];
+            eT = __ull2float_rn((unsigned long long)enT) * recip[ct];
+        }
+        const uint32_t delta = __float2uint_rn(eL) - __float2uint_rn(eT);
+        if (delta) *v += delta;
+        JaL = JbL;
+        JaT = JbT;
+        aL = bL;
+        aT = bT;
+    }
+}
+
+// The branch-free pass for warps whose windows all have a boundary table but are
+// not all full-size (the column borders): F from T and cumRx for each window's
+// own size N.  A window that is off passes N = 0 and any table (F stays 0).
+template <typename ACC>
+__device__ __forceinline__ void alg1_pair_tform(const uint32_t *hist, int nt, int c, bool p8, int B, bool lead_on,
+                                                bool trail_on, uint32_t NL, uint32_t NT, const uint8_t *JtL,
+                                                const uint8_t *JtT, uint32_t Nref, const uint32_t *cumRx,
+                                                const ACC *T, const float *recip, uint32_t *V) {
+    const uint32_t ml = lead_on ? 0xffffu : 0u, mt = trail_on ? 0xffffu : 0u;
+    uint32_t cl_sum = 0, ct_sum = 0;
+    int JaL = 0, JaT = 0;
+    ACC aL = 0, aT = 0;
+    const HistView hv(nt, c, p8);
+    const uint32_t *h = hist + hv.stride + hv.col;
+    uint32_t *v = V + c;
+    const ACC *Trow = T;
+    auto F = [&](int i, int J, ACC t, uint32_t N) -> ACC {
+        return (ACC)N * Trow[J] + (ACC)(i > J ? i - J : J - i) * (t - (ACC)N * cumRx[J]);
+    };
+#pragma unroll 4
+    for (int i = 0; i < B; i++, h += hv.stride, v += nt, Trow += B + 1) {
+        const uint32_t word = *h >> hv.sh;
+        const uint32_t cl = word & hv.lm & ml, ct = (word >> hv.ts) & hv.lm & mt;
+        cl_sum += cl;
+        ct_sum += ct;
+        const ACC bL = (ACC)Nref * cl_sum, bT = (ACC)Nref * ct_sum;
+        const int JbL = JtL[cl_sum], JbT = JtT[ct_sum];
+        const ACC enL = F(i, JbL, bL, NL) - F(i, JaL, aL, NL);
+        const ACC enT = F(i, JbT, bT, NT) - F(i, JaT, aT, NT);
         float eL, eT;
         if (sizeof(ACC) == 4) {
             eL = __uint2float_rn((uint32_t)enL) * recip[cl];
@@ -292,18 +370,21 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
     const int rw = (nt + 2 * r + 15) & ~15; // ring row width
     const int RR = ring_rows(r);
 
-    uint32_t *hist = reinterpret_cast<uint32_t *>(smem_raw);  // [B+1][nt], row 0: outside pixels
-    uint32_t *V = hist + (size_t)(B + 1) * nt;                 // [B][nt]
+    const bool p8 = CLOSED && p.p8;
+    const int hstride = p8 ? nt / 2 : nt;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem_raw);  // [B+1][hstride], row 0: outside pixels (layout 16)
+    uint32_t *V = hist + (size_t)(B + 1) * hstride;            // [B][nt]
     uint32_t *ref = V + (size_t)B * nt;                        // [B+1]: R_j (walk) or cumRx[x] (closed form)
     unsigned char *tp = reinterpret_cast<unsigned char *>(ref + B + 1);
     ACC *T = nullptr, *U = nullptr;
-    uint8_t *Jtab = nullptr;
+    uint8_t *Jtab = nullptr, *JC = nullptr;
     if (CLOSED) {
         tp = reinterpret_cast<unsigned char *>(((uintptr_t)tp + 15) & ~(uintptr_t)15);
         T = reinterpret_cast<ACC *>(tp);                       // [B][B+1]
         U = T + (size_t)B * (B + 1);                           // [B][B]
         Jtab = reinterpret_cast<uint8_t *>(U + (size_t)B * B);  // [span^2 + 1]
-        tp = Jtab + ((span * span + 1 + 15) & ~15);
+        JC = Jtab + ((span * span + 1 + 15) & ~15);             // column-border tables (coltab_bytes(r))
+        tp = JC + coltab_bytes(r);
     }
     float *recip = reinterpret_cast<float *>(((uintptr_t)tp + 15) & ~(uintptr_t)15);  // [span^2 + 1]: 2^s / (n N_ref)
     uint8_t *ring = reinterpret_cast<uint8_t *>(recip + span * span + 1);  // [RR][rw]: bin+1, 0 outside
@@ -312,7 +393,7 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
     const uint8_t *plane = im.bins + (size_t)k * H * im.pitch;
     const uint32_t Nref = im.Nref;
     const uint32_t *Rk = im.ref + (size_t)k * B;
-    for (int e = t; e < (B + 1) * nt + B * nt; e += nt) hist[e] = 0;  // hist and V
+    for (int e = t; e < (B + 1) * hstride + B * nt; e += nt) hist[e] = 0;  // hist and V
     if (CLOSED) {
         if (t == 0) {
             uint32_t acc = 0;
@@ -334,6 +415,15 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
         for (int e = t; e < B * B; e += nt) {
             const int i = e / B, J = e % B;
             U[e] = (ACC)Nint * T[i * (B + 1) + J] - (ACC)(i > J ? i - J : J - i) * ((ACC)Nint * ref[J]);
+        }
+        if (coltab_bytes(r)) {
+            const int ncol_tab = coltab_off(r, 2 * r + 1);
+            for (int e = t; e < ncol_tab; e += nt) {
+                int cols = r + 1;
+                while (coltab_off(r, cols + 1) <= e) cols++;
+                const int m = e - coltab_off(r, cols);
+                JC[e] = (uint8_t)ref_bin_at<ACC>(ref, B, (uint32_t)(span * cols), (ACC)Nref * (uint32_t)m);
+            }
         }
     } else {
         for (int b = t; b < B; b += nt) ref[b] = Rk[b];
@@ -378,11 +468,24 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
             const uint8_t *ra = ring + (size_t)((((y + 2 * r) % RR) + RR) % RR) * rw + t;
             const uint8_t *rb = ring + (size_t)((((y - 1) % RR) + RR) % RR) * rw + t;
             const uint8_t *rc = ring + (size_t)((((y - 2 * r - 2) % RR) + RR) % RR) * rw + t;
+            if (p8) {
+                // 8-bit counts: outside pixels are not counted (no carry can reach the
+                // neighbouring column); (2r+2)(2r+1) <= 240 keeps every count below 256
+                uint32_t *hc = hist + (t >> 1);
+                const int sh = 16 * (t & 1);
 #pragma unroll 4
-            for (int u = 0; u < span; u++) {
-                atomicAdd(&hist[(size_t)ra[u] * nt + t], 1u);
-                atomicAdd(&hist[(size_t)rb[u] * nt + t], 0xffffu);  // -1 low half, +1 high half
-                atomicAdd(&hist[(size_t)rc[u] * nt + t], 0xffff0000u);  // -1 high half
+                for (int u = 0; u < span; u++) {
+                    if (ra[u]) atomicAdd(&hc[(size_t)ra[u] * hstride], 1u << sh);
+                    if (rb[u]) atomicAdd(&hc[(size_t)rb[u] * hstride], 0xffu << sh);  // leading -1, trailing +1
+                    if (rc[u]) atomicAdd(&hc[(size_t)rc[u] * hstride], 0xffffff00u << sh);  // trailing -1
+                }
+            } else {
+#pragma unroll 4
+                for (int u = 0; u < span; u++) {
+                    atomicAdd(&hist[(size_t)ra[u] * nt + t], 1u);
+                    atomicAdd(&hist[(size_t)rb[u] * nt + t], 0xffffu);  // -1 low half, +1 high half
+                    atomicAdd(&hist[(size_t)rc[u] * nt + t], 0xffff0000u);  // -1 high half
+                }
             }
         }
         // ---- Algorithm 1 on the leading window (centre y+r) and the trailing one (centre y-r-1)
@@ -393,12 +496,26 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
             const uint32_t Nl = lead_on ? (uint32_t)(min(H - 1, a + r) - max(0, a - r) + 1) * wcols : 0u;
             const uint32_t Ntr = trail_on ? (uint32_t)(min(H - 1, bq + r) - max(0, bq - r) + 1) * wcols : 0u;
             const bool full = (!lead_on || Nl == Nint) && (!trail_on || Ntr == Nint);
+            // boundary table of each window: full size, a column-border size (all 2r+1 rows), or none
+            auto table = [&](uint32_t N, int rows) -> const uint8_t * {
+                if (N == Nint) return Jtab;
+                const int cols = (int)wcols;
+                if (rows == span && cols > r && cols < span && coltab_bytes(r)) return JC + coltab_off(r, cols);
+                return nullptr;
+            };
+            const int rows_l = lead_on ? min(H - 1, a + r) - max(0, a - r) + 1 : 0;
+            const int rows_t = trail_on ? min(H - 1, bq + r) - max(0, bq - r) + 1 : 0;
+            const uint8_t *jl = lead_on ? table(Nl, rows_l) : Jtab;
+            const uint8_t *jt = trail_on ? table(Ntr, rows_t) : Jtab;
             const bool warp_full = __all_sync(0xffffffffu, full);
+            const bool warp_tab = __all_sync(0xffffffffu, jl != nullptr && jt != nullptr);
             if (lead_on || trail_on) {
                 if (warp_full)
-                    alg1_pair_full<ACC>(hist, nt, t, B, lead_on, trail_on, Nref, U, Jtab, recip, V);
+                    alg1_pair_full<ACC>(hist, nt, t, p8, B, lead_on, trail_on, Nref, U, Jtab, recip, V);
+                else if (warp_tab)
+                    alg1_pair_tform<ACC>(hist, nt, t, p8, B, lead_on, trail_on, Nl, Ntr, jl, jt, Nref, ref, T, recip, V);
                 else
-                    alg1_pair<ACC>(hist, nt, t, B, lead_on, trail_on, Nl, Ntr, Nint, Nref, ref, T, U, Jtab, recip, V);
+                    alg1_pair<ACC>(hist, nt, t, p8, B, lead_on, trail_on, Nl, Ntr, Nint, Nref, ref, T, U, jl, jt, recip, V);
             }
         } else if (col_ok) {
             const int a = y + r, bq = y - r - 1;
@@ -585,6 +702,7 @@ cudaError_t launch_assoc_jobs(const AssocJob *jobs, int n, int d, int B, void *w
         ap.d = d;
         ap.B = B;
         ap.nt = nt;
+        ap.p8 = (closed && rmax <= 7) ? 1 : 0;
         long ctas = 0;
         for (int i = 0; i < m; i++) {
             const AssocJob &j = jobs[i0 + i];
