@@ -25,11 +25,13 @@
 //      Sigma_ij = 2^(e_i + e_j) T_ij 2^-40 / N - mu_i mu_j.
 //
 // One CTA (512 threads) = one 128x128 tile of the upper triangle x one range
-// of pixels; per 64-pixel sub-chunk all threads convert both channel blocks
-// into the 128-byte-swizzled K-major layout (channels are rows, pixels are K:
-// NCHW is already K-major), one thread issues the 40 MMAs (10 digit pairs x 4
-// K-steps of 16) and commits to an mbarrier (bounded wait); while the tensor
-// cores run, every thread fetches the next sub-chunk's features into registers.
+// of pixels; per 32-pixel sub-chunk all threads convert both channel blocks
+// into the 64-byte-swizzled K-major layout (channels are rows, pixels are K:
+// NCHW is already K-major) of one of two operand buffers, one thread issues
+// the sub-chunk's 12 MMAs (the 10 digit pairs stacked into 6 per K-step of 16)
+// and commits to that buffer's mbarrier; the conversion of the next sub-chunk
+// (into the other buffer) overlaps the tensor cores, and every thread fetches
+// the features after next into registers meanwhile.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -41,7 +43,10 @@ namespace qfca {
 namespace {
 
 constexpr int kTB = 128;         // channels per tile side
-constexpr int kSub = 64;         // pixels per sub-chunk (one 128-B swizzle row of BF16)
+constexpr int kSub = 32;         // pixels per sub-chunk (one 64-B swizzle row of BF16)
+constexpr int kSliceBytes = 128 * kSub * 2;  // one digit slice of a 128-channel block
+constexpr int kBlockBytes = 4 * kSliceBytes; // the four slices of one block
+constexpr int kStageBytes = 128 * kSub * 4;  // one block's FP32 features of a sub-chunk
 constexpr int kWin = 256;        // pixels per exact accumulation window
 constexpr int kThreads = 512;
 constexpr int kSlices = 4;
@@ -108,94 +113,97 @@ __device__ __forceinline__ void digits4(float y, float &d0, float &d1, float &d2
     d3 = rint_exact(t);
 }
 
+// 64-byte swizzle (rows of 32 BF16 pixels): 16-B chunk c of row r lands at
+// chunk c ^ ((r >> 1) & 3).
 __device__ __forceinline__ uint32_t swz(int row, int chunk16) {
-    return (uint32_t)(row * 128 + ((chunk16 ^ (row & 7)) << 4));
+    return (uint32_t)(row * 64 + ((chunk16 ^ ((row >> 1) & 3)) << 4));
 }
 
-// Load one operand block (128 channels starting at c0) of pixels [q0, q0+64)
-// into registers: units u = threadIdx.x + i * kThreads (i = 0, 1), each one
-// channel row and 8 consecutive pixels.
-__device__ __forceinline__ void load_block(const float *__restrict__ X, int layout, int vec_ok, int C, long N, int c0,
-                                           long q0, long q1, float (&v)[2][8]) {
+// Stage one operand block (128 channels starting at c0) of pixels [q0, q0+32)
+// into shared memory as FP32 [128][32]: thread t copies channel row t >> 2,
+// 8 consecutive pixels -- two asynchronous 16-byte copies when the row is
+// 16-byte aligned and complete, else plain loads and stores (zero outside).
+__device__ __forceinline__ void stage_block(const float *__restrict__ X, int layout, int vec_ok, int C, long N, int c0,
+                                            long q0, long q1, float *stage) {
+    const int row = threadIdx.x >> 2, g = threadIdx.x & 3;
+    const int c = c0 + row;
+    const long p = q0 + g * 8;
+    float *dst = stage + row * kSub + g * 8;
+    if (vec_ok && c < C && p + 8 <= q1) {
+        const uint32_t d = tc::smem_u32(dst);
+        tc::cp_async16(d, X + (long)c * N + p);
+        tc::cp_async16(d + 16, X + (long)c * N + p + 4);
+    } else {
 #pragma unroll
-    for (int i = 0; i < 2; i++) {
-        const int u = threadIdx.x + i * kThreads;
-        const int row = u >> 3, g = u & 7;
-        const int c = c0 + row;
-        const long p = q0 + g * 8;
-        if (vec_ok && c < C && p + 8 <= q1) {
-            const float4 a = __ldg(reinterpret_cast<const float4 *>(X + (long)c * N + p));
-            const float4 b = __ldg(reinterpret_cast<const float4 *>(X + (long)c * N + p + 4));
-            v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z; v[i][3] = a.w;
-            v[i][4] = b.x; v[i][5] = b.y; v[i][6] = b.z; v[i][7] = b.w;
-        } else {
-#pragma unroll
-            for (int e = 0; e < 8; e++) {
-                const long pe = p + e;
-                v[i][e] = (c < C && pe < q1) ? (layout == QFCA_NCHW ? X[(long)c * N + pe] : X[pe * C + c]) : 0.0f;
-            }
+        for (int e = 0; e < 8; e++) {
+            const long pe = p + e;
+            dst[e] = (c < C && pe < q1) ? (layout == QFCA_NCHW ? X[(long)c * N + pe] : X[pe * C + c]) : 0.0f;
         }
     }
 }
 
-// Convert the loaded block into 4 digit slices (K-major, 128-B swizzle);
+// This thread's 8 values of a staged block (the ones it staged itself).
+__device__ __forceinline__ void read_stage(const float *stage, float (&v)[8]) {
+    const int row = threadIdx.x >> 2, g = threadIdx.x & 3;
+    const float4 a = *reinterpret_cast<const float4 *>(stage + row * kSub + g * 8);
+    const float4 b = *reinterpret_cast<const float4 *>(stage + row * kSub + g * 8 + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+// Convert the loaded block into 4 digit slices (K-major, 64-B swizzle);
 // optionally accumulate per-row digit sums and the level-4 diagonal terms.
-__device__ __forceinline__ void convert_block(const float (&v)[2][8], int C, int c0, const float *__restrict__ scale,
+__device__ __forceinline__ void convert_block(const float (&v)[8], int C, int c0, const float *__restrict__ scale,
                                               uint8_t *slices, int *__restrict__ dsum /* [4][128] or null */,
                                               unsigned long long *__restrict__ dsq /* [128] or null */) {
+    const int row = threadIdx.x >> 2, g = threadIdx.x & 3;
+    const int c = c0 + row;
+    const float s = c < C ? scale[c] : 0.0f;
+    float dd[kSlices][8];
 #pragma unroll
-    for (int i = 0; i < 2; i++) {
-        const int u = threadIdx.x + i * kThreads;
-        const int row = u >> 3, g = u & 7;
-        const int c = c0 + row;
-        const float s = c < C ? scale[c] : 0.0f;
-        float dd[kSlices][8];
+    for (int e = 0; e < 8; e++) digits4(__fmul_rn(v[e], s), dd[0][e], dd[1][e], dd[2][e], dd[3][e]);
 #pragma unroll
-        for (int e = 0; e < 8; e++) digits4(__fmul_rn(v[i][e], s), dd[0][e], dd[1][e], dd[2][e], dd[3][e]);
-#pragma unroll
-        for (int sl = 0; sl < kSlices; sl++) {
-            uint4 pk;
-            pk.x = tc::pack_bf16x2(dd[sl][0], dd[sl][1]);
-            pk.y = tc::pack_bf16x2(dd[sl][2], dd[sl][3]);
-            pk.z = tc::pack_bf16x2(dd[sl][4], dd[sl][5]);
-            pk.w = tc::pack_bf16x2(dd[sl][6], dd[sl][7]);
-            *reinterpret_cast<uint4 *>(slices + sl * (kTB * 128) + swz(row, g)) = pk;
-            if (dsum) {
-                const float t = ((dd[sl][0] + dd[sl][1]) + (dd[sl][2] + dd[sl][3])) +
-                                ((dd[sl][4] + dd[sl][5]) + (dd[sl][6] + dd[sl][7]));
-                atomicAdd(&dsum[sl * kTB + row], (int)t);
-            }
+    for (int sl = 0; sl < kSlices; sl++) {
+        uint4 pk;
+        pk.x = tc::pack_bf16x2(dd[sl][0], dd[sl][1]);
+        pk.y = tc::pack_bf16x2(dd[sl][2], dd[sl][3]);
+        pk.z = tc::pack_bf16x2(dd[sl][4], dd[sl][5]);
+        pk.w = tc::pack_bf16x2(dd[sl][6], dd[sl][7]);
+        *reinterpret_cast<uint4 *>(slices + sl * kSliceBytes + swz(row, g)) = pk;
+        if (dsum) {
+            const float t = ((dd[sl][0] + dd[sl][1]) + (dd[sl][2] + dd[sl][3])) +
+                            ((dd[sl][4] + dd[sl][5]) + (dd[sl][6] + dd[sl][7]));
+            atomicAdd(&dsum[sl * kTB + row], (int)t);
         }
-        if (dsq) {
-            int t4 = 0;  // exact: |2 d1 d3 + d2^2| <= 3 * 2^12 per pixel
+    }
+    if (dsq) {
+        int t4 = 0;  // exact: |2 d1 d3 + d2^2| <= 3 * 2^12 per pixel
 #pragma unroll
-            for (int e = 0; e < 8; e++) {
-                const int d1 = (int)dd[1][e], d2 = (int)dd[2][e], d3 = (int)dd[3][e];
-                t4 += 2 * d1 * d3 + d2 * d2;
-            }
-            atomicAdd(&dsq[row], (unsigned long long)(long long)t4);
+        for (int e = 0; e < 8; e++) {
+            const int d1 = (int)dd[1][e], d2 = (int)dd[2][e], d3 = (int)dd[3][e];
+            t4 += 2 * d1 * d3 + d2 * d2;
         }
+        atomicAdd(&dsq[row], (unsigned long long)(long long)t4);
     }
 }
 
-// The level sums of one 64-pixel sub-chunk: A_L += sum_{i+j=L} D_i E_j^T for
+// The level sums of one 32-pixel sub-chunk: A_L += sum_{i+j=L} D_i E_j^T for
 // L = 0..3 (D: the A block's digit slices, E: the B block's).  The B slices
-// lie back to back in shared memory (128 rows each, the same 1024-B row-group
+// lie back to back in shared memory (128 rows each, the same 512-B row-group
 // stride), so slices j..j+1 form one 256-row operand: A_i times slices
 // j0..j0+1 fills the accumulators of levels i+j0 and i+j0+1 (TMEM columns
 // 128 (i+j0) .. +256) in one N = 256 instruction.  Per K-step: A_0 x E_0..1
 // and A_0 x E_2..3 (issued first: they start all four levels of a window),
 // A_1 x E_0..1, A_1 x E_2, A_2 x E_0..1, A_3 x E_0 -- 6 MMAs instead of 10.
 __device__ __forceinline__ void issue_level_mmas(uint32_t tmem, uint32_t a_addr, uint32_t b_addr, bool first) {
-    const uint64_t ad0 = tc::sdesc_kmajor_sw128(a_addr), bd0 = tc::sdesc_kmajor_sw128(b_addr);
+    const uint64_t ad0 = tc::sdesc_kmajor_sw64(a_addr), bd0 = tc::sdesc_kmajor_sw64(b_addr);
     constexpr uint32_t id256 = tc::idesc_bf16_f32(kTB, 256), id128 = tc::idesc_bf16_f32(kTB, 128);
-    constexpr int kSl = kTB * 128;  // bytes of one digit slice
     const uint32_t acc0 = first ? 0u : 1u;
 #pragma unroll
-    for (int ks = 0; ks < 4; ks++) {
+    for (int ks = 0; ks < kSub / 16; ks++) {
         // descriptors differ only in the start-address field (bytes >> 4)
-        auto A = [&](int i) { return ad0 + (uint64_t)((i * kSl + ks * 32) >> 4); };
-        auto E = [&](int j) { return bd0 + (uint64_t)((j * kSl + ks * 32) >> 4); };
+        auto A = [&](int i) { return ad0 + (uint64_t)((i * kSliceBytes + ks * 32) >> 4); };
+        auto E = [&](int j) { return bd0 + (uint64_t)((j * kSliceBytes + ks * 32) >> 4); };
         const uint32_t a0 = ks == 0 ? acc0 : 1u;
         tc::mma_bf16_ss(tmem + 0 * kTB, A(0), E(0), id256, a0);  // levels 0, 1
         tc::mma_bf16_ss(tmem + 2 * kTB, A(0), E(2), id256, a0);  // levels 2, 3
@@ -207,7 +215,10 @@ __device__ __forceinline__ void issue_level_mmas(uint32_t tmem, uint32_t a_addr,
 }
 
 // Grid: images * n_pairs * n_split CTAs.  Per image: Gint [C][C] int64 (upper
-// tiles accumulated), Dsum [4][C] int64, scale [C].
+// tiles accumulated), Dsum [4][C] int64, scale [C].  Two operand buffers: the
+// threads convert sub-chunk k into buffer k & 1 while the tensor cores work on
+// sub-chunk k - 1 from the other buffer; a buffer is rewritten only after the
+// MMAs that read it have completed (one mbarrier per buffer, bounded waits).
 __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ FitParams p,
                                                       const float *__restrict__ scale,
                                                       unsigned long long *__restrict__ Gint,
@@ -215,11 +226,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
                                                       int *__restrict__ status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = tc::align_smem<1024>(smem_raw);
-    uint8_t *As = smem;                                // 4 slices x 16 KB
-    uint8_t *Bs = smem + kSlices * kTB * 128;          // 4 slices x 16 KB
-    uint64_t *bar = (uint64_t *)(Bs + kSlices * kTB * 128);
-    uint32_t *tmem_slot = (uint32_t *)(bar + 1);
-    unsigned long long *dsq = (unsigned long long *)(tmem_slot + 4);  // [128] (8-B aligned: bar is)
+    uint8_t *As[2] = {smem, smem + 2 * kBlockBytes};               // 4 slices x 8 KB each
+    uint8_t *Bs[2] = {smem + kBlockBytes, smem + 3 * kBlockBytes};
+    float *stg = (float *)(smem + 4 * kBlockBytes);                 // [2 stages][2 blocks][128][32] FP32
+    uint64_t *bar = (uint64_t *)(smem + 4 * kBlockBytes + 4 * kStageBytes);  // [2]
+    uint32_t *tmem_slot = (uint32_t *)(bar + 2);
+    unsigned long long *dsq = (unsigned long long *)(tmem_slot + 2);  // [128] (8-B aligned)
     int *dsum = (int *)(dsq + kTB);                                    // [4][128]
 
     const long cta = blockIdx.x;
@@ -245,7 +257,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(bar, 1);
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
         tc::fence_mbar_init();
     }
     for (int i = tid; i < kSlices * kTB; i += kThreads) dsum[i] = 0;
@@ -254,45 +267,74 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t a_base = tc::smem_u32(As);
-    const uint32_t b_base = diag ? a_base : tc::smem_u32(Bs);
 
     long long tot[32];
 #pragma unroll
     for (int j = 0; j < 32; j++) tot[j] = 0;
     const int q = warp & 3, cg4 = warp >> 2;  // TMEM lane quarter, 32-column group
-    uint32_t phase = 0;
+    uint32_t phase[2] = {0u, 0u};
+    bool pending[2] = {false, false};         // MMAs reading the buffer not yet waited for
     bool failed = false;
     int in_win = 0;
+    auto wait_buf = [&](int bsel) -> bool {
+        if (!pending[bsel]) return true;
+        const bool ok = tc::mbar_wait(&bar[bsel], phase[bsel], kWaitTries);
+        phase[bsel] ^= 1u;
+        pending[bsel] = false;
+        return ok;
+    };
 
-    float va[2][8], vb[2][8];
-    load_block(X, layout, vec_ok, C, N, ti * kTB, p0, p1, va);
-    if (!diag) load_block(X, layout, vec_ok, C, N, tj * kTB, p0, p1, vb);
-    for (long q0 = p0; q0 < p1; q0 += kSub) {
-        convert_block(va, C, ti * kTB, scale, As, diag ? dsum : nullptr, diag ? dsq : nullptr);
-        if (!diag) convert_block(vb, C, tj * kTB, scale, Bs, nullptr, nullptr);
+    // features stream into two FP32 stages, two sub-chunks ahead of the conversion
+    auto stage = [&](int s, long q0) {
+        float *sa = stg + (size_t)s * 2 * kTB * kSub;
+        if (q0 < p1) {
+            stage_block(X, layout, vec_ok, C, N, ti * kTB, q0, p1, sa);
+            if (!diag) stage_block(X, layout, vec_ok, C, N, tj * kTB, q0, p1, sa + kTB * kSub);
+        }
+        tc::cp_async_commit();  // one group per sub-chunk (possibly empty)
+    };
+    stage(0, p0);
+    stage(1, p0 + kSub);
+    int kk = 0;
+    for (long q0 = p0; q0 < p1; q0 += kSub, kk++) {
+        const int bsel = kk & 1;
+        // the MMAs of sub-chunk kk-2 read this operand buffer
+        if (__syncthreads_or(!wait_buf(bsel))) {
+            failed = true;
+            break;
+        }
+        tc::cp_async_wait<1>();  // this thread's copies of sub-chunk kk have landed (kk+1 may be in flight)
+        {
+            const float *sa = stg + (size_t)bsel * 2 * kTB * kSub;
+            float v[8];
+            read_stage(sa, v);
+            convert_block(v, C, ti * kTB, scale, As[bsel], diag ? dsum : nullptr, diag ? dsq : nullptr);
+            if (!diag) {
+                read_stage(sa + kTB * kSub, v);
+                convert_block(v, C, tj * kTB, scale, Bs[bsel], nullptr, nullptr);
+            }
+        }
+        // each thread reads back only what it staged itself, so the stage can be
+        // refilled (sub-chunk kk+2) right away
+        stage(bsel, q0 + 2 * kSub);
         tc::fence_proxy_async_smem();
         tc::tc_fence_before();
         __syncthreads();
         if (tid == 0) {
             tc::tc_fence_after();
-            issue_level_mmas(tmem, a_base, b_base, in_win == 0);
-            tc::mma_commit(bar);
+            const uint32_t a_addr = tc::smem_u32(As[bsel]);
+            issue_level_mmas(tmem, a_addr, diag ? a_addr : tc::smem_u32(Bs[bsel]), in_win == 0);
+            tc::mma_commit(&bar[bsel]);
         }
-        // the next sub-chunk's features are fetched while the tensor cores run
-        if (q0 + kSub < p1) {
-            load_block(X, layout, vec_ok, C, N, ti * kTB, q0 + kSub, p1, va);
-            if (!diag) load_block(X, layout, vec_ok, C, N, tj * kTB, q0 + kSub, p1, vb);
-        }
-        const bool ok = tc::mbar_wait(bar, phase, kWaitTries);
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
+        pending[bsel] = true;
         in_win += kSub;
         if (in_win >= kWin || q0 + kSub >= p1) {
-            // drain the window's exact level sums into int64
+            // drain the window's exact level sums into int64 (the commit of this
+            // sub-chunk covers every earlier MMA of the window)
+            if (__syncthreads_or(!wait_buf(bsel))) {
+                failed = true;
+                break;
+            }
             tc::tc_fence_after();
 #pragma unroll
             for (int L = 0; L < 4; L++) {
@@ -313,11 +355,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
             tc::tc_fence_before();
             in_win = 0;
         }
-        __syncthreads();  // operand buffers and accumulators free for the next sub-chunk
     }
     if (failed) {
         if (tid == 0) atomicOr(status, kStatusMmaTimeout);
-        tc::mbar_wait(bar, phase ^ 1u, kWaitTries);
+        // MMAs still in flight finish (bounded) before the accumulators are freed
+        wait_buf(0);
+        wait_buf(1);
     } else {
         const int c1 = ti * kTB + 32 * q + lane;
         if (c1 < C) {
@@ -327,6 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
                 if (c2 < C && tot[j] != 0) atomicAdd(&Gint[(long)c1 * C + c2], (unsigned long long)tot[j]);
             }
         }
+        __syncthreads();  // dsum / dsq complete
         if (diag) {
             for (int i = tid; i < kSlices * kTB; i += kThreads) {
                 const int sl = i / kTB, row = i % kTB, c = ti * kTB + row;
@@ -338,6 +382,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
             }
         }
     }
+    tc::cp_async_wait<0>();  // no copy into this CTA's shared memory outlives it
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -414,7 +459,8 @@ static GramPlan gram_plan(int C, int nimg) {
     g.off_G = take(sizeof(unsigned long long) * (size_t)C * C * nimg);
     g.off_D = take(sizeof(unsigned long long) * (size_t)kSlices * C * nimg);
     g.total = o;
-    g.smem = 1024 + 2 * kSlices * kTB * 128 + 64 + sizeof(int) * kSlices * kTB + sizeof(unsigned long long) * kTB;
+    g.smem = 1024 + 4 * (size_t)kBlockBytes + 4 * (size_t)kStageBytes + 64 + sizeof(int) * kSlices * kTB +
+             sizeof(unsigned long long) * kTB;
     return g;
 }
 

@@ -84,6 +84,15 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
     return d;
 }
 
+// Asynchronous 16-byte global -> shared copy (bypassing L1), its group commit
+// and the wait for all but the newest `n` groups.
+__device__ __forceinline__ void cp_async16(uint32_t dst_smem, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst_smem), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int n>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory"); }
+
 // Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows of
 // 64 B, 8-row atoms 512 B apart (stride byte offset), base 512-B aligned.
 __device__ __forceinline__ uint64_t sdesc_kmajor_sw64(uint32_t saddr) {
