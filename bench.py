@@ -40,7 +40,7 @@ N_IMG, C, HW, D, B, R = 16, 256, 256, 32, 32, 7
 UNEVEN, UNEVEN_N, UNEVEN_C, UNEVEN_B = "uneven64_c512", 64, 512, 64
 # serving: sizes {128,224,320,448} x C256, d=32, B=32, r=7, 32 classes, Poisson arrivals
 SERVE, SERVE_SIZES, SERVE_CLASSES, SERVE_TRAIN_SIDE = "serve_c256", (128, 224, 320, 448), 32, 128
-SERVE_RATES = (50, 200, 500, 1000, 2000)
+SERVE_RATES = (50, 200, 500, 1000, 2000, None)  # None: every request submitted at once (saturation)
 
 # ------------------------------------------------------------------ distributed helpers (CPU-testable)
 
@@ -503,9 +503,12 @@ def run_serving(qfca, torch, fields, classes, args):
                 pass
         points = []
         for rate in SERVE_RATES:
-            n = int(min(600, max(100, rate * 1.5)))
-            gaps = rng.exponential(1.0 / rate, size=n)
-            arrive = np.cumsum(gaps)
+            if rate is None:
+                n = 1000
+                arrive = np.zeros(n)
+            else:
+                n = int(min(600, max(100, rate * 1.5)))
+                arrive = np.cumsum(rng.exponential(1.0 / rate, size=n))
             tickets = [None] * n
             done = [None] * n
             stop = threading.Event()
@@ -540,7 +543,7 @@ def run_serving(qfca, torch, fields, classes, args):
             res = [r for r in done if r is not None]
             lat = sorted((r.t_done_us - r.t_submit_us) / 1e3 for r in res)
             span_s = (max(r.t_done_us for r in res) - min(r.t_submit_us for r in res)) / 1e6
-            points.append({"rate": rate, "requests": n, "completed": len(res),
+            points.append({"rate": rate if rate is not None else "saturation", "requests": n, "completed": len(res),
                            "p50_ms": round(lat[len(lat) // 2], 3),
                            "p99_ms": round(lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)], 3),
                            "maps_per_s": round(len(res) / span_s, 1),
