@@ -162,3 +162,22 @@ def test_assoc_rejects_bad_arguments(q):
         q.score_assoc(bins, 8, 255, 40, R, 64)  # 2r > 56 with B > 128
     with pytest.raises(RuntimeError):
         q.score_assoc(bins, 8, 8, 0, R, 64)
+
+
+def test_assoc_batch_beyond_one_launch(q):
+    # more than 64 images: several launches per stage, results equal single calls
+    rng = np.random.default_rng(48)
+    B, d, n = 16, 2, 70
+    bl, Rs, Ws, rs, tot = [], [], [], [], []
+    for i in range(n):
+        H, W, r = int(rng.integers(6, 30)), int(rng.integers(6, 40)), int(rng.integers(1, 5))
+        qb = synth.random_bins(rng, d, H, W, B, smooth=(i % 2 == 0))
+        bl.append(dev_bins(q, qb))
+        Rs.append(to_dev(oracle.ref_hist(qb, B).astype(np.int32)))
+        Ws.append(W)
+        rs.append(r)
+        tot.append(H * W)
+    outs = q.score_assoc_batch(bl, Ws, rs, B, Rs, tot, sigma_s=1.0)
+    for i in (0, 33, 64, 69):
+        single = q.score_assoc(bl[i], Ws[i], B, rs[i], Rs[i], tot[i], sigma_s=1.0)
+        torch.testing.assert_close(outs[i], single, rtol=0, atol=0)

@@ -82,3 +82,21 @@ def test_median_reference_rejects_bad_arguments(q):
         q.median_reference(bins, 8, 8, 4)   # 8 x 8 has no full 9 x 9 window
     with pytest.raises(RuntimeError):
         q.median_reference(torch.zeros(1, 64, 64, dtype=torch.uint8, device="cuda"), 64, 255, 20)  # table too large
+
+
+def test_median_reference_beyond_one_launch(q):
+    rng = np.random.default_rng(430)
+    B, n = 12, 70
+    bl, Ws, rs, ro = [], [], [], []
+    for i in range(n):
+        r = int(rng.integers(1, 4))
+        H, W = int(rng.integers(2 * r + 1, 30)), int(rng.integers(2 * r + 1, 40))
+        qb = synth.random_bins(rng, 2, H, W, B, smooth=(i % 2 == 1))
+        bl.append(dev_bins(q, qb))
+        Ws.append(W)
+        rs.append(r)
+        if i in (0, 40, 64, 69):
+            ro.append((i, oracle.median_ref(qb, B, r)))
+    outs = q.median_reference_batch(bl, Ws, rs, B)
+    for i, R in ro:
+        np.testing.assert_array_equal(outs[i].cpu().numpy().astype(np.uint32), R)

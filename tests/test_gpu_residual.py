@@ -107,3 +107,17 @@ def test_batch_run_plus_equals_single_calls(q, n, C, H, W, dres):
         torch.testing.assert_close(ex["bins"][i][:, :, :W], o["bins"][:, :, :W], rtol=0, atol=0)
         torch.testing.assert_close(ex["ref_hist"][i], o["hist"], rtol=0, atol=0)
         torch.testing.assert_close(s_b[i], s1, rtol=0, atol=0)
+
+
+def test_batch_run_plus_beyond_one_launch(q):
+    # 66 images: the fit, quantisation and scoring run in more than one launch per stage
+    n, C, H, W, dres, B, r = 66, 8, 16, 24, 2, 8, 2
+    X = np.stack([synth.small_case(C, H, W, 2.0, seed=600 + i).X for i in range(n)])
+    Xd = to_dev(X)
+    s_b, ex = q.batch_run_plus(Xd, dres, B, r, extras=True)
+    torch.cuda.synchronize()
+    for i in (0, 64, 65):
+        o = q.quantize_residual(Xd[i], (ex["mean"][i], ex["V"][i]), B)
+        s1 = q.score(o["bins"], W, B, r, o["hist"], H * W)
+        torch.cuda.synchronize()
+        torch.testing.assert_close(s_b[i], s1, rtol=0, atol=0)
