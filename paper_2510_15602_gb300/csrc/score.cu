@@ -236,7 +236,17 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ S
                 const uint32_t *hb = hc + SW;  // bin 0
                 // the last bin's term is 0 (both CDFs reach 1), so the walk stops at B-2
                 if (Nloc == Nint) {
-                    if (KB > 0) {
+                    if (KB > 0 && sizeof(ACC) == 4) {
+                        // 32-bit walk: a = cumP_b N_ref accumulated directly, D += |a - c| in one
+                        // sum-of-absolute-difference instruction
+                        uint32_t a = 0, D32 = 0;
+#pragma unroll
+                        for (int b = 0; b < KB - 1; b++) {
+                            a += hb[b * SW] * Nref;
+                            D32 = __usad(a, (uint32_t)cRi[b], D32);
+                        }
+                        D = (ACC)D32;
+                    } else if (KB > 0) {
 #pragma unroll
                         for (int b = 0; b < KB - 1; b++) {
                             cnt += hb[b * SW];
