@@ -277,6 +277,7 @@ NCU_TRAFFIC = {
     "k_median_ref": 43135744,
     "k_residual": 2147958000 + 1031120000,
     "k_project_tma": 1074424000 + 125305600,
+    "k_window_emd": 33653760 + 73581056,
     "k_quantize": 134446336 + 19018240,
 }
 
