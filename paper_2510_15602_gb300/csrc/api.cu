@@ -264,7 +264,7 @@ qfca_status run_score(qfca_ctx *ctx, const ScoreJob *jobs, int n, int d, int B, 
             }
             cands.push_back(model);
             for (int SW : {128, 64})
-                for (int TH : {8, 16, 32})
+                for (int TH : {8, 16, 32, 64})
                     for (int nk : {1, 2, 4, 8, 16, 32})
                         if (nk <= d) cands.push_back(ScoreTiling{SW, TH, nk});
             for (const ScoreTiling &c : cands) {

@@ -351,7 +351,7 @@ cudaError_t emd_occupancy_kind(EmdKind kind, int KB, size_t smem, int SW, int *p
 // Modelled cost (lane-instructions) of the CTAs of one image at a given tiling.
 double image_cost(int H, int W, int d, int B, int r, int SW, int TH, int kg, int n_kg) {
     const int span = 2 * r + 1, TR = TH + 2 * r;
-    const double row = 2.0 * span * 3.0 + 5.0 * (B - 1) + 12.0;
+    const double row = 2.0 * span * 3.0 + 4.0 * (B - 1) + 12.0;
     const double setup = 3.0 * span * span + 6.0 * TR * tcp_of(SW, r) / (4.0 * SW) + 2.0 * B + 60.0;
     const double ctas = (double)((W + SW - 1) / SW) * ((H + TH - 1) / TH) * n_kg;
     (void)d;
@@ -410,7 +410,7 @@ cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, boo
     } else {
         double best_cost = 1e300;
         for (int SW : {128, 64})
-            for (int TH : {16, 32, 8}) {
+            for (int TH : {16, 32, 64, 8}) {
                 const size_t smem = score_smem(SW, TH, B, rmax);
                 if (smem > 200 * 1024 || tcp_of(SW, rmax) > 256 || TH + 2 * rmax > 256) continue;
                 int per_sm = 0;
