@@ -411,6 +411,7 @@ __global__ void k_chan_scale(const unsigned *__restrict__ amax, int C, float *__
 __global__ void k_cov_finalize(const __grid_constant__ FitParams p, const unsigned long long *__restrict__ Gint,
                                const unsigned long long *__restrict__ Dsum, const int *__restrict__ ex,
                                double *__restrict__ mean, double *__restrict__ cov, float2 *__restrict__ cov_ff) {
+    extern __shared__ double fin_sh[];  // [C] means, [C] powers 2^e_c
     const long img = blockIdx.y;
     const int C = p.C;
     const double invN = 1.0 / (double)p.img[img].N;
@@ -420,16 +421,21 @@ __global__ void k_cov_finalize(const __grid_constant__ FitParams p, const unsign
     mean += img * C;
     cov += img * C * C;
     if (cov_ff) cov_ff += img * C * C;
+    double *mu = fin_sh, *pw = fin_sh + C;
+    // per channel once per block: 2^e_c and mu_c = 2^e_c S_c / N (powers of two: every scaling is exact)
+    constexpr double kSl[kSlices] = {0x1p-6, 0x1p-13, 0x1p-20, 0x1p-27};
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        double s = 0.0;
+        for (int sl = 0; sl < kSlices; sl++) s += (double)(long long)Dsum[(long)sl * C + c] * kSl[sl];
+        pw[c] = ldexp(1.0, ex[c]);
+        mu[c] = s * pw[c] * invN;
+    }
+    __syncthreads();
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)C * C; e += (long)gridDim.x * blockDim.x) {
         const int i = (int)(e / C), j = (int)(e % C);
         const int a = min(i, j), b = max(i, j);
-        auto mu = [&](int c) {
-            double s = 0.0;
-            for (int sl = 0; sl < kSlices; sl++) s += (double)(long long)Dsum[(long)sl * C + c] * ldexp(1.0, -6 - 7 * sl);
-            return ldexp(s, ex[c]) * invN;
-        };
-        const double mi = mu(a), mj = mu(b);
-        const double g = ldexp((double)(long long)Gint[(long)a * C + b], ex[a] + ex[b] - 40) * invN;
+        const double mi = mu[a], mj = mu[b];
+        const double g = (double)(long long)Gint[(long)a * C + b] * (pw[a] * pw[b] * 0x1p-40) * invN;
         const double v = g - mi * mj;
         cov[e] = v;
         if (cov_ff) {
@@ -533,7 +539,7 @@ cudaError_t launch_gram_cov_jobs(const FitJob *jobs, int n, int layout, int C, d
         QFCA_LAUNCH("k_gram", st, k_gram<<<(unsigned)cta, kThreads, g.smem, st>>>(p, sc, Gi, Di, status));
         const long cc = (long)C * C;
         QFCA_LAUNCH("k_cov_finalize", st,
-                    k_cov_finalize<<<dim3((unsigned)((cc + 255) / 256), m), 256, 0, st>>>(
+                    k_cov_finalize<<<dim3((unsigned)((cc + 255) / 256), m), 256, 2 * sizeof(double) * C, st>>>(
                         p, Gi, Di, exi, mean + (size_t)i0 * C, cov + (size_t)i0 * C * C,
                         cov_ff ? (float2 *)cov_ff + (size_t)i0 * C * C : nullptr));
         e = cudaGetLastError();
