@@ -83,7 +83,26 @@ __global__ void k_chan_absmax(const __grid_constant__ FitParams p, unsigned *__r
     const long N = im.N;
     amax += (long)blockIdx.z * C;
     unsigned m = 0;
-    if (p.layout == QFCA_NCHW) {
+    if (p.layout == QFCA_NCHW && p.vec_ok) {
+        // 16-byte loads, four in flight per thread
+        const float4 *row = reinterpret_cast<const float4 *>(X + (long)c * N);
+        const long n4 = N / 4, stride = (long)gridDim.x * blockDim.x;
+        long q = blockIdx.x * (long)blockDim.x + threadIdx.x;
+        for (; q + 3 * stride < n4; q += 4 * stride) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) v[u] = __ldg(row + q + u * stride);
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                m = max(max(m, max(__float_as_uint(v[u].x) & 0x7fffffffu, __float_as_uint(v[u].y) & 0x7fffffffu)),
+                        max(__float_as_uint(v[u].z) & 0x7fffffffu, __float_as_uint(v[u].w) & 0x7fffffffu));
+        }
+        for (; q < n4; q += stride) {
+            const float4 v = __ldg(row + q);
+            m = max(max(m, max(__float_as_uint(v.x) & 0x7fffffffu, __float_as_uint(v.y) & 0x7fffffffu)),
+                    max(__float_as_uint(v.z) & 0x7fffffffu, __float_as_uint(v.w) & 0x7fffffffu));
+        }
+    } else if (p.layout == QFCA_NCHW) {
         const float *row = X + (long)c * N;
         for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < N; q += (long)gridDim.x * blockDim.x)
             m = max(m, __float_as_uint(row[q]) & 0x7fffffffu);
@@ -556,10 +575,13 @@ cudaError_t launch_chan_absmax_jobs(const FitJob *jobs, int n, int layout, int C
         memset(&p, 0, sizeof(p));
         p.n = m, p.C = C, p.layout = layout;
         long max_n = 1;
+        int vec_ok = layout == QFCA_NCHW;
         for (int i = 0; i < m; i++) {
             p.img[i].X = jobs[i0 + i].X, p.img[i].N = jobs[i0 + i].N;
             max_n = jobs[i0 + i].N > max_n ? jobs[i0 + i].N : max_n;
+            vec_ok = vec_ok && jobs[i0 + i].N % 4 == 0 && ((uintptr_t)jobs[i0 + i].X & 15) == 0;
         }
+        p.vec_ok = vec_ok;
         const int xb = (int)((max_n + 256 * 64 - 1) / (256 * 64));
         QFCA_LAUNCH("k_chan_absmax", st,
                     k_chan_absmax<<<dim3(xb < 1 ? 1 : xb, C, m), 256, 0, st>>>(p, amax + (size_t)i0 * C));
