@@ -105,8 +105,9 @@ __host__ __device__ inline int ring_rows(int r) { return 4 * r + 4; }
 // above it the two-pointer walk itself runs.
 constexpr int kClosedMaxB = 64;
 
-// Boundary tables of the column-border window sizes (2r+1 rows x cols, cols =
-// r+1 .. 2r), packed one after another; not kept when they would take more than
+// Boundary tables of the border window sizes N = (2r+1) k, k = r+1 .. 2r (a
+// column-border window has all 2r+1 rows and k columns, a row-border one the
+// reverse), packed one after another; not kept when they would take more than
 // kColTabMax bytes (those windows then search the reference bins).
 constexpr size_t kColTabMax = 8192;
 __host__ __device__ inline int coltab_off(int r, int cols) {
@@ -496,11 +497,15 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
             const uint32_t Nl = lead_on ? (uint32_t)(min(H - 1, a + r) - max(0, a - r) + 1) * wcols : 0u;
             const uint32_t Ntr = trail_on ? (uint32_t)(min(H - 1, bq + r) - max(0, bq - r) + 1) * wcols : 0u;
             const bool full = (!lead_on || Nl == Nint) && (!trail_on || Ntr == Nint);
-            // boundary table of each window: full size, a column-border size (all 2r+1 rows), or none
+            // boundary table of each window: full size, or (2r+1) x k with r < k < 2r+1 -- a
+            // column-border window (all rows) or a row-border one (all columns): the table
+            // depends only on N = (2r+1) k -- or none (the corners search)
             auto table = [&](uint32_t N, int rows) -> const uint8_t * {
                 if (N == Nint) return Jtab;
                 const int cols = (int)wcols;
-                if (rows == span && cols > r && cols < span && coltab_bytes(r)) return JC + coltab_off(r, cols);
+                if (!coltab_bytes(r)) return nullptr;
+                if (rows == span && cols > r && cols < span) return JC + coltab_off(r, cols);
+                if (cols == span && rows > r && rows < span) return JC + coltab_off(r, rows);
                 return nullptr;
             };
             const int rows_l = lead_on ? min(H - 1, a + r) - max(0, a - r) + 1 : 0;
