@@ -798,10 +798,15 @@ def run_ours(args):
         fp32 = {"value": round(N_IMG * ws * max(1, args.steps // 4) / fs, 3), "unit": "maps/s",
                 "path": "FP32 projection, one image per call sequence (fit, quantize, score), one stream"}
 
-    # ---- single-image latency on an idle GPU (batch of one through the batched entry point)
+    # ---- single-image latency on an idle GPU (batch of one through the batched entry point);
+    # one untimed call first, so that the window-tiling choice for a batch of one is made
+    # before the samples
     lat = []
     s1 = torch.empty(1, HW, HW, dtype=torch.float32, device="cuda")
-    for i in range(N_IMG):
+    qfca.batch_run(X_dev[0:1], D, B, R, args.precision, ctx=pipe.ctx[0], stream=main, scores=s1)
+    torch.cuda.synchronize()
+    for j in range(4 * N_IMG):
+        i = j % N_IMG
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(main)
@@ -872,7 +877,8 @@ def run_ours(args):
             "clocks": clocks,
             "fp32_single_image": fp32,
             "latency_ms_single_image": {"p50": round(lat[len(lat) // 2], 3),
-                                        "p99": round(lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)], 3)},
+                                        "p99": round(lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)], 3),
+                                        "samples": len(lat)},
             "auroc": {"gpu_mean": round(auroc_mean, 5), "gpu_image0": round(aurocs[0], 5),
                       "oracle_image0": None if auroc_oracle is None else round(auroc_oracle, 5),
                       "delta_image0": None if auroc_oracle is None else round(abs(aurocs[0] - auroc_oracle), 6)},
