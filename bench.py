@@ -20,6 +20,7 @@ program) on the host cores, on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -125,11 +126,14 @@ def make_inputs(indices):
 
 
 class ClockSampler:
-    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+    """nvidia-smi samples (every 50 ms) of SM clock and throttle reasons, each
+    carrying nvidia-smi's own timestamp (so pipe buffering cannot blur it) so
+    that only those taken inside the timed region are reported."""
 
-    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+    FIELDS = ["timestamp", "index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
               "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+    PERIOD_MS = 50
 
     def __init__(self, gpu_id: str):
         self.gpu_id = gpu_id
@@ -137,22 +141,36 @@ class ClockSampler:
         self.proc = None
         self.err = None
 
-    def start(self):
+    def start(self, wait_s: float = 3.0):
+        """Start sampling; return once the first sample has arrived (or after wait_s)."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu_id}", "--query-gpu=" + ",".join(self.FIELDS),
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception as e:  # no nvidia-smi
             self.err = str(e)
+            return
+        t_end = time.monotonic() + wait_s
+        while not self.lines and time.monotonic() < t_end:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def stop(self) -> dict:
+    @staticmethod
+    def _stamp(field: str, fallback: float) -> float:
+        try:
+            return datetime.datetime.strptime(field, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return fallback
+
+    def stop(self, t0: float | None = None, t1: float | None = None) -> dict:
+        """Stop sampling; summarise the samples stamped within [t0, t1] (host
+        wall-clock seconds), or, when none falls inside, the nearest one."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": self.err}
         self.proc.terminate()
@@ -161,22 +179,32 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.thread.join(timeout=2)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        rows = []
+        for ts, ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                rows.append((self._stamp(parts[0], ts), float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
+        inside = rows if t0 is None else [r for r in rows if t0 <= r[0] <= t1]
+        where = "inside the timed region"
+        if not inside and rows:
+            mid = 0.5 * (t0 + t1)
+            inside = [min(rows, key=lambda r: abs(r[0] - mid))]
+            where = "nearest sample to the timed region (none fell inside)"
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in inside:
+            for nm, v in zip(names, r[3]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        sm = [r[1] for r in inside]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(r[2] for r in inside) if inside else None,
+                "reasons": sorted(reasons), "samples": len(inside), "samples_from": where,
+                "period_ms": self.PERIOD_MS}
 
 
 def gpu_id_for_smi(local_rank: int) -> str:
@@ -739,9 +767,10 @@ def run_ours(args):
     # ---- timed region: fork once, K steps alternating over the two pipes, join once
     sampler = ClockSampler(gpu_id_for_smi(local))
     sampler.start()
+    t_region0 = time.time()
     dev_s, wall_s = timed(torch, main, lambda i: pipe.step(i), args.steps, fork=lambda: pipe.fork(main),
                           join=lambda: pipe.join(main))
-    clocks = sampler.stop()
+    clocks = sampler.stop(t_region0, time.time())
     dom_ms, dom_n = 0.0, 0
     for c in pipe.ctx:
         t = c.trace()
@@ -928,7 +957,7 @@ def run_profile_batch(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["f32", "bf16"])
