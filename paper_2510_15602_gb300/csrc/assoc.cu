@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(256) k_blur(const __grid_constant__ BlurParams
     }
 }
 
-int g_attr_dev_assoc = -1;
+DeviceOnce g_attrs_assoc;
 
 }  // namespace
 
@@ -675,13 +675,18 @@ cudaError_t launch_assoc_jobs(const AssocJob *jobs, int n, int d, int B, void *w
     nt = std::min(nt, ntmax);
     const size_t smem = assoc_smem(nt, B, rmax, wide);
     const bool closed = B <= kClosedMaxB;
-    if (g_attr_dev_assoc != dev) {
-        cudaFuncSetAttribute(k_assoc<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_assoc<unsigned long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_assoc<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_assoc<unsigned long long, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        g_attr_dev_assoc = dev;
-    }
+    cudaError_t ea = device_once(g_attrs_assoc, dev, [] {
+        const int lim = 200 * 1024;
+        cudaError_t r = cudaFuncSetAttribute(k_assoc<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k_assoc<unsigned long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k_assoc<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k_assoc<unsigned long long, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        return r;
+    });
+    if (ea != cudaSuccess) return ea;
     // workspace carve: F per image, then the unblurred map where the caller gave none (or a blur follows)
     std::vector<uint32_t *> F(n);
     std::vector<float *> rawp(n);

@@ -712,14 +712,13 @@ cudaError_t launch_eig(const void *cov_ff, int n, int d, int mats, double *V, do
     long region0 = 0;
     int nslots = 1;
     const size_t smem = smem_plan(n, d, R, &region0, &nslots);
-    static int attr_dev = -1;
+    static DeviceOnce attrs;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_eig_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_dev = dev;
-    }
+    cudaError_t e0 = device_once(attrs, dev, [] {
+        return cudaFuncSetAttribute(k_eig_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    });
+    if (e0 != cudaSuccess) return e0;
     const EigPlan p = eig_plan(n, d, mats);
     char *b = (char *)ws;
     EigArgs a;

@@ -509,14 +509,13 @@ cudaError_t launch_gram_cov_jobs(const FitJob *jobs, int n, int layout, int C, d
     if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, sizeof(unsigned long long) * (size_t)C * C * n, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(D, 0, sizeof(unsigned long long) * kSlices * (size_t)C * n, st);
     if (e != cudaSuccess) return e;
-    static int attr_dev = -1;
+    static DeviceOnce attrs;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (attr_dev != dev) {
-        e = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-        if (e != cudaSuccess) return e;
-        attr_dev = dev;
-    }
+    e = device_once(attrs, dev, [&] {
+        return cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+    });
+    if (e != cudaSuccess) return e;
     for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
         const int m = n - i0 < kMaxBatch ? n - i0 : kMaxBatch;
         FitParams p;

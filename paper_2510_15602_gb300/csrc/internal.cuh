@@ -23,6 +23,26 @@ constexpr int kMaxB = 255;   // bins
 // kernel's parameter block).
 constexpr int kMaxBatch = 64;
 
+// Once-per-device setup of a launcher's kernel attributes (dynamic shared
+// memory limits, carve-outs, SM counts).  Launchers run on the caller's thread
+// and on serving scheduler threads, so the record is taken under a mutex; a
+// device's bit is set only after its setup succeeded (a failure is retried on
+// the next launch).  Devices are numbered below 64.
+struct DeviceOnce {
+    std::mutex mu;
+    uint64_t done = 0;
+};
+
+template <class F>
+cudaError_t device_once(DeviceOnce &o, int dev, F &&setup) {
+    std::lock_guard<std::mutex> lk(o.mu);
+    const uint64_t bit = 1ull << (dev & 63);
+    if (o.done & bit) return cudaSuccess;
+    const cudaError_t e = setup();
+    if (e == cudaSuccess) o.done |= bit;
+    return e;
+}
+
 // ------------------------------------------------------------------ fit (fit.cu)
 
 // Batched entry points take `nimg` images of one shape stored one after the

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) k_median_fin(const __grid_constant__ MedP
     for (int b = threadIdx.x; b < B; b += blockDim.x) im.ref[(size_t)k * B + b] = R[b];
 }
 
-int g_attr_dev_med = -1;
+DeviceOnce g_attrs_med;
 
 // Threads (window centres) per CTA: the widest of 256, 128, 64, 32 whose
 // histograms and count table fit; 0 when none does.
@@ -173,12 +173,14 @@ cudaError_t launch_median_jobs(const MedianJob *jobs, int n, int d, int B, void 
     }
     const int ntcap = med_nt_cap(B, rmax);
     if (ntcap == 0) return cudaErrorNotSupported;
-    if (g_attr_dev_med != dev) {
-        cudaFuncSetAttribute(k_median_ref, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMedSmemMax);
-        cudaFuncSetAttribute(k_median_fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMedSmemMax);
-        g_attr_dev_med = dev;
-    }
-    cudaError_t e = cudaMemsetAsync(ws, 0, median_jobs_workspace_bytes(jobs, n, d, B), st);
+    cudaError_t e = device_once(g_attrs_med, dev, [] {
+        cudaError_t r = cudaFuncSetAttribute(k_median_ref, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMedSmemMax);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k_median_fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMedSmemMax);
+        return r;
+    });
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(ws, 0, median_jobs_workspace_bytes(jobs, n, d, B), st);
     if (e != cudaSuccess) return e;
     unsigned char *w = static_cast<unsigned char *>(ws);
     std::vector<uint32_t *> Dp(n);

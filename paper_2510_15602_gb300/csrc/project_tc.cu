@@ -289,25 +289,24 @@ __global__ void __launch_bounds__(kThreads) k_project_bf16(const float *__restri
 template <int DT>
 cudaError_t launch_dt(const float *X, int layout, int C, const TcShape &sh, long N, int nimg, const float *mean32,
                       const __nv_bfloat16 *Vt, int d, float *Y, uint32_t *mm_keys, int *status, cudaStream_t st) {
-    static int attr_dev = -1;
-    static int max_blocks = 0;
+    static DeviceOnce attrs;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_project_bf16<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = device_once(attrs, dev, [] {
+        cudaError_t r = cudaFuncSetAttribute(k_project_bf16<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_project_bf16<DT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k_project_bf16<DT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        attr_dev = dev;
-    }
+        return r;
+    });
+    if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project_bf16<DT>, kThreads, sh.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project_bf16<DT>, kThreads, sh.smem);
     if (e != cudaSuccess) return e;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (per_sm < 1) return cudaErrorNotSupported;
-    max_blocks = per_sm * sms;
+    const int max_blocks = per_sm * sms;
     const long tiles = (N + kM - 1) / kM;
     const long n_tiles = tiles * nimg;
     const int grid = (int)(n_tiles < max_blocks ? n_tiles : max_blocks);

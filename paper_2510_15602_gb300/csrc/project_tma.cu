@@ -442,16 +442,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
 
 template <int DT, bool F8>
 cudaError_t launch_dt(const ProjParams &p, int *status, cudaStream_t st) {
-    static int attr_dev = -1, n_sm = 0;
-    int dev = 0;
+    static DeviceOnce attrs;
+    int dev = 0, n_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (attr_dev != dev) {
-        e = cudaFuncSetAttribute(k_project_tma<DT, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        attr_dev = dev;
-    }
+    e = device_once(attrs, dev, [] {
+        return cudaFuncSetAttribute(k_project_tma<DT, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    });
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
     const size_t smem = smem_layout(p.stages, p.na, p.Cp, DT, F8).total;
     const long grid = p.total_tiles < n_sm ? p.total_tiles : n_sm;
     QFCA_LAUNCH("k_project_tma", st, (k_project_tma<DT, F8><<<(unsigned)grid, kThreads, smem, st>>>(p, status)));

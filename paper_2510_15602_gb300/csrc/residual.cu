@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kResThreads) k_residual(const __grid_constant_
     }
 }
 
-int g_attr_dev_res = -1;
+DeviceOnce g_attrs_res;
 
 }  // namespace
 
@@ -159,15 +159,17 @@ cudaError_t launch_residual(const float *X, int layout, int H, int W, int C, con
     if (dres < 0 || dres > kMaxResidual) return cudaErrorInvalidValue;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (g_attr_dev_res != dev) {
-        cudaFuncSetAttribute(k_residual<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_residual<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_residual<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_residual<4, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_residual<4, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        g_attr_dev_res = dev;
-    }
-    cudaError_t e = launch_init_keys(mm, C, nimg, st);
+    cudaError_t e = device_once(g_attrs_res, dev, [] {
+        const int lim = 200 * 1024;
+        cudaError_t r = cudaFuncSetAttribute(k_residual<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(k_residual<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(k_residual<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(k_residual<4, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(k_residual<4, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        return r;
+    });
+    if (e != cudaSuccess) return e;
+    e = launch_init_keys(mm, C, nimg, st);
     if (e != cudaSuccess) return e;
     const long N = (long)H * W;
     // four pixels per thread only when that still leaves about two waves of CTAs

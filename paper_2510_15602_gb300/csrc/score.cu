@@ -358,24 +358,20 @@ double image_cost(int H, int W, int d, int B, int r, int SW, int TH, int kg, int
     return ctas * (kg * (TH * row + setup) + 200.0);
 }
 
-int g_attr_dev = -1, g_n_sm = 0;
-std::mutex g_attr_mu;
+DeviceOnce g_attrs_emd;
 
 cudaError_t ensure_attrs(int *n_sm) {
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
-    std::lock_guard<std::mutex> lk(g_attr_mu);
-    if (g_attr_dev != dev) {
-        err = emd_set_smem_attr<uint32_t, uint32_t>();
-        if (err == cudaSuccess) err = emd_set_smem_attr<uint32_t, unsigned long long>();
-        if (err == cudaSuccess) err = emd_set_smem_attr<unsigned long long, unsigned long long>();
-        if (err == cudaSuccess) err = cudaDeviceGetAttribute(&g_n_sm, cudaDevAttrMultiProcessorCount, dev);
-        if (err != cudaSuccess) return err;
-        g_attr_dev = dev;
-    }
-    *n_sm = g_n_sm;
-    return cudaSuccess;
+    err = device_once(g_attrs_emd, dev, [] {
+        cudaError_t r = emd_set_smem_attr<uint32_t, uint32_t>();
+        if (r == cudaSuccess) r = emd_set_smem_attr<uint32_t, unsigned long long>();
+        if (r == cudaSuccess) r = emd_set_smem_attr<unsigned long long, unsigned long long>();
+        return r;
+    });
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(n_sm, cudaDevAttrMultiProcessorCount, dev);
+    return err;
 }
 
 // One launch of at most kMaxBatch jobs.
