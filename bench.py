@@ -301,6 +301,7 @@ def kernel_work(name: str, H: int, W: int, C: int, d: int, B: int, r: int, nimg:
 # removed whenever its kernel changes after the capture.
 NCU_TRAFFIC = {
     "k_eig_ff": 4851456,
+    "k_gram": 1108133000 + 18952192,
     "k_assoc": 35393280 + 78018560,
     "k_median_ref": 43135744,
     "k_residual": 2147958000 + 1031120000,
