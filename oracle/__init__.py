@@ -16,8 +16,10 @@ closed form), ``alg1`` (Algorithm 1; the supplement's correctness proof) and
 ``assoc`` (Sec. 3.1's error-to-pixel association, the final blur) and
 ``median_ref`` (Sec. 3.2's median reference) and ``residual`` (Sec. 3.3's
 QFCA+ features) are each
-pinned by tests against closed forms, library routines or brute force
-(tests/test_oracle_pins.py).
+pinned by tests against closed forms, library routines, brute force and
+hand-worked cases (tests/test_oracle_pins.py, tests/test_oracle_golden.py and
+the assoc, median and residual pin files); tests/test_oracle_mutants.py checks
+that planted mistakes fail those pins.
 """
 from __future__ import annotations
 

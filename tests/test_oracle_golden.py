@@ -58,8 +58,9 @@ def test_assoc_hand():
     np.testing.assert_array_equal(comp[0], raw)  # one component: its map is the mean
 
 
-def test_median_reference_hand():
-    g = GOLD["median_3x5"]
+@pytest.mark.parametrize("key", ["median_3x5", "median_3x4_even"])
+def test_median_reference_hand(key):
+    g = GOLD[key]
     q = np.array(g["q"], np.uint8)
     np.testing.assert_array_equal(oracle.median_ref(q, g["B"], g["r"])[0], g["ref"])
 
