@@ -49,6 +49,30 @@ MUTANTS = [
      "double a = s / (double)n;", "double a = s / (double)((2 * r + 1) * (2 * r + 1));"),
     ("smoothing: Gaussian exponent without the factor 2",
      "exp(-(double)t * t / (2.0 * sigma * sigma))", "exp(-(double)t * t / (sigma * sigma))"),
+    ("smoothing: weights not renormalised over the taps inside the image",
+     "out[(long)y * W + x] = s / w;", "out[(long)y * W + x] = s + 0.0 * w;"),
+    ("single-pixel EMD: N_loc and N_ref swapped",
+     "int64_t diff = cumL * (int64_t)Nref - cumR * (int64_t)Nloc;",
+     "int64_t diff = cumL * (int64_t)Nloc - cumR * (int64_t)Nref;"),
+    ("window histogram: last row of the window dropped",
+     "for (int yy = y - r; yy <= y + r; yy++)\n        for (int xx = x - r; xx <= x + r; xx++)\n            if (yy >= 0",
+     "for (int yy = y - r; yy < y + r; yy++)\n        for (int xx = x - r; xx <= x + r; xx++)\n            if (yy >= 0"),
+    ("quantiser (FP32 decision): rounded instead of floored",
+     "else b = (long)v;", "else b = (long)(v + 0.5f);"),
+    ("quantiser: the maximum not clamped into the last bin",
+     "if (b > B - 1) b = B - 1;", "if (b > B) b = B;"),
+    ("reference histogram: first pixel skipped",
+     "for (long p = 0; p < N; p++)\n            R[(long)k * B + q[(long)k * N + p]]++;",
+     "for (long p = 1; p < N; p++)\n            R[(long)k * B + q[(long)k * N + p]]++;"),
+    ("alg1: local masses scaled by N_loc instead of N_ref",
+     "Pw[b] = P[b] * Nref;", "Pw[b] = P[b] * Nloc;"),
+    ("median reference: last column of full windows skipped",
+     "for (int x = r; x < W - r; x++, p++) {", "for (int x = r; x < W - r - 1; x++, p++) {"),
+    ("residual: projections of uncentred features",
+     "s += (feat(X, layout, C, N, c, p) - mean[c]) * V[(long)c * dres + k];",
+     "s += feat(X, layout, C, N, c, p) * V[(long)c * dres + k];"),
+    ("Jacobi: stopped at a loose off-diagonal tolerance",
+     "if (off <= 1e-15 * frob || off == 0.0)", "if (off <= 1e-3 * frob || off == 0.0)"),
 ]
 
 DRIVER = r"""
