@@ -32,6 +32,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "arena.cuh"
 #include "internal.cuh"
 
 namespace qfca {
@@ -52,48 +53,6 @@ struct ClassRec {
         cudaFree(prep);
         cudaFree(lo);
         cudaFree(ref);
-    }
-};
-
-// First-fit allocator over [0, size) with coalescing free blocks.
-struct Arena {
-    size_t size = 0;
-    std::map<size_t, size_t> free_;  // offset -> length
-    void reset(size_t n) {
-        size = n;
-        free_.clear();
-        free_[0] = n;
-    }
-    size_t largest() const {
-        size_t m = 0;
-        for (auto &kv : free_) m = std::max(m, kv.second);
-        return m;
-    }
-    bool alloc(size_t n, size_t *off) {
-        for (auto it = free_.begin(); it != free_.end(); ++it)
-            if (it->second >= n) {
-                *off = it->first;
-                const size_t rest = it->second - n, at = it->first + n;
-                free_.erase(it);
-                if (rest) free_[at] = rest;
-                return true;
-            }
-        return false;
-    }
-    void release(size_t off, size_t n) {
-        auto it = free_.emplace(off, n).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
     }
 };
 
