@@ -291,8 +291,8 @@ def bins_pitch(W: int) -> int:
 def fit_pca(X: torch.Tensor, d: int, layout: int = NCHW, ctx: Context | None = None, stream=None, out=None):
     """qfca_fit_pca: returns (mean[C], V[C, d], eigvals[d]) FP64 device tensors."""
     _check_dev(X, "X", torch.float32)
-    ctx = ctx or default_context(X.device.index)
     fm = fmap_of(X, layout)
+    ctx = ctx or default_context(X.device.index)
     if out is None:
         mean = torch.empty(fm.C, dtype=torch.float64, device=X.device)
         V = torch.empty(fm.C, d, dtype=torch.float64, device=X.device)
@@ -307,8 +307,8 @@ def fit_pca(X: torch.Tensor, d: int, layout: int = NCHW, ctx: Context | None = N
 def covariance(X: torch.Tensor, layout: int = NCHW, ctx: Context | None = None, stream=None):
     """qfca_covariance: returns (mean[C], Sigma[C, C]) FP64 device tensors."""
     _check_dev(X, "X", torch.float32)
-    ctx = ctx or default_context(X.device.index)
     fm = fmap_of(X, layout)
+    ctx = ctx or default_context(X.device.index)
     mean = torch.empty(fm.C, dtype=torch.float64, device=X.device)
     cov = torch.empty(fm.C, fm.C, dtype=torch.float64, device=X.device)
     ctx.check(_lib.qfca_covariance(ctx.handle, _ptr(X), fm, _ptr(mean), _ptr(cov), _P(_stream_ptr(stream))))
@@ -327,8 +327,8 @@ def quantize(X: torch.Tensor, basis, B: int, precision="f32", layout: int = NCHW
     mean, V = basis[0], basis[1]
     _check_dev(mean, "mean", torch.float64)
     _check_dev(V, "V", torch.float64)
-    ctx = ctx or default_context(X.device.index)
     fm = fmap_of(X, layout)
+    ctx = ctx or default_context(X.device.index)
     d = V.shape[1]
     pitch = bins_pitch(fm.W)
     dev = X.device
@@ -357,8 +357,8 @@ def quantize_residual(X: torch.Tensor, basis, B: int, layout: int = NCHW, want_F
     mean, V = basis[0], basis[1]
     _check_dev(mean, "mean", torch.float64)
     _check_dev(V, "V", torch.float64)
-    ctx = ctx or default_context(X.device.index)
     fm = fmap_of(X, layout)
+    ctx = ctx or default_context(X.device.index)
     dres = V.shape[1]
     pitch = bins_pitch(fm.W)
     dev = X.device
@@ -541,11 +541,11 @@ def score_batch(Xs, rs, d: int, B: int, precision="bf16", layout: int = NCHW, ct
     """
     if len(Xs) != len(rs) or not Xs:
         raise ValueError("one radius per image, at least one image")
-    ctx = ctx or default_context(Xs[0].device.index)
     fms = [fmap_of(X, layout) for X in Xs]
     C = fms[0].C
     if any(fm.C != C for fm in fms):
         raise ValueError("every image needs the same channel count")
+    ctx = ctx or default_context(Xs[0].device.index)
     if scores is None:
         scores = [torch.empty(fm.H, fm.W, dtype=torch.float32, device=X.device) for fm, X in zip(fms, Xs)]
     arr = (Image * len(Xs))()
