@@ -73,6 +73,13 @@ MUTANTS = [
      "s += feat(X, layout, C, N, c, p) * V[(long)c * dres + k];"),
     ("Jacobi: stopped at a loose off-diagonal tolerance",
      "if (off <= 1e-15 * frob || off == 0.0)", "if (off <= 1e-3 * frob || off == 0.0)"),
+    ("alg1: the walk stops before the last local bin",
+     "while (i < B && j < B)", "while (i < B - 1 && j < B)"),
+    ("association: per-bin error normalised by N_loc instead of N_ref",
+     "e[b] = L[b] > 0 ? (double)En[b] / ((double)L[b] * (double)Nref) : 0.0;",
+     "e[b] = L[b] > 0 ? (double)En[b] / ((double)L[b] * (double)Nloc) : 0.0;"),
+    ("association: each window's error of its centre's bin instead of the pixel's own bin",
+     "s += E[((long)py * W + px) * B + bq];", "s += E[((long)py * W + px) * B + qk[(long)py * W + px]];"),
 ]
 
 DRIVER = r"""
