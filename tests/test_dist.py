@@ -48,3 +48,14 @@ def test_two_gloo_ranks_shard_and_time():
     assert shards[0] | shards[1] == set(range(32))
     assert all(x[1] == world for x in res)
     assert all(x[4] == 2.0 for x in res)        # the slowest rank's time, on every rank
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
+    # under torchrun the oracle's CPU timing runs once, on rank 0; other ranks exit 0 without work
+    import argparse
+
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setattr(bench, "make_inputs", lambda *a, **k: pytest.fail("rank 1 drew inputs"))
+    assert bench.run_reference(argparse.Namespace(steps=3, warmup=3)) == 0
