@@ -76,7 +76,11 @@ def test_alu_peaks_from_unit_counts(bench):
 
 
 def test_measured_peaks_are_read(bench):
-    m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if not os.path.exists(path):  # written per machine, not part of the sources
+        assert bench.measured_peaks()["source"] == "fallback"
+        return
+    m = json.load(open(path))
     p = bench.measured_peaks()
     assert p["source"] == "measured"
     assert p["hbm_gbs"] == m["hbm_gbs"] and p["bf16_tflops_sustained"] == m["bf16_tflops_sustained"]
