@@ -92,3 +92,29 @@ def test_border_discard_and_image_auroc():
     skm = pytest.importorskip("sklearn.metrics")
     y = [int(l.any()) for l in lab]
     assert image_auroc(maps, lab) == pytest.approx(skm.roc_auc_score(y, [x.max() for x in maps]), abs=1e-12)
+
+
+def test_degenerate_inputs():
+    from paper_2510_15602_gb300 import metrics as M
+    rng = np.random.default_rng(9)
+    s = rng.random((12, 12))
+    none = np.zeros((12, 12), np.uint8)
+    allm = np.ones((12, 12), np.uint8)
+    # one class only: the rank statistics are undefined
+    assert np.isnan(M.auroc(s, none)) and np.isnan(M.auroc(s, allm))
+    assert np.isnan(M.f1_max(s, none))
+    assert np.isnan(M.aupro([s], [none]))
+    assert np.isnan(M.image_auroc([s, s], [allm, allm]))
+    # every pixel anomalous: predicting all of them gives precision = recall = 1
+    assert M.f1_max(s, allm) == 1.0
+    # a constant map cannot separate anything: AUROC one half, PRO reaches the region only at FPR 1
+    m = none.copy()
+    m[3:6, 3:6] = 1
+    c = np.full((12, 12), 0.25)
+    assert M.auroc(c, m) == 0.5
+    fpr, pro = M.pro_curve([c], [m])
+    np.testing.assert_allclose(fpr, [0.0, 1.0], atol=1e-12)  # sums of 1/n weights
+    np.testing.assert_allclose(pro, [0.0, 1.0], atol=1e-12)
+    assert M.aupro([c], [m]) == pytest.approx(0.5 * 0.3 * 0.3 / 0.3)  # the diagonal: area 0.045 over 0.3
+    # a border that swallows the image leaves no pixels
+    assert np.isnan(M.auroc(s, m, border=6))
