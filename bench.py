@@ -79,9 +79,15 @@ def barrier():
 # ------------------------------------------------------------------ inputs
 
 
-def _gen(idx):
+def _gen(job):
+    # job: an image index, or (index, aniso); with aniso the unit field is mixed by a
+    # fixed class covariance Q diag(lambda) Q^T before the anomalies are planted (the
+    # anomalies' places and kinds do not change), so a rotated-covariance patch differs
+    # from its surroundings
     from paper_2510_15602_gb300 import synth
-    img = synth.make_image(WORKLOAD, idx)
+    idx, aniso = job if isinstance(job, tuple) else (job, False)
+    mix = synth.class_mixing(0, synth.WORKLOADS[WORKLOAD].C) if aniso else None
+    img = synth.make_image(WORKLOAD, idx, class_mix=mix)
     return img.X, img.mask
 
 
@@ -117,9 +123,9 @@ def _pool_map(fn, items):
         return pool.map(fn, items)
 
 
-def make_inputs(indices):
+def make_inputs(indices, aniso: bool = False):
     """Seeded synthetic images, drawn in a spawn pool (before any CUDA call)."""
-    return _pool_map(_gen, list(indices))
+    return _pool_map(_gen, [(i, aniso) for i in indices] if aniso else list(indices))
 
 
 # ------------------------------------------------------------------ clocks
@@ -296,6 +302,29 @@ def kernel_work(name: str, H: int, W: int, C: int, d: int, B: int, r: int, nimg:
     return {"bound": "hbm", "unit": "GB/s", "work": nimg * 4 * C, "peak_key": "hbm", "per_unit": "4C bytes per image"}
 
 
+def per_kind_auroc(scores, masks, kind_masks, border: int) -> dict:
+    """Pixel AUROC per anomaly kind, pooled over the maps with the border discarded:
+    the pixels of that kind's anomalies against every normal pixel (pixels of the
+    other kinds left out).  None where a class is empty."""
+    import numpy as np
+    from paper_2510_15602_gb300.metrics import auroc
+
+    def crop(a):
+        return a[border:-border, border:-border] if border > 0 else a
+
+    out = {}
+    for k in sorted({k for km in kind_masks for k in km}):
+        vals, labels = [], []
+        for s, m, km in zip(scores, masks, kind_masks):
+            pos = crop(km[k]) != 0 if k in km else np.zeros(crop(m).shape, bool)
+            keep = (crop(m) == 0) | pos
+            vals.append(crop(np.asarray(s, np.float64))[keep])
+            labels.append(pos[keep])
+        a = auroc(np.concatenate(vals), np.concatenate(labels))
+        out[k] = None if a != a else round(a, 5)
+    return out
+
+
 # DRAM bytes (read + write) per launch over the 16-image batch, from the ncu
 # captures summarised in profiles/<kernel>_batch16_256_c256.md; an entry is
 # removed whenever its kernel changes after the capture.
@@ -341,7 +370,7 @@ def run_reference(args):
     import numpy as np
     import oracle
     oracle.build()
-    imgs = make_inputs([0])
+    imgs = make_inputs([0], getattr(args, "aniso", False))
     X, mask = imgs[0]
     times = []
     for s in range(args.warmup + args.steps):
@@ -357,7 +386,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Gaussian random fields with planted anomalies)",
             "config": {"workload": WORKLOAD, "images_per_step": 1, "H": HW, "W": HW, "C": C, "d": D, "B": B,
-                       "r": R, "sample": "1 of the 16 images per step (bounded CPU sample)"},
+                       "r": R, "sample": "1 of the 16 images per step (bounded CPU sample)",
+                       "field": "class covariance (--aniso)" if getattr(args, "aniso", False) else "isotropic"},
             "cpu_baseline": {"value": round(value, 5), "unit": "maps/s", "cores": 1, "kind": "oracle",
                              "sample": "image 0 of the 16-image batch, whole path, single thread"},
             "e2e": {"value": round(value, 5), "unit": "maps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -712,7 +742,7 @@ def run_qfca_plus(qfca, torch, X_dev, masks, args):
 def run_ours(args):
     ws, rank, local = dist_env()
     indices = shard_indices(rank, ws, N_IMG)
-    host = make_inputs(indices)  # before the first CUDA call (spawn pool)
+    host = make_inputs(indices, args.aniso)  # before the first CUDA call (spawn pool)
     extra = rank == 0 and ws == 1
     host_uneven = _pool_map(_gen_uneven, list(range(UNEVEN_N))) if extra and not args.skip_uneven else None
     serve_fields = serve_classes = None
@@ -860,6 +890,12 @@ def run_ours(args):
                "f1_max": round(f1_max(scores, mstack, border=R), 5),
                "note": "pooled over the 16 maps, r-pixel border discarded; every image of the batch is anomalous, "
                        "so the image-level AUROC is undefined here"}
+    try:  # a reporting extra: a failure here is recorded, not raised
+        from paper_2510_15602_gb300 import synth
+        kms = [synth.kind_masks(WORKLOAD, i) for i in indices]
+        quality["pixel_auroc_by_kind_border_r"] = per_kind_auroc(scores, masks, kms, R)
+    except Exception as e:  # noqa: BLE001
+        quality["pixel_auroc_by_kind_border_r"] = {"error": repr(e)[:200]}
 
     peaks = measured_peaks()
     roof = roofline_entry(dominant, dom_ms, dom_n, peaks, HW, HW, C, D, B, R, nimg=N_IMG, traffic=args.traffic)
@@ -896,7 +932,8 @@ def run_ours(args):
                        "window_tiling": "autotuned (measured once during warm-up)",
                        "path": f"qfca_batch_run, CUDA graph, {args.pipes} steps in flight" if not args.no_graph
                        else f"qfca_batch_run, {args.pipes} steps in flight",
-                       "l2": "inputs 1 GiB per step > L2 (no flush needed)"},
+                       "l2": "inputs 1 GiB per step > L2 (no flush needed)",
+                       "field": "class covariance (--aniso)" if args.aniso else "isotropic"},
             "e2e": {"value": round(e2e_value, 3), "unit": "maps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,
@@ -964,6 +1001,9 @@ def main(argv=None):
     ap.add_argument("--precision", default="bf16", choices=["f32", "bf16"])
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--pipes", type=int, default=3, help="batches in flight (one context, stream and graph each)")
+    ap.add_argument("--aniso", action="store_true",
+                    help="mix the batch's unit fields by a fixed class covariance (rotated-covariance patches become "
+                         "detectable); the default is the isotropic field")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-uneven", action="store_true", help="skip the 64-image uneven batch measurement")

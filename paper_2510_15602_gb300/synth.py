@@ -233,6 +233,35 @@ def make_image(wl: Workload | str, index: int, *, side: int | None = None, r: in
     return Image(X=X, mask=mask, r=rad, seed=seed, kinds=kinds)
 
 
+def kind_masks(wl: Workload | str, index: int, *, side: int | None = None, r: int | None = None,
+               C: int | None = None) -> dict:
+    """The anomaly masks of image ``index`` of ``wl``, one per anomaly kind planted
+    ({kind: uint8 (H, W)}; their union is ``make_image(...).mask``).
+
+    Replays the image's random draws in the order ``make_image`` takes them (size,
+    radius, the field's normals, then each anomaly) on an all-zero field: the
+    planters' draws do not depend on the feature values, so the masks are those of
+    the generated image, without the cost of blurring the field."""
+    if isinstance(wl, str):
+        wl = WORKLOADS[wl]
+    rng = np.random.default_rng(1000 * wl.config_id + index)
+    S = side if side is not None else int(rng.choice(np.asarray(wl.sizes)))
+    if r is None:
+        rng.choice(np.asarray(wl.radii))
+    Cc = C if C is not None else wl.C
+    p = int(math.ceil(4.0 * wl.sigma))
+    rng.standard_normal((Cc, S + 2 * p, S + 2 * p), dtype=np.float32)  # the field's draws
+    X = np.zeros((Cc, S, S), np.float32)
+    out = {}
+    lo, hi = wl.n_anom
+    for _ in range(int(rng.integers(lo, hi + 1))):
+        kind = str(rng.choice(np.asarray(wl.kinds)))
+        m = np.zeros((S, S), np.uint8)
+        _PLANTERS[kind](rng, X, m)
+        out[kind] = np.maximum(out.get(kind, np.zeros_like(m)), m)
+    return out
+
+
 def class_mixing(class_id: int, C: int, decay: float = 0.9) -> np.ndarray:
     """Channel-mixing matrix Q diag(sqrt(lambda)) of a texture class.
 

@@ -84,3 +84,37 @@ def test_measured_peaks_are_read(bench):
     p = bench.measured_peaks()
     assert p["source"] == "measured"
     assert p["hbm_gbs"] == m["hbm_gbs"] and p["bf16_tflops_sustained"] == m["bf16_tflops_sustained"]
+
+
+def test_per_kind_auroc(bench):
+    import numpy as np
+    rng = np.random.default_rng(2)
+    H = W = 20
+    s1, s2 = rng.random((H, W)), rng.random((H, W))
+    m1, m2 = np.zeros((H, W), np.uint8), np.zeros((H, W), np.uint8)
+    ka, kb = np.zeros((H, W), np.uint8), np.zeros((H, W), np.uint8)
+    ka[3:6, 3:6] = 1          # kind "a" scores high: perfectly separated
+    s1[3:6, 3:6] = 2.0
+    kb[10:14, 10:14] = 1      # kind "b" scores low: always below the normal pixels
+    s2[10:14, 10:14] = -1.0
+    m1 |= ka
+    m2 |= kb
+    out = bench.per_kind_auroc([s1, s2], [m1, m2], [{"a": ka}, {"b": kb}], border=2)
+    assert out == {"a": 1.0, "b": 0.0}
+    # a kind whose pixels all lie inside the discarded border has no positives
+    kc = np.zeros((H, W), np.uint8)
+    kc[0, :] = 1
+    out = bench.per_kind_auroc([s1], [kc], [{"c": kc}], border=2)
+    assert out == {"c": None}
+
+
+def test_aniso_inputs_keep_the_anomalies(bench):
+    import numpy as np
+    (X0, m0), = bench.make_inputs([2])
+    (X1, m1), = bench.make_inputs([2], aniso=True)
+    np.testing.assert_array_equal(m0, m1)          # same anomalies, same places
+    assert not np.allclose(X0, X1)
+    # away from the anomalies the mixed field has the class's channel spectrum (0.9^k, mean 1)
+    Z = X1[:, m1 == 0].astype(np.float64)
+    lam = np.sort(np.linalg.eigvalsh(np.cov(Z)))[::-1]
+    assert lam[0] > 5 * lam[len(lam) // 2]          # strongly anisotropic, unlike the unit field

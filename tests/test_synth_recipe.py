@@ -67,3 +67,16 @@ def test_class_mixing_spectrum():
 def test_random_orthogonal_is_orthogonal():
     Q = synth.random_orthogonal(np.random.default_rng(3), 40)
     np.testing.assert_allclose(Q.T @ Q, np.eye(40), atol=1e-12)
+
+
+@pytest.mark.parametrize("name,index", [("batch16_256_c256", 0), ("batch16_256_c256", 5), ("uneven64_c512", 7),
+                                        ("plain_128_c64", 0)])
+def test_kind_masks_replay_make_image(name, index):
+    img = synth.make_image(name, index, C=24)
+    km = synth.kind_masks(name, index, C=24)
+    assert set(km) == set(img.kinds)
+    union = np.zeros_like(img.mask)
+    for m in km.values():
+        assert m.dtype == np.uint8 and m.shape == img.mask.shape and m.any()
+        union |= m
+    np.testing.assert_array_equal(union, img.mask)
