@@ -302,6 +302,37 @@ def kernel_work(name: str, H: int, W: int, C: int, d: int, B: int, r: int, nimg:
     return {"bound": "hbm", "unit": "GB/s", "work": nimg * 4 * C, "peak_key": "hbm", "per_unit": "4C bytes per image"}
 
 
+def host_cpu() -> dict:
+    """The host's CPU model and the cores this process may use (for the CPU baseline)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:  # Arm hosts: /proc/cpuinfo names no model, lscpu does
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for ln in out.splitlines():
+                if ln.lower().startswith("model name:"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    try:
+        avail = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        avail = os.cpu_count()
+    return {"cpu_model": model, "cores_available": avail}
+
+
 def per_kind_auroc(scores, masks, kind_masks, border: int) -> dict:
     """Pixel AUROC per anomaly kind, pooled over the maps with the border discarded:
     the pixels of that kind's anomalies against every normal pixel (pixels of the
@@ -389,7 +420,7 @@ def run_reference(args):
                        "r": R, "sample": "1 of the 16 images per step (bounded CPU sample)",
                        "field": "class covariance (--aniso)" if getattr(args, "aniso", False) else "isotropic"},
             "cpu_baseline": {"value": round(value, 5), "unit": "maps/s", "cores": 1, "kind": "oracle",
-                             "sample": "image 0 of the 16-image batch, whole path, single thread"},
+                             "sample": "image 0 of the 16-image batch, whole path, single thread", **host_cpu()},
             "e2e": {"value": round(value, 5), "unit": "maps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -912,7 +943,8 @@ def run_ours(args):
         ref = oracle.pipeline(host[0][0], D, B, R)
         dt = time.perf_counter() - t0
         cpu = {"value": round(1.0 / dt, 5), "unit": "maps/s", "cores": 1, "kind": "oracle",
-               "sample": "image 0 of the batch: fit + project + quantize + window EMD, FP64, single thread"}
+               "sample": "image 0 of the batch: fit + project + quantize + window EMD, FP64, single thread",
+               **host_cpu()}
         auroc_oracle = auroc(ref["score"], masks[0])
 
     paper = run_paper_scoring(qfca, torch, pipe, masks, args) if extra and not args.skip_paper else None

@@ -118,3 +118,9 @@ def test_aniso_inputs_keep_the_anomalies(bench):
     Z = X1[:, m1 == 0].astype(np.float64)
     lam = np.sort(np.linalg.eigvalsh(np.cov(Z)))[::-1]
     assert lam[0] > 5 * lam[len(lam) // 2]          # strongly anisotropic, unlike the unit field
+
+
+def test_host_cpu(bench):
+    h = bench.host_cpu()
+    assert isinstance(h["cpu_model"], str) and h["cpu_model"]
+    assert isinstance(h["cores_available"], int) and h["cores_available"] >= 1
