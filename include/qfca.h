@@ -113,8 +113,10 @@ const char *qfca_version(void);
  *   d     number of components, 1 <= d <= min(C, 64).
  *   out   device pointers receiving mean[C], V[C][d], eigvals[d] (FP64).
  * Computes mu = (1/N) sum_p x_p and Sigma = (1/N) sum_p (x_p - mu)(x_p - mu)^T
- * as qfca_covariance does, then the top-d eigenpairs of Sigma in FP64
- * (Householder tridiagonalisation, bisection, inverse iteration).
+ * as qfca_covariance does, then the top-d eigenpairs of Sigma in float-float
+ * arithmetic (pairs of FP32 words, about 48 bits; FP64 in and out):
+ * Householder tridiagonalisation on a thread-block cluster, multisection on
+ * the Sturm count, inverse iteration, back-transformation.
  * Requires 2 <= C <= 512 and 2 <= H*W <= 2^23. */
 qfca_status qfca_fit_pca(qfca_ctx *ctx, const float *X, qfca_fmap desc, int d,
                          const qfca_basis *out, void *stream);
