@@ -294,9 +294,13 @@ typedef struct {
  * each component's image-wide min/max; the reference of each image is its
  * own global histogram (N_ref = H*W).
  *   scores  device f32 [nimg][H][W].
- * Results equal nimg separate calls of qfca_fit_pca, qfca_quantize and
- * qfca_score (same kernels, same arithmetic).  Requires 1 <= nimg <= 4096
- * and the limits of those entry points. */
+ * Given the same bases, results equal nimg separate calls of qfca_quantize and
+ * qfca_score bit for bit (same kernels, same arithmetic).  The eigensolver's
+ * cluster size grows while the launch leaves SMs free, so it depends on the
+ * number of matrices in the launch, and with it the order of the float-float
+ * reductions: bases agree with qfca_fit_pca's to about 1e-12 relative, and bit
+ * for bit when the cluster size is the same.  Requires 1 <= nimg <= 4096 and
+ * the limits of those entry points. */
 qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int d, int B, int r,
                            int precision, float *scores, const qfca_batch_outputs *extra, void *stream);
 
