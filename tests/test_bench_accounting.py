@@ -124,3 +124,35 @@ def test_host_cpu(bench):
     h = bench.host_cpu()
     assert isinstance(h["cpu_model"], str) and h["cpu_model"]
     assert isinstance(h["cores_available"], int) and h["cores_available"] >= 1
+
+
+def test_clock_sampler_summarises_the_timed_region(bench):
+    import datetime
+
+    class Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            pass
+
+    class Thread:
+        def join(self, timeout=None):
+            pass
+
+    base = datetime.datetime(2026, 1, 2, 3, 4, 5)
+
+    def line(dt, sm, pcap="Not Active", hw="Not Active"):
+        ts = (base + datetime.timedelta(seconds=dt)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return (0.0, f"{ts}, 0, {sm}, 2070, 900, 0x0, {hw}, Not Active, Not Active, {pcap}")
+
+    c = bench.ClockSampler("0")
+    c.proc, c.thread = Proc(), Thread()
+    c.lines = [line(0.00, 1400), line(0.05, 2070, pcap="Active"), line(0.10, 2060), line(0.40, 900, hw="Active")]
+    t0 = base.timestamp()
+    out = c.stop(t0 + 0.04, t0 + 0.12)   # the nvidia-smi stamps decide, not the arrival times
+    assert out["samples"] == 2 and out["samples_from"] == "inside the timed region"
+    assert out["sm_mhz"] == 2065.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]          # the hw_slowdown sample lies outside
+    out = c.stop(t0 + 0.20, t0 + 0.25)   # no sample inside: the nearest one is reported, and said so
+    assert out["samples"] == 1 and out["sm_mhz"] == 2060.0 and "nearest" in out["samples_from"]
