@@ -304,6 +304,19 @@ typedef struct {
 qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int d, int B, int r,
                            int precision, float *scores, const qfca_batch_outputs *extra, void *stream);
 
+/* qfca_batch_run_basis -- qfca_batch_run with the PCA bases already fitted
+ * (the basis-resident part of the path: Sec. 3.3 projection, Sec. 3.1
+ * quantisation with image-wide ranges and each image's own global histogram
+ * as reference, window histograms and EMD, channel mean).
+ *   mean  device f64 [nimg][C], V device f64 [nimg][C][d] (column k =
+ *         component k), e.g. from qfca_fit_pca or qfca_batch_run's extra
+ *         outputs; read, not written.
+ *   extra as qfca_batch_run (mean, V and eigvals there are ignored).
+ * Results equal qfca_batch_run's given the same bases, bit for bit. */
+qfca_status qfca_batch_run_basis(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, const double *mean,
+                                 const double *V, int d, int B, int r, int precision, float *scores,
+                                 const qfca_batch_outputs *extra, void *stream);
+
 /* qfca_batch_run_plus -- QFCA+ (Sec. 3.3) for nimg feature maps of one shape
  * stored one after the other in X: each image's PCA fitted with dres
  * components (Sec. 3.3 fit), its residual features over all C channels (the
@@ -367,18 +380,38 @@ qfca_status qfca_last_tiling(qfca_ctx *ctx, int *strip_width, int *band_height, 
  * GPU that loads the library until the process exits.  Hence:
  *  - images are limited to H*W <= 524288 pixels; larger ones return
  *    QFCA_ERR_UNSUPPORTED without enqueuing anything;
- *  - every call shares that array: calls that overlap on the GPU (on
- *    different streams, or from different threads, without ordering between
- *    them) race and give wrong results; serialise them on one stream;
+ *  - every call shares that array (each call clears the pixels it uses on its
+ *    stream before accumulating): calls that overlap on the GPU (on different
+ *    streams, or from different threads, without ordering between them) race
+ *    and give wrong results; serialise them on one stream;
  *  - work runs on the calling thread's current CUDA device; all pointers
- *    must belong to it.  The first call on a device looks up the array's
- *    device address (once per device); make that first call before any CUDA
- *    stream capture.
- * Arguments, layouts and the result are those of qfca_score; invalid
- * arguments return QFCA_ERR_INVALID_ARG, CUDA errors QFCA_ERR_CUDA. */
+ *    must belong to it.  Each call looks up the array's device address for
+ *    that device (a lookup, no allocation; the first call on a device may
+ *    load the library's module there, so make it before any CUDA stream
+ *    capture).
+ * Arguments, layouts and the result are those of qfca_score (d up to 512
+ * planes); invalid arguments return QFCA_ERR_INVALID_ARG, CUDA errors
+ * QFCA_ERR_CUDA.  A bounded wait inside the kernel that runs out is not
+ * reported by this call (it returns before the work runs): it sets a status
+ * word that qfca_score_noalloc_status reads. */
 qfca_status qfca_score_noalloc(const uint8_t *bins, int H, int W, int pitch, int d, int B, int r,
                                const uint32_t *ref_hist, uint32_t ref_total, float *score,
                                void *stream);
+
+/* Read and clear the status word of qfca_score_noalloc on the current device,
+ * ordered after the work already enqueued on `stream` (the call waits for that
+ * stream).  *out receives the word: 0 when every bounded wait of the calls
+ * since the last read completed, non-zero when one ran out (that call's score
+ * map is incomplete).  Returns QFCA_OK, QFCA_ERR_TIMEOUT (word non-zero) or
+ * QFCA_ERR_CUDA.  Allocates nothing. */
+qfca_status qfca_score_noalloc_status(int *out, void *stream);
+
+/* Testing aid for the timeout report of qfca_score_noalloc: with
+ * give_up_at_once != 0, each CTA's first tile wait in later calls gives up
+ * without probing (the kernel then waits for its copies in flight, sets the
+ * status word and returns, leaving that map incomplete); 0 restores the
+ * normal limit.  Process-wide; not for production use. */
+qfca_status qfca_score_noalloc_test_wait_limit(int give_up_at_once);
 
 /* ---------------------------------------------------------------- serving
  *
@@ -424,6 +457,9 @@ typedef struct {
     double t_submit_us;        /* host steady-clock stamps, microseconds since the session started */
     double t_start_us;         /* batch launched */
     double t_done_us;          /* batch completed on the GPU (stream callback) */
+    int stream;                /* index of the session stream the batch ran on (0 .. streams-1) */
+    int reserved;
+    uint64_t batch_seq;        /* sequence number of the batch in the session (1, 2, ...) */
 } qfca_result;
 
 /* Start the session's scheduler (one per context).  Allocates the arena and

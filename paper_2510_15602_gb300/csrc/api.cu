@@ -672,8 +672,11 @@ qfca_status qfca_batch_run_plus(qfca_ctx *ctx, const float *X, int nimg, qfca_fm
     return run_score(ctx, jobs.data(), nimg, C, B, b + o_sc, st, "qfca_batch_run_plus/score");
 }
 
-qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int d, int B, int r,
-                           int precision, float *scores, const qfca_batch_outputs *extra, void *stream) {
+// qfca_batch_run, and (mean_in, V_in given) qfca_batch_run_basis: the fit is
+// skipped and the given bases are used.
+static qfca_status batch_run_impl(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int d, int B, int r,
+                                  int precision, float *scores, const qfca_batch_outputs *extra, void *stream,
+                                  const double *mean_in, const double *V_in) {
     qfca_status s = check_ctx(ctx);
     if (s) return s;
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -698,7 +701,8 @@ qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap de
     // workspace: [fit | basis | Y | keys | project | bins | hist | lo/hi | score]
     size_t o = 0;
     auto take = [&](size_t bytes) { const size_t at = o; o = align_up(o + bytes, 256); return at; };
-    const size_t o_fit = take(fit_workspace_bytes(C, N, d, nimg));
+    const bool fit = mean_in == nullptr;
+    const size_t o_fit = take(fit ? fit_workspace_bytes(C, N, d, nimg) : 0);
     const size_t o_mean = take(sizeof(double) * (size_t)C * nimg);
     const size_t o_V = take(sizeof(double) * (size_t)C * d * nimg);
     const size_t o_ev = take(sizeof(double) * (size_t)d * nimg);
@@ -713,17 +717,21 @@ qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap de
     const size_t o_sc = take(score_jobs_workspace_bytes(jobs.data(), nimg, d));
     if ((s = ensure_ws(ctx, o, (cudaStream_t)stream))) return s;
     char *b = (char *)ctx->ws;
-    double *mean = (extra && extra->mean) ? extra->mean : (double *)(b + o_mean);
-    double *V = (extra && extra->V) ? extra->V : (double *)(b + o_V);
-    double *ev = (extra && extra->eigvals) ? extra->eigvals : (double *)(b + o_ev);
+    const double *mean = mean_in ? mean_in : (extra && extra->mean) ? extra->mean : (double *)(b + o_mean);
+    const double *V = V_in ? V_in : (extra && extra->V) ? extra->V : (double *)(b + o_V);
     uint8_t *bins = (extra && extra->bins) ? extra->bins : (uint8_t *)(b + o_bins);
     uint32_t *hist = (extra && extra->ref_hist) ? extra->ref_hist : (uint32_t *)(b + o_hist);
     float *lo = (extra && extra->lo) ? extra->lo : (float *)(b + o_lohi);
     float *hi = (extra && extra->hi) ? extra->hi : (float *)(b + o_lohi) + (size_t)d * nimg;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = launch_fit(X, desc.layout, desc.H, desc.W, C, d, nimg, mean, V, ev, b + o_fit, ctx->status_dev, st);
-    if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "eigensolver shape C=%d d=%d", C, d);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run/fit");
+    cudaError_t e = cudaSuccess;
+    if (fit) {
+        double *ev = (extra && extra->eigvals) ? extra->eigvals : (double *)(b + o_ev);
+        e = launch_fit(X, desc.layout, desc.H, desc.W, C, d, nimg, const_cast<double *>(mean),
+                       const_cast<double *>(V), ev, b + o_fit, ctx->status_dev, st);
+        if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "eigensolver shape C=%d d=%d", C, d);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run/fit");
+    }
     float *Y = (float *)(b + o_Y);
     uint32_t *mm = (uint32_t *)(b + o_mm);
     e = launch_project(X, desc.layout, desc.H, desc.W, C, mean, V, d, nimg, precision, Y, mm, b + o_pj,
@@ -739,6 +747,18 @@ qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap de
         jobs[i].score = scores + (size_t)i * N;
     }
     return run_score(ctx, jobs.data(), nimg, d, B, b + o_sc, st, "qfca_batch_run/score");
+}
+
+qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int d, int B, int r,
+                           int precision, float *scores, const qfca_batch_outputs *extra, void *stream) {
+    return batch_run_impl(ctx, X, nimg, desc, d, B, r, precision, scores, extra, stream, nullptr, nullptr);
+}
+
+qfca_status qfca_batch_run_basis(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, const double *mean,
+                                 const double *V, int d, int B, int r, int precision, float *scores,
+                                 const qfca_batch_outputs *extra, void *stream) {
+    if (!mean || !V) return fail(ctx, QFCA_ERR_INVALID_ARG, "mean / V NULL");
+    return batch_run_impl(ctx, X, nimg, desc, d, B, r, precision, scores, extra, stream, mean, V);
 }
 
 qfca_status qfca_score_batch(qfca_ctx *ctx, const qfca_image *imgs, int n, int C, int layout, int d, int B,

@@ -662,8 +662,8 @@ size_t smem_plan(int n, int d, int R, long *region0, int *nslots) {
 
 // Cluster size: the smallest R whose shared-memory plan fits, raised for small
 // batches (a matrix's reduction is latency-bound, so idle SMs are better spent
-// on fewer rows per CTA): aim for about half of the 152 SMs across the batch.
-int pick_R(int n, int d, int mats) {
+// on fewer rows per CTA): aim for about half of the SMs across the batch.
+int pick_R(int n, int d, int mats, int n_sm) {
     int R = 0;
     for (int r = 2; r <= 8; r *= 2) {
         long reg;
@@ -671,7 +671,7 @@ int pick_R(int n, int d, int mats) {
         if (smem_plan(n, d, r, &reg, &ns) <= kSmemMax) { R = r; break; }
     }
     if (R == 0) return 0;
-    while (R < 8 && 2 * R * mats <= 76) R *= 2;
+    while (R < 8 && 2 * R * mats <= n_sm / 2) R *= 2;
     return R;
 }
 
@@ -707,14 +707,16 @@ size_t eig_workspace_bytes(int n, int d, int mats) { return eig_plan(n, d, mats)
 // cov_ff: [mats][n][n] float-float pairs (hi, lo) of the covariance.
 cudaError_t launch_eig(const void *cov_ff, int n, int d, int mats, double *V, double *eigvals, void *ws,
                        cudaStream_t st) {
-    const int R = pick_R(n, d, mats);
+    int dev = 0, n_sm = 0;
+    cudaError_t eq = cudaGetDevice(&dev);
+    if (eq == cudaSuccess) eq = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (eq != cudaSuccess) return eq;
+    const int R = pick_R(n, d, mats, n_sm);
     if (R == 0) return cudaErrorNotSupported;
     long region0 = 0;
     int nslots = 1;
     const size_t smem = smem_plan(n, d, R, &region0, &nslots);
     static DeviceOnce attrs;
-    int dev = 0;
-    cudaGetDevice(&dev);
     cudaError_t e0 = device_once(attrs, dev, [] {
         return cudaFuncSetAttribute(k_eig_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     });

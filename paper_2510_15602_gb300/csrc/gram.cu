@@ -516,6 +516,8 @@ cudaError_t launch_gram_cov_jobs(const FitJob *jobs, int n, int layout, int C, d
         return cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     });
     if (e != cudaSuccess) return e;
+    int n_sm = 0;
+    if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
         const int m = n - i0 < kMaxBatch ? n - i0 : kMaxBatch;
         FitParams p;
@@ -532,7 +534,7 @@ cudaError_t launch_gram_cov_jobs(const FitJob *jobs, int n, int layout, int C, d
         }
         p.vec_ok = vec_ok;
         // about two waves of one CTA per SM (one for a single image), chunks a multiple of the window
-        const long target = m == 1 ? 152 : 2 * 152;
+        const long target = m == 1 ? n_sm : 2L * n_sm;
         long chunk = (total_px * g.n_pairs + target - 1) / target;
         chunk = (chunk + kWin - 1) / kWin * kWin;
         if (chunk < kWin) chunk = kWin;

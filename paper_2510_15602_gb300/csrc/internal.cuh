@@ -180,6 +180,11 @@ bool score_shape_ok(int B, int r);
 // cudaErrorNotSupported: nothing was enqueued.
 cudaError_t launch_score_jobs(const ScoreJob *jobs, int n, int d, int B, void *ws, bool ws_accumulates, int *status,
                               cudaStream_t st, const ScoreTiling *tiling, ScoreTiling *chosen);
+// The same with a given probe limit for each CTA's first tile wait (the
+// allocation-free path's timeout test gives 0).
+cudaError_t launch_score_jobs_limited(const ScoreJob *jobs, int n, int d, int B, void *ws, bool ws_accumulates,
+                                      int *status, cudaStream_t st, const ScoreTiling *tiling, ScoreTiling *chosen,
+                                      uint32_t first_wait_tries);
 
 // One image of the paper's scoring (assoc.cu): bins [d][H][pitch], reference
 // [d][B] with N_ref = Nref, window radius r, final smoothing sigma_s (<= 0:

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <atomic>
 #include <mutex>
 
 #include "internal.cuh"
@@ -46,6 +47,7 @@ struct ScoreImgP {
 struct ScoreParams {
     int n, d, B, SW, TH, kg, n_kg;
     uint32_t tile_bytes;
+    uint32_t first_wait_tries;  // probes of each CTA's first tile wait (kTmaTries; fewer only to test the timeout path)
     ScoreImgP img[kMaxBatch];
     CUtensorMap tmap[kMaxBatch];  // bins of image i as [d][H][pitch] u8, box {TCp_i, TH + 2 r_i, 1}
 };
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ S
                 rv[j] = b < B ? __ldg(&ref_hist[(long)k * B + b]) : 0u;
             }
         }
-        const bool ok = tc::mbar_wait(&bar[buf], ((k - k0) >> 1) & 1, kTmaTries);
+        const bool ok = tc::mbar_wait(&bar[buf], ((k - k0) >> 1) & 1, k == k0 ? p.first_wait_tries : kTmaTries);
         waited++;
         if (__syncthreads_or(!ok)) {
             failed = true;
@@ -376,7 +378,7 @@ cudaError_t ensure_attrs(int *n_sm) {
 
 // One launch of at most kMaxBatch jobs.
 cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, bool ws_accumulates, int *status,
-                        cudaStream_t st, const ScoreTiling *tiling, ScoreTiling *chosen) {
+                        cudaStream_t st, const ScoreTiling *tiling, ScoreTiling *chosen, uint32_t first_wait_tries) {
     int rmax = 1;
     bool narrow = true, want_numer = false;
     for (int i = 0; i < n; i++) {
@@ -439,6 +441,7 @@ cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, boo
     memset(&p, 0, sizeof(p));
     p.n = n, p.d = d, p.B = B, p.SW = SW, p.TH = TH, p.kg = kg, p.n_kg = n_kg;
     p.tile_bytes = (uint32_t)align_up((size_t)(TH + 2 * rmax) * tcp_of(SW, rmax), 128);
+    p.first_wait_tries = first_wait_tries;
     FinParams f;
     memset(&f, 0, sizeof(f));
     f.n = n, f.d = d;
@@ -511,10 +514,17 @@ bool score_shape_ok(int B, int r) {
 
 cudaError_t launch_score_jobs(const ScoreJob *jobs, int n, int d, int B, void *ws, bool ws_accumulates, int *status,
                               cudaStream_t st, const ScoreTiling *tiling, ScoreTiling *chosen) {
+    return launch_score_jobs_limited(jobs, n, d, B, ws, ws_accumulates, status, st, tiling, chosen, kTmaTries);
+}
+
+cudaError_t launch_score_jobs_limited(const ScoreJob *jobs, int n, int d, int B, void *ws, bool ws_accumulates,
+                                      int *status, cudaStream_t st, const ScoreTiling *tiling, ScoreTiling *chosen,
+                                      uint32_t first_wait_tries) {
     size_t off = 0;
     for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
         const int m = std::min(kMaxBatch, n - i0);
-        cudaError_t e = score_chunk(jobs + i0, m, d, B, (char *)ws + off, ws_accumulates, status, st, tiling, chosen);
+        cudaError_t e = score_chunk(jobs + i0, m, d, B, (char *)ws + off, ws_accumulates, status, st, tiling, chosen,
+                                    first_wait_tries);
         if (e != cudaSuccess) return e;
         for (int i = i0; i < i0 + m; i++)
             off += align_up((ws_accumulates ? 1 : (size_t)d) * sizeof(unsigned long long) * jobs[i].H * jobs[i].W, 256);
@@ -525,18 +535,33 @@ cudaError_t launch_score_jobs(const ScoreJob *jobs, int n, int d, int B, void *w
 // ---------------------------------------------------------------- allocation-free variant
 
 // Scratch of qfca_score_noalloc: the per-pixel sums of the integer EMD
-// numerators, u64 [H][W].  It lives in the module image, so every device that
-// loads the library holds it (4 MiB) until the process exits; no call
-// allocates anything.
+// numerators, u64 [H][W], and the status word of its bounded waits.  Both live
+// in the module image, so every device that loads the library holds them
+// (4 MiB) until the process exits; no call allocates anything.
 namespace {
 constexpr long kNoAllocMaxPixels = 1L << 19;
 __device__ __align__(256) unsigned long long g_noalloc_acc[kNoAllocMaxPixels];
-__device__ int g_noalloc_flag;  // bounded-wait status of the variant's kernels
+__device__ __align__(256) int g_noalloc_flag;
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-unsigned long long *g_noalloc_ptr[kMaxDevices] = {};
-int *g_noalloc_status[kMaxDevices] = {};
+// Probes of each CTA's first tile wait in the allocation-free path: the
+// normal limit, or 0 (give up at once) while a test checks the timeout report.
+std::atomic<uint32_t> g_noalloc_first_tries{kTmaTries};
+
+// Device addresses of the two symbols for the current device.  In host code a
+// __device__ symbol's name is only a host-side stand-in; the address is looked
+// up on every call (a cheap table lookup that allocates nothing), so it stays
+// valid if the application resets the device and the module is reloaded.
+qfca_status noalloc_symbols(unsigned long long **acc, int **flag) {
+    void *p = nullptr, *f = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_acc) != cudaSuccess || !p ||
+        cudaGetSymbolAddress(&f, g_noalloc_flag) != cudaSuccess || !f) {
+        cudaGetLastError();
+        return QFCA_ERR_CUDA;
+    }
+    *acc = (unsigned long long *)p;
+    *flag = (int *)f;
+    return QFCA_OK;
+}
 }  // namespace
 
 }  // namespace qfca
@@ -547,38 +572,45 @@ extern "C" qfca_status qfca_score_noalloc(const uint8_t *bins, int H, int W, int
     using namespace qfca;
     if (!bins || !ref_hist || !score) return QFCA_ERR_INVALID_ARG;
     if (H < 1 || W < 1 || pitch < W || pitch % 16 != 0 || ((uintptr_t)bins & 15) != 0) return QFCA_ERR_INVALID_ARG;
-    if (d < 1 || d > kMaxD || B < 2 || B > kMaxB || r < 1 || 2 * r + 1 > 127 || ref_total < 1)
+    if (d < 1 || d > kMaxPlanes || B < 2 || B > kMaxB || r < 1 || 2 * r + 1 > 127 || ref_total < 1)
         return QFCA_ERR_INVALID_ARG;
     if ((long)H * W > kNoAllocMaxPixels) return QFCA_ERR_UNSUPPORTED;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        cudaGetLastError();
-        return QFCA_ERR_CUDA;
-    }
-    unsigned long long *acc;
-    {
-        // once per device, with that device current: the device address of the
-        // scratch array (in host code the symbol is only a stand-in)
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            void *p = nullptr, *f = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_acc) != cudaSuccess || !p ||
-                cudaGetSymbolAddress(&f, g_noalloc_flag) != cudaSuccess || !f) {
-                cudaGetLastError();
-                return QFCA_ERR_CUDA;
-            }
-            g_noalloc_ptr[dev] = (unsigned long long *)p;
-            g_noalloc_status[dev] = (int *)f;
-        }
-        acc = g_noalloc_ptr[dev];
-    }
+    unsigned long long *acc = nullptr;
+    int *flag = nullptr;
+    const qfca_status s = noalloc_symbols(&acc, &flag);
+    if (s != QFCA_OK) return s;
     const ScoreJob job{bins, H, W, pitch, r, ref_hist, ref_total, score, nullptr};
-    const cudaError_t e = launch_score_jobs(&job, 1, d, B, acc, true, g_noalloc_status[dev], (cudaStream_t)stream,
-                                            nullptr, nullptr);
+    const cudaError_t e = launch_score_jobs_limited(&job, 1, d, B, acc, true, flag, (cudaStream_t)stream, nullptr,
+                                                    nullptr, g_noalloc_first_tries.load());
     if (e == cudaErrorNotSupported) return QFCA_ERR_UNSUPPORTED;
     if (e != cudaSuccess) {
         cudaGetLastError();
         return QFCA_ERR_CUDA;
     }
+    return QFCA_OK;
+}
+
+extern "C" qfca_status qfca_score_noalloc_status(int *out, void *stream) {
+    using namespace qfca;
+    if (!out) return QFCA_ERR_INVALID_ARG;
+    unsigned long long *acc = nullptr;
+    int *flag = nullptr;
+    qfca_status s = noalloc_symbols(&acc, &flag);
+    if (s != QFCA_OK) return s;
+    int word = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&word, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return QFCA_ERR_CUDA;
+    }
+    *out = word;
+    return word ? QFCA_ERR_TIMEOUT : QFCA_OK;
+}
+
+extern "C" qfca_status qfca_score_noalloc_test_wait_limit(int give_up_at_once) {
+    qfca::g_noalloc_first_tries.store(give_up_at_once ? 0u : qfca::kTmaTries);
     return QFCA_OK;
 }

@@ -82,6 +82,7 @@ struct ServeState {
     std::unordered_map<uint64_t, char> done;
     std::vector<std::unique_ptr<Batch>> inflight;
     uint64_t next_ticket = 1;
+    uint64_t next_batch = 1;
     std::mutex m;
     std::condition_variable cv_sched, cv_done;
     bool stop = false;
@@ -272,11 +273,14 @@ void scheduler(ServeState *S) {
             auto b = std::make_unique<Batch>();
             b->S = S, b->stream = sidx, b->off = off, b->bytes = bytes, b->reqs = std::move(take);
             b->t_start = S->now_us();
+            const uint64_t seq = S->next_batch++;
             for (const Pending &p : b->reqs) {
                 auto it = S->results.find(p.ticket);
                 if (it != S->results.end()) {
                     it->second.t_start_us = b->t_start;
                     it->second.batch_size = (int)b->reqs.size();
+                    it->second.stream = sidx;
+                    it->second.batch_seq = seq;
                 }
             }
             S->stream_busy[sidx] = 1;

@@ -85,6 +85,8 @@ class BatchOutputs(ctypes.Structure):
 
 _lib.qfca_batch_run.argtypes = [_P, _P, _I, Fmap, _I, _I, _I, _I, _P, ctypes.POINTER(BatchOutputs), _P]
 _lib.qfca_batch_run.restype = _I
+_lib.qfca_batch_run_basis.argtypes = [_P, _P, _I, Fmap, _P, _P, _I, _I, _I, _I, _P, ctypes.POINTER(BatchOutputs), _P]
+_lib.qfca_batch_run_basis.restype = _I
 _lib.qfca_batch_run_plus.argtypes = [_P, _P, _I, Fmap, _I, _I, _I, _P, ctypes.POINTER(BatchOutputs), _P]
 _lib.qfca_batch_run_plus.restype = _I
 
@@ -140,7 +142,8 @@ class Request(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("batch_size", ctypes.c_int), ("t_submit_us", ctypes.c_double),
-                ("t_start_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+                ("t_start_us", ctypes.c_double), ("t_done_us", ctypes.c_double), ("stream", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("batch_seq", ctypes.c_uint64)]
 
 
 REQ_HOST_INPUT, REQ_HOST_OUTPUT = 1, 2
@@ -497,6 +500,29 @@ def batch_run(X: torch.Tensor, d: int, B: int, r: int, precision="bf16", ctx: Co
     ctx.check(_lib.qfca_batch_run(ctx.handle, _ptr(X), nimg, fm, d, B, r, _PREC[precision], _ptr(scores),
                                   ctypes.byref(ext) if ext is not None else None, _P(_stream_ptr(stream))))
     return (scores, ex) if extras else scores
+
+
+def batch_run_basis(X: torch.Tensor, mean: torch.Tensor, V: torch.Tensor, B: int, r: int, precision="bf16",
+                    ctx: Context | None = None, stream=None, scores: torch.Tensor | None = None):
+    """qfca_batch_run_basis: the path after the fit for a batch X [nimg, C, H, W]
+    (NCHW maps) with given bases mean [nimg, C] and V [nimg, C, d] (FP64).
+    Returns scores [nimg, H, W] (f32)."""
+    _check_dev(X, "X", torch.float32)
+    _check_dev(mean, "mean", torch.float64)
+    _check_dev(V, "V", torch.float64)
+    if X.dim() != 4 or V.dim() != 3:
+        raise ValueError("X must be [nimg, C, H, W] and V [nimg, C, d]")
+    nimg, C, H, W = (int(v) for v in X.shape)
+    d = int(V.shape[2])
+    if tuple(mean.shape) != (nimg, C) or tuple(V.shape[:2]) != (nimg, C):
+        raise ValueError("mean must be [nimg, C] and V [nimg, C, d]")
+    ctx = ctx or default_context(X.device.index)
+    if scores is None:
+        scores = torch.empty(nimg, H, W, dtype=torch.float32, device=X.device)
+    fm = Fmap(H, W, C, NCHW)
+    ctx.check(_lib.qfca_batch_run_basis(ctx.handle, _ptr(X), nimg, fm, _ptr(mean), _ptr(V), d, B, r,
+                                        _PREC[precision], _ptr(scores), None, _P(_stream_ptr(stream))))
+    return scores
 
 
 def batch_run_plus(X: torch.Tensor, dres: int, B: int, r: int, ctx: Context | None = None, stream=None,

@@ -66,14 +66,25 @@ def test_serving_results_equal_alone_and_in_the_mix(q, precision):
             assert res is not None, "request did not finish"
             got.append(res)
         sizes_seen = set()
+        batches = {}
         for (k, X, r), (res, sc) in zip(reqs, got):
             assert res.status == 0
             assert res.t_submit_us <= res.t_start_us <= res.t_done_us
             assert 1 <= res.batch_size <= 4
+            assert 0 <= res.stream < 2 and res.batch_seq >= 1
             sizes_seen.add(res.batch_size)
+            batches[res.batch_seq] = (res.stream, res.t_start_us, res.t_done_us, res.batch_size)
             ref = _alone(q, ctx, X, classes[k], d, B, r, precision)
             torch.cuda.synchronize()
             np.testing.assert_array_equal(sc.cpu().numpy(), ref.cpu().numpy())
+        # the mix: some request shared its batch with others ...
+        assert max(sizes_seen) > 1, sizes_seen
+        # ... and two batches were in flight on the device at once (on different
+        # streams, the later one launched before the earlier one completed)
+        seqs = sorted(batches)
+        overlap = any(batches[a][0] != batches[b][0] and batches[b][1] < batches[a][2]
+                      for i, a in enumerate(seqs) for b in seqs[i + 1:])
+        assert overlap, batches
     finally:
         srv.stop()
     assert ctx.device_status() == 0
