@@ -113,10 +113,19 @@ const char *qfca_version(void);
  *   d     number of components, 1 <= d <= min(C, 64).
  *   out   device pointers receiving mean[C], V[C][d], eigvals[d] (FP64).
  * Computes mu = (1/N) sum_p x_p and Sigma = (1/N) sum_p (x_p - mu)(x_p - mu)^T
- * as qfca_covariance does, then the top-d eigenpairs of Sigma in float-float
- * arithmetic (pairs of FP32 words, about 48 bits; FP64 in and out):
- * Householder tridiagonalisation on a thread-block cluster, multisection on
- * the Sturm count, inverse iteration, back-transformation.
+ * as qfca_covariance does (an FP32-class covariance: each entry within
+ * 2^-25 R_i R_j of the exact one, R_c the channel's power-of-two range), then
+ * the top-d eigenpairs of that Sigma.  For C <= 256 and d <= 32: FP32
+ * Householder tridiagonalisation, multisection on the Sturm count, inverse
+ * iteration and back-transformation in one CTA per matrix, then one Newton
+ * correction per eigenvector whose residual A x - sigma x is formed in
+ * float-float (pairs of FP32 words, about 48 bits), and float-float Rayleigh
+ * quotients as eigenvalues; a matrix whose relative residual
+ * |A x - lambda x| / |x| exceeds the context's tolerance (default 1e-10) times
+ * |lambda_max| is solved again by the float-float solver below.  Otherwise
+ * (and for those matrices): float-float Householder tridiagonalisation on a
+ * thread-block cluster, multisection, inverse iteration,
+ * back-transformation.  FP64 in and out.
  * Requires 2 <= C <= 512 and 2 <= H*W <= 2^23. */
 qfca_status qfca_fit_pca(qfca_ctx *ctx, const float *X, qfca_fmap desc, int d,
                          const qfca_basis *out, void *stream);
@@ -295,12 +304,13 @@ typedef struct {
  * own global histogram (N_ref = H*W).
  *   scores  device f32 [nimg][H][W].
  * Given the same bases, results equal nimg separate calls of qfca_quantize and
- * qfca_score bit for bit (same kernels, same arithmetic).  The eigensolver's
- * cluster size grows while the launch leaves SMs free, so it depends on the
- * number of matrices in the launch, and with it the order of the float-float
- * reductions: bases agree with qfca_fit_pca's to about 1e-12 relative, and bit
- * for bit when the cluster size is the same.  Requires 1 <= nimg <= 4096 and
- * the limits of those entry points. */
+ * qfca_score bit for bit (same kernels, same arithmetic).  The FP32 + Newton
+ * eigensolver (C <= 256, d <= 32) works on one matrix per CTA, so its bases do
+ * not depend on the batch; the float-float solver (larger shapes, and matrices
+ * that fail the residual check) grows its cluster size while the launch leaves
+ * SMs free, which changes the order of its reductions with the number of
+ * matrices: its bases agree with qfca_fit_pca's to about 1e-12 relative.
+ * Requires 1 <= nimg <= 4096 and the limits of those entry points. */
 qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int d, int B, int r,
                            int precision, float *scores, const qfca_batch_outputs *extra, void *stream);
 
@@ -490,6 +500,17 @@ qfca_status qfca_poll(qfca_ctx *ctx, uint64_t ticket, int timeout_us, qfca_resul
  * the session's device memory.  Unpolled results are discarded.  No other
  * serving call on the context may run concurrently with this one. */
 qfca_status qfca_serve_stop(qfca_ctx *ctx);
+
+/* Residual bound of the fit's FP32 + Newton eigensolver, relative to the
+ * largest eigenvalue (default 1e-10): matrices above it are solved again by
+ * the float-float solver.  0 sends every matrix to the float-float solver.
+ * Applies to later fits on this context.  tol >= 0. */
+qfca_status qfca_set_eig_tolerance(qfca_ctx *ctx, double tol);
+
+/* Synchronise the device, then read and clear the number of matrices that the
+ * float-float solver solved again (see qfca_set_eig_tolerance) since the last
+ * read. */
+qfca_status qfca_eig_redo_count(qfca_ctx *ctx, uint64_t *out);
 
 /* ---------------------------------------------------------------- tracing */
 

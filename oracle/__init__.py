@@ -74,13 +74,15 @@ def _load():
             lib.orc_ref_hist.restype = None
             lib.orc_window_hist.argtypes = [P, I, I, I, I, I, I, P]
             lib.orc_window_hist.restype = L
-            lib.orc_score.argtypes = [P, I, I, I, I, I, P, ctypes.c_uint64, P, P, P]
+            lib.orc_score.argtypes = [P, I, I, I, I, I, P, ctypes.c_uint64, P, P, P, P, P]
             lib.orc_score.restype = I
             lib.orc_score_at.argtypes = [P, I, I, I, I, I, P, ctypes.c_uint64, I, I, P]
             lib.orc_score_at.restype = ctypes.c_double
             lib.orc_alg1.argtypes = [P, P, I, ctypes.c_int64, ctypes.c_int64, P]
+            lib.orc_alg1_values.argtypes = [P, P, I, ctypes.c_int64, ctypes.c_int64, P, P]
+            lib.orc_alg1_values.restype = I
             lib.orc_alg1.restype = I
-            lib.orc_assoc.argtypes = [P, I, I, I, I, I, P, ctypes.c_uint64, ctypes.c_double, P, P, P]
+            lib.orc_assoc.argtypes = [P, I, I, I, I, I, P, ctypes.c_uint64, ctypes.c_double, P, P, P, P, P]
             lib.orc_assoc.restype = I
             lib.orc_blur.argtypes = [P, I, I, ctypes.c_double, P]
             lib.orc_blur.restype = I
@@ -194,10 +196,21 @@ def window_hist(qk: np.ndarray, B: int, r: int, y: int, x: int):
     return L, int(n)
 
 
-def score(q: np.ndarray, B: int, r: int, R: np.ndarray, Nref: int | None = None):
+def _ranges(lo, hi, d):
+    if lo is None:
+        return None, None
+    lo = np.ascontiguousarray(np.asarray(lo, np.float64).reshape(d))
+    hi = np.ascontiguousarray(np.asarray(hi, np.float64).reshape(d))
+    return lo, hi
+
+
+def score(q: np.ndarray, B: int, r: int, R: np.ndarray, Nref: int | None = None, lo=None, hi=None):
     """Window histograms + 1-D EMD to R + mean over components (Sec. 3.1, Sec. 3).
 
-    Returns (score float64 [H,W], numer int64 [d,H,W], nloc int32 [H,W]).
+    Bin units by default; with each component's quantisation range lo/hi [d]
+    the EMD is in value units (distances of the quantized values, the cost of
+    Algorithm 1 as Sec. 3.1 states it).
+    Returns (score float64 [H,W], numer int64 [d,H,W] (bin units), nloc int32 [H,W]).
     """
     q = np.ascontiguousarray(q, np.uint8)
     d, H, W = q.shape
@@ -207,7 +220,9 @@ def score(q: np.ndarray, B: int, r: int, R: np.ndarray, Nref: int | None = None)
     s = np.zeros((H, W), np.float64)
     numer = np.zeros((d, H, W), np.int64)
     nloc = np.zeros((H, W), np.int32)
-    rc = _load().orc_score(_p(q), d, H, W, B, r, _p(R), int(Nref), _p(s), _p(numer), _p(nloc))
+    lo, hi = _ranges(lo, hi, d)
+    rc = _load().orc_score(_p(q), d, H, W, B, r, _p(R), int(Nref), _p(s), _p(numer), _p(nloc),
+                           None if lo is None else _p(lo), None if hi is None else _p(hi))
     if rc < 0:
         raise MemoryError("oracle score")
     return s, numer, nloc
@@ -242,6 +257,22 @@ def alg1(P: np.ndarray, R: np.ndarray, Nloc: int | None = None, Nref: int | None
     if steps < 0:
         raise MemoryError("oracle alg1")
     return En, int(steps)
+
+
+def alg1_values(P: np.ndarray, R: np.ndarray, Qv: np.ndarray, Nloc: int | None = None, Nref: int | None = None):
+    """Algorithm 1 with the cost in value units: transported amounts charged at
+    |Q_i - Q_j| (Qv [B] the quantized values).  Returns (Ev float64 [B], steps)."""
+    P = np.ascontiguousarray(P, np.int64)
+    R = np.ascontiguousarray(R, np.int64)
+    Qv = np.ascontiguousarray(Qv, np.float64)
+    B = P.shape[0]
+    Nloc = int(P.sum()) if Nloc is None else int(Nloc)
+    Nref = int(R.sum()) if Nref is None else int(Nref)
+    Ev = np.zeros(B, np.float64)
+    steps = _load().orc_alg1_values(_p(P), _p(R), B, Nloc, Nref, _p(Qv), _p(Ev))
+    if steps < 0:
+        raise MemoryError("oracle alg1_values")
+    return Ev, int(steps)
 
 
 def residual(X: np.ndarray, mean: np.ndarray, V: np.ndarray, layout: int = NCHW) -> np.ndarray:
@@ -293,11 +324,13 @@ def blur(a: np.ndarray, sigma: float) -> np.ndarray:
     return out
 
 
-def assoc(q: np.ndarray, B: int, r: int, R: np.ndarray, Nref: int | None = None, sigma_s: float = 1.0):
+def assoc(q: np.ndarray, B: int, r: int, R: np.ndarray, Nref: int | None = None, sigma_s: float = 1.0,
+          lo=None, hi=None):
     """The paper's scoring: Algorithm 1 per window and component, error-to-pixel
     association (each pixel averages its own bin's error over the windows that
     contain it, sigma_p = infinity), mean over components, Gaussian blur sigma_s
     (Sec. 3.1 and its association paragraph; smoothing as in the sigma_s study).
+    Bin units by default; value units with each component's range lo/hi [d].
 
     Returns (score float64 [H,W], raw float64 [H,W] before the blur,
     comp float64 [d,H,W] per-component associated errors).
@@ -310,7 +343,9 @@ def assoc(q: np.ndarray, B: int, r: int, R: np.ndarray, Nref: int | None = None,
     s = np.zeros((H, W), np.float64)
     raw = np.zeros((H, W), np.float64)
     comp = np.zeros((d, H, W), np.float64)
-    rc = _load().orc_assoc(_p(q), d, H, W, B, r, _p(R), int(Nref), float(sigma_s), _p(raw), _p(s), _p(comp))
+    lo, hi = _ranges(lo, hi, d)
+    rc = _load().orc_assoc(_p(q), d, H, W, B, r, _p(R), int(Nref), float(sigma_s), _p(raw), _p(s), _p(comp),
+                           None if lo is None else _p(lo), None if hi is None else _p(hi))
     if rc < 0:
         raise MemoryError("oracle assoc")
     return s, raw, comp

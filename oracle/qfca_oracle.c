@@ -296,11 +296,23 @@ long orc_window_hist(const uint8_t *q, int H, int W, int B, int r, int y, int x,
     return n;
 }
 
+/* The quantized value of bin b of a component quantized between lo and hi
+ * into B equally spaced values (Sec. 3.1): the centre of the bin. */
+static double bin_value(double lo, double hi, int B, int b)
+{
+    return lo + ((double)b + 0.5) * (hi - lo) / (double)B;
+}
+
 /* Window histogram + 1-D EMD per component + mean over components.
  * q: [d][H][W] bins; R: [d][B]; Nref: reference mass.  Writes score[H][W]
- * (FP64), and optionally numer[d][H][W] (exact D) and nloc[H][W]. */
+ * (FP64), and optionally numer[d][H][W] (exact D, bin units) and nloc[H][W].
+ * Units: with lo/hi NULL the distance between bins a and b is |a - b| (bin
+ * units); with lo/hi ([d], the component's quantisation range) it is the
+ * distance of the quantized values |Q_a - Q_b| (value units), so the W1
+ * closed form weighs the CDF difference after bin b by Q_{b+1} - Q_b. */
 int orc_score(const uint8_t *q, int d, int H, int W, int B, int r, const uint32_t *R,
-              uint64_t Nref, double *score, int64_t *numer, int32_t *nloc)
+              uint64_t Nref, double *score, int64_t *numer, int32_t *nloc, const double *lo,
+              const double *hi)
 {
     long N = (long)H * W;
     int64_t *L = (int64_t *)malloc(sizeof(int64_t) * (B > 0 ? B : 1));
@@ -321,15 +333,19 @@ int orc_score(const uint8_t *q, int d, int H, int W, int B, int r, const uint32_
                     for (int xx = x0; xx <= x1; xx++)
                         L[q[(long)k * N + (long)yy * W + xx]]++;
                 int64_t cumL = 0, cumR = 0, D = 0;
+                double Dv = 0.0;
                 for (int b = 0; b < B; b++) {
                     cumL += L[b];
                     cumR += (int64_t)R[(long)k * B + b];
                     int64_t diff = cumL * (int64_t)Nref - cumR * Nloc;
-                    D += diff < 0 ? -diff : diff;
+                    int64_t ad = diff < 0 ? -diff : diff;
+                    D += ad;
+                    if (lo && b + 1 < B)
+                        Dv += (double)ad * (bin_value(lo[k], hi[k], B, b + 1) - bin_value(lo[k], hi[k], B, b));
                 }
                 if (numer)
                     numer[(long)k * N + (long)y * W + x] = D;
-                s += (double)D / ((double)Nloc * (double)Nref);
+                s += (lo ? Dv : (double)D) / ((double)Nloc * (double)Nref);
             }
             score[(long)y * W + x] = s / (double)d;
         }
@@ -413,6 +429,44 @@ int orc_alg1(const int64_t *P, const int64_t *R, int B, int64_t Nloc, int64_t Nr
     return steps;
 }
 
+/* Algorithm 1 with the paper's cost in value units: the same walk as
+ * orc_alg1, each transported amount charged at |Q_i - Q_j| (Qv[b] the
+ * quantized value of bin b).  Ev[i] receives the mass-weighted value distance
+ * charged to bin i (E_i = Ev[i] / P'_i).  Returns the number of steps. */
+int orc_alg1_values(const int64_t *P, const int64_t *R, int B, int64_t Nloc, int64_t Nref, const double *Qv,
+                    double *Ev)
+{
+    int64_t *Pw = (int64_t *)malloc(sizeof(int64_t) * (B > 0 ? B : 1));
+    int64_t *Rw = (int64_t *)malloc(sizeof(int64_t) * (B > 0 ? B : 1));
+    if (!Pw || !Rw) {
+        free(Pw);
+        free(Rw);
+        return -1;
+    }
+    for (int b = 0; b < B; b++) {
+        Pw[b] = P[b] * Nref;
+        Rw[b] = R[b] * Nloc;
+        Ev[b] = 0.0;
+    }
+    int i = 0, j = 0, steps = 0;
+    while (i < B && j < B) {
+        double dist = fabs(Qv[i] - Qv[j]);
+        steps++;
+        if (Pw[i] < Rw[j]) {
+            Ev[i] += (double)Pw[i] * dist;
+            Rw[j] -= Pw[i];
+            i++;
+        } else {
+            Ev[i] += (double)Rw[j] * dist;
+            Pw[i] -= Rw[j];
+            j++;
+        }
+    }
+    free(Pw);
+    free(Rw);
+    return steps;
+}
+
 /* Gaussian smoothing of an H x W map with standard deviation sigma (the final
  * low-pass step, sigma_s): separable, taps |t| <= ceil(4 sigma) with weights
  * exp(-t^2 / (2 sigma^2)), renormalised over the taps that fall inside the
@@ -464,38 +518,53 @@ int orc_blur(const double *in, int H, int W, double sigma, double *out)
  * before smoothing is the mean over components:
  *     raw(q) = (1/d) sum_k (1/n(q)) sum_{p in box(q)} E_{k,p}[b_k(q)].
  * Then the Gaussian smoothing orc_blur with standard deviation sigma_s.  Writes raw[H][W], score[H][W] and, when
- * non-NULL, comp[d][H][W] = the per-component averages.  Returns 0, or -1 on
- * allocation failure. */
+ * non-NULL, comp[d][H][W] = the per-component averages.  Units: bin units with
+ * lo/hi NULL, else value units (orc_alg1_values with the quantized values of
+ * each component's range lo[k]..hi[k]).  Returns 0, or -1 on allocation failure. */
 int orc_assoc(const uint8_t *q, int d, int H, int W, int B, int r, const uint32_t *R, uint64_t Nref,
-              double sigma_s, double *raw, double *score, double *comp)
+              double sigma_s, double *raw, double *score, double *comp, const double *lo, const double *hi)
 {
     long N = (long)H * W;
     double *E = (double *)malloc(sizeof(double) * (size_t)N * (B > 0 ? B : 1));
     int64_t *L = (int64_t *)malloc(sizeof(int64_t) * (B > 0 ? B : 1));
     int64_t *Rk = (int64_t *)malloc(sizeof(int64_t) * (B > 0 ? B : 1));
     int64_t *En = (int64_t *)malloc(sizeof(int64_t) * (B > 0 ? B : 1));
-    if (!E || !L || !Rk || !En) {
+    double *Ev = (double *)malloc(sizeof(double) * (B > 0 ? B : 1));
+    double *Qv = (double *)malloc(sizeof(double) * (B > 0 ? B : 1));
+    if (!E || !L || !Rk || !En || !Ev || !Qv) {
         free(E);
         free(L);
         free(Rk);
         free(En);
+        free(Ev);
+        free(Qv);
         return -1;
     }
     for (long p = 0; p < N; p++)
         raw[p] = 0.0;
     for (int k = 0; k < d; k++) {
         const uint8_t *qk = q + (long)k * N;
-        for (int b = 0; b < B; b++)
+        for (int b = 0; b < B; b++) {
             Rk[b] = (int64_t)R[(long)k * B + b];
+            if (lo)
+                Qv[b] = bin_value(lo[k], hi[k], B, b);
+        }
         /* per-bin errors of every window of component k */
         for (int y = 0; y < H; y++)
             for (int x = 0; x < W; x++) {
                 long Nloc = orc_window_hist(qk, H, W, B, r, y, x, L);
-                if (orc_alg1(L, Rk, B, Nloc, (int64_t)Nref, En) < 0)
-                    goto oom;
                 double *e = E + ((long)y * W + x) * B;
-                for (int b = 0; b < B; b++)
-                    e[b] = L[b] > 0 ? (double)En[b] / ((double)L[b] * (double)Nref) : 0.0;
+                if (lo) {
+                    if (orc_alg1_values(L, Rk, B, Nloc, (int64_t)Nref, Qv, Ev) < 0)
+                        goto oom;
+                    for (int b = 0; b < B; b++)
+                        e[b] = L[b] > 0 ? Ev[b] / ((double)L[b] * (double)Nref) : 0.0;
+                } else {
+                    if (orc_alg1(L, Rk, B, Nloc, (int64_t)Nref, En) < 0)
+                        goto oom;
+                    for (int b = 0; b < B; b++)
+                        e[b] = L[b] > 0 ? (double)En[b] / ((double)L[b] * (double)Nref) : 0.0;
+                }
             }
         /* association: each pixel averages its own bin's error over the windows that contain it */
         for (int y = 0; y < H; y++)
@@ -523,12 +592,16 @@ int orc_assoc(const uint8_t *q, int d, int H, int W, int B, int r, const uint32_
     free(L);
     free(Rk);
     free(En);
+    free(Ev);
+    free(Qv);
     return 0;
 oom:
     free(E);
     free(L);
     free(Rk);
     free(En);
+    free(Ev);
+    free(Qv);
     return -1;
 }
 

@@ -128,6 +128,7 @@ struct qfca_ctx {
     int autotune = 0;                                   // window-stage tiling: 0 model, 1 measured
     std::map<std::string, qfca::ScoreTiling> tuned;     // measured tilings per shape set
     qfca::ScoreTiling last_tiling{0, 0, 0};
+    float eig_tol = qfca::kEigTolDefault;               // residual bound of the FP32 + Newton eigensolver
     qfca::ServeState *serve = nullptr;                  // serving session (serve.cu)
 };
 
@@ -391,7 +392,7 @@ qfca_status qfca_fit_pca(qfca_ctx *ctx, const float *X, qfca_fmap desc, int d, c
     const long N = (long)desc.H * desc.W;
     if ((s = ensure_ws(ctx, fit_workspace_bytes(desc.C, N, d, 1), (cudaStream_t)stream))) return s;
     cudaError_t e = launch_fit(X, desc.layout, desc.H, desc.W, desc.C, d, 1, out->mean, out->V, out->eigvals, ctx->ws,
-                               ctx->status_dev, (cudaStream_t)stream);
+                               ctx->status_dev, (cudaStream_t)stream, ctx->eig_tol);
     if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "eigensolver shape C=%d d=%d", desc.C, d);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_fit_pca");
     return QFCA_OK;
@@ -654,7 +655,8 @@ qfca_status qfca_batch_run_plus(qfca_ctx *ctx, const float *X, int nimg, qfca_fm
     float *lo = (extra && extra->lo) ? extra->lo : (float *)(b + o_lohi);
     float *hi = (extra && extra->hi) ? extra->hi : (float *)(b + o_lohi) + (size_t)C * nimg;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = launch_fit(X, desc.layout, desc.H, desc.W, C, dres, nimg, mean, V, ev, b + o_fit, ctx->status_dev, st);
+    cudaError_t e = launch_fit(X, desc.layout, desc.H, desc.W, C, dres, nimg, mean, V, ev, b + o_fit, ctx->status_dev, st,
+                               ctx->eig_tol);
     if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "eigensolver shape C=%d d=%d", C, dres);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run_plus/fit");
     float *F = (float *)(b + o_F);
@@ -728,7 +730,7 @@ static qfca_status batch_run_impl(qfca_ctx *ctx, const float *X, int nimg, qfca_
     if (fit) {
         double *ev = (extra && extra->eigvals) ? extra->eigvals : (double *)(b + o_ev);
         e = launch_fit(X, desc.layout, desc.H, desc.W, C, d, nimg, const_cast<double *>(mean),
-                       const_cast<double *>(V), ev, b + o_fit, ctx->status_dev, st);
+                       const_cast<double *>(V), ev, b + o_fit, ctx->status_dev, st, ctx->eig_tol);
         if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "eigensolver shape C=%d d=%d", C, d);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run/fit");
     }
@@ -822,7 +824,8 @@ qfca_status qfca_score_batch(qfca_ctx *ctx, const qfca_image *imgs, int n, int C
     // fit: one launch per stage for the table
     std::vector<FitJob> fjobs(n);
     for (int i = 0; i < n; i++) fjobs[i] = FitJob{imgs[i].X, (long)imgs[i].H * imgs[i].W};
-    cudaError_t e = launch_fit_jobs(fjobs.data(), n, layout, C, d, mean, V, ev, b + o_fit, ctx->status_dev, st);
+    cudaError_t e = launch_fit_jobs(fjobs.data(), n, layout, C, d, mean, V, ev, b + o_fit, ctx->status_dev, st,
+                                    ctx->eig_tol);
     if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "eigensolver shape C=%d d=%d", C, d);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_score_batch/fit");
     // projection: the TMA-fed table kernel when every image allows it, else one call per image
@@ -890,6 +893,26 @@ qfca_status qfca_device_status(qfca_ctx *ctx, int *out) {
     if (e == cudaSuccess) e = cudaMemset(ctx->status_dev, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_device_status");
     return *out ? QFCA_ERR_TIMEOUT : QFCA_OK;
+}
+
+qfca_status qfca_set_eig_tolerance(qfca_ctx *ctx, double tol) {
+    if (!ctx || !(tol >= 0.0)) return QFCA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->eig_tol = (float)tol;
+    return QFCA_OK;
+}
+
+qfca_status qfca_eig_redo_count(qfca_ctx *ctx, uint64_t *out) {
+    if (!ctx || !out) return QFCA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    int v = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&v, ctx->status_dev + kRedoCountSlot, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ctx->status_dev + kRedoCountSlot, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_eig_redo_count");
+    *out = (uint64_t)v;
+    return QFCA_OK;
 }
 
 qfca_status qfca_launch_count(qfca_ctx *ctx, uint64_t *out) {

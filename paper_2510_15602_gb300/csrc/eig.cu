@@ -57,6 +57,7 @@ struct EigArgs {
     int *order;              // [mats][d]
     double *V;               // [mats][n][d]
     double *eig;             // [mats][d]
+    const int *redo;         // [mats] or NULL: solve only the matrices whose entry is non-zero
 };
 
 __host__ __device__ inline long row_off(int l, int r, int R) {
@@ -191,6 +192,9 @@ __global__ void __launch_bounds__(kT, 1) k_eig_ff(EigArgs a) {
     const int R = a.R;
     const int r = (int)cl.block_rank();
     const int mat = blockIdx.x / R;
+    // every CTA of the cluster leaves here together (before any cluster barrier)
+    // when the FP32 + Newton solver has already solved this matrix
+    if (a.redo && a.redo[mat] == 0) return;
     const int n = a.n, d = a.d;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nloc = r < n ? (n - r + R - 1) / R : 0;  // own rows i = r + l R
@@ -678,7 +682,7 @@ int pick_R(int n, int d, int mats, int n_sm) {
 }  // namespace
 
 struct EigPlan {
-    size_t dg, ed, tau, v0, Vh, Z, sig, lam, order, total;
+    size_t e32, flags, dg, ed, tau, v0, Vh, Z, sig, lam, order, total;
 };
 
 static EigPlan eig_plan(int n, int d, int mats) {
@@ -689,6 +693,8 @@ static EigPlan eig_plan(int n, int d, int mats) {
         o = align_up(o + bytes, 256);
         return at;
     };
+    p.e32 = take(eig32_ok(n, d) ? eig32_workspace_bytes(n, mats) : 0);
+    p.flags = take(sizeof(int) * (size_t)mats);
     p.dg = take(sizeof(ff) * (size_t)mats * n);
     p.ed = take(sizeof(ff) * (size_t)mats * n);
     p.tau = take(sizeof(ff) * (size_t)mats * n);
@@ -706,7 +712,17 @@ size_t eig_workspace_bytes(int n, int d, int mats) { return eig_plan(n, d, mats)
 
 // cov_ff: [mats][n][n] float-float pairs (hi, lo) of the covariance.
 cudaError_t launch_eig(const void *cov_ff, int n, int d, int mats, double *V, double *eigvals, void *ws,
-                       cudaStream_t st) {
+                       int *status, cudaStream_t st, float tol) {
+    const EigPlan p = eig_plan(n, d, mats);
+    char *b = (char *)ws;
+    const int *redo = nullptr;
+    if (eig32_ok(n, d)) {
+        int *flags = (int *)(b + p.flags);
+        cudaError_t e = launch_eig32(cov_ff, n, d, mats, V, eigvals, b + p.e32, flags,
+                                     status ? status + kRedoCountSlot : nullptr, tol, st);
+        if (e != cudaSuccess) return e;
+        redo = flags;
+    }
     int dev = 0, n_sm = 0;
     cudaError_t eq = cudaGetDevice(&dev);
     if (eq == cudaSuccess) eq = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -721,9 +737,8 @@ cudaError_t launch_eig(const void *cov_ff, int n, int d, int mats, double *V, do
         return cudaFuncSetAttribute(k_eig_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     });
     if (e0 != cudaSuccess) return e0;
-    const EigPlan p = eig_plan(n, d, mats);
-    char *b = (char *)ws;
     EigArgs a;
+    a.redo = redo;
     a.cov = (const ff *)cov_ff;
     a.n = n;
     a.d = d;

@@ -58,14 +58,22 @@ cudaError_t launch_gram_cov_jobs(const FitJob *jobs, int n, int layout, int C, d
                                  void *ws, int *status, cudaStream_t st);
 // max |x| per channel (float bits) of each image: amax [n][C]
 cudaError_t launch_chan_absmax_jobs(const FitJob *jobs, int n, int layout, int C, unsigned *amax, cudaStream_t st);
+// Residual bound of the FP32 + Newton eigensolver relative to the largest
+// eigenvalue; matrices above it are solved again by the float-float solver.
+constexpr float kEigTolDefault = 1e-10f;
+// Slot (in ints) of the context's status allocation that counts the matrices
+// the float-float solver redid.
+constexpr int kRedoCountSlot = 16;
+
 cudaError_t launch_fit_jobs(const FitJob *jobs, int n, int layout, int C, int d, double *mean, double *V,
-                            double *eigvals, void *ws, int *status, cudaStream_t st);
+                            double *eigvals, void *ws, int *status, cudaStream_t st, float eig_tol = kEigTolDefault);
 
 size_t fit_workspace_bytes(int C, long N, int d, int nimg);
 
 // Enqueue the PCA fit of nimg images.  ws: device scratch of fit_workspace_bytes.
 cudaError_t launch_fit(const float *X, int layout, int H, int W, int C, int d, int nimg,
-                       double *mean, double *V, double *eigvals, void *ws, int *status, cudaStream_t st);
+                       double *mean, double *V, double *eigvals, void *ws, int *status, cudaStream_t st,
+                       float eig_tol = kEigTolDefault);
 
 // Mean and covariance of one feature map (gram.cu).
 size_t gram_workspace_bytes(int C, long N, int nimg);
@@ -74,10 +82,17 @@ cudaError_t launch_gram_cov(const float *X, int layout, int C, long N, int nimg,
                             void *cov_ff, void *ws, int *status, cudaStream_t st);
 
 // Top-d eigenpairs of `mats` symmetric n x n matrices given as float-float
-// pairs (float2 [mats][n][n]) (eig.cu).
+// pairs (float2 [mats][n][n]) (eig.cu): the FP32 + Newton solver (eig32.cu)
+// where the shape allows it, the float-float solver for the matrices it flags
+// (and for every matrix of larger shapes).  status: the context's status
+// allocation (the redo counter lives at status[kRedoCountSlot]) or NULL.
 size_t eig_workspace_bytes(int n, int d, int mats);
 cudaError_t launch_eig(const void *cov_ff, int n, int d, int mats, double *V, double *eigvals, void *ws,
-                       cudaStream_t st);
+                       int *status, cudaStream_t st, float tol = kEigTolDefault);
+bool eig32_ok(int n, int d);
+size_t eig32_workspace_bytes(int n, int mats);
+cudaError_t launch_eig32(const void *cov_ff, int n, int d, int mats, double *V, double *eigvals, void *ws,
+                         int *flag_out, int *redo_count, float tol, cudaStream_t st);
 
 // ------------------------------------------------------------------ projection (project.cu)
 

@@ -87,6 +87,10 @@ _lib.qfca_batch_run.argtypes = [_P, _P, _I, Fmap, _I, _I, _I, _I, _P, ctypes.POI
 _lib.qfca_batch_run.restype = _I
 _lib.qfca_batch_run_basis.argtypes = [_P, _P, _I, Fmap, _P, _P, _I, _I, _I, _I, _P, ctypes.POINTER(BatchOutputs), _P]
 _lib.qfca_batch_run_basis.restype = _I
+_lib.qfca_set_eig_tolerance.argtypes = [_P, ctypes.c_double]
+_lib.qfca_set_eig_tolerance.restype = _I
+_lib.qfca_eig_redo_count.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64)]
+_lib.qfca_eig_redo_count.restype = _I
 _lib.qfca_batch_run_plus.argtypes = [_P, _P, _I, Fmap, _I, _I, _I, _P, ctypes.POINTER(BatchOutputs), _P]
 _lib.qfca_batch_run_plus.restype = _I
 
@@ -210,6 +214,17 @@ class Context:
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self.check(_lib.qfca_last_tiling(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return int(a.value), int(b.value), int(c.value)
+
+    def set_eig_tolerance(self, tol: float):
+        """Residual bound of the fit's FP32 + Newton eigensolver (relative to the largest
+        eigenvalue); 0 sends every matrix to the float-float solver."""
+        self.check(_lib.qfca_set_eig_tolerance(self.handle, float(tol)))
+
+    def eig_redo_count(self) -> int:
+        """Synchronise; read and clear how many matrices the float-float solver redid."""
+        n = ctypes.c_uint64()
+        self.check(_lib.qfca_eig_redo_count(self.handle, ctypes.byref(n)))
+        return int(n.value)
 
     def launch_count(self) -> int:
         n = ctypes.c_uint64()

@@ -1,0 +1,95 @@
+"""The fit's eigensolver through the C ABI against the oracle's cyclic Jacobi
+(Sec. 3.3 fit) on the SAME covariance: the GPU's qfca_covariance output is
+handed to the oracle, so the comparison isolates the eigensolver from the
+covariance's own FP32-class representation error.
+
+Tolerances (the FP32 + Newton route squares the FP32 start's error; a CPU
+emulation of its exact steps on the workloads' covariances gives about
+2e-12 lambda_1/gap_k and 1e-15 lambda_1):
+  * eigenvalues within 1e-12 lambda_1 (the oracle's Jacobi is FP64-accurate);
+  * eigenvector k within 1e-10 lambda_1 / gap_k (first-order perturbation).
+Both routes are checked: the default (FP32 + Newton, no matrix redone), and
+the float-float solver forced for every matrix (tolerance 0).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2510_15602_gb300 import synth
+from tests.gpu_helpers import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2510_15602_gb300 import qfca
+    assert torch.cuda.is_available()
+    return qfca
+
+
+def _check(V_g, ev_g, cov, d):
+    V_o, ev_o, all_o = oracle.eigh_topd(cov, d)
+    lam1 = all_o[0]
+    assert np.all(np.abs(ev_g - ev_o) <= 1e-12 * lam1), np.abs(ev_g - ev_o).max() / lam1
+    gaps = np.abs(np.diff(all_o))
+    worst = 0.0
+    for k in range(d):
+        gap = min(gaps[k - 1] if k > 0 else np.inf, gaps[k])
+        err = np.linalg.norm(V_g[:, k] - V_o[:, k]) / (lam1 / gap)
+        worst = max(worst, err)
+    assert worst <= 1e-10, worst
+    return worst
+
+
+def _fit(q, ctx, X, d):
+    mean_c, cov = q.covariance(X, ctx=ctx)
+    mean, V, ev = q.fit_pca(X, d, ctx=ctx)
+    torch.cuda.synchronize()
+    return cov.cpu().numpy(), V.cpu().numpy(), ev.cpu().numpy()
+
+
+@pytest.mark.parametrize("wl,idx,d", [("plain_128_c64", 0, 16), ("batch16_256_c256", 0, 32),
+                                      ("batch16_256_c256", 5, 32)])
+def test_eig_fp32_newton_against_oracle_on_the_same_covariance(q, wl, idx, d):
+    img = synth.make_image(wl, idx)
+    ctx = q.Context()
+    cov, V, ev = _fit(q, ctx, to_dev(img.X), d)
+    assert ctx.eig_redo_count() == 0  # the workload's covariances pass the residual check
+    worst = _check(V, ev, cov, d)
+    print(f"{wl}[{idx}] worst eigenvector error {worst:.2e} lambda_1/gap")
+
+
+@pytest.mark.parametrize("C,H,W,d", [(48, 40, 56, 8), (200, 30, 41, 24), (256, 64, 64, 1), (3, 20, 20, 2)])
+def test_eig_shapes_against_oracle(q, C, H, W, d):
+    img = synth.small_case(C=C, H=H, W=W, sigma=2.0, seed=C + d, n_square=1, side=6, nch=min(4, C))
+    ctx = q.Context()
+    cov, V, ev = _fit(q, ctx, to_dev(img.X), d)
+    _check(V, ev, cov, d)
+
+
+def test_eig_forced_fallback_float_float_solver(q):
+    # tolerance 0: every matrix is flagged and solved again by the float-float solver
+    img = synth.make_image("plain_128_c64", 0)
+    ctx = q.Context()
+    ctx.set_eig_tolerance(0.0)
+    cov, V, ev = _fit(q, ctx, to_dev(img.X), 16)
+    assert ctx.eig_redo_count() == 1
+    _check(V, ev, cov, 16)
+
+
+def test_eig_batch_mixed_fallback(q):
+    # a batch of four images fitted together, then the same with every matrix redone:
+    # both against the oracle on each image's own covariance
+    imgs = [synth.make_image("plain_128_c64", i) for i in range(4)]
+    X = torch.stack([to_dev(im.X) for im in imgs])
+    for tol, redo in [(1e-10, 0), (0.0, 4)]:
+        ctx = q.Context()
+        ctx.set_eig_tolerance(tol)
+        _, ex = q.batch_run(X, 16, 16, 4, "f32", ctx=ctx, extras=True)
+        torch.cuda.synchronize()
+        assert ctx.eig_redo_count() == redo
+        for i, im in enumerate(imgs):
+            _, cov = q.covariance(to_dev(im.X), ctx=ctx)
+            _check(ex["V"][i].cpu().numpy(), ex["eigvals"][i].cpu().numpy(), cov.cpu().numpy(), 16)
