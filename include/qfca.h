@@ -183,6 +183,12 @@ qfca_status qfca_quantize_residual(qfca_ctx *ctx, const float *X, qfca_fmap desc
  * the supplement).  For pixel p with clipped window of N_loc pixels:
  *   D_k(p) = sum_{b=0}^{B-1} |cumP_b * N_ref - cumR_b * N_loc|   (exact),
  *   score(p) = (sum_k D_k(p)) / (d * N_loc * N_ref)              (FP32 out).
+ * Units: lo = hi = NULL measures distances in bins (bins a and b are |a - b|
+ * apart).  With lo, hi (device f32 [d], each component's quantisation range,
+ * e.g. qfca_quantize's lo_out/hi_out) distances are those of the quantized
+ * values, as Sec. 3.1 states Algorithm 1's cost: |a - b| w_k with
+ * w_k = (hi_k - lo_k) / B (FP64), and
+ *   score(p) = (sum_k w_k D_k(p)) / (d * N_loc * N_ref)   (FP64 sum, FP32 out).
  *   bins       device u8 [d][H][pitch], 16-byte aligned, pitch >= W and a
  *              multiple of 16 (tiles are staged by TMA); values >= B are
  *              treated as B-1.
@@ -193,7 +199,7 @@ qfca_status qfca_quantize_residual(qfca_ctx *ctx, const float *X, qfca_fmap desc
  * components, or all C channels of qfca_quantize_residual). */
 qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pitch, int d, int B,
                        int r, const uint32_t *ref_hist, uint32_t ref_total, float *score,
-                       uint64_t *numer_out, void *stream);
+                       uint64_t *numer_out, const float *lo, const float *hi, void *stream);
 
 /* qfca_score_assoc -- the paper's own per-pixel scoring (Sec. 3.1):
  *   1. Algorithm 1 for every window and component: the window histogram P
@@ -217,13 +223,18 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
  *   raw_out    device f32 [H][W] or NULL: the map before smoothing.
  *   comp_out   device f32 [d][H][W] or NULL: each component's associated
  *              error (the map before the mean over components).
+ *   lo, hi     NULL: bin units (|Q_i - Q_j| = |i - j|).  Device f32 [d], each
+ *              component's quantisation range: value units, the cost Sec. 3.1
+ *              states (|Q_i - Q_j| = |i - j| (hi_k - lo_k) / B), applied to
+ *              the exact bin-unit sums in FP64 before the component mean.
  * Requires 1 <= r, 2 <= B <= 255, d <= 512, 2r <= 248 (B <= 32), 2r <= 120
  * (B <= 128), 2r <= 56 (B <= 255), and a shared-memory plan (histograms and
  * running sums for the window columns, (2r+1)^2 reciprocals) within 200 KB
  * (r <= 31 always fits for B <= 64); QFCA_ERR_UNSUPPORTED otherwise. */
 qfca_status qfca_score_assoc(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pitch, int d, int B,
                              int r, const uint32_t *ref_hist, uint32_t ref_total, float sigma_s,
-                             float *score, float *raw_out, float *comp_out, void *stream);
+                             float *score, float *raw_out, float *comp_out, const float *lo,
+                             const float *hi, void *stream);
 
 /* One image of qfca_score_assoc_batch (fields as in qfca_score_assoc). */
 typedef struct {
@@ -233,6 +244,7 @@ typedef struct {
     uint32_t ref_total;
     float *score;              /* device f32 [H][W], written */
     float *raw;                /* device f32 [H][W] or NULL */
+    const float *lo, *hi;      /* device f32 [d] each, or NULL: value or bin units */
 } qfca_assoc_image;
 
 /* qfca_score_assoc_batch -- qfca_score_assoc for n images (own sizes and

@@ -460,7 +460,7 @@ qfca_status qfca_quantize(qfca_ctx *ctx, const float *X, qfca_fmap desc, const q
 
 qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pitch, int d, int B, int r,
                        const uint32_t *ref_hist, uint32_t ref_total, float *score, uint64_t *numer_out,
-                       void *stream) {
+                       const float *lo, const float *hi, void *stream) {
     qfca_status s = check_ctx(ctx);
     if (s) return s;
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -472,9 +472,10 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
     if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
     if (r < 1 || 2 * r + 1 > 127) return fail(ctx, QFCA_ERR_INVALID_ARG, "r = %d outside [1, 63]", r);
     if (ref_total < 1) return fail(ctx, QFCA_ERR_INVALID_ARG, "ref_total must be >= 1");
+    if ((lo == nullptr) != (hi == nullptr)) return fail(ctx, QFCA_ERR_INVALID_ARG, "value units need both lo and hi");
     DeviceGuard g(ctx->device);
     HookScope hs(ctx);
-    const ScoreJob job{bins, H, W, pitch, r, ref_hist, ref_total, score, numer_out};
+    const ScoreJob job{bins, H, W, pitch, r, ref_hist, ref_total, score, numer_out, lo, hi};
     if ((s = ensure_ws(ctx, score_jobs_workspace_bytes(&job, 1, d), (cudaStream_t)stream))) return s;
     cudaError_t e = launch_score_jobs(&job, 1, d, B, ctx->ws, false, ctx->status_dev, (cudaStream_t)stream,
                                       nullptr, nullptr);
@@ -526,6 +527,8 @@ static qfca_status run_assoc(qfca_ctx *ctx, const AssocJob *jobs, int n, int d, 
         if (j.Nref < 1) return fail(ctx, QFCA_ERR_INVALID_ARG, "image %d: ref_total must be >= 1", i);
         if (!assoc_shape_ok(B, j.r))
             return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d does not fit the association kernel", B, j.r);
+        if ((j.lo == nullptr) != (j.hi == nullptr))
+            return fail(ctx, QFCA_ERR_INVALID_ARG, "image %d: value units need both lo and hi", i);
     }
     if (d < 1 || d > kMaxPlanes) return fail(ctx, QFCA_ERR_INVALID_ARG, "d = %d outside [1, %d]", d, kMaxPlanes);
     if (B < 2 || B > kMaxB) return fail(ctx, QFCA_ERR_INVALID_ARG, "B = %d outside [2, %d]", B, kMaxB);
@@ -543,11 +546,11 @@ static qfca_status run_assoc(qfca_ctx *ctx, const AssocJob *jobs, int n, int d, 
 
 qfca_status qfca_score_assoc(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pitch, int d, int B, int r,
                              const uint32_t *ref_hist, uint32_t ref_total, float sigma_s, float *score,
-                             float *raw_out, float *comp_out, void *stream) {
+                             float *raw_out, float *comp_out, const float *lo, const float *hi, void *stream) {
     qfca_status s = check_ctx(ctx);
     if (s) return s;
     std::lock_guard<std::mutex> lk(ctx->mu);
-    const AssocJob job{bins, H, W, pitch, r, ref_hist, ref_total, sigma_s, score, raw_out, comp_out};
+    const AssocJob job{bins, H, W, pitch, r, ref_hist, ref_total, sigma_s, score, raw_out, comp_out, lo, hi};
     return run_assoc(ctx, &job, 1, d, B, (cudaStream_t)stream);
 }
 
@@ -560,7 +563,7 @@ qfca_status qfca_score_assoc_batch(qfca_ctx *ctx, const qfca_assoc_image *imgs, 
     std::vector<AssocJob> jobs(n);
     for (int i = 0; i < n; i++)
         jobs[i] = AssocJob{imgs[i].bins, imgs[i].H, imgs[i].W, imgs[i].pitch, imgs[i].r, imgs[i].ref_hist,
-                           imgs[i].ref_total, sigma_s, imgs[i].score, imgs[i].raw, nullptr};
+                           imgs[i].ref_total, sigma_s, imgs[i].score, imgs[i].raw, nullptr, imgs[i].lo, imgs[i].hi};
     return run_assoc(ctx, jobs.data(), n, d, B, (cudaStream_t)stream);
 }
 

@@ -75,12 +75,15 @@ struct FinImg {
     long blk0;
     const uint32_t *F;
     float *raw, *comp;
+    const float *lo, *hi;  // value units: component ranges [d] (NULL: bin units)
 };
 
 struct AssocFinParams {
-    int n, d;
+    int n, d, B;
     FinImg img[kMaxBatch];
 };
+
+constexpr int kAssocMaxWeights = 512;
 
 struct BlurImg {
     int H, W;
@@ -554,11 +557,18 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
 }
 
 // raw(q) = sum_k F_k(q) / (d n(q) 2^s); comp_k(q) = F_k(q) / (n(q) 2^s) when asked.
+// Value units: F_k weighs w_k = (hi_k - lo_k) / B (the bin width: Algorithm 1's
+// cost is the distance of the quantized values), summed in FP64 over k in order.
 __global__ void __launch_bounds__(256) k_assoc_fin(const __grid_constant__ AssocFinParams p) {
+    __shared__ double wk[kAssocMaxWeights];
     const long blk = blockIdx.x;
     int ii = 0;
     while (ii + 1 < p.n && p.img[ii + 1].blk0 <= blk) ii++;
     const FinImg &im = p.img[ii];
+    if (im.lo) {
+        for (int k = threadIdx.x; k < p.d; k += 256) wk[k] = ((double)im.hi[k] - (double)im.lo[k]) / (double)p.B;
+        __syncthreads();
+    }
     const long HW = (long)im.H * im.W;
     const long q = (blk - im.blk0) * 256 + threadIdx.x;
     if (q >= HW) return;
@@ -566,6 +576,16 @@ __global__ void __launch_bounds__(256) k_assoc_fin(const __grid_constant__ Assoc
     const int r = im.r;
     const double n = (double)(min(im.H - 1, y + r) - max(0, y - r) + 1) * (double)(min(im.W - 1, x + r) - max(0, x - r) + 1);
     const double unit = n * ldexp(1.0, im.shift);
+    if (im.lo) {
+        double sv = 0.0;
+        for (int k = 0; k < p.d; k++) {
+            const double f = wk[k] * (double)im.F[(size_t)k * HW + q];
+            sv += f;
+            if (im.comp) im.comp[(size_t)k * HW + q] = (float)(f / unit);
+        }
+        im.raw[q] = (float)(sv / (unit * p.d));
+        return;
+    }
     unsigned long long s = 0;
     for (int k = 0; k < p.d; k++) {
         const uint32_t f = im.F[(size_t)k * HW + q];
@@ -741,6 +761,7 @@ cudaError_t launch_assoc_jobs(const AssocJob *jobs, int n, int d, int B, void *w
         AssocFinParams fp{};
         fp.n = m;
         fp.d = d;
+        fp.B = B;
         long blks = 0;
         for (int i = 0; i < m; i++) {
             const AssocJob &j = jobs[i0 + i];
@@ -753,6 +774,8 @@ cudaError_t launch_assoc_jobs(const AssocJob *jobs, int n, int d, int B, void *w
             q.F = F[i0 + i];
             q.raw = rawp[i0 + i];
             q.comp = j.comp;
+            q.lo = j.lo;
+            q.hi = j.hi;
             blks += ((long)j.H * j.W + 255) / 256;
         }
         QFCA_LAUNCH("k_assoc_fin", st, (k_assoc_fin<<<(unsigned)blks, 256, 0, st>>>(fp)));

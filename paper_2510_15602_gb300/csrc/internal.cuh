@@ -175,6 +175,9 @@ struct ScoreJob {
     uint32_t Nref;
     float *score;
     uint64_t *numer_out;
+    // Value units: each component's quantisation range [d] (NULL: bin units).
+    // Component k then weighs (hi_k - lo_k) / B per unit of bin distance.
+    const float *lo = nullptr, *hi = nullptr;
 };
 
 // Tiling of the window-EMD kernel: strip width SW (64 or 128 threads), band
@@ -212,6 +215,7 @@ struct AssocJob {
     uint32_t Nref;
     float sigma_s;
     float *score, *raw, *comp;
+    const float *lo = nullptr, *hi = nullptr;  // value units as in ScoreJob (NULL: bin units)
 };
 
 // True when B bins and radius r fit the association kernel.

@@ -59,12 +59,15 @@ struct FinImgP {
     const void *numer;
     const unsigned long long *accum;
     float *score;
+    const float *lo, *hi;    // value units: component ranges [d] (NULL: bin units)
 };
 
 struct FinParams {
-    int n, d;
+    int n, d, B;
     FinImgP img[kMaxBatch];
 };
+
+constexpr int kFinMaxWeights = 512;  // components whose bin widths a value-unit finalisation keeps in shared memory
 
 __host__ __device__ inline int halo_of(int r) { return (r + 15) & ~15; }
 __host__ __device__ inline int tcp_of(int SW, int r) { return SW + 2 * halo_of(r); }
@@ -287,16 +290,36 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ S
 
 // s(p) = sum_k D_k(p) / (d * N_loc * N_ref), from the per-component numerators
 // or from their running sums; blocks of 256 pixels over the table's images.
+// In value units (ranges given) the distance between bins a and b of
+// component k is |a - b| w_k with w_k = (hi_k - lo_k) / B, so
+// s(p) = sum_k w_k D_k(p) / (d N_loc N_ref), summed in FP64 over k in order.
 template <typename OUT>
 __global__ void __launch_bounds__(256) k_finalize(const __grid_constant__ FinParams p) {
+    __shared__ double wk[kFinMaxWeights];
     const long blk = blockIdx.x;
     int ii = 0;
     while (ii + 1 < p.n && p.img[ii + 1].blk0 <= blk) ii++;
     const FinImgP &im = p.img[ii];
+    const int d = p.d;
+    if (im.lo) {
+        for (int k = threadIdx.x; k < d; k += 256) wk[k] = ((double)im.hi[k] - (double)im.lo[k]) / (double)p.B;
+        __syncthreads();
+    }
     const long HW = (long)im.H * im.W;
     const long q = (blk - im.blk0) * 256 + threadIdx.x;
     if (q >= HW) return;
-    const int d = p.d;
+    const int y = (int)(q / im.W), x = (int)(q - (long)y * im.W);
+    const int r = im.r;
+    const int nr = min(im.H - 1, y + r) - max(0, y - r) + 1;
+    const int nc = min(im.W - 1, x + r) - max(0, x - r) + 1;
+    const double den = (double)nr * (double)nc * (double)im.Nref * (double)d;
+    if (im.lo) {
+        const OUT *nk = reinterpret_cast<const OUT *>(im.numer) + q;
+        double sv = 0.0;
+        for (int k = 0; k < d; k++) sv = fma(wk[k], (double)__ldg(nk + (long)k * HW), sv);
+        im.score[q] = (float)(sv / den);
+        return;
+    }
     unsigned long long s = 0;
     if (im.accum) {
         s = im.accum[q];
@@ -304,11 +327,6 @@ __global__ void __launch_bounds__(256) k_finalize(const __grid_constant__ FinPar
         const OUT *nk = reinterpret_cast<const OUT *>(im.numer) + q;
         for (int k = 0; k < d; k++) s += (unsigned long long)__ldg(nk + (long)k * HW);
     }
-    const int y = (int)(q / im.W), x = (int)(q - (long)y * im.W);
-    const int r = im.r;
-    const int nr = min(im.H - 1, y + r) - max(0, y - r) + 1;
-    const int nc = min(im.W - 1, x + r) - max(0, x - r) + 1;
-    const double den = (double)nr * (double)nc * (double)im.Nref * (double)d;
     im.score[q] = (float)((double)s / den);
 }
 
@@ -444,7 +462,7 @@ cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, boo
     p.first_wait_tries = first_wait_tries;
     FinParams f;
     memset(&f, 0, sizeof(f));
-    f.n = n, f.d = d;
+    f.n = n, f.d = d, f.B = B;
     long cta = 0, blk = 0;
     size_t off = 0;
     for (int i = 0; i < n; i++) {
@@ -474,6 +492,8 @@ cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, boo
         fi.H = j.H, fi.W = j.W, fi.r = j.r, fi.Nref = j.Nref, fi.blk0 = blk;
         blk += (HW + 255) / 256;
         fi.numer = numer, fi.accum = accum, fi.score = j.score;
+        fi.lo = j.lo, fi.hi = j.hi;
+        if (j.lo && (accum || !j.hi || d > kFinMaxWeights)) return cudaErrorNotSupported;
     }
     for (int i = 0; i < n; i++)
         if (p.img[i].accum) {

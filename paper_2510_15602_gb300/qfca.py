@@ -62,7 +62,7 @@ _lib.qfca_covariance.restype = _I
 _lib.qfca_quantize.argtypes = [_P, _P, Fmap, ctypes.POINTER(Basis), _I, _I, _I, _I, _P, _P, _P, _I, _P, _P, _P,
                                _P, _P]
 _lib.qfca_quantize.restype = _I
-_lib.qfca_score.argtypes = [_P, _P, _I, _I, _I, _I, _I, _I, _P, ctypes.c_uint32, _P, _P, _P]
+_lib.qfca_score.argtypes = [_P, _P, _I, _I, _I, _I, _I, _I, _P, ctypes.c_uint32, _P, _P, _P, _P, _P]
 _lib.qfca_score.restype = _I
 _lib.qfca_device_status.argtypes = [_P, ctypes.POINTER(ctypes.c_int)]
 _lib.qfca_device_status.restype = _I
@@ -102,14 +102,16 @@ class Image(ctypes.Structure):
 
 _lib.qfca_score_batch.argtypes = [_P, ctypes.POINTER(Image), _I, _I, _I, _I, _I, _I, _P]
 _lib.qfca_score_batch.restype = _I
-_lib.qfca_score_assoc.argtypes = [_P, _P, _I, _I, _I, _I, _I, _I, _P, ctypes.c_uint32, ctypes.c_float, _P, _P, _P, _P]
+_lib.qfca_score_assoc.argtypes = [_P, _P, _I, _I, _I, _I, _I, _I, _P, ctypes.c_uint32, ctypes.c_float, _P, _P, _P,
+                                  _P, _P, _P]
 _lib.qfca_score_assoc.restype = _I
 
 
 class AssocImage(ctypes.Structure):
     _fields_ = [("bins", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int), ("pitch", ctypes.c_int),
                 ("r", ctypes.c_int), ("ref_hist", ctypes.c_void_p), ("ref_total", ctypes.c_uint32),
-                ("score", ctypes.c_void_p), ("raw", ctypes.c_void_p)]
+                ("score", ctypes.c_void_p), ("raw", ctypes.c_void_p), ("lo", ctypes.c_void_p),
+                ("hi", ctypes.c_void_p)]
 
 
 _lib.qfca_score_assoc_batch.argtypes = [_P, ctypes.POINTER(AssocImage), _I, _I, _I, ctypes.c_float, _P]
@@ -392,9 +394,21 @@ def quantize_residual(X: torch.Tensor, basis, B: int, layout: int = NCHW, want_F
     return dict(bins=bins, lo=lo_o, hi=hi_o, hist=hist, F=F, pitch=pitch)
 
 
+def _ranges(lo, hi, d):
+    if (lo is None) != (hi is None):
+        raise ValueError("value units need both lo and hi")
+    if lo is not None:
+        for t, nm in ((lo, "lo"), (hi, "hi")):
+            _check_dev(t, nm, torch.float32)
+            if t.numel() != d:
+                raise ValueError(f"{nm} must hold one range end per component ({d})")
+    return _ptr(lo), _ptr(hi)
+
+
 def score(bins: torch.Tensor, W: int, B: int, r: int, ref_hist: torch.Tensor, ref_total: int,
-          want_numer: bool = False, ctx: Context | None = None, stream=None, out=None):
-    """qfca_score: window histograms + 1-D EMD + component mean -> f32 [H, W] score map."""
+          want_numer: bool = False, ctx: Context | None = None, stream=None, out=None, lo=None, hi=None):
+    """qfca_score: window histograms + 1-D EMD + component mean -> f32 [H, W] score map.
+    Bin units, or value units given each component's quantisation range lo/hi (f32 [d])."""
     _check_dev(bins, "bins", torch.uint8)
     if ref_hist.dtype not in (torch.int32, torch.uint32) or not ref_hist.is_cuda:
         raise ValueError("ref_hist must be a CUDA int32/uint32 tensor")
@@ -405,14 +419,15 @@ def score(bins: torch.Tensor, W: int, B: int, r: int, ref_hist: torch.Tensor, re
     else:
         s = out
     numer = torch.empty(d, H, W, dtype=torch.int64, device=bins.device) if want_numer else None
+    plo, phi = _ranges(lo, hi, d)
     ctx.check(_lib.qfca_score(ctx.handle, _ptr(bins), H, W, pitch, d, B, r, _ptr(ref_hist), int(ref_total),
-                              _ptr(s), _ptr(numer), _P(_stream_ptr(stream))))
+                              _ptr(s), _ptr(numer), plo, phi, _P(_stream_ptr(stream))))
     return (s, numer) if want_numer else s
 
 
 def score_assoc(bins: torch.Tensor, W: int, B: int, r: int, ref_hist: torch.Tensor, ref_total: int,
                 sigma_s: float = 1.0, want_raw: bool = False, want_comp: bool = False, ctx: Context | None = None,
-                stream=None, out=None):
+                stream=None, out=None, lo=None, hi=None):
     """qfca_score_assoc: the paper's scoring (Algorithm 1, error-to-pixel association,
     component mean, Gaussian smoothing) -> f32 [H, W] score map; with want_raw /
     want_comp also the map before smoothing [H, W] and the per-component maps [d, H, W]."""
@@ -424,15 +439,17 @@ def score_assoc(bins: torch.Tensor, W: int, B: int, r: int, ref_hist: torch.Tens
     s = torch.empty(H, W, dtype=torch.float32, device=bins.device) if out is None else out
     raw = torch.empty(H, W, dtype=torch.float32, device=bins.device) if want_raw else None
     comp = torch.empty(d, H, W, dtype=torch.float32, device=bins.device) if want_comp else None
+    plo, phi = _ranges(lo, hi, d)
     ctx.check(_lib.qfca_score_assoc(ctx.handle, _ptr(bins), H, W, pitch, d, B, r, _ptr(ref_hist), int(ref_total),
-                                    float(sigma_s), _ptr(s), _ptr(raw), _ptr(comp), _P(_stream_ptr(stream))))
+                                    float(sigma_s), _ptr(s), _ptr(raw), _ptr(comp), plo, phi,
+                                    _P(_stream_ptr(stream))))
     if not (want_raw or want_comp):
         return s
     return (s,) + ((raw,) if want_raw else ()) + ((comp,) if want_comp else ())
 
 
 def score_assoc_batch(bins_list, Ws, rs, B: int, refs, ref_totals, sigma_s: float = 1.0,
-                      ctx: Context | None = None, stream=None, scores=None):
+                      ctx: Context | None = None, stream=None, scores=None, los=None, his=None):
     """qfca_score_assoc_batch: qfca_score_assoc for several images (bins [d, H_i, pitch_i])
     in one launch per stage.  Returns the list of score maps [H_i, W_i]."""
     n = len(bins_list)
@@ -448,7 +465,9 @@ def score_assoc_batch(bins_list, Ws, rs, B: int, refs, ref_totals, sigma_s: floa
         _check_dev(b, f"bins_list[{i}]", torch.uint8)
         if int(b.shape[0]) != d:
             raise ValueError("every image needs the same number of components")
-        arr[i] = AssocImage(_ptr(b), int(b.shape[1]), int(w), int(b.shape[2]), int(r), _ptr(R), int(nt), _ptr(sc), None)
+        plo, phi = _ranges(None if los is None else los[i], None if his is None else his[i], d)
+        arr[i] = AssocImage(_ptr(b), int(b.shape[1]), int(w), int(b.shape[2]), int(r), _ptr(R), int(nt), _ptr(sc), None,
+                            plo, phi)
     ctx.check(_lib.qfca_score_assoc_batch(ctx.handle, arr, n, d, B, float(sigma_s), _P(_stream_ptr(stream))))
     return scores
 
