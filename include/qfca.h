@@ -384,6 +384,17 @@ qfca_status qfca_score_batch(qfca_ctx *ctx, const qfca_image *imgs, int n, int C
  * never under stream capture) and reuse the fastest. */
 qfca_status qfca_set_autotune(qfca_ctx *ctx, int mode);
 
+/* Use a given window-stage tiling for the context's later score launches
+ * (strip width 64 or 128 threads, band height 1..64 rows, component groups
+ * >= 1; more groups than components count as one per component), ahead of
+ * the cost model and the autotuner; strip_width = 0 returns to them.  With
+ * one component group each CTA sums all d components of its pixels in shared
+ * memory and writes the score itself (bin units, no numerator output);
+ * otherwise the per-component numerators go through a finalisation launch.
+ * Results do not depend on the tiling.  A tiling that does not fit shared
+ * memory for a call makes that call return QFCA_ERR_UNSUPPORTED. */
+qfca_status qfca_set_tiling(qfca_ctx *ctx, int strip_width, int band_height, int component_groups);
+
 /* The window-stage tiling used by the context's most recent score launch:
  * strip width (threads), band height (rows), component groups. */
 qfca_status qfca_last_tiling(qfca_ctx *ctx, int *strip_width, int *band_height, int *component_groups);

@@ -128,6 +128,7 @@ struct qfca_ctx {
     int autotune = 0;                                   // window-stage tiling: 0 model, 1 measured
     std::map<std::string, qfca::ScoreTiling> tuned;     // measured tilings per shape set
     qfca::ScoreTiling last_tiling{0, 0, 0};
+    qfca::ScoreTiling forced{0, 0, 0};                  // window-stage tiling set by the caller (SW 0: none)
     float eig_tol = qfca::kEigTolDefault;               // residual bound of the FP32 + Newton eigensolver
     qfca::ServeState *serve = nullptr;                  // serving session (serve.cu)
 };
@@ -241,7 +242,10 @@ qfca_status run_score(qfca_ctx *ctx, const ScoreJob *jobs, int n, int d, int B, 
                       const char *where) {
     const ScoreTiling *use = nullptr;
     ScoreTiling chosen{0, 0, 0};
-    if (ctx->autotune) {
+    if (ctx->forced.SW > 0) {
+        chosen = ctx->forced;
+        use = &chosen;
+    } else if (ctx->autotune) {
         std::string key = std::to_string(n) + ":" + std::to_string(d) + ":" + std::to_string(B);
         for (int i = 0; i < n; i++)
             key += ":" + std::to_string(jobs[i].H) + "x" + std::to_string(jobs[i].W) + "r" + std::to_string(jobs[i].r);
@@ -478,7 +482,7 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
     const ScoreJob job{bins, H, W, pitch, r, ref_hist, ref_total, score, numer_out, lo, hi};
     if ((s = ensure_ws(ctx, score_jobs_workspace_bytes(&job, 1, d), (cudaStream_t)stream))) return s;
     cudaError_t e = launch_score_jobs(&job, 1, d, B, ctx->ws, false, ctx->status_dev, (cudaStream_t)stream,
-                                      nullptr, nullptr);
+                                      ctx->forced.SW > 0 ? &ctx->forced : nullptr, &ctx->last_tiling);
     if (e == cudaErrorNotSupported)
         return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d needs more shared memory than a CTA has", B, r);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_score");
@@ -875,6 +879,20 @@ qfca_status qfca_set_autotune(qfca_ctx *ctx, int mode) {
     if (!ctx || (mode != 0 && mode != 1)) return QFCA_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->autotune = mode;
+    return QFCA_OK;
+}
+
+qfca_status qfca_set_tiling(qfca_ctx *ctx, int strip_width, int band_height, int component_groups) {
+    if (!ctx) return QFCA_ERR_INVALID_ARG;
+    if (strip_width == 0) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->forced = ScoreTiling{0, 0, 0};
+        return QFCA_OK;
+    }
+    if (!(strip_width == 64 || strip_width == 128) || band_height < 1 || band_height > 64 || component_groups < 1)
+        return fail(ctx, QFCA_ERR_INVALID_ARG, "tiling %d x %d x %d", strip_width, band_height, component_groups);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->forced = ScoreTiling{strip_width, band_height, component_groups};
     return QFCA_OK;
 }
 

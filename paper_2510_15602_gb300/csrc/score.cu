@@ -42,12 +42,15 @@ struct ScoreImgP {
     uint32_t Nref;
     void *numer;             // [d][H][W] of OUT, or NULL when accumulating
     unsigned long long *accum;  // [H][W] running sums, or NULL
+    float *score;            // [H][W]: written by the kernel itself when it sums every component (fuse)
 };
 
 struct ScoreParams {
     int n, d, B, SW, TH, kg, n_kg;
     uint32_t tile_bytes;
     uint32_t first_wait_tries;  // probes of each CTA's first tile wait (kTmaTries; fewer only to test the timeout path)
+    int fuse;                   // every CTA holds all d components: sum them per pixel in shared memory, write the score
+    uint32_t acc_off;           // byte offset of the per-pixel sums [TH][SW] u64 in shared memory (fuse)
     ScoreImgP img[kMaxBatch];
     CUtensorMap tmap[kMaxBatch];  // bins of image i as [d][H][pitch] u8, box {TCp_i, TH + 2 r_i, 1}
 };
@@ -72,10 +75,14 @@ constexpr int kFinMaxWeights = 512;  // components whose bin widths a value-unit
 __host__ __device__ inline int halo_of(int r) { return (r + 15) & ~15; }
 __host__ __device__ inline int tcp_of(int SW, int r) { return SW + 2 * halo_of(r); }
 
-size_t score_smem(int SW, int TH, int B, int rmax) {
+size_t score_smem_core(int SW, int TH, int B, int rmax) {
     const size_t tile = align_up((size_t)(TH + 2 * rmax) * tcp_of(SW, rmax), 128);
-    return 128 + 2 * tile + sizeof(uint32_t) * (size_t)(B + 1) * SW + sizeof(uint32_t) * 256 +
-           sizeof(uint64_t) * 256 + 2 * sizeof(uint64_t);
+    return 2 * tile + sizeof(uint32_t) * (size_t)(B + 1) * SW + sizeof(uint32_t) * 256 + sizeof(uint64_t) * 256 +
+           2 * sizeof(uint64_t);
+}
+// fuse: plus the per-pixel u64 sums over the components of the CTA's TH x SW pixels
+size_t score_smem(int SW, int TH, int B, int rmax, bool fuse = false) {
+    return 128 + score_smem_core(SW, TH, B, rmax) + (fuse ? sizeof(uint64_t) * (size_t)TH * SW : 0);
 }
 
 // Window histograms + exact EMD numerators for a band of TH rows x SW columns
@@ -100,6 +107,7 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ S
     uint32_t *cumR = hist + (size_t)(B + 1) * SW;
     ACC *cRi = reinterpret_cast<ACC *>(cumR + 256);  // cumR[b] * N_loc for an interior window
     uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(cumR + 256) + 256 * sizeof(uint64_t));
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(smem + p.acc_off);  // [TH][SW] (fuse only)
 
     // which image, component group, band and strip
     const long cta = blockIdx.x;
@@ -275,8 +283,14 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ S
                     }
                 }
                 const long pix = (long)yy * W + x;
-                if (im.accum) atomicAdd(&im.accum[pix], (unsigned long long)D);
-                else reinterpret_cast<OUT *>(im.numer)[(long)k * HW + pix] = (OUT)D;
+                if (p.fuse) {
+                    unsigned long long &a = acc[i * SW + t];  // this thread's own column: no other thread touches it
+                    a = (k == k0 ? 0ull : a) + (unsigned long long)D;
+                } else if (im.accum) {
+                    atomicAdd(&im.accum[pix], (unsigned long long)D);
+                } else {
+                    reinterpret_cast<OUT *>(im.numer)[(long)k * HW + pix] = (OUT)D;
+                }
             }
         }
         tc::fence_proxy_async_smem();  // this iteration's writes to the tile precede the next TMA write into it
@@ -285,6 +299,15 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ S
         if (t == 0) atomicOr(status, kStatusMmaTimeout);
         // let every issued copy (including the one whose wait ran out) land before the CTA leaves (bounded)
         for (int w = waited - 1; w < issued; w++) tc::mbar_wait(&bar[w & 1], (w >> 1) & 1, kTmaTries);
+    } else if (p.fuse && x < W) {
+        // s(p) = sum_k D_k(p) / (d N_loc N_ref): one division per pixel, no numerators leave the SM
+        for (int i = 0; i < TH; i++) {
+            const int yy = y0 + i;
+            if (yy >= H) break;
+            const int nrows = min(H - 1, yy + r) - max(0, yy - r) + 1;
+            const double den = (double)nrows * (double)ncols * (double)Nref * (double)d;
+            im.score[(long)yy * W + x] = (float)((double)acc[i * SW + t] / den);
+        }
     }
 }
 
@@ -398,8 +421,9 @@ cudaError_t ensure_attrs(int *n_sm) {
 cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, bool ws_accumulates, int *status,
                         cudaStream_t st, const ScoreTiling *tiling, ScoreTiling *chosen, uint32_t first_wait_tries) {
     int rmax = 1;
-    bool narrow = true, want_numer = false;
+    bool narrow = true, want_numer = false, value_units = false;
     for (int i = 0; i < n; i++) {
+        value_units = value_units || jobs[i].lo;
         const double span2 = (double)(2 * jobs[i].r + 1) * (2 * jobs[i].r + 1);
         // u32 walk when every partial and the numerator fit: (B-1) (2r+1)^2 N_ref < 2^32
         narrow = narrow && (double)(B - 1) * span2 * (double)jobs[i].Nref < 4294967295.0 &&
@@ -411,6 +435,8 @@ cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, boo
                          : (want_numer || ws_accumulates) ? EmdKind::U32_U64 : EmdKind::U32_U32;
     const size_t out_bytes = kind == EmdKind::U32_U32 ? 4 : 8;
     const int KB = (B == 32 || B == 64) ? B : 0;
+    // a tiling with one component group sums the components inside the CTA (bin units, no numerators asked)
+    const bool can_fuse = !want_numer && !ws_accumulates && !value_units;
     int n_sm = 0;
     cudaError_t err = ensure_attrs(&n_sm);
     if (err != cudaSuccess) return err;
@@ -420,25 +446,26 @@ cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, boo
     if (tiling && tiling->SW > 0) {
         best = *tiling;
         if (!(best.SW == 64 || best.SW == 128) || best.TH < 1 || best.TH > 64 || best.n_kg < 1) return cudaErrorNotSupported;
-        if (score_smem(best.SW, best.TH, B, rmax) > 200 * 1024 || tcp_of(best.SW, rmax) > 256 ||
-            best.TH + 2 * rmax > 256)
+        if (score_smem(best.SW, best.TH, B, rmax, can_fuse && best.n_kg == 1) > 200 * 1024 ||
+            tcp_of(best.SW, rmax) > 256 || best.TH + 2 * rmax > 256)
             return cudaErrorNotSupported;
     } else {
         double best_cost = 1e300;
         for (int SW : {128, 64})
             for (int TH : {16, 32, 64, 8}) {
-                const size_t smem = score_smem(SW, TH, B, rmax);
-                if (smem > 200 * 1024 || tcp_of(SW, rmax) > 256 || TH + 2 * rmax > 256) continue;
-                int per_sm = 0;
-                err = emd_occupancy_kind(kind, KB, smem, SW, &per_sm);
-                if (err != cudaSuccess) return err;
-                if (per_sm < 1) continue;
-                const long slots = (long)per_sm * n_sm;
+                if (score_smem(SW, TH, B, rmax) > 200 * 1024 || tcp_of(SW, rmax) > 256 || TH + 2 * rmax > 256) continue;
                 long tiles = 0;
                 for (int i = 0; i < n; i++) tiles += (long)((jobs[i].W + SW - 1) / SW) * ((jobs[i].H + TH - 1) / TH);
                 for (int nk = 1; nk <= d; nk++) {
                     const int kg = (d + nk - 1) / nk;
                     if ((d + kg - 1) / kg != nk) continue;  // same split as a smaller count
+                    const size_t smem = score_smem(SW, TH, B, rmax, can_fuse && nk == 1);
+                    if (smem > 200 * 1024) continue;
+                    int per_sm = 0;
+                    err = emd_occupancy_kind(kind, KB, smem, SW, &per_sm);
+                    if (err != cudaSuccess) return err;
+                    if (per_sm < 1) continue;
+                    const long slots = (long)per_sm * n_sm;
                     double work = 0.0;
                     for (int i = 0; i < n; i++) work += image_cost(jobs[i].H, jobs[i].W, d, B, jobs[i].r, SW, TH, kg, nk);
                     const double ctas = (double)tiles * nk;
@@ -453,13 +480,16 @@ cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, boo
     if (chosen) *chosen = best;
     const int SW = best.SW, TH = best.TH;
     const int kg = (d + best.n_kg - 1) / best.n_kg, n_kg = (d + kg - 1) / kg;
-    const size_t smem = score_smem(SW, TH, B, rmax);
+    const bool fuse = can_fuse && n_kg == 1;
+    const size_t smem = score_smem(SW, TH, B, rmax, fuse);
 
     ScoreParams p;
     memset(&p, 0, sizeof(p));
     p.n = n, p.d = d, p.B = B, p.SW = SW, p.TH = TH, p.kg = kg, p.n_kg = n_kg;
     p.tile_bytes = (uint32_t)align_up((size_t)(TH + 2 * rmax) * tcp_of(SW, rmax), 128);
     p.first_wait_tries = first_wait_tries;
+    p.fuse = fuse ? 1 : 0;
+    p.acc_off = (uint32_t)score_smem_core(SW, TH, B, rmax);
     FinParams f;
     memset(&f, 0, sizeof(f));
     f.n = n, f.d = d, f.B = B;
@@ -484,7 +514,7 @@ cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, boo
             numer = (char *)ws + off;
             off += align_up(out_bytes * (size_t)d * HW, 256);
         }
-        im.numer = numer, im.accum = accum;
+        im.numer = numer, im.accum = accum, im.score = j.score;
         err = make_tmap_u8_3d(&p.tmap[i], j.bins, (uint64_t)j.pitch, (uint64_t)j.H, (uint64_t)d, (uint64_t)j.pitch,
                               (uint64_t)j.H * j.pitch, (uint32_t)tcp_of(SW, j.r), (uint32_t)(TH + 2 * j.r));
         if (err != cudaSuccess) return err;
@@ -503,15 +533,15 @@ cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, boo
     switch (kind) {
     case EmdKind::U32_U32:
         launch_emd_kb<uint32_t, uint32_t>(KB, cta, smem, SW, st, p, status);
-        QFCA_LAUNCH("k_finalize", st, k_finalize<uint32_t><<<(unsigned)blk, 256, 0, st>>>(f));
+        if (!fuse) QFCA_LAUNCH("k_finalize", st, k_finalize<uint32_t><<<(unsigned)blk, 256, 0, st>>>(f));
         break;
     case EmdKind::U32_U64:
         launch_emd_kb<uint32_t, unsigned long long>(KB, cta, smem, SW, st, p, status);
-        QFCA_LAUNCH("k_finalize", st, k_finalize<unsigned long long><<<(unsigned)blk, 256, 0, st>>>(f));
+        if (!fuse) QFCA_LAUNCH("k_finalize", st, k_finalize<unsigned long long><<<(unsigned)blk, 256, 0, st>>>(f));
         break;
     default:
         launch_emd_kb<unsigned long long, unsigned long long>(KB, cta, smem, SW, st, p, status);
-        QFCA_LAUNCH("k_finalize", st, k_finalize<unsigned long long><<<(unsigned)blk, 256, 0, st>>>(f));
+        if (!fuse) QFCA_LAUNCH("k_finalize", st, k_finalize<unsigned long long><<<(unsigned)blk, 256, 0, st>>>(f));
         break;
     }
     return cudaGetLastError();
