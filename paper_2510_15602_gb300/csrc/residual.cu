@@ -4,8 +4,10 @@
 // for all C channels, with each channel's image-wide min/max (order-preserving
 // u32 keys) for the per-channel quantisation that follows.
 //
-// k_residual: one thread per pixel (or four adjacent pixels, one 16-byte load
-// per channel, when the layout allows).  The thread forms the dres projections
+// k_residual_tiled (NCHW maps whose rows allow 16-byte copies): a tile of
+// pixels with all channels in shared memory, both channel walks from there.
+// k_residual (other layouts): one thread per pixel (or four adjacent pixels,
+// one 16-byte load per channel, when the layout allows).  The thread forms the dres projections
 // y_k = sum_c (x_c - mean_c) V_ck in FP32 registers (mean and V staged in
 // shared memory as FP32), then walks the channels again to write
 // f_c = (x_c - mean_c) - sum_k V_ck y_k; on a 1 GB batch the second walk misses
@@ -18,6 +20,7 @@
 #include <stdint.h>
 
 #include "internal.cuh"
+#include "tc.cuh"
 
 namespace qfca {
 namespace {
@@ -149,6 +152,102 @@ __global__ void __launch_bounds__(kResThreads) k_residual(const __grid_constant_
     }
 }
 
+// The tiled form (NCHW, N % 4 == 0, X 16-byte aligned): one CTA = TP pixels of
+// one image with ALL C channels staged in shared memory by 16-byte cp.async
+// copies, so the second walk over the channels reads shared memory, not DRAM
+// (features read once, residual written once).  Thread t owns pixel t % TP and
+// the components (projection) or channels (residual) congruent to t / TP; the
+// arithmetic and its order are those of k_residual, so the results are equal.
+constexpr int kTileThreads = 256;
+
+size_t residual_tiled_smem(int C, int dres, int TP) {
+    return sizeof(float) * ((size_t)C * TP + C + (size_t)C * dres + (size_t)kMaxResidual * TP) +
+           2 * sizeof(uint32_t) * C;
+}
+
+template <int TP>
+__global__ void __launch_bounds__(kTileThreads) k_residual_tiled(const __grid_constant__ ResP p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int G = kTileThreads / TP;  // thread groups: components / channels per group stride
+    const int C = p.C, dr = p.dres;
+    const int img = blockIdx.x / p.tiles, tile = blockIdx.x % p.tiles;
+    const long N = (long)p.H * p.W;
+    const long p0 = (long)tile * TP;
+    const float *X = p.X + (size_t)img * C * N;
+    const double *mean = p.mean + (size_t)img * C, *Vg = p.V + (size_t)img * C * dr;
+    float *Fo = p.F + (size_t)img * C * N;
+    uint32_t *mm = p.mm + (size_t)img * 2 * C * kKeyStride;
+    float *xs = reinterpret_cast<float *>(smem_raw);    // [C][TP]
+    float *mu = xs + (size_t)C * TP;                    // [C]
+    float *Vs = mu + C;                                 // [C][dres]
+    float *ys = Vs + (size_t)C * dr;                    // [kMaxResidual][TP]
+    uint32_t *mn = reinterpret_cast<uint32_t *>(ys + (size_t)kMaxResidual * TP);  // [C]
+    uint32_t *mx = mn + C;                                                        // [C]
+    const int tid = threadIdx.x;
+    // stage the tile: TP/4 16-byte chunks per channel (N % 4 == 0: a chunk is all in or all out)
+    constexpr int CH = TP / 4;
+    for (int e = tid; e < C * CH; e += kTileThreads) {
+        const int c = e / CH, q4 = e % CH;
+        const long px = p0 + 4 * q4;
+        float *dst = xs + (size_t)c * TP + 4 * q4;
+        if (px < N) tc::cp_async16(tc::smem_u32(dst), X + (size_t)c * N + px);
+        else *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    tc::cp_async_commit();
+    for (int c = tid; c < C; c += kTileThreads) {
+        mu[c] = (float)mean[c];
+        mn[c] = 0xffffffffu;
+        mx[c] = 0u;
+    }
+    for (int e = tid; e < C * dr; e += kTileThreads) Vs[e] = (float)Vg[e];
+    tc::cp_async_wait<0>();
+    __syncthreads();
+    const int pl = tid % TP, grp = tid / TP;
+    const bool ok = p0 + pl < N;
+    // projections y_k = sum_c (x_c - mean_c) V_ck, components k = grp, grp + G, ...
+    {
+        constexpr int KPT = (kMaxResidual + G - 1) / G;
+        float y[KPT];
+#pragma unroll
+        for (int u = 0; u < KPT; u++) y[u] = 0.0f;
+        for (int c = 0; c < C; c++) {
+            const float xm = xs[(size_t)c * TP + pl] - mu[c];
+            const float *v = Vs + (size_t)c * dr;
+#pragma unroll
+            for (int u = 0; u < KPT; u++) {
+                const int k = grp + u * G;
+                if (k < dr) y[u] = fmaf(xm, v[k], y[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < KPT; u++) {
+            const int k = grp + u * G;
+            if (k < dr) ys[(size_t)k * TP + pl] = y[u];
+        }
+    }
+    __syncthreads();
+    // residual f_c = (x_c - mean_c) - sum_k V_ck y_k for channels c = grp, grp + G, ...; per-channel keys
+    const int lane = tid & 31;
+    for (int c = grp; c < C; c += G) {
+        const float *v = Vs + (size_t)c * dr;
+        float f = xs[(size_t)c * TP + pl] - mu[c];
+        for (int k = 0; k < dr; k++) f = fmaf(-v[k], ys[(size_t)k * TP + pl], f);
+        if (ok) Fo[(size_t)c * N + p0 + pl] = f;
+        const uint32_t key = f2key(f);
+        const uint32_t kmin = __reduce_min_sync(0xffffffffu, ok ? key : 0xffffffffu);
+        const uint32_t kmax = __reduce_max_sync(0xffffffffu, ok ? key : 0u);
+        if (lane == 0) {
+            atomicMin(&mn[c], kmin);
+            atomicMax(&mx[c], kmax);
+        }
+    }
+    __syncthreads();
+    for (int c = tid; c < C; c += kTileThreads) {
+        atomicMin(&mm[(size_t)c * kKeyStride], mn[c]);
+        atomicMax(&mm[(size_t)(C + c) * kKeyStride], mx[c]);
+    }
+}
+
 DeviceOnce g_attrs_res;
 
 }  // namespace
@@ -167,12 +266,31 @@ cudaError_t launch_residual(const float *X, int layout, int H, int W, int C, con
         if (r == cudaSuccess) r = cudaFuncSetAttribute(k_residual<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         if (r == cudaSuccess) r = cudaFuncSetAttribute(k_residual<4, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         if (r == cudaSuccess) r = cudaFuncSetAttribute(k_residual<4, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k_residual_tiled<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k_residual_tiled<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         return r;
     });
     if (e != cudaSuccess) return e;
     e = launch_init_keys(mm, C, nimg, st);
     if (e != cudaSuccess) return e;
     const long N = (long)H * W;
+    // the tiled form when every feature row can be copied in 16-byte pieces
+    if (layout == 0 && N % 4 == 0 && ((uintptr_t)X & 15) == 0) {
+        const int TP = residual_tiled_smem(C, dres, 64) <= 220 * 1024 ? 64 : 32;
+        const size_t smem = residual_tiled_smem(C, dres, TP);
+        if (smem <= 220 * 1024) {
+            const int tiles = (int)((N + TP - 1) / TP);
+            ResP p{X, layout, H, W, C, dres, tiles, mean, V, F, mm};
+            const unsigned grid = (unsigned)((long)tiles * nimg);
+            if (TP == 64)
+                QFCA_LAUNCH("k_residual", st, (k_residual_tiled<64><<<grid, kTileThreads, smem, st>>>(p)));
+            else
+                QFCA_LAUNCH("k_residual", st, (k_residual_tiled<32><<<grid, kTileThreads, smem, st>>>(p)));
+            return cudaGetLastError();
+        }
+    }
     // four pixels per thread only when that still leaves about two waves of CTAs
     const bool wide = layout == 0 && N % 4 == 0 && ((uintptr_t)X & 15) == 0 && ((uintptr_t)F & 15) == 0 &&
                       (N / (4L * kResThreads)) * nimg >= 300;
