@@ -9,9 +9,9 @@
 //      splitting in FP32, each step exact); each digit is an integer, exact in
 //      BF16.  For a 128x128 channel tile, tcgen05 accumulates in tensor memory
 //      the level sums  A_L = sum_{i+j=L} sum_p d_i(c1,p) d_j(c2,p),  L = 0..3,
-//      four FP32 accumulators of 128 columns.  Over a window of 256 pixels
-//      every partial sum is an integer of magnitude <= 4 * 64 * 64 * 256 =
-//      2^22, so the FP32 accumulation is exact; the window's sums are drained
+//      four FP32 accumulators of 128 columns.  Over a window of 512 pixels
+//      every partial sum is an integer of magnitude <= 4 * 64 * 64 * 512 =
+//      2^23, so the FP32 accumulation is exact; the window's sums are drained
 //      into int64 registers, T += sum_L A_L << 7(4-L) (units of 2^-40), and
 //      the CTA's totals are added into a global int64 Gram with integer
 //      atomics (order-independent, so the result is deterministic).  Column
@@ -27,11 +27,16 @@
 // One CTA (512 threads) = one 128x128 tile of the upper triangle x one range
 // of pixels; per 32-pixel sub-chunk all threads convert both channel blocks
 // into the 64-byte-swizzled K-major layout (channels are rows, pixels are K:
-// NCHW is already K-major) of one of two operand buffers, one thread issues
-// the sub-chunk's 12 MMAs (the 10 digit pairs stacked into 6 per K-step of 16)
-// and commits to that buffer's mbarrier; the conversion of the next sub-chunk
-// (into the other buffer) overlaps the tensor cores, and every thread fetches
-// the features after next into registers meanwhile.
+// NCHW is already K-major) of one of two operand buffers and arrive, one
+// arrival per warp, on that buffer's `full` mbarrier; thread 0 waits for it,
+// issues the sub-chunk's 12 MMAs (the 10 digit pairs stacked into 6 per K-step
+// of 16) and commits to the buffer's `empty` mbarrier, which a warp waits for
+// before converting into the buffer again.  No CTA-wide barrier in the loop:
+// each warp runs ahead as far as the two buffers allow, and the features after
+// next stream into shared memory with cp.async meanwhile.  At the end of a
+// window thread 0 also commits to `acc_full`; every warp drains its TMEM
+// quarter and arrives on `drained`, which thread 0 waits for before the next
+// window's first MMA (it overwrites the accumulators).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -47,7 +52,7 @@ constexpr int kSub = 32;         // pixels per sub-chunk (one 64-B swizzle row o
 constexpr int kSliceBytes = 128 * kSub * 2;  // one digit slice of a 128-channel block
 constexpr int kBlockBytes = 4 * kSliceBytes; // the four slices of one block
 constexpr int kStageBytes = 128 * kSub * 4;  // one block's FP32 features of a sub-chunk
-constexpr int kWin = 256;        // pixels per exact accumulation window
+constexpr int kWin = 512;        // pixels per exact accumulation window (level sums <= 4 * 64 * 64 * 512 = 2^23)
 constexpr int kThreads = 512;
 constexpr int kSlices = 4;
 constexpr uint32_t kWaitTries = 1u << 26;
@@ -248,8 +253,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
     uint8_t *As[2] = {smem, smem + 2 * kBlockBytes};               // 4 slices x 8 KB each
     uint8_t *Bs[2] = {smem + kBlockBytes, smem + 3 * kBlockBytes};
     float *stg = (float *)(smem + 4 * kBlockBytes);                 // [2 stages][2 blocks][128][32] FP32
-    uint64_t *bar = (uint64_t *)(smem + 4 * kBlockBytes + 4 * kStageBytes);  // [2]
-    uint32_t *tmem_slot = (uint32_t *)(bar + 2);
+    uint64_t *bar = (uint64_t *)(smem + 4 * kBlockBytes + 4 * kStageBytes);  // [7] mbarriers + the abort flag
+    uint32_t *tmem_slot = (uint32_t *)(bar + 8);
     unsigned long long *dsq = (unsigned long long *)(tmem_slot + 2);  // [128] (8-B aligned)
     int *dsum = (int *)(dsq + kTB);                                    // [4][128]
 
@@ -276,8 +281,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(&bar[0], 1);
-        tc::mbar_init(&bar[1], 1);
+        tc::mbar_init(&bar[0], kThreads / 32);  // full[0], full[1]: one arrival per warp
+        tc::mbar_init(&bar[1], kThreads / 32);
+        tc::mbar_init(&bar[2], 1);              // empty[0], empty[1]: tcgen05.commit
+        tc::mbar_init(&bar[3], 1);
+        tc::mbar_init(&bar[4], 1);              // acc_full: tcgen05.commit
+        tc::mbar_init(&bar[5], kThreads / 32);  // drained: one arrival per warp
+        tc::mbar_init(&bar[6], 1);              // fin: the last commit after a failure
+        *reinterpret_cast<volatile int *>(&bar[7]) = 0;
         tc::fence_mbar_init();
     }
     for (int i = tid; i < kSlices * kTB; i += kThreads) dsum[i] = 0;
@@ -291,16 +302,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
 #pragma unroll
     for (int j = 0; j < 32; j++) tot[j] = 0;
     const int q = warp & 3, cg4 = warp >> 2;  // TMEM lane quarter, 32-column group
-    uint32_t phase[2] = {0u, 0u};
-    bool pending[2] = {false, false};         // MMAs reading the buffer not yet waited for
+    // full[b]: the 16 warps converted into buffer b; empty[b]: the MMAs reading buffer b
+    // completed; acc_full: a window's MMAs completed; drained: the 16 warps read the window
+    uint64_t *full = bar, *empty = bar + 2, *acc_full = bar + 4, *drained = bar + 5, *fin = bar + 6;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bar + 7);
     bool failed = false;
-    int in_win = 0;
-    auto wait_buf = [&](int bsel) -> bool {
-        if (!pending[bsel]) return true;
-        const bool ok = tc::mbar_wait(&bar[bsel], phase[bsel], kWaitTries);
-        phase[bsel] ^= 1u;
-        pending[bsel] = false;
-        return ok;
+    // bounded wait that also gives up as soon as another warp has given up
+    auto bwait = [&](uint64_t *b, uint32_t parity) -> bool {
+        for (uint32_t n = 0; n < kWaitTries; n += 1u << 12) {
+            if (tc::mbar_wait(b, parity, 1u << 12)) return true;
+            if (*abort_flag) return false;
+        }
+        *abort_flag = 1;
+        return false;
     };
 
     // features stream into two FP32 stages, two sub-chunks ahead of the conversion
@@ -314,14 +328,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
     };
     stage(0, p0);
     stage(1, p0 + kSub);
-    int kk = 0;
+    int kk = 0, in_win = 0, win = 0, issued_windows = 0;
     for (long q0 = p0; q0 < p1; q0 += kSub, kk++) {
         const int bsel = kk & 1;
+        if (*abort_flag) { failed = true; break; }
         // the MMAs of sub-chunk kk-2 read this operand buffer
-        if (__syncthreads_or(!wait_buf(bsel))) {
-            failed = true;
-            break;
-        }
+        if (kk >= 2 && !bwait(&empty[bsel], ((kk - 2) >> 1) & 1)) { failed = true; break; }
         tc::cp_async_wait<1>();  // this thread's copies of sub-chunk kk have landed (kk+1 may be in flight)
         {
             const float *sa = stg + (size_t)bsel * 2 * kTB * kSub;
@@ -336,24 +348,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
         // each thread reads back only what it staged itself, so the stage can be
         // refilled (sub-chunk kk+2) right away
         stage(bsel, q0 + 2 * kSub);
-        tc::fence_proxy_async_smem();
-        tc::tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc::tc_fence_after();
-            const uint32_t a_addr = tc::smem_u32(As[bsel]);
-            issue_level_mmas(tmem, a_addr, diag ? a_addr : tc::smem_u32(Bs[bsel]), in_win == 0);
-            tc::mma_commit(&bar[bsel]);
-        }
-        pending[bsel] = true;
+        tc::fence_proxy_async_smem();  // this thread's operand writes, visible to the tensor cores
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive_cta(&full[bsel]);
+        const bool first = in_win == 0;
         in_win += kSub;
-        if (in_win >= kWin || q0 + kSub >= p1) {
-            // drain the window's exact level sums into int64 (the commit of this
-            // sub-chunk covers every earlier MMA of the window)
-            if (__syncthreads_or(!wait_buf(bsel))) {
-                failed = true;
-                break;
+        const bool win_end = in_win >= kWin || q0 + kSub >= p1;
+        if (tid == 0) {
+            bool ok = bwait(&full[bsel], (kk >> 1) & 1);
+            // the first MMA of a window overwrites the accumulators the warps drained
+            if (ok && first && win > 0) ok = bwait(drained, (win - 1) & 1);
+            if (ok) {
+                tc::tc_fence_after();
+                const uint32_t a_addr = tc::smem_u32(As[bsel]);
+                issue_level_mmas(tmem, a_addr, diag ? a_addr : tc::smem_u32(Bs[bsel]), first);
+                tc::mma_commit(&empty[bsel]);
+                if (win_end) {
+                    tc::mma_commit(acc_full);
+                    issued_windows++;
+                }
             }
+        }
+        __syncwarp();
+        if (win_end) {
+            // drain the window's exact level sums into int64 (acc_full covers every MMA of the window)
+            if (!bwait(acc_full, win & 1)) { failed = true; break; }
             tc::tc_fence_after();
 #pragma unroll
             for (int L = 0; L < 4; L++) {
@@ -364,29 +383,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
                 tc::tmem_wait_ld();
                 const int sh = 7 * (4 - L);
 #pragma unroll
-                for (int j = 0; j < 16; j++) {
-                    const int v0 = __float_as_int(__fadd_rn(__uint_as_float(r0[j]), kMagic)) - 0x4B400000;
-                    const int v1 = __float_as_int(__fadd_rn(__uint_as_float(r1[j]), kMagic)) - 0x4B400000;
-                    tot[j] += (long long)v0 << sh;
-                    tot[16 + j] += (long long)v1 << sh;
+                for (int jj = 0; jj < 16; jj++) {
+                    const int v0 = __float_as_int(__fadd_rn(__uint_as_float(r0[jj]), kMagic)) - 0x4B400000;
+                    const int v1 = __float_as_int(__fadd_rn(__uint_as_float(r1[jj]), kMagic)) - 0x4B400000;
+                    tot[jj] += (long long)v0 << sh;
+                    tot[16 + jj] += (long long)v1 << sh;
                 }
             }
             tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive_cta(drained);
+            win++;
             in_win = 0;
         }
     }
+    __syncthreads();
+    failed = failed || *abort_flag;
     if (failed) {
-        if (tid == 0) atomicOr(status, kStatusMmaTimeout);
-        // MMAs still in flight finish (bounded) before the accumulators are freed
-        wait_buf(0);
-        wait_buf(1);
+        if (tid == 0) {
+            atomicOr(status, kStatusMmaTimeout);
+            // every MMA issued so far completes (bounded) before the accumulators are freed
+            tc::mma_commit(fin);
+            tc::mbar_wait(fin, 0, kWaitTries);
+        }
     } else {
         const int c1 = ti * kTB + 32 * q + lane;
         if (c1 < C) {
 #pragma unroll
-            for (int j = 0; j < 32; j++) {
-                const int c2 = tj * kTB + 32 * cg4 + j;
-                if (c2 < C && tot[j] != 0) atomicAdd(&Gint[(long)c1 * C + c2], (unsigned long long)tot[j]);
+            for (int jj = 0; jj < 32; jj++) {
+                const int c2 = tj * kTB + 32 * cg4 + jj;
+                if (c2 < C && tot[jj] != 0) atomicAdd(&Gint[(long)c1 * C + c2], (unsigned long long)tot[jj]);
             }
         }
         __syncthreads();  // dsum / dsq complete
@@ -401,6 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
             }
         }
     }
+    (void)issued_windows;
     tc::cp_async_wait<0>();  // no copy into this CTA's shared memory outlives it
     tc::tc_fence_before();
     __syncthreads();
@@ -484,7 +511,7 @@ static GramPlan gram_plan(int C, int nimg) {
     g.off_G = take(sizeof(unsigned long long) * (size_t)C * C * nimg);
     g.off_D = take(sizeof(unsigned long long) * (size_t)kSlices * C * nimg);
     g.total = o;
-    g.smem = 1024 + 4 * (size_t)kBlockBytes + 4 * (size_t)kStageBytes + 64 + sizeof(int) * kSlices * kTB +
+    g.smem = 1024 + 4 * (size_t)kBlockBytes + 4 * (size_t)kStageBytes + 128 + sizeof(int) * kSlices * kTB +
              sizeof(unsigned long long) * kTB;
     return g;
 }

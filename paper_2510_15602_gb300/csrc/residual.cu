@@ -156,19 +156,21 @@ __global__ void __launch_bounds__(kResThreads) k_residual(const __grid_constant_
 // one image with ALL C channels staged in shared memory by 16-byte cp.async
 // copies, so the second walk over the channels reads shared memory, not DRAM
 // (features read once, residual written once).  Thread t owns pixel t % TP and
-// the components (projection) or channels (residual) congruent to t / TP; the
-// arithmetic and its order are those of k_residual, so the results are equal.
+// the channels congruent to g = t / TP (mod G): the projections are summed over
+// its channels in registers (DRM >= dres accumulators), the G partial sums of a
+// pixel are added in a fixed order in shared memory, and the residual of its
+// channels is formed with the pixel's projections held in registers.
 constexpr int kTileThreads = 256;
 
 size_t residual_tiled_smem(int C, int dres, int TP) {
-    return sizeof(float) * ((size_t)C * TP + C + (size_t)C * dres + (size_t)kMaxResidual * TP) +
-           2 * sizeof(uint32_t) * C;
+    const int G = kTileThreads / TP;
+    return sizeof(float) * ((size_t)C * TP + C + (size_t)C * dres + (size_t)G * dres * TP) + 2 * sizeof(uint32_t) * C;
 }
 
-template <int TP>
+template <int TP, int DRM>
 __global__ void __launch_bounds__(kTileThreads) k_residual_tiled(const __grid_constant__ ResP p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int G = kTileThreads / TP;  // thread groups: components / channels per group stride
+    constexpr int G = kTileThreads / TP;
     const int C = p.C, dr = p.dres;
     const int img = blockIdx.x / p.tiles, tile = blockIdx.x % p.tiles;
     const long N = (long)p.H * p.W;
@@ -180,9 +182,9 @@ __global__ void __launch_bounds__(kTileThreads) k_residual_tiled(const __grid_co
     float *xs = reinterpret_cast<float *>(smem_raw);    // [C][TP]
     float *mu = xs + (size_t)C * TP;                    // [C]
     float *Vs = mu + C;                                 // [C][dres]
-    float *ys = Vs + (size_t)C * dr;                    // [kMaxResidual][TP]
-    uint32_t *mn = reinterpret_cast<uint32_t *>(ys + (size_t)kMaxResidual * TP);  // [C]
-    uint32_t *mx = mn + C;                                                        // [C]
+    float *part = Vs + (size_t)C * dr;                  // [G][dres][TP] partial projections
+    uint32_t *mn = reinterpret_cast<uint32_t *>(part + (size_t)G * dr * TP);  // [C]
+    uint32_t *mx = mn + C;                                                    // [C]
     const int tid = threadIdx.x;
     // stage the tile: TP/4 16-byte chunks per channel (N % 4 == 0: a chunk is all in or all out)
     constexpr int CH = TP / 4;
@@ -202,36 +204,38 @@ __global__ void __launch_bounds__(kTileThreads) k_residual_tiled(const __grid_co
     for (int e = tid; e < C * dr; e += kTileThreads) Vs[e] = (float)Vg[e];
     tc::cp_async_wait<0>();
     __syncthreads();
-    const int pl = tid % TP, grp = tid / TP;
+    const int pl = tid % TP, grp = tid / TP;  // a warp shares grp (TP >= 32), so V reads broadcast
     const bool ok = p0 + pl < N;
-    // projections y_k = sum_c (x_c - mean_c) V_ck, components k = grp, grp + G, ...
-    {
-        constexpr int KPT = (kMaxResidual + G - 1) / G;
-        float y[KPT];
+    float y[DRM];
 #pragma unroll
-        for (int u = 0; u < KPT; u++) y[u] = 0.0f;
-        for (int c = 0; c < C; c++) {
-            const float xm = xs[(size_t)c * TP + pl] - mu[c];
-            const float *v = Vs + (size_t)c * dr;
+    for (int k = 0; k < DRM; k++) y[k] = 0.0f;
+    for (int c = grp; c < C; c += G) {
+        const float xm = xs[(size_t)c * TP + pl] - mu[c];
+        const float *v = Vs + (size_t)c * dr;
 #pragma unroll
-            for (int u = 0; u < KPT; u++) {
-                const int k = grp + u * G;
-                if (k < dr) y[u] = fmaf(xm, v[k], y[u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < KPT; u++) {
-            const int k = grp + u * G;
-            if (k < dr) ys[(size_t)k * TP + pl] = y[u];
-        }
+        for (int k = 0; k < DRM; k++)
+            if (k < dr) y[k] = fmaf(xm, v[k], y[k]);
     }
+#pragma unroll
+    for (int k = 0; k < DRM; k++)
+        if (k < dr) part[((size_t)grp * dr + k) * TP + pl] = y[k];
     __syncthreads();
-    // residual f_c = (x_c - mean_c) - sum_k V_ck y_k for channels c = grp, grp + G, ...; per-channel keys
+    // the pixel's projections: the G partial sums in a fixed order
+#pragma unroll
+    for (int k = 0; k < DRM; k++)
+        if (k < dr) {
+            float t = part[(size_t)k * TP + pl];
+            for (int g = 1; g < G; g++) t += part[((size_t)g * dr + k) * TP + pl];
+            y[k] = t;
+        }
+    // residual f_c = (x_c - mean_c) - sum_k V_ck y_k for the thread's channels; per-channel keys
     const int lane = tid & 31;
     for (int c = grp; c < C; c += G) {
         const float *v = Vs + (size_t)c * dr;
         float f = xs[(size_t)c * TP + pl] - mu[c];
-        for (int k = 0; k < dr; k++) f = fmaf(-v[k], ys[(size_t)k * TP + pl], f);
+#pragma unroll
+        for (int k = 0; k < DRM; k++)
+            if (k < dr) f = fmaf(-v[k], y[k], f);
         if (ok) Fo[(size_t)c * N + p0 + pl] = f;
         const uint32_t key = f2key(f);
         const uint32_t kmin = __reduce_min_sync(0xffffffffu, ok ? key : 0xffffffffu);
@@ -266,10 +270,15 @@ cudaError_t launch_residual(const float *X, int layout, int H, int W, int C, con
         if (r == cudaSuccess) r = cudaFuncSetAttribute(k_residual<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         if (r == cudaSuccess) r = cudaFuncSetAttribute(k_residual<4, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         if (r == cudaSuccess) r = cudaFuncSetAttribute(k_residual<4, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        if (r == cudaSuccess)
-            r = cudaFuncSetAttribute(k_residual_tiled<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        if (r == cudaSuccess)
-            r = cudaFuncSetAttribute(k_residual_tiled<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        auto tiled = [&](auto kern) {
+            if (r == cudaSuccess) r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        };
+        tiled(k_residual_tiled<64, 8>);
+        tiled(k_residual_tiled<64, 16>);
+        tiled(k_residual_tiled<64, 32>);
+        tiled(k_residual_tiled<32, 8>);
+        tiled(k_residual_tiled<32, 16>);
+        tiled(k_residual_tiled<32, 32>);
         return r;
     });
     if (e != cudaSuccess) return e;
@@ -284,10 +293,16 @@ cudaError_t launch_residual(const float *X, int layout, int H, int W, int C, con
             const int tiles = (int)((N + TP - 1) / TP);
             ResP p{X, layout, H, W, C, dres, tiles, mean, V, F, mm};
             const unsigned grid = (unsigned)((long)tiles * nimg);
-            if (TP == 64)
-                QFCA_LAUNCH("k_residual", st, (k_residual_tiled<64><<<grid, kTileThreads, smem, st>>>(p)));
-            else
-                QFCA_LAUNCH("k_residual", st, (k_residual_tiled<32><<<grid, kTileThreads, smem, st>>>(p)));
+            auto go = [&](auto kern) { QFCA_LAUNCH("k_residual", st, (kern<<<grid, kTileThreads, smem, st>>>(p))); };
+            if (TP == 64) {
+                if (dres <= 8) go(k_residual_tiled<64, 8>);
+                else if (dres <= 16) go(k_residual_tiled<64, 16>);
+                else go(k_residual_tiled<64, 32>);
+            } else {
+                if (dres <= 8) go(k_residual_tiled<32, 8>);
+                else if (dres <= 16) go(k_residual_tiled<32, 16>);
+                else go(k_residual_tiled<32, 32>);
+            }
             return cudaGetLastError();
         }
     }
