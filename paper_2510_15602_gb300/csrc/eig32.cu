@@ -4,9 +4,13 @@
 // residuals are formed in float-float; one CTA per matrix, nothing but CTA
 // barriers (n <= 256, d <= 32).
 //
-//   1. Householder tridiagonalisation A = Q T Q^T in FP32 on the packed lower
-//      triangle in shared memory (warp per row for the symmetric product and
-//      the rank-2 update); reflector k stays in column k of the packed storage.
+//   1. Householder tridiagonalisation A = Q T Q^T in FP32 on the lower
+//      triangle packed by columns in shared memory (column j contiguous).  One
+//      pass over the trailing block per step, warp per column: the rank-2
+//      update of reflector k and, on the updated entries, the symmetric product
+//      with reflector k+1 (formed first from column k+1, updated alone); the
+//      row contributions go to per-warp partial vectors, summed in a fixed
+//      order.  Reflector k stays in column k (contiguous) for the later passes.
 //   2. The top d eigenvalues sigma_j of T by warp multisection on the FP32
 //      Sturm count; eigenvectors z_j of T by two steps of inverse iteration
 //      (Gaussian elimination with partial pivoting, one lane per eigenvector);
@@ -49,6 +53,8 @@ struct Eig32Args {
 };
 
 __host__ __device__ inline int poff(int i) { return i * (i + 1) / 2; }
+// Lower triangle packed by columns: entry (i, j), i >= j, at coff(j, n) + i - j.
+__host__ __device__ inline int coff(int j, int n) { return j * n - j * (j - 1) / 2; }
 
 // Shared-memory plan in floats (every region starts on a 16-byte boundary):
 // packed triangle (later the float-float W' panel), the X and U panels, seven
@@ -170,23 +176,26 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
     float *scr = a.scr + (size_t)mat * 3 * n * 32;
     float *Zg = a.Z + (size_t)mat * n * 32;
 
-    // ---------------------------------------------------------------- 0. load hi parts
-    for (int i = warp; i < n; i += kNW) {
-        float *row = Ap + poff(i);
-        for (int j = lane; j <= i; j += 32) row[j] = A[(size_t)i * n + j].x;
+    // ---------------------------------------------------------------- 0. load hi parts (column j = row j)
+    for (int jc = warp; jc < n; jc += kNW) {
+        float *col = Ap + coff(jc, n) - jc;  // col[i] = A(i, jc), i >= jc
+        for (int i = jc + lane; i < n; i += 32) col[i] = A[(size_t)jc * n + i].x;
     }
     __syncthreads();
 
     // ---------------------------------------------------------------- 1. tridiagonalisation (FP32)
-    for (int k = 0; k + 2 < n; k++) {
-        const int m0 = k + 1;
+    // vcur: the current reflector v_k, vn: the next one (the two swap every step), pv: the
+    // product of the trailing block with v_k (unscaled), wv: w_k
+    float *vcur = vs, *pv = ps;
+    float *wv = X, *vn = X + n4;  // the X panel is free until the eigenvectors
+    float *pw = U;                // [kNW][n] per-warp partial products (the U panel likewise)
+    // reflector of column c (rows c+1..n-1) into dst; returns tau (0: nothing to reduce)
+    auto make_reflector = [&](int c, float *dst) -> float {
+        const float *col = Ap + coff(c, n) - c;
         float part = 0.0f;
-        for (int i = m0 + 1 + tid; i < n; i += kT) {
-            const float x = Ap[poff(i) + k];
-            part = fmaf(x, x, part);
-        }
+        for (int i = c + 2 + tid; i < n; i += kT) part = fmaf(col[i], col[i], part);
         const float sig = block_sum_f(part, red);
-        const float x1 = Ap[poff(m0) + k];
+        const float x1 = col[c + 1];
         float alpha = x1, tau = 0.0f, v1 = 0.0f;
         if (sig > 0.0f) {
             const float nn = fmaf(x1, x1, sig);
@@ -196,52 +205,102 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
             tau = 1.0f / (nn - alpha * x1);
         }
         if (tid == 0) {
-            dT[k] = Ap[poff(k) + k];
-            eT[k] = alpha;
-            tauv[k] = tau;
-            v1s[k] = v1;
+            eT[c] = alpha;
+            tauv[c] = tau;
+            v1s[c] = v1;
         }
-        if (tau == 0.0f) {  // column already reduced (uniform: sig is the same in every thread)
+        for (int i = c + 1 + tid; i < n; i += kT) dst[i] = i == c + 1 ? v1 : col[i];
+        return tau;
+    };
+    // one pass over the columns j0..n-1 of the trailing block: with `upd`, the rank-2
+    // update A -= v w^T + w v^T of the current reflector; with `acc`, pv = A vn on the
+    // updated entries (column part by warp sums, row part into the warp's partial vector)
+    auto fused_pass = [&](int j0, bool upd, bool acc) {
+        if (acc) {
+            for (int e = tid; e < kNW * n; e += kT) pw[e] = 0.0f;
             __syncthreads();
-            continue;
         }
-        for (int i = m0 + tid; i < n; i += kT) vs[i] = i == m0 ? v1 : Ap[poff(i) + k];
-        __syncthreads();
-        // p = tau A' v (A' rows/columns m0..n-1): warp per row, row part then column part
-        float pv = 0.0f;
-        for (int i = m0 + warp; i < n; i += kNW) {
-            const float *row = Ap + poff(i);
-            float s = 0.0f;
-            for (int j = m0 + lane; j <= i; j += 32) s = fmaf(row[j], vs[j], s);
-            for (int j = i + 1 + lane; j < n; j += 32) s = fmaf(Ap[poff(j) + i], vs[j], s);
-            s = tau * warp_sum_f(s);
-            if (lane == 0) ps[i] = s;
-            pv = fmaf(s, vs[i], pv);
-        }
-        if (lane == 0) red[32 + warp] = pv;
-        __syncthreads();
-        float K = 0.0f;
-#pragma unroll
-        for (int w = 0; w < kNW; w++) K += red[32 + w];
-        K *= 0.5f * tau;
-        // A' -= v w^T + w v^T with w = p - K v
-        for (int i = m0 + warp; i < n; i += kNW) {
-            const float vi = vs[i], wi = fmaf(-K, vs[i], ps[i]);
-            float *row = Ap + poff(i);
-            for (int j = m0 + lane; j <= i; j += 32) {
-                const float vj = vs[j], wj = fmaf(-K, vs[j], ps[j]);
-                row[j] = fmaf(-vi, wj, fmaf(-wi, vj, row[j]));
+        float *pwr = pw + (size_t)warp * n;
+        for (int jc = j0 + warp; jc < n; jc += kNW) {
+            float *col = Ap + coff(jc, n) - jc;
+            const float vj = vcur[jc], wj = upd ? wv[jc] : 0.0f, vnj = acc ? vn[jc] : 0.0f;
+            float dot = 0.0f;
+            for (int i = jc + lane; i < n; i += 32) {
+                float a = col[i];
+                if (upd) {
+                    a = fmaf(-vcur[i], wj, fmaf(-wv[i], vj, a));
+                    col[i] = a;
+                }
+                if (acc) {
+                    dot = fmaf(a, vn[i], dot);
+                    if (i > jc) pwr[i] = fmaf(a, vnj, pwr[i]);  // row i is always this lane's
+                }
+            }
+            if (acc) {
+                dot = warp_sum_f(dot);
+                if (lane == 0) pwr[jc] += dot;
             }
         }
+        __syncthreads();
+        if (acc) {
+            for (int i = j0 + tid; i < n; i += kT) {
+                float t = 0.0f;
+#pragma unroll 8
+                for (int w = 0; w < kNW; w++) t += pw[(size_t)w * n + i];
+                pv[i] = t;
+            }
+            __syncthreads();
+        }
+    };
+    if (tid == 0) {
+        for (int i = n - 2 < 0 ? 0 : n - 2; i < n; i++) eT[i] = 0.0f, tauv[i] = 0.0f;
+    }
+    // reflector 0 (into vn) and its product with the untouched trailing block; then it becomes current
+    float tau_cur = n >= 3 ? make_reflector(0, vn) : 0.0f;
+    __syncthreads();
+    if (tau_cur != 0.0f) fused_pass(1, false, true);
+    if (n >= 3 && tid == 0) Ap[coff(0, n) + 1] = v1s[0];  // column 0 now holds reflector 0
+    {
+        float *t = vcur;
+        vcur = vn;
+        vn = t;
+    }
+    __syncthreads();
+    for (int k = 0; k + 2 < n; k++) {
+        if (tid == 0) dT[k] = Ap[coff(k, n)];
+        const int m0 = k + 1;
+        if (tau_cur != 0.0f) {
+            // p = tau A v, K = (tau / 2) p.v, w = p - K v
+            float part = 0.0f;
+            for (int i = m0 + tid; i < n; i += kT) part = fmaf(pv[i], vcur[i], part);
+            const float K = 0.5f * tau_cur * tau_cur * block_sum_f(part, red);
+            for (int i = m0 + tid; i < n; i += kT) wv[i] = fmaf(-K, vcur[i], tau_cur * pv[i]);
+            __syncthreads();
+            // column k+1 alone first: reflector k+1 is formed from it
+            float *col = Ap + coff(m0, n) - m0;
+            const float vj = vcur[m0], wj = wv[m0];
+            for (int i = m0 + tid; i < n; i += kT) col[i] = fmaf(-vcur[i], wj, fmaf(-wv[i], vj, col[i]));
+            __syncthreads();
+        }
+        const bool has_next = k + 3 < n;
+        const float tau_next = has_next ? make_reflector(m0, vn) : 0.0f;
+        if (has_next) __syncthreads();
+        if (tau_cur != 0.0f || tau_next != 0.0f) fused_pass(k + 2, tau_cur != 0.0f, tau_next != 0.0f);
+        if (has_next && tid == 0) Ap[coff(m0, n) + 1] = v1s[m0];  // column k+1 now holds reflector k+1
+        // reflector k+1 becomes the current one
+        float *t = vcur;
+        vcur = vn;
+        vn = t;
+        tau_cur = tau_next;
         __syncthreads();
     }
     if (tid == 0) {
         if (n >= 2) {
-            dT[n - 2] = Ap[poff(n - 2) + n - 2];
-            eT[n - 2] = Ap[poff(n - 1) + n - 2];
+            dT[n - 2] = Ap[coff(n - 2, n)];
+            eT[n - 2] = Ap[coff(n - 2, n) + 1];
             tauv[n - 2] = 0.0f;
         }
-        dT[n - 1] = Ap[poff(n - 1) + n - 1];
+        dT[n - 1] = Ap[coff(n - 1, n)];
         eT[n - 1] = 0.0f;
         tauv[n - 1] = 0.0f;
     }
@@ -332,10 +391,10 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
             if (tau == 0.0f) continue;
             const int m0 = k + 1;
             float s = 0.0f;
-            for (int i = m0 + lane; i < n; i += 32) s = fmaf(i == m0 ? v1s[k] : Ap[poff(i) + k], x[(size_t)i * kXS], s);
+            const float *vk = Ap + coff(k, n) - k;  // reflector k: vk[i], i = k+1..n-1
+            for (int i = m0 + lane; i < n; i += 32) s = fmaf(vk[i], x[(size_t)i * kXS], s);
             s = tau * warp_sum_f(s);
-            for (int i = m0 + lane; i < n; i += 32)
-                x[(size_t)i * kXS] = fmaf(-s, i == m0 ? v1s[k] : Ap[poff(i) + k], x[(size_t)i * kXS]);
+            for (int i = m0 + lane; i < n; i += 32) x[(size_t)i * kXS] = fmaf(-s, vk[i], x[(size_t)i * kXS]);
         }
     }
     __syncthreads();
@@ -373,10 +432,10 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
             if (tau == 0.0f) continue;
             const int m0 = k + 1;
             float s = 0.0f;
-            for (int i = m0 + lane; i < n; i += 32) s = fmaf(i == m0 ? v1s[k] : Ap[poff(i) + k], u[(size_t)i * kXS], s);
+            const float *vk = Ap + coff(k, n) - k;
+            for (int i = m0 + lane; i < n; i += 32) s = fmaf(vk[i], u[(size_t)i * kXS], s);
             s = tau * warp_sum_f(s);
-            for (int i = m0 + lane; i < n; i += 32)
-                u[(size_t)i * kXS] = fmaf(-s, i == m0 ? v1s[k] : Ap[poff(i) + k], u[(size_t)i * kXS]);
+            for (int i = m0 + lane; i < n; i += 32) u[(size_t)i * kXS] = fmaf(-s, vk[i], u[(size_t)i * kXS]);
         }
         float s = 0.0f;
         for (int i = lane; i < n; i += 32) s = fmaf(Zg[(size_t)i * 32 + warp], u[(size_t)i * kXS], s);
@@ -398,10 +457,10 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
             if (tau == 0.0f) continue;
             const int m0 = k + 1;
             float t = 0.0f;
-            for (int i = m0 + lane; i < n; i += 32) t = fmaf(i == m0 ? v1s[k] : Ap[poff(i) + k], u[(size_t)i * kXS], t);
+            const float *vk = Ap + coff(k, n) - k;
+            for (int i = m0 + lane; i < n; i += 32) t = fmaf(vk[i], u[(size_t)i * kXS], t);
             t = tau * warp_sum_f(t);
-            for (int i = m0 + lane; i < n; i += 32)
-                u[(size_t)i * kXS] = fmaf(-t, i == m0 ? v1s[k] : Ap[poff(i) + k], u[(size_t)i * kXS]);
+            for (int i = m0 + lane; i < n; i += 32) u[(size_t)i * kXS] = fmaf(-t, vk[i], u[(size_t)i * kXS]);
         }
         float *x = X + warp;
         for (int i = lane; i < n; i += 32) {

@@ -177,12 +177,11 @@ __device__ __forceinline__ void read_stage(const float *stage, float (&v)[8]) {
 
 // Convert the loaded block into 4 digit slices (K-major, 64-B swizzle);
 // optionally accumulate per-row digit sums and the level-4 diagonal terms.
-__device__ __forceinline__ void convert_block(const float (&v)[8], int C, int c0, const float *__restrict__ scale,
-                                              uint8_t *slices, int *__restrict__ dsum /* [4][128] or null */,
+// s: the channel's power-of-two scale (0 for rows past C).
+__device__ __forceinline__ void convert_block(const float (&v)[8], float s, uint8_t *slices,
+                                              int *__restrict__ dsum /* [4][128] or null */,
                                               unsigned long long *__restrict__ dsq /* [128] or null */) {
     const int row = threadIdx.x >> 2, g = threadIdx.x & 3;
-    const int c = c0 + row;
-    const float s = c < C ? scale[c] : 0.0f;
     float dd[kSlices][8];
 #pragma unroll
     for (int e = 0; e < 8; e++) digits4(__fmul_rn(v[e], s), dd[0][e], dd[1][e], dd[2][e], dd[3][e]);
@@ -250,8 +249,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
                                                       int *__restrict__ status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = tc::align_smem<1024>(smem_raw);
-    uint8_t *As[2] = {smem, smem + 2 * kBlockBytes};               // 4 slices x 8 KB each
-    uint8_t *Bs[2] = {smem + kBlockBytes, smem + 3 * kBlockBytes};
+    // operand buffer b: A slices at smem + 2 b kBlockBytes, B slices right after (4 slices x 8 KB each)
+    auto As = [&](int b) { return smem + 2 * b * kBlockBytes; };
+    auto Bs = [&](int b) { return smem + (2 * b + 1) * kBlockBytes; };
     float *stg = (float *)(smem + 4 * kBlockBytes);                 // [2 stages][2 blocks][128][32] FP32
     uint64_t *bar = (uint64_t *)(smem + 4 * kBlockBytes + 4 * kStageBytes);  // [7] mbarriers + the abort flag
     uint32_t *tmem_slot = (uint32_t *)(bar + 8);
@@ -302,6 +302,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
 #pragma unroll
     for (int j = 0; j < 32; j++) tot[j] = 0;
     const int q = warp & 3, cg4 = warp >> 2;  // TMEM lane quarter, 32-column group
+    // the scales of this thread's channel row in both blocks, loaded once
+    const int crow = tid >> 2;
+    const float sA = ti * kTB + crow < C ? scale[ti * kTB + crow] : 0.0f;
+    const float sB = tj * kTB + crow < C ? scale[tj * kTB + crow] : 0.0f;
     // full[b]: the 16 warps converted into buffer b; empty[b]: the MMAs reading buffer b
     // completed; acc_full: a window's MMAs completed; drained: the 16 warps read the window
     uint64_t *full = bar, *empty = bar + 2, *acc_full = bar + 4, *drained = bar + 5, *fin = bar + 6;
@@ -339,10 +343,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
             const float *sa = stg + (size_t)bsel * 2 * kTB * kSub;
             float v[8];
             read_stage(sa, v);
-            convert_block(v, C, ti * kTB, scale, As[bsel], diag ? dsum : nullptr, diag ? dsq : nullptr);
+            convert_block(v, sA, As(bsel), diag ? dsum : nullptr, diag ? dsq : nullptr);
             if (!diag) {
                 read_stage(sa + kTB * kSub, v);
-                convert_block(v, C, tj * kTB, scale, Bs[bsel], nullptr, nullptr);
+                convert_block(v, sB, Bs(bsel), nullptr, nullptr);
             }
         }
         // each thread reads back only what it staged itself, so the stage can be
@@ -360,8 +364,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
             if (ok && first && win > 0) ok = bwait(drained, (win - 1) & 1);
             if (ok) {
                 tc::tc_fence_after();
-                const uint32_t a_addr = tc::smem_u32(As[bsel]);
-                issue_level_mmas(tmem, a_addr, diag ? a_addr : tc::smem_u32(Bs[bsel]), first);
+                const uint32_t a_addr = tc::smem_u32(As(bsel));
+                issue_level_mmas(tmem, a_addr, diag ? a_addr : tc::smem_u32(Bs(bsel)), first);
                 tc::mma_commit(&empty[bsel]);
                 if (win_end) {
                     tc::mma_commit(acc_full);

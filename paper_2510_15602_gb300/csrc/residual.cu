@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 #include "tc.cuh"
 
@@ -152,103 +154,134 @@ __global__ void __launch_bounds__(kResThreads) k_residual(const __grid_constant_
     }
 }
 
-// The tiled form (NCHW, N % 4 == 0, X 16-byte aligned): one CTA = TP pixels of
-// one image with ALL C channels staged in shared memory by 16-byte cp.async
-// copies, so the second walk over the channels reads shared memory, not DRAM
-// (features read once, residual written once).  Thread t owns pixel t % TP and
-// the channels congruent to g = t / TP (mod G): the projections are summed over
-// its channels in registers (DRM >= dres accumulators), the G partial sums of a
-// pixel are added in a fixed order in shared memory, and the residual of its
-// channels is formed with the pixel's projections held in registers.
+// The tiled form (NCHW, N % 4 == 0, X 16-byte aligned): persistent CTAs, each
+// over a contiguous range of TP-pixel tiles of the batch, with ALL C channels of
+// a tile staged in shared memory by 16-byte cp.async copies, double-buffered
+// (the next tile loads while this one is computed), so the second walk over the
+// channels reads shared memory, not DRAM (features read once, residual written
+// once).  Thread t owns pixel t % TP and the channels congruent to
+// g = t / TP (mod G): the projections are summed over its channels in registers
+// (DRM >= dres accumulators), the G partial sums of a pixel are added in a
+// fixed order in shared memory, and the residual of its channels is formed
+// with the pixel's projections held in registers.  A CTA reloads the mean and
+// basis when its range enters a new image and flushes that image's keys when
+// it leaves it.
 constexpr int kTileThreads = 256;
 
 size_t residual_tiled_smem(int C, int dres, int TP) {
     const int G = kTileThreads / TP;
-    return sizeof(float) * ((size_t)C * TP + C + (size_t)C * dres + (size_t)G * dres * TP) + 2 * sizeof(uint32_t) * C;
+    return sizeof(float) * (2 * (size_t)C * TP + C + (size_t)C * dres + (size_t)G * dres * TP) +
+           2 * sizeof(uint32_t) * C;
 }
 
 template <int TP, int DRM>
-__global__ void __launch_bounds__(kTileThreads) k_residual_tiled(const __grid_constant__ ResP p) {
+__global__ void __launch_bounds__(kTileThreads) k_residual_tiled(const __grid_constant__ ResP p, long total_tiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int G = kTileThreads / TP;
+    constexpr int CH = TP / 4;  // 16-byte chunks per channel row of a tile
     const int C = p.C, dr = p.dres;
-    const int img = blockIdx.x / p.tiles, tile = blockIdx.x % p.tiles;
     const long N = (long)p.H * p.W;
-    const long p0 = (long)tile * TP;
-    const float *X = p.X + (size_t)img * C * N;
-    const double *mean = p.mean + (size_t)img * C, *Vg = p.V + (size_t)img * C * dr;
-    float *Fo = p.F + (size_t)img * C * N;
-    uint32_t *mm = p.mm + (size_t)img * 2 * C * kKeyStride;
-    float *xs = reinterpret_cast<float *>(smem_raw);    // [C][TP]
-    float *mu = xs + (size_t)C * TP;                    // [C]
+    float *xs = reinterpret_cast<float *>(smem_raw);    // [2][C][TP]
+    float *mu = xs + 2 * (size_t)C * TP;                // [C]
     float *Vs = mu + C;                                 // [C][dres]
     float *part = Vs + (size_t)C * dr;                  // [G][dres][TP] partial projections
     uint32_t *mn = reinterpret_cast<uint32_t *>(part + (size_t)G * dr * TP);  // [C]
     uint32_t *mx = mn + C;                                                    // [C]
-    const int tid = threadIdx.x;
-    // stage the tile: TP/4 16-byte chunks per channel (N % 4 == 0: a chunk is all in or all out)
-    constexpr int CH = TP / 4;
-    for (int e = tid; e < C * CH; e += kTileThreads) {
-        const int c = e / CH, q4 = e % CH;
-        const long px = p0 + 4 * q4;
-        float *dst = xs + (size_t)c * TP + 4 * q4;
-        if (px < N) tc::cp_async16(tc::smem_u32(dst), X + (size_t)c * N + px);
-        else *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int pl = tid % TP, grp = tid / TP;  // a warp shares grp (TP >= 32), so basis reads broadcast
+    const long t_begin = total_tiles * blockIdx.x / gridDim.x, t_end = total_tiles * (blockIdx.x + 1) / gridDim.x;
+
+    auto issue_load = [&](long t, int b) {
+        const int img = (int)(t / p.tiles);
+        const long p0 = (t % p.tiles) * TP;
+        const float *X = p.X + (size_t)img * C * N;
+        float *buf = xs + (size_t)b * C * TP;
+        for (int e = tid; e < C * CH; e += kTileThreads) {
+            const int c = e / CH, q4 = e % CH;
+            const long px = p0 + 4 * q4;
+            float *dst = buf + (size_t)c * TP + 4 * q4;
+            if (px < N) tc::cp_async16(tc::smem_u32(dst), X + (size_t)c * N + px);
+            else *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto flush_keys = [&](int img) {
+        uint32_t *mm = p.mm + (size_t)img * 2 * C * kKeyStride;
+        for (int c = tid; c < C; c += kTileThreads) {
+            atomicMin(&mm[(size_t)c * kKeyStride], mn[c]);
+            atomicMax(&mm[(size_t)(C + c) * kKeyStride], mx[c]);
+        }
+    };
+    if (t_begin < t_end) issue_load(t_begin, 0);
     tc::cp_async_commit();
-    for (int c = tid; c < C; c += kTileThreads) {
-        mu[c] = (float)mean[c];
-        mn[c] = 0xffffffffu;
-        mx[c] = 0u;
+    int cur = -1;
+    for (long t = t_begin; t < t_end; t++) {
+        const int b = (int)((t - t_begin) & 1);
+        if (t + 1 < t_end) issue_load(t + 1, b ^ 1);
+        tc::cp_async_commit();
+        const int img = (int)(t / p.tiles);
+        if (img != cur) {  // the same in every thread
+            __syncthreads();
+            if (cur >= 0) flush_keys(cur);
+            __syncthreads();
+            const double *mean = p.mean + (size_t)img * C, *Vg = p.V + (size_t)img * C * dr;
+            for (int c = tid; c < C; c += kTileThreads) {
+                mu[c] = (float)mean[c];
+                mn[c] = 0xffffffffu;
+                mx[c] = 0u;
+            }
+            for (int e = tid; e < C * dr; e += kTileThreads) Vs[e] = (float)Vg[e];
+            cur = img;
+        }
+        tc::cp_async_wait<1>();  // tile t has landed (tile t+1 may still be in flight)
+        __syncthreads();
+        const float *xt = xs + (size_t)b * C * TP;
+        const long p0 = (t % p.tiles) * TP;
+        const bool ok = p0 + pl < N;
+        float y[DRM];
+#pragma unroll
+        for (int k = 0; k < DRM; k++) y[k] = 0.0f;
+        for (int c = grp; c < C; c += G) {
+            const float xm = xt[(size_t)c * TP + pl] - mu[c];
+            const float *v = Vs + (size_t)c * dr;
+#pragma unroll
+            for (int k = 0; k < DRM; k++)
+                if (k < dr) y[k] = fmaf(xm, v[k], y[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < DRM; k++)
+            if (k < dr) part[((size_t)grp * dr + k) * TP + pl] = y[k];
+        __syncthreads();
+        // the pixel's projections: the G partial sums in a fixed order
+#pragma unroll
+        for (int k = 0; k < DRM; k++)
+            if (k < dr) {
+                float s = part[(size_t)k * TP + pl];
+                for (int g = 1; g < G; g++) s += part[((size_t)g * dr + k) * TP + pl];
+                y[k] = s;
+            }
+        // residual f_c = (x_c - mean_c) - sum_k V_ck y_k for the thread's channels; per-channel keys
+        float *Fo = p.F + (size_t)img * C * N;
+        for (int c = grp; c < C; c += G) {
+            const float *v = Vs + (size_t)c * dr;
+            float f = xt[(size_t)c * TP + pl] - mu[c];
+#pragma unroll
+            for (int k = 0; k < DRM; k++)
+                if (k < dr) f = fmaf(-v[k], y[k], f);
+            if (ok) Fo[(size_t)c * N + p0 + pl] = f;
+            const uint32_t key = f2key(f);
+            const uint32_t kmin = __reduce_min_sync(0xffffffffu, ok ? key : 0xffffffffu);
+            const uint32_t kmax = __reduce_max_sync(0xffffffffu, ok ? key : 0u);
+            if (lane == 0) {
+                atomicMin(&mn[c], kmin);
+                atomicMax(&mx[c], kmax);
+            }
+        }
+        __syncthreads();  // buffer b and the partial sums are free again
     }
-    for (int e = tid; e < C * dr; e += kTileThreads) Vs[e] = (float)Vg[e];
     tc::cp_async_wait<0>();
-    __syncthreads();
-    const int pl = tid % TP, grp = tid / TP;  // a warp shares grp (TP >= 32), so V reads broadcast
-    const bool ok = p0 + pl < N;
-    float y[DRM];
-#pragma unroll
-    for (int k = 0; k < DRM; k++) y[k] = 0.0f;
-    for (int c = grp; c < C; c += G) {
-        const float xm = xs[(size_t)c * TP + pl] - mu[c];
-        const float *v = Vs + (size_t)c * dr;
-#pragma unroll
-        for (int k = 0; k < DRM; k++)
-            if (k < dr) y[k] = fmaf(xm, v[k], y[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < DRM; k++)
-        if (k < dr) part[((size_t)grp * dr + k) * TP + pl] = y[k];
-    __syncthreads();
-    // the pixel's projections: the G partial sums in a fixed order
-#pragma unroll
-    for (int k = 0; k < DRM; k++)
-        if (k < dr) {
-            float t = part[(size_t)k * TP + pl];
-            for (int g = 1; g < G; g++) t += part[((size_t)g * dr + k) * TP + pl];
-            y[k] = t;
-        }
-    // residual f_c = (x_c - mean_c) - sum_k V_ck y_k for the thread's channels; per-channel keys
-    const int lane = tid & 31;
-    for (int c = grp; c < C; c += G) {
-        const float *v = Vs + (size_t)c * dr;
-        float f = xs[(size_t)c * TP + pl] - mu[c];
-#pragma unroll
-        for (int k = 0; k < DRM; k++)
-            if (k < dr) f = fmaf(-v[k], y[k], f);
-        if (ok) Fo[(size_t)c * N + p0 + pl] = f;
-        const uint32_t key = f2key(f);
-        const uint32_t kmin = __reduce_min_sync(0xffffffffu, ok ? key : 0xffffffffu);
-        const uint32_t kmax = __reduce_max_sync(0xffffffffu, ok ? key : 0u);
-        if (lane == 0) {
-            atomicMin(&mn[c], kmin);
-            atomicMax(&mx[c], kmax);
-        }
-    }
-    __syncthreads();
-    for (int c = tid; c < C; c += kTileThreads) {
-        atomicMin(&mm[(size_t)c * kKeyStride], mn[c]);
-        atomicMax(&mm[(size_t)(C + c) * kKeyStride], mx[c]);
+    if (cur >= 0) {
+        __syncthreads();
+        flush_keys(cur);
     }
 }
 
@@ -287,13 +320,19 @@ cudaError_t launch_residual(const float *X, int layout, int H, int W, int C, con
     const long N = (long)H * W;
     // the tiled form when every feature row can be copied in 16-byte pieces
     if (layout == 0 && N % 4 == 0 && ((uintptr_t)X & 15) == 0) {
-        const int TP = residual_tiled_smem(C, dres, 64) <= 220 * 1024 ? 64 : 32;
+        const int TP = 32;
         const size_t smem = residual_tiled_smem(C, dres, TP);
-        if (smem <= 220 * 1024) {
+        if (smem <= 110 * 1024) {  // two CTAs per SM
             const int tiles = (int)((N + TP - 1) / TP);
             ResP p{X, layout, H, W, C, dres, tiles, mean, V, F, mm};
-            const unsigned grid = (unsigned)((long)tiles * nimg);
-            auto go = [&](auto kern) { QFCA_LAUNCH("k_residual", st, (kern<<<grid, kTileThreads, smem, st>>>(p))); };
+            int n_sm = 0;
+            e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            const long total = (long)tiles * nimg;
+            const unsigned grid = (unsigned)std::min<long>(total, 2L * n_sm);
+            auto go = [&](auto kern) {
+                QFCA_LAUNCH("k_residual", st, (kern<<<grid, kTileThreads, smem, st>>>(p, total)));
+            };
             if (TP == 64) {
                 if (dres <= 8) go(k_residual_tiled<64, 8>);
                 else if (dres <= 16) go(k_residual_tiled<64, 16>);
