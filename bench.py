@@ -1079,6 +1079,8 @@ def run_ours(args):
     dev_s, wall_s = timed(torch, main, lambda i: pipe.step(i), args.steps, fork=lambda: pipe.fork(main),
                           join=lambda: pipe.join(main))
     clocks = sampler.stop(t_region0, time.time())
+    tiling_used = pipe.ctx[0].last_tiling()
+    proj_used = pipe.ctx[0].last_projection_tiling()
     dom_ms, dom_n = 0.0, 0
     for c in pipe.ctx:
         t = c.trace()
@@ -1232,7 +1234,10 @@ def run_ours(args):
             "data": "synthetic (seeded Gaussian random fields with planted anomalies)",
             "config": {"workload": WORKLOAD, "images_per_rank_step": N_IMG, "H": HW, "W": HW, "C": C, "d": D,
                        "B": B, "r": R, "projection": args.precision, "fit": "exact integer Gram + float-float eig",
-                       "window_tiling": "autotuned (measured once during warm-up)",
+                       "window_tiling": "autotuned (measured once during warm-up): strip x band x groups = "
+                                        + "x".join(str(v) for v in tiling_used),
+                       "projection_rings": "autotuned: FP32 boxes in flight x operand chunks = "
+                                           + "x".join(str(v) for v in proj_used),
                        "path": f"qfca_batch_run, CUDA graph, {args.pipes} steps in flight" if not args.no_graph
                        else f"qfca_batch_run, {args.pipes} steps in flight",
                        "l2": "inputs 1 GiB per step > L2 (no flush needed)",

@@ -378,11 +378,19 @@ typedef struct {
 qfca_status qfca_score_batch(qfca_ctx *ctx, const qfca_image *imgs, int n, int C, int layout, int d, int B,
                              int precision, void *stream);
 
-/* Autotuning of the window stage's tiling (strip width, band height,
- * components per CTA) for qfca_score_batch and qfca_batch_run: 0 = the built-in
- * cost model (default), 1 = measure candidates once per shape set (blocking,
- * never under stream capture) and reuse the fastest. */
+/* Autotuning for qfca_score_batch and qfca_batch_run (and qfca_batch_run_basis):
+ * the window stage's tiling (strip width, band height, components per CTA)
+ * and the BF16 projection's ring depths (FP32 feature boxes in flight,
+ * converted operand chunks ahead of the tensor cores).  0 = the built-in cost
+ * model and the deepest rings that fit (default), 1 = measure the candidates
+ * once per shape set (blocking, never under stream capture) and reuse the
+ * fastest.  Results do not depend on either choice. */
 qfca_status qfca_set_autotune(qfca_ctx *ctx, int mode);
+
+/* The ring depths used by the context's most recent TMA-fed projection
+ * (0, 0 before the first): FP32 feature boxes in flight and converted operand
+ * chunks. */
+qfca_status qfca_last_projection_tiling(qfca_ctx *ctx, int *stages, int *operand_buffers);
 
 /* Use a given window-stage tiling for the context's later score launches
  * (strip width 64 or 128 threads, band height 1..64 rows, component groups

@@ -129,6 +129,8 @@ struct qfca_ctx {
     std::map<std::string, qfca::ScoreTiling> tuned;     // measured tilings per shape set
     qfca::ScoreTiling last_tiling{0, 0, 0};
     qfca::ScoreTiling forced{0, 0, 0};                  // window-stage tiling set by the caller (SW 0: none)
+    std::map<std::string, qfca::ProjTiling> proj_tuned; // measured projection ring depths per shape set
+    qfca::ProjTiling last_proj{0, 0};
     float eig_tol = qfca::kEigTolDefault;               // residual bound of the FP32 + Newton eigensolver
     qfca::ServeState *serve = nullptr;                  // serving session (serve.cu)
 };
@@ -307,6 +309,63 @@ qfca_status run_score(qfca_ctx *ctx, const ScoreJob *jobs, int n, int d, int B, 
     if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "%s: no window tiling fits B = %d", where, B);
     if (e != cudaSuccess) return cuda_fail(ctx, e, where);
     return QFCA_OK;
+}
+
+// The projection of a call (`enqueue` initialises its own min/max keys, so it
+// can run again) with the context's ring depths for `key`: with autotuning on,
+// the candidates that fit are timed once per shape set on this stream (outside
+// capture) and the fastest is kept.  Every candidate gives the same result.
+template <class F>
+cudaError_t run_projection(qfca_ctx *ctx, const std::string &key, int C, int d, cudaStream_t st, F &&enqueue) {
+    ProjTiling chosen{0, 0};
+    const ProjTiling *use = nullptr;
+    if (ctx->autotune) {
+        auto it = ctx->proj_tuned.find(key);
+        if (it != ctx->proj_tuned.end()) {
+            chosen = it->second;
+            use = &chosen;
+        } else if (!capturing(st)) {
+            ProjTiling cand[32];
+            const int nc = project_tilings(C, d, false, cand, 32);
+            cudaEvent_t a = nullptr, b = nullptr;
+            cudaError_t e = cudaEventCreate(&a);
+            if (e == cudaSuccess) e = cudaEventCreate(&b);
+            float best_ms = 1e30f;
+            for (int i = 0; i < nc && e == cudaSuccess; i++) {
+                tl_proj_tiling = &cand[i];
+                float tot = 0.0f;
+                for (int rep = 0; rep < 3 && e == cudaSuccess; rep++) {
+                    e = cudaEventRecord(a, st);
+                    if (e == cudaSuccess) e = enqueue();
+                    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                    float ms = 0.0f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+                    if (rep > 0) tot += ms;  // the first run warms up
+                }
+                if (e == cudaSuccess && tot < best_ms) best_ms = tot, chosen = cand[i];
+            }
+            tl_proj_tiling = nullptr;
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+            if (e != cudaSuccess) return e;
+            if (nc > 0) {
+                ctx->proj_tuned[key] = chosen;
+                use = &chosen;
+            }
+        }
+    }
+    tl_proj_tiling = use;
+    const cudaError_t e = enqueue();
+    tl_proj_tiling = nullptr;
+    ctx->last_proj = project_last_tiling();
+    return e;
+}
+
+std::string shape_key(const char *what, int n, int C, int d, const std::vector<long> &sizes) {
+    std::string k = std::string(what) + ":" + std::to_string(n) + ":" + std::to_string(C) + ":" + std::to_string(d);
+    for (long s : sizes) k += ":" + std::to_string(s);
+    return k;
 }
 
 }  // namespace
@@ -743,8 +802,11 @@ static qfca_status batch_run_impl(qfca_ctx *ctx, const float *X, int nimg, qfca_
     }
     float *Y = (float *)(b + o_Y);
     uint32_t *mm = (uint32_t *)(b + o_mm);
-    e = launch_project(X, desc.layout, desc.H, desc.W, C, mean, V, d, nimg, precision, Y, mm, b + o_pj,
-                       ctx->status_dev, st);
+    e = run_projection(ctx, shape_key("batch", nimg, C, d, {N, (long)precision, (long)desc.layout}), C, d, st,
+                       [&] {
+                           return launch_project(X, desc.layout, desc.H, desc.W, C, mean, V, d, nimg, precision, Y,
+                                                 mm, b + o_pj, ctx->status_dev, st);
+                       });
     if (e == cudaErrorNotSupported) return fail(ctx, QFCA_ERR_UNSUPPORTED, "projection precision %d", precision);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run/project");
     e = launch_quantize(Y, N, desc.H, desc.W, d, nimg, B, QFCA_RANGE_IMAGE, mm, nullptr, nullptr, bins, pitch, lo, hi,
@@ -840,17 +902,22 @@ qfca_status qfca_score_batch(qfca_ctx *ctx, const qfca_image *imgs, int n, int C
     for (int i = 0; i < n && tma; i++) tma = project_tma_ok(imgs[i].X, (long)imgs[i].H * imgs[i].W, layout);
     if (mm_stride != (size_t)2 * d * kKeyStride) return fail(ctx, QFCA_ERR_UNSUPPORTED, "key layout");
     if (tma) {
-        float *mean32 = nullptr;
-        void *Vt = nullptr;
-        int Cp = 0, DT = 0;
-        e = launch_prep_bf16(mean, V, C, d, n, b + o_pj, &mean32, &Vt, &Cp, &DT, st);
-        if (e == cudaSuccess) e = launch_init_keys(mm, d, n, st);
-        std::vector<ProjJob> pjobs(n);
-        for (int i = 0; i < n; i++)
-            pjobs[i] = ProjJob{imgs[i].X, (long)imgs[i].H * imgs[i].W, mean32 + (size_t)i * Cp,
-                               (const char *)Vt + sizeof(uint16_t) * (size_t)i * DT * Cp, (float *)(b + o_Y[i]),
-                               mm + (size_t)i * mm_stride};
-        if (e == cudaSuccess) e = launch_project_tma(pjobs.data(), n, C, d, false, ctx->status_dev, st);
+        std::vector<long> sizes;
+        for (int i = 0; i < n; i++) sizes.push_back((long)imgs[i].H * imgs[i].W);
+        e = run_projection(ctx, shape_key("table", n, C, d, sizes), C, d, st, [&] {
+            float *mean32 = nullptr;
+            void *Vt = nullptr;
+            int Cp = 0, DT = 0;
+            cudaError_t r = launch_prep_bf16(mean, V, C, d, n, b + o_pj, &mean32, &Vt, &Cp, &DT, st);
+            if (r == cudaSuccess) r = launch_init_keys(mm, d, n, st);
+            std::vector<ProjJob> pjobs(n);
+            for (int i = 0; i < n; i++)
+                pjobs[i] = ProjJob{imgs[i].X, (long)imgs[i].H * imgs[i].W, mean32 + (size_t)i * Cp,
+                                   (const char *)Vt + sizeof(uint16_t) * (size_t)i * DT * Cp, (float *)(b + o_Y[i]),
+                                   mm + (size_t)i * mm_stride};
+            if (r == cudaSuccess) r = launch_project_tma(pjobs.data(), n, C, d, false, ctx->status_dev, st);
+            return r;
+        });
     } else {
         for (int i = 0; i < n && e == cudaSuccess; i++)
             e = launch_project(imgs[i].X, layout, imgs[i].H, imgs[i].W, C, mean + (size_t)i * C, V + (size_t)i * C * d, d,
@@ -902,6 +969,14 @@ qfca_status qfca_last_tiling(qfca_ctx *ctx, int *strip_width, int *band_height, 
     *strip_width = ctx->last_tiling.SW;
     *band_height = ctx->last_tiling.TH;
     *component_groups = ctx->last_tiling.n_kg;
+    return QFCA_OK;
+}
+
+qfca_status qfca_last_projection_tiling(qfca_ctx *ctx, int *stages, int *operand_buffers) {
+    if (!ctx || !stages || !operand_buffers) return QFCA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    *stages = ctx->last_proj.stages;
+    *operand_buffers = ctx->last_proj.na;
     return QFCA_OK;
 }
 

@@ -132,6 +132,19 @@ cudaError_t launch_prep_bf16(const double *mean, const double *V, int C, int d, 
 cudaError_t launch_init_keys(uint32_t *mm_keys, int d, int nimg, cudaStream_t st);
 cudaError_t launch_project_tma(const ProjJob *jobs, int n, int C, int d, bool fp8, int *status, cudaStream_t st);
 
+// Ring depths of the TMA-fed projection: FP32 feature boxes in flight (stages)
+// and converted operand chunks ahead of the MMAs (na).  The launcher picks the
+// deepest that fit shared memory unless the calling thread has set
+// tl_proj_tiling (the API's autotuner does, around a call); the results do not
+// depend on it.
+struct ProjTiling {
+    int stages, na;
+};
+extern thread_local const ProjTiling *tl_proj_tiling;
+// The candidates that fit shared memory for (C, d); the depths the last launch on this thread used.
+int project_tilings(int C, int d, bool fp8, ProjTiling *out, int max_out);
+ProjTiling project_last_tiling();
+
 // Per-component min/max keys live 128 B apart (one L2 line each):
 // min of component j at mm_keys[j * kKeyStride], max at mm_keys[(d + j) * kKeyStride].
 constexpr int kKeyStride = 32;

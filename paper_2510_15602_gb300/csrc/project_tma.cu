@@ -457,7 +457,23 @@ cudaError_t launch_dt(const ProjParams &p, int *status, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+thread_local ProjTiling tl_last_proj{0, 0};
+
 }  // namespace
+
+thread_local const ProjTiling *tl_proj_tiling = nullptr;
+
+ProjTiling project_last_tiling() { return tl_last_proj; }
+
+int project_tilings(int C, int d, bool fp8, ProjTiling *out, int max_out) {
+    const int DT = d <= 16 ? 16 : (d <= 32 ? 32 : 64);
+    const int Cp = fp8 ? (C + 127) / 128 * 128 : (C + kKc - 1) / kKc * kKc;
+    int n = 0;
+    for (int sg = kMaxStages; sg >= 2; sg--)
+        for (int a = kMaxA; a >= 2; a--)
+            if (n < max_out && smem_layout(sg, a, Cp, DT, fp8).total <= 227 * 1024) out[n++] = ProjTiling{sg, a};
+    return n;
+}
 
 bool project_tma_ok(const float *X, long N, int layout) {
     return layout == QFCA_NCHW && N % 4 == 0 && ((uintptr_t)X & 15) == 0;
@@ -475,6 +491,11 @@ cudaError_t launch_project_tma(const ProjJob *jobs, int n, int C, int d, bool fp
         stages = 2, na = 2;
         if (smem_layout(stages, na, Cp, DT, fp8).total > 227 * 1024) return cudaErrorNotSupported;
     }
+    if (tl_proj_tiling && tl_proj_tiling->stages >= 2 && tl_proj_tiling->stages <= kMaxStages &&
+        tl_proj_tiling->na >= 2 && tl_proj_tiling->na <= kMaxA &&
+        smem_layout(tl_proj_tiling->stages, tl_proj_tiling->na, Cp, DT, fp8).total <= 227 * 1024)
+        stages = tl_proj_tiling->stages, na = tl_proj_tiling->na;
+    tl_last_proj = ProjTiling{stages, na};
     for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
         const int m = n - i0 < kMaxBatch ? n - i0 : kMaxBatch;
         ProjParams p;

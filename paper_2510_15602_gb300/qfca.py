@@ -87,6 +87,8 @@ _lib.qfca_batch_run.argtypes = [_P, _P, _I, Fmap, _I, _I, _I, _I, _P, ctypes.POI
 _lib.qfca_batch_run.restype = _I
 _lib.qfca_batch_run_basis.argtypes = [_P, _P, _I, Fmap, _P, _P, _I, _I, _I, _I, _P, ctypes.POINTER(BatchOutputs), _P]
 _lib.qfca_batch_run_basis.restype = _I
+_lib.qfca_last_projection_tiling.argtypes = [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]
+_lib.qfca_last_projection_tiling.restype = _I
 _lib.qfca_set_tiling.argtypes = [_P, _I, _I, _I]
 _lib.qfca_set_tiling.restype = _I
 _lib.qfca_set_eig_tolerance.argtypes = [_P, ctypes.c_double]
@@ -216,6 +218,12 @@ class Context:
     def set_tiling(self, strip_width: int = 0, band_height: int = 0, component_groups: int = 0):
         """Force the window stage's tiling for later calls (strip_width 0: cost model / autotuner)."""
         self.check(_lib.qfca_set_tiling(self.handle, int(strip_width), int(band_height), int(component_groups)))
+
+    def last_projection_tiling(self) -> tuple[int, int]:
+        """(FP32 boxes in flight, operand chunks) of the most recent TMA-fed projection."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self.check(_lib.qfca_last_projection_tiling(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
 
     def last_tiling(self) -> tuple[int, int, int]:
         """(strip width, band height, component groups) of the most recent window-stage launch."""
