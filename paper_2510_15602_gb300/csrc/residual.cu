@@ -8,9 +8,8 @@
 // per channel, when the layout allows).  The thread forms the dres projections
 // y_k = sum_c (x_c - mean_c) V_ck in FP32 registers (mean and V staged in
 // shared memory as FP32), then walks the channels again to write
-// f_c = (x_c - mean_c) - sum_k V_ck y_k, from the last channel down, so that the
-// channels the first walk read last may still be in L2; on a 1 GB batch most of
-// the second walk still misses L2 (the features are read about twice from DRAM).  Per channel,
+// f_c = (x_c - mean_c) - sum_k V_ck y_k; on a 1 GB batch the second walk misses
+// L2 (measured: the features are read twice from DRAM).  Per channel,
 // a warp reduces the keys with one hardware min and one max reduction, lane 0
 // folds them into the CTA's shared-memory keys, and the CTA adds its C minima
 // and maxima to the image's keys once.  The work is 4 C dres flops per pixel;
@@ -130,20 +129,18 @@ __global__ void __launch_bounds__(kResThreads) k_residual(const __grid_constant_
             atomicMax(&mx[cc], kmax);
         }
     };
-    // second walk from the last channel down: the channels the first walk read last are the
-    // likeliest to be still in L2 (each channel's residual and keys do not depend on the order)
-    c = C;
-    for (; c - U >= 0; c -= U) {
+    c = 0;
+    for (; c + U <= C; c += U) {
         float xs[U][PX];
 #pragma unroll
-        for (int u = 0; u < U; u++) load(c - 1 - u, xs[u]);
+        for (int u = 0; u < U; u++) load(c + u, xs[u]);
 #pragma unroll
-        for (int u = 0; u < U; u++) emit(c - 1 - u, xs[u]);
+        for (int u = 0; u < U; u++) emit(c + u, xs[u]);
     }
-    for (; c > 0; c--) {
+    for (; c < C; c++) {
         float xs[PX];
-        load(c - 1, xs);
-        emit(c - 1, xs);
+        load(c, xs);
+        emit(c, xs);
     }
     __syncthreads();
     for (int c2 = threadIdx.x; c2 < C; c2 += kResThreads) {

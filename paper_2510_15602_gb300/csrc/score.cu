@@ -223,13 +223,6 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ S
             for (int b = 0; b <= B; b++) hc[b * SW] = 0;
         }
         __syncthreads();
-        // B = 32 with the 32-bit walk: the interior reference terms cumR_b N_loc stay in registers
-        constexpr bool kRegCdf = KB == 32 && sizeof(ACC) == 4;
-        uint32_t cr[kRegCdf ? KB - 1 : 1];
-        if (kRegCdf) {
-#pragma unroll
-            for (int b = 0; b < (kRegCdf ? KB - 1 : 1); b++) cr[b] = (uint32_t)cRi[b];
-        }
         if (x < W) {
             // window of the band's first row: tile rows 0 .. 2r
             for (int ry = 0; ry < span; ry++) {
@@ -263,7 +256,7 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ S
 #pragma unroll
                         for (int b = 0; b < KB - 1; b++) {
                             a += hb[b * SW] * Nref;
-                            D32 = __usad(a, kRegCdf ? cr[kRegCdf ? b : 0] : (uint32_t)cRi[b], D32);
+                            D32 = __usad(a, (uint32_t)cRi[b], D32);
                         }
                         D = (ACC)D32;
                     } else if (KB > 0) {
