@@ -175,24 +175,23 @@ __device__ __forceinline__ void read_stage(const float *stage, float (&v)[8]) {
     v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
 
-// Convert the loaded block into 4 digit slices (K-major, 64-B swizzle);
-// optionally accumulate per-row digit sums and the level-4 diagonal terms.
-// s: the channel's power-of-two scale (0 for rows past C).
-__device__ __forceinline__ void convert_block(const float (&v)[8], float s, uint8_t *slices,
+// Convert this thread's 8 values of a block into its 4 digit slices, packed as
+// BF16 pairs in registers (pk[slice]); optionally accumulate per-row digit sums
+// and the level-4 diagonal terms.  The operand buffer is written afterwards
+// (store_block), so the conversion can run while the buffer is still being read.
+__device__ __forceinline__ void convert_block(const float (&v)[8], float s, uint4 (&pk)[kSlices],
                                               int *__restrict__ dsum /* [4][128] or null */,
                                               unsigned long long *__restrict__ dsq /* [128] or null */) {
-    const int row = threadIdx.x >> 2, g = threadIdx.x & 3;
+    const int row = threadIdx.x >> 2;
     float dd[kSlices][8];
 #pragma unroll
     for (int e = 0; e < 8; e++) digits4(__fmul_rn(v[e], s), dd[0][e], dd[1][e], dd[2][e], dd[3][e]);
 #pragma unroll
     for (int sl = 0; sl < kSlices; sl++) {
-        uint4 pk;
-        pk.x = tc::pack_bf16x2(dd[sl][0], dd[sl][1]);
-        pk.y = tc::pack_bf16x2(dd[sl][2], dd[sl][3]);
-        pk.z = tc::pack_bf16x2(dd[sl][4], dd[sl][5]);
-        pk.w = tc::pack_bf16x2(dd[sl][6], dd[sl][7]);
-        *reinterpret_cast<uint4 *>(slices + sl * kSliceBytes + swz(row, g)) = pk;
+        pk[sl].x = tc::pack_bf16x2(dd[sl][0], dd[sl][1]);
+        pk[sl].y = tc::pack_bf16x2(dd[sl][2], dd[sl][3]);
+        pk[sl].z = tc::pack_bf16x2(dd[sl][4], dd[sl][5]);
+        pk[sl].w = tc::pack_bf16x2(dd[sl][6], dd[sl][7]);
         if (dsum) {
             const float t = ((dd[sl][0] + dd[sl][1]) + (dd[sl][2] + dd[sl][3])) +
                             ((dd[sl][4] + dd[sl][5]) + (dd[sl][6] + dd[sl][7]));
@@ -208,6 +207,13 @@ __device__ __forceinline__ void convert_block(const float (&v)[8], float s, uint
         }
         atomicAdd(&dsq[row], (unsigned long long)(long long)t4);
     }
+}
+
+// The packed digits into the K-major, 64-byte-swizzled slices of an operand buffer.
+__device__ __forceinline__ void store_block(const uint4 (&pk)[kSlices], uint8_t *slices) {
+    const int row = threadIdx.x >> 2, g = threadIdx.x & 3;
+#pragma unroll
+    for (int sl = 0; sl < kSlices; sl++) *reinterpret_cast<uint4 *>(slices + sl * kSliceBytes + swz(row, g)) = pk[sl];
 }
 
 // The level sums of one 32-pixel sub-chunk: A_L += sum_{i+j=L} D_i E_j^T for
@@ -336,18 +342,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
     for (long q0 = p0; q0 < p1; q0 += kSub, kk++) {
         const int bsel = kk & 1;
         if (*abort_flag) { failed = true; break; }
-        // the MMAs of sub-chunk kk-2 read this operand buffer
-        if (kk >= 2 && !bwait(&empty[bsel], ((kk - 2) >> 1) & 1)) { failed = true; break; }
         tc::cp_async_wait<1>();  // this thread's copies of sub-chunk kk have landed (kk+1 may be in flight)
+        // the A block is converted into registers while the MMAs of sub-chunk kk-2 may
+        // still read the buffer (the registers of a second block would spill)
+        const float *sa = stg + (size_t)bsel * 2 * kTB * kSub;
+        uint4 pk[kSlices];
         {
-            const float *sa = stg + (size_t)bsel * 2 * kTB * kSub;
             float v[8];
             read_stage(sa, v);
-            convert_block(v, sA, As(bsel), diag ? dsum : nullptr, diag ? dsq : nullptr);
-            if (!diag) {
-                read_stage(sa + kTB * kSub, v);
-                convert_block(v, sB, Bs(bsel), nullptr, nullptr);
-            }
+            convert_block(v, sA, pk, diag ? dsum : nullptr, diag ? dsq : nullptr);
+        }
+        // the MMAs of sub-chunk kk-2 read this operand buffer
+        if (kk >= 2 && !bwait(&empty[bsel], ((kk - 2) >> 1) & 1)) { failed = true; break; }
+        store_block(pk, As(bsel));
+        if (!diag) {
+            float v[8];
+            read_stage(sa + kTB * kSub, v);
+            convert_block(v, sB, pk, nullptr, nullptr);
+            store_block(pk, Bs(bsel));
         }
         // each thread reads back only what it staged itself, so the stage can be
         // refilled (sub-chunk kk+2) right away
@@ -435,220 +447,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
     tc::cp_async_wait<0>();  // no copy into this CTA's shared memory outlives it
     tc::tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
-        tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, 512);
-    }
-}
-
-// 128 < C <= 256: the three tile pairs (0,0), (0,1), (1,1) of one pixel range run as a
-// cluster of three CTAs (cluster rank = pair index).  Ranks 0 and 2 own the diagonal
-// pairs: per sub-chunk each converts its channel block once (channels 0..127, resp.
-// 128..255), runs that block's Gram, and copies the converted slices with one bulk
-// copy into rank 1's A (rank 0) or B (rank 2) operand buffer, completing on rank 1's
-// `full` barrier.  Rank 1 converts nothing: it runs the off-diagonal pair on the two
-// copies and signals both producers with one multicast commit when its MMAs are done
-// with the buffer (`peer_empty`), which the producers wait for before converting into
-// that buffer again.  Each channel block is converted once per pixel instead of twice;
-// arithmetic, windows and drains are those of k_gram, so the Gram is the same.
-__global__ void __launch_bounds__(kThreads, 1) k_gram3(const __grid_constant__ FitParams p,
-                                                       const float *__restrict__ scale,
-                                                       unsigned long long *__restrict__ Gint,
-                                                       unsigned long long *__restrict__ Dsum,
-                                                       int *__restrict__ status) {
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = tc::align_smem<1024>(smem_raw);
-    auto As = [&](int b) { return smem + 2 * b * kBlockBytes; };
-    auto Bs = [&](int b) { return smem + (2 * b + 1) * kBlockBytes; };
-    float *stg = (float *)(smem + 4 * kBlockBytes);
-    uint64_t *bar = (uint64_t *)(smem + 4 * kBlockBytes + 4 * kStageBytes);  // [9] mbarriers + the abort flag
-    uint32_t *tmem_slot = (uint32_t *)(bar + 10);
-    unsigned long long *dsq = (unsigned long long *)(tmem_slot + 2);
-    int *dsum = (int *)(dsq + kTB);
-    uint64_t *full = bar, *empty = bar + 2, *acc_full = bar + 4, *drained = bar + 5, *fin = bar + 6,
-             *peer_empty = bar + 7;
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bar + 9);
-
-    const long cta = blockIdx.x;
-    int img = 0;
-    while (img + 1 < p.n && p.img[img + 1].cta0 <= cta) img++;
-    const FitImgP &im = p.img[img];
-    const int C = p.C, layout = p.layout, vec_ok = p.vec_ok;
-    const long N = im.N, chunk = im.chunk;
-    const float *X = im.X;
-    const int rank = (int)(blockIdx.x % 3);  // the cluster's CTAs are consecutive blocks
-    const int split = (int)((cta - im.cta0) / 3);
-    const bool consumer = rank == 1;
-    const int ti = rank == 2 ? 1 : 0, tj = rank == 0 ? 0 : 1;
-    scale += (long)img * C;
-    Gint += (long)img * C * C;
-    Dsum += (long)img * kSlices * C;
-    const long p0 = (long)split * chunk, p1 = min(N, p0 + chunk);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    if (warp == 0) {
-        tc::tmem_alloc(tmem_slot, 512);
-        tc::tmem_relinquish();
-    }
-    if (tid == 0) {
-        tc::mbar_init(&full[0], consumer ? 1 : kThreads / 32);  // consumer: its own arrive + the copies' bytes
-        tc::mbar_init(&full[1], consumer ? 1 : kThreads / 32);
-        tc::mbar_init(&empty[0], 1);
-        tc::mbar_init(&empty[1], 1);
-        tc::mbar_init(acc_full, 1);
-        tc::mbar_init(drained, kThreads / 32);
-        tc::mbar_init(fin, 1);
-        tc::mbar_init(&peer_empty[0], 1);  // the consumer's multicast commit
-        tc::mbar_init(&peer_empty[1], 1);
-        *abort_flag = 0;
-        tc::fence_mbar_init();
-        if (consumer) {  // phase 0 of both buffers: two copies of kBlockBytes each
-            tc::mbar_arrive_expect_tx(&full[0], 2 * kBlockBytes);
-            tc::mbar_arrive_expect_tx(&full[1], 2 * kBlockBytes);
-        }
-    }
-    for (int i = tid; i < kSlices * kTB; i += kThreads) dsum[i] = 0;
-    for (int i = tid; i < kTB; i += kThreads) dsq[i] = 0ull;
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::cluster_sync_all();  // every CTA's barriers exist and are armed before any copy or remote arrive
-    tc::tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-
-    long long tot[32];
-#pragma unroll
-    for (int j = 0; j < 32; j++) tot[j] = 0;
-    const int q = warp & 3, cg4 = warp >> 2;
-    const int crow = tid >> 2;
-    const float sA = ti * kTB + crow < C ? scale[ti * kTB + crow] : 0.0f;
-    bool failed = false;
-    auto abort_all = [&] {
-        for (int r = 0; r < 3; r++) tc::st_cluster_u32(tc::mapa(tc::smem_u32((const void *)abort_flag), r), 1u);
-    };
-    auto bwait = [&](uint64_t *b, uint32_t parity) -> bool {
-        for (uint32_t n = 0; n < kWaitTries; n += 1u << 12) {
-            if (tc::mbar_wait(b, parity, 1u << 12)) return true;
-            if (*abort_flag) return false;
-        }
-        abort_all();
-        return false;
-    };
-    auto stage = [&](int st_, long q0) {
-        if (!consumer && q0 < p1) stage_block(X, layout, vec_ok, C, N, ti * kTB, q0, p1, stg + (size_t)st_ * 2 * kTB * kSub);
-        tc::cp_async_commit();
-    };
-    stage(0, p0);
-    stage(1, p0 + kSub);
-    int kk = 0, in_win = 0, win = 0;
-    for (long q0 = p0; q0 < p1; q0 += kSub, kk++) {
-        const int bsel = kk & 1;
-        if (*abort_flag) { failed = true; break; }
-        const bool first = in_win == 0;
-        in_win += kSub;
-        const bool win_end = in_win >= kWin || q0 + kSub >= p1;
-        if (!consumer) {
-            // the MMAs of sub-chunk kk-2 read this buffer here and, through the copy, at rank 1
-            if (kk >= 2 && (!bwait(&empty[bsel], ((kk - 2) >> 1) & 1) ||
-                            !bwait(&peer_empty[bsel], ((kk - 2) >> 1) & 1))) { failed = true; break; }
-            tc::cp_async_wait<1>();
-            float v[8];
-            read_stage(stg + (size_t)bsel * 2 * kTB * kSub, v);
-            convert_block(v, sA, As(bsel), dsum, dsq);
-            stage(bsel, q0 + 2 * kSub);
-            tc::fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive_cta(&full[bsel]);
-            if (tid == 0) {
-                bool ok = bwait(&full[bsel], (kk >> 1) & 1);
-                if (ok && first && win > 0) ok = bwait(drained, (win - 1) & 1);
-                if (ok) {
-                    tc::tc_fence_after();
-                    const uint32_t a_addr = tc::smem_u32(As(bsel));
-                    issue_level_mmas(tmem, a_addr, a_addr, first);
-                    tc::mma_commit(&empty[bsel]);
-                    if (win_end) tc::mma_commit(acc_full);
-                    // the converted block into rank 1's A (rank 0) or B (rank 2) buffer
-                    const uint32_t dst = tc::mapa(tc::smem_u32(rank == 0 ? As(bsel) : Bs(bsel)), 1);
-                    tc::bulk_copy_to_peer(dst, As(bsel), kBlockBytes, tc::mapa(tc::smem_u32(&full[bsel]), 1));
-                }
-            }
-            __syncwarp();
-        } else if (tid == 0) {
-            bool ok = true;
-            if (first && win > 0) ok = bwait(drained, (win - 1) & 1);
-            if (ok) ok = bwait(&full[bsel], (kk >> 1) & 1);
-            if (ok) {
-                tc::mbar_arrive_expect_tx(&full[bsel], 2 * kBlockBytes);  // the buffer's next phase
-                tc::tc_fence_after();
-                issue_level_mmas(tmem, tc::smem_u32(As(bsel)), tc::smem_u32(Bs(bsel)), first);
-                tc::mma_commit_multicast(&peer_empty[bsel], (uint16_t)0x5);  // ranks 0 and 2
-                if (win_end) tc::mma_commit(acc_full);
-            }
-        }
-        if (consumer) __syncwarp();
-        if (win_end) {
-            if (!bwait(acc_full, win & 1)) { failed = true; break; }
-            tc::tc_fence_after();
-#pragma unroll
-            for (int L = 0; L < 4; L++) {
-                uint32_t r0[16], r1[16];
-                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(L * kTB + 32 * cg4);
-                tc::tmem_ld16(ta, r0);
-                tc::tmem_ld16(ta + 16, r1);
-                tc::tmem_wait_ld();
-                const int sh = 7 * (4 - L);
-#pragma unroll
-                for (int jj = 0; jj < 16; jj++) {
-                    const int v0 = __float_as_int(__fadd_rn(__uint_as_float(r0[jj]), kMagic)) - 0x4B400000;
-                    const int v1 = __float_as_int(__fadd_rn(__uint_as_float(r1[jj]), kMagic)) - 0x4B400000;
-                    tot[jj] += (long long)v0 << sh;
-                    tot[16 + jj] += (long long)v1 << sh;
-                }
-            }
-            tc::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive_cta(drained);
-            win++;
-            in_win = 0;
-        }
-    }
-    // the producers' last two buffers: rank 1's MMAs done with them (its remote arrives have landed)
-    if (!consumer && !failed && tid == 0 && kk >= 1) {
-        for (int k2 = kk - 2 < 0 ? 0 : kk - 2; k2 < kk; k2++) bwait(&peer_empty[k2 & 1], (k2 >> 1) & 1);
-    }
-    __syncthreads();
-    failed = failed || *abort_flag;
-    if (failed) {
-        if (tid == 0) {
-            atomicOr(status, kStatusMmaTimeout);
-            tc::mma_commit(fin);
-            tc::mbar_wait(fin, 0, kWaitTries);
-        }
-    } else {
-        const int c1 = ti * kTB + 32 * q + lane;
-        if (c1 < C) {
-#pragma unroll
-            for (int jj = 0; jj < 32; jj++) {
-                const int c2 = tj * kTB + 32 * cg4 + jj;
-                if (c2 < C && tot[jj] != 0) atomicAdd(&Gint[(long)c1 * C + c2], (unsigned long long)tot[jj]);
-            }
-        }
-        __syncthreads();
-        if (!consumer) {
-            for (int i = tid; i < kSlices * kTB; i += kThreads) {
-                const int sl = i / kTB, row = i % kTB, c = ti * kTB + row;
-                if (c < C && dsum[i] != 0) atomicAdd(&Dsum[(long)sl * C + c], (unsigned long long)(long long)dsum[i]);
-            }
-            for (int row = tid; row < kTB; row += kThreads) {
-                const int c = ti * kTB + row;
-                if (c < C && dsq[row] != 0ull) atomicAdd(&Gint[(long)c * C + c], dsq[row]);
-            }
-        }
-    }
-    tc::cp_async_wait<0>();
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::cluster_sync_all();  // no CTA leaves while a peer may still copy or arrive into its shared memory
     if (warp == 0) {
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem, 512);
@@ -758,9 +556,7 @@ cudaError_t launch_gram_cov_jobs(const FitJob *jobs, int n, int layout, int C, d
     int dev = 0;
     cudaGetDevice(&dev);
     e = device_once(attrs, dev, [&] {
-        cudaError_t r = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-        if (r == cudaSuccess) r = cudaFuncSetAttribute(k_gram3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-        return r;
+        return cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     });
     if (e != cudaSuccess) return e;
     int n_sm = 0;
@@ -803,26 +599,7 @@ cudaError_t launch_gram_cov_jobs(const FitJob *jobs, int n, int layout, int C, d
         QFCA_LAUNCH("k_chan_absmax", st, k_chan_absmax<<<dim3(xb < 1 ? 1 : xb, C, m), 256, 0, st>>>(p, am));
         QFCA_LAUNCH("k_chan_scale", st,
                     k_chan_scale<<<(unsigned)((C * m + 127) / 128), 128, 0, st>>>(am, C * m, sc, exi));
-        if (g.nt == 2) {
-            // the three tile pairs of a pixel range as one cluster: each block converted once per pixel
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3((unsigned)cta);
-            cfg.blockDim = dim3(kThreads);
-            cfg.dynamicSmemBytes = g.smem;
-            cfg.stream = st;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = 3;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            cudaError_t el = cudaSuccess;
-            QFCA_LAUNCH("k_gram", st, el = cudaLaunchKernelEx(&cfg, k_gram3, p, (const float *)sc, Gi, Di, status));
-            if (el != cudaSuccess) return el;
-        } else {
-            QFCA_LAUNCH("k_gram", st, k_gram<<<(unsigned)cta, kThreads, g.smem, st>>>(p, sc, Gi, Di, status));
-        }
+        QFCA_LAUNCH("k_gram", st, k_gram<<<(unsigned)cta, kThreads, g.smem, st>>>(p, sc, Gi, Di, status));
         const long cc = (long)C * C;
         QFCA_LAUNCH("k_cov_finalize", st,
                     k_cov_finalize<<<dim3((unsigned)((cc + 255) / 256), m), 256, 2 * sizeof(double) * C, st>>>(
