@@ -51,7 +51,8 @@ constexpr int kTB = 128;         // channels per tile side
 constexpr int kSub = 32;         // pixels per sub-chunk (one 64-B swizzle row of BF16)
 constexpr int kSliceBytes = 128 * kSub * 2;  // one digit slice of a 128-channel block
 constexpr int kBlockBytes = 4 * kSliceBytes; // the four slices of one block
-constexpr int kStageBytes = 128 * kSub * 4;  // one block's FP32 features of a sub-chunk
+constexpr int kStageRow = kSub + 4;           // floats per staged channel row (padded: rows start 4 banks apart)
+constexpr int kStageBytes = 128 * kStageRow * 4;  // one block's FP32 features of a sub-chunk
 constexpr int kWin = 512;        // pixels per exact accumulation window (level sums <= 4 * 64 * 64 * 512 = 2^23)
 constexpr int kThreads = 512;
 constexpr int kSlices = 4;
@@ -152,7 +153,7 @@ __device__ __forceinline__ void stage_block(const float *__restrict__ X, int lay
     const int row = threadIdx.x >> 2, g = threadIdx.x & 3;
     const int c = c0 + row;
     const long p = q0 + g * 8;
-    float *dst = stage + row * kSub + g * 8;
+    float *dst = stage + row * kStageRow + g * 8;
     if (vec_ok && c < C && p + 8 <= q1) {
         const uint32_t d = tc::smem_u32(dst);
         tc::cp_async16(d, X + (long)c * N + p);
@@ -169,8 +170,8 @@ __device__ __forceinline__ void stage_block(const float *__restrict__ X, int lay
 // This thread's 8 values of a staged block (the ones it staged itself).
 __device__ __forceinline__ void read_stage(const float *stage, float (&v)[8]) {
     const int row = threadIdx.x >> 2, g = threadIdx.x & 3;
-    const float4 a = *reinterpret_cast<const float4 *>(stage + row * kSub + g * 8);
-    const float4 b = *reinterpret_cast<const float4 *>(stage + row * kSub + g * 8 + 4);
+    const float4 a = *reinterpret_cast<const float4 *>(stage + row * kStageRow + g * 8);
+    const float4 b = *reinterpret_cast<const float4 *>(stage + row * kStageRow + g * 8 + 4);
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
     v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
     // operand buffer b: A slices at smem + 2 b kBlockBytes, B slices right after (4 slices x 8 KB each)
     auto As = [&](int b) { return smem + 2 * b * kBlockBytes; };
     auto Bs = [&](int b) { return smem + (2 * b + 1) * kBlockBytes; };
-    float *stg = (float *)(smem + 4 * kBlockBytes);                 // [2 stages][2 blocks][128][32] FP32
+    float *stg = (float *)(smem + 4 * kBlockBytes);                 // [2 stages][2 blocks][128][kStageRow] FP32
     uint64_t *bar = (uint64_t *)(smem + 4 * kBlockBytes + 4 * kStageBytes);  // [7] mbarriers + the abort flag
     uint32_t *tmem_slot = (uint32_t *)(bar + 8);
     unsigned long long *dsq = (unsigned long long *)(tmem_slot + 2);  // [128] (8-B aligned)
@@ -329,10 +330,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
 
     // features stream into two FP32 stages, two sub-chunks ahead of the conversion
     auto stage = [&](int s, long q0) {
-        float *sa = stg + (size_t)s * 2 * kTB * kSub;
+        float *sa = stg + (size_t)s * 2 * kTB * kStageRow;
         if (q0 < p1) {
             stage_block(X, layout, vec_ok, C, N, ti * kTB, q0, p1, sa);
-            if (!diag) stage_block(X, layout, vec_ok, C, N, tj * kTB, q0, p1, sa + kTB * kSub);
+            if (!diag) stage_block(X, layout, vec_ok, C, N, tj * kTB, q0, p1, sa + kTB * kStageRow);
         }
         tc::cp_async_commit();  // one group per sub-chunk (possibly empty)
     };
@@ -345,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
         tc::cp_async_wait<1>();  // this thread's copies of sub-chunk kk have landed (kk+1 may be in flight)
         // the A block is converted into registers while the MMAs of sub-chunk kk-2 may
         // still read the buffer (the registers of a second block would spill)
-        const float *sa = stg + (size_t)bsel * 2 * kTB * kSub;
+        const float *sa = stg + (size_t)bsel * 2 * kTB * kStageRow;
         uint4 pk[kSlices];
         {
             float v[8];
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
         store_block(pk, As(bsel));
         if (!diag) {
             float v[8];
-            read_stage(sa + kTB * kSub, v);
+            read_stage(sa + kTB * kStageRow, v);
             convert_block(v, sB, pk, nullptr, nullptr);
             store_block(pk, Bs(bsel));
         }

@@ -120,6 +120,11 @@ struct ProjJob {
     uint32_t *mm;
     const float *scale = nullptr;
     const float *colscale = nullptr;
+    // Fixed-range quantisation in the epilogue (bins given): bins [d][N / W][pitch] with
+    // quant_bin(y, qlo[k], qhi[k], B) instead of Y and the min/max keys.
+    const float *qlo = nullptr, *qhi = nullptr;
+    uint8_t *bins = nullptr;
+    int W = 0, pitch = 0, B = 0;
 };
 bool project_tma_ok(const float *X, long N, int layout);
 size_t project_bf16_workspace_bytes(int C, long N, int d, int nimg);
@@ -308,6 +313,20 @@ __host__ __device__ inline float key2f(uint32_t k) {
 }
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// The bin of value y among B equally spaced bins between lo and hi (Sec. 3.1),
+// decided in FP32 with IEEE-rounded operations in a fixed order:
+//     t = (y - lo) / (hi - lo);  v = t * B;  q = clamp((int)v, 0, B-1);  hi == lo gives 0.
+// Every kernel that quantises uses this function, so their bins agree bit for bit.
+#ifdef __CUDACC__
+__device__ __forceinline__ int quant_bin(float y, float lo, float hi, float fB, int B) {
+    if (!(hi > lo)) return 0;
+    const float t = __fdiv_rn(__fsub_rn(y, lo), __fsub_rn(hi, lo));
+    const float v = __fmul_rn(t, fB);
+    int q = v < 0.0f ? 0 : (int)v;
+    return q > B - 1 ? B - 1 : q;
+}
+#endif
 
 // ------------------------------------------------------------------ launch hook (tracing)
 

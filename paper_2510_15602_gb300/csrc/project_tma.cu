@@ -60,6 +60,9 @@ struct ProjImgP {
     const float *colscale;          // FP8: per-component power-of-two 1/t_j [DT]
     float *Y;                       // [d][N]
     uint32_t *mm;                   // [2 d kKeyStride]
+    const float *qlo, *qhi;         // fixed range [d] when the epilogue quantises (bins != NULL)
+    uint8_t *bins;                  // [d][N / W][pitch] or NULL
+    int W, pitch, B;
 };
 
 struct ProjParams {
@@ -406,6 +409,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
             tc::tc_fence_after();
             const long pe = (w - im.tile0) * kM + 32 * quarter + lane;
             const bool valid = pe < im.N;
+            if (im.bins) {
+                // fixed range: the bins straight from the accumulator (no Y, no range keys)
+                const long py = valid ? pe / im.W : 0, px = valid ? pe - py * im.W : 0;
+                const long H = im.N / im.W;
+                const float fB = (float)im.B;
+#pragma unroll
+                for (int g = 0; g < NG; g++) {
+                    uint32_t r[16];
+                    tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(ac * DT + 16 * g), r);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        const int j = 16 * g + i;
+                        if (j < d && valid) {
+                            const float v = F8 ? __uint_as_float(r[i]) * __ldg(im.colscale + j) : __uint_as_float(r[i]);
+                            const int q = quant_bin(v, __ldg(im.qlo + j), __ldg(im.qhi + j), fB, im.B);
+                            im.bins[((long)j * H + py) * im.pitch + px] = (uint8_t)q;
+                        }
+                    }
+                }
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[ac]);
+                continue;
+            }
 #pragma unroll
             for (int g = 0; g < NG; g++) {
                 uint32_t r[16];
@@ -509,6 +537,9 @@ cudaError_t launch_project_tma(const ProjJob *jobs, int n, int C, int d, bool fp
             ProjImgP &im = p.img[i];
             im.N = j.N, im.tile0 = tiles, im.mean32 = j.mean32, im.Vt = j.Vt, im.scale = j.scale;
             im.colscale = j.colscale, im.Y = j.Y, im.mm = j.mm;
+            im.qlo = j.qlo, im.qhi = j.qhi, im.bins = j.bins, im.W = j.W, im.pitch = j.pitch, im.B = j.B;
+            if (j.bins && (!j.qlo || !j.qhi || j.W < 1 || j.N % j.W != 0 || j.pitch < j.W || j.B < 2))
+                return cudaErrorInvalidValue;
             tiles += (j.N + kM - 1) / kM;
             cudaError_t e = make_tmap_f32_2d(&p.tmap[i], j.X, (uint64_t)j.N, (uint64_t)C, (uint64_t)j.N * 4, kM, kKc);
             if (e != cudaSuccess) return e;

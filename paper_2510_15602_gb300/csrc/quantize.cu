@@ -18,14 +18,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kRowsPerCta = 8;
 
-__device__ __forceinline__ int bin_of(float y, float lo, float hi, float fB, int B) {
-    if (!(hi > lo)) return 0;
-    const float t = __fdiv_rn(__fsub_rn(y, lo), __fsub_rn(hi, lo));
-    const float v = __fmul_rn(t, fB);
-    int q = v < 0.0f ? 0 : (int)v;
-    return q > B - 1 ? B - 1 : q;
-}
-
 struct QuantImgP {
     const float *Y;           // [d][N]
     int H, W;
@@ -75,7 +67,7 @@ __global__ void __launch_bounds__(kThreads) k_quantize(const __grid_constant__ Q
     const int y1 = min(H, y0 + kRowsPerCta);
     for (int yy = y0; yy < y1; yy++) {
         for (int x = threadIdx.x; x < W; x += kThreads) {
-            const int q = bin_of(yk[(long)yy * W + x], lo, hi, fB, B);
+            const int q = quant_bin(yk[(long)yy * W + x], lo, hi, fB, B);
             bk[(long)yy * im.pitch + x] = (uint8_t)q;
             if (im.hist) atomicAdd(&sh[q], 1u);
         }

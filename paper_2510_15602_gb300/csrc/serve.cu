@@ -183,11 +183,14 @@ cudaError_t launch_batch(ServeState *S, Batch *b) {
     for (int i = 0; i < n && tma; i++) tma = project_tma_ok(X[i], (long)b->reqs[i].req.H * b->reqs[i].req.W, QFCA_NCHW);
     if (tma) {
         e = launch_init_keys(keys, c.d, n, st);
+        // the class's fixed range is known, so the projection's epilogue writes the bins itself
         std::vector<ProjJob> pj(n);
         for (int i = 0; i < n; i++) {
             const ClassRec &cl = *b->reqs[i].cls;
-            pj[i] = ProjJob{X[i], (long)b->reqs[i].req.H * b->reqs[i].req.W, cl.mean32, cl.Vt, Y[i],
-                            keys + (size_t)i * 2 * c.d * kKeyStride};
+            const qfca_request &r = b->reqs[i].req;
+            pj[i] = ProjJob{X[i], (long)r.H * r.W, cl.mean32, cl.Vt, Y[i], keys + (size_t)i * 2 * c.d * kKeyStride};
+            pj[i].qlo = cl.lo, pj[i].qhi = cl.hi, pj[i].bins = bins[i];
+            pj[i].W = r.W, pj[i].pitch = pitch_of(r.W), pj[i].B = c.B;
         }
         if (e == cudaSuccess) e = launch_project_tma(pj.data(), n, c.C, c.d, false, S->status_dev, st);
     } else {
@@ -199,15 +202,17 @@ cudaError_t launch_batch(ServeState *S, Batch *b) {
         }
     }
     if (e != cudaSuccess) return e;
-    // quantisation with the class's fixed range; the class histogram is the reference
-    std::vector<QuantJob> qj(n);
-    for (int i = 0; i < n; i++) {
-        const qfca_request &r = b->reqs[i].req;
-        const ClassRec &cl = *b->reqs[i].cls;
-        qj[i] = QuantJob{Y[i], r.H, r.W, nullptr, cl.lo, cl.hi, bins[i], pitch_of(r.W), nullptr, nullptr, nullptr};
+    if (!tma) {
+        // quantisation with the class's fixed range; the class histogram is the reference
+        std::vector<QuantJob> qj(n);
+        for (int i = 0; i < n; i++) {
+            const qfca_request &r = b->reqs[i].req;
+            const ClassRec &cl = *b->reqs[i].cls;
+            qj[i] = QuantJob{Y[i], r.H, r.W, nullptr, cl.lo, cl.hi, bins[i], pitch_of(r.W), nullptr, nullptr, nullptr};
+        }
+        e = launch_quantize_jobs(qj.data(), n, c.d, c.B, false, st);
+        if (e != cudaSuccess) return e;
     }
-    e = launch_quantize_jobs(qj.data(), n, c.d, c.B, false, st);
-    if (e != cudaSuccess) return e;
     char *score_ws = base + o;
     e = launch_score_jobs(sj.data(), n, c.d, c.B, score_ws, false, S->status_dev, st, nullptr, nullptr);
     if (e != cudaSuccess) return e;
