@@ -271,6 +271,11 @@ def kernel_work(name: str, H: int, W: int, C: int, d: int, B: int, r: int, nimg:
         return {"bound": "tensor", "unit": "TFLOP/s", "work": nimg * N * (nt * (nt + 1) // 2) * 10 * 2 * 128 * 128,
                 "peak_key": "bf16_sustained",
                 "per_unit": "10 x 2 x 128^2 BF16 flop per pixel per channel-tile pair (exact digit products)"}
+    if name.startswith("k_eig32"):
+        return {"bound": "alu", "unit": "TFLOP/s", "work": nimg * int(4 * C ** 3 / 3 + 2 * C * C * d),
+                "peak_key": "fp32_tflops",
+                "per_unit": "4C^3/3 (Householder tridiagonalisation) + 2C^2 d (back-transform) FP32 flop per image; "
+                            "the float-float Newton correction of the d vectors is not counted"}
     if name.startswith("k_eig"):
         return {"bound": "alu", "unit": "TFLOP/s", "work": nimg * int(4 * C ** 3 / 3 + 2 * C * C * d),
                 "peak_key": "ff_tflops",
@@ -375,8 +380,6 @@ def per_kind_auroc(scores, masks, kind_masks, border: int) -> dict:
 # captures summarised in profiles/<kernel>_batch16_256_c256.md; an entry is
 # removed whenever its kernel changes after the capture.
 NCU_TRAFFIC = {
-    "k_eig_ff": 4851456,
-    "k_gram": 1108133000 + 18952192,
     "k_assoc": 35393280 + 78018560,
     "k_median_ref": 43135744,
     "k_residual": 2147958000 + 1031120000,

@@ -8,9 +8,11 @@
 //      triangle packed by columns in shared memory (column j contiguous).  One
 //      pass over the trailing block per step, warp per column: the rank-2
 //      update of reflector k and, on the updated entries, the symmetric product
-//      with reflector k+1 (formed first from column k+1, updated alone); the
-//      row contributions go to per-warp partial vectors, summed in a fixed
-//      order.  Reflector k stays in column k (contiguous) for the later passes.
+//      with reflector k+1 (formed first, in place, from column k+1, updated
+//      alone); each lane keeps the next reflector and the row sums of its rows
+//      in registers, and the row and column partial sums are added in a fixed
+//      order.  Three CTA barriers per step.  Reflector k stays in column k
+//      (contiguous) for the later passes.
 //   2. The top d eigenvalues sigma_j of T by warp multisection on the FP32
 //      Sturm count; eigenvectors z_j of T by two steps of inverse iteration
 //      (Gaussian elimination with partial pivoting, one lane per eigenvector);
@@ -18,9 +20,11 @@
 //   3. Newton correction per column (x, sigma approximate; A x = lambda x):
 //      r = A x - sigma x with A in float-float (exact FP32 products, compensated
 //      sums), u = Q^T r, u -= (z.u) z, solve (T - sigma I) y = u (the same
-//      pivoted elimination), y -= (z.y) z, x' = x - Q y carried as (x, -Q y).
-//      One step squares the FP32 start's error: about 1e-12 of lambda_1/gap.
-//   4. lambda_j = x'^T A x' / x'^T x' (float-float), the residual
+//      pivoted elimination), y -= (z.y) z, x' = x - Q y carried as an unevaluated
+//      pair.  One step squares the FP32 start's error: about 1e-12 of lambda_1/gap.
+//   4. A x' = A x - A (Q y): A x in float-float from the residual, A (Q y) in
+//      FP32 (the correction is small, so its rounding is far below the
+//      tolerance); lambda_j = x'^T A x' / x'^T x' (float-float), the residual
 //      |A x' - lambda x'| / |x'| of every column; a matrix whose residual
 //      exceeds tol * |lambda_max| is flagged for the float-float solver (eig.cu)
 //      instead.  Normalisation, sign (largest-magnitude entry positive, first on
@@ -38,6 +42,13 @@ namespace {
 using ffa::ff;
 constexpr int kT = 1024;
 constexpr int kNW = kT / 32;
+template <bool B>
+struct BoolC {
+    static constexpr bool value = B;
+};
+constexpr BoolC<true> kTrue{};
+constexpr BoolC<false> kFalse{};
+constexpr int kQ = 8;    // rows per lane in a tridiagonalisation pass (n <= 256)
 constexpr int kXS = 33;  // row stride of the n x d panels (conflict-free by rows and by columns)
 
 struct Eig32Args {
@@ -45,6 +56,7 @@ struct Eig32Args {
     int n, d;
     float *scr;         // [mats][3][n][32] U factor of the pivoted elimination (one column per lane)
     float *Z;           // [mats][n][32] eigenvectors of T
+    float2 *W;          // [mats][n][32] A x in float-float (hi, lo), from the Newton residual pass
     double *V;          // [mats][n][d]
     double *eig;        // [mats][d]
     int *flag;          // [mats] 1: residual check failed, the float-float solver redoes the matrix
@@ -65,7 +77,7 @@ struct Smem32 {
 __host__ __device__ inline int up4(int v) { return (v + 3) & ~3; }
 __host__ __device__ inline Smem32 smem32_plan(int n) {
     Smem32 s;
-    const int apsz = up4(poff(n)) > 2 * n * kXS ? up4(poff(n)) : 2 * n * kXS;
+    const int apsz = up4(poff(n) > 2 * n * kXS ? poff(n) : 2 * n * kXS);
     s.ap = 0;
     s.x = apsz;
     s.u = s.x + up4(n * kXS);
@@ -85,25 +97,46 @@ __device__ __forceinline__ float warp_sum_f(float s) {
     return s;
 }
 
-// Sum over the block, the same value in every thread (fixed order).
-__device__ __forceinline__ float block_sum_f(float s, float *red) {
-    s = warp_sum_f(s);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    float t = 0.0f;
+// Column c of an [n][kXS] panel in the registers of one warp: lane l holds rows l + 32 q.
+__device__ __forceinline__ void col_load(const float *p, int n, int lane, float (&r)[kQ]) {
 #pragma unroll
-    for (int w = 0; w < kNW; w++) t += red[w];
-    return t;
+    for (int q = 0; q < kQ; q++) {
+        const int i = lane + 32 * q;
+        r[q] = i < n ? p[(size_t)i * kXS] : 0.0f;
+    }
+}
+__device__ __forceinline__ void col_store(float *p, int n, int lane, const float (&r)[kQ]) {
+#pragma unroll
+    for (int q = 0; q < kQ; q++) {
+        const int i = lane + 32 * q;
+        if (i < n) p[(size_t)i * kXS] = r[q];
+    }
+}
+// r <- (I - tau v v^T) r for the reflector v stored in rows m0..n-1 of vk (vk[i], i >= m0).
+__device__ __forceinline__ void reflect(float (&r)[kQ], const float *vk, float tau, int m0, int n, int lane) {
+    float v[kQ], s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kQ; q++) {
+        const int i = lane + 32 * q;
+        v[q] = 0.0f;
+        if (32 * q + 31 >= m0 && i >= m0 && i < n) v[q] = vk[i];
+        s = fmaf(v[q], r[q], s);
+    }
+    s = tau * warp_sum_f(s);
+#pragma unroll
+    for (int q = 0; q < kQ; q++) r[q] = fmaf(-s, v[q], r[q]);
 }
 
+// Number of eigenvalues of T below x (the signs of the LDL^T pivots of T - x I).
+// The approximate division (2 ulp) only perturbs pivots that are not near zero, and
+// a count off by one near an eigenvalue moves that bisection by one FP32 step.
 __device__ int sturm32(const float *dg, const float *e2, int n, float x) {
     int cnt = 0;
     float q = dg[0] - x;
     if (fabsf(q) < 1e-30f) q = -1e-30f;
     cnt += q < 0.0f;
     for (int i = 1; i < n; i++) {
-        q = (dg[i] - x) - e2[i - 1] / q;
+        q = (dg[i] - x) - __fdividef(e2[i - 1], q);
         if (fabsf(q) < 1e-30f) q = -1e-30f;
         cnt += q < 0.0f;
     }
@@ -129,7 +162,7 @@ __device__ void tri_solve_piv(const float *dg, const float *ed, int n, float sig
             p0 = s0, p1 = s1, p2 = s2, pb = sb, q0 = r0, q1 = r1, q2 = r2, qb = rb;
         }
         if (fabsf(p0) < tiny) p0 = p0 < 0.0f ? -tiny : tiny;
-        const float l = q0 / p0;
+        const float l = __fdividef(q0, p0);  // |l| <= 1 except at replaced pivots
         u0[(size_t)i * 32 + j] = p0;
         u1[(size_t)i * 32 + j] = p1;
         u2[(size_t)i * 32 + j] = p2;
@@ -145,8 +178,8 @@ __device__ void tri_solve_piv(const float *dg, const float *ed, int n, float sig
     float y2 = 0.0f, y1 = rb / r0;
     b[(size_t)(n - 1) * kXS] = y1;
     for (int i = n - 2; i >= 0; i--) {
-        const float y0 = (b[(size_t)i * kXS] - u1[(size_t)i * 32 + j] * y1 - u2[(size_t)i * 32 + j] * y2) /
-                         u0[(size_t)i * 32 + j];
+        const float y0 = __fdividef(b[(size_t)i * kXS] - u1[(size_t)i * 32 + j] * y1 - u2[(size_t)i * 32 + j] * y2,
+                                    u0[(size_t)i * 32 + j]);
         b[(size_t)i * kXS] = y0;
         y2 = y1;
         y1 = y0;
@@ -175,6 +208,7 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
     const float2 *A = a.cov + (size_t)mat * n * n;
     float *scr = a.scr + (size_t)mat * 3 * n * 32;
     float *Zg = a.Z + (size_t)mat * n * 32;
+    float2 *Wg = a.W + (size_t)mat * n * 32;
 
     // ---------------------------------------------------------------- 0. load hi parts (column j = row j)
     for (int jc = warp; jc < n; jc += kNW) {
@@ -184,113 +218,180 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
     __syncthreads();
 
     // ---------------------------------------------------------------- 1. tridiagonalisation (FP32)
-    // vcur: the current reflector v_k, vn: the next one (the two swap every step), pv: the
-    // product of the trailing block with v_k (unscaled), wv: w_k
-    float *vcur = vs, *pv = ps;
-    float *wv = X, *vn = X + n4;  // the X panel is free until the eigenvectors
-    float *pw = U;                // [kNW][n] per-warp partial products (the U panel likewise)
-    // reflector of column c (rows c+1..n-1) into dst; returns tau (0: nothing to reduce)
-    auto make_reflector = [&](int c, float *dst) -> float {
-        const float *col = Ap + coff(c, n) - c;
-        float part = 0.0f;
-        for (int i = c + 2 + tid; i < n; i += kT) part = fmaf(col[i], col[i], part);
-        const float sig = block_sum_f(part, red);
-        const float x1 = col[c + 1];
-        float alpha = x1, tau = 0.0f, v1 = 0.0f;
-        if (sig > 0.0f) {
-            const float nn = fmaf(x1, x1, sig);
-            const float nrm = sqrtf(nn);
-            alpha = x1 >= 0.0f ? -nrm : nrm;
-            v1 = x1 - alpha;
-            tau = 1.0f / (nn - alpha * x1);
-        }
-        if (tid == 0) {
-            eT[c] = alpha;
-            tauv[c] = tau;
-            v1s[c] = v1;
-        }
-        for (int i = c + 1 + tid; i < n; i += kT) dst[i] = i == c + 1 ? v1 : col[i];
-        return tau;
+    // Reflector k is formed in place in column k of the packed triangle (rows k+1..n-1; its
+    // first entry v1 replaces the sub-diagonal entry, which goes to eT as alpha) and stays
+    // there for the later passes.  pv: the product of the trailing block with the current
+    // reflector (unscaled); wv: w_k; pw: per-warp row partials [kNW][n+1]; dp: per-lane
+    // column partials [n][32].  Three CTA barriers per step.
+    float *pv = ps;
+    float *wv = X, *dp = X + n4;  // the X panel is free until the eigenvectors
+    float *pw = U;                // the U panel likewise
+    const int pws = n + 1;        // row stride of pw (the four threads of a row hit four banks)
+    float *red2 = red + 32;
+    auto colp = [&](int c) { return Ap + coff(c, n) - c; };  // colp(c)[i] = A(i, c), i >= c
+    // alpha, tau and first entry v1 of the reflector that maps (x1, rest) to (alpha, 0),
+    // sig = |rest|^2; every thread computes the same values
+    auto reflector = [](float x1, float sig, float &alpha, float &v1) -> float {
+        alpha = x1;
+        v1 = 0.0f;
+        if (!(sig > 0.0f)) return 0.0f;
+        const float nn = fmaf(x1, x1, sig);
+        const float nrm = sqrtf(nn);
+        alpha = x1 >= 0.0f ? -nrm : nrm;
+        v1 = x1 - alpha;
+        return 1.0f / (nn - alpha * x1);
     };
-    // one pass over the columns j0..n-1 of the trailing block: with `upd`, the rank-2
-    // update A -= v w^T + w v^T of the current reflector; with `acc`, pv = A vn on the
-    // updated entries (column part by warp sums, row part into the warp's partial vector)
-    auto fused_pass = [&](int j0, bool upd, bool acc) {
-        if (acc) {
-            for (int e = tid; e < kNW * n; e += kT) pw[e] = 0.0f;
-            __syncthreads();
+    // One pass over columns j0..n-1 of the trailing block, warp per column (columns
+    // j0 + warp + 32 s): with `upd`, the rank-2 update A -= v w^T + w v^T of the current
+    // reflector (vc, wv); with `acc`, the product with the next reflector's column vnp as
+    // stored (rows >= j0; its first entry is corrected in reduce_pass) on the updated
+    // entries.  Lane l of a warp meets only rows i_q = j0 + warp + l + 32 q (q >= s in
+    // column s), so the column's entries and the row sums of those rows stay in
+    // registers; the row sums go to pw[warp], each lane's column dot to dp.
+    auto fused_pass = [&](auto upd_c, auto acc_c, int j0, const float *vc, const float *vnp) {
+        constexpr bool UPD = decltype(upd_c)::value, ACC = decltype(acc_c)::value;
+        const int rb = j0 + warp + lane;
+        const int S = n - j0 - warp > 0 ? (n - j0 - warp + 31) >> 5 : 0;  // columns of this warp
+        float vq[kQ], pr[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; q++) {
+            const int i = rb + 32 * q;
+            vq[q] = ACC && i < n ? vnp[i] : 0.0f;
+            pr[q] = 0.0f;
         }
-        float *pwr = pw + (size_t)warp * n;
-        for (int jc = j0 + warp; jc < n; jc += kNW) {
-            float *col = Ap + coff(jc, n) - jc;
-            const float vj = vcur[jc], wj = upd ? wv[jc] : 0.0f, vnj = acc ? vn[jc] : 0.0f;
-            float dot = 0.0f;
-            for (int i = jc + lane; i < n; i += 32) {
-                float a = col[i];
-                if (upd) {
-                    a = fmaf(-vcur[i], wj, fmaf(-wv[i], vj, a));
-                    col[i] = a;
+#pragma unroll
+        for (int s = 0; s < kQ; s++) {
+            if (s < S) {
+                const int jc = j0 + warp + 32 * s;
+                float *col = colp(jc);
+                const float vj = UPD ? vc[jc] : 0.0f, wj = UPD ? wv[jc] : 0.0f;
+                const float vnj = ACC ? vnp[jc] : 0.0f;
+                float dot = 0.0f;
+#pragma unroll
+                for (int q = s; q < kQ; q++) {
+                    const int i = rb + 32 * q;
+                    if (i < n) {
+                        float a = col[i];
+                        if (UPD) {
+                            a = fmaf(-vc[i], wj, fmaf(-wv[i], vj, a));
+                            col[i] = a;
+                        }
+                        if (ACC) {
+                            dot = fmaf(a, vq[q], dot);
+                            if (q > s || lane > 0) pr[q] = fmaf(a, vnj, pr[q]);  // below the diagonal
+                        }
+                    }
                 }
-                if (acc) {
-                    dot = fmaf(a, vn[i], dot);
-                    if (i > jc) pwr[i] = fmaf(a, vnj, pwr[i]);  // row i is always this lane's
-                }
-            }
-            if (acc) {
-                dot = warp_sum_f(dot);
-                if (lane == 0) pwr[jc] += dot;
+                if (ACC) dp[(jc - j0) * 32 + lane] = dot;
             }
         }
-        __syncthreads();
-        if (acc) {
-            for (int i = j0 + tid; i < n; i += kT) {
-                float t = 0.0f;
-#pragma unroll 8
-                for (int w = 0; w < kNW; w++) t += pw[(size_t)w * n + i];
-                pv[i] = t;
+        if (ACC) {
+#pragma unroll
+            for (int q = 0; q < kQ; q++) {
+                const int i = rb + 32 * q;
+                if (i < n) pw[warp * pws + i] = pr[q];
             }
-            __syncthreads();
         }
     };
+    // pv[i] (i >= j0): the row partials of warps 0..i-j0 (the only warps that reach row i)
+    // plus the 32 lane partials of column i, four threads per row, fixed order, plus
+    // dv A(i, j0) (dv = v1 - x1: the reflector's first entry in place of the stored one);
+    // the products pv_i vn_i summed per warp into red (the next step's K)
+    auto reduce_pass = [&](int j0, const float *vnp, float v1n, float dv) {
+        if (j0 + (warp << 3) >= n) {  // no row of this warp
+            if (lane == 0) red[warp] = 0.0f;
+            return;
+        }
+        const int i = j0 + (tid >> 2), part = tid & 3;
+        float t = 0.0f, kp = 0.0f;
+        if (i < n) {
+            const int wmax = min(kNW - 1, i - j0);
+            for (int w = part; w <= wmax; w += 4) t += pw[w * pws + i];
+            const float4 *c = reinterpret_cast<const float4 *>(dp + (i - j0) * 32 + part * 8);
+            const float4 c0 = c[0], c1 = c[1];
+            t += ((c0.x + c0.y) + (c0.z + c0.w)) + ((c1.x + c1.y) + (c1.z + c1.w));
+        }
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        if (i < n && part == 0) {
+            t = fmaf(dv, colp(j0)[i], t);
+            pv[i] = t;
+            kp = t * (i == j0 ? v1n : vnp[i]);
+        }
+        kp = warp_sum_f(kp);
+        if (lane == 0) red[warp] = kp;
+    };
+    float *bc = vs;  // reflector k+1 for all warps: v1, tau, the stored first entry x1
     if (tid == 0) {
         for (int i = n - 2 < 0 ? 0 : n - 2; i < n; i++) eT[i] = 0.0f, tauv[i] = 0.0f;
     }
-    // reflector 0 (into vn) and its product with the untouched trailing block; then it becomes current
-    float tau_cur = n >= 3 ? make_reflector(0, vn) : 0.0f;
-    __syncthreads();
-    if (tau_cur != 0.0f) fused_pass(1, false, true);
-    if (n >= 3 && tid == 0) Ap[coff(0, n) + 1] = v1s[0];  // column 0 now holds reflector 0
-    {
-        float *t = vcur;
-        vcur = vn;
-        vn = t;
+    // reflector 0 and its product with the untouched trailing block
+    float tau_cur = 0.0f;
+    if (n >= 3) {
+        const float *c0 = colp(0);
+        float sq = 0.0f;
+        for (int i = 2 + tid; i < n; i += kT) sq = fmaf(c0[i], c0[i], sq);
+        sq = warp_sum_f(sq);
+        if (lane == 0) red2[warp] = sq;
+        __syncthreads();
+        float alpha, v1;
+        const float x1 = c0[1];
+        tau_cur = reflector(x1, warp_sum_f(red2[lane]), alpha, v1);
+        if (tid == 0) eT[0] = alpha, tauv[0] = tau_cur, v1s[0] = v1;
+        if (tau_cur != 0.0f) fused_pass(kFalse, kTrue, 1, nullptr, c0);
+        __syncthreads();
+        if (tau_cur != 0.0f) reduce_pass(1, c0, v1, v1 - x1);
+        if (tid == 0) Ap[1] = v1;  // column 0 now holds reflector 0
+        __syncthreads();
     }
-    __syncthreads();
     for (int k = 0; k + 2 < n; k++) {
-        if (tid == 0) dT[k] = Ap[coff(k, n)];
         const int m0 = k + 1;
-        if (tau_cur != 0.0f) {
-            // p = tau A v, K = (tau / 2) p.v, w = p - K v
-            float part = 0.0f;
-            for (int i = m0 + tid; i < n; i += kT) part = fmaf(pv[i], vcur[i], part);
-            const float K = 0.5f * tau_cur * tau_cur * block_sum_f(part, red);
-            for (int i = m0 + tid; i < n; i += kT) wv[i] = fmaf(-K, vcur[i], tau_cur * pv[i]);
-            __syncthreads();
-            // column k+1 alone first: reflector k+1 is formed from it
-            float *col = Ap + coff(m0, n) - m0;
-            const float vj = vcur[m0], wj = wv[m0];
-            for (int i = m0 + tid; i < n; i += kT) col[i] = fmaf(-vcur[i], wj, fmaf(-wv[i], vj, col[i]));
-            __syncthreads();
-        }
+        const float *vc = colp(k);  // reflector k
+        float *cm = colp(m0);
         const bool has_next = k + 3 < n;
-        const float tau_next = has_next ? make_reflector(m0, vn) : 0.0f;
-        if (has_next) __syncthreads();
-        if (tau_cur != 0.0f || tau_next != 0.0f) fused_pass(k + 2, tau_cur != 0.0f, tau_next != 0.0f);
-        if (has_next && tid == 0) Ap[coff(m0, n) + 1] = v1s[m0];  // column k+1 now holds reflector k+1
-        // reflector k+1 becomes the current one
-        float *t = vcur;
-        vcur = vn;
-        vn = t;
+        // w = tau p - K v (K = tau^2/2 p.v, partial sums in red) for the rows of this
+        // thread, the update of column k+1 by reflector k, and the squares of its entries
+        // below the first sub-diagonal (reflector k+1); warps without rows skip it
+        float sq = 0.0f;
+        if (m0 + (warp << 5) < n) {
+            if (tau_cur != 0.0f) {
+                const float K = 0.5f * tau_cur * tau_cur * warp_sum_f(red[lane]);
+                const float vj = vc[m0], wj = fmaf(-K, vj, tau_cur * pv[m0]);
+                const int i = m0 + tid;
+                if (i < n) {
+                    const float vi = vc[i], wi = fmaf(-K, vi, tau_cur * pv[i]);
+                    wv[i] = wi;
+                    const float c = fmaf(-vi, wj, fmaf(-wi, vj, cm[i]));
+                    cm[i] = c;
+                    if (i >= m0 + 2) sq = fmaf(c, c, sq);
+                }
+            } else {
+                const int i = m0 + 2 + tid;
+                if (i < n) sq = cm[i] * cm[i];
+            }
+            sq = warp_sum_f(sq);
+        }
+        if (lane == 0) red2[warp] = sq;
+        __syncthreads();
+        // the last warp (the fewest pass entries) forms reflector k+1 while the others
+        // start the pass with the column as stored
+        if (warp == kNW - 1 && has_next) {
+            float alpha, v1;
+            const float x1 = cm[m0 + 1];
+            const float t = reflector(x1, warp_sum_f(red2[lane]), alpha, v1);
+            if (lane == 0) {
+                eT[m0] = alpha, tauv[m0] = t, v1s[m0] = v1;
+                bc[0] = v1, bc[1] = t, bc[2] = x1;
+            }
+        }
+        if (tid == 0) dT[k] = vc[k];
+        if (tau_cur != 0.0f && has_next) fused_pass(kTrue, kTrue, k + 2, vc, cm);
+        else if (tau_cur != 0.0f) fused_pass(kTrue, kFalse, k + 2, vc, cm);
+        else if (has_next) fused_pass(kFalse, kTrue, k + 2, vc, cm);
+        __syncthreads();
+        const float tau_next = has_next ? bc[1] : 0.0f;
+        if (tau_next != 0.0f) reduce_pass(k + 2, cm, bc[0], bc[0] - bc[2]);
+        if (has_next && tid == 0) cm[m0 + 1] = bc[0];  // column k+1 now holds reflector k+1
         tau_cur = tau_next;
         __syncthreads();
     }
@@ -383,19 +484,15 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
         }
     }
     __syncthreads();
-    // back-transformation x_j = H_0 ... H_{n-3} z_j, warp per column
+    // back-transformation x_j = H_0 ... H_{n-3} z_j, warp per column (held in registers)
     if (warp < d) {
-        float *x = X + warp;
+        float xr[kQ];
+        col_load(X + warp, n, lane, xr);
         for (int k = n - 3; k >= 0; k--) {
             const float tau = tauv[k];
-            if (tau == 0.0f) continue;
-            const int m0 = k + 1;
-            float s = 0.0f;
-            const float *vk = Ap + coff(k, n) - k;  // reflector k: vk[i], i = k+1..n-1
-            for (int i = m0 + lane; i < n; i += 32) s = fmaf(vk[i], x[(size_t)i * kXS], s);
-            s = tau * warp_sum_f(s);
-            for (int i = m0 + lane; i < n; i += 32) x[(size_t)i * kXS] = fmaf(-s, vk[i], x[(size_t)i * kXS]);
+            if (tau != 0.0f) reflect(xr, Ap + coff(k, n) - k, tau, k + 1, n, lane);  // reflector k: rows k+1..n-1
         }
+        col_store(X + warp, n, lane, xr);
     }
     __syncthreads();
 
@@ -415,6 +512,8 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
                 S = t.hi;
                 Cc = __fadd_rn(Cc, __fadd_rn(t.lo, e));
             }
+            const ff w = ffa::two_sum(S, Cc);  // A x, kept for the Rayleigh quotient
+            Wg[(size_t)i * 32 + lane] = make_float2(w.hi, w.lo);
             // minus sigma x (the product exact as a pair)
             const float xi = X[(size_t)i * kXS + lane], sg = lamv[lane];
             const float p = __fmul_rn(sg, xi);
@@ -426,71 +525,85 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
     __syncthreads();
     // u = Q^T r = H_{n-3} ... H_0 r, then u -= (z.u) z; warp per column
     if (warp < d) {
-        float *u = U + warp;
+        float ur[kQ], zr[kQ];
+        col_load(U + warp, n, lane, ur);
         for (int k = 0; k + 2 < n; k++) {
             const float tau = tauv[k];
-            if (tau == 0.0f) continue;
-            const int m0 = k + 1;
-            float s = 0.0f;
-            const float *vk = Ap + coff(k, n) - k;
-            for (int i = m0 + lane; i < n; i += 32) s = fmaf(vk[i], u[(size_t)i * kXS], s);
-            s = tau * warp_sum_f(s);
-            for (int i = m0 + lane; i < n; i += 32) u[(size_t)i * kXS] = fmaf(-s, vk[i], u[(size_t)i * kXS]);
+            if (tau != 0.0f) reflect(ur, Ap + coff(k, n) - k, tau, k + 1, n, lane);
         }
         float s = 0.0f;
-        for (int i = lane; i < n; i += 32) s = fmaf(Zg[(size_t)i * 32 + warp], u[(size_t)i * kXS], s);
+#pragma unroll
+        for (int q = 0; q < kQ; q++) {
+            const int i = lane + 32 * q;
+            zr[q] = i < n ? Zg[(size_t)i * 32 + warp] : 0.0f;
+            s = fmaf(zr[q], ur[q], s);
+        }
         s = warp_sum_f(s);
-        for (int i = lane; i < n; i += 32) u[(size_t)i * kXS] = fmaf(-s, Zg[(size_t)i * 32 + warp], u[(size_t)i * kXS]);
+#pragma unroll
+        for (int q = 0; q < kQ; q++) ur[q] = fmaf(-s, zr[q], ur[q]);
+        col_store(U + warp, n, lane, ur);
     }
     __syncthreads();
     if (warp == 0 && lane < d) tri_solve_piv(dT, eT, n, lamv[lane], tiny, U + lane, scr, lane);
     __syncthreads();
-    // y -= (z.y) z, then delta = Q y = H_0 ... H_{n-3} y; x' = x - delta kept as the pair (x, -delta)
+    // y -= (z.y) z, then delta = Q y = H_0 ... H_{n-3} y into U
     if (warp < d) {
         float *u = U + warp;
+        float ur[kQ], zr[kQ];
+        col_load(u, n, lane, ur);
         float s = 0.0f;
-        for (int i = lane; i < n; i += 32) s = fmaf(Zg[(size_t)i * 32 + warp], u[(size_t)i * kXS], s);
+#pragma unroll
+        for (int q = 0; q < kQ; q++) {
+            const int i = lane + 32 * q;
+            zr[q] = i < n ? Zg[(size_t)i * 32 + warp] : 0.0f;
+            s = fmaf(zr[q], ur[q], s);
+        }
         s = warp_sum_f(s);
-        for (int i = lane; i < n; i += 32) u[(size_t)i * kXS] = fmaf(-s, Zg[(size_t)i * 32 + warp], u[(size_t)i * kXS]);
+#pragma unroll
+        for (int q = 0; q < kQ; q++) ur[q] = fmaf(-s, zr[q], ur[q]);
         for (int k = n - 3; k >= 0; k--) {
             const float tau = tauv[k];
-            if (tau == 0.0f) continue;
-            const int m0 = k + 1;
-            float t = 0.0f;
-            const float *vk = Ap + coff(k, n) - k;
-            for (int i = m0 + lane; i < n; i += 32) t = fmaf(vk[i], u[(size_t)i * kXS], t);
-            t = tau * warp_sum_f(t);
-            for (int i = m0 + lane; i < n; i += 32) u[(size_t)i * kXS] = fmaf(-t, vk[i], u[(size_t)i * kXS]);
+            if (tau != 0.0f) reflect(ur, Ap + coff(k, n) - k, tau, k + 1, n, lane);
         }
-        float *x = X + warp;
-        for (int i = lane; i < n; i += 32) {
-            const ff t = ffa::two_sum(x[(size_t)i * kXS], -u[(size_t)i * kXS]);
-            x[(size_t)i * kXS] = t.hi;
-            u[(size_t)i * kXS] = t.lo;
-        }
+        col_store(u, n, lane, ur);
     }
     __syncthreads();
 
     // ---------------------------------------------------------------- 4. Rayleigh quotients, residuals, output
-    ff *Wp = reinterpret_cast<ff *>(Ap);  // [n][kXS] w' = A x' (the reflectors are no longer needed)
+    // x' = x - delta, and A x' = A x - A delta: A x in float-float from the residual pass,
+    // A delta in FP32 (delta is the Newton correction, so the rounding of its product lies
+    // far below the residual tolerance); the reflectors are no longer needed, so A delta
+    // goes where the packed triangle was
+    float *G = Ap;  // [n][kXS]
     for (int i = warp; i < n; i += kNW) {
         if (lane < d) {
             const float2 *Ar = A + (size_t)i * n;
-            ffa::acc S = ffa::acc_zero();
-            for (int l = 0; l < n; l++) {
-                const float2 av = Ar[l];
-                ffa::acc_fma(S, ffa::make(av.x, av.y), ffa::make(X[(size_t)l * kXS + lane], U[(size_t)l * kXS + lane]));
-            }
-            Wp[(size_t)i * kXS + lane] = ffa::acc_value(S);
+            float g = 0.0f;
+            for (int l = 0; l < n; l++) g = fmaf(Ar[l].x, U[(size_t)l * kXS + lane], g);
+            G[(size_t)i * kXS + lane] = g;
         }
     }
     __syncthreads();
-    // per warp and column: partial x'.w' and x'.x' over the warp's rows i = warp, warp + 32, ...
+    // x' as the pair (X, U) = two_sum(x, -delta); per warp and column, over the warp's rows
+    // i = warp, warp + 32, ...: partial x'^T A x' = x^T w - 2 w^T delta + delta^T (A delta)
+    // (A symmetric, so x^T A delta = w^T delta: only the second-order term carries the
+    // rounding of the FP32 product) and x'^T x'
+    auto wprime = [&](int i, int j) {
+        const float2 w = Wg[(size_t)i * 32 + j];
+        return ffa::sub(ffa::make(w.x, w.y), ffa::make(G[(size_t)i * kXS + j], 0.0f));
+    };
     if (lane < d) {
         ffa::acc P = ffa::acc_zero(), Q = ffa::acc_zero();
         for (int i = warp; i < n; i += kNW) {
-            const ff xv = ffa::make(X[(size_t)i * kXS + lane], U[(size_t)i * kXS + lane]);
-            ffa::acc_fma(P, xv, Wp[(size_t)i * kXS + lane]);
+            const float xi = X[(size_t)i * kXS + lane], di = U[(size_t)i * kXS + lane];
+            const float2 w2 = Wg[(size_t)i * 32 + lane];
+            const ff w = ffa::make(w2.x, w2.y);
+            ffa::acc_fma(P, ffa::make(xi, 0.0f), w);
+            ffa::acc_fma(P, ffa::make(-2.0f * di, 0.0f), w);
+            ffa::acc_fma(P, ffa::make(di, 0.0f), ffa::make(G[(size_t)i * kXS + lane], 0.0f));
+            const ff xv = ffa::two_sum(xi, -di);
+            X[(size_t)i * kXS + lane] = xv.hi;
+            U[(size_t)i * kXS + lane] = xv.lo;
             ffa::acc_fma(Q, xv, xv);
         }
         pacc[warp * 32 + lane] = P;
@@ -510,7 +623,7 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
         float rr = 0.0f;
         for (int i = lane; i < n; i += 32) {
             const ff xv = ffa::make(X[(size_t)i * kXS + j], U[(size_t)i * kXS + j]);
-            const ff r = ffa::sub(Wp[(size_t)i * kXS + j], ffa::mul(lam, xv));
+            const ff r = ffa::sub(wprime(i, j), ffa::mul(lam, xv));
             rr = fmaf(r.hi, r.hi, rr);
         }
         rr = warp_sum_f(rr);
@@ -564,7 +677,7 @@ DeviceOnce g_attrs32;
 
 bool eig32_ok(int n, int d) { return n >= 2 && n <= 256 && d >= 1 && d <= 32 && d <= n; }
 
-size_t eig32_workspace_bytes(int n, int mats) { return align_up(sizeof(float) * (size_t)mats * 4 * n * 32, 256); }
+size_t eig32_workspace_bytes(int n, int mats) { return align_up(sizeof(float) * (size_t)mats * 6 * n * 32, 256); }
 
 cudaError_t launch_eig32(const void *cov_ff, int n, int d, int mats, double *V, double *eigvals, void *ws,
                          int *flag_out, int *redo_count, float tol, cudaStream_t st) {
@@ -584,6 +697,7 @@ cudaError_t launch_eig32(const void *cov_ff, int n, int d, int mats, double *V, 
     a.d = d;
     a.scr = (float *)ws;
     a.Z = (float *)ws + (size_t)mats * 3 * n * 32;
+    a.W = (float2 *)((float *)ws + (size_t)mats * 4 * n * 32);
     a.V = V;
     a.eig = eigvals;
     a.flag = flag_out;

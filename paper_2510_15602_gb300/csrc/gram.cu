@@ -121,21 +121,20 @@ __global__ void k_chan_absmax(const __grid_constant__ FitParams p, unsigned *__r
     if ((threadIdx.x & 31) == 0 && m) atomicMax(&amax[c], m);
 }
 
-__device__ __forceinline__ float rint_exact(float v) { return __fsub_rn(__fadd_rn(v, kMagic), kMagic); }
-
-// four 7-bit digits of y (|y| < 1): y ~= d0/2^6 + d1/2^13 + d2/2^20 + d3/2^27
+// four 7-bit digits of y (|y| < 1): y ~= d0/2^6 + d1/2^13 + d2/2^20 + d3/2^27.
+// Digit k rounds the remainder left by the digits above it, scaled by 2^(6+7k);
+// the scaling is folded into the rounding add (a power-of-two product is exact,
+// so the FMA rounds only once, to the integer) and each remainder r - d/2^m is
+// exact (it is at most half a unit of the digit's place and keeps r's last
+// bit), so the digits are those of the plain multiply / round / subtract chain.
 __device__ __forceinline__ void digits4(float y, float &d0, float &d1, float &d2, float &d3) {
-    float t = __fmul_rn(y, 64.0f);
-    d0 = rint_exact(t);
-    float r = __fsub_rn(t, d0);
-    t = __fmul_rn(r, 128.0f);
-    d1 = rint_exact(t);
-    r = __fsub_rn(t, d1);
-    t = __fmul_rn(r, 128.0f);
-    d2 = rint_exact(t);
-    r = __fsub_rn(t, d2);
-    t = __fmul_rn(r, 128.0f);
-    d3 = rint_exact(t);
+    d0 = __fsub_rn(__fmaf_rn(y, 64.0f, kMagic), kMagic);
+    float r = __fmaf_rn(d0, -1.0f / 64.0f, y);
+    d1 = __fsub_rn(__fmaf_rn(r, 8192.0f, kMagic), kMagic);
+    r = __fmaf_rn(d1, -1.0f / 8192.0f, r);
+    d2 = __fsub_rn(__fmaf_rn(r, 1048576.0f, kMagic), kMagic);
+    r = __fmaf_rn(d2, -1.0f / 1048576.0f, r);
+    d3 = __fsub_rn(__fmaf_rn(r, 134217728.0f, kMagic), kMagic);
 }
 
 // 64-byte swizzle (rows of 32 BF16 pixels): 16-B chunk c of row r lands at

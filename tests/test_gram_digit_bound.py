@@ -8,7 +8,7 @@ formed from the digit-level sums A_L = sum_{i+j=L} sum_p d_i d_j for L = 0..3
     Sigma_ij = R_i R_j T_ij 2^-40 / N - mu_i mu_j,   T = sum_L A_L 2^(7(4-L)).
 
 Claims checked: the digits are exact integers in [-64, 64] that reconstruct the
-fixed-point value; partial sums over a 256-pixel window stay below 2^24 (so an
+fixed-point value; partial sums over a 512-pixel window stay within 2^23 (so an
 FP32 accumulator holds them exactly); and the covariance is within
 2^-25 R_i R_j of the FP64 definition."""
 import numpy as np
@@ -35,11 +35,11 @@ def gram_cov(X):
     D = digits(y27)
     for d in D:
         assert np.abs(d).max() <= 64
-    # level sums over 256-pixel windows: every partial sum < 2^24 (exact in FP32)
+    # level sums over 512-pixel windows: every partial sum <= 2^23 (exact in FP32)
     for L in range(4):
-        for p0 in range(0, N, 256):
-            AL = sum(D[i][:, p0:p0 + 256] @ D[L - i][:, p0:p0 + 256].T for i in range(L + 1))
-            assert np.abs(AL).max() < 2 ** 24
+        for p0 in range(0, N, 512):
+            AL = sum(D[i][:, p0:p0 + 512] @ D[L - i][:, p0:p0 + 512].T for i in range(L + 1))
+            assert np.abs(AL).max() <= 2 ** 23
     T = np.zeros((C, C), dtype=object)
     for L in range(4):
         AL = sum(D[i] @ D[L - i].T for i in range(L + 1))
