@@ -1284,14 +1284,21 @@ def run_ours(args):
 
 def run_profile_batch(args):
     """A short fixed run for profilers: `args.profile_batch` calls of
-    qfca_batch_run on one context over the 16-image batch (no timing, no output)."""
+    qfca_batch_run on one context over the 16-image batch (no timing, no output),
+    with the tilings the timed bench uses: one untimed call first measures them
+    (autotuner on), and only the calls after it lie inside the profiler range
+    (cudaProfilerStart/Stop; run ncu with --profile-from-start off)."""
     host = make_inputs(range(N_IMG))
     import numpy as np
     import torch
     from paper_2510_15602_gb300 import qfca
     X = torch.from_numpy(np.stack([x for x, _ in host])).cuda()
     ctx = qfca.Context()
+    ctx.set_autotune(True)
     scores = torch.empty(N_IMG, HW, HW, dtype=torch.float32, device="cuda")
+    qfca.batch_run(X, D, B, R, args.precision, ctx=ctx, scores=scores)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
     for _ in range(args.profile_batch):
         qfca.batch_run(X, D, B, R, args.precision, ctx=ctx, scores=scores)
     if args.profile_paper:
@@ -1306,6 +1313,7 @@ def run_profile_batch(args):
         for _ in range(args.profile_paper):
             qfca.batch_run_plus(X, QFCA_PLUS_DRES, B, R, ctx=ctx, scores=scores)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     return 0 if ctx.device_status() == 0 else 1
 
 

@@ -112,21 +112,45 @@ __device__ __forceinline__ void col_store(float *p, int n, int lane, const float
         if (i < n) p[(size_t)i * kXS] = r[q];
     }
 }
-// r <- (I - tau v v^T) r for the reflector v stored in rows m0..n-1 of vk (vk[i], i >= m0).
-__device__ __forceinline__ void reflect(float (&r)[kQ], const float *vk, float tau, int m0, int n, int lane) {
-    float v[kQ], s = 0.0f;
+// r -= (z_j . r) z_j for column j of the [n][32] eigenvectors of T.
+__device__ __forceinline__ void project_out_z(float (&r)[kQ], const float *Zg, int j, int n, int lane) {
+    float z[kQ], s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kQ; q++) {
+        const int i = lane + 32 * q;
+        z[q] = i < n ? Zg[(size_t)i * 32 + j] : 0.0f;
+        s = fmaf(z[q], r[q], s);
+    }
+    s = warp_sum_f(s);
+#pragma unroll
+    for (int q = 0; q < kQ; q++) r[q] = fmaf(-s, z[q], r[q]);
+}
+// r0, r1 <- (I - tau v v^T) r0, r1 for the reflector v stored in rows m0..n-1 of vk (vk[i],
+// i >= m0): two columns at once, so each entry of v is loaded once for both.
+__device__ __forceinline__ void reflect2(float (&r0)[kQ], float (&r1)[kQ], const float *vk, float tau, int m0, int n,
+                                         int lane) {
+    float v[kQ], s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
     for (int q = 0; q < kQ; q++) {
         const int i = lane + 32 * q;
         v[q] = 0.0f;
         if (32 * q + 31 >= m0 && i >= m0 && i < n) v[q] = vk[i];
-        s = fmaf(v[q], r[q], s);
+        s0 = fmaf(v[q], r0[q], s0);
+        s1 = fmaf(v[q], r1[q], s1);
     }
-    s = tau * warp_sum_f(s);
 #pragma unroll
-    for (int q = 0; q < kQ; q++) r[q] = fmaf(-s, v[q], r[q]);
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    s0 *= tau;
+    s1 *= tau;
+#pragma unroll
+    for (int q = 0; q < kQ; q++) {
+        r0[q] = fmaf(-s0, v[q], r0[q]);
+        r1[q] = fmaf(-s1, v[q], r1[q]);
+    }
 }
-
 // Number of eigenvalues of T below x (the signs of the LDL^T pivots of T - x I).
 // The approximate division (2 ulp) only perturbs pivots that are not near zero, and
 // a count off by one near an eigenvalue moves that bisection by one FP32 step.
@@ -221,16 +245,17 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
     // Reflector k is formed in place in column k of the packed triangle (rows k+1..n-1; its
     // first entry v1 replaces the sub-diagonal entry, which goes to eT as alpha) and stays
     // there for the later passes.  pv: the product of the trailing block with the current
-    // reflector (unscaled); wv: w_k; pw: per-warp row partials [kNW][n+1]; dp: per-lane
-    // column partials [n][32].  Three CTA barriers per step.
+    // reflector (unscaled); red: partial sums of p.v (K = tau^2/2 p.v); nv: column k+1 after
+    // the update by reflector k; pw: per-warp row partials [kNW][n+1]; dp: per-lane column
+    // partials [n][32].  Two CTA barriers per step.
     float *pv = ps;
-    float *wv = X, *dp = X + n4;  // the X panel is free until the eigenvectors
+    float *bc = vs;               // reflector k+1 for all warps: v1, tau, the stored first entry x1
+    float *nv = X, *dp = X + n4;  // the X panel is free until the eigenvectors
     float *pw = U;                // the U panel likewise
     const int pws = n + 1;        // row stride of pw (the four threads of a row hit four banks)
-    float *red2 = red + 32;
     auto colp = [&](int c) { return Ap + coff(c, n) - c; };  // colp(c)[i] = A(i, c), i >= c
     // alpha, tau and first entry v1 of the reflector that maps (x1, rest) to (alpha, 0),
-    // sig = |rest|^2; every thread computes the same values
+    // sig = |rest|^2
     auto reflector = [](float x1, float sig, float &alpha, float &v1) -> float {
         alpha = x1;
         v1 = 0.0f;
@@ -241,31 +266,45 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
         v1 = x1 - alpha;
         return 1.0f / (nn - alpha * x1);
     };
-    // One pass over columns j0..n-1 of the trailing block, warp per column (columns
-    // j0 + warp + 32 s): with `upd`, the rank-2 update A -= v w^T + w v^T of the current
-    // reflector (vc, wv); with `acc`, the product with the next reflector's column vnp as
-    // stored (rows >= j0; its first entry is corrected in reduce_pass) on the updated
-    // entries.  Lane l of a warp meets only rows i_q = j0 + warp + l + 32 q (q >= s in
-    // column s), so the column's entries and the row sums of those rows stay in
-    // registers; the row sums go to pw[warp], each lane's column dot to dp.
-    auto fused_pass = [&](auto upd_c, auto acc_c, int j0, const float *vc, const float *vnp) {
+    // Step k's pass over columns j0 = k+2 .. n-1 of the trailing block, warp per column
+    // (columns j0 + warp + 32 s).  With UPD, the rank-2 update A -= v w^T + w v^T of
+    // reflector k (v = column k, w = tau p - K v formed where needed: every thread knows K
+    // and tau); with ACC, the product of the updated entries with column k+1 updated by
+    // reflector k (the next reflector as stored: its first entry is corrected in
+    // reduce_pass).  Lane l of a warp meets only rows i_q = j0 + warp + l + 32 q (q >= s in
+    // column s), so v, w and the updated column k+1 at those rows, and their row sums, stay
+    // in registers; the row sums go to pw[warp], each lane's column dot to dp.
+    // (m0 = k+1; vjm, wjm: v and w at row m0.)
+    auto fused_pass = [&](auto upd_c, auto acc_c, int j0, const float *vc, const float *cm, float tau, float K,
+                          float vjm, float wjm) {
         constexpr bool UPD = decltype(upd_c)::value, ACC = decltype(acc_c)::value;
         const int rb = j0 + warp + lane;
         const int S = n - j0 - warp > 0 ? (n - j0 - warp + 31) >> 5 : 0;  // columns of this warp
-        float vq[kQ], pr[kQ];
+        if (S == 0) return;  // no column: nothing of this warp is read
+        float vq[kQ], pr[kQ], vcq[kQ], wq[kQ];
 #pragma unroll
         for (int q = 0; q < kQ; q++) {
             const int i = rb + 32 * q;
-            vq[q] = ACC && i < n ? vnp[i] : 0.0f;
-            pr[q] = 0.0f;
+            vcq[q] = 0.0f, wq[q] = 0.0f, vq[q] = 0.0f, pr[q] = 0.0f;
+            if (i < n) {
+                if (UPD) {
+                    vcq[q] = vc[i];
+                    wq[q] = fmaf(-K, vcq[q], tau * pv[i]);
+                }
+                if (ACC) vq[q] = UPD ? fmaf(-vcq[q], wjm, fmaf(-wq[q], vjm, cm[i])) : cm[i];
+            }
         }
 #pragma unroll
         for (int s = 0; s < kQ; s++) {
             if (s < S) {
                 const int jc = j0 + warp + 32 * s;
                 float *col = colp(jc);
-                const float vj = UPD ? vc[jc] : 0.0f, wj = UPD ? wv[jc] : 0.0f;
-                const float vnj = ACC ? vnp[jc] : 0.0f;
+                float vj = 0.0f, wj = 0.0f, vnj = 0.0f;
+                if (UPD) {
+                    vj = vc[jc];
+                    wj = fmaf(-K, vj, tau * pv[jc]);
+                }
+                if (ACC) vnj = UPD ? fmaf(-vj, wjm, fmaf(-wj, vjm, cm[jc])) : cm[jc];
                 float dot = 0.0f;
 #pragma unroll
                 for (int q = s; q < kQ; q++) {
@@ -273,7 +312,7 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
                     if (i < n) {
                         float a = col[i];
                         if (UPD) {
-                            a = fmaf(-vc[i], wj, fmaf(-wv[i], vj, a));
+                            a = fmaf(-vcq[q], wj, fmaf(-wq[q], vj, a));
                             col[i] = a;
                         }
                         if (ACC) {
@@ -293,6 +332,34 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
             }
         }
     };
+    // Column m0 = k+1 updated by reflector k (rows m0..n-1, the same operations as the
+    // pass's) into nv, and reflector k+1 from it: one warp, while the others run the pass
+    auto next_column = [&](bool upd, const float *vc, const float *cm, int m0, float tau, float K, float vjm,
+                           float wjm, bool has_next) {
+        float sq = 0.0f, x1 = 0.0f;
+#pragma unroll
+        for (int q = 0; q < kQ; q++) {
+            const int i = m0 + lane + 32 * q;
+            if (i < n) {
+                float c = cm[i];
+                if (upd) {
+                    const float vi = vc[i], wi = fmaf(-K, vi, tau * pv[i]);
+                    c = fmaf(-vi, wjm, fmaf(-wi, vjm, c));
+                }
+                nv[i] = c;
+                if (i >= m0 + 2) sq = fmaf(c, c, sq);
+                if (i == m0 + 1) x1 = c;
+            }
+        }
+        sq = warp_sum_f(sq);
+        x1 = __shfl_sync(0xffffffffu, x1, 1);  // row m0 + 1: lane 1, q = 0
+        if (has_next && lane == 0) {
+            float alpha, v1;
+            const float t = reflector(x1, sq, alpha, v1);
+            eT[m0] = alpha, tauv[m0] = t, v1s[m0] = v1;
+            bc[0] = v1, bc[1] = t, bc[2] = x1;
+        }
+    };
     // pv[i] (i >= j0): the row partials of warps 0..i-j0 (the only warps that reach row i)
     // plus the 32 lane partials of column i, four threads per row, fixed order, plus
     // dv A(i, j0) (dv = v1 - x1: the reflector's first entry in place of the stored one);
@@ -306,7 +373,11 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
         float t = 0.0f, kp = 0.0f;
         if (i < n) {
             const int wmax = min(kNW - 1, i - j0);
-            for (int w = part; w <= wmax; w += 4) t += pw[w * pws + i];
+#pragma unroll
+            for (int m = 0; m < kNW / 4; m++) {
+                const int w = part + 4 * m;
+                if (w <= wmax) t += pw[w * pws + i];
+            }
             const float4 *c = reinterpret_cast<const float4 *>(dp + (i - j0) * 32 + part * 8);
             const float4 c0 = c[0], c1 = c[1];
             t += ((c0.x + c0.y) + (c0.z + c0.w)) + ((c1.x + c1.y) + (c1.z + c1.w));
@@ -321,7 +392,6 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
         kp = warp_sum_f(kp);
         if (lane == 0) red[warp] = kp;
     };
-    float *bc = vs;  // reflector k+1 for all warps: v1, tau, the stored first entry x1
     if (tid == 0) {
         for (int i = n - 2 < 0 ? 0 : n - 2; i < n; i++) eT[i] = 0.0f, tauv[i] = 0.0f;
     }
@@ -329,19 +399,13 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
     float tau_cur = 0.0f;
     if (n >= 3) {
         const float *c0 = colp(0);
-        float sq = 0.0f;
-        for (int i = 2 + tid; i < n; i += kT) sq = fmaf(c0[i], c0[i], sq);
-        sq = warp_sum_f(sq);
-        if (lane == 0) red2[warp] = sq;
+        if (warp == kNW - 1) next_column(false, nullptr, c0, 0, 0.0f, 0.0f, 0.0f, 0.0f, true);
         __syncthreads();
-        float alpha, v1;
-        const float x1 = c0[1];
-        tau_cur = reflector(x1, warp_sum_f(red2[lane]), alpha, v1);
-        if (tid == 0) eT[0] = alpha, tauv[0] = tau_cur, v1s[0] = v1;
-        if (tau_cur != 0.0f) fused_pass(kFalse, kTrue, 1, nullptr, c0);
+        tau_cur = bc[1];
+        if (tau_cur != 0.0f) fused_pass(kFalse, kTrue, 1, nullptr, c0, 0.0f, 0.0f, 0.0f, 0.0f);
         __syncthreads();
-        if (tau_cur != 0.0f) reduce_pass(1, c0, v1, v1 - x1);
-        if (tid == 0) Ap[1] = v1;  // column 0 now holds reflector 0
+        if (tau_cur != 0.0f) reduce_pass(1, c0, bc[0], bc[0] - bc[2]);
+        if (tid == 0) Ap[1] = bc[0];  // column 0 now holds reflector 0
         __syncthreads();
     }
     for (int k = 0; k + 2 < n; k++) {
@@ -349,49 +413,24 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
         const float *vc = colp(k);  // reflector k
         float *cm = colp(m0);
         const bool has_next = k + 3 < n;
-        // w = tau p - K v (K = tau^2/2 p.v, partial sums in red) for the rows of this
-        // thread, the update of column k+1 by reflector k, and the squares of its entries
-        // below the first sub-diagonal (reflector k+1); warps without rows skip it
-        float sq = 0.0f;
-        if (m0 + (warp << 5) < n) {
-            if (tau_cur != 0.0f) {
-                const float K = 0.5f * tau_cur * tau_cur * warp_sum_f(red[lane]);
-                const float vj = vc[m0], wj = fmaf(-K, vj, tau_cur * pv[m0]);
-                const int i = m0 + tid;
-                if (i < n) {
-                    const float vi = vc[i], wi = fmaf(-K, vi, tau_cur * pv[i]);
-                    wv[i] = wi;
-                    const float c = fmaf(-vi, wj, fmaf(-wi, vj, cm[i]));
-                    cm[i] = c;
-                    if (i >= m0 + 2) sq = fmaf(c, c, sq);
-                }
-            } else {
-                const int i = m0 + 2 + tid;
-                if (i < n) sq = cm[i] * cm[i];
-            }
-            sq = warp_sum_f(sq);
+        const bool upd = tau_cur != 0.0f;
+        // K = tau^2/2 p.v from the previous reduction; v and w at row m0 (every thread)
+        float K = 0.0f, vjm = 0.0f, wjm = 0.0f;
+        if (upd) {
+            K = 0.5f * tau_cur * tau_cur * warp_sum_f(red[lane]);
+            vjm = vc[m0];
+            wjm = fmaf(-K, vjm, tau_cur * pv[m0]);
         }
-        if (lane == 0) red2[warp] = sq;
-        __syncthreads();
-        // the last warp (the fewest pass entries) forms reflector k+1 while the others
-        // start the pass with the column as stored
-        if (warp == kNW - 1 && has_next) {
-            float alpha, v1;
-            const float x1 = cm[m0 + 1];
-            const float t = reflector(x1, warp_sum_f(red2[lane]), alpha, v1);
-            if (lane == 0) {
-                eT[m0] = alpha, tauv[m0] = t, v1s[m0] = v1;
-                bc[0] = v1, bc[1] = t, bc[2] = x1;
-            }
-        }
+        if (warp == kNW - 1) next_column(upd, vc, cm, m0, tau_cur, K, vjm, wjm, has_next);
         if (tid == 0) dT[k] = vc[k];
-        if (tau_cur != 0.0f && has_next) fused_pass(kTrue, kTrue, k + 2, vc, cm);
-        else if (tau_cur != 0.0f) fused_pass(kTrue, kFalse, k + 2, vc, cm);
-        else if (has_next) fused_pass(kFalse, kTrue, k + 2, vc, cm);
+        if (upd && has_next) fused_pass(kTrue, kTrue, k + 2, vc, cm, tau_cur, K, vjm, wjm);
+        else if (upd) fused_pass(kTrue, kFalse, k + 2, vc, cm, tau_cur, K, vjm, wjm);
+        else if (has_next) fused_pass(kFalse, kTrue, k + 2, vc, cm, tau_cur, K, vjm, wjm);
         __syncthreads();
         const float tau_next = has_next ? bc[1] : 0.0f;
-        if (tau_next != 0.0f) reduce_pass(k + 2, cm, bc[0], bc[0] - bc[2]);
-        if (has_next && tid == 0) cm[m0 + 1] = bc[0];  // column k+1 now holds reflector k+1
+        if (tau_next != 0.0f) reduce_pass(k + 2, nv, bc[0], bc[0] - bc[2]);
+        // store the updated column k+1 (reflector k+1 in its rows below the diagonal)
+        for (int i = m0 + tid; i < n; i += kT) cm[i] = (has_next && i == m0 + 1) ? bc[0] : nv[i];
         tau_cur = tau_next;
         __syncthreads();
     }
@@ -484,15 +523,19 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
         }
     }
     __syncthreads();
-    // back-transformation x_j = H_0 ... H_{n-3} z_j, warp per column (held in registers)
-    if (warp < d) {
-        float xr[kQ];
-        col_load(X + warp, n, lane, xr);
+    // back-transformation x_j = H_0 ... H_{n-3} z_j, columns 2w and 2w+1 in the registers of
+    // warp w (a missing second column is carried as zeros)
+    if (2 * warp < d) {
+        const int j0 = 2 * warp, j1 = j0 + 1 < d ? j0 + 1 : j0;
+        float xr0[kQ], xr1[kQ];
+        col_load(X + j0, n, lane, xr0);
+        col_load(X + j1, n, lane, xr1);
         for (int k = n - 3; k >= 0; k--) {
             const float tau = tauv[k];
-            if (tau != 0.0f) reflect(xr, Ap + coff(k, n) - k, tau, k + 1, n, lane);  // reflector k: rows k+1..n-1
+            if (tau != 0.0f) reflect2(xr0, xr1, Ap + coff(k, n) - k, tau, k + 1, n, lane);  // rows k+1..n-1
         }
-        col_store(X + warp, n, lane, xr);
+        col_store(X + j0, n, lane, xr0);
+        if (j1 != j0) col_store(X + j1, n, lane, xr1);
     }
     __syncthreads();
 
@@ -524,48 +567,39 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
     }
     __syncthreads();
     // u = Q^T r = H_{n-3} ... H_0 r, then u -= (z.u) z; warp per column
-    if (warp < d) {
-        float ur[kQ], zr[kQ];
-        col_load(U + warp, n, lane, ur);
+    if (2 * warp < d) {
+        const int j0 = 2 * warp, j1 = j0 + 1 < d ? j0 + 1 : j0;
+        float ur0[kQ], ur1[kQ];
+        col_load(U + j0, n, lane, ur0);
+        col_load(U + j1, n, lane, ur1);
         for (int k = 0; k + 2 < n; k++) {
             const float tau = tauv[k];
-            if (tau != 0.0f) reflect(ur, Ap + coff(k, n) - k, tau, k + 1, n, lane);
+            if (tau != 0.0f) reflect2(ur0, ur1, Ap + coff(k, n) - k, tau, k + 1, n, lane);
         }
-        float s = 0.0f;
-#pragma unroll
-        for (int q = 0; q < kQ; q++) {
-            const int i = lane + 32 * q;
-            zr[q] = i < n ? Zg[(size_t)i * 32 + warp] : 0.0f;
-            s = fmaf(zr[q], ur[q], s);
+        project_out_z(ur0, Zg, j0, n, lane);
+        col_store(U + j0, n, lane, ur0);
+        if (j1 != j0) {
+            project_out_z(ur1, Zg, j1, n, lane);
+            col_store(U + j1, n, lane, ur1);
         }
-        s = warp_sum_f(s);
-#pragma unroll
-        for (int q = 0; q < kQ; q++) ur[q] = fmaf(-s, zr[q], ur[q]);
-        col_store(U + warp, n, lane, ur);
     }
     __syncthreads();
     if (warp == 0 && lane < d) tri_solve_piv(dT, eT, n, lamv[lane], tiny, U + lane, scr, lane);
     __syncthreads();
     // y -= (z.y) z, then delta = Q y = H_0 ... H_{n-3} y into U
-    if (warp < d) {
-        float *u = U + warp;
-        float ur[kQ], zr[kQ];
-        col_load(u, n, lane, ur);
-        float s = 0.0f;
-#pragma unroll
-        for (int q = 0; q < kQ; q++) {
-            const int i = lane + 32 * q;
-            zr[q] = i < n ? Zg[(size_t)i * 32 + warp] : 0.0f;
-            s = fmaf(zr[q], ur[q], s);
-        }
-        s = warp_sum_f(s);
-#pragma unroll
-        for (int q = 0; q < kQ; q++) ur[q] = fmaf(-s, zr[q], ur[q]);
+    if (2 * warp < d) {
+        const int j0 = 2 * warp, j1 = j0 + 1 < d ? j0 + 1 : j0;
+        float ur0[kQ], ur1[kQ];
+        col_load(U + j0, n, lane, ur0);
+        col_load(U + j1, n, lane, ur1);
+        project_out_z(ur0, Zg, j0, n, lane);
+        project_out_z(ur1, Zg, j1, n, lane);
         for (int k = n - 3; k >= 0; k--) {
             const float tau = tauv[k];
-            if (tau != 0.0f) reflect(ur, Ap + coff(k, n) - k, tau, k + 1, n, lane);
+            if (tau != 0.0f) reflect2(ur0, ur1, Ap + coff(k, n) - k, tau, k + 1, n, lane);
         }
-        col_store(u, n, lane, ur);
+        col_store(U + j0, n, lane, ur0);
+        if (j1 != j0) col_store(U + j1, n, lane, ur1);
     }
     __syncthreads();
 
