@@ -59,10 +59,11 @@ constexpr int kSlices = 4;
 constexpr uint32_t kWaitTries = 1u << 26;
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: (v + kMagic) - kMagic rounds v to an integer
 
-__device__ __forceinline__ int tile_pair_idx(int p, int nt, int &j) {
+// Off-diagonal tile pair p (i < j, enumerated row by row) of nt channel tiles: returns i, sets j.
+__device__ __forceinline__ int off_pair_idx(int p, int nt, int &j) {
     int i = 0;
-    while (p >= nt - i) { p -= nt - i; i++; }
-    j = i + p;
+    while (p >= nt - 1 - i) { p -= nt - 1 - i; i++; }
+    j = i + 1 + p;
     return i;
 }
 
@@ -72,11 +73,13 @@ struct FitImgP {
     long N;
     long chunk;       // pixels per Gram CTA (a multiple of the exact-accumulation window)
     int n_split;      // pixel ranges of this image
-    long cta0;        // first Gram CTA of this image
+    long cta0;        // first Gram CTA of this image's off-diagonal tile pairs
+    long cta0d;       // first Gram CTA of its diagonal tiles
 };
 
 struct FitParams {
     int n, C, layout, vec_ok, nt, n_pairs;
+    long diag_start;  // the grid's off-diagonal CTAs (the longer ones) come first, then the diagonal
     FitImgP img[kMaxBatch];
 };
 
@@ -176,13 +179,15 @@ __device__ __forceinline__ void read_stage(const float *stage, float (&v)[8]) {
 }
 
 // Convert this thread's 8 values of a block into its 4 digit slices, packed as
-// BF16 pairs in registers (pk[slice]); optionally accumulate per-row digit sums
-// and the level-4 diagonal terms.  The operand buffer is written afterwards
-// (store_block), so the conversion can run while the buffer is still being read.
+// BF16 pairs in registers (pk[slice]); with `slot` (this thread's five counters, stride
+// kThreads), also add its digit sums per slice and its level-4 diagonal terms
+// 2 d1 d3 + d2^2 (exact in FP32: 8 digits of magnitude <= 64, and 8 terms <= 3 * 2^12; the
+// integer conversion by the magic-number add is exact below 2^22).  The operand buffer is
+// written afterwards (store_slice), so the conversion can run while the buffer is still
+// being read.
+__device__ __forceinline__ int small_int(float v) { return __float_as_int(__fadd_rn(v, kMagic)) - 0x4B400000; }
 __device__ __forceinline__ void convert_block(const float (&v)[8], float s, uint4 (&pk)[kSlices],
-                                              int *__restrict__ dsum /* [4][128] or null */,
-                                              unsigned long long *__restrict__ dsq /* [128] or null */) {
-    const int row = threadIdx.x >> 2;
+                                              int *__restrict__ slot /* [5][kThreads] at this thread, or null */) {
     float dd[kSlices][8];
 #pragma unroll
     for (int e = 0; e < 8; e++) digits4(__fmul_rn(v[e], s), dd[0][e], dd[1][e], dd[2][e], dd[3][e]);
@@ -192,21 +197,35 @@ __device__ __forceinline__ void convert_block(const float (&v)[8], float s, uint
         pk[sl].y = tc::pack_bf16x2(dd[sl][2], dd[sl][3]);
         pk[sl].z = tc::pack_bf16x2(dd[sl][4], dd[sl][5]);
         pk[sl].w = tc::pack_bf16x2(dd[sl][6], dd[sl][7]);
-        if (dsum) {
+        if (slot) {
             const float t = ((dd[sl][0] + dd[sl][1]) + (dd[sl][2] + dd[sl][3])) +
                             ((dd[sl][4] + dd[sl][5]) + (dd[sl][6] + dd[sl][7]));
-            atomicAdd(&dsum[sl * kTB + row], (int)t);
+            slot[sl * kThreads] += small_int(t);
         }
     }
-    if (dsq) {
-        int t4 = 0;  // exact: |2 d1 d3 + d2^2| <= 3 * 2^12 per pixel
+    if (slot) {
+        float t4 = 0.0f;
 #pragma unroll
-        for (int e = 0; e < 8; e++) {
-            const int d1 = (int)dd[1][e], d2 = (int)dd[2][e], d3 = (int)dd[3][e];
-            t4 += 2 * d1 * d3 + d2 * d2;
-        }
-        atomicAdd(&dsq[row], (unsigned long long)(long long)t4);
+        for (int e = 0; e < 8; e++) t4 = fmaf(dd[2][e], dd[2][e], fmaf(2.0f * dd[1][e], dd[3][e], t4));
+        slot[kSlices * kThreads] += small_int(t4);
     }
+}
+
+// Both BF16 halves of a packed pair divided by two: the exponent of each nonzero half
+// lowered by one (the digits are integers of magnitude <= 64, so no half is subnormal and
+// the halving is exact; a zero stays zero, and no borrow crosses the halves).
+__device__ __forceinline__ uint32_t half_bf16x2(uint32_t w) {
+    const uint32_t hi = (w & 0x7F800000u) ? 0x00800000u : 0u, lo = (w & 0x00007F80u) ? 0x00000080u : 0u;
+    return w - (hi | lo);
+}
+__device__ __forceinline__ uint4 half_bf16x2(const uint4 &w) {
+    return make_uint4(half_bf16x2(w.x), half_bf16x2(w.y), half_bf16x2(w.z), half_bf16x2(w.w));
+}
+
+// One packed slice into slot `sl` of an operand buffer (K-major, 64-byte swizzle).
+__device__ __forceinline__ void store_slice(const uint4 &pk, uint8_t *slices, int sl) {
+    const int row = threadIdx.x >> 2, g = threadIdx.x & 3;
+    *reinterpret_cast<uint4 *>(slices + sl * kSliceBytes + swz(row, g)) = pk;
 }
 
 // The packed digits into the K-major, 64-byte-swizzled slices of an operand buffer.
@@ -243,7 +262,27 @@ __device__ __forceinline__ void issue_level_mmas(uint32_t tmem, uint32_t a_addr,
     }
 }
 
-// Grid: images * n_pairs * n_split CTAs.  Per image: Gint [C][C] int64 (upper
+// A diagonal tile (A = B = the block's digits D_0..D_3) needs only the symmetric part
+// of the level sums: with Y_L = sum over i <= j, i + j = L of c_ij D_i D_j^T, c_ij = 1 for
+// i < j and 1/2 for i = j, T = Y + Y^T (the halves exact in BF16 and in the FP32
+// accumulators).  Slots of the buffer: [D_0][D_0/2][D_1][D_1/2][D_2][D_3]; per K-step
+// D_0 x [D_0/2 | D_1] (levels 0, 1), D_0 x [D_2 | D_3] and D_1 x [D_1/2 | D_2] (levels 2, 3):
+// three N = 256 MMAs instead of six.
+__device__ __forceinline__ void issue_level_mmas_sym(uint32_t tmem, uint32_t addr, bool first) {
+    const uint64_t d0 = tc::sdesc_kmajor_sw64(addr);
+    constexpr uint32_t id256 = tc::idesc_bf16_f32(kTB, 256);
+    const uint32_t acc0 = first ? 0u : 1u;
+#pragma unroll
+    for (int ks = 0; ks < kSub / 16; ks++) {
+        auto S = [&](int sl) { return d0 + (uint64_t)((sl * kSliceBytes + ks * 32) >> 4); };
+        const uint32_t a0 = ks == 0 ? acc0 : 1u;
+        tc::mma_bf16_ss(tmem + 0 * kTB, S(0), S(1), id256, a0);  // levels 0, 1
+        tc::mma_bf16_ss(tmem + 2 * kTB, S(0), S(4), id256, a0);  // levels 2, 3
+        tc::mma_bf16_ss(tmem + 2 * kTB, S(2), S(3), id256, 1u);  // levels 2, 3
+    }
+}
+
+// Grid: images * n_pairs * n_split CTAs, off-diagonal tile pairs first.  Per image: Gint [C][C] int64 (upper
 // tiles accumulated), Dsum [4][C] int64, scale [C].  Two operand buffers: the
 // threads convert sub-chunk k into buffer k & 1 while the tensor cores work on
 // sub-chunk k - 1 from the other buffer; a buffer is rewritten only after the
@@ -261,24 +300,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
     float *stg = (float *)(smem + 4 * kBlockBytes);                 // [2 stages][2 blocks][128][kStageRow] FP32
     uint64_t *bar = (uint64_t *)(smem + 4 * kBlockBytes + 4 * kStageBytes);  // [7] mbarriers + the abort flag
     uint32_t *tmem_slot = (uint32_t *)(bar + 8);
-    unsigned long long *dsq = (unsigned long long *)(tmem_slot + 2);  // [128] (8-B aligned)
-    int *dsum = (int *)(dsq + kTB);                                    // [4][128]
+    int *slots = (int *)(tmem_slot + 4);  // [5][kThreads]: per-thread digit sums (4 slices) and level-4 terms
 
     const long cta = blockIdx.x;
+    const bool diag = cta >= p.diag_start;
     int img = 0;
-    while (img + 1 < p.n && p.img[img + 1].cta0 <= cta) img++;
+    if (diag) {
+        while (img + 1 < p.n && p.img[img + 1].cta0d <= cta) img++;
+    } else {
+        while (img + 1 < p.n && p.img[img + 1].cta0 <= cta) img++;
+    }
     const FitImgP &im = p.img[img];
-    const int C = p.C, layout = p.layout, vec_ok = p.vec_ok, nt = p.nt, n_pairs = p.n_pairs;
+    const int C = p.C, layout = p.layout, vec_ok = p.vec_ok, nt = p.nt, n_off = p.n_pairs - p.nt;
     const long N = im.N, chunk = im.chunk;
     const float *X = im.X;
-    const int rem = (int)(cta - im.cta0);
-    const int pair = rem % n_pairs, split = rem / n_pairs;
+    const int rem = (int)(cta - (diag ? im.cta0d : im.cta0));
+    int ti, tj, split;
+    if (diag) {
+        ti = tj = rem % nt;
+        split = rem / nt;
+    } else {
+        ti = off_pair_idx(rem % n_off, nt, tj);
+        split = rem / n_off;
+    }
     scale += (long)img * C;
     Gint += (long)img * C * C;
     Dsum += (long)img * kSlices * C;
-    int tj;
-    const int ti = tile_pair_idx(pair, nt, tj);
-    const bool diag = ti == tj;
     const long p0 = (long)split * chunk, p1 = min(N, p0 + chunk);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -297,8 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
         *reinterpret_cast<volatile int *>(&bar[7]) = 0;
         tc::fence_mbar_init();
     }
-    for (int i = tid; i < kSlices * kTB; i += kThreads) dsum[i] = 0;
-    for (int i = tid; i < kTB; i += kThreads) dsq[i] = 0ull;
+    for (int sl = 0; sl <= kSlices; sl++) slots[sl * kThreads + tid] = 0;
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -339,6 +385,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
     stage(0, p0);
     stage(1, p0 + kSub);
     int kk = 0, in_win = 0, win = 0, issued_windows = 0;
+    bool pending = false;  // a window's MMAs are issued and its accumulators not drained yet
+    // drain window `win`'s exact level sums into int64 (acc_full covers every MMA of the window)
+    auto drain = [&]() -> bool {
+        if (!bwait(acc_full, win & 1)) return false;
+        tc::tc_fence_after();
+#pragma unroll
+        for (int L = 0; L < 4; L++) {
+            uint32_t r0[16], r1[16];
+            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(L * kTB + 32 * cg4);
+            tc::tmem_ld16(ta, r0);
+            tc::tmem_ld16(ta + 16, r1);
+            tc::tmem_wait_ld();
+            // levels 0 and 2 of a diagonal tile hold half-integers: 2 A_L, one shift less.
+            // Every level sum is an exact FP32 integer; all are within 2^22 (the exact range of
+            // the magic-number conversion) except level 3 of an off-diagonal tile (four
+            // products: up to 2^23), which takes the exact float-to-int instruction
+            const bool hl = diag && (L == 0 || L == 2), wide = !diag && L == 3;
+            const float m2 = hl ? 2.0f : 1.0f;
+            const int sh = 7 * (4 - L) - (hl ? 1 : 0);
+#pragma unroll
+            for (int jj = 0; jj < 16; jj++) {
+                const float f0 = __fmul_rn(__uint_as_float(r0[jj]), m2), f1 = __fmul_rn(__uint_as_float(r1[jj]), m2);
+                const int v0 = wide ? __float2int_rn(f0) : small_int(f0);
+                const int v1 = wide ? __float2int_rn(f1) : small_int(f1);
+                tot[jj] += (long long)v0 << sh;
+                tot[16 + jj] += (long long)v1 << sh;
+            }
+        }
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive_cta(drained);
+        win++;
+        return true;
+    };
     for (long q0 = p0; q0 < p1; q0 += kSub, kk++) {
         const int bsel = kk & 1;
         if (*abort_flag) { failed = true; break; }
@@ -350,15 +430,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
         {
             float v[8];
             read_stage(sa, v);
-            convert_block(v, sA, pk, diag ? dsum : nullptr, diag ? dsq : nullptr);
+            convert_block(v, sA, pk, diag ? slots + tid : nullptr);
         }
         // the MMAs of sub-chunk kk-2 read this operand buffer
         if (kk >= 2 && !bwait(&empty[bsel], ((kk - 2) >> 1) & 1)) { failed = true; break; }
-        store_block(pk, As(bsel));
-        if (!diag) {
+        if (diag) {
+            uint8_t *buf = As(bsel);  // six slots across the A and B halves of the buffer
+            store_slice(pk[0], buf, 0);
+            store_slice(half_bf16x2(pk[0]), buf, 1);
+            store_slice(pk[1], buf, 2);
+            store_slice(half_bf16x2(pk[1]), buf, 3);
+            store_slice(pk[2], buf, 4);
+            store_slice(pk[3], buf, 5);
+        } else {
+            store_block(pk, As(bsel));
             float v[8];
             read_stage(sa + kTB * kStageRow, v);
-            convert_block(v, sB, pk, nullptr, nullptr);
+            convert_block(v, sB, pk, nullptr);
             store_block(pk, Bs(bsel));
         }
         // each thread reads back only what it staged itself, so the stage can be
@@ -367,6 +455,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
         tc::fence_proxy_async_smem();  // this thread's operand writes, visible to the tensor cores
         __syncwarp();
         if (lane == 0) tc::mbar_arrive_cta(&full[bsel]);
+        // the previous window is drained only now, so that its last MMAs complete behind this
+        // sub-chunk's conversion; the first MMA of this window waits for `drained`
+        if (pending) {
+            if (!drain()) { failed = true; break; }
+            pending = false;
+        }
         const bool first = in_win == 0;
         in_win += kSub;
         const bool win_end = in_win >= kWin || q0 + kSub >= p1;
@@ -377,7 +471,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
             if (ok) {
                 tc::tc_fence_after();
                 const uint32_t a_addr = tc::smem_u32(As(bsel));
-                issue_level_mmas(tmem, a_addr, diag ? a_addr : tc::smem_u32(Bs(bsel)), first);
+                if (diag) issue_level_mmas_sym(tmem, a_addr, first);
+                else issue_level_mmas(tmem, a_addr, tc::smem_u32(Bs(bsel)), first);
                 tc::mma_commit(&empty[bsel]);
                 if (win_end) {
                     tc::mma_commit(acc_full);
@@ -387,32 +482,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
         }
         __syncwarp();
         if (win_end) {
-            // drain the window's exact level sums into int64 (acc_full covers every MMA of the window)
-            if (!bwait(acc_full, win & 1)) { failed = true; break; }
-            tc::tc_fence_after();
-#pragma unroll
-            for (int L = 0; L < 4; L++) {
-                uint32_t r0[16], r1[16];
-                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(L * kTB + 32 * cg4);
-                tc::tmem_ld16(ta, r0);
-                tc::tmem_ld16(ta + 16, r1);
-                tc::tmem_wait_ld();
-                const int sh = 7 * (4 - L);
-#pragma unroll
-                for (int jj = 0; jj < 16; jj++) {
-                    const int v0 = __float_as_int(__fadd_rn(__uint_as_float(r0[jj]), kMagic)) - 0x4B400000;
-                    const int v1 = __float_as_int(__fadd_rn(__uint_as_float(r1[jj]), kMagic)) - 0x4B400000;
-                    tot[jj] += (long long)v0 << sh;
-                    tot[16 + jj] += (long long)v1 << sh;
-                }
-            }
-            tc::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive_cta(drained);
-            win++;
+            pending = true;
             in_win = 0;
         }
     }
+    if (!failed && pending && !drain()) failed = true;
     __syncthreads();
     failed = failed || *abort_flag;
     if (failed) {
@@ -428,18 +502,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
 #pragma unroll
             for (int jj = 0; jj < 32; jj++) {
                 const int c2 = tj * kTB + 32 * cg4 + jj;
-                if (c2 < C && tot[jj] != 0) atomicAdd(&Gint[(long)c1 * C + c2], (unsigned long long)tot[jj]);
+                if (c2 >= C || tot[jj] == 0) continue;
+                if (!diag) {
+                    atomicAdd(&Gint[(long)c1 * C + c2], (unsigned long long)tot[jj]);
+                } else if (c1 == c2) {  // T = Y + Y^T
+                    atomicAdd(&Gint[(long)c1 * C + c2], (unsigned long long)(2 * tot[jj]));
+                } else {
+                    atomicAdd(&Gint[(long)c1 * C + c2], (unsigned long long)tot[jj]);
+                    atomicAdd(&Gint[(long)c2 * C + c1], (unsigned long long)tot[jj]);
+                }
             }
         }
-        __syncthreads();  // dsum / dsq complete
-        if (diag) {
-            for (int i = tid; i < kSlices * kTB; i += kThreads) {
-                const int sl = i / kTB, row = i % kTB, c = ti * kTB + row;
-                if (c < C && dsum[i] != 0) atomicAdd(&Dsum[(long)sl * C + c], (unsigned long long)(long long)dsum[i]);
-            }
-            for (int row = tid; row < kTB; row += kThreads) {
-                const int c = ti * kTB + row;
-                if (c < C && dsq[row] != 0ull) atomicAdd(&Gint[(long)c * C + c], dsq[row]);
+        __syncthreads();  // every thread's counters complete
+        if (diag && tid < kTB) {  // row tid: the counters of its four threads 4 tid .. 4 tid + 3
+            const int c = ti * kTB + tid;
+            if (c < C) {
+                for (int sl = 0; sl <= kSlices; sl++) {
+                    const int *t = slots + sl * kThreads + 4 * tid;
+                    const long long v = (long long)t[0] + t[1] + t[2] + t[3];
+                    if (v == 0) continue;
+                    if (sl < kSlices) atomicAdd(&Dsum[(long)sl * C + c], (unsigned long long)v);
+                    else atomicAdd(&Gint[(long)c * C + c], (unsigned long long)v);
+                }
             }
         }
     }
@@ -527,8 +611,7 @@ static GramPlan gram_plan(int C, int nimg) {
     g.off_G = take(sizeof(unsigned long long) * (size_t)C * C * nimg);
     g.off_D = take(sizeof(unsigned long long) * (size_t)kSlices * C * nimg);
     g.total = o;
-    g.smem = 1024 + 4 * (size_t)kBlockBytes + 4 * (size_t)kStageBytes + 128 + sizeof(int) * kSlices * kTB +
-             sizeof(unsigned long long) * kTB;
+    g.smem = 1024 + 4 * (size_t)kBlockBytes + 4 * (size_t)kStageBytes + 128 + sizeof(int) * (kSlices + 1) * kThreads;
     return g;
 }
 
@@ -581,6 +664,10 @@ cudaError_t launch_gram_cov_jobs(const FitJob *jobs, int n, int layout, int C, d
         long chunk = (total_px * g.n_pairs + target - 1) / target;
         chunk = (chunk + kWin - 1) / kWin * kWin;
         if (chunk < kWin) chunk = kWin;
+        // a thread's int32 counters see chunk / 4 pixels: at most 2^16 x 3 * 2^12 level-4 terms
+        if (chunk > (1L << 18)) chunk = 1L << 18;
+        // all images' off-diagonal tile pairs first (each converts two channel blocks and
+        // issues all ten digit products, the longest CTAs), then the diagonal tiles
         long cta = 0;
         for (int i = 0; i < m; i++) {
             const FitJob &j = jobs[i0 + i];
@@ -588,7 +675,12 @@ cudaError_t launch_gram_cov_jobs(const FitJob *jobs, int n, int layout, int C, d
             im.X = j.X, im.N = j.N, im.chunk = chunk;
             im.n_split = (int)((j.N + chunk - 1) / chunk);
             im.cta0 = cta;
-            cta += (long)im.n_split * g.n_pairs;
+            cta += (long)im.n_split * (g.n_pairs - g.nt);
+        }
+        p.diag_start = cta;
+        for (int i = 0; i < m; i++) {
+            p.img[i].cta0d = cta;
+            cta += (long)p.img[i].n_split * g.nt;
         }
         unsigned *am = amax + (size_t)i0 * C;
         float *sc = scale + (size_t)i0 * C;

@@ -66,3 +66,26 @@ def test_digit_gram_within_bound(seed, C, N):
     ref = np.cov(Xd, bias=True)
     bound = 2.0 ** -25 * np.outer(Rr, Rr)
     assert (np.abs(Sigma - ref) <= bound).all(), (np.abs(Sigma - ref) / bound).max()
+
+
+@pytest.mark.parametrize("seed,C,N", [(3, 9, 1500), (4, 16, 640)])
+def test_symmetric_form_of_a_diagonal_tile(seed, C, N):
+    """A diagonal tile (the block against itself) keeps only the symmetric part of the
+    level sums: Y_L = sum over i <= j, i + j = L of c_ij D_i D_j^T with c_ij = 1 (i < j)
+    and 1/2 (i = j); then Y_L + Y_L^T equals the full level sum exactly, and every
+    partial sum of Y_L over a 512-pixel window is a half-integer of magnitude <= 2^22
+    (exact in an FP32 accumulator, and twice it converts exactly to an integer)."""
+    rng = np.random.default_rng(seed)
+    X = (rng.standard_normal((C, N)) * 2.0 ** rng.uniform(-4, 4, C)[:, None]).astype(np.float32)
+    amax = np.abs(X).max(axis=1)
+    e = np.ceil(np.log2(amax * (1 + 2.0 ** -23))).astype(int)
+    D = digits(np.rint(X.astype(np.float64) * 2.0 ** (27 - e)[:, None]).astype(np.int64))
+    for L in range(4):
+        full = sum(D[i] @ D[L - i].T for i in range(L + 1))
+        # 2 Y_L in integers: 2 D_i D_j^T for i < j, D_i D_i^T for i = j
+        twoY = sum((1 if i == L - i else 2) * (D[i] @ D[L - i].T) for i in range(L + 1) if i <= L - i)
+        assert np.array_equal(twoY + twoY.T, 2 * full)
+        for p0 in range(0, N, 512):
+            sl = slice(p0, p0 + 512)
+            tw = sum((1 if i == L - i else 2) * (D[i][:, sl] @ D[L - i][:, sl].T) for i in range(L + 1) if i <= L - i)
+            assert np.abs(tw).max() <= 2 ** 23
