@@ -112,19 +112,6 @@ __device__ __forceinline__ void col_store(float *p, int n, int lane, const float
         if (i < n) p[(size_t)i * kXS] = r[q];
     }
 }
-// r -= (z_j . r) z_j for column j of the [n][32] eigenvectors of T.
-__device__ __forceinline__ void project_out_z(float (&r)[kQ], const float *Zg, int j, int n, int lane) {
-    float z[kQ], s = 0.0f;
-#pragma unroll
-    for (int q = 0; q < kQ; q++) {
-        const int i = lane + 32 * q;
-        z[q] = i < n ? Zg[(size_t)i * 32 + j] : 0.0f;
-        s = fmaf(z[q], r[q], s);
-    }
-    s = warp_sum_f(s);
-#pragma unroll
-    for (int q = 0; q < kQ; q++) r[q] = fmaf(-s, z[q], r[q]);
-}
 // r0, r1 <- (I - tau v v^T) r0, r1 for the reflector v stored in rows m0..n-1 of vk (vk[i],
 // i >= m0): two columns at once, so each entry of v is loaded once for both.
 __device__ __forceinline__ void reflect2(float (&r0)[kQ], float (&r1)[kQ], const float *vk, float tau, int m0, int n,
@@ -150,6 +137,20 @@ __device__ __forceinline__ void reflect2(float (&r0)[kQ], float (&r1)[kQ], const
         r0[q] = fmaf(-s0, v[q], r0[q]);
         r1[q] = fmaf(-s1, v[q], r1[q]);
     }
+}
+
+// r -= (z_j . r) z_j for column j of the [n][32] eigenvectors of T.
+__device__ __forceinline__ void project_out_z(float (&r)[kQ], const float *Zg, int j, int n, int lane) {
+    float z[kQ], s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kQ; q++) {
+        const int i = lane + 32 * q;
+        z[q] = i < n ? Zg[(size_t)i * 32 + j] : 0.0f;
+        s = fmaf(z[q], r[q], s);
+    }
+    s = warp_sum_f(s);
+#pragma unroll
+    for (int q = 0; q < kQ; q++) r[q] = fmaf(-s, z[q], r[q]);
 }
 // Number of eigenvalues of T below x (the signs of the LDL^T pivots of T - x I).
 // The approximate division (2 ulp) only perturbs pivots that are not near zero, and
@@ -186,8 +187,9 @@ __device__ void tri_solve_piv(const float *dg, const float *ed, int n, float sig
             p0 = s0, p1 = s1, p2 = s2, pb = sb, q0 = r0, q1 = r1, q2 = r2, qb = rb;
         }
         if (fabsf(p0) < tiny) p0 = p0 < 0.0f ? -tiny : tiny;
-        const float l = __fdividef(q0, p0);  // |l| <= 1 except at replaced pivots
-        u0[(size_t)i * 32 + j] = p0;
+        const float rp = __fdividef(1.0f, p0);
+        const float l = q0 * rp;  // |l| <= 1 except at replaced pivots
+        u0[(size_t)i * 32 + j] = rp;  // the pivot's reciprocal: back substitution multiplies
         u1[(size_t)i * 32 + j] = p1;
         u2[(size_t)i * 32 + j] = p2;
         b[(size_t)i * kXS] = pb;
@@ -198,12 +200,12 @@ __device__ void tri_solve_piv(const float *dg, const float *ed, int n, float sig
         rb = fmaf(-l, pb, qb);
     }
     if (fabsf(r0) < tiny) r0 = r0 < 0.0f ? -tiny : tiny;
-    // back substitution
+    // back substitution (u0 holds the pivots' reciprocals)
     float y2 = 0.0f, y1 = rb / r0;
     b[(size_t)(n - 1) * kXS] = y1;
     for (int i = n - 2; i >= 0; i--) {
-        const float y0 = __fdividef(b[(size_t)i * kXS] - u1[(size_t)i * 32 + j] * y1 - u2[(size_t)i * 32 + j] * y2,
-                                    u0[(size_t)i * 32 + j]);
+        const float y0 = (b[(size_t)i * kXS] - u1[(size_t)i * 32 + j] * y1 - u2[(size_t)i * 32 + j] * y2) *
+                         u0[(size_t)i * 32 + j];
         b[(size_t)i * kXS] = y0;
         y2 = y1;
         y1 = y0;
@@ -281,12 +283,13 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
         const int rb = j0 + warp + lane;
         const int S = n - j0 - warp > 0 ? (n - j0 - warp + 31) >> 5 : 0;  // columns of this warp
         if (S == 0) return;  // no column: nothing of this warp is read
+        // row groups q >= S lie below row n - 1 in every lane (rb + 32 S >= j0 + warp + 32 S >= n)
         float vq[kQ], pr[kQ], vcq[kQ], wq[kQ];
 #pragma unroll
         for (int q = 0; q < kQ; q++) {
             const int i = rb + 32 * q;
             vcq[q] = 0.0f, wq[q] = 0.0f, vq[q] = 0.0f, pr[q] = 0.0f;
-            if (i < n) {
+            if (q < S && i < n) {
                 if (UPD) {
                     vcq[q] = vc[i];
                     wq[q] = fmaf(-K, vcq[q], tau * pv[i]);
@@ -309,7 +312,7 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
 #pragma unroll
                 for (int q = s; q < kQ; q++) {
                     const int i = rb + 32 * q;
-                    if (i < n) {
+                    if (q < S && i < n) {
                         float a = col[i];
                         if (UPD) {
                             a = fmaf(-vcq[q], wj, fmaf(-wq[q], vj, a));
@@ -328,7 +331,7 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
 #pragma unroll
             for (int q = 0; q < kQ; q++) {
                 const int i = rb + 32 * q;
-                if (i < n) pw[warp * pws + i] = pr[q];
+                if (q < S && i < n) pw[warp * pws + i] = pr[q];
             }
         }
     };
@@ -375,7 +378,7 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
             const int wmax = min(kNW - 1, i - j0);
 #pragma unroll
             for (int m = 0; m < kNW / 4; m++) {
-                const int w = part + 4 * m;
+                const int w = (kNW / 4) * part + m;  // contiguous warp ranges: the four parts hit four bank groups
                 if (w <= wmax) t += pw[w * pws + i];
             }
             const float4 *c = reinterpret_cast<const float4 *>(dp + (i - j0) * 32 + part * 8);
@@ -468,10 +471,29 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
     const float tiny = tnorm * 0x1p-40f;
 
     // ---------------------------------------------------------------- 2. eigenvalues, eigenvectors of T
+    // a first round over the whole CTA: the Sturm count at np points of the Gershgorin interval
+    // (in the U panel, free until the inverse iteration: np = kT, fewer when the panel is
+    // smaller), so that every warp starts its own multisection from a bracket of 1/(np+1)
+    const float span = ghi - glo;
+    const float lo0 = glo - 1e-3f * span - 1e-30f, hi0 = ghi + 1e-3f * span + 1e-30f;
+    const int np = n * kXS < kT ? n * kXS : kT;
+    auto grid_x = [&](int m) { return lo0 + (hi0 - lo0) * (float)(m + 1) / (float)(np + 1); };
+    int *cnt0 = reinterpret_cast<int *>(U);
+    if (tid < np) cnt0[tid] = sturm32(dT, e2, n, grid_x(tid));
+    __syncthreads();
     if (warp < d) {  // warp t: the eigenvalue of ascending index n-1-t (multisection, 32 points per round)
         const int t = warp, target = n - 1 - t;
-        const float span = ghi - glo;
-        float lo = glo - 1e-3f * span - 1e-30f, hi = ghi + 1e-3f * span + 1e-30f;
+        // the first grid point whose count exceeds the target (lane l scans points 32 l .. 32 l + 31)
+        int first = np;
+        for (int m = 32 * lane; m < 32 * lane + 32 && m < np; m++) {
+            if (cnt0[m] > target) {
+                first = m;
+                break;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+        float lo = first > 0 ? grid_x(first - 1) : lo0, hi = first < np ? grid_x(first) : hi0;
         for (int round = 0; round < 16; round++) {
             const float x = lo + (hi - lo) * (float)(lane + 1) / 33.0f;
             const int c = sturm32(dT, e2, n, x);
@@ -540,29 +562,53 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
     __syncthreads();
 
     // ---------------------------------------------------------------- 3. Newton correction
-    // r = A x - sigma x (float-float; A's hi and lo parts, exact FP32 products), rounded into U
-    for (int i = warp; i < n; i += kNW) {
+    // r = A x - sigma x (float-float; A's hi and lo parts, exact FP32 products), rounded into U;
+    // rows i and i + 32 of a warp together, two columns of A per 16-byte load when n is even
+    // (the terms of each row are added in the same order either way)
+    const bool pairs = (n & 1) == 0;  // float2 rows start on 16-byte boundaries
+    auto acc_term = [](float &S, float &Cc, float a_hi, float a_lo, float xv) {
+        const float p = __fmul_rn(a_hi, xv);
+        float e = __fmaf_rn(a_hi, xv, -p);
+        e = __fmaf_rn(a_lo, xv, e);
+        const ff t = ffa::two_sum(S, p);
+        S = t.hi;
+        Cc = __fadd_rn(Cc, __fadd_rn(t.lo, e));
+    };
+    for (int i0 = warp; i0 < n; i0 += 2 * kNW) {
+        const int i1 = i0 + kNW < n ? i0 + kNW : i0;
         if (lane < d) {
-            const float2 *Ar = A + (size_t)i * n;
-            float S = 0.0f, Cc = 0.0f;
-            for (int l = 0; l < n; l++) {
-                const float2 av = Ar[l];
-                const float xv = X[(size_t)l * kXS + lane];
-                const float p = __fmul_rn(av.x, xv);
-                float e = __fmaf_rn(av.x, xv, -p);
-                e = __fmaf_rn(av.y, xv, e);
-                const ff t = ffa::two_sum(S, p);
-                S = t.hi;
-                Cc = __fadd_rn(Cc, __fadd_rn(t.lo, e));
+            const float2 *A0 = A + (size_t)i0 * n, *A1 = A + (size_t)i1 * n;
+            float S0 = 0.0f, C0 = 0.0f, S1 = 0.0f, C1 = 0.0f;
+            int l = 0;
+            if (pairs) {
+                for (; l < n; l += 2) {
+                    const float4 a0 = *reinterpret_cast<const float4 *>(A0 + l);
+                    const float4 a1 = *reinterpret_cast<const float4 *>(A1 + l);
+                    const float x0 = X[(size_t)l * kXS + lane], x1 = X[(size_t)(l + 1) * kXS + lane];
+                    acc_term(S0, C0, a0.x, a0.y, x0);
+                    acc_term(S1, C1, a1.x, a1.y, x0);
+                    acc_term(S0, C0, a0.z, a0.w, x1);
+                    acc_term(S1, C1, a1.z, a1.w, x1);
+                }
             }
-            const ff w = ffa::two_sum(S, Cc);  // A x, kept for the Rayleigh quotient
-            Wg[(size_t)i * 32 + lane] = make_float2(w.hi, w.lo);
-            // minus sigma x (the product exact as a pair)
-            const float xi = X[(size_t)i * kXS + lane], sg = lamv[lane];
-            const float p = __fmul_rn(sg, xi);
-            const float e = __fmaf_rn(sg, xi, -p);
-            const ff t = ffa::two_sum(S, -p);
-            U[(size_t)i * kXS + lane] = __fadd_rn(t.hi, __fadd_rn(Cc, __fsub_rn(t.lo, e)));
+            for (; l < n; l++) {
+                const float xv = X[(size_t)l * kXS + lane];
+                acc_term(S0, C0, A0[l].x, A0[l].y, xv);
+                acc_term(S1, C1, A1[l].x, A1[l].y, xv);
+            }
+            for (int h = 0; h < 2; h++) {
+                const int i = h ? i1 : i0;
+                if (h && i1 == i0) break;
+                const float S = h ? S1 : S0, Cc = h ? C1 : C0;
+                const ff w = ffa::two_sum(S, Cc);  // A x, kept for the Rayleigh quotient
+                Wg[(size_t)i * 32 + lane] = make_float2(w.hi, w.lo);
+                // minus sigma x (the product exact as a pair)
+                const float xi = X[(size_t)i * kXS + lane], sg = lamv[lane];
+                const float p = __fmul_rn(sg, xi);
+                const float e = __fmaf_rn(sg, xi, -p);
+                const ff t = ffa::two_sum(S, -p);
+                U[(size_t)i * kXS + lane] = __fadd_rn(t.hi, __fadd_rn(Cc, __fsub_rn(t.lo, e)));
+            }
         }
     }
     __syncthreads();
@@ -609,12 +655,28 @@ __global__ void __launch_bounds__(kT, 1) k_eig32(Eig32Args a) {
     // far below the residual tolerance); the reflectors are no longer needed, so A delta
     // goes where the packed triangle was
     float *G = Ap;  // [n][kXS]
-    for (int i = warp; i < n; i += kNW) {
+    for (int i0 = warp; i0 < n; i0 += 2 * kNW) {
+        const int i1 = i0 + kNW < n ? i0 + kNW : i0;
         if (lane < d) {
-            const float2 *Ar = A + (size_t)i * n;
-            float g = 0.0f;
-            for (int l = 0; l < n; l++) g = fmaf(Ar[l].x, U[(size_t)l * kXS + lane], g);
-            G[(size_t)i * kXS + lane] = g;
+            const float2 *A0 = A + (size_t)i0 * n, *A1 = A + (size_t)i1 * n;
+            float g0 = 0.0f, g1 = 0.0f;
+            int l = 0;
+            if (pairs) {
+                for (; l < n; l += 2) {
+                    const float4 a0 = *reinterpret_cast<const float4 *>(A0 + l);
+                    const float4 a1 = *reinterpret_cast<const float4 *>(A1 + l);
+                    const float u0 = U[(size_t)l * kXS + lane], u1 = U[(size_t)(l + 1) * kXS + lane];
+                    g0 = fmaf(a0.z, u1, fmaf(a0.x, u0, g0));
+                    g1 = fmaf(a1.z, u1, fmaf(a1.x, u0, g1));
+                }
+            }
+            for (; l < n; l++) {
+                const float u = U[(size_t)l * kXS + lane];
+                g0 = fmaf(A0[l].x, u, g0);
+                g1 = fmaf(A1[l].x, u, g1);
+            }
+            G[(size_t)i0 * kXS + lane] = g0;
+            if (i1 != i0) G[(size_t)i1 * kXS + lane] = g1;
         }
     }
     __syncthreads();
