@@ -252,11 +252,21 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ S
                     if (KB > 0 && sizeof(ACC) == 4) {
                         // 32-bit walk: a = cumP_b N_ref accumulated directly, D += |a - c| in one
                         // sum-of-absolute-difference instruction
+                        // the reference terms four at a time (16-byte broadcast loads)
+                        const uint4 *c4 = reinterpret_cast<const uint4 *>(cRi);
                         uint32_t a = 0, D32 = 0;
 #pragma unroll
-                        for (int b = 0; b < KB - 1; b++) {
-                            a += hb[b * SW] * Nref;
-                            D32 = __usad(a, (uint32_t)cRi[b], D32);
+                        for (int b4 = 0; b4 < KB / 4; b4++) {
+                            const uint4 c = c4[b4];
+                            const uint32_t cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                            for (int e = 0; e < 4; e++) {
+                                const int b = 4 * b4 + e;
+                                if (b < KB - 1) {
+                                    a += hb[b * SW] * Nref;
+                                    D32 = __usad(a, cv[e], D32);
+                                }
+                            }
                         }
                         D = (ACC)D32;
                     } else if (KB > 0) {
