@@ -1090,6 +1090,8 @@ def run_ours(args):
                           join=lambda: pipe.join(main))
     clocks = sampler.stop(t_region0, time.time())
     tiling_used = pipe.ctx[0].last_tiling()
+    walk_used = pipe.ctx[0].last_cdf_walk()
+    run_used = pipe.ctx[0].last_band_run()
     proj_used = pipe.ctx[0].last_projection_tiling()
     dom_ms, dom_n = 0.0, 0
     for c in pipe.ctx:
@@ -1247,9 +1249,11 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
             "data": "synthetic (seeded Gaussian random fields with planted anomalies)",
             "config": {"workload": WORKLOAD, "images_per_rank_step": N_IMG, "H": HW, "W": HW, "C": C, "d": D,
-                       "B": B, "r": R, "projection": args.precision, "fit": "exact integer Gram + float-float eig",
+                       "B": B, "r": R, "projection": args.precision, "fit": "exact integer Gram + FP32 eigensolver with a float-float Newton correction",
                        "window_tiling": "autotuned (measured once during warm-up): strip x band x groups = "
-                                        + "x".join(str(v) for v in tiling_used),
+                                        + "x".join(str(v) for v in tiling_used)
+                                        + f", {run_used} band(s) per CTA"
+                                        + (", warp-shuffle CDF walk" if walk_used == 1 else ", per-thread CDF walk"),
                        "projection_rings": "autotuned: FP32 boxes in flight x operand chunks = "
                                            + "x".join(str(v) for v in proj_used),
                        "path": f"qfca_batch_run, CUDA graph, {args.pipes} steps in flight" if not args.no_graph

@@ -407,6 +407,39 @@ qfca_status qfca_set_tiling(qfca_ctx *ctx, int strip_width, int band_height, int
  * strip width (threads), band height (rows), component groups. */
 qfca_status qfca_last_tiling(qfca_ctx *ctx, int *strip_width, int *band_height, int *component_groups);
 
+/* The CDF walk of the window stage: the per-pixel sum over bins of
+ * |cumP_b N_ref - cumR_b N_loc| (the W1 closed form of the supplement applied
+ * to the histograms of Sec. 3.1).
+ *   walk -1  default: the autotuner measures both walks where both exist and
+ *            keeps the faster; without autotuning the per-thread walk runs;
+ *         0  per thread: each thread walks the B bins of its own pixel in order;
+ *         1  warp-shuffle segmented: two lanes per pixel walk 16 bins each, the
+ *            lower half's count reaches the upper lane by a shuffle as its CDF
+ *            offset and the partial sums are added by shuffles.  It exists for
+ *            B = 32 with 32-bit numerators ((B-1)(2r+1)^2 N_ref < 2^32); other
+ *            calls run the per-thread walk.
+ * Applies to later score launches of the context, with a tiling set by
+ * qfca_set_tiling or the cost model's.  The numerators are exact integers, so
+ * results do not depend on the walk.  QFCA_ERR_INVALID_ARG outside [-1, 1]. */
+qfca_status qfca_set_cdf_walk(qfca_ctx *ctx, int walk);
+
+/* The CDF walk (0 per thread, 1 warp-shuffle) of the context's most recent
+ * score launch. */
+qfca_status qfca_last_cdf_walk(qfca_ctx *ctx, int *walk);
+
+/* Bands per CTA of a tiling set by qfca_set_tiling: each CTA then takes a run
+ * of that many consecutive bands of its strip and component group, and the
+ * window histograms of Sec. 3.1 slide on from one band into the next (only the
+ * first band of a run builds its windows from scratch), while the next band's
+ * tile is fetched.  bands = 1 (default) is one band per CTA, 0 every band of
+ * the strip.  With one component group (the fused form) a CTA takes one band.
+ * The cost model and the autotuner choose the run themselves.  Results do not
+ * depend on it.  QFCA_ERR_INVALID_ARG outside [0, 4096]. */
+qfca_status qfca_set_band_run(qfca_ctx *ctx, int bands);
+
+/* The bands per CTA of the context's most recent score launch. */
+qfca_status qfca_last_band_run(qfca_ctx *ctx, int *bands);
+
 /* qfca_score_noalloc -- the same computation as qfca_score (without the
  * optional numerator output), for callers that cannot allocate device memory:
  * code that runs under a host application or memory manager that owns every

@@ -129,6 +129,8 @@ struct qfca_ctx {
     std::map<std::string, qfca::ScoreTiling> tuned;     // measured tilings per shape set
     qfca::ScoreTiling last_tiling{0, 0, 0};
     qfca::ScoreTiling forced{0, 0, 0};                  // window-stage tiling set by the caller (SW 0: none)
+    int walk_mode = -1;                                 // CDF walk: -1 the autotuner's choice (else per thread), 0, 1
+    int band_run = 1;                                   // bands per CTA of a forced tiling (0: a strip's every band)
     std::map<std::string, qfca::ProjTiling> proj_tuned; // measured projection ring depths per shape set
     qfca::ProjTiling last_proj{0, 0};
     float eig_tol = qfca::kEigTolDefault;               // residual bound of the FP32 + Newton eigensolver
@@ -246,9 +248,15 @@ qfca_status run_score(qfca_ctx *ctx, const ScoreJob *jobs, int n, int d, int B, 
     ScoreTiling chosen{0, 0, 0};
     if (ctx->forced.SW > 0) {
         chosen = ctx->forced;
+        chosen.walk = std::max(ctx->walk_mode, 0);
+        chosen.bands = ctx->band_run;
+        use = &chosen;
+    } else if (ctx->walk_mode >= 0 && !ctx->autotune) {
+        chosen = ScoreTiling{0, 0, 0, ctx->walk_mode};  // the cost model's tiling with this walk
         use = &chosen;
     } else if (ctx->autotune) {
-        std::string key = std::to_string(n) + ":" + std::to_string(d) + ":" + std::to_string(B);
+        std::string key = std::to_string(n) + ":" + std::to_string(d) + ":" + std::to_string(B) + ":w" +
+                          std::to_string(ctx->walk_mode);
         for (int i = 0; i < n; i++)
             key += ":" + std::to_string(jobs[i].H) + "x" + std::to_string(jobs[i].W) + "r" + std::to_string(jobs[i].r);
         auto it = ctx->tuned.find(key);
@@ -263,17 +271,25 @@ qfca_status run_score(qfca_ctx *ctx, const ScoreJob *jobs, int n, int d, int B, 
             ScoreTiling best{0, 0, 0};
             std::vector<ScoreTiling> cands;
             ScoreTiling model{0, 0, 0};
-            cudaError_t e = launch_score_jobs(jobs, n, d, B, ws, false, ctx->status_dev, st, nullptr, &model);
+            const ScoreTiling model_walk{0, 0, 0, std::max(ctx->walk_mode, 0)};
+            cudaError_t e = launch_score_jobs(jobs, n, d, B, ws, false, ctx->status_dev, st, &model_walk, &model);
             if (e != cudaSuccess) {
                 cudaEventDestroy(a), cudaEventDestroy(b);
                 return e == cudaErrorNotSupported ? fail(ctx, QFCA_ERR_UNSUPPORTED, "%s: no tiling fits", where)
                                                   : cuda_fail(ctx, e, where);
             }
             cands.push_back(model);
-            for (int SW : {128, 64})
-                for (int TH : {8, 16, 32, 64})
-                    for (int nk : {1, 2, 4, 8, 16, 32})
-                        if (nk <= d) cands.push_back(ScoreTiling{SW, TH, nk});
+            // both CDF walks where the shuffle walk exists (B = 32), unless the caller fixed one
+            std::vector<int> walks;
+            if (ctx->walk_mode >= 0) walks.push_back(ctx->walk_mode);
+            else walks = B == 32 ? std::vector<int>{0, 1} : std::vector<int>{0};
+            // band runs of 1, 4 or every band of a strip (a fused tiling, one group, takes one band)
+            for (int w : walks)
+                for (int SW : {128, 64})
+                    for (int TH : {8, 16, 32, 64})
+                        for (int nk : {1, 2, 4, 8, 16, 32})
+                            for (int br : {1, 4, 0})
+                                if (nk <= d && (nk > 1 || br == 1)) cands.push_back(ScoreTiling{SW, TH, nk, w, br});
             for (const ScoreTiling &c : cands) {
                 float tot = 0.0f;
                 bool okc = true;
@@ -540,8 +556,11 @@ qfca_status qfca_score(qfca_ctx *ctx, const uint8_t *bins, int H, int W, int pit
     HookScope hs(ctx);
     const ScoreJob job{bins, H, W, pitch, r, ref_hist, ref_total, score, numer_out, lo, hi};
     if ((s = ensure_ws(ctx, score_jobs_workspace_bytes(&job, 1, d), (cudaStream_t)stream))) return s;
-    cudaError_t e = launch_score_jobs(&job, 1, d, B, ctx->ws, false, ctx->status_dev, (cudaStream_t)stream,
-                                      ctx->forced.SW > 0 ? &ctx->forced : nullptr, &ctx->last_tiling);
+    // the caller's tiling (or the cost model's) with the context's CDF walk
+    const ScoreTiling tl{ctx->forced.SW, ctx->forced.TH, ctx->forced.n_kg, std::max(ctx->walk_mode, 0),
+                         ctx->band_run};
+    cudaError_t e = launch_score_jobs(&job, 1, d, B, ctx->ws, false, ctx->status_dev, (cudaStream_t)stream, &tl,
+                                      &ctx->last_tiling);
     if (e == cudaErrorNotSupported)
         return fail(ctx, QFCA_ERR_UNSUPPORTED, "B = %d with r = %d needs more shared memory than a CTA has", B, r);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_score");
@@ -960,6 +979,36 @@ qfca_status qfca_set_tiling(qfca_ctx *ctx, int strip_width, int band_height, int
         return fail(ctx, QFCA_ERR_INVALID_ARG, "tiling %d x %d x %d", strip_width, band_height, component_groups);
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->forced = ScoreTiling{strip_width, band_height, component_groups};
+    return QFCA_OK;
+}
+
+qfca_status qfca_set_cdf_walk(qfca_ctx *ctx, int walk) {
+    if (!ctx) return QFCA_ERR_INVALID_ARG;
+    if (walk < -1 || walk > 1) return fail(ctx, QFCA_ERR_INVALID_ARG, "CDF walk %d outside [-1, 1]", walk);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->walk_mode = walk;
+    return QFCA_OK;
+}
+
+qfca_status qfca_set_band_run(qfca_ctx *ctx, int bands) {
+    if (!ctx) return QFCA_ERR_INVALID_ARG;
+    if (bands < 0 || bands > 4096) return fail(ctx, QFCA_ERR_INVALID_ARG, "band run %d outside [0, 4096]", bands);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->band_run = bands;
+    return QFCA_OK;
+}
+
+qfca_status qfca_last_band_run(qfca_ctx *ctx, int *bands) {
+    if (!ctx || !bands) return QFCA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    *bands = ctx->last_tiling.bands;
+    return QFCA_OK;
+}
+
+qfca_status qfca_last_cdf_walk(qfca_ctx *ctx, int *walk) {
+    if (!ctx || !walk) return QFCA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    *walk = ctx->last_tiling.walk;
     return QFCA_OK;
 }
 

@@ -202,6 +202,8 @@ struct ScoreJob {
 // height TH (1..64 rows) and number of component groups n_kg.
 struct ScoreTiling {
     int SW, TH, n_kg;
+    int walk;   // CDF walk of the interior pixels: 0 per thread, 1 warp-shuffle segmented (B = 32, u32 walk only)
+    int bands;  // bands per CTA (a run of consecutive bands; the window carries over): 0 = every band of a strip
 };
 
 // Workspace of launch_score_jobs: the numerators D_k(p) of every job (or, when

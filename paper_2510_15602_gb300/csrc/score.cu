@@ -31,7 +31,6 @@
 namespace qfca {
 namespace {
 
-constexpr int kMaxSW = 128;  // strip width limit (threads per CTA)
 constexpr uint32_t kTmaTries = 1u << 26;
 
 // Per-image part of a window-EMD launch (kernel parameter block).
@@ -47,6 +46,7 @@ struct ScoreImgP {
 
 struct ScoreParams {
     int n, d, B, SW, TH, kg, n_kg;
+    int BR;                     // bands per CTA: a run of consecutive bands of one strip and component group
     uint32_t tile_bytes;
     uint32_t first_wait_tries;  // probes of each CTA's first tile wait (kTmaTries; fewer only to test the timeout path)
     int fuse;                   // every CTA holds all d components: sum them per pixel in shared memory, write the score
@@ -74,9 +74,12 @@ constexpr int kFinMaxWeights = 512;  // components whose bin widths a value-unit
 
 __host__ __device__ inline int halo_of(int r) { return (r + 15) & ~15; }
 __host__ __device__ inline int tcp_of(int SW, int r) { return SW + 2 * halo_of(r); }
+// Rows of a band's tile: the band's TH rows, r above and below, and one more above (the row that leaves
+// the window when the band's first row continues the previous band's last window).
+__host__ __device__ inline int tile_rows(int TH, int r) { return TH + 2 * r + 1; }
 
 size_t score_smem_core(int SW, int TH, int B, int rmax) {
-    const size_t tile = align_up((size_t)(TH + 2 * rmax) * tcp_of(SW, rmax), 128);
+    const size_t tile = align_up((size_t)tile_rows(TH, rmax) * tcp_of(SW, rmax), 128);
     return 2 * tile + sizeof(uint32_t) * (size_t)(B + 1) * SW + sizeof(uint32_t) * 256 + sizeof(uint64_t) * 256 +
            2 * sizeof(uint64_t);
 }
@@ -85,21 +88,85 @@ size_t score_smem(int SW, int TH, int B, int rmax, bool fuse = false) {
     return 128 + score_smem_core(SW, TH, B, rmax) + (fuse ? sizeof(uint64_t) * (size_t)TH * SW : 0);
 }
 
-// Window histograms + exact EMD numerators for a band of TH rows x SW columns
+// 32-bit shared-memory address of a pointer into shared memory, and the
+// fire-and-forget increment of a window count there.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void count_add(uint32_t addr, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// The window counts of one thread, bin-major (count of code v at hbase + v * 4 SWT): the span bytes
+// of a tile row from column c0 leave (rowo) or enter (rown) the window.  The row bytes come in as
+// 32-bit words (five words for a 15-pixel span instead of fifteen byte loads), aligned to c0 by a
+// funnel shift; each byte is extracted with one permute.  TWO = false: only rown, entering.
+template <int SWT, bool TWO>
+__device__ __forceinline__ void window_rows(const uint8_t *rowo, const uint8_t *rown, int c0, int span,
+                                            uint32_t hbase) {
+    constexpr int LOG = SWT == 128 ? 9 : 8;  // log2(4 SWT): bytes between consecutive codes' counts
+    const uint32_t *wo = reinterpret_cast<const uint32_t *>(rowo) + (c0 >> 2);
+    const uint32_t *wn = reinterpret_cast<const uint32_t *>(rown) + (c0 >> 2);
+    const uint32_t sh = (uint32_t)(c0 & 3) * 8u;
+    uint32_t lo_o = TWO ? wo[0] : 0u, lo_n = wn[0];
+    int q = 0;
+    for (; q + 4 <= span; q += 4) {
+        const uint32_t hi_n = wn[(q >> 2) + 1];
+        const uint32_t an = __funnelshift_r(lo_n, hi_n, sh);
+        lo_n = hi_n;
+        uint32_t ao = 0;
+        if (TWO) {
+            const uint32_t hi_o = wo[(q >> 2) + 1];
+            ao = __funnelshift_r(lo_o, hi_o, sh);
+            lo_o = hi_o;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            if (TWO) count_add(hbase + (__byte_perm(ao, 0u, 0x4440u + e) << LOG), 0xFFFFFFFFu);
+            count_add(hbase + (__byte_perm(an, 0u, 0x4440u + e) << LOG), 1u);
+        }
+    }
+    if (q < span) {  // 1..3 bytes left (span is odd)
+        const uint32_t an = __funnelshift_r(lo_n, wn[(q >> 2) + 1], sh);
+        uint32_t ao = 0;
+        if (TWO) ao = __funnelshift_r(lo_o, wo[(q >> 2) + 1], sh);
+#pragma unroll
+        for (int e = 0; e < 3; e++)
+            if (q + e < span) {
+                if (TWO) count_add(hbase + (__byte_perm(ao, 0u, 0x4440u + e) << LOG), 0xFFFFFFFFu);
+                count_add(hbase + (__byte_perm(an, 0u, 0x4440u + e) << LOG), 1u);
+            }
+    }
+}
+
+// Window histograms + exact EMD numerators for a band of TH rows x SWT columns
 // and a group of kg components of one image of the table.  Thread t owns
-// output column x0 + t; its window histogram lives at hist[b * SW + t].
-// Increments are shared-memory atomics without return, so no thread waits on
-// them.  ACC is the type of the CDF walk (u32 when (B-1)(2r+1)^2 N_ref < 2^32
-// for every image), OUT the type of the stored numerators; KB > 0 fixes B at
-// compile time.  The band's bin tile of each component (rows y0-r ..
-// y0+TH-1+r, columns from x0 - halo, halo = r rounded up to 16 bytes) is one
-// 3-D TMA box; boxes are double-buffered so the next component's tile arrives
-// while the current one is processed.  Waits are bounded; a wait that runs out
-// sets bit 0 of the status word and the CTA stops.
-template <typename ACC, typename OUT, int KB>
-__global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ ScoreParams p, int *__restrict__ status) {
+// output column x0 + t; its window histogram lives at hist[b * SWT + t]
+// (conflict-free for any bins the warp's threads touch).  Increments are
+// shared-memory reductions without return, so no thread waits on them.  ACC
+// is the type of the CDF walk (u32 when (B-1)(2r+1)^2 N_ref < 2^32 for every
+// image), OUT the type of the stored numerators; KB > 0 fixes B at compile
+// time; SWT is the strip width (64 or 128 threads), so every histogram address
+// is a constant offset from the thread's column.  The band's bin tile of each
+// component (rows y0-r .. y0+TH-1+r, columns from x0 - halo, halo = r rounded
+// up to 16 bytes) is one 3-D TMA box; boxes are double-buffered so the next
+// component's tile arrives while the current one is processed.  Waits are
+// bounded; a wait that runs out sets bit 0 of the status word and the CTA
+// stops.
+//
+// WALK selects the CDF walk of the interior pixels (the border pixels always
+// take the per-thread walk):
+//   0  per thread, sequential over the bins of its own pixel (with KB = 32 the
+//      interior reference terms cumR_b N_loc are held in registers);
+//   1  warp-shuffle segmented walk (KB = 32, u32 only): two lanes per pixel,
+//      each walks 16 bins of it; the lower lane's count reaches the upper lane
+//      by a shuffle as its CDF offset, the two partial sums are added by a
+//      shuffle, and the owner lane of the pixel receives the result by a
+//      third; 16 pixels per pass, two passes per row.
+template <typename ACC, typename OUT, int KB, int SWT, int WALK>
+__global__ void __launch_bounds__(SWT) k_window_emd(const __grid_constant__ ScoreParams p, int *__restrict__ status) {
+    static_assert(WALK == 0 || (KB == 32 && sizeof(ACC) == 4), "the shuffle walk is built for 32 bins, u32");
     const int B = KB > 0 ? KB : p.B;
-    const int SW = p.SW, TH = p.TH, d = p.d;
+    const int TH = p.TH, d = p.d;
+    constexpr int SW = SWT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *smem = tc::align_smem<128>(smem_raw);
     uint8_t *tiles = smem;
@@ -119,56 +186,70 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ S
     long local = cta - im.cta0;
     const int kgi = (int)(local % p.n_kg);
     local /= p.n_kg;
-    const int bx = (int)(local % im.nbx), by = (int)(local / im.nbx);
+    const int bx = (int)(local % im.nbx), brun = (int)(local / im.nbx);
+    const int nby = (H + TH - 1) / TH;
+    const int b_lo = brun * p.BR, nb = min(nby, b_lo + p.BR) - b_lo;  // this CTA's bands
     const int k0 = kgi * p.kg, k1 = min(d, k0 + p.kg);
+    const int nitems = (k1 - k0) * nb;  // (component, band) pairs, component-major
     const uint32_t Nref = im.Nref;
     const uint32_t *ref_hist = im.ref;
     const long HW = (long)H * W;
 
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = SW >> 5;
-    const int x0 = bx * SW, y0 = by * TH;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int nwarps = SW >> 5;
+    const int x0 = bx * SW;
     const int x = x0 + t;
-    const int halo = halo_of(r), TCp = SW + 2 * halo, TR = TH + 2 * r;
-    const int ty0 = y0 - r, tx0 = x0 - halo;  // image coordinates of the tile origin
+    const int halo = halo_of(r), TCp = SW + 2 * halo, TR = tile_rows(TH, r);
+    const int tx0 = x0 - halo;  // image column of the tile origin; its row is band * TH - r - 1
     const int span = 2 * r + 1;
     const uint32_t Nint = (uint32_t)(span * span);
     const uint32_t box_bytes = (uint32_t)(TR * TCp);
     const int wpr = TCp >> 2;  // 32-bit words per tile row
-    const bool inner = tx0 >= 0 && tx0 + TCp <= W && ty0 >= 0 && ty0 + TR <= H;
     if (t == 0) {
         tc::mbar_init(&bar[0], 1);
         tc::mbar_init(&bar[1], 1);
         tc::fence_mbar_init();
     }
     __syncthreads();
-    if (t == 0 && k0 < k1) {
+    if (t == 0 && nitems > 0) {
         tc::mbar_arrive_expect_tx(&bar[0], box_bytes);
-        tc::tma_load_3d(tiles, tmap, tx0, ty0, k0, &bar[0]);
+        tc::tma_load_3d(tiles, tmap, tx0, b_lo * TH - r - 1, k0, &bar[0]);
     }
     bool failed = false;
-    int issued = k0 < k1 ? 1 : 0, waited = 0;
+    int issued = nitems > 0 ? 1 : 0, waited = 0;
 
     const int ncols = min(W - 1, x + r) - max(0, x - r) + 1;
     const int c0 = t + halo - r;  // tile column of this thread's window's left edge
     uint32_t *hc = hist + t;
-    for (int k = k0; k < k1; k++) {
-        __syncthreads();  // the buffer of component k-1 is free again
-        const int buf = (k - k0) & 1;
-        if (t == 0 && k + 1 < k1) {
+    const uint32_t hbase = smem_addr(hc);
+    // the shuffle walk: this lane's pixel (column of the warp) in pass 0 / 1, and its half of the bins
+    const int wp0 = lane >> 1, wg = lane & 1;
+    // interior reference terms in registers (per-thread walk: all 31; shuffle walk: this lane's half)
+    constexpr int NREG = (KB == 32 && sizeof(ACC) == 4) ? (WALK == 1 ? 16 : 31) : 1;
+    uint32_t cr[NREG];
+    for (int it = 0; it < nitems; it++) {
+        const int k = k0 + it / nb, bi = it - (it / nb) * nb;
+        const int y0 = (b_lo + bi) * TH, ty0 = y0 - r - 1;  // band origin; tile origin row
+        const bool fresh = bi == 0;                       // first band of component k: a new window
+        const bool inner = tx0 >= 0 && tx0 + TCp <= W && ty0 >= 0 && ty0 + TR <= H;
+        __syncthreads();  // the buffer of item it-1 is free again
+        const int buf = it & 1;
+        if (t == 0 && it + 1 < nitems) {
+            const int kn = k0 + (it + 1) / nb, bn = b_lo + (it + 1) % nb;
             tc::mbar_arrive_expect_tx(&bar[buf ^ 1], box_bytes);
-            tc::tma_load_3d(tiles + (size_t)(buf ^ 1) * p.tile_bytes, tmap, tx0, ty0, k + 1, &bar[buf ^ 1]);
+            tc::tma_load_3d(tiles + (size_t)(buf ^ 1) * p.tile_bytes, tmap, tx0, bn * TH - r - 1, kn, &bar[buf ^ 1]);
         }
-        if (k + 1 < k1) issued++;
+        if (it + 1 < nitems) issued++;
         // warp 0: lane l loads reference bins [8l, 8l+8) of component k (in flight during the wait)
         uint32_t rv[8];
-        if (t < 32) {
+        if (fresh && t < 32) {
 #pragma unroll
             for (int j = 0; j < 8; j++) {
                 const int b = 8 * t + j;
                 rv[j] = b < B ? __ldg(&ref_hist[(long)k * B + b]) : 0u;
             }
         }
-        const bool ok = tc::mbar_wait(&bar[buf], ((k - k0) >> 1) & 1, k == k0 ? p.first_wait_tries : kTmaTries);
+        const bool ok = tc::mbar_wait(&bar[buf], (it >> 1) & 1, it == 0 ? p.first_wait_tries : kTmaTries);
         waited++;
         if (__syncthreads_or(!ok)) {
             failed = true;
@@ -195,7 +276,7 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ S
                 }
             }
         }
-        if (t < 32) {  // whole warp 0: prefix sums of the reference histogram
+        if (fresh && t < 32) {  // whole warp 0: prefix sums of the reference histogram
             uint32_t part = 0;
 #pragma unroll
             for (int j = 0; j < 8; j++) part += rv[j];
@@ -216,91 +297,137 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ S
                 }
             }
         }
-        if (KB > 0) {
+        if (fresh) {
+            if (KB > 0) {
 #pragma unroll
-            for (int b = 0; b <= KB; b++) hc[b * SW] = 0;
-        } else {
-            for (int b = 0; b <= B; b++) hc[b * SW] = 0;
+                for (int b = 0; b <= KB; b++) hc[b * SW] = 0;
+            } else {
+                for (int b = 0; b <= B; b++) hc[b * SW] = 0;
+            }
         }
         __syncthreads();
-        if (x < W) {
-            // window of the band's first row: tile rows 0 .. 2r
-            for (int ry = 0; ry < span; ry++) {
-                const uint8_t *row = tile + ry * TCp + c0;
-#pragma unroll 4
-                for (int j = 0; j < span; j++) atomicAdd(hc + row[j] * SW, 1u);
+        if (fresh && KB == 32 && sizeof(ACC) == 4) {
+            const uint32_t *c32 = reinterpret_cast<const uint32_t *>(cRi);
+#pragma unroll
+            for (int j = 0; j < NREG; j++) {
+                const int b = WALK == 1 ? 16 * wg + j : j;
+                cr[j] = b < KB - 1 ? c32[b] : 0u;
             }
-            for (int i = 0; i < TH; i++) {
-                const int yy = y0 + i;
-                if (yy >= H) break;
-                if (i > 0) {
-                    const uint8_t *ro = tile + (i - 1) * TCp + c0;       // image row yy - r - 1
-                    const uint8_t *rn = tile + (i + 2 * r) * TCp + c0;   // image row yy + r
-#pragma unroll 4
-                    for (int j = 0; j < span; j++) {
-                        atomicSub(hc + ro[j] * SW, 1u);
-                        atomicAdd(hc + rn[j] * SW, 1u);
-                    }
-                }
-                const int nrows = min(H - 1, yy + r) - max(0, yy - r) + 1;
-                const uint32_t Nloc = (uint32_t)(nrows * ncols);
-                ACC D = 0;
-                uint32_t cnt = 0;
-                const uint32_t *hb = hc + SW;  // bin 0
-                // the last bin's term is 0 (both CDFs reach 1), so the walk stops at B-2
-                if (Nloc == Nint) {
-                    if (KB > 0 && sizeof(ACC) == 4) {
-                        // 32-bit walk: a = cumP_b N_ref accumulated directly, D += |a - c| in one
-                        // sum-of-absolute-difference instruction
-                        // the reference terms four at a time (16-byte broadcast loads)
-                        const uint4 *c4 = reinterpret_cast<const uint4 *>(cRi);
-                        uint32_t a = 0, D32 = 0;
+        }
+        const bool xin = x < W;
+        // window of the band's first row (tile rows 1 .. 2r+1), or the previous band's last window continued
+        if (fresh && xin)
+            for (int ry = 1; ry <= span; ry++) window_rows<SW, false>(nullptr, tile + ry * TCp, c0, span, hbase);
+        for (int i = 0; i < TH; i++) {
+            const int yy = y0 + i;
+            if (yy >= H) break;
+            if ((i > 0 || !fresh) && xin)  // image row yy - r - 1 (tile row i) leaves, row yy + r enters
+                window_rows<SW, true>(tile + i * TCp, tile + (i + span) * TCp, c0, span, hbase);
+            const int nrows = min(H - 1, yy + r) - max(0, yy - r) + 1;
+            const uint32_t Nloc = (uint32_t)(nrows * ncols);
+            ACC D = 0;
+            const uint32_t *hb = hc + SW;  // bin 0
+            bool walked = false;
+            if (WALK == 1) {
+                // every lane of the warp takes part (shuffles), so the test is warp-wide
+                __syncwarp();
+                if (__all_sync(0xffffffffu, !xin || Nloc == Nint)) {
+                    uint32_t Dp[2];
 #pragma unroll
-                        for (int b4 = 0; b4 < KB / 4; b4++) {
-                            const uint4 c = c4[b4];
-                            const uint32_t cv[4] = {c.x, c.y, c.z, c.w};
+                    for (int pass = 0; pass < 2; pass++) {
+                        const uint32_t *h2 = hist + SW + (warp << 5) + 16 * pass + wp0 + 16 * wg * SW;
+                        uint32_t hv[16], cnt = 0, s = 0;
 #pragma unroll
-                            for (int e = 0; e < 4; e++) {
-                                const int b = 4 * b4 + e;
-                                if (b < KB - 1) {
-                                    a += hb[b * SW] * Nref;
-                                    D32 = __usad(a, cv[e], D32);
-                                }
+                        for (int j = 0; j < 16; j++) {
+                            hv[j] = h2[j * SW];
+                            cnt += hv[j];  // this half's count
+                        }
+                        // the lower half's count is the upper half's CDF offset
+                        const uint32_t below = __shfl_xor_sync(0xffffffffu, cnt, 1);
+                        uint32_t a = wg ? below * Nref : 0u;
+#pragma unroll
+                        for (int j = 0; j < 16; j++) {
+                            if (16 * wg + j < KB - 1) {  // the last bin's term is 0
+                                a += hv[j] * Nref;
+                                s = __usad(a, cr[j], s);
                             }
                         }
-                        D = (ACC)D32;
-                    } else if (KB > 0) {
+                        Dp[pass] = s + __shfl_xor_sync(0xffffffffu, s, 1);
+                    }
+                    __syncwarp();  // every lane's reads of the counts precede the next row's updates
+                    // pixel `lane` was walked by lanes 2 lane, 2 lane + 1 (pass 0) or 2 (lane - 16) (pass 1)
+                    const uint32_t d0 = __shfl_sync(0xffffffffu, Dp[0], (2 * lane) & 31);
+                    const uint32_t d1 = __shfl_sync(0xffffffffu, Dp[1], (2 * lane) & 31);
+                    D = (ACC)(lane < 16 ? d0 : d1);
+                    walked = true;
+                }
+            }
+            if (!xin) continue;
+            // the last bin's term is 0 (both CDFs reach 1), so the walk stops at B-2
+            if (walked) {
+            } else if (Nloc == Nint) {
+                if (KB == 32 && sizeof(ACC) == 4 && WALK == 0) {
+                    // 32-bit walk: a = cumP_b N_ref accumulated directly, D += |a - c| in one
+                    // sum-of-absolute-difference instruction, c from registers
+                    uint32_t a = 0, D32 = 0;
 #pragma unroll
-                        for (int b = 0; b < KB - 1; b++) {
-                            cnt += hb[b * SW];
-                            const ACC a = (ACC)cnt * (ACC)Nref, c = cRi[b];
-                            D += max(a, c) - min(a, c);
-                        }
-                    } else {
-#pragma unroll 4
-                        for (int b = 0; b < B - 1; b++) {
-                            cnt += hb[b * SW];
-                            const ACC a = (ACC)cnt * (ACC)Nref, c = cRi[b];
-                            D += max(a, c) - min(a, c);
+                    for (int b = 0; b < KB - 1; b++) {
+                        a += hb[b * SW] * Nref;
+                        D32 = __usad(a, cr[WALK == 0 ? b : 0], D32);
+                    }
+                    D = (ACC)D32;
+                } else if (KB > 0 && sizeof(ACC) == 4) {
+                    // the reference terms four at a time (16-byte broadcast loads)
+                    const uint4 *c4 = reinterpret_cast<const uint4 *>(cRi);
+                    uint32_t a = 0, D32 = 0;
+#pragma unroll
+                    for (int b4 = 0; b4 < KB / 4; b4++) {
+                        const uint4 c = c4[b4];
+                        const uint32_t cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                        for (int e = 0; e < 4; e++) {
+                            const int b = 4 * b4 + e;
+                            if (b < KB - 1) {
+                                a += hb[b * SW] * Nref;
+                                D32 = __usad(a, cv[e], D32);
+                            }
                         }
                     }
+                    D = (ACC)D32;
+                } else if (KB > 0) {
+                    uint32_t cnt = 0;
+#pragma unroll
+                    for (int b = 0; b < KB - 1; b++) {
+                        cnt += hb[b * SW];
+                        const ACC a = (ACC)cnt * (ACC)Nref, c = cRi[b];
+                        D += max(a, c) - min(a, c);
+                    }
                 } else {
+                    uint32_t cnt = 0;
 #pragma unroll 4
                     for (int b = 0; b < B - 1; b++) {
                         cnt += hb[b * SW];
-                        const ACC a = (ACC)cnt * (ACC)Nref, c = (ACC)cumR[b] * (ACC)Nloc;
+                        const ACC a = (ACC)cnt * (ACC)Nref, c = cRi[b];
                         D += max(a, c) - min(a, c);
                     }
                 }
-                const long pix = (long)yy * W + x;
-                if (p.fuse) {
-                    unsigned long long &a = acc[i * SW + t];  // this thread's own column: no other thread touches it
-                    a = (k == k0 ? 0ull : a) + (unsigned long long)D;
-                } else if (im.accum) {
-                    atomicAdd(&im.accum[pix], (unsigned long long)D);
-                } else {
-                    reinterpret_cast<OUT *>(im.numer)[(long)k * HW + pix] = (OUT)D;
+            } else {
+                uint32_t cnt = 0;
+#pragma unroll 4
+                for (int b = 0; b < B - 1; b++) {
+                    cnt += hb[b * SW];
+                    const ACC a = (ACC)cnt * (ACC)Nref, c = (ACC)cumR[b] * (ACC)Nloc;
+                    D += max(a, c) - min(a, c);
                 }
+            }
+            const long pix = (long)yy * W + x;
+            if (p.fuse) {  // one band per CTA: item it is component k0 + it
+                unsigned long long &a = acc[i * SW + t];  // this thread's own column: no other thread touches it
+                a = (it == 0 ? 0ull : a) + (unsigned long long)D;
+            } else if (im.accum) {
+                atomicAdd(&im.accum[pix], (unsigned long long)D);
+            } else {
+                reinterpret_cast<OUT *>(im.numer)[(long)k * HW + pix] = (OUT)D;
             }
         }
         tc::fence_proxy_async_smem();  // this iteration's writes to the tile precede the next TMA write into it
@@ -309,8 +436,9 @@ __global__ void __launch_bounds__(kMaxSW) k_window_emd(const __grid_constant__ S
         if (t == 0) atomicOr(status, kStatusMmaTimeout);
         // let every issued copy (including the one whose wait ran out) land before the CTA leaves (bounded)
         for (int w = waited - 1; w < issued; w++) tc::mbar_wait(&bar[w & 1], (w >> 1) & 1, kTmaTries);
-    } else if (p.fuse && x < W) {
+    } else if (p.fuse && x < W && nitems > 0) {
         // s(p) = sum_k D_k(p) / (d N_loc N_ref): one division per pixel, no numerators leave the SM
+        const int y0 = b_lo * TH;
         for (int i = 0; i < TH; i++) {
             const int yy = y0 + i;
             if (yy >= H) break;
@@ -363,52 +491,74 @@ __global__ void __launch_bounds__(256) k_finalize(const __grid_constant__ FinPar
     im.score[q] = (float)((double)s / den);
 }
 
-template <typename ACC, typename OUT>
-void launch_emd_kb(int KB, long grid, size_t smem, int SW, cudaStream_t st, const ScoreParams &p, int *status) {
-    if (KB == 32)
-        QFCA_LAUNCH("k_window_emd", st, (k_window_emd<ACC, OUT, 32><<<(unsigned)grid, SW, smem, st>>>(p, status)));
-    else if (KB == 64)
-        QFCA_LAUNCH("k_window_emd", st, (k_window_emd<ACC, OUT, 64><<<(unsigned)grid, SW, smem, st>>>(p, status)));
-    else
-        QFCA_LAUNCH("k_window_emd", st, (k_window_emd<ACC, OUT, 0><<<(unsigned)grid, SW, smem, st>>>(p, status)));
+using EmdFn = void (*)(const ScoreParams, int *);
+
+// The instantiation of k_window_emd for B (32, 64 or any), strip width and CDF walk.
+template <typename ACC, typename OUT, int KB, int SWT>
+EmdFn emd_fn_walk(int walk) {
+    if constexpr (KB == 32 && sizeof(ACC) == 4) {
+        if (walk == 1) return k_window_emd<ACC, OUT, KB, SWT, 1>;
+    }
+    return k_window_emd<ACC, OUT, KB, SWT, 0>;
+}
+
+template <typename ACC, typename OUT, int KB>
+EmdFn emd_fn_sw(int SW, int walk) {
+    return SW == 128 ? emd_fn_walk<ACC, OUT, KB, 128>(walk) : emd_fn_walk<ACC, OUT, KB, 64>(walk);
 }
 
 template <typename ACC, typename OUT>
-cudaError_t emd_occupancy(int KB, size_t smem, int SW, int *per_sm) {
-    if (KB == 32) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_window_emd<ACC, OUT, 32>, SW, smem);
-    if (KB == 64) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_window_emd<ACC, OUT, 64>, SW, smem);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_window_emd<ACC, OUT, 0>, SW, smem);
+EmdFn emd_fn(int KB, int SW, int walk) {
+    if (KB == 32) return emd_fn_sw<ACC, OUT, 32>(SW, walk);
+    if (KB == 64) return emd_fn_sw<ACC, OUT, 64>(SW, walk);
+    return emd_fn_sw<ACC, OUT, 0>(SW, walk);
+}
+
+template <typename ACC, typename OUT>
+void launch_emd_kb(int KB, int walk, long grid, size_t smem, int SW, cudaStream_t st, const ScoreParams &p,
+                   int *status) {
+    const EmdFn fn = emd_fn<ACC, OUT>(KB, SW, walk);
+    QFCA_LAUNCH("k_window_emd", st, (fn<<<(unsigned)grid, SW, smem, st>>>(p, status)));
+}
+
+template <typename ACC, typename OUT>
+cudaError_t emd_occupancy(int KB, int walk, size_t smem, int SW, int *per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, emd_fn<ACC, OUT>(KB, SW, walk), SW, smem);
 }
 
 template <typename ACC, typename OUT>
 cudaError_t emd_set_smem_attr() {
-    cudaError_t e = cudaFuncSetAttribute(k_window_emd<ACC, OUT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_window_emd<ACC, OUT, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_window_emd<ACC, OUT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaSuccess;
+    for (int KB : {32, 64, 0})
+        for (int SW : {64, 128})
+            for (int walk : {0, 1})
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(emd_fn<ACC, OUT>(KB, SW, walk), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
     return e;
 }
 
 enum class EmdKind { U32_U32, U32_U64, U64_U64 };
 
-cudaError_t emd_occupancy_kind(EmdKind kind, int KB, size_t smem, int SW, int *per_sm) {
+cudaError_t emd_occupancy_kind(EmdKind kind, int KB, int walk, size_t smem, int SW, int *per_sm) {
     switch (kind) {
-    case EmdKind::U32_U32: return emd_occupancy<uint32_t, uint32_t>(KB, smem, SW, per_sm);
-    case EmdKind::U32_U64: return emd_occupancy<uint32_t, unsigned long long>(KB, smem, SW, per_sm);
-    default: return emd_occupancy<unsigned long long, unsigned long long>(KB, smem, SW, per_sm);
+    case EmdKind::U32_U32: return emd_occupancy<uint32_t, uint32_t>(KB, walk, smem, SW, per_sm);
+    case EmdKind::U32_U64: return emd_occupancy<uint32_t, unsigned long long>(KB, walk, smem, SW, per_sm);
+    default: return emd_occupancy<unsigned long long, unsigned long long>(KB, walk, smem, SW, per_sm);
     }
 }
 
-// Modelled cost (lane-instructions) of the CTAs of one image at a given tiling.
-double image_cost(int H, int W, int d, int B, int r, int SW, int TH, int kg, int n_kg) {
-    const int span = 2 * r + 1, TR = TH + 2 * r;
+// Modelled cost (lane-instructions) of the CTAs of one image at a given tiling: a band costs its rows
+// and its tile's rewrite; the first band of each run and component also builds a window from scratch.
+double image_cost(int H, int W, int d, int B, int r, int SW, int TH, int kg, int n_kg, int BR) {
+    const int span = 2 * r + 1, TR = tile_rows(TH, r);
     const double row = 2.0 * span * 3.0 + 4.0 * (B - 1) + 12.0;
-    const double setup = 3.0 * span * span + 6.0 * TR * tcp_of(SW, r) / (4.0 * SW) + 2.0 * B + 60.0;
-    const double ctas = (double)((W + SW - 1) / SW) * ((H + TH - 1) / TH) * n_kg;
+    const double band = 6.0 * TR * tcp_of(SW, r) / (4.0 * SW) + 40.0;
+    const double fresh = 3.0 * span * span + 2.0 * B + 40.0;
+    const int nby = (H + TH - 1) / TH, runs = (nby + BR - 1) / BR;
+    const double ctas = (double)((W + SW - 1) / SW) * runs * n_kg;
     (void)d;
-    return ctas * (kg * (TH * row + setup) + 200.0);
+    return ctas * (kg * ((double)BR * (TH * row + band) + fresh) + 200.0);
 }
 
 DeviceOnce g_attrs_emd;
@@ -451,52 +601,77 @@ cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, boo
     cudaError_t err = ensure_attrs(&n_sm);
     if (err != cudaSuccess) return err;
 
-    // tiling: the caller's, else the modelled best over strip widths, band heights and component splits
-    ScoreTiling best{0, 0, 0};
+    // tiling: the caller's, else the modelled best over strip widths, band heights, component splits and
+    // band runs (a fused tiling, one component group, keeps one band per CTA: its per-pixel sums cover one band)
+    auto fits = [&](int SW, int TH, bool fz) {
+        return score_smem(SW, TH, B, rmax, fz) <= 200 * 1024 && tcp_of(SW, rmax) <= 256 && tile_rows(TH, rmax) <= 256;
+    };
+    int max_nby = 1;
+    ScoreTiling best{0, 0, 0, 0, 0};
     if (tiling && tiling->SW > 0) {
         best = *tiling;
-        if (!(best.SW == 64 || best.SW == 128) || best.TH < 1 || best.TH > 64 || best.n_kg < 1) return cudaErrorNotSupported;
-        if (score_smem(best.SW, best.TH, B, rmax, can_fuse && best.n_kg == 1) > 200 * 1024 ||
-            tcp_of(best.SW, rmax) > 256 || best.TH + 2 * rmax > 256)
+        if (!(best.SW == 64 || best.SW == 128) || best.TH < 1 || best.TH > 64 || best.n_kg < 1 || best.bands < 0)
             return cudaErrorNotSupported;
+        if (best.walk < 0 || best.walk > 1) return cudaErrorNotSupported;
+        if (!fits(best.SW, best.TH, can_fuse && best.n_kg == 1)) return cudaErrorNotSupported;
     } else {
         double best_cost = 1e300;
         for (int SW : {128, 64})
             for (int TH : {16, 32, 64, 8}) {
-                if (score_smem(SW, TH, B, rmax) > 200 * 1024 || tcp_of(SW, rmax) > 256 || TH + 2 * rmax > 256) continue;
+                if (!fits(SW, TH, false)) continue;
                 long tiles = 0;
-                for (int i = 0; i < n; i++) tiles += (long)((jobs[i].W + SW - 1) / SW) * ((jobs[i].H + TH - 1) / TH);
+                int nby_max = 1;
+                for (int i = 0; i < n; i++) {
+                    tiles += (long)((jobs[i].W + SW - 1) / SW) * ((jobs[i].H + TH - 1) / TH);
+                    nby_max = std::max(nby_max, (jobs[i].H + TH - 1) / TH);
+                }
                 for (int nk = 1; nk <= d; nk++) {
                     const int kg = (d + nk - 1) / nk;
                     if ((d + kg - 1) / kg != nk) continue;  // same split as a smaller count
-                    const size_t smem = score_smem(SW, TH, B, rmax, can_fuse && nk == 1);
+                    const bool fz = can_fuse && nk == 1;
+                    const size_t smem = score_smem(SW, TH, B, rmax, fz);
                     if (smem > 200 * 1024) continue;
                     int per_sm = 0;
-                    err = emd_occupancy_kind(kind, KB, smem, SW, &per_sm);
+                    err = emd_occupancy_kind(kind, KB, 0, smem, SW, &per_sm);
                     if (err != cudaSuccess) return err;
                     if (per_sm < 1) continue;
                     const long slots = (long)per_sm * n_sm;
-                    double work = 0.0;
-                    for (int i = 0; i < n; i++) work += image_cost(jobs[i].H, jobs[i].W, d, B, jobs[i].r, SW, TH, kg, nk);
-                    const double ctas = (double)tiles * nk;
-                    const double waves = std::ceil(ctas / (double)slots);
-                    // per-CTA average cost times the waves, plus a penalty for a tail wave
-                    const double cost = waves * (work / ctas);
-                    if (cost < best_cost * 0.999) best_cost = cost, best = ScoreTiling{SW, TH, nk};
+                    for (int BR = 1; BR <= (fz ? 1 : nby_max); BR *= 2) {
+                        double work = 0.0;
+                        long ctas = 0;
+                        for (int i = 0; i < n; i++) {
+                            work += image_cost(jobs[i].H, jobs[i].W, d, B, jobs[i].r, SW, TH, kg, nk, BR);
+                            const int nby = (jobs[i].H + TH - 1) / TH;
+                            ctas += (long)((jobs[i].W + SW - 1) / SW) * ((nby + BR - 1) / BR) * nk;
+                        }
+                        (void)tiles;
+                        const double waves = std::ceil((double)ctas / (double)slots);
+                        // per-CTA average cost times the waves
+                        const double cost = waves * (work / (double)ctas);
+                        if (cost < best_cost * 0.999) best_cost = cost, best = ScoreTiling{SW, TH, nk, 0, BR};
+                    }
                 }
             }
         if (best.SW == 0) return cudaErrorNotSupported;  // nothing enqueued
+        best.walk = tiling ? tiling->walk : 0;  // a walk asked for without a tiling (strip width 0)
     }
-    if (chosen) *chosen = best;
-    const int SW = best.SW, TH = best.TH;
+    // the shuffle walk exists for B = 32 with the u32 walk; elsewhere the per-thread walk runs
+    if (best.walk == 1 && !(KB == 32 && kind != EmdKind::U64_U64)) best.walk = 0;
+    const int SW = best.SW, TH = best.TH, walk = best.walk;
     const int kg = (d + best.n_kg - 1) / best.n_kg, n_kg = (d + kg - 1) / kg;
     const bool fuse = can_fuse && n_kg == 1;
+    for (int i = 0; i < n; i++) max_nby = std::max(max_nby, (jobs[i].H + TH - 1) / TH);
+    // bands per CTA: 0 asks for whole columns (every band of a strip); a fused tiling takes one
+    int BR = best.bands <= 0 ? max_nby : std::min(best.bands, max_nby);
+    if (fuse) BR = 1;
+    best.bands = BR;
+    if (chosen) *chosen = best;
     const size_t smem = score_smem(SW, TH, B, rmax, fuse);
 
     ScoreParams p;
     memset(&p, 0, sizeof(p));
-    p.n = n, p.d = d, p.B = B, p.SW = SW, p.TH = TH, p.kg = kg, p.n_kg = n_kg;
-    p.tile_bytes = (uint32_t)align_up((size_t)(TH + 2 * rmax) * tcp_of(SW, rmax), 128);
+    p.n = n, p.d = d, p.B = B, p.SW = SW, p.TH = TH, p.kg = kg, p.n_kg = n_kg, p.BR = BR;
+    p.tile_bytes = (uint32_t)align_up((size_t)tile_rows(TH, rmax) * tcp_of(SW, rmax), 128);
     p.first_wait_tries = first_wait_tries;
     p.fuse = fuse ? 1 : 0;
     p.acc_off = (uint32_t)score_smem_core(SW, TH, B, rmax);
@@ -511,7 +686,8 @@ cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, boo
         ScoreImgP &im = p.img[i];
         im.H = j.H, im.W = j.W, im.r = j.r, im.nbx = (j.W + SW - 1) / SW;
         im.cta0 = cta;
-        cta += (long)im.nbx * ((j.H + TH - 1) / TH) * n_kg;
+        const int nby = (j.H + TH - 1) / TH;
+        cta += (long)im.nbx * ((nby + BR - 1) / BR) * n_kg;
         im.ref = j.ref, im.Nref = j.Nref;
         void *numer = nullptr;
         unsigned long long *accum = nullptr;
@@ -526,7 +702,7 @@ cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, boo
         }
         im.numer = numer, im.accum = accum, im.score = j.score;
         err = make_tmap_u8_3d(&p.tmap[i], j.bins, (uint64_t)j.pitch, (uint64_t)j.H, (uint64_t)d, (uint64_t)j.pitch,
-                              (uint64_t)j.H * j.pitch, (uint32_t)tcp_of(SW, j.r), (uint32_t)(TH + 2 * j.r));
+                              (uint64_t)j.H * j.pitch, (uint32_t)tcp_of(SW, j.r), (uint32_t)tile_rows(TH, j.r));
         if (err != cudaSuccess) return err;
         FinImgP &fi = f.img[i];
         fi.H = j.H, fi.W = j.W, fi.r = j.r, fi.Nref = j.Nref, fi.blk0 = blk;
@@ -542,15 +718,15 @@ cudaError_t score_chunk(const ScoreJob *jobs, int n, int d, int B, void *ws, boo
         }
     switch (kind) {
     case EmdKind::U32_U32:
-        launch_emd_kb<uint32_t, uint32_t>(KB, cta, smem, SW, st, p, status);
+        launch_emd_kb<uint32_t, uint32_t>(KB, walk, cta, smem, SW, st, p, status);
         if (!fuse) QFCA_LAUNCH("k_finalize", st, k_finalize<uint32_t><<<(unsigned)blk, 256, 0, st>>>(f));
         break;
     case EmdKind::U32_U64:
-        launch_emd_kb<uint32_t, unsigned long long>(KB, cta, smem, SW, st, p, status);
+        launch_emd_kb<uint32_t, unsigned long long>(KB, walk, cta, smem, SW, st, p, status);
         if (!fuse) QFCA_LAUNCH("k_finalize", st, k_finalize<unsigned long long><<<(unsigned)blk, 256, 0, st>>>(f));
         break;
     default:
-        launch_emd_kb<unsigned long long, unsigned long long>(KB, cta, smem, SW, st, p, status);
+        launch_emd_kb<unsigned long long, unsigned long long>(KB, walk, cta, smem, SW, st, p, status);
         if (!fuse) QFCA_LAUNCH("k_finalize", st, k_finalize<unsigned long long><<<(unsigned)blk, 256, 0, st>>>(f));
         break;
     }
@@ -568,7 +744,7 @@ size_t score_jobs_workspace_bytes(const ScoreJob *jobs, int n, int d) {
 bool score_shape_ok(int B, int r) {
     for (int SW : {128, 64})
         for (int TH : {16, 32, 8})
-            if (score_smem(SW, TH, B, r) <= 200 * 1024 && tcp_of(SW, r) <= 256 && TH + 2 * r <= 256) return true;
+            if (score_smem(SW, TH, B, r) <= 200 * 1024 && tcp_of(SW, r) <= 256 && tile_rows(TH, r) <= 256) return true;
     return false;
 }
 

@@ -137,6 +137,14 @@ _lib.qfca_set_autotune.argtypes = [_P, _I]
 _lib.qfca_set_autotune.restype = _I
 _lib.qfca_last_tiling.argtypes = [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]
 _lib.qfca_last_tiling.restype = _I
+_lib.qfca_set_cdf_walk.argtypes = [_P, _I]
+_lib.qfca_set_cdf_walk.restype = _I
+_lib.qfca_last_cdf_walk.argtypes = [_P, ctypes.POINTER(_I)]
+_lib.qfca_last_cdf_walk.restype = _I
+_lib.qfca_set_band_run.argtypes = [_P, _I]
+_lib.qfca_set_band_run.restype = _I
+_lib.qfca_last_band_run.argtypes = [_P, ctypes.POINTER(_I)]
+_lib.qfca_last_band_run.restype = _I
 
 
 class ServeConfig(ctypes.Structure):
@@ -218,6 +226,27 @@ class Context:
     def set_tiling(self, strip_width: int = 0, band_height: int = 0, component_groups: int = 0):
         """Force the window stage's tiling for later calls (strip_width 0: cost model / autotuner)."""
         self.check(_lib.qfca_set_tiling(self.handle, int(strip_width), int(band_height), int(component_groups)))
+
+    def set_cdf_walk(self, walk: int = -1):
+        """CDF walk of the window stage: -1 the autotuner's choice (per thread without
+        autotuning), 0 per thread, 1 warp-shuffle segmented (B = 32, 32-bit numerators)."""
+        self.check(_lib.qfca_set_cdf_walk(self.handle, int(walk)))
+
+    def set_band_run(self, bands: int = 1):
+        """Bands per CTA of a tiling forced by set_tiling (1 default, 0 every band of a strip)."""
+        self.check(_lib.qfca_set_band_run(self.handle, int(bands)))
+
+    def last_band_run(self) -> int:
+        """Bands per CTA of the most recent window-stage launch."""
+        v = ctypes.c_int()
+        self.check(_lib.qfca_last_band_run(self.handle, ctypes.byref(v)))
+        return int(v.value)
+
+    def last_cdf_walk(self) -> int:
+        """The CDF walk (0 per thread, 1 warp-shuffle) of the most recent window-stage launch."""
+        v = ctypes.c_int()
+        self.check(_lib.qfca_last_cdf_walk(self.handle, ctypes.byref(v)))
+        return int(v.value)
 
     def last_projection_tiling(self) -> tuple[int, int]:
         """(FP32 boxes in flight, operand chunks) of the most recent TMA-fed projection."""

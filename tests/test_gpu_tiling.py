@@ -4,7 +4,10 @@ numerators per pixel in shared memory and writes the score itself (the fused
 form); with several groups the per-component numerators go through the
 finalisation launch.  Both divide the same exact integer sum once in FP64, so
 every tiling must agree bit for bit with the numerator path, and within one
-FP32 rounding with the oracle.  Tilings are forced through qfca_set_tiling."""
+FP32 rounding with the oracle.  Tilings are forced through qfca_set_tiling;
+a CTA may also take a run of consecutive bands (qfca_set_band_run), sliding
+its windows on from one band into the next, which must not change a bit
+either."""
 import numpy as np
 import pytest
 import torch
@@ -42,17 +45,30 @@ def test_every_tiling_gives_the_same_map(q, d, H, W, B, r, seed):
     ref = ref.cpu().numpy()
     np.testing.assert_allclose(ref, s_o, rtol=2.0 ** -23, atol=1e-12)
     fused_seen = False
+    runs_seen = set()
     for tl in TILINGS:
-        ctx.set_tiling(*tl)
-        try:
-            s = q.score(bins, W, B, r, Rd, H * W, ctx=ctx)
-        except q.QfcaError:
-            continue  # this tiling does not fit shared memory for (B, r)
-        torch.cuda.synchronize()
-        used = ctx.last_tiling()
-        assert used == tl
-        fused_seen = fused_seen or tl[2] == 1
-        np.testing.assert_array_equal(s.cpu().numpy(), ref)
+        for run in (1, 2, 3, 0):
+            ctx.set_tiling(*tl)
+            ctx.set_band_run(run)
+            try:
+                s = q.score(bins, W, B, r, Rd, H * W, ctx=ctx)
+            except q.QfcaError:
+                continue  # this tiling does not fit shared memory for (B, r)
+            torch.cuda.synchronize()
+            used = ctx.last_tiling()
+            assert used == tl
+            nby = (H + tl[1] - 1) // tl[1]
+            kg = -(-d // tl[2])
+            fused = -(-d // kg) == 1
+            # a fused tiling (one group) takes one band; 0 asks for every band of the strip
+            want = 1 if fused else min(run if run > 0 else nby, nby)
+            assert ctx.last_band_run() == want
+            runs_seen.add(want)
+            fused_seen = fused_seen or fused
+            np.testing.assert_array_equal(s.cpu().numpy(), ref)
     ctx.set_tiling(0)
+    ctx.set_band_run(1)
     assert fused_seen
+    if d > 1 and H > 16:
+        assert max(runs_seen) > 1
     assert ctx.device_status() == 0
