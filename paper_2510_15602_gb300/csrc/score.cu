@@ -88,11 +88,21 @@ size_t score_smem(int SW, int TH, int B, int rmax, bool fuse = false) {
     return 128 + score_smem_core(SW, TH, B, rmax) + (fuse ? sizeof(uint64_t) * (size_t)TH * SW : 0);
 }
 
-// 32-bit shared-memory address of a pointer into shared memory, and the
-// fire-and-forget increment of a window count there.
+// 32-bit shared-memory address of a pointer into shared memory, the
+// fire-and-forget increment of a window count there, and the read of a count.
+// Both are volatile asm with no memory clobber: the compiler keeps them in
+// program order with respect to each other (a thread reads its own counts after
+// its increments; the hardware orders one thread's accesses to one address), and
+// the CTA and warp barriers order them against every other access, while the
+// kernel's parameters and pointers stay in registers across them.
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void count_add(uint32_t addr, uint32_t v) {
-    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+__device__ __forceinline__ uint32_t count_ld(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)));
+    return v;
 }
 
 // The window counts of one thread, bin-major (count of code v at hbase + v * 4 SWT): the span bytes
@@ -180,7 +190,7 @@ __global__ void __launch_bounds__(SWT) k_window_emd(const __grid_constant__ Scor
     const long cta = blockIdx.x;
     int ii = 0;
     while (ii + 1 < p.n && p.img[ii + 1].cta0 <= cta) ii++;
-    const ScoreImgP &im = p.img[ii];
+    const ScoreImgP im = p.img[ii];  // in registers
     const CUtensorMap *tmap = &p.tmap[ii];
     const int H = im.H, W = im.W, r = im.r;
     long local = cta - im.cta0;
@@ -315,6 +325,9 @@ __global__ void __launch_bounds__(SWT) k_window_emd(const __grid_constant__ Scor
             }
         }
         const bool xin = x < W;
+        // this thread's column of the outputs
+        OUT *numer_col = im.numer ? reinterpret_cast<OUT *>(im.numer) + (long)k * HW + x : nullptr;
+        unsigned long long *accum_col = im.accum ? im.accum + x : nullptr;
         // window of the band's first row (tile rows 1 .. 2r+1), or the previous band's last window continued
         if (fresh && xin)
             for (int ry = 1; ry <= span; ry++) window_rows<SW, false>(nullptr, tile + ry * TCp, c0, span, hbase);
@@ -339,7 +352,7 @@ __global__ void __launch_bounds__(SWT) k_window_emd(const __grid_constant__ Scor
                         uint32_t hv[16], cnt = 0, s = 0;
 #pragma unroll
                         for (int j = 0; j < 16; j++) {
-                            hv[j] = h2[j * SW];
+                            hv[j] = count_ld(h2 + j * SW);
                             cnt += hv[j];  // this half's count
                         }
                         // the lower half's count is the upper half's CDF offset
@@ -372,7 +385,7 @@ __global__ void __launch_bounds__(SWT) k_window_emd(const __grid_constant__ Scor
                     uint32_t a = 0, D32 = 0;
 #pragma unroll
                     for (int b = 0; b < KB - 1; b++) {
-                        a += hb[b * SW] * Nref;
+                        a += count_ld(hb + b * SW) * Nref;
                         D32 = __usad(a, cr[WALK == 0 ? b : 0], D32);
                     }
                     D = (ACC)D32;
@@ -388,7 +401,7 @@ __global__ void __launch_bounds__(SWT) k_window_emd(const __grid_constant__ Scor
                         for (int e = 0; e < 4; e++) {
                             const int b = 4 * b4 + e;
                             if (b < KB - 1) {
-                                a += hb[b * SW] * Nref;
+                                a += count_ld(hb + b * SW) * Nref;
                                 D32 = __usad(a, cv[e], D32);
                             }
                         }
@@ -398,7 +411,7 @@ __global__ void __launch_bounds__(SWT) k_window_emd(const __grid_constant__ Scor
                     uint32_t cnt = 0;
 #pragma unroll
                     for (int b = 0; b < KB - 1; b++) {
-                        cnt += hb[b * SW];
+                        cnt += count_ld(hb + b * SW);
                         const ACC a = (ACC)cnt * (ACC)Nref, c = cRi[b];
                         D += max(a, c) - min(a, c);
                     }
@@ -406,7 +419,7 @@ __global__ void __launch_bounds__(SWT) k_window_emd(const __grid_constant__ Scor
                     uint32_t cnt = 0;
 #pragma unroll 4
                     for (int b = 0; b < B - 1; b++) {
-                        cnt += hb[b * SW];
+                        cnt += count_ld(hb + b * SW);
                         const ACC a = (ACC)cnt * (ACC)Nref, c = cRi[b];
                         D += max(a, c) - min(a, c);
                     }
@@ -415,19 +428,18 @@ __global__ void __launch_bounds__(SWT) k_window_emd(const __grid_constant__ Scor
                 uint32_t cnt = 0;
 #pragma unroll 4
                 for (int b = 0; b < B - 1; b++) {
-                    cnt += hb[b * SW];
+                    cnt += count_ld(hb + b * SW);
                     const ACC a = (ACC)cnt * (ACC)Nref, c = (ACC)cumR[b] * (ACC)Nloc;
                     D += max(a, c) - min(a, c);
                 }
             }
-            const long pix = (long)yy * W + x;
             if (p.fuse) {  // one band per CTA: item it is component k0 + it
                 unsigned long long &a = acc[i * SW + t];  // this thread's own column: no other thread touches it
                 a = (it == 0 ? 0ull : a) + (unsigned long long)D;
-            } else if (im.accum) {
-                atomicAdd(&im.accum[pix], (unsigned long long)D);
+            } else if (accum_col) {
+                atomicAdd(accum_col + (long)yy * W, (unsigned long long)D);
             } else {
-                reinterpret_cast<OUT *>(im.numer)[(long)k * HW + pix] = (OUT)D;
+                numer_col[(long)yy * W] = (OUT)D;
             }
         }
         tc::fence_proxy_async_smem();  // this iteration's writes to the tile precede the next TMA write into it
