@@ -65,10 +65,17 @@ __global__ void __launch_bounds__(kThreads) k_quantize(const __grid_constant__ Q
     uint8_t *bk = im.bins + (long)k * H * im.pitch;
     const int y0 = band * kRowsPerCta;
     const int y1 = min(H, y0 + kRowsPerCta);
-    for (int yy = y0; yy < y1; yy++) {
-        for (int x = threadIdx.x; x < W; x += kThreads) {
-            const int q = quant_bin(yk[(long)yy * W + x], lo, hi, fB, B);
-            bk[(long)yy * im.pitch + x] = (uint8_t)q;
+    // a thread's pixels of the band's rows are loaded before any is used: eight loads in flight
+    // per thread (the bins and counts written in between would otherwise keep them in order)
+    for (int x = threadIdx.x; x < W; x += kThreads) {
+        float v[kRowsPerCta];
+#pragma unroll
+        for (int i = 0; i < kRowsPerCta; i++) v[i] = y0 + i < y1 ? __ldg(yk + (long)(y0 + i) * W + x) : 0.0f;
+#pragma unroll
+        for (int i = 0; i < kRowsPerCta; i++) {
+            if (y0 + i >= y1) break;
+            const int q = quant_bin(v[i], lo, hi, fB, B);
+            bk[(long)(y0 + i) * im.pitch + x] = (uint8_t)q;
             if (im.hist) atomicAdd(&sh[q], 1u);
         }
     }

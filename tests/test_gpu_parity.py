@@ -172,6 +172,25 @@ def test_quantize_fixed_range_clamps(q):
     assert (exp == 0).any() and (exp == 15).any()
 
 
+def test_quantize_histogram_of_constant_and_blocky_components(q):
+    # a zero basis column makes its component constant (hi == lo: every pixel in bin 0), the others
+    # come from a smooth field: whole warps share a bin, the counting groups lanes by bin
+    img = _case(48, 64, 96, seed=21)
+    mean, V, _, _ = oracle.fit(img.X, 6)
+    V[:, 2] = 0.0
+    for W in (96, 93):  # four pixels per thread, and the per-pixel route for a ragged width
+        X = np.ascontiguousarray(img.X[:, :, :W])
+        out = q.quantize(to_dev(X), (to_dev(mean), to_dev(V)), 32, "f32", want_Y=True)
+        torch.cuda.synchronize()
+        Y_g = out["Y"].cpu().numpy().astype(np.float64)
+        exp, _, _ = oracle.quantize(Y_g, 32, fp32_decision=True)
+        qb = bins_np(out["bins"], W)
+        np.testing.assert_array_equal(qb, exp)
+        hist = out["hist"].cpu().numpy().astype(np.uint32)
+        np.testing.assert_array_equal(hist, oracle.ref_hist(qb, 32))
+        assert hist[2, 0] == 64 * W and hist.sum() == 6 * 64 * W
+
+
 # ------------------------------------------------------------------ PCA fit (FP64)
 
 @pytest.mark.parametrize("C,H,W,d,layout", [
