@@ -5,7 +5,14 @@
 // One CTA = one component k x a band of rows.  The bin decision is taken in
 // FP32 with IEEE-rounded operations in a fixed order:
 //     t = (y - lo) / (hi - lo);  v = t * B;  q = clamp((int)v, 0, B-1)
-// (hi == lo gives q = 0).  Histogram: shared-memory counters per CTA, then one
+// (hi == lo gives q = 0).  Every rounded step is monotone in y, so q(y) is a
+// non-decreasing step function of y: q(y) = #{j in 1..B-1 : y >= e_j} with
+// e_j the smallest float whose decision is >= j.  Each CTA finds its
+// component's B-1 edges by bisection over the order-preserving keys of the
+// floats, evaluating the decision itself (so the edges are exact by
+// construction), and each pixel's bin is then a branch-free search of that
+// table: the same bins as evaluating the division per pixel, at a fraction of
+// its instructions.  Histogram: shared-memory counters per CTA, then one
 // global atomicAdd per bin (integer adds: order-independent, exact).
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -16,7 +23,8 @@ namespace qfca {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kRowsPerCta = 8;
+constexpr int kRowsPerCta = 32;  // rows per CTA (the edge search is amortised over them)
+constexpr int kLoadRows = 8;     // rows whose pixels a thread loads before using any
 
 struct QuantImgP {
     const float *Y;           // [d][N]
@@ -35,9 +43,33 @@ struct QuantParams {
     QuantImgP img[kMaxBatch];
 };
 
+// e_j = the smallest float y with quant_bin(y) >= j (1 <= j <= B-1; needs hi > lo): bisection on the
+// order-preserving keys, q(key2f(a)) < j <= q(key2f(b)) throughout (q(-inf) = 0, q(+inf) = B-1).
+__device__ float bin_edge(int j, float lo, float hi, float fB, int B) {
+    uint32_t a = f2key(-INFINITY), b = f2key(INFINITY);
+    for (int it = 0; it < 33 && b - a > 1; it++) {
+        const uint32_t m = a + ((b - a) >> 1);
+        if (quant_bin(key2f(m), lo, hi, fB, B) >= j) b = m;
+        else a = m;
+    }
+    return key2f(b);
+}
+
+// The bin of y from the edge table E[0..P-1] (E[j-1] = e_j, NaN past B-1; P a power of two >= B):
+// the number of edges <= y (NaN compares false, so a NaN y gets 0 as quant_bin gives it).
+template <int P>
+__device__ __forceinline__ int edge_bin(float y, const float *E) {
+    int q = 0;
+#pragma unroll
+    for (int s = P >> 1; s > 0; s >>= 1)
+        if (y >= E[q + s - 1]) q += s;
+    return q;
+}
+
 // One CTA = one component x a band of rows of one image of the table.
 __global__ void __launch_bounds__(kThreads) k_quantize(const __grid_constant__ QuantParams p) {
     __shared__ uint32_t sh[256];
+    __shared__ float edge[256];
     const long cta = blockIdx.x;
     int ii = 0;
     while (ii + 1 < p.n && p.img[ii + 1].cta0 <= cta) ii++;
@@ -59,26 +91,31 @@ __global__ void __launch_bounds__(kThreads) k_quantize(const __grid_constant__ Q
         if (im.hi_out) im.hi_out[k] = hi;
     }
     for (int b = threadIdx.x; b < B; b += kThreads) sh[b] = 0;
-    __syncthreads();
     const float fB = (float)B;
+    {  // the component's bin edges, one per thread (kThreads >= 256 >= P)
+        const int j = threadIdx.x;
+        edge[j] = (j < B - 1 && hi > lo) ? bin_edge(j + 1, lo, hi, fB, B) : __int_as_float(0x7fc00000);
+    }
+    __syncthreads();
     const float *yk = im.Y + (long)k * N;
     uint8_t *bk = im.bins + (long)k * H * im.pitch;
     const int y0 = band * kRowsPerCta;
     const int y1 = min(H, y0 + kRowsPerCta);
-    // a thread's pixels of the band's rows are loaded before any is used: eight loads in flight
-    // per thread (the bins and counts written in between would otherwise keep them in order)
-    for (int x = threadIdx.x; x < W; x += kThreads) {
-        float v[kRowsPerCta];
+    // a thread's pixels of kLoadRows rows are loaded before any is used (the bins and counts
+    // written in between would otherwise keep the loads in order)
+    for (int x = threadIdx.x; x < W; x += kThreads)
+        for (int g = y0; g < y1; g += kLoadRows) {
+            float v[kLoadRows];
 #pragma unroll
-        for (int i = 0; i < kRowsPerCta; i++) v[i] = y0 + i < y1 ? __ldg(yk + (long)(y0 + i) * W + x) : 0.0f;
+            for (int i = 0; i < kLoadRows; i++) v[i] = g + i < y1 ? __ldg(yk + (long)(g + i) * W + x) : 0.0f;
 #pragma unroll
-        for (int i = 0; i < kRowsPerCta; i++) {
-            if (y0 + i >= y1) break;
-            const int q = quant_bin(v[i], lo, hi, fB, B);
-            bk[(long)(y0 + i) * im.pitch + x] = (uint8_t)q;
-            if (im.hist) atomicAdd(&sh[q], 1u);
+            for (int i = 0; i < kLoadRows; i++) {
+                if (g + i >= y1) break;
+                const int q = B <= 32 ? edge_bin<32>(v[i], edge) : edge_bin<256>(v[i], edge);
+                bk[(long)(g + i) * im.pitch + x] = (uint8_t)q;
+                if (im.hist) atomicAdd(&sh[q], 1u);
+            }
         }
-    }
     __syncthreads();
     if (im.hist)
         for (int b = threadIdx.x; b < B; b += kThreads)

@@ -191,6 +191,35 @@ def test_quantize_histogram_of_constant_and_blocky_components(q):
         assert hist[2, 0] == 64 * W and hist.sum() == 6 * 64 * W
 
 
+@pytest.mark.parametrize("lo,hi,B", [(-2.7, 3.1, 32), (-1e-3, 5e-4, 64), (0.0, 1.0, 16), (10.0, 13.0, 255)])
+def test_quantize_at_the_bin_edges(q, lo, hi, B):
+    # values exactly at every bin edge and at the floats on either side of it, through a one-hot
+    # basis (the projection returns the values themselves) and a fixed range: the bins must be the
+    # FP32 decision taken per value on the host
+    from tests.quant_edges import decision, edges
+    lo, hi = np.float32(lo), np.float32(hi)
+    e = edges(lo, hi, B)
+    vals = np.concatenate([e, np.nextafter(e, np.float32(-np.inf)), np.nextafter(e, np.float32(np.inf)),
+                           np.array([lo, hi, -np.inf, np.inf, 0.0, -0.0], dtype=np.float32)])
+    vals = vals[np.isfinite(vals)]
+    W = 64
+    H = -(-vals.size // W)
+    C = 4
+    X = np.zeros((C, H, W), dtype=np.float32)
+    X[0].reshape(-1)[:vals.size] = vals
+    X[1] = 7.0  # weighed by zero in the basis
+    mean = np.zeros(C)
+    V = np.zeros((C, 1))
+    V[0, 0] = 1.0
+    out = q.quantize(to_dev(X), (to_dev(mean), to_dev(V)), B, "f32", lo=to_dev(np.array([lo], np.float32)),
+                     hi=to_dev(np.array([hi], np.float32)), want_Y=True)
+    torch.cuda.synchronize()
+    Y = out["Y"].cpu().numpy().reshape(1, H, W)
+    np.testing.assert_array_equal(Y[0], X[0])
+    exp = np.array([decision(y, lo, hi, B) for y in X[0].reshape(-1)]).reshape(1, H, W)
+    np.testing.assert_array_equal(bins_np(out["bins"], W), exp)
+
+
 # ------------------------------------------------------------------ PCA fit (FP64)
 
 @pytest.mark.parametrize("C,H,W,d,layout", [
