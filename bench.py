@@ -380,12 +380,14 @@ def per_kind_auroc(scores, masks, kind_masks, border: int) -> dict:
 # captures summarised in profiles/<kernel>_batch16_256_c256.md; an entry is
 # removed whenever its kernel changes after the capture.
 NCU_TRAFFIC = {
-    "k_assoc": 35393280 + 78018560,
-    "k_median_ref": 43135744,
-    "k_residual": 2147958000 + 1031120000,
-    "k_project_tma": 1074424000 + 125305600,
-    "k_window_emd": 33653760 + 73581056,
-    "k_quantize": 134446336 + 19018240,
+    "k_gram": 2023529216 + 14163456,
+    "k_eig32": 8524800,
+    "k_assoc": 35176192 + 74977024,
+    "k_median_ref": 43221504,
+    "k_residual": 2148438016 + 1026944256,
+    "k_project_tma": 1074511616 + 125724160,
+    "k_window_emd": 33870080 + 75218176,
+    "k_quantize": 134453248 + 18565376,
 }
 
 
