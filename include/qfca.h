@@ -326,6 +326,22 @@ typedef struct {
 qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int d, int B, int r,
                            int precision, float *scores, const qfca_batch_outputs *extra, void *stream);
 
+/* qfca_batch_run_host -- qfca_batch_run with the feature maps and the score
+ * maps in host memory: the end-to-end call of the batch path.  On `stream` it
+ * enqueues the copy of X_host [nimg][C][H][W] (the layout of desc) into a
+ * device staging buffer the context owns, the whole path of qfca_batch_run
+ * (per-image fit, projection, quantisation, window EMD; Sec. 3.1, 3.3), and
+ * the copy of the score maps into scores_host [nimg][H][W] (FP32); one
+ * cudaMemcpyAsync each way.  Host buffers should be page-locked (pinned): then
+ * the copies are asynchronous and the call can be captured in a CUDA graph;
+ * pageable buffers work outside capture, with copies that wait for the host.
+ * The staging buffer (4 (C + 1) H W bytes per image) grows on a larger call
+ * and is freed with the context; it cannot grow during stream capture (run
+ * the call once before capturing).  The host buffers must stay valid until
+ * the stream reaches the call's end.  Same limits as qfca_batch_run. */
+qfca_status qfca_batch_run_host(qfca_ctx *ctx, const float *X_host, int nimg, qfca_fmap desc, int d, int B, int r,
+                                int precision, float *scores_host, void *stream);
+
 /* qfca_batch_run_basis -- qfca_batch_run with the PCA bases already fitted
  * (the basis-resident part of the path: Sec. 3.3 projection, Sec. 3.1
  * quantisation with image-wide ranges and each image's own global histogram

@@ -120,6 +120,8 @@ struct qfca_ctx {
     int device = 0;
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    void *io = nullptr;                                 // device staging of qfca_batch_run_host (features, maps)
+    size_t io_bytes = 0;
     int *status_dev = nullptr;  // device status word (bits set by kernels)
     bool sticky = false;
     std::string err;
@@ -450,8 +452,9 @@ qfca_status qfca_destroy(qfca_ctx *ctx) {
     if (ctx->serve) qfca_serve_stop(ctx);
     {
         DeviceGuard g(ctx->device);
-        if (ctx->ws || ctx->status_dev) cudaDeviceSynchronize();
+        if (ctx->ws || ctx->io || ctx->status_dev) cudaDeviceSynchronize();
         if (ctx->ws) cudaFree(ctx->ws);
+        if (ctx->io) cudaFree(ctx->io);
         if (ctx->status_dev) cudaFree(ctx->status_dev);
     }
     delete ctx;
@@ -842,6 +845,60 @@ static qfca_status batch_run_impl(qfca_ctx *ctx, const float *X, int nimg, qfca_
 qfca_status qfca_batch_run(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, int d, int B, int r,
                            int precision, float *scores, const qfca_batch_outputs *extra, void *stream) {
     return batch_run_impl(ctx, X, nimg, desc, d, B, r, precision, scores, extra, stream, nullptr, nullptr);
+}
+
+qfca_status qfca_batch_run_host(qfca_ctx *ctx, const float *X_host, int nimg, qfca_fmap desc, int d, int B, int r,
+                                int precision, float *scores_host, void *stream) {
+    qfca_status s = check_ctx(ctx);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t o_s = 0, sb = 0;
+    char *io = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (!X_host || !scores_host) return fail(ctx, QFCA_ERR_INVALID_ARG, "X_host / scores_host NULL");
+        if (nimg < 1 || nimg > 4096) return fail(ctx, QFCA_ERR_INVALID_ARG, "nimg = %d outside [1, 4096]", nimg);
+        if (desc.H < 1 || desc.W < 1 || desc.C < 1 || (long)desc.H * desc.W > (1L << 23) || desc.C > kMaxC)
+            return fail(ctx, QFCA_ERR_INVALID_ARG, "bad shape %d x %d x %d", desc.C, desc.H, desc.W);
+        const size_t xb = sizeof(float) * (size_t)nimg * desc.C * desc.H * desc.W;
+        sb = sizeof(float) * (size_t)nimg * desc.H * desc.W;
+        o_s = align_up(xb, 256);
+        DeviceGuard g(ctx->device);
+        if (o_s + sb > ctx->io_bytes) {  // grows like the workspace: never during stream capture
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (st && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+                return fail(ctx, QFCA_ERR_INVALID_ARG,
+                            "the staging buffer must grow to %zu bytes during stream capture: run the call once "
+                            "before capturing", o_s + sb);
+            if (ctx->io) {
+                cudaError_t e = cudaFree(ctx->io);
+                ctx->io = nullptr;
+                ctx->io_bytes = 0;
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFree(staging)");
+            }
+            void *p = nullptr;
+            const size_t sz = align_up(o_s + sb, 1 << 20);
+            cudaError_t e = cudaMalloc(&p, sz);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ctx, QFCA_ERR_OOM, "staging of %zu bytes: %s", sz, cudaGetErrorString(e));
+            }
+            ctx->io = p;
+            ctx->io_bytes = sz;
+        }
+        io = (char *)ctx->io;
+        cudaError_t e = cudaMemcpyAsync(io, X_host, xb, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_batch_run_host/H2D");
+    }
+    s = batch_run_impl(ctx, (const float *)io, nimg, desc, d, B, r, precision, (float *)(io + o_s), nullptr, stream,
+                       nullptr, nullptr);
+    if (s) return s;
+    cudaError_t e = cudaMemcpyAsync(scores_host, io + o_s, sb, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        return cuda_fail(ctx, e, "qfca_batch_run_host/D2H");
+    }
+    return QFCA_OK;
 }
 
 qfca_status qfca_batch_run_basis(qfca_ctx *ctx, const float *X, int nimg, qfca_fmap desc, const double *mean,

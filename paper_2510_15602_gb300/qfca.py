@@ -85,6 +85,8 @@ class BatchOutputs(ctypes.Structure):
 
 _lib.qfca_batch_run.argtypes = [_P, _P, _I, Fmap, _I, _I, _I, _I, _P, ctypes.POINTER(BatchOutputs), _P]
 _lib.qfca_batch_run.restype = _I
+_lib.qfca_batch_run_host.argtypes = [_P, _P, _I, Fmap, _I, _I, _I, _I, _P, _P]
+_lib.qfca_batch_run_host.restype = _I
 _lib.qfca_batch_run_basis.argtypes = [_P, _P, _I, Fmap, _P, _P, _I, _I, _I, _I, _P, ctypes.POINTER(BatchOutputs), _P]
 _lib.qfca_batch_run_basis.restype = _I
 _lib.qfca_last_projection_tiling.argtypes = [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]
@@ -577,6 +579,25 @@ def batch_run(X: torch.Tensor, d: int, B: int, r: int, precision="bf16", ctx: Co
     ctx.check(_lib.qfca_batch_run(ctx.handle, _ptr(X), nimg, fm, d, B, r, _PREC[precision], _ptr(scores),
                                   ctypes.byref(ext) if ext is not None else None, _P(_stream_ptr(stream))))
     return (scores, ex) if extras else scores
+
+
+def batch_run_host(X: torch.Tensor, d: int, B: int, r: int, precision="bf16", ctx: Context | None = None,
+                   stream=None, scores: torch.Tensor | None = None, device: int = 0):
+    """qfca_batch_run_host: the whole path for a batch X [nimg, C, H, W] (NCHW maps) held in
+    host memory (pinned for asynchronous copies); the score maps come back into the host tensor
+    ``scores`` [nimg, H, W] (f32, allocated pinned when not given).  Enqueued on ``stream``: the
+    host tensors must stay alive until the stream has passed the call."""
+    if X.is_cuda or X.dtype != torch.float32 or not X.is_contiguous() or X.dim() != 4:
+        raise ValueError("X must be a contiguous host float32 tensor [nimg, C, H, W]")
+    nimg, C, H, W = (int(v) for v in X.shape)
+    ctx = ctx or default_context(device)
+    if scores is None:
+        scores = torch.empty(nimg, H, W, dtype=torch.float32).pin_memory()
+    if scores.is_cuda or scores.dtype != torch.float32 or not scores.is_contiguous() or tuple(scores.shape) != (nimg, H, W):
+        raise ValueError("scores must be a contiguous host float32 tensor [nimg, H, W]")
+    ctx.check(_lib.qfca_batch_run_host(ctx.handle, _P(X.data_ptr()), nimg, Fmap(H, W, C, NCHW), d, B, r,
+                                       _PREC[precision], _P(scores.data_ptr()), _P(_stream_ptr(stream))))
+    return scores
 
 
 def batch_run_basis(X: torch.Tensor, mean: torch.Tensor, V: torch.Tensor, B: int, r: int, precision="bf16",
