@@ -76,8 +76,12 @@ __device__ __forceinline__ uint32_t swz_off(int row, int chunk16) {
     return (uint32_t)(row * 128 + ((chunk16 ^ (row & 7)) << 4));
 }
 
-__device__ __forceinline__ int find_img(const ProjParams &p, long w) {
-    int i = 0;
+// The image of tile w, searched forward from image `from` (a role walks its tiles in increasing
+// order, so it passes each image boundary once: O(1) per tile instead of a scan of the table --
+// the scan, up to 64 dependent parameter loads per box in the producer thread, had made the
+// kernel's time grow with the number of images in the table).
+__device__ __forceinline__ int find_img(const ProjParams &p, long w, int from) {
+    int i = from < 0 ? 0 : from;
     while (i + 1 < p.n && p.img[i + 1].tile0 <= w) i++;
     return i;
 }
@@ -213,6 +217,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
     if (warp == 0) {
         // ---------------------------------------------------------------- TMA producer
         long q = 0;
+        int pimg = -1;
         for (; q < n_chunks; q++) {
             const int s = (int)(q % S);
             const bool ok = q < S || warp_wait(&empty[s], (uint32_t)((q / S - 1) & 1), abort_flag);
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
             if (lane == 0) {
                 const long w = w0 + q / nk;
                 const int kc = (int)(q % nk);
-                const int i = find_img(p, w);
+                const int i = pimg = find_img(p, w, pimg);
                 tc::mbar_arrive_expect_tx(&full[s], kStageBytes);
                 tc::tma_load_2d(stage + (size_t)s * kStageBytes, &p.tmap[i], (int)((w - p.img[i].tile0) * kM),
                                 kc * kKc, &full[s]);
@@ -281,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
         bool ok = true;  // warp-uniform; once false the warp only keeps passing the named barriers
         for (long tile = 0; tile < w1 - w0; tile++) {
             const long w = w0 + tile;
-            const int img = find_img(p, w);
+            const int img = find_img(p, w, cur);
             if (img != cur) {
                 // image change: wait for the MMAs in flight (they read the old V^T), then reload
                 if (ok && q >= 1)
@@ -397,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tma(const __grid_consta
         bool ok = true;
         for (long tile = 0; tile < w1 - w0; tile++) {
             const long w = w0 + tile;
-            const int img = find_img(p, w);
+            const int img = find_img(p, w, cur);
             if (img != cur) {
                 if (cur >= 0) flush(cur);
                 cur = img;
