@@ -553,13 +553,24 @@ __global__ void k_chan_scale(const unsigned *__restrict__ amax, int C, float *__
 
 // Sigma_ij = 2^(e_i+e_j) T_ij 2^-40 / N - mu_i mu_j ;  mu_c = 2^e_c S_c / N,
 // S_c = sum_i D_i,c 2^(-6-7i).  Writes mean[C] and the full symmetric cov[C][C]
-// of each image (grid.y = image).
-__global__ void k_cov_finalize(const __grid_constant__ FitParams p, const unsigned long long *__restrict__ Gint,
-                               const unsigned long long *__restrict__ Dsum, const int *__restrict__ ex,
-                               double *__restrict__ mean, double *__restrict__ cov, float2 *__restrict__ cov_ff) {
-    extern __shared__ double fin_sh[];  // [C] means, [C] powers 2^e_c
+// of each image (grid.y = image).  One block = one 32 x 32 tile of the output
+// (grid.x = tile): it forms the means and powers of two of its 32 rows and 32
+// columns only, reads its tile of the upper triangle of T coalesced (rows
+// a0.., columns b0.. with a0 <= b0) and, below the diagonal, writes it
+// transposed through shared memory; every entry is formed from T[min][max]
+// with the same operations in the same order as for the entry above the
+// diagonal, so the matrix is exactly symmetric.
+constexpr int kFinT = 32;
+__global__ void __launch_bounds__(256) k_cov_finalize(const __grid_constant__ FitParams p,
+                                                       const unsigned long long *__restrict__ Gint,
+                                                       const unsigned long long *__restrict__ Dsum,
+                                                       const int *__restrict__ ex, double *__restrict__ mean,
+                                                       double *__restrict__ cov, float2 *__restrict__ cov_ff) {
+    __shared__ long long Ts[kFinT][kFinT + 1];
+    __shared__ double mu_s[2][kFinT], pw_s[2][kFinT];  // [0]: the tile's rows, [1]: its columns
     const long img = blockIdx.y;
-    const int C = p.C;
+    const int C = p.C, nt = (C + kFinT - 1) / kFinT;
+    const int ti = (int)(blockIdx.x / nt), tj = (int)(blockIdx.x % nt);
     const double invN = 1.0 / (double)p.img[img].N;
     Gint += img * C * C;
     Dsum += img * kSlices * C;
@@ -567,26 +578,43 @@ __global__ void k_cov_finalize(const __grid_constant__ FitParams p, const unsign
     mean += img * C;
     cov += img * C * C;
     if (cov_ff) cov_ff += img * C * C;
-    double *mu = fin_sh, *pw = fin_sh + C;
-    // per channel once per block: 2^e_c and mu_c = 2^e_c S_c / N (powers of two: every scaling is exact)
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    // 2^e_c and mu_c = 2^e_c S_c / N of the tile's rows and columns (powers of two: every scaling is exact)
     constexpr double kSl[kSlices] = {0x1p-6, 0x1p-13, 0x1p-20, 0x1p-27};
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        double s = 0.0;
-        for (int sl = 0; sl < kSlices; sl++) s += (double)(long long)Dsum[(long)sl * C + c] * kSl[sl];
-        pw[c] = ldexp(1.0, ex[c]);
-        mu[c] = s * pw[c] * invN;
+    if (threadIdx.x < 2 * kFinT) {
+        const int side = threadIdx.x / kFinT, c = (side ? tj : ti) * kFinT + tx;
+        double s = 0.0, pw = 1.0;
+        if (c < C) {
+            for (int sl = 0; sl < kSlices; sl++) s += (double)(long long)Dsum[(long)sl * C + c] * kSl[sl];
+            pw = ldexp(1.0, ex[c]);
+        }
+        pw_s[side][tx] = pw;
+        mu_s[side][tx] = s * pw * invN;
+    }
+    // the tile of the upper triangle that holds this tile's entries: rows a0.., columns b0..
+    const int a0 = min(ti, tj) * kFinT, b0 = max(ti, tj) * kFinT;
+    for (int y = ty; y < kFinT; y += 8) {
+        const int a = a0 + y, b = b0 + tx;
+        Ts[y][tx] = (a < C && b < C) ? (long long)Gint[(long)a * C + b] : 0;
     }
     __syncthreads();
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)C * C; e += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(e / C), j = (int)(e % C);
-        const int a = min(i, j), b = max(i, j);
-        const double mi = mu[a], mj = mu[b];
-        const double g = (double)(long long)Gint[(long)a * C + b] * (pw[a] * pw[b] * 0x1p-40) * invN;
+    for (int y = ty; y < kFinT; y += 8) {
+        const int i = ti * kFinT + y, j = tj * kFinT + tx;
+        if (i >= C || j >= C) continue;
+        // entry (i, j) from T[min(i, j)][max(i, j)]; (la, lb): its row and column within Ts
+        const bool upper = ti < tj || (ti == tj && y <= tx);
+        const int la = upper ? y : tx, lb = upper ? tx : y;
+        // the row channel min(i, j) and the column channel max(i, j), as the upper entry takes them
+        const int sa = ti <= tj ? 0 : 1, sb = 1 - sa;  // which side holds channel a (rows: 0, columns: 1)
+        const int ca = ti == tj ? la : (sa == 0 ? y : tx), cb = ti == tj ? lb : (sb == 0 ? y : tx);
+        const double mi = mu_s[ti == tj ? 0 : sa][ca], mj = mu_s[ti == tj ? 1 : sb][cb];
+        const double pa = pw_s[ti == tj ? 0 : sa][ca], pb = pw_s[ti == tj ? 1 : sb][cb];
+        const double g = (double)Ts[la][lb] * (pa * pb * 0x1p-40) * invN;
         const double v = g - mi * mj;
-        cov[e] = v;
+        cov[(long)i * C + j] = v;
         if (cov_ff) {
             const float h = (float)v;
-            cov_ff[e] = make_float2(h, (float)(v - (double)h));
+            cov_ff[(long)i * C + j] = make_float2(h, (float)(v - (double)h));
         }
         if (i == j) mean[i] = mi;
     }
@@ -692,9 +720,9 @@ cudaError_t launch_gram_cov_jobs(const FitJob *jobs, int n, int layout, int C, d
         QFCA_LAUNCH("k_chan_scale", st,
                     k_chan_scale<<<(unsigned)((C * m + 127) / 128), 128, 0, st>>>(am, C * m, sc, exi));
         QFCA_LAUNCH("k_gram", st, k_gram<<<(unsigned)cta, kThreads, g.smem, st>>>(p, sc, Gi, Di, status));
-        const long cc = (long)C * C;
+        const int nt32 = (C + kFinT - 1) / kFinT;
         QFCA_LAUNCH("k_cov_finalize", st,
-                    k_cov_finalize<<<dim3((unsigned)((cc + 255) / 256), m), 256, 2 * sizeof(double) * C, st>>>(
+                    k_cov_finalize<<<dim3((unsigned)(nt32 * nt32), m), 256, 0, st>>>(
                         p, Gi, Di, exi, mean + (size_t)i0 * C, cov + (size_t)i0 * C * C,
                         cov_ff ? (float2 *)cov_ff + (size_t)i0 * C * C : nullptr));
         e = cudaGetLastError();
