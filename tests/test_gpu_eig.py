@@ -93,3 +93,18 @@ def test_eig_batch_mixed_fallback(q):
         for i, im in enumerate(imgs):
             _, cov = q.covariance(to_dev(im.X), ctx=ctx)
             _check(ex["V"][i].cpu().numpy(), ex["eigvals"][i].cpu().numpy(), cov.cpu().numpy(), 16)
+
+
+def test_eig_c512_batch_against_oracle(q):
+    # seven C = 512 images fitted together: the float-float cluster solver runs clusters of six
+    # CTAs (the plan that fits C = 512 with room for 25 clusters on the GPU); two images checked
+    imgs = [synth.small_case(C=512, H=24, W=40, sigma=2.0, seed=700 + i, n_square=1, side=6, nch=4) for i in range(7)]
+    X = torch.stack([to_dev(im.X) for im in imgs])
+    ctx = q.Context()
+    _, ex = q.batch_run(X, 32, 16, 4, "bf16", ctx=ctx, extras=True)
+    torch.cuda.synchronize()
+    assert ctx.device_status() == 0
+    for i in (0, 6):
+        _, cov = q.covariance(to_dev(imgs[i].X), ctx=ctx)
+        _check(ex["V"][i].cpu().numpy(), ex["eigvals"][i].cpu().numpy(), cov.cpu().numpy(), 32)
+
