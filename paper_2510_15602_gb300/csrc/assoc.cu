@@ -362,8 +362,7 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
     const int B = p.B, nt = p.nt;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const long cta = blockIdx.x;
-    int ii = 0;
-    while (ii + 1 < p.n && p.img[ii + 1].cta0 <= cta) ii++;
+    const int ii = table_image(p.n, cta, [&](int i) { return p.img[i].cta0; });
     const AssocImgP &im = p.img[ii];
     const int H = im.H, W = im.W, r = im.r, span = 2 * r + 1;
     long local = cta - im.cta0;
@@ -562,8 +561,7 @@ __global__ void __launch_bounds__(256) k_assoc(const __grid_constant__ AssocPara
 __global__ void __launch_bounds__(256) k_assoc_fin(const __grid_constant__ AssocFinParams p) {
     __shared__ double wk[kAssocMaxWeights];
     const long blk = blockIdx.x;
-    int ii = 0;
-    while (ii + 1 < p.n && p.img[ii + 1].blk0 <= blk) ii++;
+    const int ii = table_image(p.n, blk, [&](int i) { return p.img[i].blk0; });
     const FinImg &im = p.img[ii];
     if (im.lo) {
         for (int k = threadIdx.x; k < p.d; k += 256) wk[k] = ((double)im.hi[k] - (double)im.lo[k]) / (double)p.B;
@@ -601,8 +599,7 @@ __global__ void __launch_bounds__(256) k_blur(const __grid_constant__ BlurParams
     __shared__ float tile[32 + 2 * 16][32 + 2 * 16 + 1];
     __shared__ float mid[32 + 2 * 16][33];
     const long blk = blockIdx.x;
-    int ii = 0;
-    while (ii + 1 < p.n && p.img[ii + 1].blk0 <= blk) ii++;
+    const int ii = table_image(p.n, blk, [&](int i) { return p.img[i].blk0; });
     const BlurImg &im = p.img[ii];
     const int H = im.H, W = im.W, R4 = p.R4;
     const int nbx = (W + 31) / 32;

@@ -304,12 +304,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram(const __grid_constant__ Fi
 
     const long cta = blockIdx.x;
     const bool diag = cta >= p.diag_start;
-    int img = 0;
-    if (diag) {
-        while (img + 1 < p.n && p.img[img + 1].cta0d <= cta) img++;
-    } else {
-        while (img + 1 < p.n && p.img[img + 1].cta0 <= cta) img++;
-    }
+    const int img = diag ? table_image(p.n, cta, [&](int i) { return p.img[i].cta0d; })
+                         : table_image(p.n, cta, [&](int i) { return p.img[i].cta0; });
     const FitImgP &im = p.img[img];
     const int C = p.C, layout = p.layout, vec_ok = p.vec_ok, nt = p.nt, n_off = p.n_pairs - p.nt;
     const long N = im.N, chunk = im.chunk;

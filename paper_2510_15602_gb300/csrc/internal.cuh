@@ -316,6 +316,23 @@ __host__ __device__ inline float key2f(uint32_t k) {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+#ifdef __CUDACC__
+// The image of a table-driven launch that owns index x (a CTA, block or tile):
+// the last i in [0, n) with first(i) <= x, for first() non-decreasing and
+// first(0) <= x.  Binary search: about log2(n) parameter loads instead of up to
+// n - 1 in a scan.
+template <class F>
+__device__ __forceinline__ int table_image(int n, long x, F first) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first(mid) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+#endif
+
 // The bin of value y among B equally spaced bins between lo and hi (Sec. 3.1),
 // decided in FP32 with IEEE-rounded operations in a fixed order:
 //     t = (y - lo) / (hi - lo);  v = t * B;  q = clamp((int)v, 0, B-1);  hi == lo gives 0.

@@ -50,8 +50,7 @@ __global__ void __launch_bounds__(256) k_median_ref(const __grid_constant__ MedP
     const int B = p.B, nt = p.nt;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const long cta = blockIdx.x;
-    int ii = 0;
-    while (ii + 1 < p.n && p.img[ii + 1].cta0 <= cta) ii++;
+    const int ii = table_image(p.n, cta, [&](int i) { return p.img[i].cta0; });
     const MedImgP &im = p.img[ii];
     const int H = im.H, W = im.W, r = im.r, span = 2 * r + 1, T2 = span * span;
     const long local = cta - im.cta0;

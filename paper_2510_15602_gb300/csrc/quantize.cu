@@ -71,8 +71,7 @@ __global__ void __launch_bounds__(kThreads) k_quantize(const __grid_constant__ Q
     __shared__ uint32_t sh[256];
     __shared__ float edge[256];
     const long cta = blockIdx.x;
-    int ii = 0;
-    while (ii + 1 < p.n && p.img[ii + 1].cta0 <= cta) ii++;
+    const int ii = table_image(p.n, cta, [&](int i) { return p.img[i].cta0; });
     const QuantImgP &im = p.img[ii];
     const int d = p.d, B = p.B, H = im.H, W = im.W;
     const long N = (long)H * W;

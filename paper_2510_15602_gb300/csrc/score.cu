@@ -188,8 +188,7 @@ __global__ void __launch_bounds__(SWT) k_window_emd(const __grid_constant__ Scor
 
     // which image, component group, band and strip
     const long cta = blockIdx.x;
-    int ii = 0;
-    while (ii + 1 < p.n && p.img[ii + 1].cta0 <= cta) ii++;
+    const int ii = table_image(p.n, cta, [&](int i) { return p.img[i].cta0; });
     const ScoreImgP im = p.img[ii];  // in registers
     const CUtensorMap *tmap = &p.tmap[ii];
     const int H = im.H, W = im.W, r = im.r;
@@ -470,8 +469,7 @@ template <typename OUT>
 __global__ void __launch_bounds__(256) k_finalize(const __grid_constant__ FinParams p) {
     __shared__ double wk[kFinMaxWeights];
     const long blk = blockIdx.x;
-    int ii = 0;
-    while (ii + 1 < p.n && p.img[ii + 1].blk0 <= blk) ii++;
+    const int ii = table_image(p.n, blk, [&](int i) { return p.img[i].blk0; });
     const FinImgP &im = p.img[ii];
     const int d = p.d;
     if (im.lo) {
