@@ -385,7 +385,7 @@ NCU_TRAFFIC = {
     "k_assoc": 35176192 + 74977024,
     "k_median_ref": 43221504,
     "k_residual": 2148438016 + 1026944256,
-    "k_project_tma": 1074511616 + 125724160,
+    "k_project_tma": 1074400256 + 124910592,
     "k_window_emd": 33870080 + 75218176,
     "k_quantize": 134453248 + 18565376,
 }
