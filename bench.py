@@ -1218,6 +1218,18 @@ def run_ours(args):
                "f1_max": round(f1_max(scores, mstack, border=R), 5),
                "note": "pooled over the 16 maps, r-pixel border discarded; every image of the batch is anomalous, "
                        "so the image-level AUROC is undefined here"}
+    # the same metrics by the GPU stage (qfca_metrics) on the device maps and masks, with its time
+    mdev = torch.from_numpy(mstack.astype(np.uint8)).cuda()
+    ctx_m = qfca.Context()  # its own workspace: the pipes' captured graphs keep theirs
+    gm = qfca.metrics(pipe.scores[0], mdev, border=R, ctx=ctx_m)  # once untimed (workspace)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(main)
+    gm = qfca.metrics(pipe.scores[0], mdev, border=R, ctx=ctx_m, stream=main)
+    ev1.record(main)
+    torch.cuda.synchronize()
+    quality["gpu_stage"] = {"pixel_auroc_border_r": round(gm["pixel_auroc"], 5), "aupro_30": round(gm["aupro"], 5),
+                            "f1_max": round(gm["f1_max"], 5), "ms": round(ev0.elapsed_time(ev1), 3),
+                            "path": "qfca_metrics: bitonic sort of the kept pixels, union-find regions, prefix sums"}
     try:  # a reporting extra: a failure here is recorded, not raised
         from paper_2510_15602_gb300 import synth
         kms = [synth.kind_masks(WORKLOAD, i) for i in indices]

@@ -283,6 +283,32 @@ typedef struct {
 qfca_status qfca_median_reference_batch(qfca_ctx *ctx, const qfca_median_image *imgs, int n, int d, int B,
                                         void *stream);
 
+/* qfca_metrics -- the evaluation of Sec. 4.2 for nimg score maps and their
+ * ground-truth masks, after discarding `border` pixels on each side of every
+ * map (the paper discards a border of the size of the window radius):
+ *   out[0]  pixel AUROC over the kept pixels of all maps (Mann-Whitney, ties
+ *           counting one half);
+ *   out[1]  F1 at the optimal threshold (maximum of 2 TP / (predicted +
+ *           anomalous) over every distinct score, score >= threshold
+ *           predicting an anomaly);
+ *   out[2]  AUPRO: the per-region overlap curve (false-positive rate over the
+ *           normal pixels; mean over the 8-connected anomalous regions of
+ *           every cropped mask of the fraction of the region at or above the
+ *           threshold) integrated by trapezoids from (0, 0) up to fpr_limit,
+ *           linearly interpolated there, divided by fpr_limit;
+ *   out[3]  image-level AUROC of the maximum of each cropped map, an image
+ *           being anomalous when its (whole) mask has an anomalous pixel.
+ * NaN where a class is empty.  Every distinct score is a threshold, so the
+ * curves are exact; integer counts are exact and the FP64 sums use a fixed
+ * order (deterministic results).
+ *   scores  device f32 [nimg][H][W];  masks device u8 [nimg][H][W], non-zero =
+ *   anomalous;  out device double[4].
+ * Requires 1 <= nimg <= 4096, 2 border < H and < W, 0 < fpr_limit <= 1 and at
+ * most 2^22 kept pixels per call (QFCA_ERR_UNSUPPORTED above).  Uses the
+ * context's workspace (about 40 bytes per kept pixel). */
+qfca_status qfca_metrics(qfca_ctx *ctx, const float *scores, const uint8_t *masks, int nimg, int H, int W, int border,
+                         double fpr_limit, double *out, void *stream);
+
 /* Synchronise the device and read-and-clear the context's device status
  * word.  Kernels whose bounded waits (on tensor-core completion, on a peer
  * stage) run out set a bit there and return early instead of hanging.

@@ -684,6 +684,29 @@ qfca_status qfca_median_reference(qfca_ctx *ctx, const uint8_t *bins, int H, int
     return run_median(ctx, &job, 1, d, B, (cudaStream_t)stream);
 }
 
+qfca_status qfca_metrics(qfca_ctx *ctx, const float *scores, const uint8_t *masks, int nimg, int H, int W, int border,
+                         double fpr_limit, double *out, void *stream) {
+    qfca_status s = check_ctx(ctx);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!scores || !masks || !out) return fail(ctx, QFCA_ERR_INVALID_ARG, "scores / masks / out NULL");
+    if (nimg < 1 || nimg > 4096) return fail(ctx, QFCA_ERR_INVALID_ARG, "nimg = %d outside [1, 4096]", nimg);
+    if (H < 1 || W < 1 || border < 0 || 2 * border >= H || 2 * border >= W)
+        return fail(ctx, QFCA_ERR_INVALID_ARG, "H x W = %d x %d with border %d leaves no pixel", H, W, border);
+    if (!(fpr_limit > 0.0 && fpr_limit <= 1.0))
+        return fail(ctx, QFCA_ERR_INVALID_ARG, "fpr_limit = %g outside (0, 1]", fpr_limit);
+    const long M = (long)nimg * (H - 2 * border) * (W - 2 * border);
+    if (M > metrics_max_pixels())
+        return fail(ctx, QFCA_ERR_UNSUPPORTED, "%ld kept pixels above the %ld one call ranks", M, metrics_max_pixels());
+    DeviceGuard g(ctx->device);
+    HookScope hs(ctx);
+    if ((s = ensure_ws(ctx, metrics_workspace_bytes(nimg, H, W, border), (cudaStream_t)stream))) return s;
+    const cudaError_t e = launch_metrics(scores, masks, nimg, H, W, border, fpr_limit, out, ctx->ws, ctx->status_dev,
+                                         (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qfca_metrics");
+    return QFCA_OK;
+}
+
 qfca_status qfca_median_reference_batch(qfca_ctx *ctx, const qfca_median_image *imgs, int n, int d, int B,
                                         void *stream) {
     qfca_status s = check_ctx(ctx);

@@ -291,6 +291,14 @@ cudaError_t make_tmap_u8_3d(void *tmap_out, const void *base, uint64_t dim0, uin
 cudaError_t make_tmap_f32_2d(void *tmap_out, const void *base, uint64_t dim0, uint64_t dim1, uint64_t stride1_bytes,
                              uint32_t box0, uint32_t box1, bool swizzle128 = false);
 
+// ------------------------------------------------------------------ evaluation metrics (metrics.cu)
+
+// Pixel AUROC, F1 max, AUPRO to fpr_limit and image-level AUROC of nimg maps (out: device double[4]).
+long metrics_max_pixels();
+size_t metrics_workspace_bytes(int nimg, int H, int W, int border);
+cudaError_t launch_metrics(const float *scores, const uint8_t *masks, int nimg, int H, int W, int border,
+                           double fpr_limit, double *out, void *ws, int *status, cudaStream_t st);
+
 // ------------------------------------------------------------------ helpers
 
 // Order-preserving map float -> u32 (larger float -> larger key).

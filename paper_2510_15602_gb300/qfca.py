@@ -87,6 +87,8 @@ _lib.qfca_batch_run.argtypes = [_P, _P, _I, Fmap, _I, _I, _I, _I, _P, ctypes.POI
 _lib.qfca_batch_run.restype = _I
 _lib.qfca_batch_run_host.argtypes = [_P, _P, _I, Fmap, _I, _I, _I, _I, _P, _P]
 _lib.qfca_batch_run_host.restype = _I
+_lib.qfca_metrics.argtypes = [_P, _P, _P, _I, _I, _I, _I, ctypes.c_double, _P, _P]
+_lib.qfca_metrics.restype = _I
 _lib.qfca_batch_run_basis.argtypes = [_P, _P, _I, Fmap, _P, _P, _I, _I, _I, _I, _P, ctypes.POINTER(BatchOutputs), _P]
 _lib.qfca_batch_run_basis.restype = _I
 _lib.qfca_last_projection_tiling.argtypes = [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]
@@ -598,6 +600,28 @@ def batch_run_host(X: torch.Tensor, d: int, B: int, r: int, precision="bf16", ct
     ctx.check(_lib.qfca_batch_run_host(ctx.handle, _P(X.data_ptr()), nimg, Fmap(H, W, C, NCHW), d, B, r,
                                        _PREC[precision], _P(scores.data_ptr()), _P(_stream_ptr(stream))))
     return scores
+
+
+def metrics(scores: torch.Tensor, masks: torch.Tensor, border: int = 0, fpr_limit: float = 0.3,
+            ctx: Context | None = None, stream=None) -> dict:
+    """qfca_metrics on device maps scores [nimg, H, W] (f32) and masks [nimg, H, W] (u8 or bool):
+    pixel AUROC, F1 max, AUPRO up to ``fpr_limit`` and image AUROC after a ``border`` discard.
+    Synchronises the stream to return the four values."""
+    _check_dev(scores, "scores", torch.float32)
+    if scores.dim() == 2:
+        scores, masks = scores[None], masks[None]
+    if masks.dtype == torch.bool:
+        masks = masks.to(torch.uint8)
+    _check_dev(masks, "masks", torch.uint8)
+    if tuple(masks.shape) != tuple(scores.shape):
+        raise ValueError("scores and masks must have the same shape [nimg, H, W]")
+    nimg, H, W = (int(v) for v in scores.shape)
+    ctx = ctx or default_context(scores.device.index)
+    out = torch.empty(4, dtype=torch.float64, device=scores.device)
+    ctx.check(_lib.qfca_metrics(ctx.handle, _ptr(scores), _ptr(masks), nimg, H, W, int(border), float(fpr_limit),
+                                _ptr(out), _P(_stream_ptr(stream))))
+    v = out.cpu().tolist()
+    return {"pixel_auroc": v[0], "f1_max": v[1], "aupro": v[2], "image_auroc": v[3]}
 
 
 def batch_run_basis(X: torch.Tensor, mean: torch.Tensor, V: torch.Tensor, B: int, r: int, precision="bf16",
