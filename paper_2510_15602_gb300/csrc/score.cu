@@ -258,12 +258,10 @@ __global__ void __launch_bounds__(SWT) k_window_emd(const __grid_constant__ Scor
                 rv[j] = b < B ? __ldg(&ref_hist[(long)k * B + b]) : 0u;
             }
         }
+        // every thread waits for the tile itself; a wait that ran out is reported at the barrier after the
+        // rewrite (one CTA barrier fewer per item), and the CTA then stops
         const bool ok = tc::mbar_wait(&bar[buf], (it >> 1) & 1, it == 0 ? p.first_wait_tries : kTmaTries);
         waited++;
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
         uint8_t *tile = tiles + (size_t)buf * p.tile_bytes;
         // in-image bytes -> min(bin, B-1) + 1, everything else -> 0; a warp per tile row
         {
@@ -314,7 +312,10 @@ __global__ void __launch_bounds__(SWT) k_window_emd(const __grid_constant__ Scor
                 for (int b = 0; b <= B; b++) hc[b * SW] = 0;
             }
         }
-        __syncthreads();
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
         if (fresh && KB == 32 && sizeof(ACC) == 4) {
             const uint32_t *c32 = reinterpret_cast<const uint32_t *>(cRi);
 #pragma unroll
