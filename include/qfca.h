@@ -311,7 +311,9 @@ qfca_status qfca_metrics(qfca_ctx *ctx, const float *scores, const uint8_t *mask
 
 /* Synchronise the device and read-and-clear the context's device status
  * word.  Kernels whose bounded waits (on tensor-core completion, on a peer
- * stage) run out set a bit there and return early instead of hanging.
+ * stage) run out set bit 0 (value 1) there and return early instead of
+ * hanging; the metric suite's union-find sets bit 4 (value 16) when one of its
+ * loops reaches its iteration limit (its results are then not valid).
  * *out receives the word; returns QFCA_ERR_TIMEOUT when it was non-zero. */
 qfca_status qfca_device_status(qfca_ctx *ctx, int *out);
 

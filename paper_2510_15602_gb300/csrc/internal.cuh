@@ -156,6 +156,7 @@ constexpr int kKeyStride = 32;
 
 // Device status word bits (set by kernels; read by qfca_device_status).
 constexpr int kStatusMmaTimeout = 1;
+constexpr int kStatusMetricsLimit = 1 << 4;  // the metric suite's union-find ran out of its iteration limit
 
 // ------------------------------------------------------------------ quantize (quantize.cu)
 

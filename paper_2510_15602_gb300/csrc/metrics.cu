@@ -37,7 +37,6 @@ namespace {
 
 constexpr int kTile = 2048;       // elements of a shared-memory bitonic tile (and of a scan block)
 constexpr int kTileThreads = 1024;
-constexpr int kStatusMetricsLimit = 1 << 4;  // a union-find loop ran out of its iteration limit
 
 struct MetCounters {
     unsigned long long u2;   // 2 U of the Mann-Whitney statistic (exact)
