@@ -380,14 +380,14 @@ def per_kind_auroc(scores, masks, kind_masks, border: int) -> dict:
 # captures summarised in profiles/<kernel>_batch16_256_c256.md; an entry is
 # removed whenever its kernel changes after the capture.
 NCU_TRAFFIC = {
-    "k_gram": 2023529216 + 14163456,
-    "k_eig32": 8524800,
-    "k_assoc": 35176192 + 74977024,
-    "k_median_ref": 43221504,
-    "k_residual": 2148438016 + 1026944256,
-    "k_project_tma": 1074400256 + 124910592,
-    "k_window_emd": 33870080 + 75218176,
-    "k_quantize": 134453248 + 18565376,
+    "k_gram": 2026978560 + 13541120,
+    "k_eig32": 8589824,
+    "k_project_tma": 1074385152 + 121330432,
+    "k_quantize": 134450688 + 15431424,
+    "k_window_emd": 33655040 + 71612160,
+    "k_assoc": 33809408 + 74420224,
+    "k_median_ref": 43260928,
+    "k_residual": 2147922432 + 1026563840,
 }
 
 

@@ -121,5 +121,7 @@ def test_metrics_full_batch_size(q):
             mk[i, y:y + 30, x:x + 20] = 1
             sc[i, y:y + 30, x:x + 20] += np.float32(0.2)
     mk[15] = 0
-    g = q.metrics(torch.from_numpy(sc).cuda(), torch.from_numpy(mk).cuda(), border=7)
+    ctx = q.Context()
+    g = q.metrics(torch.from_numpy(sc).cuda(), torch.from_numpy(mk).cuda(), border=7, ctx=ctx)
     _compare(g, _host(sc, mk, 7))
+    assert ctx.device_status() == 0  # no union-find loop reached its limit
