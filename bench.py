@@ -670,8 +670,8 @@ def run_basis_resident(qfca, torch, X_dev, args, peaks):
             "roofline_isolated_step": path_roofline(single_ms, N_IMG, HW, HW, C, D, B, R, peaks)}
 
 
-def run_config1(qfca, torch, args):
-    """Config 1: one 128 x 128 x C64 map, d = 16, B = 16, r = 4, FP32 projection,
+def run_plain_single_image(qfca, torch, args):
+    """The plain single-image workload: one 128 x 128 x C64 map, d = 16, B = 16, r = 4, FP32 projection,
     one image per call sequence (fit, quantize, score) on one stream; maps/s,
     per-image latency, and the oracle's bins, score and AUROC beside it."""
     import numpy as np
@@ -729,7 +729,7 @@ def run_config1(qfca, torch, args):
 
 
 def run_precision_sweep(qfca, torch):
-    """Config 3: config 1's image with the projection in FP32, BF16 and FP8 e4m3
+    """The precision sweep on the plain 128 x 128 x C64 image: the projection in FP32, BF16 and FP8 e4m3
     (per-channel power-of-two scales), FP32 accumulation, the same fitted basis;
     against the FP64 oracle: bin-flip rate, max/mean score-map error, pixel AUROC."""
     import numpy as np
@@ -1268,9 +1268,9 @@ def run_ours(args):
                **host_cpu()}
         aurocs_oracle = [auroc(oscores[i], masks[i]) for i in range(N_IMG)]
 
-    # ---- the basis-resident unit, config 1 and the precision sweep (config 3)
+    # ---- the basis-resident unit, the plain single-image workload and its precision sweep
     basis_res = run_basis_resident(qfca, torch, X_dev, args, peaks) if extra else None
-    cfg1 = run_config1(qfca, torch, args) if extra else None
+    plain = run_plain_single_image(qfca, torch, args) if extra else None
     sweep = run_precision_sweep(qfca, torch) if extra else None
 
     paper = run_paper_scoring(qfca, torch, pipe, masks, args) if extra and not args.skip_paper else None
@@ -1319,8 +1319,8 @@ def run_ours(args):
                       "images": N_IMG},
             "long_run": long_run,
             "basis_resident": basis_res,
-            "config1_fp32_single_image": cfg1,
-            "precision_sweep_config3": sweep,
+            "plain_128_c64_fp32_single_image": plain,
+            "precision_sweep_plain_128_c64": sweep,
             "metrics": quality,
             "kernel_ms_per_step": {k: round(v[0], 3) for k, v in sorted(agg.items(), key=lambda kv: -kv[1][0])},
             "paper_scoring": paper,

@@ -83,7 +83,7 @@ def test_assoc_matches_oracle(q, d, H, W, B, r, seed):
     check(q, qb, B, r)
 
 
-def test_assoc_config1_shape_with_planted_square(q):
+def test_assoc_plain_128_c64_with_planted_square(q):
     # 128 x 128, d = 16, B = 16, r = 4: the small single-image workload
     rng = np.random.default_rng(41)
     qb = synth.random_bins(rng, 16, 128, 128, 16, smooth=True)

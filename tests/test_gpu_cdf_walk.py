@@ -38,7 +38,7 @@ def _case(q, d, H, W, B, r, seed):
 
 
 # ragged widths (lanes past the image), one-row and one-column-band images, windows
-# wider than the image, the config-2 radius and larger ones
+# wider than the image, the 15 x 15 window's radius and larger ones
 @pytest.mark.parametrize("d,H,W,B,r,seed", [(5, 70, 150, 32, 7, 0), (32, 64, 64, 32, 7, 1), (3, 1, 45, 32, 3, 2),
                                             (2, 40, 7, 32, 12, 3), (4, 97, 131, 32, 1, 4), (2, 60, 200, 32, 20, 5)])
 def test_both_walks_give_the_same_map(q, d, H, W, B, r, seed):

@@ -265,7 +265,7 @@ def test_covariance_exact_slices_against_oracle(q, C, H, W, layout):
 # ------------------------------------------------------------------ the whole path
 
 @pytest.mark.parametrize("layout", [0, 1])
-def test_pipeline_fp32_config1(q, layout):
+def test_pipeline_fp32_plain_128_c64(q, layout):
     img = synth.make_image("plain_128_c64", 0)
     d, B, r = 16, 16, 4
     ref = oracle.pipeline(img.X, d, B, r)
@@ -370,7 +370,7 @@ def test_project_bf16_matches_rounded_operands(q, C, H, W, d, layout):
     np.testing.assert_array_equal(bins_np(out["bins"], W), qb)
 
 
-def test_bf16_flips_and_auroc_config1(q):
+def test_bf16_flips_and_auroc_plain_128_c64(q):
     img = synth.make_image("plain_128_c64", 0)
     d, B, r = 16, 16, 4
     ref = oracle.pipeline(img.X, d, B, r)
@@ -573,7 +573,7 @@ def test_project_fp8_matches_rounded_operands(q, C, H, W, d):
     np.testing.assert_array_equal(bins_np(out["bins"], W), qb)
 
 
-def test_fp8_precision_sweep_config1(q):
+def test_fp8_precision_sweep_plain_128_c64(q):
     # precision sweep on the single-image workload: FP32 / BF16 / FP8 projection
     # against the FP64 oracle (bin flips, score error, AUROC)
     img = synth.make_image("plain_128_c64", 0)
