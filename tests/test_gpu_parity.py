@@ -478,6 +478,26 @@ def test_score_batch_uneven_equals_single_image_calls(q, precision):
     assert ctx.device_status() == 0
 
 
+def test_score_batch_uneven_c512_equals_single_image_calls(q):
+    # C = 512 (the float-float cluster solver, the TMA projection's image cursor over a table of
+    # mixed sizes, B = 64, mixed radii): the batch equals the single-image calls bit for bit
+    C, d, B = 512, 32, 64
+    sizes = [(40, 48), (32, 56), (48, 40)]
+    rs = [5, 12, 9]
+    imgs = _uneven_images(C, sizes, 130)
+    Xs = [to_dev(im.X) for im in imgs]
+    ctx = q.Context()
+    sb = q.score_batch(Xs, rs, d, B, "bf16", ctx=ctx)
+    torch.cuda.synchronize()
+    for i, (X, (H, W), r) in enumerate(zip(Xs, sizes, rs)):
+        basis = q.fit_pca(X, d, ctx=ctx)
+        out = q.quantize(X, basis, B, "bf16", ctx=ctx)
+        s1 = q.score(out["bins"], W, B, r, out["hist"], H * W, ctx=ctx)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(sb[i].cpu().numpy(), s1.cpu().numpy())
+    assert ctx.device_status() == 0
+
+
 def test_score_batch_uneven_integer_stages_against_oracle(q):
     # one image of the batch checked end to end: eigenvalues against the
     # oracle's fit, and the oracle's window EMD on the GPU's own bins
