@@ -1372,6 +1372,27 @@ def run_profile_batch(args):
     return 0 if ctx.device_status() == 0 else 1
 
 
+def run_profile_uneven(args):
+    """A short fixed run for profilers: the 64-image uneven batch through qfca_score_batch, once
+    untimed (the autotuner measures the window tilings), then `args.profile_uneven` calls inside
+    the profiler range (cudaProfilerStart/Stop; run ncu with --profile-from-start off)."""
+    host = _pool_map(_gen_uneven, list(range(UNEVEN_N)))
+    import torch
+    from paper_2510_15602_gb300 import qfca
+    Xs = [torch.from_numpy(x).cuda() for x, _, _ in host]
+    rs = [r for _, _, r in host]
+    ctx = qfca.Context()
+    ctx.set_autotune(True)
+    qfca.score_batch(Xs, rs, D, UNEVEN_B, "bf16", ctx=ctx)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for _ in range(args.profile_uneven):
+        qfca.score_batch(Xs, rs, D, UNEVEN_B, "bf16", ctx=ctx)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    return 0 if ctx.device_status() == 0 else 1
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1395,6 +1416,8 @@ def main(argv=None):
                          "median reference and QFCA+ on the batch")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="only run this many batches through qfca_batch_run (for profilers), then exit")
+    ap.add_argument("--profile-uneven", type=int, default=0,
+                    help="only run this many 64-image uneven batches through qfca_score_batch (for profilers)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args(argv)
@@ -1402,6 +1425,8 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_uneven:
+        return run_profile_uneven(args)
     if args.profile_batch or args.profile_paper:
         return run_profile_batch(args)
     return run_ours(args)
