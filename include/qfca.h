@@ -298,9 +298,10 @@ qfca_status qfca_median_reference_batch(qfca_ctx *ctx, const qfca_median_image *
  *           linearly interpolated there, divided by fpr_limit;
  *   out[3]  image-level AUROC of the maximum of each cropped map, an image
  *           being anomalous when its (whole) mask has an anomalous pixel.
- * NaN where a class is empty.  Every distinct score is a threshold, so the
- * curves are exact; integer counts are exact and the FP64 sums use a fixed
- * order (deterministic results).
+ * NaN where a class is empty.  Every distinct score is a threshold (-0 and
+ * +0 being one score; scores must not be NaN), so the curves are exact;
+ * integer counts are exact and the FP64 sums use a fixed order
+ * (deterministic results).
  *   scores  device f32 [nimg][H][W];  masks device u8 [nimg][H][W], non-zero =
  *   anomalous;  out device double[4].
  * Requires 1 <= nimg <= 4096, 2 border < H and < W, 0 < fpr_limit <= 1 and at

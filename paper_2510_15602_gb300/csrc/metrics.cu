@@ -68,7 +68,9 @@ __global__ void k_met_init(const float *__restrict__ scores, const uint8_t *__re
         const long img = p / hw, rem = p - img * hw;
         const int y = (int)(rem / w) + border, x = (int)(rem % w) + border;
         const long src = (img * H + y) * (long)W + x;
-        const uint32_t key = ~f2key(scores[src]);  // ascending key order = descending score
+        // -0 and +0 are one score: adding +0 maps -0 to +0 (round to nearest) and leaves every
+        // other value as it is, so equal scores share one key
+        const uint32_t key = ~f2key(__fadd_rn(scores[src], 0.0f));  // ascending key order = descending score
         keys[p] = (unsigned long long)key << 32 | (unsigned long long)p;
         const bool m = masks[src] != 0;
         parent[p] = m ? (int)p : -1;

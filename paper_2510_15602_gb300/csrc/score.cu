@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(SWT) k_window_emd(const __grid_constant__ Scor
         unsigned long long *accum_col = im.accum ? im.accum + x : nullptr;
         // window of the band's first row (tile rows 1 .. 2r+1), or the previous band's last window continued
         if (fresh && xin)
-            for (int ry = 1; ry <= span; ry++) window_rows<SW, false>(nullptr, tile + ry * TCp, c0, span, hbase);
+            for (int ry = 1; ry <= span; ry++) window_rows<SW, false>(tile + ry * TCp, tile + ry * TCp, c0, span, hbase);  // rowo unused
         for (int i = 0; i < TH; i++) {
             const int yy = y0 + i;
             if (yy >= H) break;

@@ -125,3 +125,19 @@ def test_metrics_full_batch_size(q):
     g = q.metrics(torch.from_numpy(sc).cuda(), torch.from_numpy(mk).cuda(), border=7, ctx=ctx)
     _compare(g, _host(sc, mk, 7))
     assert ctx.device_status() == 0  # no union-find loop reached its limit
+
+
+def test_metrics_signed_zero_scores_are_one_threshold(q):
+    # -0 and +0 are one score value: a run of ties across both signs, on anomalous and normal pixels
+    rng = np.random.default_rng(21)
+    sc = (np.floor(rng.random((3, 24, 20)) * 4) / 4).astype(np.float32)  # 0, 0.25, 0.5, 0.75
+    sc[(sc == 0) & (rng.random(sc.shape) < 0.5)] = np.float32(-0.0)    # about half the zeros become -0
+    assert np.signbit(sc[sc == 0]).any() and (~np.signbit(sc[sc == 0])).any()
+    mk = np.zeros(sc.shape, np.uint8)
+    mk[0, 4:12, 3:9] = 1
+    mk[1, 10:20, 10:18] = 1
+    g = q.metrics(torch.from_numpy(sc).cuda(), torch.from_numpy(mk).cuda(), border=2)
+    _compare(g, _host(sc, mk, 2))
+    # the same maps with every zero positive give the same metrics bit for bit
+    g0 = q.metrics(torch.from_numpy(np.where(sc == 0, np.float32(0.0), sc)).cuda(), torch.from_numpy(mk).cuda(), border=2)
+    assert g == g0
