@@ -76,6 +76,24 @@ def test_scores_against_the_median_reference(q):
     np.testing.assert_allclose(s_g, s_o, rtol=2.0 ** -20, atol=4 * 2.0 ** -24 * (B - 1) + 2.0 ** -21)
 
 
+def test_median_reference_full_size_batch_sampled(q):
+    # the benchmark's launch: 16 images of 32 x 256 x 256 bins, B = 32, r = 7, one batched call.
+    # Each component's reference depends on its own plane only, so sampled planes of the first
+    # and last image are checked bit for bit against the oracle, and every row of every image
+    # counts each of the (2r + 1)^2-pixel windows once
+    n, d, H, W, B, r = 16, 32, 256, 256, 32, 7
+    rng = np.random.default_rng(430)
+    qbs = [synth.random_bins(rng, d, H, W, B, smooth=True) for _ in range(n)]
+    outs = q.median_reference_batch([dev_bins(q, qb) for qb in qbs], [W] * n, [r] * n, B)
+    torch.cuda.synchronize()
+    for o in outs:
+        assert (o.cpu().numpy().astype(np.int64).sum(axis=1) == (2 * r + 1) ** 2).all()
+    planes = [0, 17, d - 1]
+    for i in (0, n - 1):
+        R_o = oracle.median_ref(np.ascontiguousarray(qbs[i][planes]), B, r)
+        np.testing.assert_array_equal(outs[i].cpu().numpy().astype(np.uint32)[planes], R_o)
+
+
 def test_median_reference_rejects_bad_arguments(q):
     bins = torch.zeros(1, 8, 16, dtype=torch.uint8, device="cuda")
     with pytest.raises(RuntimeError):
