@@ -152,6 +152,21 @@ def test_assoc_full_size_256_c32(q):
     check(q, qb, 32, 7)
 
 
+def test_assoc_full_size_batch_equals_single_calls(q):
+    # the benchmark's launch: 16 images of 32 x 256 x 256 bins, B = 32, r = 7, each image's own
+    # global histogram as reference, one batched call; images 0, 7 and 15 equal the single-image
+    # call (itself checked against the oracle at this size above) bit for bit
+    n, d, H, W, B, r = 16, 32, 256, 256, 32, 7
+    rng = np.random.default_rng(49)
+    qbs = [synth.random_bins(rng, d, H, W, B, smooth=True) for _ in range(n)]
+    bl = [dev_bins(q, qb) for qb in qbs]
+    Rs = [to_dev(oracle.ref_hist(qb, B).astype(np.int32)) for qb in qbs]
+    outs = q.score_assoc_batch(bl, [W] * n, [r] * n, B, Rs, [H * W] * n, sigma_s=1.0)
+    for i in (0, 7, n - 1):
+        single = q.score_assoc(bl[i], W, B, r, Rs[i], H * W, sigma_s=1.0)
+        torch.testing.assert_close(outs[i], single, rtol=0, atol=0)
+
+
 def test_assoc_rejects_bad_arguments(q):
     bins = torch.zeros(1, 8, 16, dtype=torch.uint8, device="cuda")
     R = torch.zeros(1, 8, dtype=torch.int32, device="cuda")
